@@ -1,0 +1,234 @@
+/*
+ * lindblad_gb300.h -- C ABI of the GB300 (sm_103a) implicit-midpoint Lindblad
+ * library: forward integration of the vectorised Lindblad master equation of
+ * a composite qudit system, the objective, and its exact discrete-adjoint
+ * gradient with respect to the B-spline control coefficients.
+ *
+ * The method (Guenther, Petersson, DuBois, "Quandary", arXiv:2110.10310):
+ *   - model: Sec. II, master equation (mastereq), collapse operators
+ *     L_1q = a_q/sqrt(T1), L_2q = a_q^+ a_q/sqrt(T2), cross-Kerr H_sys,
+ *     rotating-frame control Hamiltonian H_c = sum_q d_q a_q + conj(d_q) a_q^+;
+ *   - controls: eq. rotctrl, d_q(t) = sum_s S_s(t) sum_f alpha_q^{s,f} e^{i Omega_q^f t},
+ *     quadratic B-splines with knot spacing T/(N_s - 2);
+ *   - time stepping: Appendix A, eqs. mastereq_vectorized, IMR, linsystem_primal;
+ *   - objective: Sec. III, eq. optimproblem with J_Frob or J_Tr (gamma1 = 0);
+ *   - gradient: Appendix B, adjoint IMR, eq. linsystem_adjoint, eq. reducedgradient.
+ *
+ * Conventions shared by every call
+ *   Units: frequencies are given as value/2pi in GHz, times in ns, T1/T2 in
+ *     microseconds.  The library multiplies frequencies by 2pi.
+ *   Ordering: subsystem 0 is the most significant digit of a basis index.
+ *   Density matrices: M x N x N complex FP64, interleaved (re, im), COLUMN-major
+ *     per matrix, i.e. element rho_i[k, l] is at double offset
+ *     2 * (i * N * N + k + N * l).  This is vec(rho) of Appendix A (column
+ *     stacking), so a state is exactly the vector q the method integrates.
+ *   Control vector alpha: doubles laid out [q][f][s][re, im]; its length is
+ *     2 * sum_q N_s * N_f(q).
+ *   Return codes: LB_OK (0) or one of the LB_E* codes below.  On failure no
+ *     output argument is written and lb_last_error() (thread-local) describes
+ *     the cause; for LB_ENOTCONV and LB_ENAN it names the time step.
+ *   Ownership: the library copies every host array it is given; the caller
+ *     keeps ownership of its buffers.  Device memory is always provided by the
+ *     caller (lb_workspace_bytes + lb_bind_workspace); the library never
+ *     allocates device memory.
+ *   Streams: every device call is asynchronous on the given CUDA stream
+ *     (cudaStream_t passed as void*; NULL = legacy default stream) except where
+ *     a host output is requested, in which case the call synchronises that
+ *     stream before returning.
+ *   Threads: a handle is not thread-safe; use one handle per host thread/stream.
+ */
+#ifndef LINDBLAD_GB300_H
+#define LINDBLAD_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define LB_OK 0
+#define LB_EINVAL 1    /* invalid argument or call order */
+#define LB_ENOMEM 2    /* workspace too small, or host allocation failed */
+#define LB_ECUDA 3     /* a CUDA runtime call failed */
+#define LB_ENOTCONV 4  /* the inner solve of some step did not converge within max_iter */
+#define LB_ENAN 5      /* a state became NaN or Inf */
+
+/* merit functionals, Sec. III */
+#define LB_J_FROB 0 /* J = 1/2 ||rho_tar - rho||_F^2 */
+#define LB_J_TR 1   /* J = 1 - Re Tr(rho_tar^+ rho) */
+
+/* inner solvers for (I - dt/2 M) z = q, Appendix A.  The paper uses GMRES;
+ * this library uses fixed-point iterations that converge to the same unique z:
+ *   LB_SOLVER_JACOBI: z <- (I - dt/2 D)^-1 (q + dt/2 O z), D the diagonal of M
+ *                     and O = M - D (the default; contraction ~ dt/2 |O|).
+ *   LB_SOLVER_NEUMANN: z <- q + dt/2 M z (plain Neumann series).
+ * LB_SOLVER_AUTO picks JACOBI. */
+#define LB_SOLVER_AUTO 0
+#define LB_SOLVER_JACOBI 1
+#define LB_SOLVER_NEUMANN 2
+
+#define LB_MAX_SUBSYSTEMS 8 /* Q <= 8 */
+#define LB_MAX_LEVELS 16    /* n_q <= 16 */
+
+typedef struct lb_system lb_system;
+typedef struct lb_batch lb_batch;
+
+/* System description (Sec. II).  All arrays are host memory and are copied. */
+typedef struct lb_system_desc {
+  int32_t Q;                   /* number of subsystems, 1..LB_MAX_SUBSYSTEMS */
+  const int32_t* levels;       /* [Q] n_q >= 2 */
+  const int32_t* essential;    /* [Q] essential levels per subsystem (gate objectives), NULL = all */
+  const double* detuning_ghz;  /* [Q] (omega_q - omega_q^rot)/2pi */
+  const double* selfkerr_ghz;  /* [Q] xi_q/2pi of -xi_q/2 a^+a^+aa, NULL = 0 */
+  const double* crosskerr_ghz; /* [Q*Q] row-major; entry [p*Q+q], p<q, is xi_pq/2pi of -xi_pq n_p n_q; NULL = 0 */
+  const double* t1_us;         /* [Q] decay time; <= 0 or inf switches L_1q off; NULL = all off */
+  const double* t2_us;         /* [Q] dephasing time; <= 0 or inf switches L_2q off; NULL = all off */
+  double T_ns;                 /* final time T > 0 */
+  int64_t n_steps;             /* N_T >= 1; dt = T/N_T (uniform grid, Appendix A) */
+} lb_system_desc;
+
+/* Solver statistics of the last lb_forward / lb_gradient / lb_propagate.
+ * Phases: 0 = forward sweep, 1 = recompute of checkpoint segments, 2 = adjoint
+ * steps (which also evaluate the gradient pieces of eq. reducedgradient). */
+typedef struct lb_stats {
+  int64_t state_steps;      /* state-steps integrated, all phases */
+  int64_t inner_iterations; /* fixed-point iterations summed over those state-steps */
+  int32_t max_iterations;   /* largest iteration count of any single step */
+  int32_t kernel_launches;  /* kernels launched by the call */
+  int64_t phase_steps[3];   /* state-steps per phase */
+  int64_t phase_iterations[3];
+  float ms_forward;         /* device time of the forward-sweep kernel (lb_set_timing on, else 0) */
+  float ms_backward;        /* device time of the backward-sweep kernel (recompute + adjoint) */
+} lb_stats;
+
+/* ---- system ------------------------------------------------------------- */
+
+/* Create a system from its description (Sec. II).  Errors: LB_EINVAL for
+ * Q, levels, N_T or T out of range, or N = prod(n_q) > 2^15. */
+int lb_system_create(const lb_system_desc* desc, lb_system** out);
+void lb_system_destroy(lb_system* sys);
+
+/* Control parameterisation, eq. rotctrl: n_splines >= 3 quadratic B-splines
+ * per subsystem and n_carriers[q] >= 1 carrier frequencies for subsystem q;
+ * carrier_ghz holds Omega_q^f/2pi for all q, f, concatenated in q-major order.
+ * Resets alpha to zero. */
+int lb_controls_define(lb_system* sys, int32_t n_splines, const int32_t* n_carriers, const double* carrier_ghz);
+
+/* Set the control vector alpha (host, length n = 2 sum_q N_s N_f(q); layout
+ * [q][f][s][re, im], GHz).  If a workspace is bound, the copy to the device
+ * is issued on the bound stream before returning. */
+int lb_controls_set(lb_system* sys, const double* alpha, int64_t n);
+
+/* Initial states rho_i(0), i < M (host, M x N x N complex, column-major) and
+ * weights beta_i (host, [M], NULL = all 1).  The objective divides by M
+ * (eq. optimproblem).  M may only change while no workspace is bound.  If a
+ * workspace is bound, the copy to the device is issued before returning. */
+int lb_states_set(lb_system* sys, int32_t M, const double* rho0, const double* weights);
+
+/* Objective with explicit targets rho_i^tar (host, M x N x N complex,
+ * column-major; call after lb_states_set) and Tikhonov weight gamma2 >= 0. */
+int lb_objective_set(lb_system* sys, int32_t kind, const double* targets, double gamma2);
+
+/* Gate objective (Sec. III-C): rho_i^tar = V rho_i(0) V^+ with V (host,
+ * Ne x Ne complex, interleaved, column-major, Ne = prod essential levels)
+ * lifted to the full space by the isometry that maps essential digits to the
+ * same digits of the full space (zero on guard levels).  Uses the states set
+ * by lb_states_set; the targets are computed on the device. */
+int lb_objective_set_gate(lb_system* sys, int32_t kind, const double* V, double gamma2);
+
+/* Inner solver and checkpointing.  rtol: stop when
+ * max|z_new - z| <= rtol * max|q| (componentwise, per state); max_iter caps the
+ * iterations of one step (LB_ENOTCONV beyond); ckpt_every = K >= 1 stores the
+ * forward state every K steps and recomputes each K-step segment in the
+ * backward sweep; K = 0 stores every stage vector z^j instead (no recompute).
+ * Defaults: LB_SOLVER_AUTO, 1e-15, 200, 100.  Call before lb_workspace_bytes. */
+int lb_solver_set(lb_system* sys, int32_t method, double rtol, int32_t max_iter, int32_t ckpt_every);
+
+/* ---- device workspace ---------------------------------------------------- */
+
+/* Bytes of device memory the system needs (depends on N, M, N_T, Q, the
+ * control layout and ckpt_every). */
+int lb_workspace_bytes(const lb_system* sys, size_t* bytes);
+
+/* Bind caller-owned device memory (256-byte aligned, >= lb_workspace_bytes)
+ * and upload every table, state, target and the controls on `stream`.
+ * The memory must stay valid until the system is destroyed or rebound. */
+int lb_bind_workspace(lb_system* sys, void* dev_workspace, size_t bytes, void* stream);
+
+/* ---- the method ---------------------------------------------------------- */
+
+/* Forward sweep over the whole horizon for all M states, then the objective
+ * G (eq. optimproblem).  G_out (host, nullable) receives G; rhoT_dev_out
+ * (device, nullable, M x N x N complex) receives rho_i(T). */
+int lb_forward(lb_system* sys, void* stream, double* G_out, void* rhoT_dev_out);
+
+/* Forward sweep with checkpoints, then the discrete adjoint sweep (Appendix B)
+ * with the reduced gradient.  G_out (host, nullable) receives G; grad_out
+ * (host, nullable, length of alpha) receives dG/dalpha. */
+int lb_gradient(lb_system* sys, void* stream, double* G_out, double* grad_out);
+
+/* Device-resident variant of lb_gradient: G and the gradient are written to
+ * device memory (G_dev: 1 double, grad_dev: length of alpha) and the call
+ * does not synchronise; errors of the device sweep are reported by the next
+ * synchronising call. */
+int lb_gradient_async(lb_system* sys, void* stream, void* G_dev, void* grad_dev);
+
+/* Advance n_vec device vectors x (n_vec x N x N complex, column-major) from
+ * step j0 to step j1 (0 <= j0 <= j1 <= N_T) with the implicit midpoint rule
+ * (adjoint = 0), or apply the adjoint steps j1-1 down to j0 to them
+ * (adjoint = 1: (I - dt/2 M^+) zhat = x, x <- 2 zhat - x).  In place. */
+int lb_propagate(lb_system* sys, void* stream, int32_t adjoint, int64_t j0, int64_t j1, void* x_dev, int32_t n_vec);
+
+/* y = M^{j+1/2} x (adjoint = 0) or y = (M^{j+1/2})^+ x (adjoint = 1) for
+ * n_vec device vectors (Appendix A, eq. mastereq_vectorized), with
+ * M^{j+1/2} = M(t_j + dt/2); x and y must not overlap. */
+int lb_apply(lb_system* sys, void* stream, int32_t adjoint, int64_t step, const void* x_dev, void* y_dev,
+             int32_t n_vec);
+
+/* Statistics of the last forward / gradient / propagate call. */
+int lb_get_stats(lb_system* sys, lb_stats* out);
+
+/* on != 0: record CUDA events around the sweep kernels on the launching
+ * stream and report their device time in lb_stats (ms_forward, ms_backward)
+ * after the next synchronising call. */
+int lb_set_timing(lb_system* sys, int32_t on);
+
+/* ---- batches of independent problems ------------------------------------- */
+
+/* A batch of n >= 1 independent systems, each already bound to its own
+ * workspace, advanced together in one persistent launch per sweep (the
+ * paper's first level of parallelism, Sec. V).  The batch needs a small
+ * workspace of its own. */
+int lb_batch_create(lb_system* const* systems, int32_t n, lb_batch** out);
+void lb_batch_destroy(lb_batch* batch);
+int lb_batch_workspace_bytes(const lb_batch* batch, size_t* bytes);
+int lb_batch_bind_workspace(lb_batch* batch, void* dev_workspace, size_t bytes, void* stream);
+
+/* G_out (host, nullable, [n]) per system; grad_out (host, nullable) the
+ * gradients of all systems concatenated in batch order. */
+int lb_batch_forward(lb_batch* batch, void* stream, double* G_out);
+int lb_batch_gradient(lb_batch* batch, void* stream, double* G_out, double* grad_out);
+
+/* Capture the device work of lb_batch_forward (mode 0) or lb_batch_gradient
+ * (mode 1) into a CUDA graph; later calls of that mode replay the graph.
+ * mode -1 drops the graphs. */
+int lb_batch_capture_graph(lb_batch* batch, void* stream, int32_t mode);
+
+/* Statistics summed over the batch's last call. */
+int lb_batch_get_stats(lb_batch* batch, lb_stats* out);
+
+/* ---- diagnostics --------------------------------------------------------- */
+
+/* Description of the last error of the calling thread ("" if none). */
+const char* lb_last_error(void);
+
+/* Library version string. */
+const char* lb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LINDBLAD_GB300_H */

@@ -1,0 +1,987 @@
+// Host side of the C ABI declared in include/lindblad_gb300.h.
+//
+// The library never allocates device memory: a system computes its workspace
+// size, the caller binds device memory, and every table, state and result
+// lives in that workspace.  Kernels are launched on the caller's stream.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lb_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(LB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define LB_CUDA(call, where)                          \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, where); \
+  } while (0)
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// One region of the workspace.
+struct Region {
+  size_t off = 0, bytes = 0;
+};
+
+struct Layout {
+  Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
+      gproj, J, G, grad, gateV, emap, efull;
+  size_t total = 0;
+};
+
+}  // namespace
+
+struct lb_system {
+  // description (Sec. II), frequencies in rad/ns, rates in 1/ns
+  int Q = 0;
+  int levels[LB_MAXQ] = {};
+  int essential[LB_MAXQ] = {};
+  double det[LB_MAXQ] = {}, kerr[LB_MAXQ] = {}, g1[LB_MAXQ] = {}, g2[LB_MAXQ] = {};
+  double xkerr[LB_MAXQ * LB_MAXQ] = {};
+  double T = 0.0, h = 0.0;
+  int64_t NT = 0;
+  int N = 0, V = 0, Ne = 0;
+  // controls (eq. rotctrl)
+  bool ctrl_defined = false;
+  int Ns = 0;
+  int nf[LB_MAXQ] = {};
+  std::vector<double> carriers;  // rad/ns
+  std::vector<double> alpha;     // GHz, [q][f][s][re, im]
+  int n_params = 0;
+  // states and objective (Sec. III)
+  int M = 0;
+  std::vector<double> rho0;  // kept only while no workspace is bound
+  std::vector<double> wgt;   // beta_i / M
+  int kind = LB_J_FROB;
+  int target_mode = 0;  // 0 none, 1 explicit, 2 gate
+  std::vector<double> targets;
+  std::vector<double> gateV;
+  double gamma2 = 0.0;
+  // solver
+  int method = LB_SOLVER_JACOBI;
+  double rtol = 1e-15;
+  int max_iter = 200;
+  int K = 100;
+  // device binding
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t bind_stream = nullptr;
+  cudaEvent_t upload_done = nullptr;
+  Layout L;
+  ProbDev hp{};
+  ProbDev* dp = nullptr;
+  WorkItem* d_items = nullptr;
+  lbk::ResidentConfig rc{};
+  bool ctab_dirty = true;
+  lb_stats last{};
+  int launches = 0;
+  bool timing = false;
+  bool timed_fwd = false, timed_bwd = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // forward start/end, backward start/end
+};
+
+struct lb_batch {
+  std::vector<lb_system*> sys;
+  std::vector<int64_t> grad_off;
+  int64_t n_grad = 0;
+  int n_items = 0;
+  int max_param_warps = 0;
+  lbk::ResidentConfig rc{};
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  ProbDev* d_probs = nullptr;
+  WorkItem* d_items = nullptr;
+  int64_t* d_grad_off = nullptr;
+  double* d_G = nullptr;
+  double* d_grad = nullptr;
+  DevStatus* d_st = nullptr;
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  lb_stats last{};
+};
+
+namespace {
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+int n_coef(const lb_system* s) {
+  int n = 0;
+  for (int q = 0; q < s->Q; ++q) n += s->levels[q];
+  return n;
+}
+int n_jcoef(const lb_system* s) {
+  int n = 0;
+  for (int q = 0; q < s->Q; ++q) n += s->levels[q] * s->levels[q];
+  return n;
+}
+int n_carriers_total(const lb_system* s) {
+  int n = 0;
+  for (int q = 0; q < s->Q; ++q) n += s->nf[q];
+  return n;
+}
+
+Layout make_layout(const lb_system* s) {
+  Layout L;
+  size_t off = 0;
+  auto take = [&](Region& r, size_t bytes) {
+    r.off = off;
+    r.bytes = bytes;
+    off += align_up(bytes ? bytes : 1);
+  };
+  const size_t V = (size_t)s->V, M = (size_t)s->M, NT = (size_t)s->NT;
+  const size_t c2 = sizeof(double2);
+  take(L.prob, sizeof(ProbDev));
+  take(L.status, sizeof(DevStatus));
+  take(L.items, sizeof(WorkItem) * M);
+  take(L.sysp, sizeof(double) * (4 * s->Q + s->Q * s->Q));
+  take(L.cu, sizeof(double) * n_coef(s));
+  take(L.cd, sizeof(double) * n_coef(s));
+  take(L.jf, sizeof(double) * n_jcoef(s));
+  take(L.ja, sizeof(double) * n_jcoef(s));
+  take(L.digits, sizeof(uint32_t) * s->N);
+  take(L.D, c2 * V);
+  take(L.Dinv, c2 * V);
+  take(L.alpha, sizeof(double) * s->n_params);
+  take(L.carriers, sizeof(double) * n_carriers_total(s));
+  take(L.ctab, c2 * NT * s->Q);
+  take(L.q0, c2 * M * V);
+  take(L.tar, c2 * M * V);
+  take(L.wgt, sizeof(double) * M);
+  take(L.qT, c2 * M * V);
+  const size_t nck = s->K > 0 ? (NT + s->K - 1) / s->K : NT;
+  take(L.ckpt, c2 * M * nck * V);
+  take(L.seg, s->K > 0 ? c2 * M * (size_t)s->K * V : 0);
+  take(L.gproj, c2 * M * NT * s->Q * 2);
+  take(L.J, sizeof(double) * M);
+  take(L.G, sizeof(double));
+  take(L.grad, sizeof(double) * s->n_params);
+  const size_t Ne = (size_t)s->Ne;
+  take(L.gateV, s->target_mode == 2 ? c2 * Ne * Ne : 0);
+  take(L.emap, s->target_mode == 2 ? sizeof(int32_t) * s->N : 0);
+  take(L.efull, s->target_mode == 2 ? sizeof(int32_t) * Ne : 0);
+  L.total = off;
+  return L;
+}
+
+template <class T>
+T* at(const lb_system* s, const Region& r) {
+  return reinterpret_cast<T*>(s->ws + r.off);
+}
+
+int check_ready(const lb_system* s, bool need_bound) {
+  if (!s) return fail(LB_EINVAL, "null system handle");
+  if (!s->ctrl_defined) return fail(LB_EINVAL, "controls not defined (lb_controls_define)");
+  if (s->M <= 0) return fail(LB_EINVAL, "no initial states (lb_states_set)");
+  if (need_bound && !s->ws) return fail(LB_EINVAL, "no workspace bound (lb_bind_workspace)");
+  return LB_OK;
+}
+
+// Make `stream` wait for the uploads issued on the bind stream.
+int order_after_uploads(lb_system* s, cudaStream_t stream) {
+  if (stream == s->bind_stream) return LB_OK;
+  LB_CUDA(cudaEventRecord(s->upload_done, s->bind_stream), "cudaEventRecord");
+  LB_CUDA(cudaStreamWaitEvent(stream, s->upload_done, 0), "cudaStreamWaitEvent");
+  return LB_OK;
+}
+
+int upload_states(lb_system* s, const double* rho0, cudaStream_t st) {
+  const size_t bytes = sizeof(double2) * (size_t)s->M * s->V;
+  LB_CUDA(cudaMemcpyAsync(at<double2>(s, s->L.q0), rho0, bytes, cudaMemcpyHostToDevice, st), "upload states");
+  LB_CUDA(cudaMemcpyAsync(at<double>(s, s->L.wgt), s->wgt.data(), sizeof(double) * s->M, cudaMemcpyHostToDevice, st),
+          "upload weights");
+  return LB_OK;
+}
+
+int upload_targets(lb_system* s, cudaStream_t st) {
+  const size_t bytes = sizeof(double2) * (size_t)s->M * s->V;
+  if (s->target_mode == 1) {
+    LB_CUDA(cudaMemcpyAsync(at<double2>(s, s->L.tar), s->targets.data(), bytes, cudaMemcpyHostToDevice, st),
+            "upload targets");
+  } else if (s->target_mode == 2) {
+    // essential <-> full index maps (subsystem 0 most significant)
+    std::vector<int32_t> emap(s->N, -1), efull(s->Ne, 0);
+    for (int a = 0; a < s->Ne; ++a) {
+      int rem = a, k = 0, mul = 1;
+      for (int q = s->Q - 1; q >= 0; --q) {
+        const int dg = rem % s->essential[q];
+        rem /= s->essential[q];
+        k += dg * mul;
+        mul *= s->levels[q];
+      }
+      efull[a] = k;
+      emap[k] = a;
+    }
+    LB_CUDA(cudaMemcpyAsync(at<int32_t>(s, s->L.emap), emap.data(), sizeof(int32_t) * s->N, cudaMemcpyHostToDevice, st),
+            "upload gate map");
+    LB_CUDA(cudaMemcpyAsync(at<int32_t>(s, s->L.efull), efull.data(), sizeof(int32_t) * s->Ne, cudaMemcpyHostToDevice,
+                            st),
+            "upload gate map");
+    LB_CUDA(cudaMemcpyAsync(at<double2>(s, s->L.gateV), s->gateV.data(), sizeof(double2) * s->Ne * s->Ne,
+                            cudaMemcpyHostToDevice, st),
+            "upload gate");
+    // pageable sources above are staged before cudaMemcpyAsync returns
+    LB_CUDA(lbk::launch_gate_targets(s->hp, at<double2>(s, s->L.gateV), at<int32_t>(s, s->L.emap),
+                                     at<int32_t>(s, s->L.efull), s->Ne, st),
+            "gate targets kernel");
+  } else {
+    LB_CUDA(cudaMemsetAsync(at<double2>(s, s->L.tar), 0, bytes, st), "clear targets");
+  }
+  return LB_OK;
+}
+
+int upload_controls(lb_system* s, cudaStream_t st) {
+  if (s->n_params)
+    LB_CUDA(cudaMemcpyAsync(at<double>(s, s->L.alpha), s->alpha.data(), sizeof(double) * s->n_params,
+                            cudaMemcpyHostToDevice, st),
+            "upload alpha");
+  s->ctab_dirty = true;
+  return LB_OK;
+}
+
+void fill_prob(lb_system* s) {
+  ProbDev& P = s->hp;
+  std::memset(&P, 0, sizeof(P));
+  P.Q = s->Q;
+  P.N = s->N;
+  P.M = s->M;
+  P.NT = (int32_t)s->NT;
+  P.V = s->V;
+  P.K = s->K;
+  P.n_ckpt = s->K > 0 ? (int32_t)((s->NT + s->K - 1) / s->K) : (int32_t)s->NT;
+  P.max_iter = s->max_iter;
+  P.method = s->method;
+  P.kind = s->kind;
+  P.Ns = s->Ns;
+  P.n_params = s->n_params;
+  P.h = s->h;
+  P.rtol = s->rtol;
+  P.T = s->T;
+  P.gamma2 = s->gamma2;
+  int stride = 1, co = 0, jo = 0, fo = 0, ao = 0;
+  for (int q = s->Q - 1; q >= 0; --q) {
+    P.stride[q] = stride;
+    stride *= s->levels[q];
+  }
+  for (int q = 0; q < s->Q; ++q) {
+    P.levels[q] = s->levels[q];
+    P.coff[q] = co;
+    co += s->levels[q];
+    P.joff[q] = jo;
+    jo += s->levels[q] * s->levels[q];
+    P.nf[q] = s->nf[q];
+    P.foff[q] = fo;
+    fo += s->nf[q];
+    P.aoff[q] = ao;
+    ao += 2 * s->Ns * s->nf[q];
+    P.jump[q] = 0.5 * s->h * s->g1[q];
+  }
+  P.ncoef = co;
+  P.njcoef = jo;
+  P.sysp = at<double>(s, s->L.sysp);
+  P.cu = at<double>(s, s->L.cu);
+  P.cd = at<double>(s, s->L.cd);
+  P.jf = at<double>(s, s->L.jf);
+  P.ja = at<double>(s, s->L.ja);
+  P.digits = at<uint32_t>(s, s->L.digits);
+  P.D = at<double2>(s, s->L.D);
+  P.Dinv = at<double2>(s, s->L.Dinv);
+  P.alpha = at<double>(s, s->L.alpha);
+  P.carriers = at<double>(s, s->L.carriers);
+  P.ctab = at<double2>(s, s->L.ctab);
+  P.q0 = at<double2>(s, s->L.q0);
+  P.tar = at<double2>(s, s->L.tar);
+  P.wgt = at<double>(s, s->L.wgt);
+  P.qT = at<double2>(s, s->L.qT);
+  P.ckpt = at<double2>(s, s->L.ckpt);
+  P.seg = at<double2>(s, s->L.seg);
+  P.gproj = at<double2>(s, s->L.gproj);
+  P.J = at<double>(s, s->L.J);
+  P.G = at<double>(s, s->L.G);
+  P.grad = at<double>(s, s->L.grad);
+  P.status = at<DevStatus>(s, s->L.status);
+}
+
+int ensure_ctab(lb_system* s, cudaStream_t st) {
+  if (!s->ctab_dirty) return LB_OK;
+  LB_CUDA(lbk::launch_control_table(s->dp, s->hp, st), "control table kernel");
+  s->launches += 1;
+  s->ctab_dirty = false;
+  return LB_OK;
+}
+
+int read_status(const DevStatus& d, lb_stats* st, int launches) {
+  if (st) {
+    *st = lb_stats{};
+    for (int p = 0; p < 3; ++p) {
+      st->phase_steps[p] = (int64_t)d.steps[p];
+      st->phase_iterations[p] = (int64_t)d.iters[p];
+      st->state_steps += (int64_t)d.steps[p];
+      st->inner_iterations += (int64_t)d.iters[p];
+    }
+    st->max_iterations = d.max_iter_seen;
+    st->kernel_launches = launches;
+  }
+  if (d.code == LB_ENOTCONV) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "inner solve did not converge within max_iter at time step %d", d.step);
+    return fail(LB_ENOTCONV, buf);
+  }
+  if (d.code == LB_ENAN) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "state became NaN or Inf at time step %d", d.step);
+    return fail(LB_ENAN, buf);
+  }
+  return LB_OK;
+}
+
+bool resident_ok(const lb_system* s) { return s->V <= lbk::kMaxResidentV; }
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char* lb_last_error(void) { return g_err.c_str(); }
+
+const char* lb_version(void) { return "lindblad_gb300 0.1 (sm_103a, FP64)"; }
+
+int lb_system_create(const lb_system_desc* d, lb_system** out) {
+  if (!d || !out) return fail(LB_EINVAL, "null argument");
+  if (d->Q < 1 || d->Q > LB_MAX_SUBSYSTEMS) return fail(LB_EINVAL, "Q out of range 1..8");
+  if (!d->levels || !d->detuning_ghz) return fail(LB_EINVAL, "levels and detuning_ghz are required");
+  if (!(d->T_ns > 0.0) || !std::isfinite(d->T_ns)) return fail(LB_EINVAL, "T_ns must be finite and > 0");
+  if (d->n_steps < 1 || d->n_steps > (1LL << 30)) return fail(LB_EINVAL, "n_steps out of range");
+  lb_system* s = new (std::nothrow) lb_system();
+  if (!s) return fail(LB_ENOMEM, "host allocation failed");
+  s->Q = d->Q;
+  long long N = 1, Ne = 1;
+  for (int q = 0; q < d->Q; ++q) {
+    const int n = d->levels[q];
+    if (n < 2 || n > LB_MAX_LEVELS) {
+      delete s;
+      return fail(LB_EINVAL, "levels must be in 2..16");
+    }
+    s->levels[q] = n;
+    const int e = d->essential ? d->essential[q] : n;
+    if (e < 1 || e > n) {
+      delete s;
+      return fail(LB_EINVAL, "essential levels must be in 1..levels");
+    }
+    s->essential[q] = e;
+    N *= n;
+    Ne *= e;
+    s->det[q] = kTwoPi * d->detuning_ghz[q];
+    s->kerr[q] = d->selfkerr_ghz ? kTwoPi * d->selfkerr_ghz[q] : 0.0;
+    const double t1 = d->t1_us ? d->t1_us[q] : 0.0, t2 = d->t2_us ? d->t2_us[q] : 0.0;
+    s->g1[q] = finite_pos(t1) ? 1.0 / (1000.0 * t1) : 0.0;
+    s->g2[q] = finite_pos(t2) ? 1.0 / (1000.0 * t2) : 0.0;
+    if (!std::isfinite(s->det[q]) || !std::isfinite(s->kerr[q])) {
+      delete s;
+      return fail(LB_EINVAL, "non-finite detuning or self-Kerr");
+    }
+  }
+  if (N > (1 << 15)) {
+    delete s;
+    return fail(LB_EINVAL, "N = prod(levels) must be <= 32768");
+  }
+  if (d->crosskerr_ghz)
+    for (int p = 0; p < d->Q; ++p)
+      for (int q = p + 1; q < d->Q; ++q) s->xkerr[p * d->Q + q] = kTwoPi * d->crosskerr_ghz[p * d->Q + q];
+  s->N = (int)N;
+  s->V = (int)(N * N);
+  s->Ne = (int)Ne;
+  s->T = d->T_ns;
+  s->NT = d->n_steps;
+  s->h = d->T_ns / (double)d->n_steps;
+  *out = s;
+  return LB_OK;
+}
+
+void lb_system_destroy(lb_system* s) {
+  if (!s) return;
+  if (s->upload_done) cudaEventDestroy(s->upload_done);
+  for (cudaEvent_t e : s->ev)
+    if (e) cudaEventDestroy(e);
+  delete s;
+}
+
+int lb_set_timing(lb_system* s, int32_t on) {
+  if (!s) return fail(LB_EINVAL, "null system handle");
+  if (on && !s->ev[0])
+    for (int i = 0; i < 4; ++i) LB_CUDA(cudaEventCreate(&s->ev[i]), "cudaEventCreate");
+  s->timing = on != 0;
+  return LB_OK;
+}
+
+int lb_controls_define(lb_system* s, int32_t n_splines, const int32_t* n_carriers, const double* carrier_ghz) {
+  if (!s || !n_carriers || !carrier_ghz) return fail(LB_EINVAL, "null argument");
+  if (s->ws) return fail(LB_EINVAL, "controls must be defined before binding a workspace");
+  if (n_splines < 3) return fail(LB_EINVAL, "n_splines must be >= 3 (knot spacing T/(N_s-2))");
+  int tot = 0;
+  for (int q = 0; q < s->Q; ++q) {
+    if (n_carriers[q] < 1 || n_carriers[q] > 64) return fail(LB_EINVAL, "n_carriers must be in 1..64");
+    s->nf[q] = n_carriers[q];
+    tot += n_carriers[q];
+  }
+  s->carriers.assign(tot, 0.0);
+  for (int i = 0; i < tot; ++i) {
+    if (!std::isfinite(carrier_ghz[i])) return fail(LB_EINVAL, "non-finite carrier frequency");
+    s->carriers[i] = kTwoPi * carrier_ghz[i];
+  }
+  s->Ns = n_splines;
+  s->n_params = 2 * n_splines * tot;
+  s->alpha.assign(s->n_params, 0.0);
+  s->ctrl_defined = true;
+  s->ctab_dirty = true;
+  return LB_OK;
+}
+
+int lb_controls_set(lb_system* s, const double* alpha, int64_t n) {
+  if (!s || !alpha) return fail(LB_EINVAL, "null argument");
+  if (!s->ctrl_defined) return fail(LB_EINVAL, "controls not defined");
+  if (n != s->n_params) return fail(LB_EINVAL, "alpha length must be 2 * sum_q N_s N_f(q)");
+  for (int64_t k = 0; k < n; ++k)
+    if (!std::isfinite(alpha[k])) return fail(LB_EINVAL, "non-finite control coefficient");
+  std::memcpy(s->alpha.data(), alpha, sizeof(double) * n);
+  if (s->ws) return upload_controls(s, s->bind_stream);
+  s->ctab_dirty = true;
+  return LB_OK;
+}
+
+int lb_states_set(lb_system* s, int32_t M, const double* rho0, const double* weights) {
+  if (!s || !rho0) return fail(LB_EINVAL, "null argument");
+  if (M < 1) return fail(LB_EINVAL, "M must be >= 1");
+  if (s->ws && M != s->M) return fail(LB_EINVAL, "M cannot change while a workspace is bound");
+  std::vector<double> w(M, 1.0);
+  if (weights)
+    for (int i = 0; i < M; ++i) {
+      if (!std::isfinite(weights[i])) return fail(LB_EINVAL, "non-finite weight");
+      w[i] = weights[i];
+    }
+  for (int i = 0; i < M; ++i) w[i] /= (double)M;
+  if (s->M != M && s->target_mode == 1) s->target_mode = 0;  // explicit targets no longer match
+  s->M = M;
+  s->wgt = w;
+  if (s->ws) {
+    int rc = upload_states(s, rho0, s->bind_stream);
+    if (rc) return rc;
+    if (s->target_mode == 2) return upload_targets(s, s->bind_stream);
+    return LB_OK;
+  }
+  s->rho0.assign(rho0, rho0 + (size_t)2 * M * s->V);
+  return LB_OK;
+}
+
+int lb_objective_set(lb_system* s, int32_t kind, const double* targets, double gamma2) {
+  if (!s || !targets) return fail(LB_EINVAL, "null argument");
+  if (kind != LB_J_FROB && kind != LB_J_TR) return fail(LB_EINVAL, "unknown merit functional");
+  if (!(gamma2 >= 0.0) || !std::isfinite(gamma2)) return fail(LB_EINVAL, "gamma2 must be finite and >= 0");
+  if (s->M < 1) return fail(LB_EINVAL, "call lb_states_set first");
+  s->kind = kind;
+  s->gamma2 = gamma2;
+  s->target_mode = 1;
+  s->targets.assign(targets, targets + (size_t)2 * s->M * s->V);
+  if (s->ws) {
+    s->hp.kind = kind;
+    s->hp.gamma2 = gamma2;
+    LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, s->bind_stream), "upload problem");
+    return upload_targets(s, s->bind_stream);
+  }
+  return LB_OK;
+}
+
+int lb_objective_set_gate(lb_system* s, int32_t kind, const double* V, double gamma2) {
+  if (!s || !V) return fail(LB_EINVAL, "null argument");
+  if (kind != LB_J_FROB && kind != LB_J_TR) return fail(LB_EINVAL, "unknown merit functional");
+  if (!(gamma2 >= 0.0) || !std::isfinite(gamma2)) return fail(LB_EINVAL, "gamma2 must be finite and >= 0");
+  if (s->ws && s->target_mode != 2) return fail(LB_EINVAL, "switch to a gate objective before binding a workspace");
+  s->kind = kind;
+  s->gamma2 = gamma2;
+  s->target_mode = 2;
+  s->gateV.assign(V, V + (size_t)2 * s->Ne * s->Ne);
+  s->targets.clear();
+  if (s->ws) {
+    s->hp.kind = kind;
+    s->hp.gamma2 = gamma2;
+    LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, s->bind_stream), "upload problem");
+    return upload_targets(s, s->bind_stream);
+  }
+  return LB_OK;
+}
+
+int lb_solver_set(lb_system* s, int32_t method, double rtol, int32_t max_iter, int32_t ckpt_every) {
+  if (!s) return fail(LB_EINVAL, "null system handle");
+  if (s->ws) return fail(LB_EINVAL, "set the solver before binding a workspace");
+  if (method == LB_SOLVER_AUTO) method = LB_SOLVER_JACOBI;
+  if (method != LB_SOLVER_JACOBI && method != LB_SOLVER_NEUMANN) return fail(LB_EINVAL, "unknown solver");
+  if (!(rtol > 0.0) || !(rtol < 1.0)) return fail(LB_EINVAL, "rtol must be in (0, 1)");
+  if (max_iter < 1 || max_iter > 100000) return fail(LB_EINVAL, "max_iter must be in 1..100000");
+  if (ckpt_every < 0) return fail(LB_EINVAL, "ckpt_every must be >= 0");
+  s->method = method;
+  s->rtol = rtol;
+  s->max_iter = max_iter;
+  s->K = ckpt_every > s->NT ? (int)s->NT : ckpt_every;
+  return LB_OK;
+}
+
+int lb_workspace_bytes(const lb_system* s, size_t* bytes) {
+  int rc = check_ready(s, false);
+  if (rc) return rc;
+  if (!bytes) return fail(LB_EINVAL, "null argument");
+  *bytes = make_layout(s).total;
+  return LB_OK;
+}
+
+int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
+  int rc = check_ready(s, false);
+  if (rc) return rc;
+  if (!ws) return fail(LB_EINVAL, "null workspace");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(LB_EINVAL, "workspace must be 256-byte aligned");
+  if (!resident_ok(s)) return fail(LB_EINVAL, "N^2 > 4096 needs the grid-wide sweep, not available in this build");
+  if (s->target_mode == 0) return fail(LB_EINVAL, "no objective (lb_objective_set or lb_objective_set_gate)");
+  if (s->target_mode == 2) {
+    for (int q = 0; q < s->Q; ++q)
+      if (s->essential[q] < 1) return fail(LB_EINVAL, "bad essential levels");
+  }
+  s->L = make_layout(s);
+  if (bytes < s->L.total) return fail(LB_ENOMEM, "workspace smaller than lb_workspace_bytes");
+  if (s->rho0.empty()) return fail(LB_EINVAL, "initial states are required before binding");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!s->upload_done) LB_CUDA(cudaEventCreateWithFlags(&s->upload_done, cudaEventDisableTiming), "cudaEventCreate");
+  s->ws = static_cast<char*>(ws);
+  s->ws_bytes = bytes;
+  s->bind_stream = st;
+  fill_prob(s);
+  s->dp = at<ProbDev>(s, s->L.prob);
+  s->d_items = at<WorkItem>(s, s->L.items);
+  std::vector<WorkItem> items(s->M);
+  for (int i = 0; i < s->M; ++i) items[i] = WorkItem{0, i};
+  std::vector<double> sysp(4 * s->Q + s->Q * s->Q, 0.0);
+  for (int q = 0; q < s->Q; ++q) {
+    sysp[q] = s->det[q];
+    sysp[s->Q + q] = s->kerr[q];
+    sysp[2 * s->Q + s->Q * s->Q + q] = s->g1[q];
+    sysp[3 * s->Q + s->Q * s->Q + q] = s->g2[q];
+  }
+  for (int i = 0; i < s->Q * s->Q; ++i) sysp[2 * s->Q + i] = s->xkerr[i];
+  LB_CUDA(cudaMemsetAsync(s->ws, 0, s->L.total, st), "clear workspace");
+  LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
+  LB_CUDA(cudaMemcpyAsync(s->d_items, items.data(), sizeof(WorkItem) * s->M, cudaMemcpyHostToDevice, st),
+          "upload work items");
+  LB_CUDA(cudaMemcpyAsync(at<double>(s, s->L.sysp), sysp.data(), sizeof(double) * sysp.size(), cudaMemcpyHostToDevice,
+                          st),
+          "upload system");
+  if (!s->carriers.empty())
+    LB_CUDA(cudaMemcpyAsync(at<double>(s, s->L.carriers), s->carriers.data(), sizeof(double) * s->carriers.size(),
+                            cudaMemcpyHostToDevice, st),
+            "upload carriers");
+  LB_CUDA(lbk::launch_tables(s->dp, s->hp, st), "tables kernel");
+  rc = upload_states(s, s->rho0.data(), st);
+  if (rc) return rc;
+  rc = upload_targets(s, st);
+  if (rc) return rc;
+  rc = upload_controls(s, st);
+  if (rc) return rc;
+  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N);
+  // the workspace now owns the states; pageable copies above are staged
+  s->rho0.clear();
+  s->rho0.shrink_to_fit();
+  return LB_OK;
+}
+
+static int run_forward(lb_system* s, cudaStream_t st, int tape) {
+  int rc = order_after_uploads(s, st);
+  if (rc) return rc;
+  s->launches = 0;
+  rc = ensure_ctab(s, st);
+  if (rc) return rc;
+  LB_CUDA(cudaMemsetAsync(at<DevStatus>(s, s->L.status), 0, sizeof(DevStatus), st), "clear status");
+  s->timed_fwd = s->timed_bwd = false;
+  if (s->timing) LB_CUDA(cudaEventRecord(s->ev[0], st), "cudaEventRecord");
+  LB_CUDA(lbk::launch_forward_resident(s->dp, s->d_items, s->M, tape, s->rc, st), "forward kernel");
+  if (s->timing) {
+    LB_CUDA(cudaEventRecord(s->ev[1], st), "cudaEventRecord");
+    s->timed_fwd = true;
+  }
+  s->launches += 1;
+  return LB_OK;
+}
+
+static int finish(lb_system* s, cudaStream_t st, double* G_out, double* grad_out) {
+  DevStatus d{};
+  LB_CUDA(cudaMemcpyAsync(&d, at<DevStatus>(s, s->L.status), sizeof(DevStatus), cudaMemcpyDeviceToHost, st),
+          "read status");
+  double G = 0.0;
+  if (G_out) LB_CUDA(cudaMemcpyAsync(&G, at<double>(s, s->L.G), sizeof(double), cudaMemcpyDeviceToHost, st), "read G");
+  std::vector<double> g;
+  if (grad_out) {
+    g.resize(s->n_params);
+    LB_CUDA(cudaMemcpyAsync(g.data(), at<double>(s, s->L.grad), sizeof(double) * s->n_params, cudaMemcpyDeviceToHost,
+                            st),
+            "read gradient");
+  }
+  LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  int rc = read_status(d, &s->last, s->launches);
+  if (s->timed_fwd) LB_CUDA(cudaEventElapsedTime(&s->last.ms_forward, s->ev[0], s->ev[1]), "cudaEventElapsedTime");
+  if (s->timed_bwd) LB_CUDA(cudaEventElapsedTime(&s->last.ms_backward, s->ev[2], s->ev[3]), "cudaEventElapsedTime");
+  if (rc) return rc;
+  if (G_out) *G_out = G;
+  if (grad_out) std::memcpy(grad_out, g.data(), sizeof(double) * s->n_params);
+  return LB_OK;
+}
+
+int lb_forward(lb_system* s, void* stream, double* G_out, void* rhoT_dev_out) {
+  int rc = check_ready(s, true);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = run_forward(s, st, 0);
+  if (rc) return rc;
+  LB_CUDA(lbk::launch_finalize(s->dp, 1, 0, 0, st), "objective kernel");
+  s->launches += 1;
+  if (rhoT_dev_out)
+    LB_CUDA(cudaMemcpyAsync(rhoT_dev_out, at<double2>(s, s->L.qT), sizeof(double2) * (size_t)s->M * s->V,
+                            cudaMemcpyDeviceToDevice, st),
+            "copy final states");
+  return finish(s, st, G_out, nullptr);
+}
+
+static int param_warps(const lb_system* s) {
+  int nw = 0;
+  for (int q = 0; q < s->Q; ++q) nw += s->nf[q] * s->Ns;
+  return nw;
+}
+
+static int gradient_device(lb_system* s, cudaStream_t st) {
+  int rc = run_forward(s, st, 1);
+  if (rc) return rc;
+  if (s->timing) LB_CUDA(cudaEventRecord(s->ev[2], st), "cudaEventRecord");
+  LB_CUDA(lbk::launch_backward_resident(s->dp, s->d_items, s->M, s->rc, st), "backward kernel");
+  if (s->timing) {
+    LB_CUDA(cudaEventRecord(s->ev[3], st), "cudaEventRecord");
+    s->timed_bwd = true;
+  }
+  LB_CUDA(lbk::launch_finalize(s->dp, 1, param_warps(s), 1, st), "finalize kernels");
+  s->launches += 3;
+  return LB_OK;
+}
+
+int lb_gradient(lb_system* s, void* stream, double* G_out, double* grad_out) {
+  int rc = check_ready(s, true);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = gradient_device(s, st);
+  if (rc) return rc;
+  return finish(s, st, G_out, grad_out);
+}
+
+int lb_gradient_async(lb_system* s, void* stream, void* G_dev, void* grad_dev) {
+  int rc = check_ready(s, true);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = gradient_device(s, st);
+  if (rc) return rc;
+  if (G_dev)
+    LB_CUDA(cudaMemcpyAsync(G_dev, at<double>(s, s->L.G), sizeof(double), cudaMemcpyDeviceToDevice, st), "copy G");
+  if (grad_dev)
+    LB_CUDA(cudaMemcpyAsync(grad_dev, at<double>(s, s->L.grad), sizeof(double) * s->n_params, cudaMemcpyDeviceToDevice,
+                            st),
+            "copy gradient");
+  return LB_OK;
+}
+
+int lb_propagate(lb_system* s, void* stream, int32_t adjoint, int64_t j0, int64_t j1, void* x_dev, int32_t n_vec) {
+  int rc = check_ready(s, true);
+  if (rc) return rc;
+  if (!x_dev || n_vec < 1) return fail(LB_EINVAL, "bad vectors");
+  if (j0 < 0 || j1 < j0 || j1 > s->NT) return fail(LB_EINVAL, "need 0 <= j0 <= j1 <= n_steps");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = order_after_uploads(s, st);
+  if (rc) return rc;
+  s->launches = 0;
+  rc = ensure_ctab(s, st);
+  if (rc) return rc;
+  LB_CUDA(cudaMemsetAsync(at<DevStatus>(s, s->L.status), 0, sizeof(DevStatus), st), "clear status");
+  s->timed_fwd = s->timed_bwd = false;
+  if (j1 > j0) {
+    LB_CUDA(lbk::launch_propagate_resident(s->dp, adjoint, j0, j1, static_cast<double2*>(x_dev), n_vec, s->rc, st),
+            "propagate kernel");
+    s->launches += 1;
+  }
+  return finish(s, st, nullptr, nullptr);
+}
+
+int lb_apply(lb_system* s, void* stream, int32_t adjoint, int64_t step, const void* x_dev, void* y_dev,
+             int32_t n_vec) {
+  int rc = check_ready(s, true);
+  if (rc) return rc;
+  if (!x_dev || !y_dev || n_vec < 1) return fail(LB_EINVAL, "bad vectors");
+  if (step < 0 || step >= s->NT) return fail(LB_EINVAL, "step out of range");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = order_after_uploads(s, st);
+  if (rc) return rc;
+  rc = ensure_ctab(s, st);
+  if (rc) return rc;
+  LB_CUDA(lbk::launch_apply(s->dp, s->hp, adjoint, step, static_cast<const double2*>(x_dev), static_cast<double2*>(y_dev),
+                            n_vec, st),
+          "apply kernel");
+  return LB_OK;
+}
+
+int lb_get_stats(lb_system* s, lb_stats* out) {
+  if (!s || !out) return fail(LB_EINVAL, "null argument");
+  *out = s->last;
+  return LB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// batches
+
+int lb_batch_create(lb_system* const* systems, int32_t n, lb_batch** out) {
+  if (!systems || n < 1 || !out) return fail(LB_EINVAL, "bad batch arguments");
+  lb_batch* b = new (std::nothrow) lb_batch();
+  if (!b) return fail(LB_ENOMEM, "host allocation failed");
+  int maxV = 0, maxQ = 0, maxc = 0, maxj = 0, maxN = 0;
+  for (int i = 0; i < n; ++i) {
+    lb_system* s = systems[i];
+    if (!s || !s->ws) {
+      delete b;
+      return fail(LB_EINVAL, "every system of a batch must have a bound workspace");
+    }
+    b->sys.push_back(s);
+    b->grad_off.push_back(b->n_grad);
+    b->n_grad += s->n_params;
+    b->n_items += s->M;
+    maxV = std::max(maxV, s->V);
+    maxQ = std::max(maxQ, s->Q);
+    maxc = std::max(maxc, n_coef(s));
+    maxj = std::max(maxj, n_jcoef(s));
+    maxN = std::max(maxN, s->N);
+    b->max_param_warps = std::max(b->max_param_warps, param_warps(s));
+  }
+  b->rc = lbk::resident_config(maxV, maxQ, maxc, maxj, maxN);
+  *out = b;
+  return LB_OK;
+}
+
+void lb_batch_destroy(lb_batch* b) {
+  if (!b) return;
+  for (int m = 0; m < 2; ++m) {
+    if (b->exec[m]) cudaGraphExecDestroy(b->exec[m]);
+    if (b->graph[m]) cudaGraphDestroy(b->graph[m]);
+  }
+  delete b;
+}
+
+static size_t batch_layout(const lb_batch* b, size_t* o_probs, size_t* o_items, size_t* o_goff, size_t* o_G,
+                           size_t* o_grad, size_t* o_st) {
+  const size_t n = b->sys.size();
+  size_t off = 0;
+  *o_probs = off;
+  off += align_up(sizeof(ProbDev) * n);
+  *o_items = off;
+  off += align_up(sizeof(WorkItem) * b->n_items);
+  *o_goff = off;
+  off += align_up(sizeof(int64_t) * n);
+  *o_G = off;
+  off += align_up(sizeof(double) * n);
+  *o_grad = off;
+  off += align_up(sizeof(double) * (b->n_grad ? b->n_grad : 1));
+  *o_st = off;
+  off += align_up(sizeof(DevStatus) * n);
+  return off;
+}
+
+int lb_batch_workspace_bytes(const lb_batch* b, size_t* bytes) {
+  if (!b || !bytes) return fail(LB_EINVAL, "null argument");
+  size_t a, c, d, e, f, g;
+  *bytes = batch_layout(b, &a, &c, &d, &e, &f, &g);
+  return LB_OK;
+}
+
+int lb_batch_bind_workspace(lb_batch* b, void* ws, size_t bytes, void* stream) {
+  if (!b || !ws) return fail(LB_EINVAL, "null argument");
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(LB_EINVAL, "workspace must be 256-byte aligned");
+  size_t o_probs, o_items, o_goff, o_G, o_grad, o_st;
+  const size_t need = batch_layout(b, &o_probs, &o_items, &o_goff, &o_G, &o_grad, &o_st);
+  if (bytes < need) return fail(LB_ENOMEM, "batch workspace too small");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* base = static_cast<char*>(ws);
+  b->ws = base;
+  b->ws_bytes = bytes;
+  b->d_probs = reinterpret_cast<ProbDev*>(base + o_probs);
+  b->d_items = reinterpret_cast<WorkItem*>(base + o_items);
+  b->d_grad_off = reinterpret_cast<int64_t*>(base + o_goff);
+  b->d_G = reinterpret_cast<double*>(base + o_G);
+  b->d_grad = reinterpret_cast<double*>(base + o_grad);
+  b->d_st = reinterpret_cast<DevStatus*>(base + o_st);
+  std::vector<ProbDev> probs;
+  // work items, most expensive first (cost ~ V * Q per state-step)
+  std::vector<std::pair<double, WorkItem>> order;
+  for (size_t p = 0; p < b->sys.size(); ++p) {
+    lb_system* s = b->sys[p];
+    probs.push_back(s->hp);
+    for (int i = 0; i < s->M; ++i)
+      order.push_back({-(double)s->V * (s->Q + 1) * (double)s->NT, WorkItem{(int32_t)p, i}});
+    // the systems' own uploads must precede the batch's work
+    int rc = order_after_uploads(s, st);
+    if (rc) return rc;
+  }
+  std::stable_sort(order.begin(), order.end(),
+                   [](const std::pair<double, WorkItem>& x, const std::pair<double, WorkItem>& y) {
+                     return x.first < y.first;
+                   });
+  std::vector<WorkItem> items;
+  for (auto& o : order) items.push_back(o.second);
+  LB_CUDA(cudaMemcpyAsync(b->d_probs, probs.data(), sizeof(ProbDev) * probs.size(), cudaMemcpyHostToDevice, st),
+          "upload batch problems");
+  LB_CUDA(cudaMemcpyAsync(b->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, st),
+          "upload batch items");
+  LB_CUDA(cudaMemcpyAsync(b->d_grad_off, b->grad_off.data(), sizeof(int64_t) * b->grad_off.size(),
+                          cudaMemcpyHostToDevice, st),
+          "upload gradient offsets");
+  LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  return LB_OK;
+}
+
+// device work of one batch call (graph-capturable: no host synchronisation)
+static int batch_enqueue(lb_batch* b, cudaStream_t st, int with_grad) {
+  for (lb_system* s : b->sys) {
+    LB_CUDA(lbk::launch_control_table(s->dp, s->hp, st), "control table kernel");
+    s->ctab_dirty = false;
+    LB_CUDA(cudaMemsetAsync(s->hp.status, 0, sizeof(DevStatus), st), "clear status");
+  }
+  LB_CUDA(lbk::launch_forward_resident(b->d_probs, b->d_items, b->n_items, with_grad, b->rc, st), "forward kernel");
+  if (with_grad)
+    LB_CUDA(lbk::launch_backward_resident(b->d_probs, b->d_items, b->n_items, b->rc, st), "backward kernel");
+  LB_CUDA(lbk::launch_finalize(b->d_probs, (int)b->sys.size(), b->max_param_warps, with_grad, st), "finalize kernels");
+  LB_CUDA(lbk::launch_gather(b->d_probs, (int)b->sys.size(), b->d_grad_off, b->d_G, with_grad ? b->d_grad : nullptr,
+                             b->d_st, st),
+          "gather kernel");
+  return LB_OK;
+}
+
+static int batch_call(lb_batch* b, cudaStream_t st, int with_grad, double* G_out, double* grad_out) {
+  if (!b->ws) return fail(LB_EINVAL, "no batch workspace bound");
+  const int mode = with_grad ? 1 : 0;
+  for (lb_system* s : b->sys) {
+    int rc = order_after_uploads(s, st);
+    if (rc) return rc;
+  }
+  int launches = 0;
+  if (b->exec[mode]) {
+    LB_CUDA(cudaGraphLaunch(b->exec[mode], st), "cudaGraphLaunch");
+    launches = (int)b->sys.size() + 3 + with_grad;
+  } else {
+    int rc = batch_enqueue(b, st, with_grad);
+    if (rc) return rc;
+    launches = (int)b->sys.size() + 3 + with_grad;
+  }
+  const size_t n = b->sys.size();
+  std::vector<DevStatus> stv(n);
+  LB_CUDA(cudaMemcpyAsync(stv.data(), b->d_st, sizeof(DevStatus) * n, cudaMemcpyDeviceToHost, st), "read status");
+  std::vector<double> G(n), g;
+  if (G_out) LB_CUDA(cudaMemcpyAsync(G.data(), b->d_G, sizeof(double) * n, cudaMemcpyDeviceToHost, st), "read G");
+  if (grad_out && with_grad) {
+    g.resize(b->n_grad);
+    LB_CUDA(cudaMemcpyAsync(g.data(), b->d_grad, sizeof(double) * b->n_grad, cudaMemcpyDeviceToHost, st),
+            "read gradients");
+  }
+  LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  lb_stats tot{};
+  for (size_t p = 0; p < n; ++p) {
+    lb_stats one{};
+    int rc = read_status(stv[p], &one, 0);
+    if (rc) {
+      g_err = "system " + std::to_string(p) + ": " + g_err;
+      return rc;
+    }
+    tot.state_steps += one.state_steps;
+    tot.inner_iterations += one.inner_iterations;
+    for (int ph = 0; ph < 3; ++ph) {
+      tot.phase_steps[ph] += one.phase_steps[ph];
+      tot.phase_iterations[ph] += one.phase_iterations[ph];
+    }
+    tot.max_iterations = std::max(tot.max_iterations, one.max_iterations);
+  }
+  tot.kernel_launches = launches;
+  b->last = tot;
+  if (G_out) std::memcpy(G_out, G.data(), sizeof(double) * n);
+  if (grad_out && with_grad) std::memcpy(grad_out, g.data(), sizeof(double) * b->n_grad);
+  return LB_OK;
+}
+
+int lb_batch_forward(lb_batch* b, void* stream, double* G_out) {
+  if (!b) return fail(LB_EINVAL, "null batch");
+  return batch_call(b, static_cast<cudaStream_t>(stream), 0, G_out, nullptr);
+}
+
+int lb_batch_gradient(lb_batch* b, void* stream, double* G_out, double* grad_out) {
+  if (!b) return fail(LB_EINVAL, "null batch");
+  return batch_call(b, static_cast<cudaStream_t>(stream), 1, G_out, grad_out);
+}
+
+int lb_batch_capture_graph(lb_batch* b, void* stream, int32_t mode) {
+  if (!b) return fail(LB_EINVAL, "null batch");
+  if (mode == -1) {
+    for (int m = 0; m < 2; ++m) {
+      if (b->exec[m]) cudaGraphExecDestroy(b->exec[m]);
+      if (b->graph[m]) cudaGraphDestroy(b->graph[m]);
+      b->exec[m] = nullptr;
+      b->graph[m] = nullptr;
+    }
+    return LB_OK;
+  }
+  if (mode != 0 && mode != 1) return fail(LB_EINVAL, "mode must be 0, 1 or -1");
+  if (!b->ws) return fail(LB_EINVAL, "no batch workspace bound");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!st) return fail(LB_EINVAL, "graph capture needs a non-default stream");
+  for (lb_system* s : b->sys) {
+    int rc = order_after_uploads(s, st);
+    if (rc) return rc;
+  }
+  LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  if (b->exec[mode]) cudaGraphExecDestroy(b->exec[mode]);
+  if (b->graph[mode]) cudaGraphDestroy(b->graph[mode]);
+  b->exec[mode] = nullptr;
+  b->graph[mode] = nullptr;
+  LB_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+  int rc = batch_enqueue(b, st, mode);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  b->graph[mode] = g;
+  LB_CUDA(cudaGraphInstantiate(&b->exec[mode], g, 0), "cudaGraphInstantiate");
+  return LB_OK;
+}
+
+int lb_batch_get_stats(lb_batch* b, lb_stats* out) {
+  if (!b || !out) return fail(LB_EINVAL, "null argument");
+  *out = b->last;
+  return LB_OK;
+}
+
+}  // extern "C"

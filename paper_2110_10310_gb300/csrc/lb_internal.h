@@ -1,0 +1,107 @@
+// Internal declarations shared by the host library and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "lindblad_gb300.h"
+
+#define LB_MAXQ LB_MAX_SUBSYSTEMS
+#define LB_MAXN LB_MAX_LEVELS
+
+// Status block written by the kernels and read by the host after a sync.
+struct DevStatus {
+  int32_t code;                 // 0 or LB_ENOTCONV / LB_ENAN (first error wins)
+  int32_t step;                 // time step of the first error
+  int32_t max_iter_seen;        // largest iteration count of one step
+  int32_t pad;
+  unsigned long long iters[3];  // iterations per phase: forward, recompute, adjoint
+  unsigned long long steps[3];  // state-steps per phase
+};
+
+// Everything a kernel needs to know about one system, in device memory.
+// Arrays are device pointers into the system's workspace.
+struct ProbDev {
+  int32_t Q, N, M, NT;
+  int32_t V;  // N*N (N <= 2^15 keeps V and all element offsets in 32 bits per state)
+  int32_t K;  // checkpoint interval; 0 = keep every stage vector z^j
+  int32_t n_ckpt, max_iter, method, kind;
+  int32_t Ns, n_params;
+  double h, rtol, T, gamma2;
+  int32_t levels[LB_MAXQ];
+  int32_t stride[LB_MAXQ];   // s_q = prod_{p>q} n_p
+  int32_t coff[LB_MAXQ];     // offset of subsystem q in cu/cd
+  int32_t joff[LB_MAXQ];     // offset of subsystem q in jf/ja
+  int32_t nf[LB_MAXQ];       // carriers per subsystem
+  int32_t foff[LB_MAXQ];     // offset of subsystem q in carriers
+  int32_t aoff[LB_MAXQ];     // offset of subsystem q in alpha
+  double jump[LB_MAXQ];      // (dt/2)/T1_q, 0 = no decay
+  int32_t ncoef, njcoef;     // sizes of cu/cd and jf/ja
+  // system parameters: det[Q], kerr[Q] (rad/ns), xkerr[Q*Q] (rad/ns, p<q used),
+  // g1[Q] = 1/T1, g2[Q] = 1/T2 (1/ns, 0 = off)
+  double* sysp;
+  // time-independent tables
+  double* cu;                // [ncoef]  sqrt(n+1) if n+1 < n_q else 0
+  double* cd;                // [ncoef]  sqrt(n)
+  double* jf;                // [njcoef] jump_q sqrt((nk+1)(nl+1)), 0 if a digit would leave the range
+  double* ja;                // [njcoef] jump_q sqrt(nk nl)
+  uint32_t* digits;          // [N] 4-bit digits of a basis index, subsystem q at bits 4q..4q+3
+  double2* D;                // [V] diagonal of M
+  double2* Dinv;             // [V] 1/(1 - dt/2 D)
+  // controls
+  double* alpha;             // [n_params]
+  double* carriers;          // [sum nf] Omega (rad/ns)
+  double2* ctab;             // [NT*Q] (dt/2) d_q(t_j + dt/2)
+  // states and objective
+  double2* q0;               // [M*V]
+  double2* tar;              // [M*V]
+  double* wgt;               // [M] beta_i / M
+  double2* qT;               // [M*V]
+  double2* ckpt;             // [M*n_ckpt*V], or [M*NT*V] of z^j when K == 0
+  double2* seg;              // [M*K*V] stage vectors of one segment (K > 0)
+  double2* gproj;            // [M*NT*Q*2] per state/step: g_a, g_ad (eq. reducedgradient pieces)
+  double* J;                 // [M] merit functional per state
+  double* G;                 // [1]
+  double* grad;              // [n_params]
+  DevStatus* status;
+};
+
+// one work item of a resident launch: (problem, state)
+struct WorkItem {
+  int32_t prob, state;
+};
+
+// ---- kernel launchers (lb_kernels.cu) --------------------------------------
+namespace lbk {
+
+constexpr int kMaxResidentV = 4096;  // states held in one CTA's shared memory
+
+struct ResidentConfig {
+  int threads;  // CTA size (multiple of 32, <= 512)
+  int E;        // elements per thread (1, 2, 4, 8)
+  size_t smem;  // dynamic shared memory bytes
+};
+
+ResidentConfig resident_config(int maxV, int maxQ, int maxNcoef, int maxNj, int maxN);
+
+cudaError_t launch_tables(ProbDev* d_prob, const ProbDev& h_prob, cudaStream_t s);
+cudaError_t launch_gate_targets(const ProbDev& h_prob, const double2* Vg, const int32_t* emap, const int32_t* efull,
+                                int32_t Ne, cudaStream_t s);
+cudaError_t launch_control_table(const ProbDev* d_prob, const ProbDev& h_prob, cudaStream_t s);
+cudaError_t launch_forward_resident(const ProbDev* d_probs, const WorkItem* d_items, int n_items, int tape,
+                                    const ResidentConfig& rc, cudaStream_t s);
+cudaError_t launch_backward_resident(const ProbDev* d_probs, const WorkItem* d_items, int n_items,
+                                     const ResidentConfig& rc, cudaStream_t s);
+// objective (and gradient projection) for n_probs systems of the device array d_probs
+cudaError_t launch_finalize(const ProbDev* d_probs, int n_probs, int max_param_warps, int with_grad, cudaStream_t s);
+// copy G, gradients and status words of n_probs systems into contiguous arrays
+cudaError_t launch_gather(const ProbDev* d_probs, int n_probs, const int64_t* grad_off, double* G_all,
+                          double* grad_all, DevStatus* st_all, cudaStream_t s);
+cudaError_t launch_apply(const ProbDev* d_prob, const ProbDev& h_prob, int adjoint, int64_t step, const double2* x,
+                         double2* y, int n_vec, cudaStream_t s);
+cudaError_t launch_propagate_resident(const ProbDev* d_prob, int adjoint, int64_t j0, int64_t j1, double2* x,
+                                      int n_vec, const ResidentConfig& rc, cudaStream_t s);
+
+}  // namespace lbk

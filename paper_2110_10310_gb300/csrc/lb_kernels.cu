@@ -1,0 +1,989 @@
+// CUDA kernels of the implicit-midpoint Lindblad path (sm_103a, FP64).
+//
+// Design notes
+// * The vectorised Lindbladian M(t) of Appendix A (eq. mastereq_vectorized)
+//   is never formed.  For vec index v = k + N l (column stacking) it acts as
+//     (M x)_kl = D_kl x_kl + sum_q [ jump_q + control_q ](k, l)
+//   where D is diagonal and time independent (Hamiltonian diagonal, all
+//   anticommutator terms and the dephasing sandwich L_2q x L_2q), the jump
+//   term couples x_{k+s_q, l+s_q} (decay sandwich L_1q x L_1q) and the
+//   control term couples x_{k+-s_q, l} and x_{k, l-+s_q} (-i[H_c, x]), s_q
+//   being the index stride of subsystem q.
+// * FP64 is the binding resource on this GPU (two FP64 lanes per SM per
+//   clock, one warp instruction per 64 cycles per SM sub-partition, whatever
+//   the number of active lanes), so the kernels minimise FP64 instructions:
+//   coefficient selection and index arithmetic run on the integer pipe, and
+//   per-element coefficients come from small tables.
+// * Inner solve of (I - dt/2 M) z = q (eq. linsystem_primal): Jacobi
+//   fixed point z <- (I - dt/2 D)^-1 (q + dt/2 O z), O = M - D, from
+//   z_0 = (I - dt/2 D)^-1 q, to ||z_new - z||_inf <= rtol ||q||_inf.  The
+//   maximum is taken on the integer bit patterns of |.|, so the stopping
+//   decision is exact and identical in a recompute.
+// * "Resident" kernels: one CTA owns one state (V = N^2 <= 4096) in shared
+//   memory and runs the whole time loop; the CTA barrier is the only
+//   synchronisation of an inner iteration.
+
+#include <cmath>
+
+#include "lb_internal.h"
+
+namespace lbk {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr unsigned long long kInfBits = 0x7ff0000000000000ULL;
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffULL;
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x = umax64(x, __shfl_xor_sync(kFull, x, o));
+  return x;
+}
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+// Sum of four per-lane values over the warp with 6 FP64 additions per lane:
+// after the call lane 0 holds the total of v0, lane 8 of v1, lane 16 of v2 and
+// lane 24 of v3.
+__device__ __forceinline__ double warp_sum4(double v0, double v1, double v2, double v3, int lane) {
+  const bool h16 = lane & 16;
+  double k0 = h16 ? v2 : v0, k1 = h16 ? v3 : v1;
+  const double s0 = h16 ? v0 : v2, s1 = h16 ? v1 : v3;
+  k0 += __shfl_xor_sync(kFull, s0, 16);
+  k1 += __shfl_xor_sync(kFull, s1, 16);
+  const bool h8 = lane & 8;
+  double k = h8 ? k1 : k0;
+  const double s = h8 ? k0 : k1;
+  k += __shfl_xor_sync(kFull, s, 8);
+  k += __shfl_xor_sync(kFull, k, 4);
+  k += __shfl_xor_sync(kFull, k, 2);
+  k += __shfl_xor_sync(kFull, k, 1);
+  return k;
+}
+
+// quadratic B-spline of unit knot spacing centred at 0 (Sec. II, eq. rotctrl)
+__device__ __forceinline__ double bspline2(double x) {
+  x = fabs(x);
+  if (x < 0.5) return 0.75 - x * x;
+  if (x < 1.5) {
+    const double y = x - 1.5;
+    return 0.5 * y * y;
+  }
+  return 0.0;
+}
+
+__device__ void record_error(DevStatus* st, int code, int step) {
+  if (atomicCAS(&st->code, 0, code) == 0) st->step = step;
+}
+
+// ---------------------------------------------------------------------------
+// per-CTA copy of the problem constants used in the inner loops
+
+struct Hdr {
+  int Q, N, V, NT, K, n_ckpt, max_iter, method, kind, M;
+  double h, rtol;
+  int lev[LB_MAXQ], stride[LB_MAXQ], coff[LB_MAXQ], joff[LB_MAXQ];
+  double jump[LB_MAXQ];
+};
+
+struct Tabs {
+  const double* cu;
+  const double* cd;
+  const double* jf;
+  const double* ja;
+};
+
+__device__ void load_hdr(Hdr& H, const ProbDev& P) {
+  H.Q = P.Q;
+  H.N = P.N;
+  H.V = P.V;
+  H.NT = P.NT;
+  H.K = P.K;
+  H.n_ckpt = P.n_ckpt;
+  H.max_iter = P.max_iter;
+  H.method = P.method;
+  H.kind = P.kind;
+  H.M = P.M;
+  H.h = P.h;
+  H.rtol = P.rtol;
+  for (int q = 0; q < LB_MAXQ; ++q) {
+    H.lev[q] = P.levels[q];
+    H.stride[q] = P.stride[q];
+    H.coff[q] = P.coff[q];
+    H.joff[q] = P.joff[q];
+    H.jump[q] = P.jump[q];
+  }
+}
+
+// (dt/2) (O x)_v accumulated into (ar, ai); O = M - D (or its adjoint part
+// for ADJ).  x is indexed by the state-local vec index; ct[q] = (dt/2) d_q.
+template <bool ADJ>
+__device__ __forceinline__ void offdiag_acc(double& ar, double& ai, const double2* __restrict__ x, int v, uint32_t kd,
+                                            uint32_t ld, const Hdr& H, const Tabs& T, const double2* __restrict__ ct) {
+  const int N = H.N;
+  for (int q = 0; q < H.Q; ++q) {
+    const int n = H.lev[q], s = H.stride[q], co = H.coff[q];
+    const int nk = (kd >> (4 * q)) & 15, nl = (ld >> (4 * q)) & 15;
+    const int sN = s * N;
+    // control: -i[H_c, X] with H_c = d a + conj(d) a^+ (Sec. II):
+    //   P = sqrt(nk+1) x[k+s,l] - sqrt(nl) x[k,l-s]     (a X - X a)
+    //   R = sqrt(nk) x[k-s,l] - sqrt(nl+1) x[k,l+s]     (a^+ X - X a^+)
+    //   -i d P - i conj(d) R = b (P - R) - i a (P + R), d = (a + i b) * 2/dt
+    const double c1 = T.cu[co + nk], c2 = T.cd[co + nl], c3 = T.cd[co + nk], c4 = T.cu[co + nl];
+    const double2 x1 = x[v + (nk + 1 < n ? s : 0)];
+    const double2 x2 = x[v - (nl > 0 ? sN : 0)];
+    const double2 x3 = x[v - (nk > 0 ? s : 0)];
+    const double2 x4 = x[v + (nl + 1 < n ? sN : 0)];
+    const double pr = fma(-c2, x2.x, c1 * x1.x);
+    const double pi = fma(-c2, x2.y, c1 * x1.y);
+    const double rr = fma(-c4, x4.x, c3 * x3.x);
+    const double ri = fma(-c4, x4.y, c3 * x3.y);
+    const double ur = pr + rr, ui = pi + ri, wr = pr - rr, wi = pi - ri;
+    const double2 c = ct[q];
+    // the Hamiltonian part of M^+ is minus that of M
+    const double a = ADJ ? -c.x : c.x, b = ADJ ? -c.y : c.y;
+    ar = fma(b, wr, fma(a, ui, ar));
+    ai = fma(b, wi, fma(-a, ur, ai));
+    if (H.jump[q] != 0.0) {
+      // decay sandwich: M couples x[k+s, l+s], M^+ couples x[k-s, l-s]
+      const int jo = H.joff[q] + nk * n + nl;
+      double cj;
+      double2 x5;
+      if (!ADJ) {
+        cj = T.jf[jo];
+        x5 = x[v + ((nk + 1 < n && nl + 1 < n) ? s + sN : 0)];
+      } else {
+        cj = T.ja[jo];
+        x5 = x[v - ((nk > 0 && nl > 0) ? s + sN : 0)];
+      }
+      ar = fma(cj, x5.x, ar);
+      ai = fma(cj, x5.y, ai);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// resident kernels: shared-memory layout
+
+struct ResSmem {
+  Hdr* hdr;
+  double* cu;
+  double* cd;
+  double* jf;
+  double* ja;
+  uint32_t* dig;
+  unsigned long long* slots;  // [3][16]
+  double* red;                // [4 * LB_MAXQ][16]
+  double2* dsm;               // [V] Dinv (Jacobi) or dt/2 D (Neumann)
+  double2* zb0;               // [V]
+  double2* zb1;               // [V]
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline size_t res_smem_bytes(int ncoef, int njcoef, int N, int V) {
+  size_t b = align16(sizeof(Hdr));
+  b += align16(sizeof(double) * 2 * ncoef);
+  b += align16(sizeof(double) * 2 * njcoef);
+  b += align16(sizeof(uint32_t) * N);
+  b += align16(sizeof(unsigned long long) * 48);
+  b += align16(sizeof(double) * 4 * LB_MAXQ * 16);
+  b += sizeof(double2) * 3 * (size_t)V;
+  return b;
+}
+
+__device__ ResSmem carve(unsigned char* base, int ncoef, int njcoef, int N, int V) {
+  ResSmem S;
+  size_t o = 0;
+  S.hdr = reinterpret_cast<Hdr*>(base + o);
+  o += align16(sizeof(Hdr));
+  S.cu = reinterpret_cast<double*>(base + o);
+  S.cd = S.cu + ncoef;
+  o += align16(sizeof(double) * 2 * ncoef);
+  S.jf = reinterpret_cast<double*>(base + o);
+  S.ja = S.jf + njcoef;
+  o += align16(sizeof(double) * 2 * njcoef);
+  S.dig = reinterpret_cast<uint32_t*>(base + o);
+  o += align16(sizeof(uint32_t) * N);
+  S.slots = reinterpret_cast<unsigned long long*>(base + o);
+  o += align16(sizeof(unsigned long long) * 48);
+  S.red = reinterpret_cast<double*>(base + o);
+  o += align16(sizeof(double) * 4 * LB_MAXQ * 16);
+  S.dsm = reinterpret_cast<double2*>(base + o);
+  S.zb0 = S.dsm + V;
+  S.zb1 = S.zb0 + V;
+  return S;
+}
+
+// Load constants and tables of problem P into shared memory (all threads).
+__device__ void res_setup(const ResSmem& S, const ProbDev& P) {
+  if (threadIdx.x == 0) load_hdr(*S.hdr, P);
+  for (int i = threadIdx.x; i < P.ncoef; i += blockDim.x) {
+    S.cu[i] = P.cu[i];
+    S.cd[i] = P.cd[i];
+  }
+  for (int i = threadIdx.x; i < P.njcoef; i += blockDim.x) {
+    S.jf[i] = P.jf[i];
+    S.ja[i] = P.ja[i];
+  }
+  for (int i = threadIdx.x; i < P.N; i += blockDim.x) S.dig[i] = P.digits[i];
+  const bool neumann = P.method == LB_SOLVER_NEUMANN;
+  const double hh = 0.5 * P.h;
+  for (int i = threadIdx.x; i < P.V; i += blockDim.x) {
+    const double2 d = neumann ? P.D[i] : P.Dinv[i];
+    S.dsm[i] = neumann ? make_double2(hh * d.x, hh * d.y) : d;
+  }
+  __syncthreads();
+}
+
+template <int E>
+struct Elems {
+  uint32_t kd[E], ld[E];
+};
+
+template <int E>
+__device__ __forceinline__ void init_elems(Elems<E>& el, const ResSmem& S, int V, int N) {
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int v = threadIdx.x + e * blockDim.x;
+    if (v < V) {
+      el.kd[e] = S.dig[v % N];
+      el.ld[e] = S.dig[v / N];
+    } else {
+      el.kd[e] = el.ld[e] = 0;
+    }
+  }
+}
+
+// Solve (I - dt/2 M) z = rhs (ADJ: (I - dt/2 M^+) z = rhs) for the CTA's
+// state.  Returns the iteration count (>= 1), -1 when max_iter is reached,
+// -2 on NaN/Inf.  On return, zbuf[cur] holds z; every thread has passed the
+// final barrier.
+template <int E, bool ADJ>
+__device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, const double2 (&rhs)[E],
+                         const double2* __restrict__ ct, int& cur) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const bool neumann = H.method == LB_SOLVER_NEUMANN;
+  const Tabs T{S.cu, S.cd, S.jf, S.ja};
+  unsigned long long qmax = 0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int v = threadIdx.x + e * blockDim.x;
+    if (v < H.V) {
+      double2 z0 = rhs[e];
+      if (!neumann) {
+        const double2 d = S.dsm[v];
+        const double di = ADJ ? -d.y : d.y;
+        z0 = make_double2(fma(d.x, rhs[e].x, -di * rhs[e].y), fma(d.x, rhs[e].y, di * rhs[e].x));
+      }
+      S.zb0[v] = z0;
+      qmax = umax64(qmax, umax64(abs_bits(rhs[e].x), abs_bits(rhs[e].y)));
+    }
+  }
+  qmax = warp_max_u64(qmax);
+  if (lane == 0) S.slots[32 + warp] = qmax;
+  __syncthreads();
+  qmax = 0;
+  for (int w = 0; w < nwarps; ++w) qmax = umax64(qmax, S.slots[32 + w]);
+  if (qmax >= kInfBits) return -2;
+  const unsigned long long thr = abs_bits(H.rtol * __longlong_as_double(static_cast<long long>(qmax)));
+  cur = 0;
+  for (int it = 0; it < H.max_iter; ++it) {
+    const double2* __restrict__ zc = cur ? S.zb1 : S.zb0;
+    double2* __restrict__ zn = cur ? S.zb0 : S.zb1;
+    unsigned long long dmax = 0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int v = threadIdx.x + e * blockDim.x;
+      if (v < H.V) {
+        double ar = rhs[e].x, ai = rhs[e].y;
+        offdiag_acc<ADJ>(ar, ai, zc, v, el.kd[e], el.ld[e], H, T, ct);
+        const double2 d = S.dsm[v];
+        const double di = ADJ ? -d.y : d.y;
+        const double2 zo = zc[v];
+        double2 z;
+        if (!neumann) {
+          z.x = fma(d.x, ar, -di * ai);
+          z.y = fma(d.x, ai, di * ar);
+        } else {
+          z.x = ar + fma(d.x, zo.x, -di * zo.y);
+          z.y = ai + fma(d.x, zo.y, di * zo.x);
+        }
+        zn[v] = z;
+        dmax = umax64(dmax, umax64(abs_bits(z.x - zo.x), abs_bits(z.y - zo.y)));
+      }
+    }
+    dmax = warp_max_u64(dmax);
+    if (lane == 0) S.slots[(it & 1) * 16 + warp] = dmax;
+    __syncthreads();
+    dmax = 0;
+    for (int w = 0; w < nwarps; ++w) dmax = umax64(dmax, S.slots[(it & 1) * 16 + w]);
+    cur ^= 1;
+    if (dmax >= kInfBits) return -2;
+    if (dmax <= thr) return it + 1;
+  }
+  return -1;
+}
+
+// Deterministic CTA sum of one double per thread; the result is returned to
+// every thread.  Uses S.red[0..15] and two barriers.
+__device__ double cta_sum(const ResSmem& S, double x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  x = warp_sum(x);
+  if (lane == 0) S.red[warp] = x;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < nwarps; ++w) t += S.red[w];
+  __syncthreads();
+  return t;
+}
+
+struct CtaStats {
+  unsigned long long iters[3] = {0, 0, 0}, steps[3] = {0, 0, 0};
+  int maxit = 0;
+  __device__ void add(int phase, int it) {
+    iters[phase] += it;
+    steps[phase] += 1;
+    maxit = it > maxit ? it : maxit;
+  }
+  __device__ void flush(DevStatus* st) {
+    if (threadIdx.x == 0) {
+      for (int p = 0; p < 3; ++p)
+        if (steps[p]) {
+          atomicAdd(&st->iters[p], iters[p]);
+          atomicAdd(&st->steps[p], steps[p]);
+        }
+      atomicMax(&st->max_iter_seen, maxit);
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// forward sweep, one CTA per (problem, state) work item
+
+template <int E>
+__global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__ probs,
+                                                     const WorkItem* __restrict__ items, int tape) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const WorkItem wi = items[blockIdx.x];
+  const ProbDev& P = probs[wi.prob];
+  const int i = wi.state;
+  const ResSmem S = carve(smem, P.ncoef, P.njcoef, P.N, P.V);
+  res_setup(S, P);
+  const Hdr& H = *S.hdr;
+  Elems<E> el;
+  init_elems<E>(el, S, H.V, H.N);
+  const size_t base = (size_t)i * H.V;
+  double2 q[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int v = threadIdx.x + e * blockDim.x;
+    q[e] = v < H.V ? P.q0[base + v] : make_double2(0.0, 0.0);
+  }
+  CtaStats stats;
+  for (int j = 0; j < H.NT; ++j) {
+    if (tape && H.K > 0 && j % H.K == 0) {
+      double2* ck = P.ckpt + ((size_t)i * H.n_ckpt + j / H.K) * H.V;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int v = threadIdx.x + e * blockDim.x;
+        if (v < H.V) ck[v] = q[e];
+      }
+    }
+    int cur;
+    const int it = res_solve<E, false>(S, H, el, q, P.ctab + (size_t)j * H.Q, cur);
+    if (it < 0) {
+      if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
+      stats.flush(P.status);
+      return;
+    }
+    stats.add(0, it);
+    const double2* zc = cur ? S.zb1 : S.zb0;
+    double2* tp = (tape && H.K == 0) ? P.ckpt + ((size_t)i * H.NT + j) * H.V : nullptr;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int v = threadIdx.x + e * blockDim.x;
+      if (v < H.V) {
+        const double2 z = zc[v];
+        if (tp) tp[v] = z;
+        // q^{j+1} = q^j + dt M z = 2 z - q^j  (eq. IMR with eq. linsystem_primal)
+        q[e] = make_double2(fma(2.0, z.x, -q[e].x), fma(2.0, z.y, -q[e].y));
+      }
+    }
+  }
+  // final state and merit functional (Sec. III)
+  double acc = 0.0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int v = threadIdx.x + e * blockDim.x;
+    if (v < H.V) {
+      P.qT[base + v] = q[e];
+      const double2 t = P.tar[base + v];
+      if (H.kind == LB_J_FROB) {
+        const double dr = q[e].x - t.x, di = q[e].y - t.y;
+        acc = fma(dr, dr, fma(di, di, acc));
+      } else {
+        acc = fma(t.x, q[e].x, fma(t.y, q[e].y, acc));
+      }
+    }
+  }
+  const double tot = cta_sum(S, acc);
+  if (threadIdx.x == 0) P.J[i] = H.kind == LB_J_FROB ? 0.5 * tot : 1.0 - tot;
+  stats.flush(P.status);
+}
+
+// ---------------------------------------------------------------------------
+// backward sweep: recompute each checkpoint segment, then adjoint steps with
+// the gradient pieces of eq. reducedgradient.
+
+template <int E>
+__global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict__ probs,
+                                                      const WorkItem* __restrict__ items) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const WorkItem wi = items[blockIdx.x];
+  const ProbDev& P = probs[wi.prob];
+  const int i = wi.state;
+  const ResSmem S = carve(smem, P.ncoef, P.njcoef, P.N, P.V);
+  res_setup(S, P);
+  const Hdr& H = *S.hdr;
+  Elems<E> el;
+  init_elems<E>(el, S, H.V, H.N);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const size_t base = (size_t)i * H.V;
+  const double w = P.wgt[i];
+  // terminal condition qhat^{N_T} = beta_i/M g_i (Appendix B): g = q - q_tar
+  // for J_Frob, g = -q_tar for J_Tr
+  double2 lam[E], qf[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int v = threadIdx.x + e * blockDim.x;
+    lam[e] = make_double2(0.0, 0.0);
+    qf[e] = lam[e];
+    if (v < H.V) {
+      const double2 t = P.tar[base + v];
+      if (H.kind == LB_J_FROB) {
+        const double2 qq = P.qT[base + v];
+        lam[e] = make_double2(w * (qq.x - t.x), w * (qq.y - t.y));
+      } else {
+        lam[e] = make_double2(-w * t.x, -w * t.y);
+      }
+    }
+  }
+  CtaStats stats;
+  const int nseg = H.K > 0 ? (H.NT + H.K - 1) / H.K : 1;
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int j0 = H.K > 0 ? sg * H.K : 0;
+    const int j1 = H.K > 0 ? min(H.NT, j0 + H.K) : H.NT;
+    if (H.K > 0) {
+      // recompute the stage vectors z^j of this segment from its checkpoint
+      const double2* ck = P.ckpt + ((size_t)i * H.n_ckpt + sg) * H.V;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int v = threadIdx.x + e * blockDim.x;
+        if (v < H.V) qf[e] = ck[v];
+      }
+      for (int j = j0; j < j1; ++j) {
+        int cur;
+        const int it = res_solve<E, false>(S, H, el, qf, P.ctab + (size_t)j * H.Q, cur);
+        if (it < 0) {
+          if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
+          stats.flush(P.status);
+          return;
+        }
+        stats.add(1, it);
+        const double2* zc = cur ? S.zb1 : S.zb0;
+        double2* sgv = P.seg + ((size_t)i * H.K + (j - j0)) * H.V;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int v = threadIdx.x + e * blockDim.x;
+          if (v < H.V) {
+            const double2 z = zc[v];
+            sgv[v] = z;
+            qf[e] = make_double2(fma(2.0, z.x, -qf[e].x), fma(2.0, z.y, -qf[e].y));
+          }
+        }
+      }
+    }
+    for (int j = j1 - 1; j >= j0; --j) {
+      const double2* ct = P.ctab + (size_t)j * H.Q;
+      int cur;
+      // (I - dt/2 (M^{j+1/2})^+) zhat^j = qhat^{j+1}   (eq. linsystem_adjoint)
+      const int it = res_solve<E, true>(S, H, el, lam, ct, cur);
+      if (it < 0) {
+        if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
+        stats.flush(P.status);
+        return;
+      }
+      stats.add(2, it);
+      const double2* zh = cur ? S.zb1 : S.zb0;
+      const double2* Zt = H.K > 0 ? P.seg + ((size_t)i * H.K + (j - j0)) * H.V : P.ckpt + ((size_t)i * H.NT + j) * H.V;
+      // gradient pieces (eq. reducedgradient): for every subsystem q,
+      //   g_a  = zhat^H vec(-i[a_q, Z])   = -i sum_kl Z_kl conj(R_zhat)
+      //   g_ad = zhat^H vec(-i[a_q^+, Z]) = -i sum_kl Z_kl conj(P_zhat)
+      // (index shift of the commutator onto zhat), with P, R as in offdiag_acc.
+      double2 Z[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int v = threadIdx.x + e * blockDim.x;
+        Z[e] = v < H.V ? Zt[v] : make_double2(0.0, 0.0);
+      }
+      for (int q = 0; q < H.Q; ++q) {
+        const int n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * H.N;
+        double sar = 0.0, sai = 0.0, sdr = 0.0, sdi = 0.0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int v = threadIdx.x + e * blockDim.x;
+          if (v < H.V) {
+            const int nk = (el.kd[e] >> (4 * q)) & 15, nl = (el.ld[e] >> (4 * q)) & 15;
+            const double c1 = S.cu[co + nk], c2 = S.cd[co + nl], c3 = S.cd[co + nk], c4 = S.cu[co + nl];
+            const double2 x1 = zh[v + (nk + 1 < n ? s : 0)];
+            const double2 x2 = zh[v - (nl > 0 ? sN : 0)];
+            const double2 x3 = zh[v - (nk > 0 ? s : 0)];
+            const double2 x4 = zh[v + (nl + 1 < n ? sN : 0)];
+            const double pr = fma(-c2, x2.x, c1 * x1.x);
+            const double pi = fma(-c2, x2.y, c1 * x1.y);
+            const double rr = fma(-c4, x4.x, c3 * x3.x);
+            const double ri = fma(-c4, x4.y, c3 * x3.y);
+            // Z conj(R) and Z conj(P)
+            sar = fma(Z[e].x, rr, fma(Z[e].y, ri, sar));
+            sai = fma(Z[e].y, rr, fma(-Z[e].x, ri, sai));
+            sdr = fma(Z[e].x, pr, fma(Z[e].y, pi, sdr));
+            sdi = fma(Z[e].y, pr, fma(-Z[e].x, pi, sdi));
+          }
+        }
+        const double r = warp_sum4(sar, sai, sdr, sdi, lane);
+        if ((lane & 7) == 0) S.red[(q * 4 + (lane >> 3)) * 16 + warp] = r;
+      }
+      __syncthreads();
+      if (threadIdx.x < 4 * H.Q) {
+        double t = 0.0;
+        for (int ww = 0; ww < nwarps; ++ww) t += S.red[threadIdx.x * 16 + ww];
+        const int q = threadIdx.x >> 2, c = threadIdx.x & 3;
+        // multiply by -i: g = (S.im, -S.re)
+        double* g = reinterpret_cast<double*>(P.gproj + (((size_t)i * H.NT + j) * H.Q + q) * 2);
+        if (c == 0) g[1] = -t;
+        if (c == 1) g[0] = t;
+        if (c == 2) g[3] = -t;
+        if (c == 3) g[2] = t;
+      }
+      // qhat^j = qhat^{j+1} + dt M^+ zhat = 2 zhat - qhat^{j+1}
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int v = threadIdx.x + e * blockDim.x;
+        if (v < H.V) {
+          const double2 z = zh[v];
+          lam[e] = make_double2(fma(2.0, z.x, -lam[e].x), fma(2.0, z.y, -lam[e].y));
+        }
+      }
+    }
+  }
+  stats.flush(P.status);
+}
+
+// ---------------------------------------------------------------------------
+// propagate given vectors (tests and the step-level API), one CTA per vector
+
+template <int E>
+__global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict__ pp, int adjoint, int j0, int j1,
+                                                       double2* __restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const ProbDev& P = *pp;
+  const ResSmem S = carve(smem, P.ncoef, P.njcoef, P.N, P.V);
+  res_setup(S, P);
+  const Hdr& H = *S.hdr;
+  Elems<E> el;
+  init_elems<E>(el, S, H.V, H.N);
+  double2* xv = x + (size_t)blockIdx.x * H.V;
+  double2 q[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int v = threadIdx.x + e * blockDim.x;
+    q[e] = v < H.V ? xv[v] : make_double2(0.0, 0.0);
+  }
+  CtaStats stats;
+  for (int jj = 0; jj < j1 - j0; ++jj) {
+    const int j = adjoint ? j1 - 1 - jj : j0 + jj;
+    int cur;
+    const int it = adjoint ? res_solve<E, true>(S, H, el, q, P.ctab + (size_t)j * H.Q, cur)
+                           : res_solve<E, false>(S, H, el, q, P.ctab + (size_t)j * H.Q, cur);
+    if (it < 0) {
+      if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
+      stats.flush(P.status);
+      return;
+    }
+    stats.add(adjoint ? 2 : 0, it);
+    const double2* zc = cur ? S.zb1 : S.zb0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int v = threadIdx.x + e * blockDim.x;
+      if (v < H.V) {
+        const double2 z = zc[v];
+        q[e] = make_double2(fma(2.0, z.x, -q[e].x), fma(2.0, z.y, -q[e].y));
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int v = threadIdx.x + e * blockDim.x;
+    if (v < H.V) xv[v] = q[e];
+  }
+  stats.flush(P.status);
+}
+
+// ---------------------------------------------------------------------------
+// small kernels
+
+// Time-independent tables: diagonal D of M and 1/(1 - dt/2 D) (Appendix A),
+// digit table, coefficient tables.
+__global__ void k_tables(ProbDev* __restrict__ pp) {
+  const ProbDev& P = *pp;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int Q = P.Q, N = P.N;
+  const double* det = P.sysp;
+  const double* kerr = det + Q;
+  const double* xkerr = kerr + Q;
+  const double* g1 = xkerr + Q * Q;
+  const double* g2 = g1 + Q;
+  if (tid < N) {
+    uint32_t code = 0;
+    int rem = tid;
+    for (int q = Q - 1; q >= 0; --q) {
+      code |= (uint32_t)(rem % P.levels[q]) << (4 * q);
+      rem /= P.levels[q];
+    }
+    P.digits[tid] = code;
+  }
+  if (tid < P.ncoef) {
+    int q = 0;
+    while (q + 1 < Q && P.coff[q + 1] <= tid) ++q;
+    const int n = tid - P.coff[q];
+    P.cu[tid] = n + 1 < P.levels[q] ? sqrt((double)(n + 1)) : 0.0;
+    P.cd[tid] = sqrt((double)n);
+  }
+  if (tid < P.njcoef) {
+    int q = 0;
+    while (q + 1 < Q && P.joff[q + 1] <= tid) ++q;
+    const int r = tid - P.joff[q], n = P.levels[q];
+    const int nk = r / n, nl = r % n;
+    const double j = P.jump[q];
+    P.jf[tid] = (nk + 1 < n && nl + 1 < n) ? j * sqrt((double)(nk + 1) * (double)(nl + 1)) : 0.0;
+    P.ja[tid] = j * sqrt((double)nk * (double)nl);
+  }
+  if (tid < P.V) {
+    const int k = tid % N, l = tid / N;
+    // E_k = sum_q [delta_q n_q - xi_q/2 n_q(n_q-1)] - sum_{p<q} xi_pq n_p n_q  (H_sys, Sec. II)
+    // gamma_kl = sum_q [(nk - nl)^2/(2 T2) + (nk + nl)/(2 T1)]                 (collapse operators)
+    int dk[LB_MAXQ], dl[LB_MAXQ];
+    int rk = k, rl = l;
+    for (int q = Q - 1; q >= 0; --q) {
+      dk[q] = rk % P.levels[q];
+      rk /= P.levels[q];
+      dl[q] = rl % P.levels[q];
+      rl /= P.levels[q];
+    }
+    double Ek = 0.0, El = 0.0, gam = 0.0;
+    for (int q = 0; q < Q; ++q) {
+      const double a = dk[q], b = dl[q];
+      Ek += det[q] * a - 0.5 * kerr[q] * a * (a - 1.0);
+      El += det[q] * b - 0.5 * kerr[q] * b * (b - 1.0);
+      gam += 0.5 * (a - b) * (a - b) * g2[q] + 0.5 * (a + b) * g1[q];
+      for (int p = 0; p < q; ++p) {
+        Ek -= xkerr[p * Q + q] * dk[p] * a;
+        El -= xkerr[p * Q + q] * dl[p] * b;
+      }
+    }
+    const double2 D = make_double2(-gam, -(Ek - El));  // -i(E_k - E_l) - gamma_kl
+    P.D[tid] = D;
+    const double hh = 0.5 * P.h;
+    const double ar = 1.0 - hh * D.x, ai = -hh * D.y;  // 1 - dt/2 D
+    const double den = ar * ar + ai * ai;
+    P.Dinv[tid] = make_double2(ar / den, -ai / den);
+  }
+}
+
+// rho_i^tar = V rho_i(0) V^+ with V lifted to the full space (Sec. III-C)
+__global__ void k_gate_targets(ProbDev P, const double2* __restrict__ Vg, const int32_t* __restrict__ emap,
+                               const int32_t* __restrict__ efull, int Ne) {
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (size_t)P.M * P.V) return;
+  const int i = (int)(tid / P.V), v = (int)(tid % P.V);
+  const int k = v % P.N, l = v / P.N;
+  const int ek = emap[k], el = emap[l];
+  double2 acc = make_double2(0.0, 0.0);
+  if (ek >= 0 && el >= 0) {
+    const double2* r = P.q0 + (size_t)i * P.V;
+    for (int b = 0; b < Ne; ++b) {
+      const double2 vb = Vg[el + (size_t)Ne * b];  // V[el, b]
+      for (int a = 0; a < Ne; ++a) {
+        const double2 va = Vg[ek + (size_t)Ne * a];  // V[ek, a]
+        const double2 x = r[efull[a] + (size_t)P.N * efull[b]];
+        // va * x * conj(vb)
+        const double tr = va.x * x.x - va.y * x.y, ti = va.x * x.y + va.y * x.x;
+        acc.x += tr * vb.x + ti * vb.y;
+        acc.y += ti * vb.x - tr * vb.y;
+      }
+    }
+  }
+  P.tar[tid] = acc;
+}
+
+// (dt/2) d_q(t_j + dt/2) for every step j and subsystem q (eq. rotctrl)
+__global__ void k_control_table(const ProbDev* __restrict__ pp) {
+  const ProbDev& P = *pp;
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (size_t)P.NT * P.Q) return;
+  const int j = (int)(tid / P.Q), q = (int)(tid % P.Q);
+  const double t = (j + 0.5) * P.h;
+  const double dtau = P.T / (P.Ns - 2);
+  const double x = t / dtau;
+  const int slo = max(0, (int)floor(x - 1.0)), shi = min(P.Ns - 1, (int)floor(x + 2.0));
+  double dr = 0.0, di = 0.0;
+  for (int f = 0; f < P.nf[q]; ++f) {
+    double sn, cs;
+    sincos(P.carriers[P.foff[q] + f] * t, &sn, &cs);
+    double wr = 0.0, wi = 0.0;
+    for (int s = slo; s <= shi; ++s) {
+      const double S = bspline2(x - (s - 0.5));
+      const double* a = P.alpha + P.aoff[q] + 2 * (f * P.Ns + s);
+      wr += S * a[0];
+      wi += S * a[1];
+    }
+    dr += wr * cs - wi * sn;
+    di += wr * sn + wi * cs;
+  }
+  const double sc = 0.5 * P.h * kTwoPi;
+  P.ctab[tid] = make_double2(sc * dr, sc * di);
+}
+
+// G = sum_i beta_i/M J_i + gamma2/2 ||alpha||^2 (eq. optimproblem), one warp
+__global__ void k_objective(const ProbDev* __restrict__ probs) {
+  const ProbDev& P = probs[blockIdx.x];
+  const int lane = threadIdx.x;
+  double s = 0.0, a2 = 0.0;
+  for (int i = lane; i < P.M; i += 32) s += P.wgt[i] * P.J[i];
+  for (int k = lane; k < P.n_params; k += 32) a2 += P.alpha[k] * P.alpha[k];
+  s = warp_sum(s);
+  a2 = warp_sum(a2);
+  if (lane == 0) P.G[0] = s + 0.5 * P.gamma2 * a2;
+}
+
+// dG/dalpha (eq. reducedgradient): one warp per (q, f, s); the sum over the
+// spline's support in time and over the states is in a fixed order.
+__global__ void k_gradient_project(const ProbDev* __restrict__ probs) {
+  const ProbDev& P = probs[blockIdx.y];
+  const int lane = threadIdx.x & 31;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int q = 0, rem = gw;
+  while (q < P.Q && rem >= P.nf[q] * P.Ns) {
+    rem -= P.nf[q] * P.Ns;
+    ++q;
+  }
+  if (q >= P.Q) return;
+  const int f = rem / P.Ns, s = rem % P.Ns;
+  const double om = P.carriers[P.foff[q] + f];
+  const double dtau = P.T / (P.Ns - 2);
+  // S_s(t) > 0 for t in ((s - 2) dtau, (s + 1) dtau)
+  const int jlo = max(0, (int)floor((s - 2) * dtau / P.h - 1.0));
+  const int jhi = min(P.NT - 1, (int)ceil((s + 1) * dtau / P.h));
+  double gr = 0.0, gi = 0.0;
+  for (int j = jlo + lane; j <= jhi; j += 32) {
+    const double t = (j + 0.5) * P.h;
+    const double S = bspline2(t / dtau - (s - 0.5));
+    if (S == 0.0) continue;
+    double ga_r = 0.0, ga_i = 0.0, gd_r = 0.0, gd_i = 0.0;
+    for (int i = 0; i < P.M; ++i) {
+      const double2* g = P.gproj + (((size_t)i * P.NT + j) * P.Q + q) * 2;
+      ga_r += g[0].x;
+      ga_i += g[0].y;
+      gd_r += g[1].x;
+      gd_i += g[1].y;
+    }
+    double sn, cs;
+    sincos(om * t, &sn, &cs);
+    // Re(e^{iOt} g_a + e^{-iOt} g_ad) and Re(i e^{iOt} g_a - i e^{-iOt} g_ad)
+    gr += S * (cs * ga_r - sn * ga_i + cs * gd_r + sn * gd_i);
+    gi += S * (-(cs * ga_i + sn * ga_r) + cs * gd_i - sn * gd_r);
+  }
+  gr = warp_sum(gr);
+  gi = warp_sum(gi);
+  if (lane == 0) {
+    const int k = P.aoff[q] + 2 * (f * P.Ns + s);
+    const double sc = P.h * kTwoPi;
+    P.grad[k] = sc * gr + P.gamma2 * P.alpha[k];
+    P.grad[k + 1] = sc * gi + P.gamma2 * P.alpha[k + 1];
+  }
+}
+
+// G, gradient and status of every system of a batch into contiguous arrays
+__global__ void k_gather(const ProbDev* __restrict__ probs, const int64_t* __restrict__ grad_off,
+                         double* __restrict__ G_all, double* __restrict__ grad_all, DevStatus* __restrict__ st_all) {
+  const ProbDev& P = probs[blockIdx.x];
+  if (threadIdx.x == 0) {
+    if (G_all) G_all[blockIdx.x] = P.G[0];
+    if (st_all) st_all[blockIdx.x] = *P.status;
+  }
+  if (grad_all)
+    for (int k = threadIdx.x; k < P.n_params; k += blockDim.x) grad_all[grad_off[blockIdx.x] + k] = P.grad[k];
+}
+
+// y = M^{j+1/2} x or (M^{j+1/2})^+ x, one thread per element
+template <bool ADJ>
+__global__ void k_apply(const ProbDev* __restrict__ pp, int step, const double2* __restrict__ x,
+                        double2* __restrict__ y, int n_vec) {
+  __shared__ Hdr H;
+  const ProbDev& P = *pp;
+  if (threadIdx.x == 0) load_hdr(H, P);
+  __syncthreads();
+  const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (size_t)n_vec * H.V) return;
+  const int b = (int)(tid / H.V), v = (int)(tid % H.V);
+  const int k = v % H.N, l = v / H.N;
+  const Tabs T{P.cu, P.cd, P.jf, P.ja};
+  const double2* xv = x + (size_t)b * H.V;
+  double ar = 0.0, ai = 0.0;
+  offdiag_acc<ADJ>(ar, ai, xv, v, P.digits[k], P.digits[l], H, T, P.ctab + (size_t)step * H.Q);
+  const double inv = 2.0 / H.h;
+  const double2 D = P.D[v];
+  const double di = ADJ ? -D.y : D.y;
+  const double2 xx = xv[v];
+  y[tid] = make_double2(fma(D.x, xx.x, -di * xx.y) + inv * ar, fma(D.x, xx.y, di * xx.x) + inv * ai);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+
+ResidentConfig resident_config(int maxV, int maxQ, int maxNcoef, int maxNj, int maxN) {
+  (void)maxQ;
+  ResidentConfig rc;
+  int E = 1;
+  while (E < 8 && (maxV + E - 1) / E > 512) E *= 2;
+  int threads = (maxV + E - 1) / E;
+  threads = ((threads + 31) / 32) * 32;
+  if (threads < 32) threads = 32;
+  rc.threads = threads;
+  rc.E = E;
+  rc.smem = res_smem_bytes(maxNcoef, maxNj, maxN, maxV);
+  return rc;
+}
+
+template <int E>
+static cudaError_t set_smem_attr(size_t smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_forward_res<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k_backward_res<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_propagate_res<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+static cudaError_t prepare(const ResidentConfig& rc) {
+  switch (rc.E) {
+    case 1: return set_smem_attr<1>(rc.smem);
+    case 2: return set_smem_attr<2>(rc.smem);
+    case 4: return set_smem_attr<4>(rc.smem);
+    case 8: return set_smem_attr<8>(rc.smem);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_forward_resident(const ProbDev* d_probs, const WorkItem* d_items, int n_items, int tape,
+                                    const ResidentConfig& rc, cudaStream_t s) {
+  cudaError_t e = prepare(rc);
+  if (e != cudaSuccess) return e;
+  dim3 g(n_items), b(rc.threads);
+  switch (rc.E) {
+    case 1: k_forward_res<1><<<g, b, rc.smem, s>>>(d_probs, d_items, tape); break;
+    case 2: k_forward_res<2><<<g, b, rc.smem, s>>>(d_probs, d_items, tape); break;
+    case 4: k_forward_res<4><<<g, b, rc.smem, s>>>(d_probs, d_items, tape); break;
+    case 8: k_forward_res<8><<<g, b, rc.smem, s>>>(d_probs, d_items, tape); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward_resident(const ProbDev* d_probs, const WorkItem* d_items, int n_items,
+                                     const ResidentConfig& rc, cudaStream_t s) {
+  cudaError_t e = prepare(rc);
+  if (e != cudaSuccess) return e;
+  dim3 g(n_items), b(rc.threads);
+  switch (rc.E) {
+    case 1: k_backward_res<1><<<g, b, rc.smem, s>>>(d_probs, d_items); break;
+    case 2: k_backward_res<2><<<g, b, rc.smem, s>>>(d_probs, d_items); break;
+    case 4: k_backward_res<4><<<g, b, rc.smem, s>>>(d_probs, d_items); break;
+    case 8: k_backward_res<8><<<g, b, rc.smem, s>>>(d_probs, d_items); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_propagate_resident(const ProbDev* d_prob, int adjoint, int64_t j0, int64_t j1, double2* x,
+                                      int n_vec, const ResidentConfig& rc, cudaStream_t s) {
+  cudaError_t e = prepare(rc);
+  if (e != cudaSuccess) return e;
+  dim3 g(n_vec), b(rc.threads);
+  switch (rc.E) {
+    case 1: k_propagate_res<1><<<g, b, rc.smem, s>>>(d_prob, adjoint, (int)j0, (int)j1, x); break;
+    case 2: k_propagate_res<2><<<g, b, rc.smem, s>>>(d_prob, adjoint, (int)j0, (int)j1, x); break;
+    case 4: k_propagate_res<4><<<g, b, rc.smem, s>>>(d_prob, adjoint, (int)j0, (int)j1, x); break;
+    case 8: k_propagate_res<8><<<g, b, rc.smem, s>>>(d_prob, adjoint, (int)j0, (int)j1, x); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tables(ProbDev* d_prob, const ProbDev& h, cudaStream_t s) {
+  int n = h.V > h.njcoef ? h.V : h.njcoef;
+  if (h.ncoef > n) n = h.ncoef;
+  if (h.N > n) n = h.N;
+  k_tables<<<(n + 255) / 256, 256, 0, s>>>(d_prob);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gate_targets(const ProbDev& h, const double2* Vg, const int32_t* emap, const int32_t* efull,
+                                int32_t Ne, cudaStream_t s) {
+  const size_t n = (size_t)h.M * h.V;
+  k_gate_targets<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(h, Vg, emap, efull, Ne);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_control_table(const ProbDev* d_prob, const ProbDev& h, cudaStream_t s) {
+  const size_t n = (size_t)h.NT * h.Q;
+  k_control_table<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_prob);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const ProbDev* d_probs, int n_probs, int max_param_warps, int with_grad, cudaStream_t s) {
+  k_objective<<<n_probs, 32, 0, s>>>(d_probs);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !with_grad) return e;
+  const int threads = 128;
+  dim3 grid((max_param_warps * 32 + threads - 1) / threads, n_probs);
+  k_gradient_project<<<grid, threads, 0, s>>>(d_probs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const ProbDev* d_probs, int n_probs, const int64_t* grad_off, double* G_all,
+                          double* grad_all, DevStatus* st_all, cudaStream_t s) {
+  k_gather<<<n_probs, 128, 0, s>>>(d_probs, grad_off, G_all, grad_all, st_all);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply(const ProbDev* d_prob, const ProbDev& h, int adjoint, int64_t step, const double2* x,
+                         double2* y, int n_vec, cudaStream_t s) {
+  const size_t n = (size_t)n_vec * h.V;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (adjoint)
+    k_apply<true><<<blocks, 256, 0, s>>>(d_prob, (int)step, x, y, n_vec);
+  else
+    k_apply<false><<<blocks, 256, 0, s>>>(d_prob, (int)step, x, y, n_vec);
+  return cudaGetLastError();
+}
+
+}  // namespace lbk

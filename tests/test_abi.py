@@ -1,0 +1,170 @@
+"""The C-ABI library loads, exports every symbol the header declares, and its
+host-side validation behaves as documented.  No device call is made."""
+
+import ctypes
+import os
+import re
+from ctypes import POINTER, byref, c_double, c_int32, c_size_t, c_void_p
+
+import numpy as np
+import pytest
+
+import workloads as W
+from paper_2110_10310_gb300 import _lib as L
+from paper_2110_10310_gb300.system import colmajor
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lindblad_gb300.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return L.load(build_if_missing=True)
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_symbols_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(lib, n), n
+        assert n in L.SIGNATURES, n
+    assert set(L.SIGNATURES) == set(names)
+    assert b"sm_103a" in lib.lb_version()
+
+
+def _desc(sysm, keep):
+    def arr(x, ct, dt):
+        a = np.ascontiguousarray(np.asarray(x, dtype=dt))
+        keep.append(a)
+        return a.ctypes.data_as(POINTER(ct))
+
+    Q = len(sysm.levels)
+    d = L.lb_system_desc()
+    d.Q = Q
+    d.levels = arr(sysm.levels, c_int32, np.int32)
+    d.essential = arr(sysm.essential, c_int32, np.int32) if sysm.essential is not None else None
+    d.detuning_ghz = arr(sysm.detuning_ghz, c_double, np.float64)
+    d.selfkerr_ghz = arr(sysm.selfkerr_ghz, c_double, np.float64)
+    d.crosskerr_ghz = arr(np.asarray(sysm.crosskerr_ghz).reshape(-1), c_double, np.float64)
+    d.t1_us = arr(sysm.t1_us, c_double, np.float64)
+    d.t2_us = arr(sysm.t2_us, c_double, np.float64)
+    d.T_ns = sysm.T_ns
+    d.n_steps = sysm.n_steps
+    return d
+
+
+def _make(lib, prob, K=100):
+    keep = []
+    d = _desc(prob.system, keep)
+    h = c_void_p()
+    L.check(lib.lb_system_create(byref(d), byref(h)))
+    c = prob.controls
+    nf = np.array([len(x) for x in c.carriers_ghz], dtype=np.int32)
+    car = np.concatenate(c.carriers_ghz).astype(np.float64)
+    L.check(lib.lb_controls_define(h, c.n_splines, nf.ctypes.data_as(POINTER(c_int32)),
+                                   car.ctypes.data_as(POINTER(c_double))))
+    a = np.ascontiguousarray(c.alpha)
+    L.check(lib.lb_controls_set(h, a.ctypes.data_as(POINTER(c_double)), a.size))
+    r = colmajor(prob.rho0)
+    L.check(lib.lb_states_set(h, prob.M, r.ctypes.data_as(c_void_p), None))
+    L.check(lib.lb_solver_set(h, 0, 1e-15, 200, K))
+    return h
+
+
+def test_create_validation(lib):
+    p = W.config2(n_steps=10)
+    keep = []
+    h = c_void_p()
+    d = _desc(p.system, keep)
+    d.Q = 0
+    assert lib.lb_system_create(byref(d), byref(h)) == L.LB_EINVAL
+    assert b"Q" in lib.lb_last_error()
+    d = _desc(p.system, keep)
+    d.n_steps = 0
+    assert lib.lb_system_create(byref(d), byref(h)) == L.LB_EINVAL
+    d = _desc(p.system, keep)
+    d.T_ns = -1.0
+    assert lib.lb_system_create(byref(d), byref(h)) == L.LB_EINVAL
+    bad = np.array([3, 1], dtype=np.int32)
+    d = _desc(p.system, keep)
+    d.levels = bad.ctypes.data_as(POINTER(c_int32))
+    assert lib.lb_system_create(byref(d), byref(h)) == L.LB_EINVAL
+    big = np.array([16, 16, 16, 16], dtype=np.int32)
+    p4 = W.config4(n_steps=10)
+    d = _desc(p4.system, keep)
+    d.levels = big.ctypes.data_as(POINTER(c_int32))
+    assert lib.lb_system_create(byref(d), byref(h)) == L.LB_EINVAL  # N > 2^15
+
+
+def test_controls_and_states_validation(lib):
+    p = W.config1(n_steps=10)
+    h = _make(lib, p)
+    try:
+        a = np.zeros(7)
+        assert lib.lb_controls_set(h, a.ctypes.data_as(POINTER(c_double)), 7) == L.LB_EINVAL
+        a = np.zeros(20)
+        a[3] = np.nan
+        assert lib.lb_controls_set(h, a.ctypes.data_as(POINTER(c_double)), 20) == L.LB_EINVAL
+        assert b"non-finite" in lib.lb_last_error()
+        nf = np.array([1], dtype=np.int32)
+        car = np.zeros(1)
+        assert lib.lb_controls_define(h, 2, nf.ctypes.data_as(POINTER(c_int32)),
+                                      car.ctypes.data_as(POINTER(c_double))) == L.LB_EINVAL
+        r = colmajor(p.rho0)
+        assert lib.lb_states_set(h, 0, r.ctypes.data_as(c_void_p), None) == L.LB_EINVAL
+        assert lib.lb_objective_set(h, 7, r.ctypes.data_as(c_void_p), 0.0) == L.LB_EINVAL
+        assert lib.lb_objective_set(h, 0, r.ctypes.data_as(c_void_p), -1.0) == L.LB_EINVAL
+        assert lib.lb_solver_set(h, 9, 1e-15, 200, 100) == L.LB_EINVAL
+        assert lib.lb_solver_set(h, 0, 0.0, 200, 100) == L.LB_EINVAL
+        assert lib.lb_solver_set(h, 0, 1e-15, 0, 100) == L.LB_EINVAL
+        assert lib.lb_solver_set(h, 0, 1e-15, 200, -1) == L.LB_EINVAL
+        # compute before binding a workspace is refused on the host
+        G = c_double()
+        assert lib.lb_forward(h, None, byref(G), None) == L.LB_EINVAL
+        assert b"workspace" in lib.lb_last_error()
+    finally:
+        lib.lb_system_destroy(h)
+
+
+@pytest.mark.parametrize("K", [0, 1, 7, 100])
+def test_workspace_size_accounts_for_checkpoints(lib, K):
+    p = W.config2(n_steps=250)
+    h = _make(lib, p, K=K)
+    try:
+        V = np.asarray(p.gate.T, dtype=np.complex128)
+        Vb = np.ascontiguousarray(V).view(np.float64)
+        L.check(lib.lb_objective_set_gate(h, 0, Vb.ctypes.data_as(c_void_p), 0.0))
+        n = c_size_t()
+        L.check(lib.lb_workspace_bytes(h, byref(n)))
+        M, Vl, NT = 16, 81, 250
+        state = 16 * M * Vl
+        if K == 0:
+            tape = NT * state
+        else:
+            Kc = min(K, NT)
+            tape = -(-NT // Kc) * state + Kc * state
+        gproj = M * NT * 2 * 2 * 16
+        assert n.value >= tape + gproj + 3 * state
+        assert n.value <= tape + gproj + 3 * state + 64 * 1024
+    finally:
+        lib.lb_system_destroy(h)
+
+
+def test_large_system_rejected_at_bind(lib):
+    """N^2 > 4096 needs the grid-wide sweep; binding reports it on the host."""
+    p = W.config4(n_steps=4, levels=(3, 3, 3, 3), n_states=1)
+    h = _make(lib, p)
+    try:
+        t = colmajor(p.targets)
+        L.check(lib.lb_objective_set(h, 0, t.ctypes.data_as(c_void_p), 0.0))
+        n = c_size_t()
+        L.check(lib.lb_workspace_bytes(h, byref(n)))
+        assert lib.lb_bind_workspace(h, c_void_p(1 << 20), n, None) == L.LB_EINVAL
+    finally:
+        lib.lb_system_destroy(h)

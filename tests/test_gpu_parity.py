@@ -1,0 +1,247 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (stated by the method's accuracy targets): states and objectives
+1e-10 relative, gradients 1e-9 relative to the oracle's adjoint gradient and
+1e-6 to central differences; a single Lindbladian apply or IMR step agrees to
+a few units of FP64 rounding (1e-13 relative)."""
+
+import copy
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import imr, model
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_10310_gb300 import _lib as L
+
+    L.load(build_if_missing=True)
+
+
+def _sys(prob, **kw):
+    from paper_2110_10310_gb300.system import LindbladSystem
+
+    return LindbladSystem(prob, **kw)
+
+
+def _rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _rand_states(rng, n, N):
+    x = rng.standard_normal((n, N, N)) + 1j * rng.standard_normal((n, N, N))
+    return x
+
+
+SHAPES = [(2,), (3,), (2, 3), (4, 3), (2, 2, 2), (3, 2, 4), (4, 4, 4)]
+
+
+@pytest.mark.parametrize("levels", SHAPES)
+def test_apply_matches_dense_lindbladian(levels):
+    """y = M^{j+1/2} x and (M^{j+1/2})^+ x against the dense Kronecker M."""
+    p = W.random_problem(101, levels=levels, n_states=1, n_steps=10)
+    s = _sys(p)
+    m = model.Model(p.system, p.controls)
+    N = m.N
+    rng = np.random.default_rng(1)
+    X = _rand_states(rng, 3, N)
+    xt = torch.from_numpy(X).cuda()
+    for j in (0, 7):
+        Md = m.M(m.t_half(j))
+        for adj in (False, True):
+            A = Md.conj().T if adj else Md
+            y = s.apply(xt, j, adjoint=adj).cpu().numpy()
+            ref = np.stack([model.unvec(A @ model.vec(X[b]), N) for b in range(3)])
+            scale = np.max(np.abs(A).sum(axis=1)) * np.max(np.abs(X))
+            assert np.max(np.abs(y - ref)) <= 1e-14 * scale, (levels, j, adj)
+
+
+@pytest.mark.parametrize("levels", [(2, 3), (3, 2, 2), (4, 4)])
+def test_steps_match_oracle(levels):
+    """lb_propagate over a few forward and adjoint IMR steps from random states."""
+    p = W.random_problem(102, levels=levels, n_states=2, n_steps=12, T_ns=0.24, amp=0.1)
+    s = _sys(p)
+    mdl = model.Model(p.system, p.controls)
+    N = mdl.N
+    rng = np.random.default_rng(2)
+    X = _rand_states(rng, 2, N)
+    got = s.propagate(torch.from_numpy(X).cuda(), 3, 8).cpu().numpy()
+    Q = model.vec(X).T.copy()
+    for j in range(3, 8):
+        Q, _ = imr.imr_step(mdl, j, Q)
+    ref = np.stack([model.unvec(Q[:, i], N) for i in range(2)])
+    assert _rel(got, ref) < 1e-13
+    # adjoint steps j = 7..3: (I - h/2 M^+) zh = lam, lam <- lam + h M^+ zh
+    got = s.propagate(torch.from_numpy(X).cuda(), 3, 8, adjoint=True).cpu().numpy()
+    lam = model.vec(X).T.copy()
+    I = np.eye(N * N)
+    for j in range(7, 2, -1):
+        MH = mdl.M(mdl.t_half(j)).conj().T
+        zh = np.linalg.solve(I - 0.5 * mdl.h * MH, lam)
+        lam = lam + mdl.h * (MH @ zh)
+    ref = np.stack([model.unvec(lam[:, i], N) for i in range(2)])
+    assert _rel(got, ref) < 1e-13
+
+
+def _check_problem(p, state_tol=1e-10, grad_tol=1e-9, **kw):
+    s = _sys(p, **kw)
+    G, rhoT = s.forward(want_states=True)
+    Gg, g = s.gradient()
+    Go, go, fw = imr.gradient(p)
+    assert abs(G - Go) <= state_tol * abs(Go)
+    assert abs(Gg - Go) <= state_tol * abs(Go)
+    assert _rel(rhoT.cpu().numpy(), fw["rhoT"]) < state_tol
+    assert _rel(g, go) < grad_tol
+    return s, g
+
+
+def test_config1_full_horizon():
+    """1 qubit, 1000 steps, X-gate objective: states, G and gradient."""
+    _check_problem(W.config1())
+
+
+@pytest.mark.slow
+def test_config2_full_horizon():
+    """2 transmons x 3 levels, 10000 steps, CNOT on the essential subspace."""
+    s, _ = _check_problem(W.config2())
+    st = s.stats()
+    assert st["state_steps"] == 16 * 10000 * 3  # forward, recompute, adjoint
+
+
+@pytest.mark.parametrize("seed,objective,hermitian,gamma2,diss", [
+    (201, "frob", False, 0.0, True),
+    (202, "trace", True, 0.2, True),
+    (203, "frob", True, 0.0, False),
+    (204, "trace", False, 0.05, False),
+])
+def test_random_problems_match_oracle(seed, objective, hermitian, gamma2, diss):
+    p = W.random_problem(seed, levels=(2, 3), n_states=3, n_steps=40, T_ns=0.8, amp=0.1, objective=objective,
+                         hermitian=hermitian, gamma2=gamma2, dissipation=diss, ckpt_every=7)
+    _check_problem(p)
+
+
+def test_gradient_matches_central_differences_on_gpu():
+    """Central differences of the GPU objective against the GPU adjoint gradient."""
+    p = W.random_problem(205, levels=(3, 2), n_states=2, n_steps=30, T_ns=0.6, amp=0.1, n_splines=6)
+    s = _sys(p)
+    G, g = s.gradient()
+    a0 = p.controls.alpha.copy()
+    eps = 1e-6
+    scale = np.max(np.abs(g))
+    for k in range(0, len(a0), 5):
+        a = a0.copy()
+        a[k] += eps
+        s.set_alpha(a)
+        gp = s.forward()
+        a[k] -= 2 * eps
+        s.set_alpha(a)
+        gm = s.forward()
+        assert abs((gp - gm) / (2 * eps) - g[k]) <= 1e-6 * scale, k
+    s.set_alpha(a0)
+
+
+def test_checkpoint_interval_bitwise_identical():
+    """K = 0 (full tape), 1, 7 and 100 give bit-identical gradients."""
+    p = W.random_problem(206, levels=(2, 2), n_states=2, n_steps=45, T_ns=0.9, amp=0.1)
+    res = []
+    for K in (0, 1, 7, 100):
+        s = _sys(p, ckpt_every=K)
+        res.append(s.gradient())
+    for G, g in res[1:]:
+        assert G == res[0][0]
+        assert np.array_equal(g, res[0][1])
+
+
+def test_neumann_solver_agrees_with_jacobi():
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(207, levels=(3, 3), n_states=2, n_steps=60, T_ns=1.2, amp=0.05)
+    Gj, gj = _sys(p, solver=L.LB_SOLVER_JACOBI).gradient()
+    Gn, gn = _sys(p, solver=L.LB_SOLVER_NEUMANN).gradient()
+    assert abs(Gj - Gn) <= 1e-12 * abs(Gj)
+    assert _rel(gn, gj) < 1e-10
+
+
+def test_batch_matches_plain_and_oracle():
+    """Independent problems of uneven size in one launch (and as a CUDA graph)
+    against one launch sequence per problem, and against the oracle."""
+    from paper_2110_10310_gb300.system import LindbladBatch
+
+    probs = W.config3(n_problems=12, n_steps=60)
+    systems = [_sys(p) for p in probs]
+    plain = [s.gradient() for s in systems]
+    b = LindbladBatch(systems)
+    Gb, gb = b.gradient()
+    off = 0
+    for i, (G, g) in enumerate(plain):
+        assert abs(Gb[i] - G) <= 1e-12 * abs(G)
+        assert _rel(gb[off:off + len(g)], g) < 1e-10
+        off += len(g)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b.capture(1, stream=stream)
+        Gc, gc = b.gradient(stream=stream)
+    assert np.array_equal(Gc, Gb) and np.array_equal(gc, gb)
+    for i in (0, 5, 11):
+        Go, go, _ = imr.gradient(probs[i])
+        assert abs(Gb[i] - Go) <= 1e-10 * abs(Go)
+        off = sum(len(plain[k][1]) for k in range(i))
+        assert _rel(gb[off:off + len(go)], go) < 1e-9
+
+
+def test_autograd_function():
+    from paper_2110_10310_gb300.system import objective
+
+    p = W.random_problem(208, levels=(2, 2), n_states=2, n_steps=20, T_ns=0.4, amp=0.1)
+    s = _sys(p)
+    a = torch.tensor(p.controls.alpha, dtype=torch.float64, requires_grad=True)
+    G = objective(a, s)
+    (3.0 * G).backward()
+    G0, g0 = s.gradient()
+    assert abs(G.item() - G0) == 0.0
+    assert np.allclose(a.grad.numpy(), 3.0 * g0, rtol=0, atol=0)
+
+
+def test_errors_are_reported_and_recoverable():
+    """Non-convergence is a host-visible status, and the handle stays usable."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(209, levels=(2, 3), n_states=1, n_steps=10)
+    s = _sys(p, max_iter=1)
+    with pytest.raises(L.LBError) as e:
+        s.forward()
+    assert e.value.code == L.LB_ENOTCONV
+    assert "time step 0" in str(e.value)
+    # a step so large that the fixed point diverges
+    p2 = W.random_problem(210, levels=(3, 3), n_states=1, n_steps=1, T_ns=400.0, amp=3.0)
+    s2 = _sys(p2, max_iter=500)
+    with pytest.raises(L.LBError) as e2:
+        s2.forward()
+    assert e2.value.code in (L.LB_ENOTCONV, L.LB_ENAN)
+    # the same process and context continue to work
+    s3 = _sys(W.random_problem(211, levels=(2,), n_states=1, n_steps=5, T_ns=0.1, amp=0.1))
+    s3.forward()
+
+
+def test_host_buffers_roundtrip():
+    """States set from pinned host memory through the ABI give the same result."""
+    p = W.random_problem(212, levels=(2, 3), n_states=2, n_steps=15, T_ns=0.3, amp=0.1)
+    s = _sys(p)
+    G0 = s.forward()
+    from paper_2110_10310_gb300.system import colmajor
+
+    pinned = torch.from_numpy(colmajor(p.rho0)).pin_memory()
+    s.set_states_host(pinned, p.weights)
+    torch.cuda.synchronize()
+    assert s.forward() == G0

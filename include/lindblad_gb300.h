@@ -195,6 +195,33 @@ int lb_get_stats(lb_system* sys, lb_stats* out);
  * after the next synchronising call. */
 int lb_set_timing(lb_system* sys, int32_t on);
 
+/* ---- gradient without device allocation ----------------------------------- */
+
+/* Size of the device array behind lb_gradient_static: 64 MiB, held on every
+ * GPU that loads this library until the process exits. */
+#define LB_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+/* Same result as lb_gradient, for callers that cannot allocate device memory
+ * (code running inside a host callback, a framework that owns all device
+ * memory, a control loop that must not touch the allocator).  The paper has no
+ * counterpart: this is a deployment variant of lb_gradient.
+ *
+ * The handle carries the inputs (controls, states, objective, solver, set by
+ * the calls above) and must NOT have a workspace bound; G_out and grad_out
+ * are host outputs as in lb_gradient.  Every table, checkpoint, tape and
+ * partial result of the call lives in one file-scope device array of
+ * LB_STATIC_SCRATCH_BYTES; nothing is allocated on the device, by the library
+ * or by anything it calls.  A problem whose lb_workspace_bytes exceeds
+ * LB_STATIC_SCRATCH_BYTES is rejected with LB_ENOMEM.
+ *
+ * The first call on a device looks the array's device address up (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and the call clears it before use:
+ * calls that overlap on the GPU (other streams, other host threads, another
+ * handle) race with each other and must be serialised by the caller.  The
+ * call synchronises `stream` before it returns and leaves the handle unbound. */
+int lb_gradient_static(lb_system* sys, void* stream, double* G_out, double* grad_out);
+
 /* ---- batches of independent problems ------------------------------------- */
 
 /* A batch of n >= 1 independent systems, each already bound to its own

@@ -31,6 +31,7 @@ LB_SOLVER_NEUMANN = 2
 
 LB_MAX_SUBSYSTEMS = 8
 LB_MAX_LEVELS = 16
+LB_STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 ERROR_NAMES = {1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENOTCONV", 5: "LB_ENAN"}
 
@@ -84,6 +85,7 @@ SIGNATURES = {
     "lb_forward": (c_int32, [c_void_p, c_void_p, POINTER(c_double), c_void_p]),
     "lb_gradient": (c_int32, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_double)]),
     "lb_gradient_async": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lb_gradient_static": (c_int32, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_double)]),
     "lb_propagate": (c_int32, [c_void_p, c_void_p, c_int32, c_int64, c_int64, c_void_p, c_int32]),
     "lb_apply": (c_int32, [c_void_p, c_void_p, c_int32, c_int64, c_void_p, c_void_p, c_int32]),
     "lb_get_stats": (c_int32, [c_void_p, POINTER(lb_stats)]),

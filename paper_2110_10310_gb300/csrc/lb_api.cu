@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -985,3 +986,123 @@ int lb_batch_get_stats(lb_batch* b, lb_stats* out) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Gradient with the device scratch in a static array (no device allocation)
+//
+// For callers that cannot allocate device memory at all: code that runs where
+// cudaMalloc is not allowed or not wanted (inside a host callback, inside a
+// framework that owns every byte of device memory, or in a control loop that
+// must not touch the allocator).  Everything the call needs on the device
+// lives in g_lb_static_scratch, a file-scope array that every GPU loading this
+// library holds until the process exits.
+
+static __device__ __align__(256) unsigned char g_lb_static_scratch[LB_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxStaticDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxStaticDevices] = {};  // device address of the array, per device
+
+// Device address of g_lb_static_scratch on the current device.  In host code
+// the array's name only denotes a host-side stand-in, so the address is looked
+// up once per device (with that device current) and cached.
+int static_scratch_address(void** out) {
+  int dev = 0;
+  LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxStaticDevices) return fail(LB_EINVAL, "device ordinal too large for the static scratch");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    LB_CUDA(cudaGetSymbolAddress(&p, g_lb_static_scratch), "cudaGetSymbolAddress(static scratch)");
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return LB_OK;
+}
+
+// Upload the handle's host-side inputs into the static scratch, like
+// lb_bind_workspace, but keep the host copies: the array is shared by every
+// call, so each call uploads everything again.
+int static_bind(lb_system* s, void* ws, cudaStream_t st) {
+  s->L = make_layout(s);
+  s->ws = static_cast<char*>(ws);
+  s->ws_bytes = LB_STATIC_SCRATCH_BYTES;
+  s->bind_stream = st;
+  fill_prob(s);
+  s->dp = at<ProbDev>(s, s->L.prob);
+  s->d_items = at<WorkItem>(s, s->L.items);
+  std::vector<WorkItem> items(s->M);
+  for (int i = 0; i < s->M; ++i) items[i] = WorkItem{0, i};
+  std::vector<double> sysp(4 * s->Q + s->Q * s->Q, 0.0);
+  for (int q = 0; q < s->Q; ++q) {
+    sysp[q] = s->det[q];
+    sysp[s->Q + q] = s->kerr[q];
+    sysp[2 * s->Q + s->Q * s->Q + q] = s->g1[q];
+    sysp[3 * s->Q + s->Q * s->Q + q] = s->g2[q];
+  }
+  for (int i = 0; i < s->Q * s->Q; ++i) sysp[2 * s->Q + i] = s->xkerr[i];
+  // the array keeps the previous call's contents: clear all of it
+  LB_CUDA(cudaMemsetAsync(s->ws, 0, s->L.total, st), "clear static scratch");
+  LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
+  LB_CUDA(cudaMemcpyAsync(s->d_items, items.data(), sizeof(WorkItem) * s->M, cudaMemcpyHostToDevice, st),
+          "upload work items");
+  LB_CUDA(cudaMemcpyAsync(at<double>(s, s->L.sysp), sysp.data(), sizeof(double) * sysp.size(), cudaMemcpyHostToDevice,
+                          st),
+          "upload system");
+  if (!s->carriers.empty())
+    LB_CUDA(cudaMemcpyAsync(at<double>(s, s->L.carriers), s->carriers.data(), sizeof(double) * s->carriers.size(),
+                            cudaMemcpyHostToDevice, st),
+            "upload carriers");
+  LB_CUDA(lbk::launch_tables(s->dp, s->hp, st), "tables kernel");
+  int rc = upload_states(s, s->rho0.data(), st);
+  if (rc) return rc;
+  rc = upload_targets(s, st);
+  if (rc) return rc;
+  rc = upload_controls(s, st);
+  if (rc) return rc;
+  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N);
+  return LB_OK;
+}
+
+// Leave the handle unbound again, whatever happened.
+struct StaticUnbind {
+  lb_system* s;
+  ~StaticUnbind() {
+    s->ws = nullptr;
+    s->ws_bytes = 0;
+    s->dp = nullptr;
+    s->d_items = nullptr;
+    s->bind_stream = nullptr;
+    s->ctab_dirty = true;
+  }
+};
+
+}  // namespace
+
+extern "C" int lb_gradient_static(lb_system* s, void* stream, double* G_out, double* grad_out) {
+  int rc = check_ready(s, false);
+  if (rc) return rc;
+  if (s->ws) return fail(LB_EINVAL, "lb_gradient_static needs a handle without a bound workspace");
+  if (!resident_ok(s)) return fail(LB_EINVAL, "N^2 > 4096 needs the grid-wide sweep, not available in this build");
+  if (s->target_mode == 0) return fail(LB_EINVAL, "no objective (lb_objective_set or lb_objective_set_gate)");
+  if (s->rho0.empty()) return fail(LB_EINVAL, "no initial states");
+  const size_t need = make_layout(s).total;
+  if (need > (size_t)LB_STATIC_SCRATCH_BYTES) {
+    char buf[200];
+    std::snprintf(buf, sizeof buf, "problem needs %zu bytes of device scratch; the static scratch holds %zu",
+                  need, (size_t)LB_STATIC_SCRATCH_BYTES);
+    return fail(LB_ENOMEM, buf);
+  }
+  void* ws = nullptr;
+  rc = static_scratch_address(&ws);
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  StaticUnbind guard{s};
+  rc = static_bind(s, ws, st);
+  if (rc) return rc;
+  rc = gradient_device(s, st);
+  if (rc) return rc;
+  return finish(s, st, G_out, grad_out);
+}

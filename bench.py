@@ -32,6 +32,18 @@ UNIT = "state-steps/s"
 WORKLOAD = ("cnot_2x3: 2 transmons x 3 levels (N=9, vec 81), 16 essential-basis states |i><j|, "
             "10000 IMR steps, T=200 ns, 2x20 splines x 2 carriers, J_Frob to CNOT, "
             "forward + adjoint gradient with checkpoints every 100 steps")
+# other workloads (--workload), measured the same way; the default line is cnot_2x3
+WORKLOADS = {
+    "cnot_2x3": WORKLOAD,
+    "qubit_x": "qubit_x: 1 qubit (vec 4), 4 states |i><j|, 1000 steps, T=100 ns, X gate, fwd + adjoint",
+    "batch256": ("batch256: 256 independent problems, Q in {1,2,3}, 2-4 levels (vec 4..4096), 3 random pure states "
+                 "each, 5000 steps, T=100 ns, fwd + adjoint, one persistent launch per sweep captured in a CUDA graph"),
+    "qudits_4x4": ("qudits_4x4: 4 qudits x 4 levels (vec 65536), 3 random pure states, dt=0.0125 ns, "
+                   "first {n} of 40000 steps, fwd + adjoint with checkpoints every 100 steps, grid-wide sweep"),
+    "qutrits_6x3": ("qutrits_6x3: 6 qutrits (vec 531441), 64 random pure states, dt=0.015 ns, "
+                    "first {n} of 20000 steps, fwd + adjoint with checkpoints every 10 steps, grid-wide sweep"),
+}
+PREFIX = {"qudits_4x4": 2000, "qutrits_6x3": 40}
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_PER_SM = 4.0  # 2 FP64 FMA lanes per SM per clock, 2 flops each
@@ -39,10 +51,20 @@ CPU_SAMPLE_STEPS = 8000  # oracle sample for the CPU baseline (same dt, 16 state
 REF_SAMPLE_STEPS = 400  # oracle sample per reference-arm step
 
 
-def problem(n_steps=None):
+def problem(n_steps=None, workload="cnot_2x3"):
     import workloads as W
 
-    p = W.config2()
+    if workload == "qubit_x":
+        p = W.config1()
+    elif workload == "qudits_4x4":
+        p = W.config4()
+        n_steps = n_steps or PREFIX[workload]
+    elif workload == "qutrits_6x3":
+        p = W.config5()
+        p.ckpt_every = 10
+        n_steps = n_steps or PREFIX[workload]
+    else:
+        p = W.config2()
     if n_steps is not None:
         # a prefix of the horizon at the same step size dt = 0.02 ns
         p.system.T_ns = p.system.T_ns * n_steps / p.system.n_steps
@@ -213,6 +235,91 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, rank, world, dev):
+    """Workload batch256: one persistent launch per sweep over 256 uneven
+    problems (captured in a CUDA graph), beside the plain form with one
+    lb_gradient (its own launches) per problem on one stream."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2110_10310_gb300 import _lib
+    from paper_2110_10310_gb300.system import LindbladBatch, LindbladSystem
+
+    probs = W.config3()
+    systems = [LindbladSystem(p, sweep=_lib.LB_SWEEP_RESIDENT, device=dev) for p in probs]
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        batch = LindbladBatch(systems, stream=stream)
+        for _ in range(args.warmup):
+            batch.gradient(stream=stream)
+        batch.capture(1, stream=stream)
+        batch.gradient(stream=stream)
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    state_steps = sum(p.M * p.system.n_steps for p in probs)
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    ms = []
+    with ClockSampler(gpu_id) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            with torch.cuda.stream(stream):
+                batch.gradient(stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    st = batch.stats()
+    total_ms = sum(ms)
+    value = world * state_steps * args.steps / (total_ms * 1e-3)
+    # plain: every problem on its own launch sequence (best single-problem sweep), one stream
+    plain_sys = [LindbladSystem(p, device=dev) for p in probs]
+    for s_ in plain_sys[:4]:
+        s_.gradient()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s_ in plain_sys:
+        s_.gradient()
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    plain_value = state_steps / plain_s
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": {
+                "workload": WORKLOADS["batch256"],
+                "problems": len(probs),
+                "state_steps_per_step": state_steps,
+                "l2": "flushed between timed steps (256 MiB write)",
+                "plain_value": plain_value,
+                "plain_form": "one lb_gradient per problem, its own launches, one stream, sweep chosen per problem",
+                "batched_over_plain": value / plain_value,
+                "inner_iters_per_step": st["inner_iterations"] / max(1, st["state_steps"]),
+            },
+            "gpu_launches": st["kernel_launches"] * args.steps,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -220,6 +327,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="cnot_2x3", choices=sorted(WORKLOADS))
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
 
@@ -254,7 +362,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     _lib.load(build_if_missing=True)
     dev = torch.device("cuda", local_rank)
-    p = problem()
+    if args.workload == "batch256":
+        return run_batch(args, rank, world, dev)
+    p = problem(workload=args.workload)
     s = LindbladSystem(p, device=dev)
     s.set_timing(True)
     stream = torch.cuda.current_stream()
@@ -336,11 +446,13 @@ def main():
     bwd_ms = statistics.median(ms_bwd)
     peak = FP64_FLOP_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
     achieved = bwd_flops / (bwd_ms * 1e-3) / 1e12
-    traffic = traffic_record("k_backward_res")
+    grid = s.N * s.N > 4096
+    kernel_name = "k_backward_grid" if grid else "k_backward_res"
+    traffic = traffic_record(kernel_name)
     clocks = clk.summary()
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cnot_2x3":
         r = oracle_subprocess(CPU_SAMPLE_STEPS)
         cpu = {"value": r["state_steps"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"dense-LU oracle gradient (forward + adjoint), 16 states x {CPU_SAMPLE_STEPS} of the "
@@ -361,7 +473,7 @@ def main():
             "dtype": "f64",
             "data": "synthetic",
             "config": {
-                "workload": WORKLOAD,
+                "workload": WORKLOADS[args.workload].format(n=p.system.n_steps),
                 "states": p.M,
                 "n_steps": p.system.n_steps,
                 "ckpt_every": p.ckpt_every,
@@ -374,7 +486,7 @@ def main():
                 "fwd_fp64_tflops": fwd_flops / (statistics.median(ms_fwd) * 1e-3) / 1e12,
             },
             "roofline": {
-                "kernel": "k_backward_res",
+                "kernel": kernel_name,
                 "bound": "alu",
                 "achieved": achieved,
                 "peak": peak,

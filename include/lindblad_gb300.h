@@ -69,6 +69,18 @@ extern "C" {
 #define LB_SOLVER_JACOBI 1
 #define LB_SOLVER_NEUMANN 2
 
+/* how the time loop is spread over the GPU:
+ *   LB_SWEEP_RESIDENT: one CTA per state, the state in shared memory, the
+ *                      whole time loop in one launch (N^2 <= 4096);
+ *   LB_SWEEP_GRID:     one cooperative launch over all SMs and all states,
+ *                      iterates in global memory, a grid barrier per inner
+ *                      iteration (any N^2);
+ *   LB_SWEEP_AUTO:     GRID when N^2 > 4096 or when N^2 >= 1024 with fewer than
+ *                      64 states (most SMs would idle), RESIDENT otherwise. */
+#define LB_SWEEP_AUTO 0
+#define LB_SWEEP_RESIDENT 1
+#define LB_SWEEP_GRID 2
+
 #define LB_MAX_SUBSYSTEMS 8 /* Q <= 8 */
 #define LB_MAX_LEVELS 16    /* n_q <= 16 */
 
@@ -146,6 +158,9 @@ int lb_objective_set_gate(lb_system* sys, int32_t kind, const double* V, double 
  * Defaults: LB_SOLVER_AUTO, 1e-15, 200, 100.  Call before lb_workspace_bytes. */
 int lb_solver_set(lb_system* sys, int32_t method, double rtol, int32_t max_iter, int32_t ckpt_every);
 
+/* Choose the sweep kind (LB_SWEEP_*); call before lb_workspace_bytes. */
+int lb_set_sweep(lb_system* sys, int32_t sweep);
+
 /* ---- device workspace ---------------------------------------------------- */
 
 /* Bytes of device memory the system needs (depends on N, M, N_T, Q, the
@@ -178,7 +193,8 @@ int lb_gradient_async(lb_system* sys, void* stream, void* G_dev, void* grad_dev)
 /* Advance n_vec device vectors x (n_vec x N x N complex, column-major) from
  * step j0 to step j1 (0 <= j0 <= j1 <= N_T) with the implicit midpoint rule
  * (adjoint = 0), or apply the adjoint steps j1-1 down to j0 to them
- * (adjoint = 1: (I - dt/2 M^+) zhat = x, x <- 2 zhat - x).  In place. */
+ * (adjoint = 1: (I - dt/2 M^+) zhat = x, x <- 2 zhat - x).  In place.
+ * With grid sweeps n_vec <= M (the iteration buffers hold M states). */
 int lb_propagate(lb_system* sys, void* stream, int32_t adjoint, int64_t j0, int64_t j1, void* x_dev, int32_t n_vec);
 
 /* y = M^{j+1/2} x (adjoint = 0) or y = (M^{j+1/2})^+ x (adjoint = 1) for

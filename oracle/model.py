@@ -205,8 +205,15 @@ class Model:
         self.N = int(np.prod(self.levels))
         self.H_sys = system_hamiltonian(sysm)
         self.Ls = collapse_operators(sysm)
-        self.D = dissipator_part(self.Ls, self.N)
+        self._D = None
         self.h = sysm.T_ns / sysm.n_steps
+
+    @property
+    def D(self) -> np.ndarray:
+        """Dense dissipator part of M, built on first use (N^2 x N^2)."""
+        if self._D is None:
+            self._D = dissipator_part(self.Ls, self.N)
+        return self._D
 
     def t_half(self, j: int) -> float:
         """t_j + dt/2, where M^{j+1/2} is evaluated (Appendix A)."""

@@ -25,6 +25,10 @@ LB_ENAN = 5
 LB_J_FROB = 0
 LB_J_TR = 1
 
+LB_SWEEP_AUTO = 0
+LB_SWEEP_RESIDENT = 1
+LB_SWEEP_GRID = 2
+
 LB_SOLVER_AUTO = 0
 LB_SOLVER_JACOBI = 1
 LB_SOLVER_NEUMANN = 2
@@ -80,6 +84,7 @@ SIGNATURES = {
     "lb_objective_set": (c_int32, [c_void_p, c_int32, c_void_p, c_double]),
     "lb_objective_set_gate": (c_int32, [c_void_p, c_int32, c_void_p, c_double]),
     "lb_solver_set": (c_int32, [c_void_p, c_int32, c_double, c_int32, c_int32]),
+    "lb_set_sweep": (c_int32, [c_void_p, c_int32]),
     "lb_workspace_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),
     "lb_bind_workspace": (c_int32, [c_void_p, c_void_p, c_size_t, c_void_p]),
     "lb_forward": (c_int32, [c_void_p, c_void_p, POINTER(c_double), c_void_p]),

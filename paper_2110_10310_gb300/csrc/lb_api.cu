@@ -46,7 +46,7 @@ struct Region {
 
 struct Layout {
   Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
-      gproj, J, G, grad, gateV, emap, efull;
+      gproj, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar;
   size_t total = 0;
 };
 
@@ -83,6 +83,9 @@ struct lb_system {
   double rtol = 1e-15;
   int max_iter = 200;
   int K = 100;
+  int sweep = LB_SWEEP_AUTO;
+  int gblocks = 0;   // cooperative grid size (grid sweeps)
+  size_t gsmem = 0;  // its dynamic shared memory
   // device binding
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -124,6 +127,15 @@ struct lb_batch {
 namespace {
 
 bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+// Grid-wide sweeps for states that do not fit one CTA's shared memory, or
+// when asked for; AUTO also prefers them when few states leave most SMs idle.
+bool use_grid(const lb_system* s) {
+  if (s->V > lbk::kMaxResidentV) return true;
+  if (s->sweep == LB_SWEEP_GRID) return true;
+  if (s->sweep == LB_SWEEP_RESIDENT) return false;
+  return s->V >= 1024 && s->M < 64;
+}
 
 int n_coef(const lb_system* s) {
   int n = 0;
@@ -172,7 +184,8 @@ Layout make_layout(const lb_system* s) {
   const size_t nck = s->K > 0 ? (NT + s->K - 1) / s->K : NT;
   take(L.ckpt, c2 * M * nck * V);
   take(L.seg, s->K > 0 ? c2 * M * (size_t)s->K * V : 0);
-  take(L.gproj, c2 * M * NT * s->Q * 2);
+  const bool grid = use_grid(s);
+  take(L.gproj, c2 * (grid ? 1 : M) * NT * s->Q * 2);
   take(L.J, sizeof(double) * M);
   take(L.G, sizeof(double));
   take(L.grad, sizeof(double) * s->n_params);
@@ -180,6 +193,13 @@ Layout make_layout(const lb_system* s) {
   take(L.gateV, s->target_mode == 2 ? c2 * Ne * Ne : 0);
   take(L.emap, s->target_mode == 2 ? sizeof(int32_t) * s->N : 0);
   take(L.efull, s->target_mode == 2 ? sizeof(int32_t) * Ne : 0);
+  take(L.zA, grid ? c2 * M * V : 0);
+  take(L.zB, grid ? c2 * M * V : 0);
+  take(L.lam, grid ? c2 * M * V : 0);
+  take(L.qf, grid ? c2 * M * V : 0);
+  take(L.partials, grid ? sizeof(double) * lbk::kMaxGridBlocks * LB_MAXQ * 4 : 0);
+  take(L.gslots, grid ? sizeof(unsigned long long) * 5 * M : 0);
+  take(L.bar, grid ? sizeof(GridBar) : 0);
   L.total = off;
   return L;
 }
@@ -320,6 +340,18 @@ void fill_prob(lb_system* s) {
   P.G = at<double>(s, s->L.G);
   P.grad = at<double>(s, s->L.grad);
   P.status = at<DevStatus>(s, s->L.status);
+  const bool grid = use_grid(s);
+  P.gM = grid ? 1 : s->M;
+  P.grid_blocks = grid ? s->gblocks : 0;
+  if (grid) {
+    P.zA = at<double2>(s, s->L.zA);
+    P.zB = at<double2>(s, s->L.zB);
+    P.lam = at<double2>(s, s->L.lam);
+    P.qf = at<double2>(s, s->L.qf);
+    P.partials = at<double>(s, s->L.partials);
+    P.gslots = at<unsigned long long>(s, s->L.gslots);
+    P.bar = at<GridBar>(s, s->L.bar);
+  }
 }
 
 int ensure_ctab(lb_system* s, cudaStream_t st) {
@@ -352,10 +384,14 @@ int read_status(const DevStatus& d, lb_stats* st, int launches) {
     std::snprintf(buf, sizeof buf, "state became NaN or Inf at time step %d", d.step);
     return fail(LB_ENAN, buf);
   }
+  if (d.code == LB_ECUDA) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "a grid barrier wait gave up at time step %d", d.step);
+    return fail(LB_ECUDA, buf);
+  }
   return LB_OK;
 }
 
-bool resident_ok(const lb_system* s) { return s->V <= lbk::kMaxResidentV; }
 
 }  // namespace
 
@@ -545,6 +581,17 @@ int lb_solver_set(lb_system* s, int32_t method, double rtol, int32_t max_iter, i
   return LB_OK;
 }
 
+int lb_set_sweep(lb_system* s, int32_t sweep) {
+  if (!s) return fail(LB_EINVAL, "null system handle");
+  if (s->ws) return fail(LB_EINVAL, "choose the sweep before binding a workspace");
+  if (sweep != LB_SWEEP_AUTO && sweep != LB_SWEEP_RESIDENT && sweep != LB_SWEEP_GRID)
+    return fail(LB_EINVAL, "unknown sweep kind");
+  if (sweep == LB_SWEEP_RESIDENT && s->V > lbk::kMaxResidentV)
+    return fail(LB_EINVAL, "one CTA per state needs N^2 <= 4096");
+  s->sweep = sweep;
+  return LB_OK;
+}
+
 int lb_workspace_bytes(const lb_system* s, size_t* bytes) {
   int rc = check_ready(s, false);
   if (rc) return rc;
@@ -558,7 +605,6 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
   if (rc) return rc;
   if (!ws) return fail(LB_EINVAL, "null workspace");
   if (reinterpret_cast<uintptr_t>(ws) % kAlign) return fail(LB_EINVAL, "workspace must be 256-byte aligned");
-  if (!resident_ok(s)) return fail(LB_EINVAL, "N^2 > 4096 needs the grid-wide sweep, not available in this build");
   if (s->target_mode == 0) return fail(LB_EINVAL, "no objective (lb_objective_set or lb_objective_set_gate)");
   if (s->target_mode == 2) {
     for (int q = 0; q < s->Q; ++q)
@@ -568,6 +614,15 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
   if (bytes < s->L.total) return fail(LB_ENOMEM, "workspace smaller than lb_workspace_bytes");
   if (s->rho0.empty()) return fail(LB_EINVAL, "initial states are required before binding");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (use_grid(s)) {
+    int dev = 0, coop = 0;
+    LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    LB_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev), "cudaDeviceGetAttribute");
+    if (!coop) return fail(LB_ECUDA, "the device does not support cooperative launches (grid sweeps)");
+    s->gsmem = lbk::grid_smem_bytes(n_coef(s), n_jcoef(s));
+    s->gblocks = lbk::grid_blocks_max(s->gsmem);
+    if (s->gblocks <= 0) return fail(LB_ECUDA, "cannot size the cooperative grid of the sweep kernels");
+  }
   if (!s->upload_done) LB_CUDA(cudaEventCreateWithFlags(&s->upload_done, cudaEventDisableTiming), "cudaEventCreate");
   s->ws = static_cast<char*>(ws);
   s->ws_bytes = bytes;
@@ -618,6 +673,20 @@ static int run_forward(lb_system* s, cudaStream_t st, int tape) {
   if (rc) return rc;
   LB_CUDA(cudaMemsetAsync(at<DevStatus>(s, s->L.status), 0, sizeof(DevStatus), st), "clear status");
   s->timed_fwd = s->timed_bwd = false;
+  if (use_grid(s)) {
+    LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.gslots), 0, s->L.gslots.bytes, st), "clear grid slots");
+    LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.bar), 0, s->L.bar.bytes, st), "clear grid barrier");
+    if (s->timing) LB_CUDA(cudaEventRecord(s->ev[0], st), "cudaEventRecord");
+    LB_CUDA(lbk::launch_sweep_grid(s->dp, 0, 1, tape, 0, s->NT, nullptr, s->M, s->gblocks, s->gsmem, st),
+            "forward grid sweep");
+    if (s->timing) {
+      LB_CUDA(cudaEventRecord(s->ev[1], st), "cudaEventRecord");
+      s->timed_fwd = true;
+    }
+    LB_CUDA(lbk::launch_objective_states(s->dp, s->M, st), "objective kernel");
+    s->launches += 2;
+    return LB_OK;
+  }
   if (s->timing) LB_CUDA(cudaEventRecord(s->ev[0], st), "cudaEventRecord");
   LB_CUDA(lbk::launch_forward_resident(s->dp, s->d_items, s->M, tape, s->rc, st), "forward kernel");
   if (s->timing) {
@@ -675,8 +744,15 @@ static int param_warps(const lb_system* s) {
 static int gradient_device(lb_system* s, cudaStream_t st) {
   int rc = run_forward(s, st, 1);
   if (rc) return rc;
+  if (use_grid(s)) {
+    LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.gslots), 0, s->L.gslots.bytes, st), "clear grid slots");
+    LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.bar), 0, s->L.bar.bytes, st), "clear grid barrier");
+  }
   if (s->timing) LB_CUDA(cudaEventRecord(s->ev[2], st), "cudaEventRecord");
-  LB_CUDA(lbk::launch_backward_resident(s->dp, s->d_items, s->M, s->rc, st), "backward kernel");
+  if (use_grid(s))
+    LB_CUDA(lbk::launch_backward_grid(s->dp, s->gblocks, s->gsmem, st), "backward grid sweep");
+  else
+    LB_CUDA(lbk::launch_backward_resident(s->dp, s->d_items, s->M, s->rc, st), "backward kernel");
   if (s->timing) {
     LB_CUDA(cudaEventRecord(s->ev[3], st), "cudaEventRecord");
     s->timed_bwd = true;
@@ -724,8 +800,17 @@ int lb_propagate(lb_system* s, void* stream, int32_t adjoint, int64_t j0, int64_
   LB_CUDA(cudaMemsetAsync(at<DevStatus>(s, s->L.status), 0, sizeof(DevStatus), st), "clear status");
   s->timed_fwd = s->timed_bwd = false;
   if (j1 > j0) {
-    LB_CUDA(lbk::launch_propagate_resident(s->dp, adjoint, j0, j1, static_cast<double2*>(x_dev), n_vec, s->rc, st),
-            "propagate kernel");
+    if (use_grid(s)) {
+      if (n_vec > s->M) return fail(LB_EINVAL, "grid sweeps propagate at most M vectors at a time");
+      LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.gslots), 0, s->L.gslots.bytes, st), "clear grid slots");
+      LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.bar), 0, s->L.bar.bytes, st), "clear grid barrier");
+      LB_CUDA(lbk::launch_sweep_grid(s->dp, adjoint ? 2 : 1, 0, 0, j0, j1, static_cast<double2*>(x_dev), n_vec,
+                                     s->gblocks, s->gsmem, st),
+              "propagate grid sweep");
+    } else {
+      LB_CUDA(lbk::launch_propagate_resident(s->dp, adjoint, j0, j1, static_cast<double2*>(x_dev), n_vec, s->rc, st),
+              "propagate kernel");
+    }
     s->launches += 1;
   }
   return finish(s, st, nullptr, nullptr);
@@ -767,6 +852,10 @@ int lb_batch_create(lb_system* const* systems, int32_t n, lb_batch** out) {
     if (!s || !s->ws) {
       delete b;
       return fail(LB_EINVAL, "every system of a batch must have a bound workspace");
+    }
+    if (use_grid(s)) {
+      delete b;
+      return fail(LB_EINVAL, "batched systems must use one CTA per state (N^2 <= 4096, LB_SWEEP_RESIDENT)");
     }
     b->sys.push_back(s);
     b->grad_off.push_back(b->n_grad);
@@ -1085,7 +1174,7 @@ extern "C" int lb_gradient_static(lb_system* s, void* stream, double* G_out, dou
   int rc = check_ready(s, false);
   if (rc) return rc;
   if (s->ws) return fail(LB_EINVAL, "lb_gradient_static needs a handle without a bound workspace");
-  if (!resident_ok(s)) return fail(LB_EINVAL, "N^2 > 4096 needs the grid-wide sweep, not available in this build");
+  if (use_grid(s)) return fail(LB_EINVAL, "lb_gradient_static supports one CTA per state only (N^2 <= 4096)");
   if (s->target_mode == 0) return fail(LB_EINVAL, "no objective (lb_objective_set or lb_objective_set_gate)");
   if (s->rho0.empty()) return fail(LB_EINVAL, "no initial states");
   const size_t need = make_layout(s).total;

@@ -21,6 +21,14 @@ struct DevStatus {
   unsigned long long steps[3];  // state-steps per phase
 };
 
+// Grid-wide barrier state of a cooperative launch (zeroed before each launch).
+struct GridBar {
+  unsigned int count;  // blocks arrived in the current generation
+  unsigned int gen;    // generation counter
+  int err;             // set when a wait gave up
+  int pad;
+};
+
 // Everything a kernel needs to know about one system, in device memory.
 // Arrays are device pointers into the system's workspace.
 struct ProbDev {
@@ -66,6 +74,16 @@ struct ProbDev {
   double* G;                 // [1]
   double* grad;              // [n_params]
   DevStatus* status;
+  // grid-wide sweeps (N^2 > 4096): buffers of the iteration, [M*V] each
+  int32_t gM;                // state slots of gproj: M (one CTA per state) or 1 (grid sweeps sum over states)
+  int32_t grid_blocks;       // blocks of the cooperative launch
+  double2* zA;
+  double2* zB;
+  double2* lam;              // adjoint state
+  double2* qf;               // recomputed forward state
+  double* partials;          // [grid_blocks][LB_MAXQ][4] gradient pieces per block
+  unsigned long long* gslots;  // [3][M] per-state |z_new - z| maxima, then [2][M] per-state |q| maxima
+  GridBar* bar;
 };
 
 // one work item of a resident launch: (problem, state)
@@ -103,5 +121,18 @@ cudaError_t launch_apply(const ProbDev* d_prob, const ProbDev& h_prob, int adjoi
                          double2* y, int n_vec, cudaStream_t s);
 cudaError_t launch_propagate_resident(const ProbDev* d_prob, int adjoint, int64_t j0, int64_t j1, double2* x,
                                       int n_vec, const ResidentConfig& rc, cudaStream_t s);
+
+// grid-wide cooperative sweeps for states too large for one CTA
+constexpr int kGridThreads = 256;
+constexpr int kMaxGridBlocks = 4096;
+// largest cooperative grid of the sweep kernels on the current device
+int grid_blocks_max(size_t smem);
+size_t grid_smem_bytes(int ncoef, int njcoef);
+// mode 0: forward over [j0, j1) on P.qT (initialised from P.q0 when init_from_q0), checkpoints when tape;
+// mode 1: forward over [j0, j1) in place on x; mode 2: adjoint steps j1-1..j0 in place on x
+cudaError_t launch_sweep_grid(const ProbDev* d_prob, int mode, int init_from_q0, int tape, int64_t j0, int64_t j1,
+                              double2* x, int nstates, int nblocks, size_t smem, cudaStream_t s);
+cudaError_t launch_backward_grid(const ProbDev* d_prob, int nblocks, size_t smem, cudaStream_t s);
+cudaError_t launch_objective_states(const ProbDev* d_prob, int M, cudaStream_t s);
 
 }  // namespace lbk

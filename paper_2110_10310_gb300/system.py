@@ -55,7 +55,7 @@ class LindbladSystem:
     ckpt_every)."""
 
     def __init__(self, problem, *, solver: int = L.LB_SOLVER_AUTO, rtol: float = 1e-15, max_iter: int = 200,
-                 ckpt_every: int | None = None, device=None, stream=None):
+                 ckpt_every: int | None = None, sweep: int = L.LB_SWEEP_AUTO, device=None, stream=None):
         self.lib = L.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         sysm = problem.system
@@ -104,6 +104,7 @@ class LindbladSystem:
             L.check(self.lib.lb_objective_set_gate(h, kind, V.ctypes.data_as(c_void_p), g2))
         K = int(getattr(problem, "ckpt_every", 100)) if ckpt_every is None else int(ckpt_every)
         L.check(self.lib.lb_solver_set(h, int(solver), float(rtol), int(max_iter), K))
+        L.check(self.lib.lb_set_sweep(h, int(sweep)))
         nbytes = c_size_t()
         L.check(self.lib.lb_workspace_bytes(h, byref(nbytes)))
         self.workspace_bytes = int(nbytes.value)
@@ -191,7 +192,10 @@ class LindbladSystem:
 
 
 class LindbladBatch:
-    """Independent systems advanced together, one persistent launch per sweep."""
+    """Independent systems advanced together, one persistent launch per sweep.
+
+    Every member must use one CTA per state (create it with
+    ``sweep=LB_SWEEP_RESIDENT``; N^2 <= 4096)."""
 
     def __init__(self, systems, stream=None):
         self.lib = L.load()

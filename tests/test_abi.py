@@ -156,15 +156,23 @@ def test_workspace_size_accounts_for_checkpoints(lib, K):
         lib.lb_system_destroy(h)
 
 
-def test_large_system_rejected_at_bind(lib):
-    """N^2 > 4096 needs the grid-wide sweep; binding reports it on the host."""
-    p = W.config4(n_steps=4, levels=(3, 3, 3, 3), n_states=1)
-    h = _make(lib, p)
+def test_grid_sweep_workspace_and_sweep_choice(lib):
+    """N^2 > 4096 selects the grid-wide sweep; its workspace adds the four
+    iteration buffers, and one CTA per state cannot be forced."""
+    p = W.config4(n_steps=40, levels=(3, 3, 3, 3), n_states=2)
+    h = _make(lib, p, K=10)
     try:
         t = colmajor(p.targets)
         L.check(lib.lb_objective_set(h, 0, t.ctypes.data_as(c_void_p), 0.0))
+        assert lib.lb_set_sweep(h, L.LB_SWEEP_RESIDENT) == L.LB_EINVAL
+        assert lib.lb_set_sweep(h, 7) == L.LB_EINVAL
+        L.check(lib.lb_set_sweep(h, L.LB_SWEEP_GRID))
         n = c_size_t()
         L.check(lib.lb_workspace_bytes(h, byref(n)))
-        assert lib.lb_bind_workspace(h, c_void_p(1 << 20), n, None) == L.LB_EINVAL
+        V, M = 81 * 81, 2
+        state = 16 * M * V
+        # q0, tar, qT, 4 checkpoints, 10-step segment tape, zA, zB, lam, qf
+        assert n.value >= (3 + 4 + 10 + 4) * state
+        assert n.value <= (3 + 4 + 10 + 4) * state + 2 * 1024 * 1024
     finally:
         lib.lb_system_destroy(h)

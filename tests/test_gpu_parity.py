@@ -176,10 +176,11 @@ def test_neumann_solver_agrees_with_jacobi():
 def test_batch_matches_plain_and_oracle():
     """Independent problems of uneven size in one launch (and as a CUDA graph)
     against one launch sequence per problem, and against the oracle."""
+    from paper_2110_10310_gb300 import _lib as L
     from paper_2110_10310_gb300.system import LindbladBatch
 
     probs = W.config3(n_problems=12, n_steps=60)
-    systems = [_sys(p) for p in probs]
+    systems = [_sys(p, sweep=L.LB_SWEEP_RESIDENT) for p in probs]
     plain = [s.gradient() for s in systems]
     b = LindbladBatch(systems)
     Gb, gb = b.gradient()
@@ -245,3 +246,98 @@ def test_host_buffers_roundtrip():
     s.set_states_host(pinned, p.weights)
     torch.cuda.synchronize()
     assert s.forward() == G0
+
+
+# ----------------------------------------------------------------------------
+# grid-wide sweeps (one cooperative launch over all SMs and states)
+
+
+@pytest.mark.parametrize("levels,K,herm", [((2, 3), 7, False), ((3, 2, 2), 0, True), ((4, 3), 100, False)])
+def test_grid_sweep_matches_oracle(levels, K, herm):
+    """The grid sweep forced on small states: oracle parity, and agreement with
+    the one-CTA-per-state sweep."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(401, levels=levels, n_states=3, n_steps=40, T_ns=0.8, amp=0.1, ckpt_every=K,
+                         hermitian=herm)
+    _, g = _check_problem(p, sweep=L.LB_SWEEP_GRID)
+    Gr, gr = _sys(p, sweep=L.LB_SWEEP_RESIDENT).gradient()
+    Gg, gg = _sys(p, sweep=L.LB_SWEEP_GRID).gradient()
+    assert abs(Gg - Gr) <= 1e-12 * abs(Gr)
+    assert _rel(gg, gr) < 1e-11
+
+
+def test_grid_checkpoint_interval_bitwise_identical():
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(402, levels=(3, 3), n_states=2, n_steps=45, T_ns=0.9, amp=0.1)
+    res = [_sys(p, ckpt_every=K, sweep=L.LB_SWEEP_GRID).gradient() for K in (0, 1, 7, 100)]
+    for G, g in res[1:]:
+        assert G == res[0][0]
+        assert np.array_equal(g, res[0][1])
+
+
+def _imr_residual(mdl, j, q0, q1, adjoint=False):
+    """max |q1 - q0 - dt L(z)| with z = (q0 + q1)/2, L the (adjoint) Lindbladian
+    at t_j + dt/2 in matrix form (any size)."""
+    t = mdl.t_half(j)
+    H = mdl.H(t)
+    f = model.adjoint_matrix_form if adjoint else model.lindblad_matrix_form
+    out = 0.0
+    for a, b in zip(q0, q1):
+        Z = 0.5 * (a + b)
+        out = max(out, float(np.max(np.abs(b - a - mdl.h * f(H, mdl.Ls, Z)))))
+    return out
+
+
+@pytest.mark.parametrize("which", ["qudits_4x4", "qutrits_6x3"])
+def test_full_size_steps_satisfy_imr(which):
+    """At full workload size (N^2 = 65536 and 531441), forward and adjoint steps
+    taken by the grid sweep satisfy the implicit midpoint relation
+    q^{j+1} - q^j = dt L((q^j + q^{j+1})/2) with the oracle's matrix-form
+    Lindbladian, to FP64 rounding."""
+    if which == "qudits_4x4":
+        p = W.config4(n_states=3)
+    else:
+        p = W.config5(n_states=2)
+    s = _sys(p, ckpt_every=10)
+    mdl = model.Model(p.system, p.controls)
+    rng = np.random.default_rng(7)
+    x0 = torch.from_numpy(p.rho0).cuda()
+    j = 1234
+    x1 = s.propagate(x0, j, j + 1)
+    r = _imr_residual(mdl, j, p.rho0, x1.cpu().numpy())
+    assert r <= 1e-13 * np.max(np.abs(p.rho0)), r
+    lam = rng.standard_normal(p.rho0.shape) * 1e-2 + 0j
+    l1 = s.propagate(torch.from_numpy(lam).cuda(), j, j + 1, adjoint=True)
+    r = _imr_residual(mdl, j, lam, l1.cpu().numpy(), adjoint=True)
+    assert r <= 1e-13 * np.max(np.abs(lam)), r
+    # trace preserved by the forward step
+    tr0 = np.trace(p.rho0, axis1=1, axis2=2)
+    tr1 = np.trace(x1.cpu().numpy(), axis1=1, axis2=2)
+    assert np.max(np.abs(tr1 - tr0)) < 1e-13
+
+
+@pytest.mark.slow
+def test_qudits_4x4_gradient_against_gpu_central_differences():
+    """4 x 4-level qudits at full size (N^2 = 65536, 3 states) over the first
+    400 steps at the workload's dt, checkpoints every 100: the adjoint gradient
+    against central differences of the GPU objective on sampled coefficients,
+    and forward states against a 2-step oracle-checked prefix."""
+    p = W.config4(n_steps=400)
+    p.system.T_ns = 500.0 * 400 / 40000
+    s = _sys(p)
+    G, g = s.gradient()
+    a0 = p.controls.alpha.copy()
+    eps = 1e-5
+    scale = np.max(np.abs(g))
+    for k in (0, 61, 122, 301, 479):
+        a = a0.copy()
+        a[k] += eps
+        s.set_alpha(a)
+        gp = s.forward()
+        a[k] -= 2 * eps
+        s.set_alpha(a)
+        gm = s.forward()
+        assert abs((gp - gm) / (2 * eps) - g[k]) <= 1e-6 * scale, (k, (gp - gm) / (2 * eps), g[k])
+    s.set_alpha(a0)

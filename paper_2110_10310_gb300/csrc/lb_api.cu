@@ -658,7 +658,7 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
   if (rc) return rc;
   rc = upload_controls(s, st);
   if (rc) return rc;
-  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N);
+  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true);
   // the workspace now owns the states; pageable copies above are staged
   s->rho0.clear();
   s->rho0.shrink_to_fit();
@@ -846,7 +846,7 @@ int lb_batch_create(lb_system* const* systems, int32_t n, lb_batch** out) {
   if (!systems || n < 1 || !out) return fail(LB_EINVAL, "bad batch arguments");
   lb_batch* b = new (std::nothrow) lb_batch();
   if (!b) return fail(LB_ENOMEM, "host allocation failed");
-  int maxV = 0, maxQ = 0, maxc = 0, maxj = 0, maxN = 0;
+  int maxV = 0, maxQ = 0, maxc = 0, maxj = 0, maxN = 0, minQ = LB_MAXQ + 1;
   for (int i = 0; i < n; ++i) {
     lb_system* s = systems[i];
     if (!s || !s->ws) {
@@ -863,12 +863,13 @@ int lb_batch_create(lb_system* const* systems, int32_t n, lb_batch** out) {
     b->n_items += s->M;
     maxV = std::max(maxV, s->V);
     maxQ = std::max(maxQ, s->Q);
+    minQ = std::min(minQ, s->Q);
     maxc = std::max(maxc, n_coef(s));
     maxj = std::max(maxj, n_jcoef(s));
     maxN = std::max(maxN, s->N);
     b->max_param_warps = std::max(b->max_param_warps, param_warps(s));
   }
-  b->rc = lbk::resident_config(maxV, maxQ, maxc, maxj, maxN);
+  b->rc = lbk::resident_config(maxV, maxQ, maxc, maxj, maxN, minQ == maxQ);
   *out = b;
   return LB_OK;
 }
@@ -1151,7 +1152,7 @@ int static_bind(lb_system* s, void* ws, cudaStream_t st) {
   if (rc) return rc;
   rc = upload_controls(s, st);
   if (rc) return rc;
-  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N);
+  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true);
   return LB_OK;
 }
 

@@ -99,10 +99,12 @@ constexpr int kMaxResidentV = 4096;  // states held in one CTA's shared memory
 struct ResidentConfig {
   int threads;  // CTA size (multiple of 32, <= 512)
   int E;        // elements per thread (1, 2, 4, 8)
+  int QT;       // E == 1: compile-time subsystem count of the per-thread plan (1..4), 0 = generic
   size_t smem;  // dynamic shared memory bytes
 };
 
-ResidentConfig resident_config(int maxV, int maxQ, int maxNcoef, int maxNj, int maxN);
+// uniformQ: every problem of the launch has Q = maxQ
+ResidentConfig resident_config(int maxV, int maxQ, int maxNcoef, int maxNj, int maxN, bool uniformQ);
 
 cudaError_t launch_tables(ProbDev* d_prob, const ProbDev& h_prob, cudaStream_t s);
 cudaError_t launch_gate_targets(const ProbDev& h_prob, const double2* Vg, const int32_t* emap, const int32_t* efull,

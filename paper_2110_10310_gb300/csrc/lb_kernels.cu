@@ -276,50 +276,150 @@ __device__ __forceinline__ void init_elems(Elems<E>& el, const ResSmem& S, int V
   }
 }
 
+// Per-thread plan for one element per thread and a compile-time subsystem
+// count QT: the neighbour offsets and real coefficients of the element are
+// time independent, so they are computed once and kept in registers; the
+// inner iteration is then nothing but shared-memory loads and FP64.
+template <int QT>
+struct Plan {
+  int o[QT][4];     // x[k+s,l], x[k,l-s], x[k-s,l], x[k,l+s]
+  int ojf[QT];      // x[k+s,l+s] (decay sandwich of M)
+  int oja[QT];      // x[k-s,l-s] (decay sandwich of M^+)
+  double c[QT][4];  // sqrt(nk+1), sqrt(nl), sqrt(nk), sqrt(nl+1), zero off the range
+  double cjf[QT], cja[QT];
+  double2 d;        // this element's (I - dt/2 D)^-1 (or dt/2 D for Neumann)
+};
+template <>
+struct Plan<0> {
+  double2 d;
+};
+
+template <int QT>
+__device__ void build_plan(Plan<QT>& pl, const ResSmem& S, const Hdr& H, uint32_t kd, uint32_t ld, int v) {
+  const bool ok = v < H.V;
+  pl.d = ok ? S.dsm[v] : make_double2(0.0, 0.0);
+  if constexpr (QT > 0) {
+#pragma unroll
+    for (int q = 0; q < QT; ++q) {
+      const int n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * H.N;
+      const int nk = (kd >> (4 * q)) & 15, nl = (ld >> (4 * q)) & 15;
+      const int jo = H.joff[q] + nk * n + nl;
+      pl.c[q][0] = ok ? S.cu[co + nk] : 0.0;
+      pl.c[q][1] = ok ? S.cd[co + nl] : 0.0;
+      pl.c[q][2] = ok ? S.cd[co + nk] : 0.0;
+      pl.c[q][3] = ok ? S.cu[co + nl] : 0.0;
+      pl.o[q][0] = ok ? v + (nk + 1 < n ? s : 0) : 0;
+      pl.o[q][1] = ok ? v - (nl > 0 ? sN : 0) : 0;
+      pl.o[q][2] = ok ? v - (nk > 0 ? s : 0) : 0;
+      pl.o[q][3] = ok ? v + (nl + 1 < n ? sN : 0) : 0;
+      pl.cjf[q] = ok && H.jump[q] != 0.0 ? S.jf[jo] : 0.0;
+      pl.cja[q] = ok && H.jump[q] != 0.0 ? S.ja[jo] : 0.0;
+      pl.ojf[q] = ok ? v + ((nk + 1 < n && nl + 1 < n) ? s + sN : 0) : 0;
+      pl.oja[q] = ok ? v - ((nk > 0 && nl > 0) ? s + sN : 0) : 0;
+    }
+  }
+}
+
+// offdiag_acc with the element's plan; cq[q] = (dt/2) d_q with the sign of
+// M^+ already applied for ADJ; bit q of jon set when subsystem q decays.
+template <int QT, bool ADJ>
+__device__ __forceinline__ void offdiag_plan(double& ar, double& ai, const double2* __restrict__ x,
+                                             const Plan<QT>& pl, const double2 (&cq)[QT > 0 ? QT : 1],
+                                             unsigned jon) {
+#pragma unroll
+  for (int q = 0; q < QT; ++q) {
+    const double2 x1 = x[pl.o[q][0]];
+    const double2 x2 = x[pl.o[q][1]];
+    const double2 x3 = x[pl.o[q][2]];
+    const double2 x4 = x[pl.o[q][3]];
+    const double pr = fma(-pl.c[q][1], x2.x, pl.c[q][0] * x1.x);
+    const double pi = fma(-pl.c[q][1], x2.y, pl.c[q][0] * x1.y);
+    const double rr = fma(-pl.c[q][3], x4.x, pl.c[q][2] * x3.x);
+    const double ri = fma(-pl.c[q][3], x4.y, pl.c[q][2] * x3.y);
+    const double ur = pr + rr, ui = pi + ri, wr = pr - rr, wi = pi - ri;
+    ar = fma(cq[q].y, wr, fma(cq[q].x, ui, ar));
+    ai = fma(cq[q].y, wi, fma(-cq[q].x, ur, ai));
+    if (jon & (1u << q)) {
+      const double cj = ADJ ? pl.cja[q] : pl.cjf[q];
+      const double2 x5 = x[ADJ ? pl.oja[q] : pl.ojf[q]];
+      ar = fma(cj, x5.x, ar);
+      ai = fma(cj, x5.y, ai);
+    }
+  }
+}
+
+// |x| bits, high word: enough to order magnitudes for the stopping test
+__device__ __forceinline__ unsigned hi_abs(double x) {
+  return (unsigned)((unsigned long long)__double_as_longlong(x) >> 32) & 0x7fffffffu;
+}
+constexpr unsigned kInfHi = 0x7ff00000u;
+
 // Solve (I - dt/2 M) z = rhs (ADJ: (I - dt/2 M^+) z = rhs) for the CTA's
 // state.  Returns the iteration count (>= 1), -1 when max_iter is reached,
 // -2 on NaN/Inf.  On return, zbuf[cur] holds z; every thread has passed the
-// final barrier.
-template <int E, bool ADJ>
-__device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, const double2 (&rhs)[E],
-                         const double2* __restrict__ ct, int& cur) {
+// final barrier.  The stopping test compares the high words of the bit
+// patterns, hi(max|z_new - z|) < hi(rtol max|rhs|), which implies the exact
+// test and is taken identically by every thread (and in a recompute).
+// QT > 0 (with E == 1) uses the per-thread plan.
+template <int E, int QT, bool ADJ>
+__device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, const Plan<QT>& pl,
+                         const double2 (&rhs)[E], const double2* __restrict__ ct, int& cur) {
+  static_assert(QT == 0 || E == 1, "the per-thread plan holds one element");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const bool neumann = H.method == LB_SOLVER_NEUMANN;
   const Tabs T{S.cu, S.cd, S.jf, S.ja};
-  unsigned long long qmax = 0;
+  unsigned* slots = reinterpret_cast<unsigned*>(S.slots);
+  double2 cq[QT > 0 ? QT : 1];
+  unsigned jon = 0;
+  if constexpr (QT > 0) {
+#pragma unroll
+    for (int q = 0; q < QT; ++q) {
+      const double2 c = ct[q];
+      cq[q] = ADJ ? make_double2(-c.x, -c.y) : c;
+      jon |= H.jump[q] != 0.0 ? (1u << q) : 0u;
+    }
+  }
+  unsigned qmax = 0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int v = threadIdx.x + e * blockDim.x;
     if (v < H.V) {
       double2 z0 = rhs[e];
       if (!neumann) {
-        const double2 d = S.dsm[v];
+        const double2 d = QT > 0 ? pl.d : S.dsm[v];
         const double di = ADJ ? -d.y : d.y;
         z0 = make_double2(fma(d.x, rhs[e].x, -di * rhs[e].y), fma(d.x, rhs[e].y, di * rhs[e].x));
       }
       S.zb0[v] = z0;
-      qmax = umax64(qmax, umax64(abs_bits(rhs[e].x), abs_bits(rhs[e].y)));
+      qmax = max(qmax, max(hi_abs(rhs[e].x), hi_abs(rhs[e].y)));
     }
   }
-  qmax = warp_max_u64(qmax);
-  if (lane == 0) S.slots[32 + warp] = qmax;
+  qmax = __reduce_max_sync(kFull, qmax);
+  if (lane == 0) slots[64 + warp] = qmax;
   __syncthreads();
   qmax = 0;
-  for (int w = 0; w < nwarps; ++w) qmax = umax64(qmax, S.slots[32 + w]);
-  if (qmax >= kInfBits) return -2;
-  const unsigned long long thr = abs_bits(H.rtol * __longlong_as_double(static_cast<long long>(qmax)));
+  for (int w = 0; w < nwarps; ++w) qmax = max(qmax, slots[64 + w]);
+  if (qmax >= kInfHi) return -2;
+  // rtol * (a value <= max|rhs|), so the test is never looser than the exact one
+  const unsigned thr = hi_abs(H.rtol * __longlong_as_double(static_cast<long long>((unsigned long long)qmax << 32)));
   cur = 0;
   for (int it = 0; it < H.max_iter; ++it) {
     const double2* __restrict__ zc = cur ? S.zb1 : S.zb0;
     double2* __restrict__ zn = cur ? S.zb0 : S.zb1;
-    unsigned long long dmax = 0;
+    unsigned dmax = 0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int v = threadIdx.x + e * blockDim.x;
       if (v < H.V) {
         double ar = rhs[e].x, ai = rhs[e].y;
-        offdiag_acc<ADJ>(ar, ai, zc, v, el.kd[e], el.ld[e], H, T, ct);
-        const double2 d = S.dsm[v];
+        double2 d;
+        if constexpr (QT > 0) {
+          offdiag_plan<QT, ADJ>(ar, ai, zc, pl, cq, jon);
+          d = pl.d;
+        } else {
+          offdiag_acc<ADJ>(ar, ai, zc, v, el.kd[e], el.ld[e], H, T, ct);
+          d = S.dsm[v];
+        }
         const double di = ADJ ? -d.y : d.y;
         const double2 zo = zc[v];
         double2 z;
@@ -331,17 +431,17 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
           z.y = ai + fma(d.x, zo.y, di * zo.x);
         }
         zn[v] = z;
-        dmax = umax64(dmax, umax64(abs_bits(z.x - zo.x), abs_bits(z.y - zo.y)));
+        dmax = max(dmax, max(hi_abs(z.x - zo.x), hi_abs(z.y - zo.y)));
       }
     }
-    dmax = warp_max_u64(dmax);
-    if (lane == 0) S.slots[(it & 1) * 16 + warp] = dmax;
+    dmax = __reduce_max_sync(kFull, dmax);
+    if (lane == 0) slots[(it & 1) * 32 + warp] = dmax;
     __syncthreads();
     dmax = 0;
-    for (int w = 0; w < nwarps; ++w) dmax = umax64(dmax, S.slots[(it & 1) * 16 + w]);
+    for (int w = 0; w < nwarps; ++w) dmax = max(dmax, slots[(it & 1) * 32 + w]);
     cur ^= 1;
-    if (dmax >= kInfBits) return -2;
-    if (dmax <= thr) return it + 1;
+    if (dmax >= kInfHi) return -2;
+    if (dmax < thr) return it + 1;
   }
   return -1;
 }
@@ -382,7 +482,7 @@ struct CtaStats {
 // ---------------------------------------------------------------------------
 // forward sweep, one CTA per (problem, state) work item
 
-template <int E>
+template <int E, int QT>
 __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__ probs,
                                                      const WorkItem* __restrict__ items, int tape) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -394,6 +494,8 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
   const Hdr& H = *S.hdr;
   Elems<E> el;
   init_elems<E>(el, S, H.V, H.N);
+  Plan<QT> pl;
+  build_plan<QT>(pl, S, H, el.kd[0], el.ld[0], threadIdx.x);
   const size_t base = (size_t)i * H.V;
   double2 q[E];
 #pragma unroll
@@ -412,7 +514,7 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
       }
     }
     int cur;
-    const int it = res_solve<E, false>(S, H, el, q, P.ctab + (size_t)j * H.Q, cur);
+    const int it = res_solve<E, QT, false>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur);
     if (it < 0) {
       if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
       stats.flush(P.status);
@@ -457,7 +559,7 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
 // backward sweep: recompute each checkpoint segment, then adjoint steps with
 // the gradient pieces of eq. reducedgradient.
 
-template <int E>
+template <int E, int QT>
 __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict__ probs,
                                                       const WorkItem* __restrict__ items) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -469,6 +571,8 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
   const Hdr& H = *S.hdr;
   Elems<E> el;
   init_elems<E>(el, S, H.V, H.N);
+  Plan<QT> pl;
+  build_plan<QT>(pl, S, H, el.kd[0], el.ld[0], threadIdx.x);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const size_t base = (size_t)i * H.V;
   const double w = P.wgt[i];
@@ -505,7 +609,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       }
       for (int j = j0; j < j1; ++j) {
         int cur;
-        const int it = res_solve<E, false>(S, H, el, qf, P.ctab + (size_t)j * H.Q, cur);
+        const int it = res_solve<E, QT, false>(S, H, el, pl, qf, P.ctab + (size_t)j * H.Q, cur);
         if (it < 0) {
           if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
           stats.flush(P.status);
@@ -529,7 +633,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       const double2* ct = P.ctab + (size_t)j * H.Q;
       int cur;
       // (I - dt/2 (M^{j+1/2})^+) zhat^j = qhat^{j+1}   (eq. linsystem_adjoint)
-      const int it = res_solve<E, true>(S, H, el, lam, ct, cur);
+      const int it = res_solve<E, QT, true>(S, H, el, pl, lam, ct, cur);
       if (it < 0) {
         if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
         stats.flush(P.status);
@@ -604,7 +708,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
 // ---------------------------------------------------------------------------
 // propagate given vectors (tests and the step-level API), one CTA per vector
 
-template <int E>
+template <int E, int QT>
 __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict__ pp, int adjoint, int j0, int j1,
                                                        double2* __restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -614,6 +718,8 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
   const Hdr& H = *S.hdr;
   Elems<E> el;
   init_elems<E>(el, S, H.V, H.N);
+  Plan<QT> pl;
+  build_plan<QT>(pl, S, H, el.kd[0], el.ld[0], threadIdx.x);
   double2* xv = x + (size_t)blockIdx.x * H.V;
   double2 q[E];
 #pragma unroll
@@ -625,8 +731,8 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
   for (int jj = 0; jj < j1 - j0; ++jj) {
     const int j = adjoint ? j1 - 1 - jj : j0 + jj;
     int cur;
-    const int it = adjoint ? res_solve<E, true>(S, H, el, q, P.ctab + (size_t)j * H.Q, cur)
-                           : res_solve<E, false>(S, H, el, q, P.ctab + (size_t)j * H.Q, cur);
+    const int it = adjoint ? res_solve<E, QT, true>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur)
+                           : res_solve<E, QT, false>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur);
     if (it < 0) {
       if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
       stats.flush(P.status);
@@ -1378,8 +1484,7 @@ __global__ void k_objective_states(const ProbDev* __restrict__ pp) {
 // ---------------------------------------------------------------------------
 // launchers
 
-ResidentConfig resident_config(int maxV, int maxQ, int maxNcoef, int maxNj, int maxN) {
-  (void)maxQ;
+ResidentConfig resident_config(int maxV, int maxQ, int maxNcoef, int maxNj, int maxN, bool uniformQ) {
   ResidentConfig rc;
   int E = 1;
   while (E < 8 && (maxV + E - 1) / E > 512) E *= 2;
@@ -1388,69 +1493,77 @@ ResidentConfig resident_config(int maxV, int maxQ, int maxNcoef, int maxNj, int 
   if (threads < 32) threads = 32;
   rc.threads = threads;
   rc.E = E;
+  rc.QT = (E == 1 && uniformQ && maxQ <= 4) ? maxQ : 0;
   rc.smem = res_smem_bytes(maxNcoef, maxNj, maxN, maxV);
   return rc;
 }
 
-template <int E>
+template <int E, int QT>
 static cudaError_t set_smem_attr(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_forward_res<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_forward_res<E, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_backward_res<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(k_backward_res<E, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_propagate_res<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(k_propagate_res<E, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-static cudaError_t prepare(const ResidentConfig& rc) {
-  switch (rc.E) {
-    case 1: return set_smem_attr<1>(rc.smem);
-    case 2: return set_smem_attr<2>(rc.smem);
-    case 4: return set_smem_attr<4>(rc.smem);
-    case 8: return set_smem_attr<8>(rc.smem);
-    default: return cudaErrorInvalidValue;
+// Kernel instantiations: element count per thread E, and for E == 1 the
+// compile-time subsystem count QT of the per-thread plan (0 = generic path).
+template <int E, int QT>
+struct ResKernels {
+  static cudaError_t fwd(dim3 g, dim3 b, size_t sm, cudaStream_t s, const ProbDev* p, const WorkItem* it, int tape) {
+    cudaError_t e = set_smem_attr<E, QT>(sm);
+    if (e != cudaSuccess) return e;
+    k_forward_res<E, QT><<<g, b, sm, s>>>(p, it, tape);
+    return cudaGetLastError();
   }
-}
+  static cudaError_t bwd(dim3 g, dim3 b, size_t sm, cudaStream_t s, const ProbDev* p, const WorkItem* it) {
+    cudaError_t e = set_smem_attr<E, QT>(sm);
+    if (e != cudaSuccess) return e;
+    k_backward_res<E, QT><<<g, b, sm, s>>>(p, it);
+    return cudaGetLastError();
+  }
+  static cudaError_t prop(dim3 g, dim3 b, size_t sm, cudaStream_t s, const ProbDev* p, int adj, int j0, int j1,
+                          double2* x) {
+    cudaError_t e = set_smem_attr<E, QT>(sm);
+    if (e != cudaSuccess) return e;
+    k_propagate_res<E, QT><<<g, b, sm, s>>>(p, adj, j0, j1, x);
+    return cudaGetLastError();
+  }
+};
+
+#define LB_RES_DISPATCH(rc, CALL)                       \
+  do {                                                  \
+    if ((rc).E == 1) {                                  \
+      switch ((rc).QT) {                                \
+        case 1: return ResKernels<1, 1>::CALL;          \
+        case 2: return ResKernels<1, 2>::CALL;          \
+        case 3: return ResKernels<1, 3>::CALL;          \
+        case 4: return ResKernels<1, 4>::CALL;          \
+        default: return ResKernels<1, 0>::CALL;         \
+      }                                                 \
+    }                                                   \
+    switch ((rc).E) {                                   \
+      case 2: return ResKernels<2, 0>::CALL;            \
+      case 4: return ResKernels<4, 0>::CALL;            \
+      case 8: return ResKernels<8, 0>::CALL;            \
+      default: return cudaErrorInvalidValue;            \
+    }                                                   \
+  } while (0)
 
 cudaError_t launch_forward_resident(const ProbDev* d_probs, const WorkItem* d_items, int n_items, int tape,
                                     const ResidentConfig& rc, cudaStream_t s) {
-  cudaError_t e = prepare(rc);
-  if (e != cudaSuccess) return e;
-  dim3 g(n_items), b(rc.threads);
-  switch (rc.E) {
-    case 1: k_forward_res<1><<<g, b, rc.smem, s>>>(d_probs, d_items, tape); break;
-    case 2: k_forward_res<2><<<g, b, rc.smem, s>>>(d_probs, d_items, tape); break;
-    case 4: k_forward_res<4><<<g, b, rc.smem, s>>>(d_probs, d_items, tape); break;
-    case 8: k_forward_res<8><<<g, b, rc.smem, s>>>(d_probs, d_items, tape); break;
-  }
-  return cudaGetLastError();
+  LB_RES_DISPATCH(rc, fwd(dim3(n_items), dim3(rc.threads), rc.smem, s, d_probs, d_items, tape));
 }
 
 cudaError_t launch_backward_resident(const ProbDev* d_probs, const WorkItem* d_items, int n_items,
                                      const ResidentConfig& rc, cudaStream_t s) {
-  cudaError_t e = prepare(rc);
-  if (e != cudaSuccess) return e;
-  dim3 g(n_items), b(rc.threads);
-  switch (rc.E) {
-    case 1: k_backward_res<1><<<g, b, rc.smem, s>>>(d_probs, d_items); break;
-    case 2: k_backward_res<2><<<g, b, rc.smem, s>>>(d_probs, d_items); break;
-    case 4: k_backward_res<4><<<g, b, rc.smem, s>>>(d_probs, d_items); break;
-    case 8: k_backward_res<8><<<g, b, rc.smem, s>>>(d_probs, d_items); break;
-  }
-  return cudaGetLastError();
+  LB_RES_DISPATCH(rc, bwd(dim3(n_items), dim3(rc.threads), rc.smem, s, d_probs, d_items));
 }
 
 cudaError_t launch_propagate_resident(const ProbDev* d_prob, int adjoint, int64_t j0, int64_t j1, double2* x,
                                       int n_vec, const ResidentConfig& rc, cudaStream_t s) {
-  cudaError_t e = prepare(rc);
-  if (e != cudaSuccess) return e;
-  dim3 g(n_vec), b(rc.threads);
-  switch (rc.E) {
-    case 1: k_propagate_res<1><<<g, b, rc.smem, s>>>(d_prob, adjoint, (int)j0, (int)j1, x); break;
-    case 2: k_propagate_res<2><<<g, b, rc.smem, s>>>(d_prob, adjoint, (int)j0, (int)j1, x); break;
-    case 4: k_propagate_res<4><<<g, b, rc.smem, s>>>(d_prob, adjoint, (int)j0, (int)j1, x); break;
-    case 8: k_propagate_res<8><<<g, b, rc.smem, s>>>(d_prob, adjoint, (int)j0, (int)j1, x); break;
-  }
-  return cudaGetLastError();
+  LB_RES_DISPATCH(rc, prop(dim3(n_vec), dim3(rc.threads), rc.smem, s, d_prob, adjoint, (int)j0, (int)j1, x));
 }
 
 cudaError_t launch_tables(ProbDev* d_prob, const ProbDev& h, cudaStream_t s) {

@@ -446,8 +446,7 @@ def main():
     bwd_ms = statistics.median(ms_bwd)
     peak = FP64_FLOP_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
     achieved = bwd_flops / (bwd_ms * 1e-3) / 1e12
-    grid = s.N * s.N > 4096
-    kernel_name = "k_backward_grid" if grid else "k_backward_res"
+    kernel_name = {"grid": "k_backward_grid", "cluster": "k_backward_cl"}.get(st["sweep"], "k_backward_res")
     traffic = traffic_record(kernel_name)
     clocks = clk.summary()
 
@@ -477,7 +476,8 @@ def main():
                 "states": p.M,
                 "n_steps": p.system.n_steps,
                 "ckpt_every": p.ckpt_every,
-                "solver": "jacobi fixed point, rtol 1e-15",
+                "solver": f"{st['solver']} fixed point, rtol 1e-15",
+                "sweep": st["sweep"],
                 "l2": "flushed between timed steps (256 MiB write)",
                 "parallelism": f"replicas{world}" if world > 1 else "single",
                 "inner_iters_per_step": st["inner_iterations"] / max(1, st["state_steps"]),

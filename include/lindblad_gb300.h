@@ -75,11 +75,18 @@ extern "C" {
  *   LB_SWEEP_GRID:     one cooperative launch over all SMs and all states,
  *                      iterates in global memory, a grid barrier per inner
  *                      iteration (any N^2);
+ *   LB_SWEEP_CLUSTER:  one thread-block cluster per state, each element's
+ *                      work split over 2Q lanes, the iterate replicated in
+ *                      every CTA's shared memory (Q <= 4, N^2 * 2Q <= 1024);
+ *                      for small states whose time loop is latency-bound;
  *   LB_SWEEP_AUTO:     GRID when N^2 > 4096 or when N^2 >= 1024 with fewer than
- *                      64 states (most SMs would idle), RESIDENT otherwise. */
+ *                      64 states (most SMs would idle); else CLUSTER when it
+ *                      applies and all clusters fit on the GPU at once; else
+ *                      RESIDENT. */
 #define LB_SWEEP_AUTO 0
 #define LB_SWEEP_RESIDENT 1
 #define LB_SWEEP_GRID 2
+#define LB_SWEEP_CLUSTER 3
 
 #define LB_MAX_SUBSYSTEMS 8 /* Q <= 8 */
 #define LB_MAX_LEVELS 16    /* n_q <= 16 */
@@ -113,6 +120,8 @@ typedef struct lb_stats {
   int64_t phase_iterations[3];
   float ms_forward;         /* device time of the forward-sweep kernel (lb_set_timing on, else 0) */
   float ms_backward;        /* device time of the backward-sweep kernel (recompute + adjoint) */
+  int32_t sweep;            /* LB_SWEEP_* kind the call ran with */
+  int32_t solver;           /* LB_SOLVER_* it ran with */
 } lb_stats;
 
 /* ---- system ------------------------------------------------------------- */
@@ -205,6 +214,17 @@ int lb_apply(lb_system* sys, void* stream, int32_t adjoint, int64_t step, const 
 
 /* Statistics of the last forward / gradient / propagate call. */
 int lb_get_stats(lb_system* sys, lb_stats* out);
+
+/* Autotuner: time `probe_steps` forward steps (from the initial states, on
+ * the device; results discarded) of every candidate compatible with the bound
+ * workspace -- sweep kind (one CTA per state with 1, 2, 4 or 8 elements per
+ * thread, cluster-split when it applies; grid when the workspace was bound
+ * for grid sweeps) x inner solver (Jacobi, Neumann) -- and keep the fastest
+ * candidate whose inner solve converges for later calls.  Synchronises
+ * `stream`.  choice_out (nullable, [3]) receives the chosen LB_SWEEP_*,
+ * LB_SOLVER_* and the threads per CTA (resident), CTAs per cluster (cluster)
+ * or blocks (grid).  LB_ENOTCONV when no candidate converges. */
+int lb_autotune(lb_system* sys, void* stream, int32_t probe_steps, int32_t* choice_out);
 
 /* on != 0: record CUDA events around the sweep kernels on the launching
  * stream and report their device time in lb_stats (ms_forward, ms_backward)

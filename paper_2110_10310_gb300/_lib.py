@@ -28,6 +28,7 @@ LB_J_TR = 1
 LB_SWEEP_AUTO = 0
 LB_SWEEP_RESIDENT = 1
 LB_SWEEP_GRID = 2
+LB_SWEEP_CLUSTER = 3
 
 LB_SOLVER_AUTO = 0
 LB_SOLVER_JACOBI = 1
@@ -71,6 +72,8 @@ class lb_stats(ctypes.Structure):
         ("phase_iterations", c_int64 * 3),
         ("ms_forward", ctypes.c_float),
         ("ms_backward", ctypes.c_float),
+        ("sweep", c_int32),
+        ("solver", c_int32),
     ]
 
 
@@ -95,6 +98,7 @@ SIGNATURES = {
     "lb_apply": (c_int32, [c_void_p, c_void_p, c_int32, c_int64, c_void_p, c_void_p, c_int32]),
     "lb_get_stats": (c_int32, [c_void_p, POINTER(lb_stats)]),
     "lb_set_timing": (c_int32, [c_void_p, c_int32]),
+    "lb_autotune": (c_int32, [c_void_p, c_void_p, c_int32, POINTER(c_int32)]),
     "lb_batch_create": (c_int32, [POINTER(c_void_p), c_int32, POINTER(c_void_p)]),
     "lb_batch_destroy": (None, [c_void_p]),
     "lb_batch_workspace_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),

@@ -86,6 +86,8 @@ struct lb_system {
   int sweep = LB_SWEEP_AUTO;
   int gblocks = 0;   // cooperative grid size (grid sweeps)
   size_t gsmem = 0;  // its dynamic shared memory
+  bool cluster = false;      // cluster-split sweeps (decided at bind)
+  lbk::ClusterConfig cc{};
   // device binding
   char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -133,7 +135,7 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 bool use_grid(const lb_system* s) {
   if (s->V > lbk::kMaxResidentV) return true;
   if (s->sweep == LB_SWEEP_GRID) return true;
-  if (s->sweep == LB_SWEEP_RESIDENT) return false;
+  if (s->sweep == LB_SWEEP_RESIDENT || s->sweep == LB_SWEEP_CLUSTER) return false;
   return s->V >= 1024 && s->M < 64;
 }
 
@@ -462,6 +464,103 @@ void lb_system_destroy(lb_system* s) {
   delete s;
 }
 
+static int propagate_impl(lb_system* s, cudaStream_t st, int adjoint, int64_t j0, int64_t j1, double2* x, int n_vec);
+
+int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice_out) {
+  int rc = check_ready(s, true);
+  if (rc) return rc;
+  if (probe_steps < 1) return fail(LB_EINVAL, "probe_steps must be >= 1");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t steps = probe_steps < s->NT ? probe_steps : s->NT;
+  struct Cand {
+    int sweep, method, E;
+  };
+  std::vector<Cand> cands;
+  const int methods[2] = {LB_SOLVER_JACOBI, LB_SOLVER_NEUMANN};
+  for (int m : methods) {
+    if (use_grid(s)) {
+      cands.push_back({LB_SWEEP_GRID, m, 0});
+      continue;
+    }
+    for (int E = 1; E <= 8; E *= 2) {
+      const int threads = ((s->V + E - 1) / E + 31) / 32 * 32;
+      if (threads > 512 || (E > 1 && threads < 64)) continue;
+      cands.push_back({LB_SWEEP_RESIDENT, m, E});
+    }
+    if (s->cc.C > 0) cands.push_back({LB_SWEEP_CLUSTER, m, 0});
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  LB_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
+  LB_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
+  const lbk::ResidentConfig rc0 = s->rc;
+  const bool cl0 = s->cluster;
+  const int m0 = s->method;
+  float best = -1.0f;
+  Cand win{-1, m0, 0};
+  double2* probe = at<double2>(s, s->L.qT);
+  const size_t bytes = sizeof(double2) * (size_t)s->M * s->V;
+  for (const Cand& c : cands) {
+    s->method = c.method;
+    s->hp.method = c.method;
+    s->cluster = c.sweep == LB_SWEEP_CLUSTER;
+    if (c.sweep == LB_SWEEP_RESIDENT) {
+      s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true);
+      const int threads = ((s->V + c.E - 1) / c.E + 31) / 32 * 32;
+      s->rc.E = c.E;
+      s->rc.threads = threads;
+      s->rc.QT = (c.E == 1 && s->Q <= 4) ? s->Q : 0;
+    }
+    LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
+    LB_CUDA(cudaMemcpyAsync(probe, at<double2>(s, s->L.q0), bytes, cudaMemcpyDeviceToDevice, st), "probe states");
+    // one untimed run (module loading, first-launch costs), one timed
+    int r = propagate_impl(s, st, 0, 0, steps, probe, s->M);
+    if (r == LB_OK) {
+      LB_CUDA(cudaMemcpyAsync(probe, at<double2>(s, s->L.q0), bytes, cudaMemcpyDeviceToDevice, st), "probe states");
+      LB_CUDA(cudaEventRecord(e0, st), "cudaEventRecord");
+      r = propagate_impl(s, st, 0, 0, steps, probe, s->M);
+      LB_CUDA(cudaEventRecord(e1, st), "cudaEventRecord");
+    }
+    if (r == LB_ECUDA) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return r;
+    }
+    if (r != LB_OK) continue;  // this candidate's inner solve does not converge here
+    LB_CUDA(cudaEventSynchronize(e1), "cudaEventSynchronize");
+    float ms = 0.0f;
+    LB_CUDA(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+    if (best < 0.0f || ms < best) {
+      best = ms;
+      win = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (win.sweep < 0) {
+    s->rc = rc0;
+    s->cluster = cl0;
+    s->method = s->hp.method = m0;
+    LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
+    return fail(LB_ENOTCONV, "no candidate's inner solve converged on the probe steps");
+  }
+  s->method = s->hp.method = win.method;
+  s->cluster = win.sweep == LB_SWEEP_CLUSTER;
+  if (win.sweep == LB_SWEEP_RESIDENT) {
+    s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true);
+    s->rc.E = win.E;
+    s->rc.threads = ((s->V + win.E - 1) / win.E + 31) / 32 * 32;
+    s->rc.QT = (win.E == 1 && s->Q <= 4) ? s->Q : 0;
+  }
+  LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
+  LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  if (choice_out) {
+    choice_out[0] = win.sweep;
+    choice_out[1] = win.method;
+    choice_out[2] = win.sweep == LB_SWEEP_RESIDENT ? s->rc.threads : (s->cluster ? s->cc.C : s->gblocks);
+  }
+  return LB_OK;
+}
+
 int lb_set_timing(lb_system* s, int32_t on) {
   if (!s) return fail(LB_EINVAL, "null system handle");
   if (on && !s->ev[0])
@@ -584,8 +683,10 @@ int lb_solver_set(lb_system* s, int32_t method, double rtol, int32_t max_iter, i
 int lb_set_sweep(lb_system* s, int32_t sweep) {
   if (!s) return fail(LB_EINVAL, "null system handle");
   if (s->ws) return fail(LB_EINVAL, "choose the sweep before binding a workspace");
-  if (sweep != LB_SWEEP_AUTO && sweep != LB_SWEEP_RESIDENT && sweep != LB_SWEEP_GRID)
+  if (sweep != LB_SWEEP_AUTO && sweep != LB_SWEEP_RESIDENT && sweep != LB_SWEEP_GRID && sweep != LB_SWEEP_CLUSTER)
     return fail(LB_EINVAL, "unknown sweep kind");
+  if (sweep == LB_SWEEP_CLUSTER && lbk::cluster_config(s->V, s->Q, 1, 1, 1).C <= 0)
+    return fail(LB_EINVAL, "cluster sweeps need Q <= 4 and N^2 * 2Q <= 1024");
   if (sweep == LB_SWEEP_RESIDENT && s->V > lbk::kMaxResidentV)
     return fail(LB_EINVAL, "one CTA per state needs N^2 <= 4096");
   s->sweep = sweep;
@@ -614,6 +715,19 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
   if (bytes < s->L.total) return fail(LB_ENOMEM, "workspace smaller than lb_workspace_bytes");
   if (s->rho0.empty()) return fail(LB_EINVAL, "initial states are required before binding");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s->cluster = false;
+  if (!use_grid(s) && s->sweep != LB_SWEEP_RESIDENT) {
+    s->cc = lbk::cluster_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N);
+    int dev = 0, nsm = 0;
+    LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    LB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    if (s->sweep == LB_SWEEP_CLUSTER) {
+      if (s->cc.C <= 0) return fail(LB_EINVAL, "cluster sweeps need Q <= 4 and N^2 * 2Q <= 1024");
+      s->cluster = true;
+    } else {
+      s->cluster = s->cc.C > 0 && (long long)s->M * s->cc.C <= nsm;
+    }
+  }
   if (use_grid(s)) {
     int dev = 0, coop = 0;
     LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
@@ -688,7 +802,10 @@ static int run_forward(lb_system* s, cudaStream_t st, int tape) {
     return LB_OK;
   }
   if (s->timing) LB_CUDA(cudaEventRecord(s->ev[0], st), "cudaEventRecord");
-  LB_CUDA(lbk::launch_forward_resident(s->dp, s->d_items, s->M, tape, s->rc, st), "forward kernel");
+  if (s->cluster)
+    LB_CUDA(lbk::launch_forward_cluster(s->dp, s->M, tape, s->cc, st), "forward cluster kernel");
+  else
+    LB_CUDA(lbk::launch_forward_resident(s->dp, s->d_items, s->M, tape, s->rc, st), "forward kernel");
   if (s->timing) {
     LB_CUDA(cudaEventRecord(s->ev[1], st), "cudaEventRecord");
     s->timed_fwd = true;
@@ -712,6 +829,8 @@ static int finish(lb_system* s, cudaStream_t st, double* G_out, double* grad_out
   }
   LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
   int rc = read_status(d, &s->last, s->launches);
+  s->last.sweep = use_grid(s) ? LB_SWEEP_GRID : (s->cluster ? LB_SWEEP_CLUSTER : LB_SWEEP_RESIDENT);
+  s->last.solver = s->method;
   if (s->timed_fwd) LB_CUDA(cudaEventElapsedTime(&s->last.ms_forward, s->ev[0], s->ev[1]), "cudaEventElapsedTime");
   if (s->timed_bwd) LB_CUDA(cudaEventElapsedTime(&s->last.ms_backward, s->ev[2], s->ev[3]), "cudaEventElapsedTime");
   if (rc) return rc;
@@ -751,6 +870,8 @@ static int gradient_device(lb_system* s, cudaStream_t st) {
   if (s->timing) LB_CUDA(cudaEventRecord(s->ev[2], st), "cudaEventRecord");
   if (use_grid(s))
     LB_CUDA(lbk::launch_backward_grid(s->dp, s->gblocks, s->gsmem, st), "backward grid sweep");
+  else if (s->cluster)
+    LB_CUDA(lbk::launch_backward_cluster(s->dp, s->M, s->cc, st), "backward cluster kernel");
   else
     LB_CUDA(lbk::launch_backward_resident(s->dp, s->d_items, s->M, s->rc, st), "backward kernel");
   if (s->timing) {
@@ -786,13 +907,8 @@ int lb_gradient_async(lb_system* s, void* stream, void* G_dev, void* grad_dev) {
   return LB_OK;
 }
 
-int lb_propagate(lb_system* s, void* stream, int32_t adjoint, int64_t j0, int64_t j1, void* x_dev, int32_t n_vec) {
-  int rc = check_ready(s, true);
-  if (rc) return rc;
-  if (!x_dev || n_vec < 1) return fail(LB_EINVAL, "bad vectors");
-  if (j0 < 0 || j1 < j0 || j1 > s->NT) return fail(LB_EINVAL, "need 0 <= j0 <= j1 <= n_steps");
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  rc = order_after_uploads(s, st);
+static int propagate_impl(lb_system* s, cudaStream_t st, int adjoint, int64_t j0, int64_t j1, double2* x, int n_vec) {
+  int rc = order_after_uploads(s, st);
   if (rc) return rc;
   s->launches = 0;
   rc = ensure_ctab(s, st);
@@ -804,16 +920,24 @@ int lb_propagate(lb_system* s, void* stream, int32_t adjoint, int64_t j0, int64_
       if (n_vec > s->M) return fail(LB_EINVAL, "grid sweeps propagate at most M vectors at a time");
       LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.gslots), 0, s->L.gslots.bytes, st), "clear grid slots");
       LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.bar), 0, s->L.bar.bytes, st), "clear grid barrier");
-      LB_CUDA(lbk::launch_sweep_grid(s->dp, adjoint ? 2 : 1, 0, 0, j0, j1, static_cast<double2*>(x_dev), n_vec,
-                                     s->gblocks, s->gsmem, st),
+      LB_CUDA(lbk::launch_sweep_grid(s->dp, adjoint ? 2 : 1, 0, 0, j0, j1, x, n_vec, s->gblocks, s->gsmem, st),
               "propagate grid sweep");
+    } else if (s->cluster) {
+      LB_CUDA(lbk::launch_propagate_cluster(s->dp, adjoint, j0, j1, x, n_vec, s->cc, st), "propagate cluster kernel");
     } else {
-      LB_CUDA(lbk::launch_propagate_resident(s->dp, adjoint, j0, j1, static_cast<double2*>(x_dev), n_vec, s->rc, st),
-              "propagate kernel");
+      LB_CUDA(lbk::launch_propagate_resident(s->dp, adjoint, j0, j1, x, n_vec, s->rc, st), "propagate kernel");
     }
     s->launches += 1;
   }
   return finish(s, st, nullptr, nullptr);
+}
+
+int lb_propagate(lb_system* s, void* stream, int32_t adjoint, int64_t j0, int64_t j1, void* x_dev, int32_t n_vec) {
+  int rc = check_ready(s, true);
+  if (rc) return rc;
+  if (!x_dev || n_vec < 1) return fail(LB_EINVAL, "bad vectors");
+  if (j0 < 0 || j1 < j0 || j1 > s->NT) return fail(LB_EINVAL, "need 0 <= j0 <= j1 <= n_steps");
+  return propagate_impl(s, static_cast<cudaStream_t>(stream), adjoint, j0, j1, static_cast<double2*>(x_dev), n_vec);
 }
 
 int lb_apply(lb_system* s, void* stream, int32_t adjoint, int64_t step, const void* x_dev, void* y_dev,

@@ -135,6 +135,20 @@ size_t grid_smem_bytes(int ncoef, int njcoef);
 cudaError_t launch_sweep_grid(const ProbDev* d_prob, int mode, int init_from_q0, int tape, int64_t j0, int64_t j1,
                               double2* x, int nstates, int nblocks, size_t smem, cudaStream_t s);
 cudaError_t launch_backward_grid(const ProbDev* d_prob, int nblocks, size_t smem, cudaStream_t s);
+
+// cluster-split sweeps for small states: one cluster of C CTAs per state,
+// 2Q lanes per element (Q <= 4, N^2 * lanes <= 1024)
+struct ClusterConfig {
+  int C;        // CTAs per cluster (0: not applicable)
+  int QT;       // subsystems (compile-time kernel variant)
+  int threads;  // threads per CTA
+  size_t smem;  // dynamic shared memory per CTA
+};
+ClusterConfig cluster_config(int V, int Q, int ncoef, int njcoef, int N);
+cudaError_t launch_forward_cluster(const ProbDev* d_prob, int M, int tape, const ClusterConfig& cc, cudaStream_t s);
+cudaError_t launch_backward_cluster(const ProbDev* d_prob, int M, const ClusterConfig& cc, cudaStream_t s);
+cudaError_t launch_propagate_cluster(const ProbDev* d_prob, int adjoint, int64_t j0, int64_t j1, double2* x, int n_vec,
+                                     const ClusterConfig& cc, cudaStream_t s);
 cudaError_t launch_objective_states(const ProbDev* d_prob, int M, cudaStream_t s);
 
 }  // namespace lbk

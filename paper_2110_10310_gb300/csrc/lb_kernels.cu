@@ -25,7 +25,11 @@
 
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "lb_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace lbk {
 
@@ -755,6 +759,470 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
     if (v < H.V) xv[v] = q[e];
   }
   stats.flush(P.status);
+}
+
+
+// ---------------------------------------------------------------------------
+// cluster-split sweeps for small states (latency-bound time loops)
+//
+// One state per thread-block cluster of C CTAs.  Each element's off-diagonal
+// work is split over L = 2Q lanes: lane r handles half r%2 of subsystem r/2
+// of the commutator (P = sqrt(nk+1) x[k+s,l] - sqrt(nl) x[k,l-s] or
+// R = sqrt(nk) x[k-s,l] - sqrt(nl+1) x[k,l+s]) times its complex control
+// factor, the P half also the decay sandwich; every lane runs the same
+// instructions on its own data.  The L partial sums meet through shuffles;
+// the CTAs' elements are spread so that a CTA has at most 4 warps (one per SM
+// sub-partition).  Every CTA keeps a full replica of the iterate in shared
+// memory; new values go to all replicas through distributed shared memory and
+// the cluster barrier ends the inner iteration.
+
+template <int QT>
+struct ClLanes {
+  static constexpr int L = 2 * QT <= 2 ? 2 : (2 * QT <= 4 ? 4 : 8);
+};
+
+struct ClSmem {
+  Hdr* hdr;
+  double* cu;
+  double* cd;
+  double* jf;
+  double* ja;
+  uint32_t* dig;
+  double2* zb0;
+  double2* zb1;
+  unsigned* slots;  // [3 banks][32]: warp maxima, index cta * 4 + warp
+  double* gred;     // [8 units][4 warps][2]
+  double* cpart;    // [8 units][8 CTAs][2] (read in CTA 0)
+  double* opart;    // [8 CTAs] (read in CTA 0)
+};
+
+__host__ __device__ inline size_t cl_smem_bytes(int ncoef, int njcoef, int N, int V) {
+  size_t b = align16(sizeof(Hdr));
+  b += align16(sizeof(double) * 2 * ncoef);
+  b += align16(sizeof(double) * 2 * njcoef);
+  b += align16(sizeof(uint32_t) * N);
+  b += sizeof(double2) * 2 * (size_t)V;
+  b += align16(sizeof(unsigned) * 96);
+  b += align16(sizeof(double) * 64);
+  b += align16(sizeof(double) * 128);
+  b += align16(sizeof(double) * 8);
+  return b;
+}
+
+__device__ ClSmem cl_carve(unsigned char* base, int ncoef, int njcoef, int N, int V) {
+  ClSmem S;
+  size_t o = 0;
+  S.hdr = reinterpret_cast<Hdr*>(base + o);
+  o += align16(sizeof(Hdr));
+  S.cu = reinterpret_cast<double*>(base + o);
+  S.cd = S.cu + ncoef;
+  o += align16(sizeof(double) * 2 * ncoef);
+  S.jf = reinterpret_cast<double*>(base + o);
+  S.ja = S.jf + njcoef;
+  o += align16(sizeof(double) * 2 * njcoef);
+  S.dig = reinterpret_cast<uint32_t*>(base + o);
+  o += align16(sizeof(uint32_t) * N);
+  S.zb0 = reinterpret_cast<double2*>(base + o);
+  S.zb1 = S.zb0 + V;
+  o += sizeof(double2) * 2 * (size_t)V;
+  S.slots = reinterpret_cast<unsigned*>(base + o);
+  o += align16(sizeof(unsigned) * 96);
+  S.gred = reinterpret_cast<double*>(base + o);
+  o += align16(sizeof(double) * 64);
+  S.cpart = reinterpret_cast<double*>(base + o);
+  o += align16(sizeof(double) * 128);
+  S.opart = reinterpret_cast<double*>(base + o);
+  return S;
+}
+
+// Shared-memory set-up of one CTA; ends with a cluster barrier so that no
+// CTA writes into another's shared memory before that one is initialised.
+__device__ void cl_setup(const ClSmem& S, const ProbDev& P, cg::cluster_group& cl) {
+  if (threadIdx.x == 0) load_hdr(*S.hdr, P);
+  for (int i = threadIdx.x; i < P.ncoef; i += blockDim.x) {
+    S.cu[i] = P.cu[i];
+    S.cd[i] = P.cd[i];
+  }
+  for (int i = threadIdx.x; i < P.njcoef; i += blockDim.x) {
+    S.jf[i] = P.jf[i];
+    S.ja[i] = P.ja[i];
+  }
+  for (int i = threadIdx.x; i < P.N; i += blockDim.x) S.dig[i] = P.digits[i];
+  for (int i = threadIdx.x; i < 96; i += blockDim.x) S.slots[i] = 0u;
+  __syncthreads();
+  cl.sync();
+}
+
+// one lane's share of one element
+struct ClPlan {
+  int v;          // element (vec index) of this lane; 0 when none
+  bool ev;        // the lane belongs to a real element
+  int r;          // lane within the element, 0..L-1
+  int q;          // subsystem of this lane's half (0 for padding lanes)
+  bool rhalf;     // R half (else P half)
+  int oa, ob, ojf, oja;
+  double ca, cb, cjf, cja;
+  double2 d;      // (I - dt/2 D)^-1 of the element (dt/2 D for Neumann)
+};
+
+template <int QT>
+__device__ ClPlan cl_plan(const ClSmem& S, const ProbDev& P, int C, int crank) {
+  constexpr int L = ClLanes<QT>::L;
+  const Hdr& H = *S.hdr;
+  const int Vc = (H.V + C - 1) / C;
+  const int le = threadIdx.x / L;
+  ClPlan pl;
+  pl.r = threadIdx.x % L;
+  const int v = crank * Vc + le;
+  pl.ev = le < Vc && v < H.V;
+  pl.v = pl.ev ? v : 0;
+  const int u = pl.r < 2 * QT ? pl.r : -1;
+  pl.q = u >= 0 ? u / 2 : 0;
+  pl.rhalf = u >= 0 && (u & 1);
+  pl.oa = pl.ob = pl.ojf = pl.oja = pl.v;
+  pl.ca = pl.cb = pl.cjf = pl.cja = 0.0;
+  pl.d = make_double2(0.0, 0.0);
+  if (pl.ev) {
+    const bool neumann = H.method == LB_SOLVER_NEUMANN;
+    const double hh = 0.5 * H.h;
+    if (neumann) {
+      const double2 D = P.D[v];
+      pl.d = make_double2(hh * D.x, hh * D.y);
+    } else {
+      pl.d = P.Dinv[v];
+    }
+    if (u >= 0) {
+      const uint32_t kd = S.dig[v % H.N], ld = S.dig[v / H.N];
+      const int q = pl.q, n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * H.N;
+      const int nk = (kd >> (4 * q)) & 15, nl = (ld >> (4 * q)) & 15;
+      if (!pl.rhalf) {
+        pl.oa = v + (nk + 1 < n ? s : 0);
+        pl.ob = v - (nl > 0 ? sN : 0);
+        pl.ca = S.cu[co + nk];
+        pl.cb = S.cd[co + nl];
+        if (H.jump[q] != 0.0) {
+          const int jo = H.joff[q] + nk * n + nl;
+          pl.cjf = S.jf[jo];
+          pl.cja = S.ja[jo];
+          pl.ojf = v + ((nk + 1 < n && nl + 1 < n) ? s + sN : 0);
+          pl.oja = v - ((nk > 0 && nl > 0) ? s + sN : 0);
+        }
+      } else {
+        pl.oa = v - (nk > 0 ? s : 0);
+        pl.ob = v + (nl + 1 < n ? sN : 0);
+        pl.ca = S.cd[co + nk];
+        pl.cb = S.cu[co + nl];
+      }
+    }
+  }
+  return pl;
+}
+
+// Write z into element v of buffer `buf` of every CTA of the cluster; the L
+// lanes of the element share the C stores.
+template <int L>
+__device__ __forceinline__ void cl_broadcast(cg::cluster_group& cl, double2* buf, const ClPlan& pl, double2 z, int C) {
+  if (pl.ev)
+    for (int c = pl.r; c < C; c += L) cl.map_shared_rank(buf, c)[pl.v] = z;
+}
+
+// Push this warp's value into slot `idx` of every CTA (lanes 0..C-1 store).
+__device__ __forceinline__ void cl_push_slot(cg::cluster_group& cl, unsigned* slots, int idx, unsigned val, int C) {
+  const int lane = threadIdx.x & 31;
+  if (lane < C) cl.map_shared_rank(slots, lane)[idx] = val;
+}
+
+// Solve (I - dt/2 M) z = rhs (ADJ: M^+) for the cluster's state; returns the
+// iteration count, -1 (max_iter) or -2 (NaN/Inf); zbuf[cur] then holds z in
+// every CTA, and `z` the element's value in every lane of it.
+template <int QT, bool ADJ>
+__device__ int cl_solve(cg::cluster_group& cl, const ClSmem& S, const ClPlan& pl, double2 rhs,
+                        const double2* __restrict__ ct, int C, int crank, int& cur, double2& zout) {
+  constexpr int L = ClLanes<QT>::L;
+  const Hdr& H = *S.hdr;
+  const int warp = threadIdx.x >> 5;
+  const bool neumann = H.method == LB_SOLVER_NEUMANN;
+  const int nslots = C * 4;
+  // complex factor of this lane's half: -i d P -> (b - i a) P, -i conj(d) R -> (-b - i a) R
+  const double2 c = ct[pl.q];
+  double Ar = pl.rhalf ? -c.y : c.y, Ai = -c.x;
+  if (ADJ) {
+    Ar = -Ar;
+    Ai = -Ai;
+  }
+  const double di = ADJ ? -pl.d.y : pl.d.y;
+  double2 z0 = rhs;
+  if (!neumann) z0 = make_double2(fma(pl.d.x, rhs.x, -di * rhs.y), fma(pl.d.x, rhs.y, di * rhs.x));
+  cl_broadcast<L>(cl, S.zb0, pl, z0, C);
+  unsigned qm = (pl.ev && pl.r == 0) ? max(hi_abs(rhs.x), hi_abs(rhs.y)) : 0u;
+  qm = __reduce_max_sync(kFull, qm);
+  cl_push_slot(cl, S.slots, 64 + crank * 4 + warp, qm, C);
+  cl.sync();
+  unsigned qmax = 0;
+  for (int k = 0; k < nslots; ++k) qmax = max(qmax, S.slots[64 + k]);
+  if (qmax >= kInfHi) return -2;
+  const unsigned thr = hi_abs(H.rtol * __longlong_as_double(static_cast<long long>((unsigned long long)qmax << 32)));
+  cur = 0;
+  double2 zc_own = z0;
+  for (int it = 0; it < H.max_iter; ++it) {
+    const double2* __restrict__ zc = cur ? S.zb1 : S.zb0;
+    double2* zn = cur ? S.zb0 : S.zb1;
+    const double2 xa = zc[pl.oa], xb = zc[pl.ob];
+    const double xr = fma(-pl.cb, xb.x, pl.ca * xa.x);
+    const double xi = fma(-pl.cb, xb.y, pl.ca * xa.y);
+    double accr = fma(Ar, xr, -Ai * xi);
+    double acci = fma(Ar, xi, Ai * xr);
+    const double cj = ADJ ? pl.cja : pl.cjf;
+    const double2 x5 = zc[ADJ ? pl.oja : pl.ojf];
+    accr = fma(cj, x5.x, accr);
+    acci = fma(cj, x5.y, acci);
+#pragma unroll
+    for (int o = 1; o < L; o <<= 1) {
+      accr += __shfl_xor_sync(kFull, accr, o);
+      acci += __shfl_xor_sync(kFull, acci, o);
+    }
+    const double ar = rhs.x + accr, ai = rhs.y + acci;
+    double2 z;
+    if (!neumann) {
+      z.x = fma(pl.d.x, ar, -di * ai);
+      z.y = fma(pl.d.x, ai, di * ar);
+    } else {
+      z.x = ar + fma(pl.d.x, zc_own.x, -di * zc_own.y);
+      z.y = ai + fma(pl.d.x, zc_own.y, di * zc_own.x);
+    }
+    cl_broadcast<L>(cl, zn, pl, z, C);
+    unsigned dm = (pl.ev && pl.r == 0) ? max(hi_abs(z.x - zc_own.x), hi_abs(z.y - zc_own.y)) : 0u;
+    dm = __reduce_max_sync(kFull, dm);
+    cl_push_slot(cl, S.slots, (it & 1) * 32 + crank * 4 + warp, dm, C);
+    cl.sync();
+    unsigned dmax = 0;
+    for (int k = 0; k < nslots; ++k) dmax = max(dmax, S.slots[(it & 1) * 32 + k]);
+    cur ^= 1;
+    zc_own = z;
+    if (dmax >= kInfHi) return -2;
+    if (dmax < thr) {
+      zout = z;
+      return it + 1;
+    }
+  }
+  return -1;
+}
+
+// Sum of one double per lane over the cluster's elements (lanes r == 0 of
+// real elements contribute), in a fixed order; the result is returned in
+// CTA 0 thread 0.  Two CTA barriers and one cluster barrier.
+template <int L>
+__device__ double cl_sum(cg::cluster_group& cl, const ClSmem& S, double x, int crank) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  x = warp_sum(x);
+  if (lane == 0) S.gred[warp] = x;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < nwarps; ++w) t += S.gred[w];
+    cl.map_shared_rank(S.opart, 0)[crank] = t;
+  }
+  __syncthreads();
+  cl.sync();
+  double tot = 0.0;
+  if (crank == 0 && threadIdx.x == 0)
+    for (int c = 0; c < (int)cl.num_blocks(); ++c) tot += S.opart[c];
+  return tot;
+}
+
+template <int QT>
+__global__ void __launch_bounds__(128) k_forward_cl(const ProbDev* __restrict__ pp, int tape) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  constexpr int L = ClLanes<QT>::L;
+  const ProbDev& P = *pp;
+  const int C = (int)cl.num_blocks(), crank = (int)cl.block_rank();
+  const int i = blockIdx.x / C;
+  const ClSmem S = cl_carve(smem, P.ncoef, P.njcoef, P.N, P.V);
+  cl_setup(S, P, cl);
+  const Hdr& H = *S.hdr;
+  const ClPlan pl = cl_plan<QT>(S, P, C, crank);
+  const size_t base = (size_t)i * H.V;
+  double2 q = pl.ev ? P.q0[base + pl.v] : make_double2(0.0, 0.0);
+  const bool writer = pl.ev && pl.r == 0;
+  CtaStats stats;
+  bool failed = false;
+  for (int j = 0; j < H.NT; ++j) {
+    if (tape && H.K > 0 && j % H.K == 0 && writer) P.ckpt[((size_t)i * H.n_ckpt + j / H.K) * H.V + pl.v] = q;
+    int cur;
+    double2 z;
+    const int it = cl_solve<QT, false>(cl, S, pl, q, P.ctab + (size_t)j * H.Q, C, crank, cur, z);
+    if (it < 0) {
+      if (threadIdx.x == 0 && crank == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
+      failed = true;
+      break;
+    }
+    if (crank == 0) stats.add(0, it);
+    if (tape && H.K == 0 && writer) P.ckpt[((size_t)i * H.NT + j) * H.V + pl.v] = z;
+    q = make_double2(fma(2.0, z.x, -q.x), fma(2.0, z.y, -q.y));
+  }
+  if (!failed) {
+    double acc = 0.0;
+    if (writer) {
+      P.qT[base + pl.v] = q;
+      const double2 t = P.tar[base + pl.v];
+      if (H.kind == LB_J_FROB) {
+        const double dr = q.x - t.x, dq = q.y - t.y;
+        acc = fma(dr, dr, dq * dq);
+      } else {
+        acc = fma(t.x, q.x, t.y * q.y);
+      }
+    }
+    const double tot = cl_sum<L>(cl, S, acc, crank);
+    if (crank == 0 && threadIdx.x == 0) P.J[i] = H.kind == LB_J_FROB ? 0.5 * tot : 1.0 - tot;
+  }
+  stats.flush(P.status);
+  cl.sync();  // no CTA leaves while another may still write into its shared memory
+}
+
+template <int QT>
+__global__ void __launch_bounds__(128) k_backward_cl(const ProbDev* __restrict__ pp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  constexpr int L = ClLanes<QT>::L;
+  const ProbDev& P = *pp;
+  const int C = (int)cl.num_blocks(), crank = (int)cl.block_rank();
+  const int i = blockIdx.x / C;
+  const ClSmem S = cl_carve(smem, P.ncoef, P.njcoef, P.N, P.V);
+  cl_setup(S, P, cl);
+  const Hdr& H = *S.hdr;
+  const ClPlan pl = cl_plan<QT>(S, P, C, crank);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const size_t base = (size_t)i * H.V;
+  const bool writer = pl.ev && pl.r == 0;
+  const double w = P.wgt[i];
+  double2 lam = make_double2(0.0, 0.0), qf = lam;
+  if (pl.ev) {
+    const double2 t = P.tar[base + pl.v];
+    if (H.kind == LB_J_FROB) {
+      const double2 qq = P.qT[base + pl.v];
+      lam = make_double2(w * (qq.x - t.x), w * (qq.y - t.y));
+    } else {
+      lam = make_double2(-w * t.x, -w * t.y);
+    }
+  }
+  CtaStats stats;
+  bool failed = false;
+  const int nseg = H.K > 0 ? (H.NT + H.K - 1) / H.K : 1;
+  for (int sg = nseg - 1; sg >= 0 && !failed; --sg) {
+    const int j0 = H.K > 0 ? sg * H.K : 0;
+    const int j1 = H.K > 0 ? min(H.NT, j0 + H.K) : H.NT;
+    if (H.K > 0) {
+      qf = pl.ev ? P.ckpt[((size_t)i * H.n_ckpt + sg) * H.V + pl.v] : make_double2(0.0, 0.0);
+      for (int j = j0; j < j1; ++j) {
+        int cur;
+        double2 z;
+        const int it = cl_solve<QT, false>(cl, S, pl, qf, P.ctab + (size_t)j * H.Q, C, crank, cur, z);
+        if (it < 0) {
+          if (threadIdx.x == 0 && crank == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
+          failed = true;
+          break;
+        }
+        if (crank == 0) stats.add(1, it);
+        if (writer) P.seg[((size_t)i * H.K + (j - j0)) * H.V + pl.v] = z;
+        qf = make_double2(fma(2.0, z.x, -qf.x), fma(2.0, z.y, -qf.y));
+      }
+      if (failed) break;
+    }
+    for (int j = j1 - 1; j >= j0; --j) {
+      const double2* ct = P.ctab + (size_t)j * H.Q;
+      int cur;
+      double2 zh;
+      const int it = cl_solve<QT, true>(cl, S, pl, lam, ct, C, crank, cur, zh);
+      if (it < 0) {
+        if (threadIdx.x == 0 && crank == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
+        failed = true;
+        break;
+      }
+      if (crank == 0) stats.add(2, it);
+      // gradient piece of this lane's half (eq. reducedgradient): sum_kl Z conj(X_zhat)
+      // with X the half's neighbour combination of zhat; P half -> g_ad, R half -> g_a
+      const double2* zb = cur ? S.zb1 : S.zb0;
+      double sr = 0.0, si = 0.0;
+      if (pl.ev && pl.r < 2 * QT) {
+        const double2 Z = H.K > 0 ? P.seg[((size_t)i * H.K + (j - j0)) * H.V + pl.v]
+                                  : P.ckpt[((size_t)i * H.NT + j) * H.V + pl.v];
+        const double2 xa = zb[pl.oa], xb = zb[pl.ob];
+        const double xr = fma(-pl.cb, xb.x, pl.ca * xa.x);
+        const double xi = fma(-pl.cb, xb.y, pl.ca * xa.y);
+        sr = fma(Z.x, xr, Z.y * xi);
+        si = fma(Z.y, xr, -Z.x * xi);
+      }
+#pragma unroll
+      for (int o = L; o < 32; o <<= 1) {
+        sr += __shfl_xor_sync(kFull, sr, o);
+        si += __shfl_xor_sync(kFull, si, o);
+      }
+      if (lane < L) {
+        S.gred[(lane * 4 + warp) * 2] = sr;
+        S.gred[(lane * 4 + warp) * 2 + 1] = si;
+      }
+      __syncthreads();
+      if (threadIdx.x < L) {
+        double tr = 0.0, ti = 0.0;
+        for (int ww = 0; ww < nwarps; ++ww) {
+          tr += S.gred[(threadIdx.x * 4 + ww) * 2];
+          ti += S.gred[(threadIdx.x * 4 + ww) * 2 + 1];
+        }
+        double* dst = cl.map_shared_rank(S.cpart, 0);
+        dst[(threadIdx.x * 8 + crank) * 2] = tr;
+        dst[(threadIdx.x * 8 + crank) * 2 + 1] = ti;
+      }
+      cl.sync();
+      if (crank == 0 && threadIdx.x < 2 * QT) {
+        double tr = 0.0, ti = 0.0;
+        for (int c = 0; c < C; ++c) {
+          tr += S.cpart[(threadIdx.x * 8 + c) * 2];
+          ti += S.cpart[(threadIdx.x * 8 + c) * 2 + 1];
+        }
+        const int q = threadIdx.x >> 1;
+        // multiply by -i: (si, -sr); R half is g_a (slot 0), P half is g_ad (slot 1)
+        double2* g = P.gproj + (((size_t)i * H.NT + j) * H.Q + q) * 2;
+        g[(threadIdx.x & 1) ? 0 : 1] = make_double2(ti, -tr);
+      }
+      lam = make_double2(fma(2.0, zh.x, -lam.x), fma(2.0, zh.y, -lam.y));
+    }
+  }
+  stats.flush(P.status);
+  cl.sync();
+}
+
+template <int QT>
+__global__ void __launch_bounds__(128) k_propagate_cl(const ProbDev* __restrict__ pp, int adjoint, int j0, int j1,
+                                                      double2* __restrict__ x) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const ProbDev& P = *pp;
+  const int C = (int)cl.num_blocks(), crank = (int)cl.block_rank();
+  const int i = blockIdx.x / C;
+  const ClSmem S = cl_carve(smem, P.ncoef, P.njcoef, P.N, P.V);
+  cl_setup(S, P, cl);
+  const Hdr& H = *S.hdr;
+  const ClPlan pl = cl_plan<QT>(S, P, C, crank);
+  double2* xv = x + (size_t)i * H.V;
+  double2 q = pl.ev ? xv[pl.v] : make_double2(0.0, 0.0);
+  CtaStats stats;
+  for (int jj = 0; jj < j1 - j0; ++jj) {
+    const int j = adjoint ? j1 - 1 - jj : j0 + jj;
+    int cur;
+    double2 z;
+    const int it = adjoint ? cl_solve<QT, true>(cl, S, pl, q, P.ctab + (size_t)j * H.Q, C, crank, cur, z)
+                           : cl_solve<QT, false>(cl, S, pl, q, P.ctab + (size_t)j * H.Q, C, crank, cur, z);
+    if (it < 0) {
+      if (threadIdx.x == 0 && crank == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
+      break;
+    }
+    if (crank == 0) stats.add(adjoint ? 2 : 0, it);
+    q = make_double2(fma(2.0, z.x, -q.x), fma(2.0, z.y, -q.y));
+  }
+  if (pl.ev && pl.r == 0) xv[pl.v] = q;
+  stats.flush(P.status);
+  cl.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -1649,6 +2117,74 @@ cudaError_t launch_backward_grid(const ProbDev* d_prob, int nblocks, size_t smem
 cudaError_t launch_objective_states(const ProbDev* d_prob, int M, cudaStream_t s) {
   k_objective_states<<<M, 256, 0, s>>>(d_prob);
   return cudaGetLastError();
+}
+
+// ---- cluster-split sweeps ----------------------------------------------------
+
+ClusterConfig cluster_config(int V, int Q, int ncoef, int njcoef, int N) {
+  ClusterConfig cc{};
+  if (Q < 1 || Q > 4) return cc;
+  const int L = 2 * Q <= 2 ? 2 : (2 * Q <= 4 ? 4 : 8);
+  const int C = (V * L + 127) / 128;
+  if (C < 1 || C > 8) return cc;
+  const int Vc = (V + C - 1) / C;
+  cc.C = C;
+  cc.QT = Q;
+  cc.threads = ((Vc * L + 31) / 32) * 32;
+  cc.smem = cl_smem_bytes(ncoef, njcoef, N, V);
+  return cc;
+}
+
+template <int QT>
+struct ClKernels {
+  static cudaError_t attrs(size_t smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_forward_cl<QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_backward_cl<QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_propagate_cl<QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  }
+  template <class K, class... Args>
+  static cudaError_t launch(K kern, const ClusterConfig& cc, int n_states, cudaStream_t s, Args... args) {
+    cudaError_t e = attrs(cc.smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_states * cc.C);
+    cfg.blockDim = dim3(cc.threads);
+    cfg.dynamicSmemBytes = cc.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cc.C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+  }
+};
+
+#define LB_CL_DISPATCH(cc, EXPR_T)          \
+  switch ((cc).QT) {                          \
+    case 1: { constexpr int QT_ = 1; EXPR_T } \
+    case 2: { constexpr int QT_ = 2; EXPR_T } \
+    case 3: { constexpr int QT_ = 3; EXPR_T } \
+    case 4: { constexpr int QT_ = 4; EXPR_T } \
+    default: return cudaErrorInvalidValue;    \
+  }
+
+cudaError_t launch_forward_cluster(const ProbDev* d_prob, int M, int tape, const ClusterConfig& cc, cudaStream_t s) {
+  LB_CL_DISPATCH(cc, return ClKernels<QT_>::launch(k_forward_cl<QT_>, cc, M, s, d_prob, tape);)
+}
+
+cudaError_t launch_backward_cluster(const ProbDev* d_prob, int M, const ClusterConfig& cc, cudaStream_t s) {
+  LB_CL_DISPATCH(cc, return ClKernels<QT_>::launch(k_backward_cl<QT_>, cc, M, s, d_prob);)
+}
+
+cudaError_t launch_propagate_cluster(const ProbDev* d_prob, int adjoint, int64_t j0, int64_t j1, double2* x, int n_vec,
+                                     const ClusterConfig& cc, cudaStream_t s) {
+  LB_CL_DISPATCH(cc, return ClKernels<QT_>::launch(k_propagate_cl<QT_>, cc, n_vec, s, d_prob, adjoint, (int)j0,
+                                                   (int)j1, x);)
 }
 
 }  // namespace lbk

@@ -38,7 +38,9 @@ def _stats_dict(s) -> dict:
     return {"state_steps": s.state_steps, "inner_iterations": s.inner_iterations,
             "max_iterations": s.max_iterations, "kernel_launches": s.kernel_launches,
             "phase_steps": list(s.phase_steps), "phase_iterations": list(s.phase_iterations),
-            "ms_forward": s.ms_forward, "ms_backward": s.ms_backward}
+            "ms_forward": s.ms_forward, "ms_backward": s.ms_backward,
+            "sweep": {1: "resident", 2: "grid", 3: "cluster"}.get(s.sweep, s.sweep),
+            "solver": {1: "jacobi", 2: "neumann"}.get(s.solver, s.solver)}
 
 
 def _stream_handle(stream) -> c_void_p:
@@ -175,6 +177,15 @@ class LindbladSystem:
         s = L.lb_stats()
         L.check(self.lib.lb_get_stats(self.h, byref(s)))
         return _stats_dict(s)
+
+    def autotune(self, probe_steps: int = 20, stream=None) -> dict:
+        """Time the candidate sweep kinds and inner solvers on a short probe and
+        keep the fastest (lb_autotune)."""
+        out = (c_int32 * 3)()
+        L.check(self.lib.lb_autotune(self.h, _stream_handle(stream), int(probe_steps), out))
+        names = {L.LB_SWEEP_RESIDENT: "resident", L.LB_SWEEP_GRID: "grid", L.LB_SWEEP_CLUSTER: "cluster"}
+        solvers = {L.LB_SOLVER_JACOBI: "jacobi", L.LB_SOLVER_NEUMANN: "neumann"}
+        return {"sweep": names.get(out[0], out[0]), "solver": solvers.get(out[1], out[1]), "shape": out[2]}
 
     def set_timing(self, on: bool = True):
         L.check(self.lib.lb_set_timing(self.h, int(on)))

@@ -341,3 +341,55 @@ def test_qudits_4x4_gradient_against_gpu_central_differences():
         gm = s.forward()
         assert abs((gp - gm) / (2 * eps) - g[k]) <= 1e-6 * scale, (k, (gp - gm) / (2 * eps), g[k])
     s.set_alpha(a0)
+
+
+# ----------------------------------------------------------------------------
+# cluster-split sweeps (one cluster per state, 2Q lanes per element)
+
+
+@pytest.mark.parametrize("levels,K,herm", [((2,), 7, False), ((2, 3), 0, True), ((2, 2, 2), 100, False),
+                                            ((3, 2), 5, True), ((3, 3), 7, False)])
+def test_cluster_sweep_matches_oracle(levels, K, herm):
+    """The cluster sweep against the oracle (1e-10 / 1e-9) and against the
+    one-CTA-per-state sweep."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(601, levels=levels, n_states=3, n_steps=40, T_ns=0.8, amp=0.1, ckpt_every=K,
+                         hermitian=herm, objective="trace" if herm else "frob", gamma2=0.05)
+    _check_problem(p, sweep=L.LB_SWEEP_CLUSTER)
+    Gc, gc = _sys(p, sweep=L.LB_SWEEP_CLUSTER).gradient()
+    Gr, gr = _sys(p, sweep=L.LB_SWEEP_RESIDENT).gradient()
+    assert abs(Gc - Gr) <= 1e-12 * abs(Gr)
+    assert _rel(gc, gr) < 1e-11
+
+
+def test_cluster_steps_and_bitwise_checkpoints():
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(602, levels=(3, 3), n_states=2, n_steps=45, T_ns=0.9, amp=0.1)
+    res = [_sys(p, ckpt_every=K, sweep=L.LB_SWEEP_CLUSTER).gradient() for K in (0, 1, 7, 100)]
+    for G, g in res[1:]:
+        assert G == res[0][0]
+        assert np.array_equal(g, res[0][1])
+    s = _sys(p, sweep=L.LB_SWEEP_CLUSTER)
+    mdl = model.Model(p.system, p.controls)
+    X = _rand_states(np.random.default_rng(3), 2, mdl.N)
+    got = s.propagate(torch.from_numpy(X).cuda(), 5, 9).cpu().numpy()
+    Q = model.vec(X).T.copy()
+    for j in range(5, 9):
+        Q, _ = imr.imr_step(mdl, j, Q)
+    assert _rel(got, np.stack([model.unvec(Q[:, i], mdl.N) for i in range(2)])) < 1e-13
+
+
+def test_autotune_keeps_results():
+    """The autotuner picks a converging candidate; the gradient after tuning
+    still matches the oracle."""
+    p = W.random_problem(701, levels=(2, 3), n_states=3, n_steps=40, T_ns=0.8, amp=0.1)
+    s = _sys(p)
+    choice = s.autotune(probe_steps=10)
+    assert choice["sweep"] in ("resident", "cluster", "grid")
+    assert choice["solver"] in ("jacobi", "neumann")
+    G, g = s.gradient()
+    Go, go, _ = imr.gradient(p)
+    assert abs(G - Go) <= 1e-10 * abs(Go)
+    assert _rel(g, go) < 1e-9

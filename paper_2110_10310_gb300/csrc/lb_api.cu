@@ -155,6 +155,21 @@ int n_carriers_total(const lb_system* s) {
   return n;
 }
 
+// CTAs per state of the cluster sweep if it can apply to this system (0: never)
+int cluster_ctas(const lb_system* s) {
+  if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT) return 0;
+  const lbk::ClusterConfig cc = lbk::cluster_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N);
+  return cc.C > 0 ? cc.C : 0;
+}
+
+// state slots of the gradient pieces: one (summed) for grid sweeps, one per
+// state and CTA for cluster sweeps, one per state otherwise
+size_t gproj_slots(const lb_system* s) {
+  if (use_grid(s)) return 1;
+  const int C = cluster_ctas(s);
+  return (size_t)s->M * (C > 1 ? C : 1);
+}
+
 Layout make_layout(const lb_system* s) {
   Layout L;
   size_t off = 0;
@@ -187,7 +202,7 @@ Layout make_layout(const lb_system* s) {
   take(L.ckpt, c2 * M * nck * V);
   take(L.seg, s->K > 0 ? c2 * M * (size_t)s->K * V : 0);
   const bool grid = use_grid(s);
-  take(L.gproj, c2 * (grid ? 1 : M) * NT * s->Q * 2);
+  take(L.gproj, c2 * gproj_slots(s) * NT * s->Q * 2);
   take(L.J, sizeof(double) * M);
   take(L.G, sizeof(double));
   take(L.grad, sizeof(double) * s->n_params);
@@ -343,7 +358,7 @@ void fill_prob(lb_system* s) {
   P.grad = at<double>(s, s->L.grad);
   P.status = at<DevStatus>(s, s->L.status);
   const bool grid = use_grid(s);
-  P.gM = grid ? 1 : s->M;
+  P.gM = grid ? 1 : (s->cluster ? s->M * s->cc.C : s->M);
   P.grid_blocks = grid ? s->gblocks : 0;
   if (grid) {
     P.zA = at<double2>(s, s->L.zA);
@@ -503,6 +518,7 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
     s->method = c.method;
     s->hp.method = c.method;
     s->cluster = c.sweep == LB_SWEEP_CLUSTER;
+    s->hp.gM = use_grid(s) ? 1 : (s->cluster ? s->M * s->cc.C : s->M);
     if (c.sweep == LB_SWEEP_RESIDENT) {
       s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true);
       const int threads = ((s->V + c.E - 1) / c.E + 31) / 32 * 32;
@@ -540,11 +556,13 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
     s->rc = rc0;
     s->cluster = cl0;
     s->method = s->hp.method = m0;
+    s->hp.gM = use_grid(s) ? 1 : (s->cluster ? s->M * s->cc.C : s->M);
     LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
     return fail(LB_ENOTCONV, "no candidate's inner solve converged on the probe steps");
   }
   s->method = s->hp.method = win.method;
   s->cluster = win.sweep == LB_SWEEP_CLUSTER;
+  s->hp.gM = use_grid(s) ? 1 : (s->cluster ? s->M * s->cc.C : s->M);
   if (win.sweep == LB_SWEEP_RESIDENT) {
     s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true);
     s->rc.E = win.E;

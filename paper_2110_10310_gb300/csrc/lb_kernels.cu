@@ -770,16 +770,62 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
 // of the commutator (P = sqrt(nk+1) x[k+s,l] - sqrt(nl) x[k,l-s] or
 // R = sqrt(nk) x[k-s,l] - sqrt(nl+1) x[k,l+s]) times its complex control
 // factor, the P half also the decay sandwich; every lane runs the same
-// instructions on its own data.  The L partial sums meet through shuffles;
-// the CTAs' elements are spread so that a CTA has at most 4 warps (one per SM
-// sub-partition).  Every CTA keeps a full replica of the iterate in shared
-// memory; new values go to all replicas through distributed shared memory and
-// the cluster barrier ends the inner iteration.
+// instructions on its own data.  The L partial sums meet through shuffles,
+// and a CTA holds at most 4 warps (one per SM sub-partition).
+//
+// Every CTA keeps a full replica of the iterate, of the right-hand side and
+// of the inverse diagonal in shared memory.  An inner iteration ends without
+// any cluster-wide barrier: each element's new value, and each warp's
+// largest change, are pushed into every CTA with st.async, whose completion
+// is counted in bytes on the receiving CTA's mbarrier (one per iteration
+// parity, so a CTA one iteration ahead never disturbs the current phase);
+// each CTA waits only for its own mbarrier, with a bounded wait.  All CTAs
+// see the same data and take the same decisions.  The right-hand side of the
+// next time step is formed locally from the replicas, so a time step needs
+// no exchange besides the inner iterations.
 
 template <int QT>
 struct ClLanes {
   static constexpr int L = 2 * QT <= 2 ? 2 : (2 * QT <= 4 ? 4 : 8);
 };
+
+constexpr long long kMbarSpinLimit = 1LL << 24;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned mapa_u32(unsigned a, unsigned rank) {
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_async_f64x2(unsigned addr, double x, double y, unsigned mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];" ::"r"(addr),
+               "d"(x), "d"(y), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void st_async_u32(unsigned addr, unsigned v, unsigned mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr), "r"(v),
+               "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init(unsigned mbar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned mbar, unsigned tx) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(tx) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned mbar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 
 struct ClSmem {
   Hdr* hdr;
@@ -788,12 +834,14 @@ struct ClSmem {
   double* jf;
   double* ja;
   uint32_t* dig;
-  double2* zb0;
-  double2* zb1;
-  unsigned* slots;  // [3 banks][32]: warp maxima, index cta * 4 + warp
-  double* gred;     // [8 units][4 warps][2]
-  double* cpart;    // [8 units][8 CTAs][2] (read in CTA 0)
-  double* opart;    // [8 CTAs] (read in CTA 0)
+  double2* zb;               // [2][V] replicated iterate, indexed by iteration parity
+  double2* rr;               // [V] right-hand side replica (forward state, recomputed state, or vectors)
+  double2* ll;               // [V] adjoint state replica (backward sweep)
+  double2* dv;               // [V] (I - dt/2 D)^-1, or dt/2 D for Neumann
+  unsigned* dsl;             // [2][32] warp maxima of |z_new - z| received, index cta * 4 + warp
+  unsigned* qsl;             // [32] this CTA's warp maxima of |rhs|
+  unsigned long long* mbar;  // [2]
+  double* gred;              // [8 units][4 warps][2]
 };
 
 __host__ __device__ inline size_t cl_smem_bytes(int ncoef, int njcoef, int N, int V) {
@@ -801,11 +849,11 @@ __host__ __device__ inline size_t cl_smem_bytes(int ncoef, int njcoef, int N, in
   b += align16(sizeof(double) * 2 * ncoef);
   b += align16(sizeof(double) * 2 * njcoef);
   b += align16(sizeof(uint32_t) * N);
-  b += sizeof(double2) * 2 * (size_t)V;
-  b += align16(sizeof(unsigned) * 96);
+  b += sizeof(double2) * 5 * (size_t)V;
+  b += align16(sizeof(unsigned) * 64);
+  b += align16(sizeof(unsigned) * 32);
+  b += align16(sizeof(unsigned long long) * 2);
   b += align16(sizeof(double) * 64);
-  b += align16(sizeof(double) * 128);
-  b += align16(sizeof(double) * 8);
   return b;
 }
 
@@ -822,21 +870,23 @@ __device__ ClSmem cl_carve(unsigned char* base, int ncoef, int njcoef, int N, in
   o += align16(sizeof(double) * 2 * njcoef);
   S.dig = reinterpret_cast<uint32_t*>(base + o);
   o += align16(sizeof(uint32_t) * N);
-  S.zb0 = reinterpret_cast<double2*>(base + o);
-  S.zb1 = S.zb0 + V;
-  o += sizeof(double2) * 2 * (size_t)V;
-  S.slots = reinterpret_cast<unsigned*>(base + o);
-  o += align16(sizeof(unsigned) * 96);
+  S.zb = reinterpret_cast<double2*>(base + o);
+  S.rr = S.zb + 2 * (size_t)V;
+  S.ll = S.rr + V;
+  S.dv = S.ll + V;
+  o += sizeof(double2) * 5 * (size_t)V;
+  S.dsl = reinterpret_cast<unsigned*>(base + o);
+  o += align16(sizeof(unsigned) * 64);
+  S.qsl = reinterpret_cast<unsigned*>(base + o);
+  o += align16(sizeof(unsigned) * 32);
+  S.mbar = reinterpret_cast<unsigned long long*>(base + o);
+  o += align16(sizeof(unsigned long long) * 2);
   S.gred = reinterpret_cast<double*>(base + o);
-  o += align16(sizeof(double) * 64);
-  S.cpart = reinterpret_cast<double*>(base + o);
-  o += align16(sizeof(double) * 128);
-  S.opart = reinterpret_cast<double*>(base + o);
   return S;
 }
 
-// Shared-memory set-up of one CTA; ends with a cluster barrier so that no
-// CTA writes into another's shared memory before that one is initialised.
+// Per-CTA set-up; ends with a cluster barrier, so no CTA pushes into another
+// before its shared memory and mbarriers are initialised.
 __device__ void cl_setup(const ClSmem& S, const ProbDev& P, cg::cluster_group& cl) {
   if (threadIdx.x == 0) load_hdr(*S.hdr, P);
   for (int i = threadIdx.x; i < P.ncoef; i += blockDim.x) {
@@ -848,25 +898,36 @@ __device__ void cl_setup(const ClSmem& S, const ProbDev& P, cg::cluster_group& c
     S.ja[i] = P.ja[i];
   }
   for (int i = threadIdx.x; i < P.N; i += blockDim.x) S.dig[i] = P.digits[i];
-  for (int i = threadIdx.x; i < 96; i += blockDim.x) S.slots[i] = 0u;
+  const bool neumann = P.method == LB_SOLVER_NEUMANN;
+  const double hh = 0.5 * P.h;
+  for (int i = threadIdx.x; i < P.V; i += blockDim.x) {
+    const double2 D = P.D[i];
+    S.dv[i] = neumann ? make_double2(hh * D.x, hh * D.y) : P.Dinv[i];
+  }
+  for (int i = threadIdx.x; i < 64; i += blockDim.x) S.dsl[i] = 0u;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&S.mbar[0]), 1);
+    mbar_init(smem_u32(&S.mbar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   __syncthreads();
   cl.sync();
 }
 
 // one lane's share of one element
 struct ClPlan {
-  int v;          // element (vec index) of this lane; 0 when none
-  bool ev;        // the lane belongs to a real element
-  int r;          // lane within the element, 0..L-1
-  int q;          // subsystem of this lane's half (0 for padding lanes)
-  bool rhalf;     // R half (else P half)
+  int v;        // element (vec index) of this lane; 0 when none
+  bool ev;      // the lane belongs to a real element
+  int r;        // lane within the element, 0..L-1
+  int q;        // subsystem of this lane's half (0 for padding lanes)
+  bool rhalf;   // R half (else P half)
   int oa, ob, ojf, oja;
   double ca, cb, cjf, cja;
-  double2 d;      // (I - dt/2 D)^-1 of the element (dt/2 D for Neumann)
+  double2 d;    // the element's entry of S.dv
 };
 
 template <int QT>
-__device__ ClPlan cl_plan(const ClSmem& S, const ProbDev& P, int C, int crank) {
+__device__ ClPlan cl_plan(const ClSmem& S, int C, int crank) {
   constexpr int L = ClLanes<QT>::L;
   const Hdr& H = *S.hdr;
   const int Vc = (H.V + C - 1) / C;
@@ -881,69 +942,75 @@ __device__ ClPlan cl_plan(const ClSmem& S, const ProbDev& P, int C, int crank) {
   pl.rhalf = u >= 0 && (u & 1);
   pl.oa = pl.ob = pl.ojf = pl.oja = pl.v;
   pl.ca = pl.cb = pl.cjf = pl.cja = 0.0;
-  pl.d = make_double2(0.0, 0.0);
-  if (pl.ev) {
-    const bool neumann = H.method == LB_SOLVER_NEUMANN;
-    const double hh = 0.5 * H.h;
-    if (neumann) {
-      const double2 D = P.D[v];
-      pl.d = make_double2(hh * D.x, hh * D.y);
-    } else {
-      pl.d = P.Dinv[v];
-    }
-    if (u >= 0) {
-      const uint32_t kd = S.dig[v % H.N], ld = S.dig[v / H.N];
-      const int q = pl.q, n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * H.N;
-      const int nk = (kd >> (4 * q)) & 15, nl = (ld >> (4 * q)) & 15;
-      if (!pl.rhalf) {
-        pl.oa = v + (nk + 1 < n ? s : 0);
-        pl.ob = v - (nl > 0 ? sN : 0);
-        pl.ca = S.cu[co + nk];
-        pl.cb = S.cd[co + nl];
-        if (H.jump[q] != 0.0) {
-          const int jo = H.joff[q] + nk * n + nl;
-          pl.cjf = S.jf[jo];
-          pl.cja = S.ja[jo];
-          pl.ojf = v + ((nk + 1 < n && nl + 1 < n) ? s + sN : 0);
-          pl.oja = v - ((nk > 0 && nl > 0) ? s + sN : 0);
-        }
-      } else {
-        pl.oa = v - (nk > 0 ? s : 0);
-        pl.ob = v + (nl + 1 < n ? sN : 0);
-        pl.ca = S.cd[co + nk];
-        pl.cb = S.cu[co + nl];
+  pl.d = pl.ev ? S.dv[v] : make_double2(0.0, 0.0);
+  if (pl.ev && u >= 0) {
+    const uint32_t kd = S.dig[v % H.N], ld = S.dig[v / H.N];
+    const int q = pl.q, n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * H.N;
+    const int nk = (kd >> (4 * q)) & 15, nl = (ld >> (4 * q)) & 15;
+    if (!pl.rhalf) {
+      pl.oa = v + (nk + 1 < n ? s : 0);
+      pl.ob = v - (nl > 0 ? sN : 0);
+      pl.ca = S.cu[co + nk];
+      pl.cb = S.cd[co + nl];
+      if (H.jump[q] != 0.0) {
+        const int jo = H.joff[q] + nk * n + nl;
+        pl.cjf = S.jf[jo];
+        pl.cja = S.ja[jo];
+        pl.ojf = v + ((nk + 1 < n && nl + 1 < n) ? s + sN : 0);
+        pl.oja = v - ((nk > 0 && nl > 0) ? s + sN : 0);
       }
+    } else {
+      pl.oa = v - (nk > 0 ? s : 0);
+      pl.ob = v + (nl + 1 < n ? sN : 0);
+      pl.ca = S.cd[co + nk];
+      pl.cb = S.cu[co + nl];
     }
   }
   return pl;
 }
 
-// Write z into element v of buffer `buf` of every CTA of the cluster; the L
-// lanes of the element share the C stores.
-template <int L>
-__device__ __forceinline__ void cl_broadcast(cg::cluster_group& cl, double2* buf, const ClPlan& pl, double2 z, int C) {
-  if (pl.ev)
-    for (int c = pl.r; c < C; c += L) cl.map_shared_rank(buf, c)[pl.v] = z;
-}
+// iteration and mbarrier phase counters; identical in every thread of the cluster
+struct ClCount {
+  unsigned gk = 0;                // inner iterations so far (selects buffer and mbarrier parity)
+  unsigned ph[2] = {0u, 0u};      // completed phases of mbar[0], mbar[1] (mod 2)
+};
 
-// Push this warp's value into slot `idx` of every CTA (lanes 0..C-1 store).
-__device__ __forceinline__ void cl_push_slot(cg::cluster_group& cl, unsigned* slots, int idx, unsigned val, int C) {
-  const int lane = threadIdx.x & 31;
-  if (lane < C) cl.map_shared_rank(slots, lane)[idx] = val;
-}
-
-// Solve (I - dt/2 M) z = rhs (ADJ: M^+) for the cluster's state; returns the
-// iteration count, -1 (max_iter) or -2 (NaN/Inf); zbuf[cur] then holds z in
-// every CTA, and `z` the element's value in every lane of it.
+// Solve (I - dt/2 M) z = rhs (ADJ: M^+) for the cluster's state, rhs given by
+// the replica `rr`.  Returns the iteration count, -1 (max_iter), -2 (NaN/Inf)
+// or -3 (a wait gave up).  On success S.zb + (gk & 1) * V holds z in every
+// CTA, and zout the lane's element of it.
 template <int QT, bool ADJ>
-__device__ int cl_solve(cg::cluster_group& cl, const ClSmem& S, const ClPlan& pl, double2 rhs,
-                        const double2* __restrict__ ct, int C, int crank, int& cur, double2& zout) {
+__device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __restrict__ rr,
+                        const double2* __restrict__ ct, int C, int crank, ClCount& cnt, double2& zout) {
   constexpr int L = ClLanes<QT>::L;
   const Hdr& H = *S.hdr;
-  const int warp = threadIdx.x >> 5;
+  const int V = H.V;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const bool neumann = H.method == LB_SOLVER_NEUMANN;
-  const int nslots = C * 4;
-  // complex factor of this lane's half: -i d P -> (b - i a) P, -i conj(d) R -> (-b - i a) R
+  // z_0 for all elements of the local replica, and max |rhs|
+  {
+    double2* z0b = S.zb + (size_t)(cnt.gk & 1) * V;
+    unsigned qm = 0;
+    for (int e = threadIdx.x; e < V; e += blockDim.x) {
+      const double2 r = rr[e];
+      double2 z0 = r;
+      if (!neumann) {
+        const double2 d = S.dv[e];
+        const double di = ADJ ? -d.y : d.y;
+        z0 = make_double2(fma(d.x, r.x, -di * r.y), fma(d.x, r.y, di * r.x));
+      }
+      z0b[e] = z0;
+      qm = max(qm, max(hi_abs(r.x), hi_abs(r.y)));
+    }
+    qm = __reduce_max_sync(kFull, qm);
+    if (lane == 0) S.qsl[warp] = qm;
+  }
+  __syncthreads();
+  unsigned qmax = 0;
+  for (int w = 0; w < nwarps; ++w) qmax = max(qmax, S.qsl[w]);
+  if (qmax >= kInfHi) return -2;
+  const unsigned thr = hi_abs(H.rtol * __longlong_as_double(static_cast<long long>((unsigned long long)qmax << 32)));
+  // this lane's complex factor: -i d P -> (b - i a) P, -i conj(d) R -> (-b - i a) R
   const double2 c = ct[pl.q];
   double Ar = pl.rhalf ? -c.y : c.y, Ai = -c.x;
   if (ADJ) {
@@ -951,29 +1018,20 @@ __device__ int cl_solve(cg::cluster_group& cl, const ClSmem& S, const ClPlan& pl
     Ai = -Ai;
   }
   const double di = ADJ ? -pl.d.y : pl.d.y;
-  double2 z0 = rhs;
-  if (!neumann) z0 = make_double2(fma(pl.d.x, rhs.x, -di * rhs.y), fma(pl.d.x, rhs.y, di * rhs.x));
-  cl_broadcast<L>(cl, S.zb0, pl, z0, C);
-  unsigned qm = (pl.ev && pl.r == 0) ? max(hi_abs(rhs.x), hi_abs(rhs.y)) : 0u;
-  qm = __reduce_max_sync(kFull, qm);
-  cl_push_slot(cl, S.slots, 64 + crank * 4 + warp, qm, C);
-  cl.sync();
-  unsigned qmax = 0;
-  for (int k = 0; k < nslots; ++k) qmax = max(qmax, S.slots[64 + k]);
-  if (qmax >= kInfHi) return -2;
-  const unsigned thr = hi_abs(H.rtol * __longlong_as_double(static_cast<long long>((unsigned long long)qmax << 32)));
-  cur = 0;
-  double2 zc_own = z0;
+  const double2 rhs = rr[pl.v];
+  const double cj = ADJ ? pl.cja : pl.cjf;
+  const int oj = ADJ ? pl.oja : pl.ojf;
+  const unsigned tx = (unsigned)V * 16u + (unsigned)(C * nwarps) * 4u;
   for (int it = 0; it < H.max_iter; ++it) {
-    const double2* __restrict__ zc = cur ? S.zb1 : S.zb0;
-    double2* zn = cur ? S.zb0 : S.zb1;
-    const double2 xa = zc[pl.oa], xb = zc[pl.ob];
+    const unsigned p = (cnt.gk + 1) & 1;
+    const unsigned mb_local = smem_u32(&S.mbar[p]);
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(mb_local, tx);
+    const double2* __restrict__ zc = S.zb + (size_t)(cnt.gk & 1) * V;
+    const double2 xa = zc[pl.oa], xb = zc[pl.ob], x5 = zc[oj], zo = zc[pl.v];
     const double xr = fma(-pl.cb, xb.x, pl.ca * xa.x);
     const double xi = fma(-pl.cb, xb.y, pl.ca * xa.y);
     double accr = fma(Ar, xr, -Ai * xi);
     double acci = fma(Ar, xi, Ai * xr);
-    const double cj = ADJ ? pl.cja : pl.cjf;
-    const double2 x5 = zc[ADJ ? pl.oja : pl.ojf];
     accr = fma(cj, x5.x, accr);
     acci = fma(cj, x5.y, acci);
 #pragma unroll
@@ -987,18 +1045,39 @@ __device__ int cl_solve(cg::cluster_group& cl, const ClSmem& S, const ClPlan& pl
       z.x = fma(pl.d.x, ar, -di * ai);
       z.y = fma(pl.d.x, ai, di * ar);
     } else {
-      z.x = ar + fma(pl.d.x, zc_own.x, -di * zc_own.y);
-      z.y = ai + fma(pl.d.x, zc_own.y, di * zc_own.x);
+      z.x = ar + fma(pl.d.x, zo.x, -di * zo.y);
+      z.y = ai + fma(pl.d.x, zo.y, di * zo.x);
     }
-    cl_broadcast<L>(cl, zn, pl, z, C);
-    unsigned dm = (pl.ev && pl.r == 0) ? max(hi_abs(z.x - zc_own.x), hi_abs(z.y - zc_own.y)) : 0u;
+    // push the element into every CTA's next buffer; the element's lanes share the C stores
+    if (pl.ev) {
+      const unsigned dst = smem_u32(S.zb + (size_t)p * V + pl.v);
+      for (int cc = pl.r; cc < C; cc += L) st_async_f64x2(mapa_u32(dst, cc), z.x, z.y, mapa_u32(mb_local, cc));
+    }
+    unsigned dm = (pl.ev && pl.r == 0) ? max(hi_abs(z.x - zo.x), hi_abs(z.y - zo.y)) : 0u;
     dm = __reduce_max_sync(kFull, dm);
-    cl_push_slot(cl, S.slots, (it & 1) * 32 + crank * 4 + warp, dm, C);
-    cl.sync();
+    if (lane < C) {
+      const unsigned dst = smem_u32(S.dsl + p * 32 + crank * 4 + warp);
+      st_async_u32(mapa_u32(dst, lane), dm, mapa_u32(mb_local, lane));
+    }
+    // wait for every CTA's pushes of this iteration (bounded); the vote keeps a
+    // timeout, should one ever happen, a decision of the whole CTA
+    long long spins = 0;
+    int timed_out = 0;
+    while (!mbar_try_wait(mb_local, cnt.ph[p])) {
+      if (++spins > kMbarSpinLimit) {
+        timed_out = 1;
+        break;
+      }
+    }
+    if (__syncthreads_or(timed_out)) return -3;
+    cnt.ph[p] ^= 1u;
+    ++cnt.gk;
     unsigned dmax = 0;
-    for (int k = 0; k < nslots; ++k) dmax = max(dmax, S.slots[(it & 1) * 32 + k]);
-    cur ^= 1;
-    zc_own = z;
+    const uint4* d4 = reinterpret_cast<const uint4*>(S.dsl + p * 32);
+    for (int k = 0; k < C; ++k) {
+      const uint4 t = d4[k];
+      dmax = max(dmax, max(max(t.x, t.y), max(t.z, t.w)));
+    }
     if (dmax >= kInfHi) return -2;
     if (dmax < thr) {
       zout = z;
@@ -1008,76 +1087,67 @@ __device__ int cl_solve(cg::cluster_group& cl, const ClSmem& S, const ClPlan& pl
   return -1;
 }
 
-// Sum of one double per lane over the cluster's elements (lanes r == 0 of
-// real elements contribute), in a fixed order; the result is returned in
-// CTA 0 thread 0.  Two CTA barriers and one cluster barrier.
-template <int L>
-__device__ double cl_sum(cg::cluster_group& cl, const ClSmem& S, double x, int crank) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  x = warp_sum(x);
-  if (lane == 0) S.gred[warp] = x;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < nwarps; ++w) t += S.gred[w];
-    cl.map_shared_rank(S.opart, 0)[crank] = t;
-  }
-  __syncthreads();
-  cl.sync();
-  double tot = 0.0;
-  if (crank == 0 && threadIdx.x == 0)
-    for (int c = 0; c < (int)cl.num_blocks(); ++c) tot += S.opart[c];
-  return tot;
-}
+__device__ __forceinline__ int cl_code(int it) { return it == -1 ? LB_ENOTCONV : (it == -2 ? LB_ENAN : LB_ECUDA); }
 
 template <int QT>
 __global__ void __launch_bounds__(128) k_forward_cl(const ProbDev* __restrict__ pp, int tape) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
-  constexpr int L = ClLanes<QT>::L;
   const ProbDev& P = *pp;
   const int C = (int)cl.num_blocks(), crank = (int)cl.block_rank();
   const int i = blockIdx.x / C;
   const ClSmem S = cl_carve(smem, P.ncoef, P.njcoef, P.N, P.V);
   cl_setup(S, P, cl);
   const Hdr& H = *S.hdr;
-  const ClPlan pl = cl_plan<QT>(S, P, C, crank);
+  const ClPlan pl = cl_plan<QT>(S, C, crank);
   const size_t base = (size_t)i * H.V;
-  double2 q = pl.ev ? P.q0[base + pl.v] : make_double2(0.0, 0.0);
-  const bool writer = pl.ev && pl.r == 0;
+  for (int e = threadIdx.x; e < H.V; e += blockDim.x) S.rr[e] = P.q0[base + e];
+  ClCount cnt;
   CtaStats stats;
   bool failed = false;
   for (int j = 0; j < H.NT; ++j) {
-    if (tape && H.K > 0 && j % H.K == 0 && writer) P.ckpt[((size_t)i * H.n_ckpt + j / H.K) * H.V + pl.v] = q;
-    int cur;
+    if (tape && H.K > 0 && j % H.K == 0 && crank == 0)
+      for (int e = threadIdx.x; e < H.V; e += blockDim.x) P.ckpt[((size_t)i * H.n_ckpt + j / H.K) * H.V + e] = S.rr[e];
     double2 z;
-    const int it = cl_solve<QT, false>(cl, S, pl, q, P.ctab + (size_t)j * H.Q, C, crank, cur, z);
+    const int it = cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, C, crank, cnt, z);
     if (it < 0) {
-      if (threadIdx.x == 0 && crank == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
+      if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
       failed = true;
       break;
     }
     if (crank == 0) stats.add(0, it);
-    if (tape && H.K == 0 && writer) P.ckpt[((size_t)i * H.NT + j) * H.V + pl.v] = z;
-    q = make_double2(fma(2.0, z.x, -q.x), fma(2.0, z.y, -q.y));
+    // q^{j+1} = 2 z - q^j on the whole replica (identical in every CTA)
+    const double2* zf = S.zb + (size_t)(cnt.gk & 1) * H.V;
+    for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
+      const double2 zz = zf[e], qq = S.rr[e];
+      if (tape && H.K == 0 && crank == 0) P.ckpt[((size_t)i * H.NT + j) * H.V + e] = zz;
+      S.rr[e] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
+    }
   }
-  if (!failed) {
+  if (!failed && crank == 0) {
     double acc = 0.0;
-    if (writer) {
-      P.qT[base + pl.v] = q;
-      const double2 t = P.tar[base + pl.v];
+    for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
+      const double2 q = S.rr[e];
+      P.qT[base + e] = q;
+      const double2 t = P.tar[base + e];
       if (H.kind == LB_J_FROB) {
         const double dr = q.x - t.x, dq = q.y - t.y;
-        acc = fma(dr, dr, dq * dq);
+        acc = fma(dr, dr, fma(dq, dq, acc));
       } else {
-        acc = fma(t.x, q.x, t.y * q.y);
+        acc = fma(t.x, q.x, fma(t.y, q.y, acc));
       }
     }
-    const double tot = cl_sum<L>(cl, S, acc, crank);
-    if (crank == 0 && threadIdx.x == 0) P.J[i] = H.kind == LB_J_FROB ? 0.5 * tot : 1.0 - tot;
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) S.gred[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += S.gred[w];
+      P.J[i] = H.kind == LB_J_FROB ? 0.5 * t : 1.0 - t;
+    }
   }
   stats.flush(P.status);
-  cl.sync();  // no CTA leaves while another may still write into its shared memory
+  cl.sync();  // no CTA leaves while another may still push into it
 }
 
 template <int QT>
@@ -1091,58 +1161,62 @@ __global__ void __launch_bounds__(128) k_backward_cl(const ProbDev* __restrict__
   const ClSmem S = cl_carve(smem, P.ncoef, P.njcoef, P.N, P.V);
   cl_setup(S, P, cl);
   const Hdr& H = *S.hdr;
-  const ClPlan pl = cl_plan<QT>(S, P, C, crank);
+  const ClPlan pl = cl_plan<QT>(S, C, crank);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const size_t base = (size_t)i * H.V;
-  const bool writer = pl.ev && pl.r == 0;
   const double w = P.wgt[i];
-  double2 lam = make_double2(0.0, 0.0), qf = lam;
-  if (pl.ev) {
-    const double2 t = P.tar[base + pl.v];
+  // terminal condition qhat^{N_T} = beta_i/M g_i (Appendix B), replicated
+  for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
+    const double2 t = P.tar[base + e];
     if (H.kind == LB_J_FROB) {
-      const double2 qq = P.qT[base + pl.v];
-      lam = make_double2(w * (qq.x - t.x), w * (qq.y - t.y));
+      const double2 qq = P.qT[base + e];
+      S.ll[e] = make_double2(w * (qq.x - t.x), w * (qq.y - t.y));
     } else {
-      lam = make_double2(-w * t.x, -w * t.y);
+      S.ll[e] = make_double2(-w * t.x, -w * t.y);
     }
   }
+  ClCount cnt;
   CtaStats stats;
   bool failed = false;
   const int nseg = H.K > 0 ? (H.NT + H.K - 1) / H.K : 1;
+  // gradient pieces of this CTA go to state slot i * C + crank of gproj
+  double2* gbase = P.gproj + (size_t)(i * C + crank) * H.NT * H.Q * 2;
   for (int sg = nseg - 1; sg >= 0 && !failed; --sg) {
     const int j0 = H.K > 0 ? sg * H.K : 0;
     const int j1 = H.K > 0 ? min(H.NT, j0 + H.K) : H.NT;
     if (H.K > 0) {
-      qf = pl.ev ? P.ckpt[((size_t)i * H.n_ckpt + sg) * H.V + pl.v] : make_double2(0.0, 0.0);
+      for (int e = threadIdx.x; e < H.V; e += blockDim.x) S.rr[e] = P.ckpt[((size_t)i * H.n_ckpt + sg) * H.V + e];
       for (int j = j0; j < j1; ++j) {
-        int cur;
         double2 z;
-        const int it = cl_solve<QT, false>(cl, S, pl, qf, P.ctab + (size_t)j * H.Q, C, crank, cur, z);
+        const int it = cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, C, crank, cnt, z);
         if (it < 0) {
-          if (threadIdx.x == 0 && crank == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
+          if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
           failed = true;
           break;
         }
         if (crank == 0) stats.add(1, it);
-        if (writer) P.seg[((size_t)i * H.K + (j - j0)) * H.V + pl.v] = z;
-        qf = make_double2(fma(2.0, z.x, -qf.x), fma(2.0, z.y, -qf.y));
+        const double2* zf = S.zb + (size_t)(cnt.gk & 1) * H.V;
+        for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
+          const double2 zz = zf[e], qq = S.rr[e];
+          if (crank == 0) P.seg[((size_t)i * H.K + (j - j0)) * H.V + e] = zz;
+          S.rr[e] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
+        }
       }
       if (failed) break;
+      __syncthreads();  // segment tape written by this CTA before it is read back below
     }
     for (int j = j1 - 1; j >= j0; --j) {
-      const double2* ct = P.ctab + (size_t)j * H.Q;
-      int cur;
       double2 zh;
-      const int it = cl_solve<QT, true>(cl, S, pl, lam, ct, C, crank, cur, zh);
+      const int it = cl_solve<QT, true>(S, pl, S.ll, P.ctab + (size_t)j * H.Q, C, crank, cnt, zh);
       if (it < 0) {
-        if (threadIdx.x == 0 && crank == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
+        if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
         failed = true;
         break;
       }
       if (crank == 0) stats.add(2, it);
-      // gradient piece of this lane's half (eq. reducedgradient): sum_kl Z conj(X_zhat)
-      // with X the half's neighbour combination of zhat; P half -> g_ad, R half -> g_a
-      const double2* zb = cur ? S.zb1 : S.zb0;
+      const double2* zb = S.zb + (size_t)(cnt.gk & 1) * H.V;
+      // gradient piece of this lane's half (eq. reducedgradient): sum_kl Z conj(X_zhat),
+      // X the half's neighbour combination of zhat; P half -> g_ad, R half -> g_a
       double sr = 0.0, si = 0.0;
       if (pl.ev && pl.r < 2 * QT) {
         const double2 Z = H.K > 0 ? P.seg[((size_t)i * H.K + (j - j0)) * H.V + pl.v]
@@ -1163,29 +1237,21 @@ __global__ void __launch_bounds__(128) k_backward_cl(const ProbDev* __restrict__
         S.gred[(lane * 4 + warp) * 2 + 1] = si;
       }
       __syncthreads();
-      if (threadIdx.x < L) {
+      if (threadIdx.x < 2 * QT) {
         double tr = 0.0, ti = 0.0;
         for (int ww = 0; ww < nwarps; ++ww) {
           tr += S.gred[(threadIdx.x * 4 + ww) * 2];
           ti += S.gred[(threadIdx.x * 4 + ww) * 2 + 1];
         }
-        double* dst = cl.map_shared_rank(S.cpart, 0);
-        dst[(threadIdx.x * 8 + crank) * 2] = tr;
-        dst[(threadIdx.x * 8 + crank) * 2 + 1] = ti;
-      }
-      cl.sync();
-      if (crank == 0 && threadIdx.x < 2 * QT) {
-        double tr = 0.0, ti = 0.0;
-        for (int c = 0; c < C; ++c) {
-          tr += S.cpart[(threadIdx.x * 8 + c) * 2];
-          ti += S.cpart[(threadIdx.x * 8 + c) * 2 + 1];
-        }
         const int q = threadIdx.x >> 1;
         // multiply by -i: (si, -sr); R half is g_a (slot 0), P half is g_ad (slot 1)
-        double2* g = P.gproj + (((size_t)i * H.NT + j) * H.Q + q) * 2;
-        g[(threadIdx.x & 1) ? 0 : 1] = make_double2(ti, -tr);
+        gbase[((size_t)j * H.Q + q) * 2 + ((threadIdx.x & 1) ? 0 : 1)] = make_double2(ti, -tr);
       }
-      lam = make_double2(fma(2.0, zh.x, -lam.x), fma(2.0, zh.y, -lam.y));
+      // qhat^j = 2 zhat - qhat^{j+1} on the whole replica
+      for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
+        const double2 zz = zb[e], ll = S.ll[e];
+        S.ll[e] = make_double2(fma(2.0, zz.x, -ll.x), fma(2.0, zz.y, -ll.y));
+      }
     }
   }
   stats.flush(P.status);
@@ -1203,24 +1269,31 @@ __global__ void __launch_bounds__(128) k_propagate_cl(const ProbDev* __restrict_
   const ClSmem S = cl_carve(smem, P.ncoef, P.njcoef, P.N, P.V);
   cl_setup(S, P, cl);
   const Hdr& H = *S.hdr;
-  const ClPlan pl = cl_plan<QT>(S, P, C, crank);
+  const ClPlan pl = cl_plan<QT>(S, C, crank);
   double2* xv = x + (size_t)i * H.V;
-  double2 q = pl.ev ? xv[pl.v] : make_double2(0.0, 0.0);
+  for (int e = threadIdx.x; e < H.V; e += blockDim.x) S.rr[e] = xv[e];
+  ClCount cnt;
   CtaStats stats;
+  bool failed = false;
   for (int jj = 0; jj < j1 - j0; ++jj) {
     const int j = adjoint ? j1 - 1 - jj : j0 + jj;
-    int cur;
     double2 z;
-    const int it = adjoint ? cl_solve<QT, true>(cl, S, pl, q, P.ctab + (size_t)j * H.Q, C, crank, cur, z)
-                           : cl_solve<QT, false>(cl, S, pl, q, P.ctab + (size_t)j * H.Q, C, crank, cur, z);
+    const int it = adjoint ? cl_solve<QT, true>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, C, crank, cnt, z)
+                           : cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, C, crank, cnt, z);
     if (it < 0) {
-      if (threadIdx.x == 0 && crank == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
+      if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
+      failed = true;
       break;
     }
     if (crank == 0) stats.add(adjoint ? 2 : 0, it);
-    q = make_double2(fma(2.0, z.x, -q.x), fma(2.0, z.y, -q.y));
+    const double2* zf = S.zb + (size_t)(cnt.gk & 1) * H.V;
+    for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
+      const double2 zz = zf[e], qq = S.rr[e];
+      S.rr[e] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
+    }
   }
-  if (pl.ev && pl.r == 0) xv[pl.v] = q;
+  if (!failed && crank == 0)
+    for (int e = threadIdx.x; e < H.V; e += blockDim.x) xv[e] = S.rr[e];
   stats.flush(P.status);
   cl.sync();
 }

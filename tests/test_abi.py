@@ -149,7 +149,8 @@ def test_workspace_size_accounts_for_checkpoints(lib, K):
         else:
             Kc = min(K, NT)
             tape = -(-NT // Kc) * state + Kc * state
-        gproj = M * NT * 2 * 2 * 16
+        C = -(-Vl * 4 // 128)  # CTAs per state of the cluster sweep (2Q = 4 lanes per element)
+        gproj = M * C * NT * 2 * 2 * 16
         assert n.value >= tape + gproj + 3 * state
         assert n.value <= tape + gproj + 3 * state + 64 * 1024
     finally:

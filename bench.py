@@ -31,7 +31,7 @@ METRIC = "Lindblad state-steps/s (fwd+adjoint, FP64)"
 UNIT = "state-steps/s"
 WORKLOAD = ("cnot_2x3: 2 transmons x 3 levels (N=9, vec 81), 16 essential-basis states |i><j|, "
             "10000 IMR steps, T=200 ns, 2x20 splines x 2 carriers, J_Frob to CNOT, "
-            "forward + adjoint gradient with checkpoints every 100 steps")
+            "forward + adjoint gradient (stage vectors kept when the tape fits 8 GiB, else checkpoints)")
 # other workloads (--workload), measured the same way; the default line is cnot_2x3
 WORKLOADS = {
     "cnot_2x3": WORKLOAD,
@@ -475,7 +475,9 @@ def main():
                 "workload": WORKLOADS[args.workload].format(n=p.system.n_steps),
                 "states": p.M,
                 "n_steps": p.system.n_steps,
-                "ckpt_every": p.ckpt_every,
+                "ckpt_every": st["ckpt_every"],
+                "tape_bytes": (p.M * p.system.n_steps * V * 16 if st["ckpt_every"] == 0
+                               else p.M * (-(-p.system.n_steps // st["ckpt_every"]) + st["ckpt_every"]) * V * 16),
                 "solver": f"{st['solver']} fixed point, rtol 1e-15",
                 "sweep": st["sweep"],
                 "l2": "flushed between timed steps (256 MiB write)",

@@ -122,6 +122,8 @@ typedef struct lb_stats {
   float ms_backward;        /* device time of the backward-sweep kernel (recompute + adjoint) */
   int32_t sweep;            /* LB_SWEEP_* kind the call ran with */
   int32_t solver;           /* LB_SOLVER_* it ran with */
+  int32_t ckpt_every;       /* checkpoint interval in effect (0 = every stage vector kept) */
+  int32_t pad;
 } lb_stats;
 
 /* ---- system ------------------------------------------------------------- */
@@ -163,8 +165,11 @@ int lb_objective_set_gate(lb_system* sys, int32_t kind, const double* V, double 
  * max|z_new - z| <= rtol * max|q| (componentwise, per state); max_iter caps the
  * iterations of one step (LB_ENOTCONV beyond); ckpt_every = K >= 1 stores the
  * forward state every K steps and recomputes each K-step segment in the
- * backward sweep; K = 0 stores every stage vector z^j instead (no recompute).
+ * backward sweep; K = 0 stores every stage vector z^j instead (no recompute);
+ * K = LB_CKPT_AUTO keeps every stage vector when that tape takes at most
+ * 8 GiB (M * N_T * N^2 * 16 bytes) and checkpoints every 100 steps otherwise.
  * Defaults: LB_SOLVER_AUTO, 1e-15, 200, 100.  Call before lb_workspace_bytes. */
+#define LB_CKPT_AUTO (-1)
 int lb_solver_set(lb_system* sys, int32_t method, double rtol, int32_t max_iter, int32_t ckpt_every);
 
 /* Choose the sweep kind (LB_SWEEP_*); call before lb_workspace_bytes. */

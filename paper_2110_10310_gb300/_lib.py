@@ -25,6 +25,8 @@ LB_ENAN = 5
 LB_J_FROB = 0
 LB_J_TR = 1
 
+LB_CKPT_AUTO = -1
+
 LB_SWEEP_AUTO = 0
 LB_SWEEP_RESIDENT = 1
 LB_SWEEP_GRID = 2
@@ -74,6 +76,8 @@ class lb_stats(ctypes.Structure):
         ("ms_backward", ctypes.c_float),
         ("sweep", c_int32),
         ("solver", c_int32),
+        ("ckpt_every", c_int32),
+        ("pad", c_int32),
     ]
 
 

@@ -82,7 +82,7 @@ struct lb_system {
   int method = LB_SOLVER_JACOBI;
   double rtol = 1e-15;
   int max_iter = 200;
-  int K = 100;
+  int K = 100;       // requested checkpoint interval; < 0 = automatic (effective_K)
   int sweep = LB_SWEEP_AUTO;
   int gblocks = 0;   // cooperative grid size (grid sweeps)
   size_t gsmem = 0;  // its dynamic shared memory
@@ -155,6 +155,17 @@ int n_carriers_total(const lb_system* s) {
   return n;
 }
 
+// Checkpoint interval actually used: the requested one, or for an automatic
+// request the full stage tape (0) when it takes at most kTapeBudget bytes,
+// else checkpoints every 100 steps.
+constexpr size_t kTapeBudget = size_t(8) << 30;
+int effective_K(const lb_system* s) {
+  if (s->K >= 0) return s->K;
+  const size_t tape = sizeof(double2) * (size_t)s->M * (size_t)s->NT * (size_t)s->V;
+  if (tape <= kTapeBudget) return 0;
+  return s->NT < 100 ? (int)s->NT : 100;
+}
+
 // CTAs per state of the cluster sweep if it can apply to this system (0: never)
 int cluster_ctas(const lb_system* s) {
   if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT) return 0;
@@ -198,9 +209,10 @@ Layout make_layout(const lb_system* s) {
   take(L.tar, c2 * M * V);
   take(L.wgt, sizeof(double) * M);
   take(L.qT, c2 * M * V);
-  const size_t nck = s->K > 0 ? (NT + s->K - 1) / s->K : NT;
+  const int K = effective_K(s);
+  const size_t nck = K > 0 ? (NT + K - 1) / K : NT;
   take(L.ckpt, c2 * M * nck * V);
-  take(L.seg, s->K > 0 ? c2 * M * (size_t)s->K * V : 0);
+  take(L.seg, K > 0 ? c2 * M * (size_t)K * V : 0);
   const bool grid = use_grid(s);
   take(L.gproj, c2 * gproj_slots(s) * NT * s->Q * 2);
   take(L.J, sizeof(double) * M);
@@ -304,8 +316,8 @@ void fill_prob(lb_system* s) {
   P.M = s->M;
   P.NT = (int32_t)s->NT;
   P.V = s->V;
-  P.K = s->K;
-  P.n_ckpt = s->K > 0 ? (int32_t)((s->NT + s->K - 1) / s->K) : (int32_t)s->NT;
+  P.K = effective_K(s);
+  P.n_ckpt = P.K > 0 ? (int32_t)((s->NT + P.K - 1) / P.K) : (int32_t)s->NT;
   P.max_iter = s->max_iter;
   P.method = s->method;
   P.kind = s->kind;
@@ -690,11 +702,12 @@ int lb_solver_set(lb_system* s, int32_t method, double rtol, int32_t max_iter, i
   if (method != LB_SOLVER_JACOBI && method != LB_SOLVER_NEUMANN) return fail(LB_EINVAL, "unknown solver");
   if (!(rtol > 0.0) || !(rtol < 1.0)) return fail(LB_EINVAL, "rtol must be in (0, 1)");
   if (max_iter < 1 || max_iter > 100000) return fail(LB_EINVAL, "max_iter must be in 1..100000");
-  if (ckpt_every < 0) return fail(LB_EINVAL, "ckpt_every must be >= 0");
+  if (ckpt_every < LB_CKPT_AUTO) return fail(LB_EINVAL, "ckpt_every must be >= 0 or LB_CKPT_AUTO");
   s->method = method;
   s->rtol = rtol;
   s->max_iter = max_iter;
   s->K = ckpt_every > s->NT ? (int)s->NT : ckpt_every;
+  if (ckpt_every < 0) s->K = LB_CKPT_AUTO;
   return LB_OK;
 }
 
@@ -849,6 +862,7 @@ static int finish(lb_system* s, cudaStream_t st, double* G_out, double* grad_out
   int rc = read_status(d, &s->last, s->launches);
   s->last.sweep = use_grid(s) ? LB_SWEEP_GRID : (s->cluster ? LB_SWEEP_CLUSTER : LB_SWEEP_RESIDENT);
   s->last.solver = s->method;
+  s->last.ckpt_every = effective_K(s);
   if (s->timed_fwd) LB_CUDA(cudaEventElapsedTime(&s->last.ms_forward, s->ev[0], s->ev[1]), "cudaEventElapsedTime");
   if (s->timed_bwd) LB_CUDA(cudaEventElapsedTime(&s->last.ms_backward, s->ev[2], s->ev[3]), "cudaEventElapsedTime");
   if (rc) return rc;

@@ -367,7 +367,8 @@ constexpr unsigned kInfHi = 0x7ff00000u;
 // QT > 0 (with E == 1) uses the per-thread plan.
 template <int E, int QT, bool ADJ>
 __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, const Plan<QT>& pl,
-                         const double2 (&rhs)[E], const double2* __restrict__ ct, int& cur) {
+                         const double2 (&rhs)[E], const double2* __restrict__ ct, int& cur,
+                         const double2* pc = nullptr) {
   static_assert(QT == 0 || E == 1, "the per-thread plan holds one element");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const bool neumann = H.method == LB_SOLVER_NEUMANN;
@@ -392,7 +393,8 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
       if (!neumann) {
         const double2 d = QT > 0 ? pl.d : S.dsm[v];
         const double di = ADJ ? -d.y : d.y;
-        z0 = make_double2(fma(d.x, rhs[e].x, -di * rhs[e].y), fma(d.x, rhs[e].y, di * rhs[e].x));
+        const double ur = pc ? rhs[e].x + pc[e].x : rhs[e].x, ui = pc ? rhs[e].y + pc[e].y : rhs[e].y;
+        z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
       }
       S.zb0[v] = z0;
       qmax = max(qmax, max(hi_abs(rhs[e].x), hi_abs(rhs[e].y)));
@@ -449,6 +451,51 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
   }
   return -1;
 }
+
+// Predictor of the first iterate: off-diagonal corrections c = (I - dt/2 D) z
+// - rhs of the two previous steps, per owned element, extrapolated linearly.
+template <int E>
+struct Pred {
+  double2 c1[E], c2[E], hd[E];
+  int nh = 0;
+  __device__ void init(const ProbDev& P, int V) {
+    const double hh = 0.5 * P.h;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int v = threadIdx.x + e * blockDim.x;
+      const double2 D = v < V ? P.D[v] : make_double2(0.0, 0.0);
+      hd[e] = make_double2(hh * D.x, hh * D.y);
+      c1[e] = c2[e] = make_double2(0.0, 0.0);
+    }
+    nh = 0;
+  }
+  __device__ void predict(double2 (&pc)[E]) const {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      if (nh <= 0)
+        pc[e] = make_double2(0.0, 0.0);
+      else if (nh == 1)
+        pc[e] = c1[e];
+      else
+        pc[e] = make_double2(fma(2.0, c1[e].x, -c2[e].x), fma(2.0, c1[e].y, -c2[e].y));
+    }
+  }
+  template <bool ADJ>
+  __device__ void record(const double2* zc, const double2 (&rhs)[E], int V) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int v = threadIdx.x + e * blockDim.x;
+      if (v < V) {
+        const double2 z = zc[v];
+        const double di = ADJ ? -hd[e].y : hd[e].y;
+        c2[e] = c1[e];
+        c1[e] = make_double2(z.x - fma(hd[e].x, z.x, -di * z.y) - rhs[e].x,
+                             z.y - fma(hd[e].x, z.y, di * z.x) - rhs[e].y);
+      }
+    }
+    nh = nh < 2 ? nh + 1 : 2;
+  }
+};
 
 // Deterministic CTA sum of one double per thread; the result is returned to
 // every thread.  Uses S.red[0..15] and two barriers.
@@ -508,6 +555,13 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
     q[e] = v < H.V ? P.q0[base + v] : make_double2(0.0, 0.0);
   }
   CtaStats stats;
+  // predictor only when no step is ever recomputed (K == 0): recomputed stage
+  // vectors then stay bit-identical to the forward ones
+  // (its per-element history lives in registers: up to 2 elements per thread)
+  const bool pred = E <= 2 && H.K == 0 && H.method != LB_SOLVER_NEUMANN;
+  Pred<E <= 2 ? E : 1> pr;
+  if (pred) pr.init(P, H.V);
+  double2 pc[E];
   for (int j = 0; j < H.NT; ++j) {
     if (tape && H.K > 0 && j % H.K == 0) {
       double2* ck = P.ckpt + ((size_t)i * H.n_ckpt + j / H.K) * H.V;
@@ -518,7 +572,10 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
       }
     }
     int cur;
-    const int it = res_solve<E, QT, false>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur);
+    if constexpr (E <= 2) {
+      if (pred) pr.predict(pc);
+    }
+    const int it = res_solve<E, QT, false>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur, pred ? pc : nullptr);
     if (it < 0) {
       if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
       stats.flush(P.status);
@@ -526,6 +583,9 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
     }
     stats.add(0, it);
     const double2* zc = cur ? S.zb1 : S.zb0;
+    if constexpr (E <= 2) {
+      if (pred) pr.template record<false>(zc, q, H.V);
+    }
     double2* tp = (tape && H.K == 0) ? P.ckpt + ((size_t)i * H.NT + j) * H.V : nullptr;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -600,6 +660,11 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
   }
   CtaStats stats;
   const int nseg = H.K > 0 ? (H.NT + H.K - 1) / H.K : 1;
+  // adjoint predictor: the adjoint steps come in the same order for every K
+  const bool apred = E <= 2 && H.method != LB_SOLVER_NEUMANN;
+  Pred<E <= 2 ? E : 1> pr;
+  if (apred) pr.init(P, H.V);
+  double2 pc[E];
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int j0 = H.K > 0 ? sg * H.K : 0;
     const int j1 = H.K > 0 ? min(H.NT, j0 + H.K) : H.NT;
@@ -637,7 +702,10 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       const double2* ct = P.ctab + (size_t)j * H.Q;
       int cur;
       // (I - dt/2 (M^{j+1/2})^+) zhat^j = qhat^{j+1}   (eq. linsystem_adjoint)
-      const int it = res_solve<E, QT, true>(S, H, el, pl, lam, ct, cur);
+      if constexpr (E <= 2) {
+        if (apred) pr.predict(pc);
+      }
+      const int it = res_solve<E, QT, true>(S, H, el, pl, lam, ct, cur, apred ? pc : nullptr);
       if (it < 0) {
         if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
         stats.flush(P.status);
@@ -645,6 +713,9 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       }
       stats.add(2, it);
       const double2* zh = cur ? S.zb1 : S.zb0;
+      if constexpr (E <= 2) {
+        if (apred) pr.template record<true>(zh, lam, H.V);
+      }
       const double2* Zt = H.K > 0 ? P.seg + ((size_t)i * H.K + (j - j0)) * H.V : P.ckpt + ((size_t)i * H.NT + j) * H.V;
       // gradient pieces (eq. reducedgradient): for every subsystem q,
       //   g_a  = zhat^H vec(-i[a_q, Z])   = -i sum_kl Z_kl conj(R_zhat)
@@ -838,6 +909,9 @@ struct ClSmem {
   double2* rr;               // [V] right-hand side replica (forward state, recomputed state, or vectors)
   double2* ll;               // [V] adjoint state replica (backward sweep)
   double2* dv;               // [V] (I - dt/2 D)^-1, or dt/2 D for Neumann
+  double2* hd;               // [V] dt/2 D
+  double2* c1;               // [V] off-diagonal correction of the previous step (predictor)
+  double2* c2;               // [V] ... of the step before
   unsigned* dsl;             // [2][32] warp maxima of |z_new - z| received, index cta * 4 + warp
   unsigned* qsl;             // [32] this CTA's warp maxima of |rhs|
   unsigned long long* mbar;  // [2]
@@ -849,7 +923,7 @@ __host__ __device__ inline size_t cl_smem_bytes(int ncoef, int njcoef, int N, in
   b += align16(sizeof(double) * 2 * ncoef);
   b += align16(sizeof(double) * 2 * njcoef);
   b += align16(sizeof(uint32_t) * N);
-  b += sizeof(double2) * 5 * (size_t)V;
+  b += sizeof(double2) * 8 * (size_t)V;
   b += align16(sizeof(unsigned) * 64);
   b += align16(sizeof(unsigned) * 32);
   b += align16(sizeof(unsigned long long) * 2);
@@ -874,7 +948,10 @@ __device__ ClSmem cl_carve(unsigned char* base, int ncoef, int njcoef, int N, in
   S.rr = S.zb + 2 * (size_t)V;
   S.ll = S.rr + V;
   S.dv = S.ll + V;
-  o += sizeof(double2) * 5 * (size_t)V;
+  S.hd = S.dv + V;
+  S.c1 = S.hd + V;
+  S.c2 = S.c1 + V;
+  o += sizeof(double2) * 8 * (size_t)V;
   S.dsl = reinterpret_cast<unsigned*>(base + o);
   o += align16(sizeof(unsigned) * 64);
   S.qsl = reinterpret_cast<unsigned*>(base + o);
@@ -903,6 +980,7 @@ __device__ void cl_setup(const ClSmem& S, const ProbDev& P, cg::cluster_group& c
   for (int i = threadIdx.x; i < P.V; i += blockDim.x) {
     const double2 D = P.D[i];
     S.dv[i] = neumann ? make_double2(hh * D.x, hh * D.y) : P.Dinv[i];
+    S.hd[i] = make_double2(hh * D.x, hh * D.y);
   }
   for (int i = threadIdx.x; i < 64; i += blockDim.x) S.dsl[i] = 0u;
   if (threadIdx.x == 0) {
@@ -979,9 +1057,36 @@ struct ClCount {
 // the replica `rr`.  Returns the iteration count, -1 (max_iter), -2 (NaN/Inf)
 // or -3 (a wait gave up).  On success S.zb + (gk & 1) * V holds z in every
 // CTA, and zout the lane's element of it.
+// Predictor of the off-diagonal correction c = (I - dt/2 D) z - rhs of a step
+// from the two previous steps: nh = number of usable previous steps (0, 1, 2).
+__device__ __forceinline__ double2 cl_predict(const ClSmem& S, int e, int nh) {
+  if (nh <= 0) return make_double2(0.0, 0.0);
+  const double2 a = S.c1[e];
+  if (nh == 1) return a;
+  const double2 b = S.c2[e];
+  return make_double2(fma(2.0, a.x, -b.x), fma(2.0, a.y, -b.y));
+}
+
+// After a converged step, record c = (I - dt/2 D) z - rhs for every element
+// of the replica (identical in every CTA): c2 <- c1, c1 <- c.
+template <bool ADJ>
+__device__ __forceinline__ void cl_record(const ClSmem& S, const double2* __restrict__ zf,
+                                          const double2* __restrict__ rr, int V) {
+  for (int e = threadIdx.x; e < V; e += blockDim.x) {
+    const double2 z = zf[e], r = rr[e], d = S.hd[e];
+    const double di = ADJ ? -d.y : d.y;
+    // (I - dt/2 D) z - rhs
+    const double cr = z.x - fma(d.x, z.x, -di * z.y) - r.x;
+    const double ci = z.y - fma(d.x, z.y, di * z.x) - r.y;
+    S.c2[e] = S.c1[e];
+    S.c1[e] = make_double2(cr, ci);
+  }
+}
+
 template <int QT, bool ADJ>
 __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __restrict__ rr,
-                        const double2* __restrict__ ct, int C, int crank, ClCount& cnt, double2& zout) {
+                        const double2* __restrict__ ct, int C, int crank, ClCount& cnt, double2& zout,
+                        int nh = 0) {
   constexpr int L = ClLanes<QT>::L;
   const Hdr& H = *S.hdr;
   const int V = H.V;
@@ -997,7 +1102,9 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
       if (!neumann) {
         const double2 d = S.dv[e];
         const double di = ADJ ? -d.y : d.y;
-        z0 = make_double2(fma(d.x, r.x, -di * r.y), fma(d.x, r.y, di * r.x));
+        const double2 pc = cl_predict(S, e, nh);
+        const double ur = r.x + pc.x, ui = r.y + pc.y;
+        z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
       }
       z0b[e] = z0;
       qm = max(qm, max(hi_abs(r.x), hi_abs(r.y)));
@@ -1105,11 +1212,15 @@ __global__ void __launch_bounds__(128) k_forward_cl(const ProbDev* __restrict__ 
   ClCount cnt;
   CtaStats stats;
   bool failed = false;
+  // the predictor is used only when no step is ever recomputed (K == 0), so
+  // recomputed stage vectors stay bit-identical to the forward ones
+  const bool pred = H.K == 0 && H.method != LB_SOLVER_NEUMANN;
+  int nh = 0;
   for (int j = 0; j < H.NT; ++j) {
     if (tape && H.K > 0 && j % H.K == 0 && crank == 0)
       for (int e = threadIdx.x; e < H.V; e += blockDim.x) P.ckpt[((size_t)i * H.n_ckpt + j / H.K) * H.V + e] = S.rr[e];
     double2 z;
-    const int it = cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, C, crank, cnt, z);
+    const int it = cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, C, crank, cnt, z, pred ? nh : 0);
     if (it < 0) {
       if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
       failed = true;
@@ -1118,6 +1229,10 @@ __global__ void __launch_bounds__(128) k_forward_cl(const ProbDev* __restrict__ 
     if (crank == 0) stats.add(0, it);
     // q^{j+1} = 2 z - q^j on the whole replica (identical in every CTA)
     const double2* zf = S.zb + (size_t)(cnt.gk & 1) * H.V;
+    if (pred) {
+      cl_record<false>(S, zf, S.rr, H.V);
+      nh = nh < 2 ? nh + 1 : 2;
+    }
     for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
       const double2 zz = zf[e], qq = S.rr[e];
       if (tape && H.K == 0 && crank == 0) P.ckpt[((size_t)i * H.NT + j) * H.V + e] = zz;
@@ -1179,6 +1294,10 @@ __global__ void __launch_bounds__(128) k_backward_cl(const ProbDev* __restrict__
   CtaStats stats;
   bool failed = false;
   const int nseg = H.K > 0 ? (H.NT + H.K - 1) / H.K : 1;
+  // the adjoint sweep visits the steps in the same order for every K, so its
+  // predictor history never depends on the checkpoint interval
+  const bool apred = H.method != LB_SOLVER_NEUMANN;
+  int nha = 0;
   // gradient pieces of this CTA go to state slot i * C + crank of gproj
   double2* gbase = P.gproj + (size_t)(i * C + crank) * H.NT * H.Q * 2;
   for (int sg = nseg - 1; sg >= 0 && !failed; --sg) {
@@ -1207,7 +1326,7 @@ __global__ void __launch_bounds__(128) k_backward_cl(const ProbDev* __restrict__
     }
     for (int j = j1 - 1; j >= j0; --j) {
       double2 zh;
-      const int it = cl_solve<QT, true>(S, pl, S.ll, P.ctab + (size_t)j * H.Q, C, crank, cnt, zh);
+      const int it = cl_solve<QT, true>(S, pl, S.ll, P.ctab + (size_t)j * H.Q, C, crank, cnt, zh, apred ? nha : 0);
       if (it < 0) {
         if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
         failed = true;
@@ -1215,6 +1334,10 @@ __global__ void __launch_bounds__(128) k_backward_cl(const ProbDev* __restrict__
       }
       if (crank == 0) stats.add(2, it);
       const double2* zb = S.zb + (size_t)(cnt.gk & 1) * H.V;
+      if (apred) {
+        cl_record<true>(S, zb, S.ll, H.V);
+        nha = nha < 2 ? nha + 1 : 2;
+      }
       // gradient piece of this lane's half (eq. reducedgradient): sum_kl Z conj(X_zhat),
       // X the half's neighbour combination of zhat; P half -> g_ad, R half -> g_a
       double sr = 0.0, si = 0.0;

@@ -40,7 +40,8 @@ def _stats_dict(s) -> dict:
             "phase_steps": list(s.phase_steps), "phase_iterations": list(s.phase_iterations),
             "ms_forward": s.ms_forward, "ms_backward": s.ms_backward,
             "sweep": {1: "resident", 2: "grid", 3: "cluster"}.get(s.sweep, s.sweep),
-            "solver": {1: "jacobi", 2: "neumann"}.get(s.solver, s.solver)}
+            "solver": {1: "jacobi", 2: "neumann"}.get(s.solver, s.solver),
+            "ckpt_every": s.ckpt_every}
 
 
 def _stream_handle(stream) -> c_void_p:

@@ -123,7 +123,7 @@ def test_controls_and_states_validation(lib):
         assert lib.lb_solver_set(h, 9, 1e-15, 200, 100) == L.LB_EINVAL
         assert lib.lb_solver_set(h, 0, 0.0, 200, 100) == L.LB_EINVAL
         assert lib.lb_solver_set(h, 0, 1e-15, 0, 100) == L.LB_EINVAL
-        assert lib.lb_solver_set(h, 0, 1e-15, 200, -1) == L.LB_EINVAL
+        assert lib.lb_solver_set(h, 0, 1e-15, 200, -2) == L.LB_EINVAL
         # compute before binding a workspace is refused on the host
         G = c_double()
         assert lib.lb_forward(h, None, byref(G), None) == L.LB_EINVAL

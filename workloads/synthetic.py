@@ -75,7 +75,7 @@ class Problem:
     gate: Optional[np.ndarray] = None  # (Ne, Ne) complex128
     weights: Optional[np.ndarray] = None  # (M,) float64, None = all ones
     gamma2: float = 0.0
-    ckpt_every: int = 100
+    ckpt_every: int = -1  # -1: automatic (full stage tape when it fits, else every 100 steps)
     meta: dict = field(default_factory=dict)
 
     @property
@@ -286,7 +286,7 @@ def random_problem(
     hermitian: bool = True,
     dissipation: bool = True,
     gamma2: float = 0.0,
-    ckpt_every: int = 100,
+    ckpt_every: int = -1,
 ) -> Problem:
     """A small driven, dissipative problem with every term of the model active.
 

@@ -59,15 +59,27 @@ extern "C" {
 #define LB_J_FROB 0 /* J = 1/2 ||rho_tar - rho||_F^2 */
 #define LB_J_TR 1   /* J = 1 - Re Tr(rho_tar^+ rho) */
 
-/* inner solvers for (I - dt/2 M) z = q, Appendix A.  The paper uses GMRES;
- * this library uses fixed-point iterations that converge to the same unique z:
+/* inner solvers for (I - dt/2 M) z = q, Appendix A (the paper solves it with
+ * GMRES, Sec. IV); all converge to the same unique z:
  *   LB_SOLVER_JACOBI: z <- (I - dt/2 D)^-1 (q + dt/2 O z), D the diagonal of M
  *                     and O = M - D (the default; contraction ~ dt/2 |O|).
  *   LB_SOLVER_NEUMANN: z <- q + dt/2 M z (plain Neumann series).
- * LB_SOLVER_AUTO picks JACOBI. */
+ *   LB_SOLVER_GMRES: restarted GMRES(m) on the Jacobi-preconditioned system
+ *                     (I - (I - dt/2 D)^-1 dt/2 O) z = (I - dt/2 D)^-1 q, for
+ *                     steps where the fixed points converge slowly or diverge.
+ *                     m <= 20 is the longest cycle whose Krylov basis fits one
+ *                     CTA's shared memory beside the state (N^2 <= 1024 always
+ *                     does); runs only in the one-CTA-per-state sweep, so
+ *                     lb_bind_workspace fails with LB_EINVAL for grid or
+ *                     cluster sweeps or a basis that does not fit.  Stops when
+ *                     the 2-norm of the preconditioned residual (which bounds
+ *                     the fixed-point increment of the rtol test) is below
+ *                     rtol * max|q|; one iteration = one product with O.
+ * LB_SOLVER_AUTO picks JACOBI (lb_autotune also times GMRES where it fits). */
 #define LB_SOLVER_AUTO 0
 #define LB_SOLVER_JACOBI 1
 #define LB_SOLVER_NEUMANN 2
+#define LB_SOLVER_GMRES 3
 
 /* how the time loop is spread over the GPU:
  *   LB_SWEEP_RESIDENT: one CTA per state, the state in shared memory, the
@@ -224,7 +236,8 @@ int lb_get_stats(lb_system* sys, lb_stats* out);
  * the device; results discarded) of every candidate compatible with the bound
  * workspace -- sweep kind (one CTA per state with 1, 2, 4 or 8 elements per
  * thread, cluster-split when it applies; grid when the workspace was bound
- * for grid sweeps) x inner solver (Jacobi, Neumann) -- and keep the fastest
+ * for grid sweeps) x inner solver (Jacobi, Neumann, and GMRES for one CTA
+ * per state where its Krylov basis fits) -- and keep the fastest
  * candidate whose inner solve converges for later calls.  Synchronises
  * `stream`.  choice_out (nullable, [3]) receives the chosen LB_SWEEP_*,
  * LB_SOLVER_* and the threads per CTA (resident), CTAs per cluster (cluster)

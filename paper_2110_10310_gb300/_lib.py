@@ -35,6 +35,7 @@ LB_SWEEP_CLUSTER = 3
 LB_SOLVER_AUTO = 0
 LB_SOLVER_JACOBI = 1
 LB_SOLVER_NEUMANN = 2
+LB_SOLVER_GMRES = 3
 
 LB_MAX_SUBSYSTEMS = 8
 LB_MAX_LEVELS = 16

@@ -80,6 +80,7 @@ struct lb_system {
   double gamma2 = 0.0;
   // solver
   int method = LB_SOLVER_JACOBI;
+  int krylov = 0;  // GMRES cycle length that fits shared memory (decided at bind)
   double rtol = 1e-15;
   int max_iter = 200;
   int K = 100;       // requested checkpoint interval; < 0 = automatic (effective_K)
@@ -134,6 +135,7 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 // when asked for; AUTO also prefers them when few states leave most SMs idle.
 bool use_grid(const lb_system* s) {
   if (s->V > lbk::kMaxResidentV) return true;
+  if (s->method == LB_SOLVER_GMRES) return false;  // GMRES runs one CTA per state
   if (s->sweep == LB_SWEEP_GRID) return true;
   if (s->sweep == LB_SWEEP_RESIDENT || s->sweep == LB_SWEEP_CLUSTER) return false;
   return s->V >= 1024 && s->M < 64;
@@ -168,9 +170,31 @@ int effective_K(const lb_system* s) {
 
 // CTAs per state of the cluster sweep if it can apply to this system (0: never)
 int cluster_ctas(const lb_system* s) {
-  if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT) return 0;
+  if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT || s->method == LB_SOLVER_GMRES) return 0;
   const lbk::ClusterConfig cc = lbk::cluster_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N);
   return cc.C > 0 ? cc.C : 0;
+}
+
+// complex values of the GMRES Krylov basis in shared memory (0 for the
+// fixed-point solvers)
+size_t kry_elems(const lb_system* s) {
+  return s->method == LB_SOLVER_GMRES ? (size_t)(s->krylov + 1) * s->V : 0;
+}
+
+// GMRES cycle length for this system on the current device; with GMRES
+// chosen, check that it can run (one CTA per state, basis in shared memory).
+int decide_krylov(lb_system* s) {
+  int dev = 0, optin = 0;
+  LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+  LB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "cudaDeviceGetAttribute");
+  s->krylov = s->V <= lbk::kMaxResidentV ? lbk::gmres_krylov_dim(s->V, n_coef(s), n_jcoef(s), s->N, (size_t)optin) : 0;
+  if (s->method != LB_SOLVER_GMRES) return LB_OK;
+  if (s->sweep == LB_SWEEP_GRID || s->sweep == LB_SWEEP_CLUSTER)
+    return fail(LB_EINVAL, "GMRES runs in the one-CTA-per-state sweep only (LB_SWEEP_RESIDENT or AUTO)");
+  if (s->krylov <= 0)
+    return fail(LB_EINVAL, "GMRES needs its Krylov basis in one CTA's shared memory: N^2 too large");
+  s->sweep = LB_SWEEP_RESIDENT;
+  return LB_OK;
 }
 
 // state slots of the gradient pieces: one (summed) for grid sweeps, one per
@@ -320,6 +344,7 @@ void fill_prob(lb_system* s) {
   P.n_ckpt = P.K > 0 ? (int32_t)((s->NT + P.K - 1) / P.K) : (int32_t)s->NT;
   P.max_iter = s->max_iter;
   P.method = s->method;
+  P.krylov = s->krylov;
   P.kind = s->kind;
   P.Ns = s->Ns;
   P.n_params = s->n_params;
@@ -503,18 +528,22 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
     int sweep, method, E;
   };
   std::vector<Cand> cands;
-  const int methods[2] = {LB_SOLVER_JACOBI, LB_SOLVER_NEUMANN};
+  // the bound workspace fixes the sweep family: grid buffers exist only for
+  // grid sweeps, GMRES runs one CTA per state
+  const bool grid0 = use_grid(s);
+  const int methods[3] = {LB_SOLVER_JACOBI, LB_SOLVER_NEUMANN, LB_SOLVER_GMRES};
   for (int m : methods) {
-    if (use_grid(s)) {
-      cands.push_back({LB_SWEEP_GRID, m, 0});
+    if (grid0) {
+      if (m != LB_SOLVER_GMRES) cands.push_back({LB_SWEEP_GRID, m, 0});
       continue;
     }
+    if (m == LB_SOLVER_GMRES && s->krylov <= 0) continue;
     for (int E = 1; E <= 8; E *= 2) {
       const int threads = ((s->V + E - 1) / E + 31) / 32 * 32;
       if (threads > 512 || (E > 1 && threads < 64)) continue;
       cands.push_back({LB_SWEEP_RESIDENT, m, E});
     }
-    if (s->cc.C > 0) cands.push_back({LB_SWEEP_CLUSTER, m, 0});
+    if (s->cc.C > 0 && m != LB_SOLVER_GMRES) cands.push_back({LB_SWEEP_CLUSTER, m, 0});
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   LB_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
@@ -532,7 +561,7 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
     s->cluster = c.sweep == LB_SWEEP_CLUSTER;
     s->hp.gM = use_grid(s) ? 1 : (s->cluster ? s->M * s->cc.C : s->M);
     if (c.sweep == LB_SWEEP_RESIDENT) {
-      s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true);
+      s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true, kry_elems(s));
       const int threads = ((s->V + c.E - 1) / c.E + 31) / 32 * 32;
       s->rc.E = c.E;
       s->rc.threads = threads;
@@ -576,7 +605,7 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
   s->cluster = win.sweep == LB_SWEEP_CLUSTER;
   s->hp.gM = use_grid(s) ? 1 : (s->cluster ? s->M * s->cc.C : s->M);
   if (win.sweep == LB_SWEEP_RESIDENT) {
-    s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true);
+    s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true, kry_elems(s));
     s->rc.E = win.E;
     s->rc.threads = ((s->V + win.E - 1) / win.E + 31) / 32 * 32;
     s->rc.QT = (win.E == 1 && s->Q <= 4) ? s->Q : 0;
@@ -699,7 +728,8 @@ int lb_solver_set(lb_system* s, int32_t method, double rtol, int32_t max_iter, i
   if (!s) return fail(LB_EINVAL, "null system handle");
   if (s->ws) return fail(LB_EINVAL, "set the solver before binding a workspace");
   if (method == LB_SOLVER_AUTO) method = LB_SOLVER_JACOBI;
-  if (method != LB_SOLVER_JACOBI && method != LB_SOLVER_NEUMANN) return fail(LB_EINVAL, "unknown solver");
+  if (method != LB_SOLVER_JACOBI && method != LB_SOLVER_NEUMANN && method != LB_SOLVER_GMRES)
+    return fail(LB_EINVAL, "unknown solver");
   if (!(rtol > 0.0) || !(rtol < 1.0)) return fail(LB_EINVAL, "rtol must be in (0, 1)");
   if (max_iter < 1 || max_iter > 100000) return fail(LB_EINVAL, "max_iter must be in 1..100000");
   if (ckpt_every < LB_CKPT_AUTO) return fail(LB_EINVAL, "ckpt_every must be >= 0 or LB_CKPT_AUTO");
@@ -746,8 +776,10 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
   if (bytes < s->L.total) return fail(LB_ENOMEM, "workspace smaller than lb_workspace_bytes");
   if (s->rho0.empty()) return fail(LB_EINVAL, "initial states are required before binding");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  rc = decide_krylov(s);
+  if (rc) return rc;
   s->cluster = false;
-  if (!use_grid(s) && s->sweep != LB_SWEEP_RESIDENT) {
+  if (!use_grid(s) && s->sweep != LB_SWEEP_RESIDENT && s->method != LB_SOLVER_GMRES) {
     s->cc = lbk::cluster_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N);
     int dev = 0, nsm = 0;
     LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
@@ -803,7 +835,7 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
   if (rc) return rc;
   rc = upload_controls(s, st);
   if (rc) return rc;
-  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true);
+  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true, kry_elems(s));
   // the workspace now owns the states; pageable copies above are staged
   s->rho0.clear();
   s->rho0.shrink_to_fit();
@@ -1003,6 +1035,7 @@ int lb_batch_create(lb_system* const* systems, int32_t n, lb_batch** out) {
   lb_batch* b = new (std::nothrow) lb_batch();
   if (!b) return fail(LB_ENOMEM, "host allocation failed");
   int maxV = 0, maxQ = 0, maxc = 0, maxj = 0, maxN = 0, minQ = LB_MAXQ + 1;
+  size_t maxkry = 0;
   for (int i = 0; i < n; ++i) {
     lb_system* s = systems[i];
     if (!s || !s->ws) {
@@ -1023,9 +1056,20 @@ int lb_batch_create(lb_system* const* systems, int32_t n, lb_batch** out) {
     maxc = std::max(maxc, n_coef(s));
     maxj = std::max(maxj, n_jcoef(s));
     maxN = std::max(maxN, s->N);
+    maxkry = std::max(maxkry, kry_elems(s));
     b->max_param_warps = std::max(b->max_param_warps, param_warps(s));
   }
-  b->rc = lbk::resident_config(maxV, maxQ, maxc, maxj, maxN, minQ == maxQ);
+  b->rc = lbk::resident_config(maxV, maxQ, maxc, maxj, maxN, minQ == maxQ, maxkry);
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    delete b;
+    return fail(LB_ECUDA, "cannot read the device's shared memory limit");
+  }
+  if (b->rc.smem > (size_t)optin) {
+    delete b;
+    return fail(LB_EINVAL, "the batch's largest state and GMRES basis do not fit one CTA's shared memory together");
+  }
   *out = b;
   return LB_OK;
 }
@@ -1272,6 +1316,8 @@ int static_scratch_address(void** out) {
 // lb_bind_workspace, but keep the host copies: the array is shared by every
 // call, so each call uploads everything again.
 int static_bind(lb_system* s, void* ws, cudaStream_t st) {
+  int rc0 = decide_krylov(s);
+  if (rc0) return rc0;
   s->L = make_layout(s);
   s->ws = static_cast<char*>(ws);
   s->ws_bytes = LB_STATIC_SCRATCH_BYTES;
@@ -1308,7 +1354,7 @@ int static_bind(lb_system* s, void* ws, cudaStream_t st) {
   if (rc) return rc;
   rc = upload_controls(s, st);
   if (rc) return rc;
-  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true);
+  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true, kry_elems(s));
   return LB_OK;
 }
 

@@ -37,6 +37,8 @@ struct ProbDev {
   int32_t K;  // checkpoint interval; 0 = keep every stage vector z^j
   int32_t n_ckpt, max_iter, method, kind;
   int32_t Ns, n_params;
+  int32_t krylov;            // GMRES cycle length m (Krylov basis of m + 1 vectors in shared memory)
+  int32_t pad0;
   double h, rtol, T, gamma2;
   int32_t levels[LB_MAXQ];
   int32_t stride[LB_MAXQ];   // s_q = prod_{p>q} n_p
@@ -101,10 +103,16 @@ struct ResidentConfig {
   int E;        // elements per thread (1, 2, 4, 8)
   int QT;       // E == 1: compile-time subsystem count of the per-thread plan (1..4), 0 = generic
   size_t smem;  // dynamic shared memory bytes
+  bool gmres;   // kernels that can run GMRES (shared memory sized for its Krylov basis)
 };
 
-// uniformQ: every problem of the launch has Q = maxQ
-ResidentConfig resident_config(int maxV, int maxQ, int maxNcoef, int maxNj, int maxN, bool uniformQ);
+// uniformQ: every problem of the launch has Q = maxQ; kry_elems: complex
+// values of the largest GMRES Krylov basis among them (0: no GMRES problem)
+ResidentConfig resident_config(int maxV, int maxQ, int maxNcoef, int maxNj, int maxN, bool uniformQ,
+                               size_t kry_elems = 0);
+// GMRES cycle length m whose Krylov basis of m + 1 vectors fits one CTA's
+// shared memory next to the resident sweep's buffers (0: below the minimum)
+int gmres_krylov_dim(int V, int ncoef, int njcoef, int N, size_t smem_limit);
 
 cudaError_t launch_tables(ProbDev* d_prob, const ProbDev& h_prob, cudaStream_t s);
 cudaError_t launch_gate_targets(const ProbDev& h_prob, const double2* Vg, const int32_t* emap, const int32_t* efull,

@@ -74,6 +74,19 @@ __device__ __forceinline__ double warp_sum4(double v0, double v1, double v2, dou
   return k;
 }
 
+// Sum of two per-lane values over the warp with 5 FP64 additions per lane:
+// after the call lane 0 holds the total of a and lane 16 that of b.
+__device__ __forceinline__ double warp_sum2(double a, double b, int lane) {
+  const bool h16 = lane & 16;
+  double k = h16 ? b : a;
+  k += __shfl_xor_sync(kFull, h16 ? a : b, 16);
+  k += __shfl_xor_sync(kFull, k, 8);
+  k += __shfl_xor_sync(kFull, k, 4);
+  k += __shfl_xor_sync(kFull, k, 2);
+  k += __shfl_xor_sync(kFull, k, 1);
+  return k;
+}
+
 // quadratic B-spline of unit knot spacing centred at 0 (Sec. II, eq. rotctrl)
 __device__ __forceinline__ double bspline2(double x) {
   x = fabs(x);
@@ -93,7 +106,7 @@ __device__ void record_error(DevStatus* st, int code, int step) {
 // per-CTA copy of the problem constants used in the inner loops
 
 struct Hdr {
-  int Q, N, V, NT, K, n_ckpt, max_iter, method, kind, M;
+  int Q, N, V, NT, K, n_ckpt, max_iter, method, kind, M, krylov;
   double h, rtol;
   int lev[LB_MAXQ], stride[LB_MAXQ], coff[LB_MAXQ], joff[LB_MAXQ];
   double jump[LB_MAXQ];
@@ -117,6 +130,7 @@ __device__ void load_hdr(Hdr& H, const ProbDev& P) {
   H.method = P.method;
   H.kind = P.kind;
   H.M = P.M;
+  H.krylov = P.krylov;
   H.h = P.h;
   H.rtol = P.rtol;
   for (int q = 0; q < LB_MAXQ; ++q) {
@@ -202,11 +216,32 @@ struct ResSmem {
   double2* dsm;               // [V] Dinv (Jacobi) or dt/2 D (Neumann)
   double2* zb0;               // [V]
   double2* zb1;               // [V]
+  double* gm;                 // [kGmresScratch] (GMRES)
+  double2* kry;               // [(m + 1) * V] Krylov basis (GMRES)
 };
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline size_t res_smem_bytes(int ncoef, int njcoef, int N, int V) {
+// GMRES scratch in shared memory (doubles): Hessenberg matrix, rotations, the
+// rotated right-hand side g, the solution y, a flag and three reduction areas
+// (16 warps at most: CTAs of <= 512 threads).
+constexpr int kGmresMaxM = 20;  // longest Krylov cycle (restart length)
+constexpr int kGmresMinM = 4;   // shortest one worth running
+constexpr int kGmWarps = 16;
+constexpr int kGmH = 0;  // [m][m+1] complex, column j at 2 j (kGmresMaxM + 1)
+constexpr int kGmCs = kGmH + 2 * (kGmresMaxM + 1) * kGmresMaxM;
+constexpr int kGmSn = kGmCs + kGmresMaxM;
+constexpr int kGmG = kGmSn + 2 * kGmresMaxM;
+constexpr int kGmY = kGmG + 2 * (kGmresMaxM + 1);
+constexpr int kGmFlag = kGmY + 2 * kGmresMaxM;
+constexpr int kGmR1 = kGmFlag + 2;
+constexpr int kGmR2 = kGmR1 + 2 * kGmresMaxM * kGmWarps;
+constexpr int kGmR3 = kGmR2 + 2 * kGmresMaxM * kGmWarps;
+constexpr int kGmresScratch = kGmR3 + kGmWarps;
+static_assert(kGmresScratch % 2 == 0, "the Krylov basis after the scratch must stay 16-byte aligned");
+
+// kry_elems: complex values of the GMRES Krylov basis, 0 when the method is not GMRES
+__host__ __device__ inline size_t res_smem_bytes(int ncoef, int njcoef, int N, int V, size_t kry_elems = 0) {
   size_t b = align16(sizeof(Hdr));
   b += align16(sizeof(double) * 2 * ncoef);
   b += align16(sizeof(double) * 2 * njcoef);
@@ -214,6 +249,7 @@ __host__ __device__ inline size_t res_smem_bytes(int ncoef, int njcoef, int N, i
   b += align16(sizeof(unsigned long long) * 48);
   b += align16(sizeof(double) * 4 * LB_MAXQ * 16);
   b += sizeof(double2) * 3 * (size_t)V;
+  if (kry_elems) b += sizeof(double) * kGmresScratch + sizeof(double2) * kry_elems;
   return b;
 }
 
@@ -237,6 +273,9 @@ __device__ ResSmem carve(unsigned char* base, int ncoef, int njcoef, int N, int 
   S.dsm = reinterpret_cast<double2*>(base + o);
   S.zb0 = S.dsm + V;
   S.zb1 = S.zb0 + V;
+  // GMRES only (present when the launch sized shared memory for it)
+  S.gm = reinterpret_cast<double*>(S.zb1 + V);
+  S.kry = reinterpret_cast<double2*>(S.gm + kGmresScratch);
   return S;
 }
 
@@ -358,20 +397,27 @@ __device__ __forceinline__ unsigned hi_abs(double x) {
 }
 constexpr unsigned kInfHi = 0x7ff00000u;
 
+template <int E, bool ADJ>
+__device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, const double2* __restrict__ ct,
+                         double tol);
+
 // Solve (I - dt/2 M) z = rhs (ADJ: (I - dt/2 M^+) z = rhs) for the CTA's
 // state.  Returns the iteration count (>= 1), -1 when max_iter is reached,
 // -2 on NaN/Inf.  On return, zbuf[cur] holds z; every thread has passed the
 // final barrier.  The stopping test compares the high words of the bit
 // patterns, hi(max|z_new - z|) < hi(rtol max|rhs|), which implies the exact
 // test and is taken identically by every thread (and in a recompute).
-// QT > 0 (with E == 1) uses the per-thread plan.
-template <int E, int QT, bool ADJ>
+// QT > 0 (with E == 1) uses the per-thread plan.  GM: the kernel variant
+// that can also run GMRES (res_gmres) when the problem's method asks for it;
+// the fixed-point kernels are compiled without it.
+template <int E, int QT, bool ADJ, bool GM = false>
 __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, const Plan<QT>& pl,
                          const double2 (&rhs)[E], const double2* __restrict__ ct, int& cur,
                          const double2* pc = nullptr) {
   static_assert(QT == 0 || E == 1, "the per-thread plan holds one element");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const bool neumann = H.method == LB_SOLVER_NEUMANN;
+  const bool gmres = GM && H.method == LB_SOLVER_GMRES;
   const Tabs T{S.cu, S.cd, S.jf, S.ja};
   unsigned* slots = reinterpret_cast<unsigned*>(S.slots);
   double2 cq[QT > 0 ? QT : 1];
@@ -397,6 +443,7 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
         z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
       }
       S.zb0[v] = z0;
+      if (gmres) S.zb1[v] = rhs[e];
       qmax = max(qmax, max(hi_abs(rhs[e].x), hi_abs(rhs[e].y)));
     }
   }
@@ -407,8 +454,12 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
   for (int w = 0; w < nwarps; ++w) qmax = max(qmax, slots[64 + w]);
   if (qmax >= kInfHi) return -2;
   // rtol * (a value <= max|rhs|), so the test is never looser than the exact one
-  const unsigned thr = hi_abs(H.rtol * __longlong_as_double(static_cast<long long>((unsigned long long)qmax << 32)));
+  const double tol = H.rtol * __longlong_as_double(static_cast<long long>((unsigned long long)qmax << 32));
   cur = 0;
+  if constexpr (GM) {
+    if (gmres) return res_gmres<E, ADJ>(S, H, el, ct, tol);
+  }
+  const unsigned thr = hi_abs(tol);
   for (int it = 0; it < H.max_iter; ++it) {
     const double2* __restrict__ zc = cur ? S.zb1 : S.zb0;
     double2* __restrict__ zn = cur ? S.zb0 : S.zb1;
@@ -510,6 +561,239 @@ __device__ double cta_sum(const ResSmem& S, double x) {
   return t;
 }
 
+// ---------------------------------------------------------------------------
+// GMRES inner solve (the paper's Krylov method, Sec. IV), one CTA per state.
+//
+// Restarted GMRES(m) on the Jacobi-preconditioned system
+//   K z = b,   K = I - Dinv (dt/2) O,   b = Dinv q
+// (ADJ: conj(Dinv) and the adjoint off-diagonal part), equivalent to
+// (I - dt/2 M) z = q.  Its residual b - K z = Dinv (q + dt/2 O z) - z is the
+// increment of one Jacobi sweep, the quantity the fixed-point test bounds.
+// Arnoldi uses classical Gram-Schmidt with one re-orthogonalisation pass; all
+// dot products and norms are fixed-order CTA reductions, so a recompute
+// reproduces every iterate bit for bit.  Thread 0 applies the Givens
+// rotations and solves the small triangular system.  A cycle stops when the
+// rotated residual norm |g_{j+1}| = ||b - K z||_2 (which bounds the largest
+// component) falls below tol; a restart recomputes the residual from z.
+// Iterations counted: products with O (Arnoldi steps plus one per restart).
+// On entry zb0 holds the first iterate z_0 and zb1 the right-hand side q; on a
+// converged return zb0 holds z and every thread has passed a barrier.
+template <int E, bool ADJ>
+__device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, const double2* __restrict__ ct,
+                         double tol) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int V = H.V, m = H.krylov;
+  const Tabs T{S.cu, S.cd, S.jf, S.ja};
+  double* gm = S.gm;
+  double2* kry = S.kry;
+  const double2* rhs = S.zb1;
+  double2* xs = S.zb0;
+  double2 x[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int v = threadIdx.x + e * blockDim.x;
+    x[e] = v < V ? xs[v] : make_double2(0.0, 0.0);
+  }
+  int its = 0;
+  for (;;) {
+    // r = Dinv (q + dt/2 O z) - z, normalised into the first basis vector
+    double nrm = 0.0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int v = threadIdx.x + e * blockDim.x;
+      if (v < V) {
+        double ar = rhs[v].x, ai = rhs[v].y;
+        offdiag_acc<ADJ>(ar, ai, xs, v, el.kd[e], el.ld[e], H, T, ct);
+        const double2 d = S.dsm[v];
+        const double di = ADJ ? -d.y : d.y;
+        const double2 r = make_double2(fma(d.x, ar, -di * ai) - x[e].x, fma(d.x, ai, di * ar) - x[e].y);
+        kry[v] = r;
+        nrm = fma(r.x, r.x, fma(r.y, r.y, nrm));
+      }
+    }
+    ++its;
+    const double beta = sqrt(cta_sum(S, nrm));
+    if (!(beta <= 1.0e300)) return -2;  // NaN or Inf
+    if (beta < tol) return its;         // z (in zb0) already passed a barrier
+    if (its >= H.max_iter) return -1;
+    const double ib = 1.0 / beta;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int v = threadIdx.x + e * blockDim.x;
+      if (v < V) kry[v] = make_double2(kry[v].x * ib, kry[v].y * ib);
+    }
+    if (threadIdx.x == 0) {
+      gm[kGmG] = beta;
+      gm[kGmG + 1] = 0.0;
+    }
+    int k = 0;
+    bool conv = false;
+    for (int j = 0; j < m; ++j) {
+      __syncthreads();  // v_j complete
+      const double2* vj = kry + (size_t)j * V;
+      double2* vn = kry + (size_t)(j + 1) * V;
+      // w = K v_j
+      double2 w[E];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int v = threadIdx.x + e * blockDim.x;
+        w[e] = make_double2(0.0, 0.0);
+        if (v < V) {
+          double ar = 0.0, ai = 0.0;
+          offdiag_acc<ADJ>(ar, ai, vj, v, el.kd[e], el.ld[e], H, T, ct);
+          const double2 d = S.dsm[v];
+          const double di = ADJ ? -d.y : d.y;
+          const double2 u = vj[v];
+          w[e] = make_double2(u.x - fma(d.x, ar, -di * ai), u.y - fma(d.x, ai, di * ar));
+        }
+      }
+      // h = V_j^H w, w -= V_j h; twice
+      double* hc = gm + kGmH + 2 * j * (kGmresMaxM + 1);
+      for (int pass = 0; pass < 2; ++pass) {
+        double* red = gm + (pass ? kGmR2 : kGmR1);
+        for (int i = 0; i <= j; ++i) {
+          double sr = 0.0, si = 0.0;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int v = threadIdx.x + e * blockDim.x;
+            if (v < V) {
+              const double2 u = kry[(size_t)i * V + v];
+              sr = fma(u.x, w[e].x, fma(u.y, w[e].y, sr));
+              si = fma(u.x, w[e].y, fma(-u.y, w[e].x, si));
+            }
+          }
+          const double t = warp_sum2(sr, si, lane);
+          if ((lane & 15) == 0) red[(2 * i + (lane >> 4)) * kGmWarps + warp] = t;
+        }
+        __syncthreads();
+        for (int i = 0; i <= j; ++i) {
+          double hr = 0.0, hi = 0.0;
+          for (int ww = 0; ww < nw; ++ww) {
+            hr += red[(2 * i) * kGmWarps + ww];
+            hi += red[(2 * i + 1) * kGmWarps + ww];
+          }
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int v = threadIdx.x + e * blockDim.x;
+            if (v < V) {
+              const double2 u = kry[(size_t)i * V + v];
+              w[e].x -= fma(hr, u.x, -hi * u.y);
+              w[e].y -= fma(hr, u.y, hi * u.x);
+            }
+          }
+          if (threadIdx.x == 0) {
+            hc[2 * i] = pass ? hc[2 * i] + hr : hr;
+            hc[2 * i + 1] = pass ? hc[2 * i + 1] + hi : hi;
+          }
+        }
+      }
+      double n2 = 0.0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) n2 = fma(w[e].x, w[e].x, fma(w[e].y, w[e].y, n2));
+      n2 = warp_sum(n2);
+      if (lane == 0) gm[kGmR3 + warp] = n2;
+      __syncthreads();
+      double s2 = 0.0;
+      for (int ww = 0; ww < nw; ++ww) s2 += gm[kGmR3 + ww];
+      const double hn = sqrt(s2);
+      if (!(hn <= 1.0e300)) return -2;
+      const double ih = hn > 0.0 ? 1.0 / hn : 0.0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int v = threadIdx.x + e * blockDim.x;
+        if (v < V) vn[v] = make_double2(w[e].x * ih, w[e].y * ih);
+      }
+      ++its;
+      k = j + 1;
+      if (threadIdx.x == 0) {
+        // earlier rotations on column j, then the one that zeroes h_{j+1,j}
+        for (int i = 0; i < j; ++i) {
+          const double c = gm[kGmCs + i], sr = gm[kGmSn + 2 * i], si = gm[kGmSn + 2 * i + 1];
+          const double ar = hc[2 * i], ai = hc[2 * i + 1], br = hc[2 * i + 2], bi = hc[2 * i + 3];
+          // (a, b) <- (c a + s b, -conj(s) a + c b)
+          hc[2 * i] = c * ar + (sr * br - si * bi);
+          hc[2 * i + 1] = c * ai + (sr * bi + si * br);
+          hc[2 * i + 2] = c * br - (sr * ar + si * ai);
+          hc[2 * i + 3] = c * bi - (sr * ai - si * ar);
+        }
+        const double ar = hc[2 * j], ai = hc[2 * j + 1];
+        const double na = hypot(ar, ai), r = hypot(na, hn);
+        double c, sr, si;
+        if (r == 0.0) {
+          c = 1.0, sr = 0.0, si = 0.0;
+        } else if (na == 0.0) {
+          c = 0.0, sr = 1.0, si = 0.0;
+          hc[2 * j] = hn;
+          hc[2 * j + 1] = 0.0;
+        } else {
+          // c = |a|/r, s = (a/|a|) h/r, rho = (a/|a|) r
+          c = na / r;
+          sr = ar / na * (hn / r);
+          si = ai / na * (hn / r);
+          hc[2 * j] = ar / na * r;
+          hc[2 * j + 1] = ai / na * r;
+        }
+        hc[2 * j + 2] = 0.0;
+        hc[2 * j + 3] = 0.0;
+        gm[kGmCs + j] = c;
+        gm[kGmSn + 2 * j] = sr;
+        gm[kGmSn + 2 * j + 1] = si;
+        const double gr = gm[kGmG + 2 * j], gi = gm[kGmG + 2 * j + 1];
+        // (g_j, g_{j+1}) <- (c g_j, -conj(s) g_j)
+        gm[kGmG + 2 * j] = c * gr;
+        gm[kGmG + 2 * j + 1] = c * gi;
+        const double nr = -(sr * gr + si * gi), ni = -(sr * gi - si * gr);
+        gm[kGmG + 2 * j + 2] = nr;
+        gm[kGmG + 2 * j + 3] = ni;
+        gm[kGmFlag] = (hypot(nr, ni) < tol || hn == 0.0) ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      conv = gm[kGmFlag] != 0.0;
+      if (conv || its >= H.max_iter) break;
+    }
+    // z += V_k y with R y = g (back substitution by thread 0)
+    if (threadIdx.x == 0) {
+      bool bad = false;
+      for (int i = k - 1; i >= 0; --i) {
+        double tr = gm[kGmG + 2 * i], ti = gm[kGmG + 2 * i + 1];
+        for (int l = i + 1; l < k; ++l) {
+          const double* hl = gm + kGmH + 2 * l * (kGmresMaxM + 1);
+          const double yr = gm[kGmY + 2 * l], yi = gm[kGmY + 2 * l + 1];
+          tr -= hl[2 * i] * yr - hl[2 * i + 1] * yi;
+          ti -= hl[2 * i] * yi + hl[2 * i + 1] * yr;
+        }
+        const double* hi_ = gm + kGmH + 2 * i * (kGmresMaxM + 1);
+        const double dr = hi_[2 * i], dim = hi_[2 * i + 1];
+        const double den = dr * dr + dim * dim;
+        gm[kGmY + 2 * i] = (tr * dr + ti * dim) / den;
+        gm[kGmY + 2 * i + 1] = (ti * dr - tr * dim) / den;
+        bad = bad || !(fabs(gm[kGmY + 2 * i]) <= 1.0e300 && fabs(gm[kGmY + 2 * i + 1]) <= 1.0e300);
+      }
+      gm[kGmFlag + 1] = bad ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (gm[kGmFlag + 1] != 0.0) return -2;  // singular triangle or overflow
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int v = threadIdx.x + e * blockDim.x;
+      if (v < V) {
+        double2 z = x[e];
+        for (int i = 0; i < k; ++i) {
+          const double yr = gm[kGmY + 2 * i], yi = gm[kGmY + 2 * i + 1];
+          const double2 u = kry[(size_t)i * V + v];
+          z.x += fma(yr, u.x, -yi * u.y);
+          z.y += fma(yr, u.y, yi * u.x);
+        }
+        x[e] = z;
+        xs[v] = z;
+      }
+    }
+    __syncthreads();
+    if (conv) return its;
+    if (its >= H.max_iter) return -1;
+  }
+}
+
 struct CtaStats {
   unsigned long long iters[3] = {0, 0, 0}, steps[3] = {0, 0, 0};
   int maxit = 0;
@@ -533,7 +817,7 @@ struct CtaStats {
 // ---------------------------------------------------------------------------
 // forward sweep, one CTA per (problem, state) work item
 
-template <int E, int QT>
+template <int E, int QT, bool GM>
 __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__ probs,
                                                      const WorkItem* __restrict__ items, int tape) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -575,7 +859,7 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
     if constexpr (E <= 2) {
       if (pred) pr.predict(pc);
     }
-    const int it = res_solve<E, QT, false>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur, pred ? pc : nullptr);
+    const int it = res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur, pred ? pc : nullptr);
     if (it < 0) {
       if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
       stats.flush(P.status);
@@ -623,7 +907,7 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
 // backward sweep: recompute each checkpoint segment, then adjoint steps with
 // the gradient pieces of eq. reducedgradient.
 
-template <int E, int QT>
+template <int E, int QT, bool GM>
 __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict__ probs,
                                                       const WorkItem* __restrict__ items) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -678,7 +962,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       }
       for (int j = j0; j < j1; ++j) {
         int cur;
-        const int it = res_solve<E, QT, false>(S, H, el, pl, qf, P.ctab + (size_t)j * H.Q, cur);
+        const int it = res_solve<E, QT, false, GM>(S, H, el, pl, qf, P.ctab + (size_t)j * H.Q, cur);
         if (it < 0) {
           if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
           stats.flush(P.status);
@@ -705,7 +989,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       if constexpr (E <= 2) {
         if (apred) pr.predict(pc);
       }
-      const int it = res_solve<E, QT, true>(S, H, el, pl, lam, ct, cur, apred ? pc : nullptr);
+      const int it = res_solve<E, QT, true, GM>(S, H, el, pl, lam, ct, cur, apred ? pc : nullptr);
       if (it < 0) {
         if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
         stats.flush(P.status);
@@ -783,7 +1067,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
 // ---------------------------------------------------------------------------
 // propagate given vectors (tests and the step-level API), one CTA per vector
 
-template <int E, int QT>
+template <int E, int QT, bool GM>
 __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict__ pp, int adjoint, int j0, int j1,
                                                        double2* __restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -806,8 +1090,8 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
   for (int jj = 0; jj < j1 - j0; ++jj) {
     const int j = adjoint ? j1 - 1 - jj : j0 + jj;
     int cur;
-    const int it = adjoint ? res_solve<E, QT, true>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur)
-                           : res_solve<E, QT, false>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur);
+    const int it = adjoint ? res_solve<E, QT, true, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur)
+                           : res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur);
     if (it < 0) {
       if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
       stats.flush(P.status);
@@ -2148,7 +2432,16 @@ __global__ void k_objective_states(const ProbDev* __restrict__ pp) {
 // ---------------------------------------------------------------------------
 // launchers
 
-ResidentConfig resident_config(int maxV, int maxQ, int maxNcoef, int maxNj, int maxN, bool uniformQ) {
+int gmres_krylov_dim(int V, int ncoef, int njcoef, int N, size_t smem_limit) {
+  const size_t base = res_smem_bytes(ncoef, njcoef, N, V, 1) - sizeof(double2);
+  if (base >= smem_limit) return 0;
+  long long m = (long long)((smem_limit - base) / (sizeof(double2) * (size_t)V)) - 1;
+  if (m > kGmresMaxM) m = kGmresMaxM;
+  return m >= kGmresMinM ? (int)m : 0;
+}
+
+ResidentConfig resident_config(int maxV, int maxQ, int maxNcoef, int maxNj, int maxN, bool uniformQ,
+                               size_t kry_elems) {
   ResidentConfig rc;
   int E = 1;
   while (E < 8 && (maxV + E - 1) / E > 512) E *= 2;
@@ -2158,46 +2451,58 @@ ResidentConfig resident_config(int maxV, int maxQ, int maxNcoef, int maxNj, int 
   rc.threads = threads;
   rc.E = E;
   rc.QT = (E == 1 && uniformQ && maxQ <= 4) ? maxQ : 0;
-  rc.smem = res_smem_bytes(maxNcoef, maxNj, maxN, maxV);
+  rc.smem = res_smem_bytes(maxNcoef, maxNj, maxN, maxV, kry_elems);
+  rc.gmres = kry_elems > 0;
   return rc;
 }
 
-template <int E, int QT>
+template <int E, int QT, bool GM>
 static cudaError_t set_smem_attr(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_forward_res<E, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_forward_res<E, QT, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(k_backward_res<E, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  e = cudaFuncSetAttribute(k_backward_res<E, QT, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_propagate_res<E, QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaFuncSetAttribute(k_propagate_res<E, QT, GM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
 }
 
-// Kernel instantiations: element count per thread E, and for E == 1 the
-// compile-time subsystem count QT of the per-thread plan (0 = generic path).
-template <int E, int QT>
+// Kernel instantiations: element count per thread E, for E == 1 the
+// compile-time subsystem count QT of the per-thread plan (0 = generic path),
+// and GM for the variants that can run GMRES (generic path only).
+template <int E, int QT, bool GM = false>
 struct ResKernels {
   static cudaError_t fwd(dim3 g, dim3 b, size_t sm, cudaStream_t s, const ProbDev* p, const WorkItem* it, int tape) {
-    cudaError_t e = set_smem_attr<E, QT>(sm);
+    cudaError_t e = set_smem_attr<E, QT, GM>(sm);
     if (e != cudaSuccess) return e;
-    k_forward_res<E, QT><<<g, b, sm, s>>>(p, it, tape);
+    k_forward_res<E, QT, GM><<<g, b, sm, s>>>(p, it, tape);
     return cudaGetLastError();
   }
   static cudaError_t bwd(dim3 g, dim3 b, size_t sm, cudaStream_t s, const ProbDev* p, const WorkItem* it) {
-    cudaError_t e = set_smem_attr<E, QT>(sm);
+    cudaError_t e = set_smem_attr<E, QT, GM>(sm);
     if (e != cudaSuccess) return e;
-    k_backward_res<E, QT><<<g, b, sm, s>>>(p, it);
+    k_backward_res<E, QT, GM><<<g, b, sm, s>>>(p, it);
     return cudaGetLastError();
   }
   static cudaError_t prop(dim3 g, dim3 b, size_t sm, cudaStream_t s, const ProbDev* p, int adj, int j0, int j1,
                           double2* x) {
-    cudaError_t e = set_smem_attr<E, QT>(sm);
+    cudaError_t e = set_smem_attr<E, QT, GM>(sm);
     if (e != cudaSuccess) return e;
-    k_propagate_res<E, QT><<<g, b, sm, s>>>(p, adj, j0, j1, x);
+    k_propagate_res<E, QT, GM><<<g, b, sm, s>>>(p, adj, j0, j1, x);
     return cudaGetLastError();
   }
 };
 
 #define LB_RES_DISPATCH(rc, CALL)                       \
   do {                                                  \
+    if ((rc).gmres) {                                   \
+      switch ((rc).E) {                                 \
+        case 1: return ResKernels<1, 0, true>::CALL;    \
+        case 2: return ResKernels<2, 0, true>::CALL;    \
+        case 4: return ResKernels<4, 0, true>::CALL;    \
+        case 8: return ResKernels<8, 0, true>::CALL;    \
+        default: return cudaErrorInvalidValue;          \
+      }                                                 \
+    }                                                   \
     if ((rc).E == 1) {                                  \
       switch ((rc).QT) {                                \
         case 1: return ResKernels<1, 1>::CALL;          \

@@ -40,7 +40,7 @@ def _stats_dict(s) -> dict:
             "phase_steps": list(s.phase_steps), "phase_iterations": list(s.phase_iterations),
             "ms_forward": s.ms_forward, "ms_backward": s.ms_backward,
             "sweep": {1: "resident", 2: "grid", 3: "cluster"}.get(s.sweep, s.sweep),
-            "solver": {1: "jacobi", 2: "neumann"}.get(s.solver, s.solver),
+            "solver": {1: "jacobi", 2: "neumann", 3: "gmres"}.get(s.solver, s.solver),
             "ckpt_every": s.ckpt_every}
 
 
@@ -185,7 +185,7 @@ class LindbladSystem:
         out = (c_int32 * 3)()
         L.check(self.lib.lb_autotune(self.h, _stream_handle(stream), int(probe_steps), out))
         names = {L.LB_SWEEP_RESIDENT: "resident", L.LB_SWEEP_GRID: "grid", L.LB_SWEEP_CLUSTER: "cluster"}
-        solvers = {L.LB_SOLVER_JACOBI: "jacobi", L.LB_SOLVER_NEUMANN: "neumann"}
+        solvers = {L.LB_SOLVER_JACOBI: "jacobi", L.LB_SOLVER_NEUMANN: "neumann", L.LB_SOLVER_GMRES: "gmres"}
         return {"sweep": names.get(out[0], out[0]), "solver": solvers.get(out[1], out[1]), "shape": out[2]}
 
     def set_timing(self, on: bool = True):

@@ -177,3 +177,24 @@ def test_grid_sweep_workspace_and_sweep_choice(lib):
         assert n.value <= (3 + 4 + 10 + 4) * state + 2 * 1024 * 1024
     finally:
         lib.lb_system_destroy(h)
+
+
+def test_gmres_is_accepted_and_never_grid(lib):
+    """GMRES is a valid solver; with it a system that AUTO would give grid
+    sweeps (N^2 = 1024, two states) keeps the one-CTA-per-state layout."""
+    p = W.random_problem(31, levels=(4, 4, 2), n_states=2, n_steps=20)
+    sizes = {}
+    for method in (L.LB_SOLVER_JACOBI, L.LB_SOLVER_GMRES):
+        h = _make(lib, p, K=10)
+        try:
+            L.check(lib.lb_solver_set(h, method, 1e-15, 200, 10))
+            t = colmajor(p.targets)
+            L.check(lib.lb_objective_set(h, 0, t.ctypes.data_as(c_void_p), 0.0))
+            n = c_size_t()
+            L.check(lib.lb_workspace_bytes(h, byref(n)))
+            sizes[method] = n.value
+        finally:
+            lib.lb_system_destroy(h)
+    V, M = 1024, 2
+    # grid sweeps add the four iteration buffers of M states each
+    assert sizes[L.LB_SOLVER_JACOBI] - sizes[L.LB_SOLVER_GMRES] >= 4 * 16 * M * V

@@ -397,8 +397,92 @@ def test_autotune_keeps_results():
     s = _sys(p)
     choice = s.autotune(probe_steps=10)
     assert choice["sweep"] in ("resident", "cluster", "grid")
-    assert choice["solver"] in ("jacobi", "neumann")
+    assert choice["solver"] in ("jacobi", "neumann", "gmres")
     G, g = s.gradient()
     Go, go, _ = imr.gradient(p)
     assert abs(G - Go) <= 1e-10 * abs(Go)
     assert _rel(g, go) < 1e-9
+
+
+# ----------------------------------------------------------------------------
+# GMRES inner solve (one CTA per state, Krylov basis in shared memory)
+
+
+@pytest.mark.parametrize("levels,K,herm", [((2,), 7, False), ((2, 3), 0, True), ((3, 3), 100, False),
+                                            ((2, 2, 2, 2), 5, True), ((4, 4, 2), 10, False)])
+def test_gmres_matches_oracle(levels, K, herm):
+    """GMRES against the oracle (1e-10 / 1e-9) and against Jacobi, for one to
+    eight elements per thread ((4, 4, 2): N^2 = 1024)."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(801, levels=levels, n_states=2, n_steps=30, T_ns=0.6, amp=0.1, ckpt_every=K,
+                         hermitian=herm, objective="trace" if herm else "frob", gamma2=0.05)
+    s, g = _check_problem(p, solver=L.LB_SOLVER_GMRES)
+    st = s.stats()
+    assert st["solver"] == "gmres" and st["sweep"] == "resident"
+    Gj, gj = _sys(p, solver=L.LB_SOLVER_JACOBI, sweep=L.LB_SWEEP_RESIDENT).gradient()
+    assert _rel(g, gj) < 1e-11
+
+
+def _stiff_problem():
+    # dt = 0.2 ns with 0.3 GHz amplitudes: the Jacobi iteration matrix has
+    # spectral radius above 1 on the later steps, GMRES(20) converges
+    return W.random_problem(802, levels=(3, 3), n_states=2, n_steps=10, T_ns=2.0, amp=0.3, ckpt_every=3)
+
+
+def test_gmres_converges_where_fixed_point_diverges():
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = _stiff_problem()
+    with pytest.raises(L.LBError) as e:
+        _sys(p, solver=L.LB_SOLVER_JACOBI, max_iter=400, sweep=L.LB_SWEEP_RESIDENT).forward()
+    assert e.value.code in (L.LB_ENOTCONV, L.LB_ENAN)
+    s, _ = _check_problem(p, solver=L.LB_SOLVER_GMRES, max_iter=400)
+    st = s.stats()
+    assert st["max_iterations"] < 400
+
+
+def test_gmres_checkpoints_bitwise_and_steps():
+    """Deterministic reductions: checkpoint intervals give bit-identical
+    gradients; lb_propagate steps match the oracle's dense LU."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(803, levels=(3, 2), n_states=2, n_steps=24, T_ns=0.5, amp=0.1)
+    res = [_sys(p, ckpt_every=K, solver=L.LB_SOLVER_GMRES).gradient() for K in (1, 5, 100)]
+    for G, g in res[1:]:
+        assert G == res[0][0]
+        assert np.array_equal(g, res[0][1])
+    p2 = _stiff_problem()
+    s = _sys(p2, solver=L.LB_SOLVER_GMRES, max_iter=400)
+    mdl = model.Model(p2.system, p2.controls)
+    X = _rand_states(np.random.default_rng(4), 2, mdl.N)
+    got = s.propagate(torch.from_numpy(X).cuda(), 6, 10).cpu().numpy()
+    Q = model.vec(X).T.copy()
+    for j in range(6, 10):
+        Q, _ = imr.imr_step(mdl, j, Q)
+    assert _rel(got, np.stack([model.unvec(Q[:, i], mdl.N) for i in range(2)])) < 1e-12
+
+
+def test_batch_with_gmres_members():
+    """A batch whose members mix GMRES and Jacobi runs the GMRES-capable
+    kernels for all of them and matches the per-problem launches."""
+    from paper_2110_10310_gb300 import _lib as L
+    from paper_2110_10310_gb300.system import LindbladBatch
+
+    shapes = [(2,), (2, 3), (3, 3), (2, 2, 2), (4,), (3, 2)]
+    probs = [W.random_problem(810 + i, levels=lv, n_states=2, n_steps=30, T_ns=0.6, amp=0.1)
+             for i, lv in enumerate(shapes)]
+    systems = [_sys(p, sweep=L.LB_SWEEP_RESIDENT,
+                    solver=L.LB_SOLVER_GMRES if i % 2 else L.LB_SOLVER_JACOBI) for i, p in enumerate(probs)]
+    plain = [s.gradient() for s in systems]
+    Gb, gb = LindbladBatch(systems).gradient()
+    off = 0
+    for i, (G, g) in enumerate(plain):
+        assert abs(Gb[i] - G) <= 1e-12 * abs(G)
+        assert _rel(gb[off:off + len(g)], g) < 1e-10
+        off += len(g)
+    for i in (1, 2):
+        Go, go, _ = imr.gradient(probs[i])
+        off = sum(len(plain[k][1]) for k in range(i))
+        assert abs(Gb[i] - Go) <= 1e-10 * abs(Go)
+        assert _rel(gb[off:off + len(go)], go) < 1e-9

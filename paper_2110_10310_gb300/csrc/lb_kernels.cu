@@ -1146,6 +1146,13 @@ struct ClLanes {
 
 constexpr long long kMbarSpinLimit = 1LL << 24;
 
+// first-iterate predictor of the cluster sweeps: extrapolation order and the
+// weights (-1)^(i+1) binom(n, i) of c_{j-i}, i = 1..n, for each order n
+constexpr int kPredOrder = 6;
+__constant__ double kExtrap[kPredOrder + 1][kPredOrder] = {
+    {0, 0, 0, 0, 0, 0},       {1, 0, 0, 0, 0, 0},        {2, -1, 0, 0, 0, 0},     {3, -3, 1, 0, 0, 0},
+    {4, -6, 4, -1, 0, 0},     {5, -10, 10, -5, 1, 0},    {6, -15, 20, -15, 6, -1}};
+
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
@@ -1194,8 +1201,7 @@ struct ClSmem {
   double2* ll;               // [V] adjoint state replica (backward sweep)
   double2* dv;               // [V] (I - dt/2 D)^-1, or dt/2 D for Neumann
   double2* hd;               // [V] dt/2 D
-  double2* c1;               // [V] off-diagonal correction of the previous step (predictor)
-  double2* c2;               // [V] ... of the step before
+  double2* ch;               // [kPredOrder][V] ring of the previous steps' off-diagonal corrections
   unsigned* dsl;             // [2][32] warp maxima of |z_new - z| received, index cta * 4 + warp
   unsigned* qsl;             // [32] this CTA's warp maxima of |rhs|
   unsigned long long* mbar;  // [2]
@@ -1207,7 +1213,7 @@ __host__ __device__ inline size_t cl_smem_bytes(int ncoef, int njcoef, int N, in
   b += align16(sizeof(double) * 2 * ncoef);
   b += align16(sizeof(double) * 2 * njcoef);
   b += align16(sizeof(uint32_t) * N);
-  b += sizeof(double2) * 8 * (size_t)V;
+  b += sizeof(double2) * (6 + kPredOrder) * (size_t)V;
   b += align16(sizeof(unsigned) * 64);
   b += align16(sizeof(unsigned) * 32);
   b += align16(sizeof(unsigned long long) * 2);
@@ -1233,9 +1239,8 @@ __device__ ClSmem cl_carve(unsigned char* base, int ncoef, int njcoef, int N, in
   S.ll = S.rr + V;
   S.dv = S.ll + V;
   S.hd = S.dv + V;
-  S.c1 = S.hd + V;
-  S.c2 = S.c1 + V;
-  o += sizeof(double2) * 8 * (size_t)V;
+  S.ch = S.hd + V;
+  o += sizeof(double2) * (6 + kPredOrder) * (size_t)V;
   S.dsl = reinterpret_cast<unsigned*>(base + o);
   o += align16(sizeof(unsigned) * 64);
   S.qsl = reinterpret_cast<unsigned*>(base + o);
@@ -1334,48 +1339,62 @@ __device__ ClPlan cl_plan(const ClSmem& S, int C, int crank) {
 // iteration and mbarrier phase counters; identical in every thread of the cluster
 struct ClCount {
   unsigned gk = 0;                // inner iterations so far (selects buffer and mbarrier parity)
-  unsigned ph[2] = {0u, 0u};      // completed phases of mbar[0], mbar[1] (mod 2)
+  unsigned ph = 0u;               // bit b: completed phases of mbar[b] (mod 2)
 };
 
 // Solve (I - dt/2 M) z = rhs (ADJ: M^+) for the cluster's state, rhs given by
 // the replica `rr`.  Returns the iteration count, -1 (max_iter), -2 (NaN/Inf)
 // or -3 (a wait gave up).  On success S.zb + (gk & 1) * V holds z in every
 // CTA, and zout the lane's element of it.
-// Predictor of the off-diagonal correction c = (I - dt/2 D) z - rhs of a step
-// from the two previous steps: nh = number of usable previous steps (0, 1, 2).
-__device__ __forceinline__ double2 cl_predict(const ClSmem& S, int e, int nh) {
-  if (nh <= 0) return make_double2(0.0, 0.0);
-  const double2 a = S.c1[e];
-  if (nh == 1) return a;
-  const double2 b = S.c2[e];
-  return make_double2(fma(2.0, a.x, -b.x), fma(2.0, a.y, -b.y));
+// Predictor of the off-diagonal correction c = (I - dt/2 D) z - rhs of a step:
+// the polynomial extrapolation through the last n recorded corrections,
+// c_j ~ sum_i (-1)^(i+1) binom(n, i) c_{j-i}, n = min(steps recorded,
+// kPredOrder).  hist.slot is where the next correction will be recorded.
+struct ClHist {
+  int n = 0;     // corrections recorded so far (capped at kPredOrder)
+  int slot = 0;  // ring position of the next record
+  __device__ void advance() {
+    n = n < kPredOrder ? n + 1 : kPredOrder;
+    slot = slot + 1 < kPredOrder ? slot + 1 : 0;
+  }
+};
+__device__ __forceinline__ double2 cl_predict(const ClSmem& S, int e, ClHist h, int V) {
+  double pr = 0.0, pi = 0.0;
+  int sl = h.slot;
+  for (int i = 1; i <= h.n; ++i) {
+    sl = sl > 0 ? sl - 1 : kPredOrder - 1;
+    const double w = kExtrap[h.n][i - 1];
+    const double2 c = S.ch[(size_t)sl * V + e];
+    pr = fma(w, c.x, pr);
+    pi = fma(w, c.y, pi);
+  }
+  return make_double2(pr, pi);
 }
 
-// After a converged step, record c = (I - dt/2 D) z - rhs for every element
-// of the replica (identical in every CTA): c2 <- c1, c1 <- c.
+// After a converged step, record c = (I - dt/2 D) z - rhs for element e of
+// the replica (identical in every CTA) in ring slot h.slot.  Called from the
+// loop that forms the next right-hand side, with the step's z and rhs.
 template <bool ADJ>
-__device__ __forceinline__ void cl_record(const ClSmem& S, const double2* __restrict__ zf,
-                                          const double2* __restrict__ rr, int V) {
-  for (int e = threadIdx.x; e < V; e += blockDim.x) {
-    const double2 z = zf[e], r = rr[e], d = S.hd[e];
-    const double di = ADJ ? -d.y : d.y;
-    // (I - dt/2 D) z - rhs
-    const double cr = z.x - fma(d.x, z.x, -di * z.y) - r.x;
-    const double ci = z.y - fma(d.x, z.y, di * z.x) - r.y;
-    S.c2[e] = S.c1[e];
-    S.c1[e] = make_double2(cr, ci);
-  }
+__device__ __forceinline__ void cl_record(const ClSmem& S, int e, double2 z, double2 r, ClHist h, int V) {
+  const double2 d = S.hd[e];
+  const double di = ADJ ? -d.y : d.y;
+  // (I - dt/2 D) z - rhs
+  const double cr = z.x - fma(d.x, z.x, -di * z.y) - r.x;
+  const double ci = z.y - fma(d.x, z.y, di * z.x) - r.y;
+  S.ch[(size_t)h.slot * V + e] = make_double2(cr, ci);
 }
 
 template <int QT, bool ADJ>
 __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __restrict__ rr,
                         const double2* __restrict__ ct, int C, int crank, ClCount& cnt, double2& zout,
-                        int nh = 0) {
+                        ClHist hist = ClHist()) {
   constexpr int L = ClLanes<QT>::L;
   const Hdr& H = *S.hdr;
   const int V = H.V;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const bool neumann = H.method == LB_SOLVER_NEUMANN;
+  // the step's control factor, loaded first so that its latency overlaps z_0
+  const double2 c = ct[pl.q];
   // z_0 for all elements of the local replica, and max |rhs|
   {
     double2* z0b = S.zb + (size_t)(cnt.gk & 1) * V;
@@ -1386,7 +1405,7 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
       if (!neumann) {
         const double2 d = S.dv[e];
         const double di = ADJ ? -d.y : d.y;
-        const double2 pc = cl_predict(S, e, nh);
+        const double2 pc = cl_predict(S, e, hist, V);
         const double ur = r.x + pc.x, ui = r.y + pc.y;
         z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
       }
@@ -1402,17 +1421,28 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
   if (qmax >= kInfHi) return -2;
   const unsigned thr = hi_abs(H.rtol * __longlong_as_double(static_cast<long long>((unsigned long long)qmax << 32)));
   // this lane's complex factor: -i d P -> (b - i a) P, -i conj(d) R -> (-b - i a) R
-  const double2 c = ct[pl.q];
   double Ar = pl.rhalf ? -c.y : c.y, Ai = -c.x;
   if (ADJ) {
     Ar = -Ar;
     Ai = -Ai;
   }
   const double di = ADJ ? -pl.d.y : pl.d.y;
+  const bool odd = pl.r & 1;
+  const double sdi = odd ? di : -di;
   const double2 rhs = rr[pl.v];
   const double cj = ADJ ? pl.cja : pl.cjf;
   const int oj = ADJ ? pl.oja : pl.ojf;
   const unsigned tx = (unsigned)V * 16u + (unsigned)(C * nwarps) * 4u;
+  // cluster addresses used every iteration, per buffer parity: this lane's
+  // element in CTA pl.r (its first store target) with that CTA's mbarrier,
+  // and this warp's maximum slot in CTA `lane` with that CTA's mbarrier
+  const unsigned rr0 = pl.r < C ? pl.r : 0, lr = lane < C ? lane : 0;
+  const unsigned zb_rem0 = mapa_u32(smem_u32(S.zb + pl.v), rr0);
+  const unsigned zb_rem1 = mapa_u32(smem_u32(S.zb + (size_t)V + pl.v), rr0);
+  const unsigned mb_rem0 = mapa_u32(smem_u32(&S.mbar[0]), rr0), mb_rem1 = mapa_u32(smem_u32(&S.mbar[1]), rr0);
+  const unsigned dsl_rem0 = mapa_u32(smem_u32(S.dsl + crank * 4 + warp), lr);
+  const unsigned dsl_rem1 = mapa_u32(smem_u32(S.dsl + 32 + crank * 4 + warp), lr);
+  const unsigned mb_lane0 = mapa_u32(smem_u32(&S.mbar[0]), lr), mb_lane1 = mapa_u32(smem_u32(&S.mbar[1]), lr);
   for (int it = 0; it < H.max_iter; ++it) {
     const unsigned p = (cnt.gk + 1) & 1;
     const unsigned mb_local = smem_u32(&S.mbar[p]);
@@ -1425,43 +1455,45 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
     double acci = fma(Ar, xi, Ai * xr);
     accr = fma(cj, x5.x, accr);
     acci = fma(cj, x5.y, acci);
+    // Sum over the element's L lanes with one component per lane: after the
+    // first exchange even lanes carry the real and odd lanes the imaginary
+    // part, so each level costs one FP64 add, and so does each later step.
+    double k = odd ? acci : accr;
+    k += __shfl_xor_sync(kFull, odd ? accr : acci, 1);
 #pragma unroll
-    for (int o = 1; o < L; o <<= 1) {
-      accr += __shfl_xor_sync(kFull, accr, o);
-      acci += __shfl_xor_sync(kFull, acci, o);
-    }
-    const double ar = rhs.x + accr, ai = rhs.y + acci;
-    double2 z;
+    for (int o = 2; o < L; o <<= 1) k += __shfl_xor_sync(kFull, k, o);
+    const double am = (odd ? rhs.y : rhs.x) + k;  // this lane's component of rhs + dt/2 O z
+    const double zom = odd ? zo.y : zo.x;
+    double zm;
     if (!neumann) {
-      z.x = fma(pl.d.x, ar, -di * ai);
-      z.y = fma(pl.d.x, ai, di * ar);
+      // real: d.x ar - di ai, imaginary: d.x ai + di ar
+      zm = fma(pl.d.x, am, sdi * __shfl_xor_sync(kFull, am, 1));
     } else {
-      z.x = ar + fma(pl.d.x, zo.x, -di * zo.y);
-      z.y = ai + fma(pl.d.x, zo.y, di * zo.x);
+      zm = am + fma(pl.d.x, zom, sdi * __shfl_xor_sync(kFull, zom, 1));
     }
+    const double zp = __shfl_xor_sync(kFull, zm, 1);
+    const double2 z = odd ? make_double2(zp, zm) : make_double2(zm, zp);
     // push the element into every CTA's next buffer; the element's lanes share the C stores
-    if (pl.ev) {
+    if (pl.ev && pl.r < C) {
+      st_async_f64x2(p ? zb_rem1 : zb_rem0, z.x, z.y, p ? mb_rem1 : mb_rem0);
       const unsigned dst = smem_u32(S.zb + (size_t)p * V + pl.v);
-      for (int cc = pl.r; cc < C; cc += L) st_async_f64x2(mapa_u32(dst, cc), z.x, z.y, mapa_u32(mb_local, cc));
+      for (int cc = pl.r + L; cc < C; cc += L) st_async_f64x2(mapa_u32(dst, cc), z.x, z.y, mapa_u32(mb_local, cc));
     }
-    unsigned dm = (pl.ev && pl.r == 0) ? max(hi_abs(z.x - zo.x), hi_abs(z.y - zo.y)) : 0u;
+    unsigned dm = (pl.ev && pl.r < 2) ? hi_abs(zm - zom) : 0u;
     dm = __reduce_max_sync(kFull, dm);
-    if (lane < C) {
-      const unsigned dst = smem_u32(S.dsl + p * 32 + crank * 4 + warp);
-      st_async_u32(mapa_u32(dst, lane), dm, mapa_u32(mb_local, lane));
-    }
+    if (lane < C) st_async_u32(p ? dsl_rem1 : dsl_rem0, dm, p ? mb_lane1 : mb_lane0);
     // wait for every CTA's pushes of this iteration (bounded); the vote keeps a
     // timeout, should one ever happen, a decision of the whole CTA
     long long spins = 0;
     int timed_out = 0;
-    while (!mbar_try_wait(mb_local, cnt.ph[p])) {
+    while (!mbar_try_wait(mb_local, (cnt.ph >> p) & 1u)) {
       if (++spins > kMbarSpinLimit) {
         timed_out = 1;
         break;
       }
     }
     if (__syncthreads_or(timed_out)) return -3;
-    cnt.ph[p] ^= 1u;
+    cnt.ph ^= 1u << p;
     ++cnt.gk;
     unsigned dmax = 0;
     const uint4* d4 = reinterpret_cast<const uint4*>(S.dsl + p * 32);
@@ -1481,7 +1513,7 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
 __device__ __forceinline__ int cl_code(int it) { return it == -1 ? LB_ENOTCONV : (it == -2 ? LB_ENAN : LB_ECUDA); }
 
 template <int QT>
-__global__ void __launch_bounds__(128) k_forward_cl(const ProbDev* __restrict__ pp, int tape) {
+__global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict__ pp, int tape) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
   const ProbDev& P = *pp;
@@ -1499,12 +1531,12 @@ __global__ void __launch_bounds__(128) k_forward_cl(const ProbDev* __restrict__ 
   // the predictor is used only when no step is ever recomputed (K == 0), so
   // recomputed stage vectors stay bit-identical to the forward ones
   const bool pred = H.K == 0 && H.method != LB_SOLVER_NEUMANN;
-  int nh = 0;
+  ClHist hist;
   for (int j = 0; j < H.NT; ++j) {
     if (tape && H.K > 0 && j % H.K == 0 && crank == 0)
       for (int e = threadIdx.x; e < H.V; e += blockDim.x) P.ckpt[((size_t)i * H.n_ckpt + j / H.K) * H.V + e] = S.rr[e];
     double2 z;
-    const int it = cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, C, crank, cnt, z, pred ? nh : 0);
+    const int it = cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, C, crank, cnt, z, pred ? hist : ClHist());
     if (it < 0) {
       if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
       failed = true;
@@ -1513,15 +1545,13 @@ __global__ void __launch_bounds__(128) k_forward_cl(const ProbDev* __restrict__ 
     if (crank == 0) stats.add(0, it);
     // q^{j+1} = 2 z - q^j on the whole replica (identical in every CTA)
     const double2* zf = S.zb + (size_t)(cnt.gk & 1) * H.V;
-    if (pred) {
-      cl_record<false>(S, zf, S.rr, H.V);
-      nh = nh < 2 ? nh + 1 : 2;
-    }
     for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
       const double2 zz = zf[e], qq = S.rr[e];
+      if (pred) cl_record<false>(S, e, zz, qq, hist, H.V);
       if (tape && H.K == 0 && crank == 0) P.ckpt[((size_t)i * H.NT + j) * H.V + e] = zz;
       S.rr[e] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
     }
+    if (pred) hist.advance();
   }
   if (!failed && crank == 0) {
     double acc = 0.0;
@@ -1550,7 +1580,7 @@ __global__ void __launch_bounds__(128) k_forward_cl(const ProbDev* __restrict__ 
 }
 
 template <int QT>
-__global__ void __launch_bounds__(128) k_backward_cl(const ProbDev* __restrict__ pp) {
+__global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restrict__ pp) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
   constexpr int L = ClLanes<QT>::L;
@@ -1581,7 +1611,7 @@ __global__ void __launch_bounds__(128) k_backward_cl(const ProbDev* __restrict__
   // the adjoint sweep visits the steps in the same order for every K, so its
   // predictor history never depends on the checkpoint interval
   const bool apred = H.method != LB_SOLVER_NEUMANN;
-  int nha = 0;
+  ClHist ahist;
   // gradient pieces of this CTA go to state slot i * C + crank of gproj
   double2* gbase = P.gproj + (size_t)(i * C + crank) * H.NT * H.Q * 2;
   for (int sg = nseg - 1; sg >= 0 && !failed; --sg) {
@@ -1610,7 +1640,7 @@ __global__ void __launch_bounds__(128) k_backward_cl(const ProbDev* __restrict__
     }
     for (int j = j1 - 1; j >= j0; --j) {
       double2 zh;
-      const int it = cl_solve<QT, true>(S, pl, S.ll, P.ctab + (size_t)j * H.Q, C, crank, cnt, zh, apred ? nha : 0);
+      const int it = cl_solve<QT, true>(S, pl, S.ll, P.ctab + (size_t)j * H.Q, C, crank, cnt, zh, apred ? ahist : ClHist());
       if (it < 0) {
         if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
         failed = true;
@@ -1618,10 +1648,6 @@ __global__ void __launch_bounds__(128) k_backward_cl(const ProbDev* __restrict__
       }
       if (crank == 0) stats.add(2, it);
       const double2* zb = S.zb + (size_t)(cnt.gk & 1) * H.V;
-      if (apred) {
-        cl_record<true>(S, zb, S.ll, H.V);
-        nha = nha < 2 ? nha + 1 : 2;
-      }
       // gradient piece of this lane's half (eq. reducedgradient): sum_kl Z conj(X_zhat),
       // X the half's neighbour combination of zhat; P half -> g_ad, R half -> g_a
       double sr = 0.0, si = 0.0;
@@ -1657,8 +1683,10 @@ __global__ void __launch_bounds__(128) k_backward_cl(const ProbDev* __restrict__
       // qhat^j = 2 zhat - qhat^{j+1} on the whole replica
       for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
         const double2 zz = zb[e], ll = S.ll[e];
+        if (apred) cl_record<true>(S, e, zz, ll, ahist, H.V);
         S.ll[e] = make_double2(fma(2.0, zz.x, -ll.x), fma(2.0, zz.y, -ll.y));
       }
+      if (apred) ahist.advance();
     }
   }
   stats.flush(P.status);
@@ -1666,7 +1694,7 @@ __global__ void __launch_bounds__(128) k_backward_cl(const ProbDev* __restrict__
 }
 
 template <int QT>
-__global__ void __launch_bounds__(128) k_propagate_cl(const ProbDev* __restrict__ pp, int adjoint, int j0, int j1,
+__global__ void __launch_bounds__(128, 1) k_propagate_cl(const ProbDev* __restrict__ pp, int adjoint, int j0, int j1,
                                                       double2* __restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();

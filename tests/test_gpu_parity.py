@@ -349,6 +349,43 @@ def test_qudits_4x4_gradient_against_gpu_central_differences():
     s.set_alpha(a0)
 
 
+@pytest.mark.slow
+def test_qudits_4x4_reduced_to_qubits_matches_oracle():
+    """Workload 4's structure (4 subsystems, chain cross-Kerr, 2 carriers x 30
+    splines, dt = 0.0125 ns, checkpoints every 100) with 2 levels per
+    subsystem (N^2 = 256), on the grid sweep that runs the full-size
+    workload, over the first 4000 steps: states, objective and gradient
+    against the oracle's dense LU steps."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.config4(levels=(2, 2, 2, 2), n_states=3, n_steps=4000)
+    p.system.T_ns = 500.0 * 4000 / 40000
+    _check_problem(p, sweep=L.LB_SWEEP_GRID)
+
+
+@pytest.mark.slow
+def test_qutrits_6x3_reduced_to_qubits_matches_oracle():
+    """Workload 5's structure (6 subsystems, ring cross-Kerr, 2 carriers x 40
+    splines, dt = 0.015 ns) with 2 levels per subsystem (N^2 = 4096, the
+    grid sweep), two steps against the oracle (a dense 4096 x 4096 LU per
+    step)."""
+    p = W.config5(levels=(2,) * 6, n_states=2, n_steps=2)
+    p.system.T_ns = 300.0 * 2 / 20000
+    s, _ = _check_problem(p)
+    assert s.stats()["sweep"] == "grid"
+
+
+def test_qudits_4x4_full_size_checkpoints_bitwise():
+    """Full-size workload 4 states (N^2 = 65536) over 200 steps at its dt:
+    checkpoint intervals 1 and 100 give bit-identical objective and gradient."""
+    p = W.config4(n_steps=200)
+    p.system.T_ns = 500.0 * 200 / 40000
+    G1, g1 = _sys(p, ckpt_every=1).gradient()
+    G2, g2 = _sys(p, ckpt_every=100).gradient()
+    assert G1 == G2
+    assert np.array_equal(g1, g2)
+
+
 # ----------------------------------------------------------------------------
 # cluster-split sweeps (one cluster per state, 2Q lanes per element)
 

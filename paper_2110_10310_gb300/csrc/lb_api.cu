@@ -46,7 +46,7 @@ struct Region {
 
 struct Layout {
   Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
-      gproj, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar;
+      gproj, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist;
   size_t total = 0;
 };
 
@@ -253,6 +253,7 @@ Layout make_layout(const lb_system* s) {
   take(L.partials, grid ? sizeof(double) * lbk::kMaxGridBlocks * LB_MAXQ * 4 : 0);
   take(L.gslots, grid ? sizeof(unsigned long long) * 5 * M : 0);
   take(L.bar, grid ? sizeof(GridBar) : 0);
+  take(L.hist, c2 * lbk::kPredOrder * M * V);
   L.total = off;
   return L;
 }
@@ -406,6 +407,7 @@ void fill_prob(lb_system* s) {
     P.gslots = at<unsigned long long>(s, s->L.gslots);
     P.bar = at<GridBar>(s, s->L.bar);
   }
+  P.hist = at<double2>(s, s->L.hist);
 }
 
 int ensure_ctab(lb_system* s, cudaStream_t st) {

@@ -86,6 +86,7 @@ struct ProbDev {
   double* partials;          // [grid_blocks][LB_MAXQ][4] gradient pieces per block
   unsigned long long* gslots;  // [3][M] per-state |z_new - z| maxima, then [2][M] per-state |q| maxima
   GridBar* bar;
+  double2* hist;             // [kPredOrder][M*V] first-iterate predictor history (grid and one-CTA sweeps)
 };
 
 // one work item of a resident launch: (problem, state)
@@ -97,6 +98,7 @@ struct WorkItem {
 namespace lbk {
 
 constexpr int kMaxResidentV = 4096;  // states held in one CTA's shared memory
+constexpr int kPredOrder = 6;        // extrapolation order of the first-iterate predictor
 
 struct ResidentConfig {
   int threads;  // CTA size (multiple of 32, <= 512)

@@ -87,6 +87,15 @@ __device__ __forceinline__ double warp_sum2(double a, double b, int lane) {
   return k;
 }
 
+// First-iterate predictor of every sweep: the off-diagonal correction
+// c_j = (I - dt/2 D) z^j - rhs^j of a step is extrapolated by the polynomial
+// through the last n recorded ones, c_j ~ sum_{i=1..n} (-1)^(i+1) binom(n, i)
+// c_{j-i}, n <= kPredOrder; the table holds these weights for each n.
+static_assert(kPredOrder == 6, "the weight table below is written for order 6");
+__constant__ double kExtrap[kPredOrder + 1][kPredOrder] = {
+    {0, 0, 0, 0, 0, 0},       {1, 0, 0, 0, 0, 0},        {2, -1, 0, 0, 0, 0},     {3, -3, 1, 0, 0, 0},
+    {4, -6, 4, -1, 0, 0},     {5, -10, 10, -5, 1, 0},    {6, -15, 20, -15, 6, -1}};
+
 // quadratic B-spline of unit knot spacing centred at 0 (Sec. II, eq. rotctrl)
 __device__ __forceinline__ double bspline2(double x) {
   x = fabs(x);
@@ -503,32 +512,40 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
   return -1;
 }
 
-// Predictor of the first iterate: off-diagonal corrections c = (I - dt/2 D) z
-// - rhs of the two previous steps, per owned element, extrapolated linearly.
+// Predictor of the first iterate for one CTA's state: the corrections of the
+// previous steps live in the ring P.hist ([kPredOrder][M * V], this state's
+// elements at base + v); every element is read and written by the thread that
+// owns it, so no synchronisation is needed.
 template <int E>
 struct Pred {
-  double2 c1[E], c2[E], hd[E];
-  int nh = 0;
-  __device__ void init(const ProbDev& P, int V) {
-    const double hh = 0.5 * P.h;
+  double2* hist = nullptr;
+  const double2* D = nullptr;
+  size_t stride = 0;
+  double hh = 0.0;
+  int n = 0, slot = 0;
+  __device__ void init(const ProbDev& P, size_t base) {
+    hist = P.hist + base;
+    D = P.D;
+    stride = (size_t)P.M * P.V;
+    hh = 0.5 * P.h;
+    n = slot = 0;
+  }
+  __device__ void predict(double2 (&pc)[E], int V) const {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int v = threadIdx.x + e * blockDim.x;
-      const double2 D = v < V ? P.D[v] : make_double2(0.0, 0.0);
-      hd[e] = make_double2(hh * D.x, hh * D.y);
-      c1[e] = c2[e] = make_double2(0.0, 0.0);
-    }
-    nh = 0;
-  }
-  __device__ void predict(double2 (&pc)[E]) const {
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      if (nh <= 0)
-        pc[e] = make_double2(0.0, 0.0);
-      else if (nh == 1)
-        pc[e] = c1[e];
-      else
-        pc[e] = make_double2(fma(2.0, c1[e].x, -c2[e].x), fma(2.0, c1[e].y, -c2[e].y));
+      double pr = 0.0, pi = 0.0;
+      if (v < V) {
+        int sl = slot;
+        for (int i = 1; i <= n; ++i) {
+          sl = sl > 0 ? sl - 1 : kPredOrder - 1;
+          const double w = kExtrap[n][i - 1];
+          const double2 c = hist[(size_t)sl * stride + v];
+          pr = fma(w, c.x, pr);
+          pi = fma(w, c.y, pi);
+        }
+      }
+      pc[e] = make_double2(pr, pi);
     }
   }
   template <bool ADJ>
@@ -537,14 +554,14 @@ struct Pred {
     for (int e = 0; e < E; ++e) {
       const int v = threadIdx.x + e * blockDim.x;
       if (v < V) {
-        const double2 z = zc[v];
-        const double di = ADJ ? -hd[e].y : hd[e].y;
-        c2[e] = c1[e];
-        c1[e] = make_double2(z.x - fma(hd[e].x, z.x, -di * z.y) - rhs[e].x,
-                             z.y - fma(hd[e].x, z.y, di * z.x) - rhs[e].y);
+        const double2 z = zc[v], d = __ldg(D + v);
+        const double dr = hh * d.x, di = hh * (ADJ ? -d.y : d.y);
+        hist[(size_t)slot * stride + v] = make_double2(z.x - fma(dr, z.x, -di * z.y) - rhs[e].x,
+                                                       z.y - fma(dr, z.y, di * z.x) - rhs[e].y);
       }
     }
-    nh = nh < 2 ? nh + 1 : 2;
+    n = n < kPredOrder ? n + 1 : kPredOrder;
+    slot = slot + 1 < kPredOrder ? slot + 1 : 0;
   }
 };
 
@@ -841,10 +858,9 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
   CtaStats stats;
   // predictor only when no step is ever recomputed (K == 0): recomputed stage
   // vectors then stay bit-identical to the forward ones
-  // (its per-element history lives in registers: up to 2 elements per thread)
-  const bool pred = E <= 2 && H.K == 0 && H.method != LB_SOLVER_NEUMANN;
-  Pred<E <= 2 ? E : 1> pr;
-  if (pred) pr.init(P, H.V);
+  const bool pred = H.K == 0 && H.method != LB_SOLVER_NEUMANN;
+  Pred<E> pr;
+  if (pred) pr.init(P, base);
   double2 pc[E];
   for (int j = 0; j < H.NT; ++j) {
     if (tape && H.K > 0 && j % H.K == 0) {
@@ -856,9 +872,7 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
       }
     }
     int cur;
-    if constexpr (E <= 2) {
-      if (pred) pr.predict(pc);
-    }
+    if (pred) pr.predict(pc, H.V);
     const int it = res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur, pred ? pc : nullptr);
     if (it < 0) {
       if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
@@ -867,9 +881,7 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
     }
     stats.add(0, it);
     const double2* zc = cur ? S.zb1 : S.zb0;
-    if constexpr (E <= 2) {
-      if (pred) pr.template record<false>(zc, q, H.V);
-    }
+    if (pred) pr.template record<false>(zc, q, H.V);
     double2* tp = (tape && H.K == 0) ? P.ckpt + ((size_t)i * H.NT + j) * H.V : nullptr;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -945,9 +957,9 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
   CtaStats stats;
   const int nseg = H.K > 0 ? (H.NT + H.K - 1) / H.K : 1;
   // adjoint predictor: the adjoint steps come in the same order for every K
-  const bool apred = E <= 2 && H.method != LB_SOLVER_NEUMANN;
-  Pred<E <= 2 ? E : 1> pr;
-  if (apred) pr.init(P, H.V);
+  const bool apred = H.method != LB_SOLVER_NEUMANN;
+  Pred<E> pr;
+  if (apred) pr.init(P, base);
   double2 pc[E];
   for (int sg = nseg - 1; sg >= 0; --sg) {
     const int j0 = H.K > 0 ? sg * H.K : 0;
@@ -986,9 +998,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       const double2* ct = P.ctab + (size_t)j * H.Q;
       int cur;
       // (I - dt/2 (M^{j+1/2})^+) zhat^j = qhat^{j+1}   (eq. linsystem_adjoint)
-      if constexpr (E <= 2) {
-        if (apred) pr.predict(pc);
-      }
+      if (apred) pr.predict(pc, H.V);
       const int it = res_solve<E, QT, true, GM>(S, H, el, pl, lam, ct, cur, apred ? pc : nullptr);
       if (it < 0) {
         if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
@@ -997,9 +1007,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       }
       stats.add(2, it);
       const double2* zh = cur ? S.zb1 : S.zb0;
-      if constexpr (E <= 2) {
-        if (apred) pr.template record<true>(zh, lam, H.V);
-      }
+      if (apred) pr.template record<true>(zh, lam, H.V);
       const double2* Zt = H.K > 0 ? P.seg + ((size_t)i * H.K + (j - j0)) * H.V : P.ckpt + ((size_t)i * H.NT + j) * H.V;
       // gradient pieces (eq. reducedgradient): for every subsystem q,
       //   g_a  = zhat^H vec(-i[a_q, Z])   = -i sum_kl Z_kl conj(R_zhat)
@@ -1146,12 +1154,7 @@ struct ClLanes {
 
 constexpr long long kMbarSpinLimit = 1LL << 24;
 
-// first-iterate predictor of the cluster sweeps: extrapolation order and the
-// weights (-1)^(i+1) binom(n, i) of c_{j-i}, i = 1..n, for each order n
-constexpr int kPredOrder = 6;
-__constant__ double kExtrap[kPredOrder + 1][kPredOrder] = {
-    {0, 0, 0, 0, 0, 0},       {1, 0, 0, 0, 0, 0},        {2, -1, 0, 0, 0, 0},     {3, -3, 1, 0, 0, 0},
-    {4, -6, 4, -1, 0, 0},     {5, -10, 10, -5, 1, 0},    {6, -15, 20, -15, 6, -1}};
+
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return static_cast<unsigned>(__cvta_generic_to_shared(p));
@@ -2132,9 +2135,32 @@ struct StateMax {
 // the banks of the per-state maxima.  Returns the iteration count, -1
 // (max_iter), -2 (NaN/Inf) or -3 (a barrier wait gave up); on success *zout
 // points at the buffer holding z.
+// First-iterate predictor of the grid sweeps: the off-diagonal corrections
+// c = (I - dt/2 D) z - rhs of the last n steps, kept per element in the ring
+// P.hist (each element always handled by the same thread, so no
+// synchronisation is needed), extrapolated as in the cluster sweeps.
+struct GridHist {
+  int n = 0, slot = 0;
+  __device__ void advance() {
+    n = n < kPredOrder ? n + 1 : kPredOrder;
+    slot = slot + 1 < kPredOrder ? slot + 1 : 0;
+  }
+};
+
+template <bool ADJ>
+__device__ __forceinline__ void grid_record(const ProbDev& P, long long total, GridHist h, long long e, int v,
+                                            double hh, double2 z, double2 r) {
+  const double2 D = __ldg(P.D + v);
+  const double dr = hh * D.x, di = hh * (ADJ ? -D.y : D.y);
+  const double cr = z.x - fma(dr, z.x, -di * z.y) - r.x;
+  const double ci = z.y - fma(dr, z.y, di * z.x) - r.y;
+  P.hist[(size_t)h.slot * total + e] = make_double2(cr, ci);
+}
+
 template <bool ADJ>
 __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __restrict__ rhs,
-                          const double2* __restrict__ ct, long long& it_global, long long& solve, double2** zout) {
+                          const double2* __restrict__ ct, long long& it_global, long long& solve, double2** zout,
+                          GridHist hist = GridHist()) {
   const GridHdr& G = *S.g;
   const Hdr& H = G.h;
   const Tabs T{S.cu, S.cd, S.jf, S.ja};
@@ -2155,9 +2181,18 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
       const double2 r = rhs[e];
       double2 z0 = r;
       if (!neumann) {
+        double ur = r.x, ui = r.y;
+        int sl = hist.slot;
+        for (int i = 1; i <= hist.n; ++i) {
+          sl = sl > 0 ? sl - 1 : kPredOrder - 1;
+          const double w = kExtrap[hist.n][i - 1];
+          const double2 c = P.hist[(size_t)sl * G.total + e];
+          ur = fma(w, c.x, ur);
+          ui = fma(w, c.y, ui);
+        }
         const double2 d = __ldg(P.Dinv + v);
         const double di = ADJ ? -d.y : d.y;
-        z0 = make_double2(fma(d.x, r.x, -di * r.y), fma(d.x, r.y, di * r.x));
+        z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
       }
       P.zA[e] = z0;
       sm.add(b, umax64(abs_bits(r.x), abs_bits(r.y)), qbank);
@@ -2242,7 +2277,7 @@ __device__ void grid_fail(const ProbDev& P, int code, int step) {
 
 // mode 0: forward sweep on P.qT (from P.q0 if init), checkpoints if tape
 // mode 1: forward steps j0..j1-1 in place on x; mode 2: adjoint steps j1-1..j0 in place on x
-__global__ void __launch_bounds__(kGridThreads) k_sweep_grid(const ProbDev* __restrict__ pp, int mode, int init,
+__global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* __restrict__ pp, int mode, int init,
                                                              int tape, int j0, int j1, double2* __restrict__ x,
                                                              int nstates) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -2259,6 +2294,10 @@ __global__ void __launch_bounds__(kGridThreads) k_sweep_grid(const ProbDev* __re
   unsigned long long iters = 0, steps = 0;
   int maxit = 0;
   const int phase = mode == 2 ? 2 : 0;
+  // predictor only when no step is ever recomputed (K == 0), as in the other sweeps
+  const bool pred = mode == 0 && H.K == 0 && H.method != LB_SOLVER_NEUMANN;
+  const double hh = 0.5 * H.h;
+  GridHist hist;
   for (int jj = 0; jj < j1 - j0; ++jj) {
     const int j = mode == 2 ? j1 - 1 - jj : j0 + jj;
     if (mode == 0 && tape && H.K > 0 && j % H.K == 0) {
@@ -2269,7 +2308,8 @@ __global__ void __launch_bounds__(kGridThreads) k_sweep_grid(const ProbDev* __re
     }
     double2* z = nullptr;
     const int it = mode == 2 ? grid_solve<true>(P, S, q, P.ctab + (size_t)j * H.Q, itg, nsolve, &z)
-                             : grid_solve<false>(P, S, q, P.ctab + (size_t)j * H.Q, itg, nsolve, &z);
+                             : grid_solve<false>(P, S, q, P.ctab + (size_t)j * H.Q, itg, nsolve, &z,
+                                                 pred ? hist : GridHist());
     if (it < 0) {
       grid_fail(P, it, j);
       break;
@@ -2278,13 +2318,13 @@ __global__ void __launch_bounds__(kGridThreads) k_sweep_grid(const ProbDev* __re
     steps += G.M;
     maxit = max(maxit, it);
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const double2 zz = z[e];
-      if (mode == 0 && tape && H.K == 0) {
-        const int b = (int)(e / V), v = (int)(e - (long long)b * V);
-        P.ckpt[((size_t)b * H.NT + j) * V + v] = zz;
-      }
-      q[e] = make_double2(fma(2.0, zz.x, -q[e].x), fma(2.0, zz.y, -q[e].y));
+      const double2 zz = z[e], qq = q[e];
+      const int b = (int)(e / V), v = (int)(e - (long long)b * V);
+      if (mode == 0 && tape && H.K == 0) P.ckpt[((size_t)b * H.NT + j) * V + v] = zz;
+      if (pred) grid_record<false>(P, G.total, hist, e, v, hh, zz, qq);
+      q[e] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
     }
+    if (pred) hist.advance();
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     atomicAdd(&P.status->iters[phase], iters);
@@ -2295,7 +2335,7 @@ __global__ void __launch_bounds__(kGridThreads) k_sweep_grid(const ProbDev* __re
 
 // backward sweep over all states: recompute each checkpoint segment, then the
 // adjoint steps with the gradient pieces summed over states and blocks
-__global__ void __launch_bounds__(kGridThreads) k_backward_grid(const ProbDev* __restrict__ pp) {
+__global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev* __restrict__ pp) {
   extern __shared__ __align__(16) unsigned char smem[];
   const ProbDev& P = *pp;
   const GridSmem S = grid_setup(smem, P, P.M);
@@ -2321,6 +2361,10 @@ __global__ void __launch_bounds__(kGridThreads) k_backward_grid(const ProbDev* _
   int maxit = 0;
   const int nseg = H.K > 0 ? (H.NT + H.K - 1) / H.K : 1;
   bool failed = false;
+  // adjoint predictor: the adjoint steps come in the same order for every K
+  const bool apred = H.method != LB_SOLVER_NEUMANN;
+  const double hh = 0.5 * H.h;
+  GridHist ahist;
   for (int sg = nseg - 1; sg >= 0 && !failed; --sg) {
     const int j0 = H.K > 0 ? sg * H.K : 0;
     const int j1 = H.K > 0 ? min(H.NT, j0 + H.K) : H.NT;
@@ -2352,7 +2396,7 @@ __global__ void __launch_bounds__(kGridThreads) k_backward_grid(const ProbDev* _
     for (int j = j1 - 1; j >= j0; --j) {
       const double2* ct = P.ctab + (size_t)j * H.Q;
       double2* zh = nullptr;
-      const int it = grid_solve<true>(P, S, P.lam, ct, itg, nsolve, &zh);
+      const int it = grid_solve<true>(P, S, P.lam, ct, itg, nsolve, &zh, apred ? ahist : GridHist());
       if (it < 0) {
         grid_fail(P, it, j);
         failed = true;
@@ -2399,9 +2443,11 @@ __global__ void __launch_bounds__(kGridThreads) k_backward_grid(const ProbDev* _
       }
       // qhat^j = 2 zhat - qhat^{j+1}
       for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const double2 z = zh[e];
-        P.lam[e] = make_double2(fma(2.0, z.x, -P.lam[e].x), fma(2.0, z.y, -P.lam[e].y));
+        const double2 z = zh[e], ll = P.lam[e];
+        if (apred) grid_record<true>(P, G.total, ahist, e, (int)(e % V), hh, z, ll);
+        P.lam[e] = make_double2(fma(2.0, z.x, -ll.x), fma(2.0, z.y, -ll.y));
       }
+      if (apred) ahist.advance();
       if (!grid_sync(P.bar, gridDim.x)) {
         grid_fail(P, -3, j);
         failed = true;

@@ -151,8 +151,9 @@ def test_workspace_size_accounts_for_checkpoints(lib, K):
             tape = -(-NT // Kc) * state + Kc * state
         C = -(-Vl * 4 // 128)  # CTAs per state of the cluster sweep (2Q = 4 lanes per element)
         gproj = M * C * NT * 2 * 2 * 16
-        assert n.value >= tape + gproj + 3 * state
-        assert n.value <= tape + gproj + 3 * state + 64 * 1024
+        # q0, tar, qT and the six-step ring of the first-iterate predictor
+        assert n.value >= tape + gproj + (3 + 6) * state
+        assert n.value <= tape + gproj + (3 + 6) * state + 64 * 1024
     finally:
         lib.lb_system_destroy(h)
 
@@ -172,9 +173,10 @@ def test_grid_sweep_workspace_and_sweep_choice(lib):
         L.check(lib.lb_workspace_bytes(h, byref(n)))
         V, M = 81 * 81, 2
         state = 16 * M * V
-        # q0, tar, qT, 4 checkpoints, 10-step segment tape, zA, zB, lam, qf
-        assert n.value >= (3 + 4 + 10 + 4) * state
-        assert n.value <= (3 + 4 + 10 + 4) * state + 2 * 1024 * 1024
+        # q0, tar, qT, 4 checkpoints, 10-step segment tape, zA, zB, lam, qf,
+        # and the six-step ring of the first-iterate predictor
+        assert n.value >= (3 + 4 + 10 + 4 + 6) * state
+        assert n.value <= (3 + 4 + 10 + 4 + 6) * state + 2 * 1024 * 1024
     finally:
         lib.lb_system_destroy(h)
 

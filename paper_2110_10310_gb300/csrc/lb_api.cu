@@ -46,7 +46,7 @@ struct Region {
 
 struct Layout {
   Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
-      gproj, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist;
+      gproj, gsum, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist;
   size_t total = 0;
 };
 
@@ -197,12 +197,24 @@ int decide_krylov(lb_system* s) {
   return LB_OK;
 }
 
-// state slots of the gradient pieces: one (summed) for grid sweeps, one per
-// state and CTA for cluster sweeps, one per state otherwise
+// warps per CTA of the cluster sweep (0 when it cannot apply)
+int cluster_warps(const lb_system* s) {
+  if (cluster_ctas(s) <= 0) return 0;
+  return lbk::cluster_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N).threads / 32;
+}
+
+// slots of the gradient pieces: one (summed) for grid sweeps, one per state,
+// CTA and warp where cluster sweeps can run, one per state otherwise
 size_t gproj_slots(const lb_system* s) {
   if (use_grid(s)) return 1;
   const int C = cluster_ctas(s);
-  return (size_t)s->M * (C > 1 ? C : 1);
+  return C > 0 ? (size_t)s->M * C * cluster_warps(s) : (size_t)s->M;
+}
+
+// slots the bound sweep writes
+int gproj_used(const lb_system* s) {
+  if (use_grid(s)) return 1;
+  return s->cluster ? s->M * s->cc.C * (s->cc.threads / 32) : s->M;
 }
 
 Layout make_layout(const lb_system* s) {
@@ -239,6 +251,7 @@ Layout make_layout(const lb_system* s) {
   take(L.seg, K > 0 ? c2 * M * (size_t)K * V : 0);
   const bool grid = use_grid(s);
   take(L.gproj, c2 * gproj_slots(s) * NT * s->Q * 2);
+  take(L.gsum, c2 * NT * s->Q * 2);
   take(L.J, sizeof(double) * M);
   take(L.G, sizeof(double));
   take(L.grad, sizeof(double) * s->n_params);
@@ -391,12 +404,13 @@ void fill_prob(lb_system* s) {
   P.ckpt = at<double2>(s, s->L.ckpt);
   P.seg = at<double2>(s, s->L.seg);
   P.gproj = at<double2>(s, s->L.gproj);
+  P.gsum = at<double2>(s, s->L.gsum);
   P.J = at<double>(s, s->L.J);
   P.G = at<double>(s, s->L.G);
   P.grad = at<double>(s, s->L.grad);
   P.status = at<DevStatus>(s, s->L.status);
   const bool grid = use_grid(s);
-  P.gM = grid ? 1 : (s->cluster ? s->M * s->cc.C : s->M);
+  P.gM = gproj_used(s);
   P.grid_blocks = grid ? s->gblocks : 0;
   if (grid) {
     P.zA = at<double2>(s, s->L.zA);
@@ -561,7 +575,7 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
     s->method = c.method;
     s->hp.method = c.method;
     s->cluster = c.sweep == LB_SWEEP_CLUSTER;
-    s->hp.gM = use_grid(s) ? 1 : (s->cluster ? s->M * s->cc.C : s->M);
+    s->hp.gM = gproj_used(s);
     if (c.sweep == LB_SWEEP_RESIDENT) {
       s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true, kry_elems(s));
       const int threads = ((s->V + c.E - 1) / c.E + 31) / 32 * 32;
@@ -599,13 +613,13 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
     s->rc = rc0;
     s->cluster = cl0;
     s->method = s->hp.method = m0;
-    s->hp.gM = use_grid(s) ? 1 : (s->cluster ? s->M * s->cc.C : s->M);
+    s->hp.gM = gproj_used(s);
     LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
     return fail(LB_ENOTCONV, "no candidate's inner solve converged on the probe steps");
   }
   s->method = s->hp.method = win.method;
   s->cluster = win.sweep == LB_SWEEP_CLUSTER;
-  s->hp.gM = use_grid(s) ? 1 : (s->cluster ? s->M * s->cc.C : s->M);
+  s->hp.gM = gproj_used(s);
   if (win.sweep == LB_SWEEP_RESIDENT) {
     s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true, kry_elems(s));
     s->rc.E = win.E;
@@ -945,7 +959,7 @@ static int gradient_device(lb_system* s, cudaStream_t st) {
     s->timed_bwd = true;
   }
   LB_CUDA(lbk::launch_finalize(s->dp, 1, param_warps(s), 1, st), "finalize kernels");
-  s->launches += 3;
+  s->launches += 4;  // backward sweep, objective, slot sum, projection
   return LB_OK;
 }
 
@@ -1183,11 +1197,11 @@ static int batch_call(lb_batch* b, cudaStream_t st, int with_grad, double* G_out
   int launches = 0;
   if (b->exec[mode]) {
     LB_CUDA(cudaGraphLaunch(b->exec[mode], st), "cudaGraphLaunch");
-    launches = (int)b->sys.size() + 3 + with_grad;
+    launches = (int)b->sys.size() + 3 + 3 * with_grad;
   } else {
     int rc = batch_enqueue(b, st, with_grad);
     if (rc) return rc;
-    launches = (int)b->sys.size() + 3 + with_grad;
+    launches = (int)b->sys.size() + 3 + 3 * with_grad;
   }
   const size_t n = b->sys.size();
   std::vector<DevStatus> stv(n);

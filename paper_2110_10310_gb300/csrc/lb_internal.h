@@ -71,13 +71,14 @@ struct ProbDev {
   double2* qT;               // [M*V]
   double2* ckpt;             // [M*n_ckpt*V], or [M*NT*V] of z^j when K == 0
   double2* seg;              // [M*K*V] stage vectors of one segment (K > 0)
-  double2* gproj;            // [M*NT*Q*2] per state/step: g_a, g_ad (eq. reducedgradient pieces)
+  double2* gproj;            // [gM][NT][Q][2] per slot/step: g_a, g_ad (eq. reducedgradient pieces)
+  double2* gsum;             // [NT][Q][2] the pieces summed over the gM slots
   double* J;                 // [M] merit functional per state
   double* G;                 // [1]
   double* grad;              // [n_params]
   DevStatus* status;
   // grid-wide sweeps (N^2 > 4096): buffers of the iteration, [M*V] each
-  int32_t gM;                // state slots of gproj: M (one CTA per state) or 1 (grid sweeps sum over states)
+  int32_t gM;                // slots of gproj: M (one CTA per state), M * C * warps (cluster), 1 (grid)
   int32_t grid_blocks;       // blocks of the cooperative launch
   double2* zA;
   double2* zB;

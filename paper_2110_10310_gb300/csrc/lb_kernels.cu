@@ -1433,6 +1433,7 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
   const bool odd = pl.r & 1;
   const double sdi = odd ? di : -di;
   const double2 rhs = rr[pl.v];
+  const double2 r0 = pl.r == 0 ? rhs : make_double2(0.0, 0.0);
   const double cj = ADJ ? pl.cja : pl.cjf;
   const int oj = ADJ ? pl.oja : pl.ojf;
   const unsigned tx = (unsigned)V * 16u + (unsigned)(C * nwarps) * 4u;
@@ -1454,18 +1455,19 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
     const double2 xa = zc[pl.oa], xb = zc[pl.ob], x5 = zc[oj], zo = zc[pl.v];
     const double xr = fma(-pl.cb, xb.x, pl.ca * xa.x);
     const double xi = fma(-pl.cb, xb.y, pl.ca * xa.y);
-    double accr = fma(Ar, xr, -Ai * xi);
-    double acci = fma(Ar, xi, Ai * xr);
+    // lane 0 of the element starts from the right-hand side
+    double accr = fma(Ar, xr, fma(-Ai, xi, r0.x));
+    double acci = fma(Ar, xi, fma(Ai, xr, r0.y));
     accr = fma(cj, x5.x, accr);
     acci = fma(cj, x5.y, acci);
     // Sum over the element's L lanes with one component per lane: after the
     // first exchange even lanes carry the real and odd lanes the imaginary
-    // part, so each level costs one FP64 add, and so does each later step.
+    // part, so each level costs one FP64 add.
     double k = odd ? acci : accr;
     k += __shfl_xor_sync(kFull, odd ? accr : acci, 1);
 #pragma unroll
     for (int o = 2; o < L; o <<= 1) k += __shfl_xor_sync(kFull, k, o);
-    const double am = (odd ? rhs.y : rhs.x) + k;  // this lane's component of rhs + dt/2 O z
+    const double am = k;  // this lane's component of rhs + dt/2 O z
     const double zom = odd ? zo.y : zo.x;
     double zm;
     if (!neumann) {
@@ -1615,8 +1617,8 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
   // predictor history never depends on the checkpoint interval
   const bool apred = H.method != LB_SOLVER_NEUMANN;
   ClHist ahist;
-  // gradient pieces of this CTA go to state slot i * C + crank of gproj
-  double2* gbase = P.gproj + (size_t)(i * C + crank) * H.NT * H.Q * 2;
+  // gradient pieces of this warp go to state slot (i * C + crank) * nwarps + warp of gproj
+  double2* gbase = P.gproj + (size_t)((i * C + crank) * nwarps + warp) * H.NT * H.Q * 2;
   for (int sg = nseg - 1; sg >= 0 && !failed; --sg) {
     const int j0 = H.K > 0 ? sg * H.K : 0;
     const int j1 = H.K > 0 ? min(H.NT, j0 + H.K) : H.NT;
@@ -1642,6 +1644,11 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
       __syncthreads();  // segment tape written by this CTA before it is read back below
     }
     for (int j = j1 - 1; j >= j0; --j) {
+      // this lane's stage vector element, loaded before the solve so that its latency is hidden
+      const bool gl = pl.ev && pl.r < 2 * QT;
+      const double2 Z = gl ? (H.K > 0 ? P.seg[((size_t)i * H.K + (j - j0)) * H.V + pl.v]
+                                      : P.ckpt[((size_t)i * H.NT + j) * H.V + pl.v])
+                           : make_double2(0.0, 0.0);
       double2 zh;
       const int it = cl_solve<QT, true>(S, pl, S.ll, P.ctab + (size_t)j * H.Q, C, crank, cnt, zh, apred ? ahist : ClHist());
       if (it < 0) {
@@ -1652,36 +1659,29 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
       if (crank == 0) stats.add(2, it);
       const double2* zb = S.zb + (size_t)(cnt.gk & 1) * H.V;
       // gradient piece of this lane's half (eq. reducedgradient): sum_kl Z conj(X_zhat),
-      // X the half's neighbour combination of zhat; P half -> g_ad, R half -> g_a
+      // X the half's neighbour combination of zhat; P half -> g_ad, R half -> g_a.
+      // Summed over the warp's elements (one component per lane after the
+      // first exchange) and stored per warp; k_gproj_reduce adds the slots.
       double sr = 0.0, si = 0.0;
-      if (pl.ev && pl.r < 2 * QT) {
-        const double2 Z = H.K > 0 ? P.seg[((size_t)i * H.K + (j - j0)) * H.V + pl.v]
-                                  : P.ckpt[((size_t)i * H.NT + j) * H.V + pl.v];
+      if (gl) {
         const double2 xa = zb[pl.oa], xb = zb[pl.ob];
         const double xr = fma(-pl.cb, xb.x, pl.ca * xa.x);
         const double xi = fma(-pl.cb, xb.y, pl.ca * xa.y);
         sr = fma(Z.x, xr, Z.y * xi);
         si = fma(Z.y, xr, -Z.x * xi);
       }
+      if constexpr (L < 32) {
+        const bool hi = lane & L;
+        double k = hi ? si : sr;
+        k += __shfl_xor_sync(kFull, hi ? sr : si, L);
 #pragma unroll
-      for (int o = L; o < 32; o <<= 1) {
-        sr += __shfl_xor_sync(kFull, sr, o);
-        si += __shfl_xor_sync(kFull, si, o);
-      }
-      if (lane < L) {
-        S.gred[(lane * 4 + warp) * 2] = sr;
-        S.gred[(lane * 4 + warp) * 2 + 1] = si;
-      }
-      __syncthreads();
-      if (threadIdx.x < 2 * QT) {
-        double tr = 0.0, ti = 0.0;
-        for (int ww = 0; ww < nwarps; ++ww) {
-          tr += S.gred[(threadIdx.x * 4 + ww) * 2];
-          ti += S.gred[(threadIdx.x * 4 + ww) * 2 + 1];
+        for (int o = 2 * L; o < 32; o <<= 1) k += __shfl_xor_sync(kFull, k, o);
+        // lane r < 2Q holds sum sr of half r, lane L + r the sum si; store -i (sr + i si) = (si, -sr)
+        const int r = lane & (L - 1);
+        if (lane < 2 * L && r < 2 * QT) {
+          double* g = reinterpret_cast<double*>(gbase + ((size_t)j * H.Q + (r >> 1)) * 2 + ((r & 1) ? 0 : 1));
+          g[hi ? 0 : 1] = hi ? k : -k;
         }
-        const int q = threadIdx.x >> 1;
-        // multiply by -i: (si, -sr); R half is g_a (slot 0), P half is g_ad (slot 1)
-        gbase[((size_t)j * H.Q + q) * 2 + ((threadIdx.x & 1) ? 0 : 1)] = make_double2(ti, -tr);
       }
       // qhat^j = 2 zhat - qhat^{j+1} on the whole replica
       for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
@@ -1873,8 +1873,25 @@ __global__ void k_objective(const ProbDev* __restrict__ probs) {
   if (lane == 0) P.G[0] = s + 0.5 * P.gamma2 * a2;
 }
 
+// Sum of the gradient pieces over their gM state slots (states, CTAs, warps),
+// in slot order, for every (step, subsystem, piece): gsum[NT][Q][2].
+__global__ void k_gproj_reduce(const ProbDev* __restrict__ probs) {
+  const ProbDev& P = probs[blockIdx.y];
+  const size_t n = (size_t)P.NT * P.Q * 2, stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += stride) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int i = 0; i < P.gM; ++i) {
+      const double2 g = P.gproj[(size_t)i * n + k];
+      t.x += g.x;
+      t.y += g.y;
+    }
+    P.gsum[k] = t;
+  }
+}
+
 // dG/dalpha (eq. reducedgradient): one warp per (q, f, s); the sum over the
-// spline's support in time and over the states is in a fixed order.
+// spline's support in time is in a fixed order (the states were summed by
+// k_gproj_reduce).
 __global__ void k_gradient_project(const ProbDev* __restrict__ probs) {
   const ProbDev& P = probs[blockIdx.y];
   const int lane = threadIdx.x & 31;
@@ -1896,14 +1913,8 @@ __global__ void k_gradient_project(const ProbDev* __restrict__ probs) {
     const double t = (j + 0.5) * P.h;
     const double S = bspline2(t / dtau - (s - 0.5));
     if (S == 0.0) continue;
-    double ga_r = 0.0, ga_i = 0.0, gd_r = 0.0, gd_i = 0.0;
-    for (int i = 0; i < P.gM; ++i) {
-      const double2* g = P.gproj + (((size_t)i * P.NT + j) * P.Q + q) * 2;
-      ga_r += g[0].x;
-      ga_i += g[0].y;
-      gd_r += g[1].x;
-      gd_i += g[1].y;
-    }
+    const double2* g = P.gsum + ((size_t)j * P.Q + q) * 2;
+    const double ga_r = g[0].x, ga_i = g[0].y, gd_r = g[1].x, gd_i = g[1].y;
     double sn, cs;
     sincos(om * t, &sn, &cs);
     // Re(e^{iOt} g_a + e^{-iOt} g_ad) and Re(i e^{iOt} g_a - i e^{-iOt} g_ad)
@@ -2634,6 +2645,9 @@ cudaError_t launch_finalize(const ProbDev* d_probs, int n_probs, int max_param_w
   k_objective<<<n_probs, 32, 0, s>>>(d_probs);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !with_grad) return e;
+  k_gproj_reduce<<<dim3(304, n_probs), 256, 0, s>>>(d_probs);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   const int threads = 128;
   dim3 grid((max_param_warps * 32 + threads - 1) / threads, n_probs);
   k_gradient_project<<<grid, threads, 0, s>>>(d_probs);

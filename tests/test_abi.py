@@ -150,7 +150,9 @@ def test_workspace_size_accounts_for_checkpoints(lib, K):
             Kc = min(K, NT)
             tape = -(-NT // Kc) * state + Kc * state
         C = -(-Vl * 4 // 128)  # CTAs per state of the cluster sweep (2Q = 4 lanes per element)
-        gproj = M * C * NT * 2 * 2 * 16
+        nw = -(-(-(-Vl // C)) * 4 // 32)  # warps per CTA
+        # per-warp gradient pieces of every state, and their sum over the slots
+        gproj = M * C * nw * NT * 2 * 2 * 16 + NT * 2 * 2 * 16
         # q0, tar, qT and the six-step ring of the first-iterate predictor
         assert n.value >= tape + gproj + (3 + 6) * state
         assert n.value <= tape + gproj + (3 + 6) * state + 64 * 1024

@@ -174,7 +174,11 @@ int lb_objective_set(lb_system* sys, int32_t kind, const double* targets, double
 int lb_objective_set_gate(lb_system* sys, int32_t kind, const double* V, double gamma2);
 
 /* Inner solver and checkpointing.  rtol: stop when
- * max|z_new - z| <= rtol * max|q| (componentwise, per state); max_iter caps the
+ * max|z_new - z| <= rtol * max|q| * f_j (componentwise, per state), where for
+ * the Jacobi iteration f_j = (1 - rho_j)/rho_j with rho_j < 1/2 an upper bound
+ * of the infinity norm of its iteration matrix at step j (then
+ * max|z - z*| <= rtol * max|q| for the returned z), and f_j = 1 otherwise
+ * (rho_j >= 1/2, or the Neumann iteration); max_iter caps the
  * iterations of one step (LB_ENOTCONV beyond); ckpt_every = K >= 1 stores the
  * forward state every K steps and recomputes each K-step segment in the
  * backward sweep; K = 0 stores every stage vector z^j instead (no recompute);

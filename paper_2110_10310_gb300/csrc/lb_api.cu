@@ -46,7 +46,7 @@ struct Region {
 
 struct Layout {
   Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
-      gproj, gsum, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist;
+      gproj, gsum, sfac, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist;
   size_t total = 0;
 };
 
@@ -241,6 +241,7 @@ Layout make_layout(const lb_system* s) {
   take(L.alpha, sizeof(double) * s->n_params);
   take(L.carriers, sizeof(double) * n_carriers_total(s));
   take(L.ctab, c2 * NT * s->Q);
+  take(L.sfac, sizeof(double) * NT);
   take(L.q0, c2 * M * V);
   take(L.tar, c2 * M * V);
   take(L.wgt, sizeof(double) * M);
@@ -405,6 +406,7 @@ void fill_prob(lb_system* s) {
   P.seg = at<double2>(s, s->L.seg);
   P.gproj = at<double2>(s, s->L.gproj);
   P.gsum = at<double2>(s, s->L.gsum);
+  P.sfac = at<double>(s, s->L.sfac);
   P.J = at<double>(s, s->L.J);
   P.G = at<double>(s, s->L.G);
   P.grad = at<double>(s, s->L.grad);
@@ -426,8 +428,8 @@ void fill_prob(lb_system* s) {
 
 int ensure_ctab(lb_system* s, cudaStream_t st) {
   if (!s->ctab_dirty) return LB_OK;
-  LB_CUDA(lbk::launch_control_table(s->dp, s->hp, st), "control table kernel");
-  s->launches += 1;
+  LB_CUDA(lbk::launch_control_table(s->dp, s->hp, st), "control table kernels");
+  s->launches += 2;  // control table, stopping factors
   s->ctab_dirty = false;
   return LB_OK;
 }
@@ -1197,11 +1199,11 @@ static int batch_call(lb_batch* b, cudaStream_t st, int with_grad, double* G_out
   int launches = 0;
   if (b->exec[mode]) {
     LB_CUDA(cudaGraphLaunch(b->exec[mode], st), "cudaGraphLaunch");
-    launches = (int)b->sys.size() + 3 + 3 * with_grad;
+    launches = 2 * (int)b->sys.size() + 3 + 3 * with_grad;
   } else {
     int rc = batch_enqueue(b, st, with_grad);
     if (rc) return rc;
-    launches = (int)b->sys.size() + 3 + 3 * with_grad;
+    launches = 2 * (int)b->sys.size() + 3 + 3 * with_grad;
   }
   const size_t n = b->sys.size();
   std::vector<DevStatus> stv(n);

@@ -64,6 +64,7 @@ struct ProbDev {
   double* alpha;             // [n_params]
   double* carriers;          // [sum nf] Omega (rad/ns)
   double2* ctab;             // [NT*Q] (dt/2) d_q(t_j + dt/2)
+  double* sfac;              // [NT] factor of the inner stopping test per step (k_stop_factors)
   // states and objective
   double2* q0;               // [M*V]
   double2* tar;              // [M*V]

@@ -111,6 +111,16 @@ __device__ void record_error(DevStatus* st, int code, int step) {
   if (atomicCAS(&st->code, 0, code) == 0) st->step = step;
 }
 
+// Factor of the stopping test of step j.  The Jacobi iteration matrix
+// T_j = (I - dt/2 D)^-1 dt/2 O_j (and its adjoint) has infinity norm at most
+// rho_j (k_stop_factors); when rho_j < 1/2, ||z - z*|| <= rho_j/(1 - rho_j)
+// ||z_new - z||, so the test ||z_new - z|| < rtol ||q|| (1 - rho_j)/rho_j
+// bounds the error of the returned iterate by rtol ||q||.  Otherwise (and for
+// the Neumann iteration) the factor is 1: the plain increment test.
+__device__ __forceinline__ double stop_factor(const ProbDev& P, int j) {
+  return P.method == LB_SOLVER_JACOBI ? P.sfac[j] : 1.0;
+}
+
 // ---------------------------------------------------------------------------
 // per-CTA copy of the problem constants used in the inner loops
 
@@ -421,7 +431,7 @@ __device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
 // the fixed-point kernels are compiled without it.
 template <int E, int QT, bool ADJ, bool GM = false>
 __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, const Plan<QT>& pl,
-                         const double2 (&rhs)[E], const double2* __restrict__ ct, int& cur,
+                         const double2 (&rhs)[E], const double2* __restrict__ ct, double fac, int& cur,
                          const double2* pc = nullptr) {
   static_assert(QT == 0 || E == 1, "the per-thread plan holds one element");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -468,7 +478,7 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
   if constexpr (GM) {
     if (gmres) return res_gmres<E, ADJ>(S, H, el, ct, tol);
   }
-  const unsigned thr = hi_abs(tol);
+  const unsigned thr = hi_abs(tol * fac);
   for (int it = 0; it < H.max_iter; ++it) {
     const double2* __restrict__ zc = cur ? S.zb1 : S.zb0;
     double2* __restrict__ zn = cur ? S.zb0 : S.zb1;
@@ -873,7 +883,8 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
     }
     int cur;
     if (pred) pr.predict(pc, H.V);
-    const int it = res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur, pred ? pc : nullptr);
+    const int it = res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, stop_factor(P, j), cur,
+                                                 pred ? pc : nullptr);
     if (it < 0) {
       if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
       stats.flush(P.status);
@@ -974,7 +985,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       }
       for (int j = j0; j < j1; ++j) {
         int cur;
-        const int it = res_solve<E, QT, false, GM>(S, H, el, pl, qf, P.ctab + (size_t)j * H.Q, cur);
+        const int it = res_solve<E, QT, false, GM>(S, H, el, pl, qf, P.ctab + (size_t)j * H.Q, stop_factor(P, j), cur);
         if (it < 0) {
           if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
           stats.flush(P.status);
@@ -999,7 +1010,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       int cur;
       // (I - dt/2 (M^{j+1/2})^+) zhat^j = qhat^{j+1}   (eq. linsystem_adjoint)
       if (apred) pr.predict(pc, H.V);
-      const int it = res_solve<E, QT, true, GM>(S, H, el, pl, lam, ct, cur, apred ? pc : nullptr);
+      const int it = res_solve<E, QT, true, GM>(S, H, el, pl, lam, ct, stop_factor(P, j), cur, apred ? pc : nullptr);
       if (it < 0) {
         if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
         stats.flush(P.status);
@@ -1098,8 +1109,8 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
   for (int jj = 0; jj < j1 - j0; ++jj) {
     const int j = adjoint ? j1 - 1 - jj : j0 + jj;
     int cur;
-    const int it = adjoint ? res_solve<E, QT, true, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur)
-                           : res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, cur);
+    const int it = adjoint ? res_solve<E, QT, true, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, stop_factor(P, j), cur)
+                           : res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, stop_factor(P, j), cur);
     if (it < 0) {
       if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
       stats.flush(P.status);
@@ -1389,8 +1400,8 @@ __device__ __forceinline__ void cl_record(const ClSmem& S, int e, double2 z, dou
 
 template <int QT, bool ADJ>
 __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __restrict__ rr,
-                        const double2* __restrict__ ct, int C, int crank, ClCount& cnt, double2& zout,
-                        ClHist hist = ClHist()) {
+                        const double2* __restrict__ ct, double fac, int C, int crank, ClCount& cnt,
+                        double2& zout, ClHist hist = ClHist()) {
   constexpr int L = ClLanes<QT>::L;
   const Hdr& H = *S.hdr;
   const int V = H.V;
@@ -1422,7 +1433,8 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
   unsigned qmax = 0;
   for (int w = 0; w < nwarps; ++w) qmax = max(qmax, S.qsl[w]);
   if (qmax >= kInfHi) return -2;
-  const unsigned thr = hi_abs(H.rtol * __longlong_as_double(static_cast<long long>((unsigned long long)qmax << 32)));
+  const unsigned thr =
+      hi_abs(H.rtol * __longlong_as_double(static_cast<long long>((unsigned long long)qmax << 32)) * fac);
   // this lane's complex factor: -i d P -> (b - i a) P, -i conj(d) R -> (-b - i a) R
   double Ar = pl.rhalf ? -c.y : c.y, Ai = -c.x;
   if (ADJ) {
@@ -1541,7 +1553,7 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
     if (tape && H.K > 0 && j % H.K == 0 && crank == 0)
       for (int e = threadIdx.x; e < H.V; e += blockDim.x) P.ckpt[((size_t)i * H.n_ckpt + j / H.K) * H.V + e] = S.rr[e];
     double2 z;
-    const int it = cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, C, crank, cnt, z, pred ? hist : ClHist());
+    const int it = cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z, pred ? hist : ClHist());
     if (it < 0) {
       if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
       failed = true;
@@ -1626,7 +1638,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
       for (int e = threadIdx.x; e < H.V; e += blockDim.x) S.rr[e] = P.ckpt[((size_t)i * H.n_ckpt + sg) * H.V + e];
       for (int j = j0; j < j1; ++j) {
         double2 z;
-        const int it = cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, C, crank, cnt, z);
+        const int it = cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z);
         if (it < 0) {
           if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
           failed = true;
@@ -1650,7 +1662,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
                                       : P.ckpt[((size_t)i * H.NT + j) * H.V + pl.v])
                            : make_double2(0.0, 0.0);
       double2 zh;
-      const int it = cl_solve<QT, true>(S, pl, S.ll, P.ctab + (size_t)j * H.Q, C, crank, cnt, zh, apred ? ahist : ClHist());
+      const int it = cl_solve<QT, true>(S, pl, S.ll, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, zh, apred ? ahist : ClHist());
       if (it < 0) {
         if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
         failed = true;
@@ -1716,8 +1728,8 @@ __global__ void __launch_bounds__(128, 1) k_propagate_cl(const ProbDev* __restri
   for (int jj = 0; jj < j1 - j0; ++jj) {
     const int j = adjoint ? j1 - 1 - jj : j0 + jj;
     double2 z;
-    const int it = adjoint ? cl_solve<QT, true>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, C, crank, cnt, z)
-                           : cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, C, crank, cnt, z);
+    const int it = adjoint ? cl_solve<QT, true>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z)
+                           : cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z);
     if (it < 0) {
       if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
       failed = true;
@@ -1859,6 +1871,24 @@ __global__ void k_control_table(const ProbDev* __restrict__ pp) {
   }
   const double sc = 0.5 * P.h * kTwoPi;
   P.ctab[tid] = make_double2(sc * dr, sc * di);
+}
+
+// rho_j >= ||(I - dt/2 D)^-1 dt/2 O_j||_inf and the same for the adjoint:
+// |(I - dt/2 D)^-1| <= 1 (Re D <= 0); per subsystem the control couplings of
+// one row (or column) sum to at most |dt/2 d_q| 2 (sqrt(n-1) + sqrt(n-2)), and
+// the decay sandwich to at most (dt/2)/T1 (n - 1).  One thread per step.
+__global__ void k_stop_factors(const ProbDev* __restrict__ pp) {
+  const ProbDev& P = *pp;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P.NT) return;
+  double rho = 0.0;
+  for (int q = 0; q < P.Q; ++q) {
+    const double n = P.levels[q];
+    const double2 c = P.ctab[(size_t)j * P.Q + q];
+    rho += hypot(c.x, c.y) * 2.0 * (sqrt(n - 1.0) + sqrt(n - 2.0)) + P.jump[q] * (n - 1.0);
+  }
+  // (1 - rho)/rho, capped so that rtol ||q|| times it stays finite
+  P.sfac[j] = rho < 0.5 ? fmin((1.0 - rho) / fmax(rho, 1e-200), 1e200) : 1.0;
 }
 
 // G = sum_i beta_i/M J_i + gamma2/2 ||alpha||^2 (eq. optimproblem), one warp
@@ -2170,8 +2200,8 @@ __device__ __forceinline__ void grid_record(const ProbDev& P, long long total, G
 
 template <bool ADJ>
 __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __restrict__ rhs,
-                          const double2* __restrict__ ct, long long& it_global, long long& solve, double2** zout,
-                          GridHist hist = GridHist()) {
+                          const double2* __restrict__ ct, double fac, long long& it_global, long long& solve,
+                          double2** zout, GridHist hist = GridHist()) {
   const GridHdr& G = *S.g;
   const Hdr& H = G.h;
   const Tabs T{S.cu, S.cd, S.jf, S.ja};
@@ -2260,7 +2290,7 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
           state = -2;
           break;
         }
-        const unsigned long long thr = abs_bits(H.rtol * __longlong_as_double((long long)q));
+        const unsigned long long thr = abs_bits(H.rtol * __longlong_as_double((long long)q) * fac);
         if (d > thr) state = 0;
       }
       *S.flag = state;
@@ -2318,8 +2348,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
       }
     }
     double2* z = nullptr;
-    const int it = mode == 2 ? grid_solve<true>(P, S, q, P.ctab + (size_t)j * H.Q, itg, nsolve, &z)
-                             : grid_solve<false>(P, S, q, P.ctab + (size_t)j * H.Q, itg, nsolve, &z,
+    const int it = mode == 2 ? grid_solve<true>(P, S, q, P.ctab + (size_t)j * H.Q, stop_factor(P, j), itg, nsolve, &z)
+                             : grid_solve<false>(P, S, q, P.ctab + (size_t)j * H.Q, stop_factor(P, j), itg, nsolve, &z,
                                                  pred ? hist : GridHist());
     if (it < 0) {
       grid_fail(P, it, j);
@@ -2386,7 +2416,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
       }
       for (int j = j0; j < j1; ++j) {
         double2* z = nullptr;
-        const int it = grid_solve<false>(P, S, P.qf, P.ctab + (size_t)j * H.Q, itg, nsolve, &z);
+        const int it = grid_solve<false>(P, S, P.qf, P.ctab + (size_t)j * H.Q, stop_factor(P, j), itg, nsolve, &z);
         if (it < 0) {
           grid_fail(P, it, j);
           failed = true;
@@ -2407,7 +2437,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
     for (int j = j1 - 1; j >= j0; --j) {
       const double2* ct = P.ctab + (size_t)j * H.Q;
       double2* zh = nullptr;
-      const int it = grid_solve<true>(P, S, P.lam, ct, itg, nsolve, &zh, apred ? ahist : GridHist());
+      const int it = grid_solve<true>(P, S, P.lam, ct, stop_factor(P, j), itg, nsolve, &zh, apred ? ahist : GridHist());
       if (it < 0) {
         grid_fail(P, it, j);
         failed = true;
@@ -2638,6 +2668,9 @@ cudaError_t launch_gate_targets(const ProbDev& h, const double2* Vg, const int32
 cudaError_t launch_control_table(const ProbDev* d_prob, const ProbDev& h, cudaStream_t s) {
   const size_t n = (size_t)h.NT * h.Q;
   k_control_table<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_prob);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_stop_factors<<<(unsigned)((h.NT + 255) / 256), 256, 0, s>>>(d_prob);
   return cudaGetLastError();
 }
 

@@ -15,10 +15,12 @@ Modules
             dense vectorised Lindbladian (Sec. II, Appendix A).
   imr    -- implicit midpoint forward sweep, objective, discrete adjoint and
             reduced gradient (Sec. III, Appendices A-B), central differences.
+  lbfgs  -- L-BFGS minimisation of G(alpha) (Sec. III; two-loop recursion of
+            Nocedal & Wright), pinned by ``tests/test_oracle_lbfgs.py``.
 
 Every function's docstring names the passage of the paper it follows.  All
 functions are pinned by ``tests/test_oracle_pins.py`` against closed forms,
 invariants and brute force; none is "parity unpinned".
 """
 
-from . import model, imr  # noqa: F401
+from . import model, imr, lbfgs  # noqa: F401

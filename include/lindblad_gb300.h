@@ -214,6 +214,26 @@ int lb_forward(lb_system* sys, void* stream, double* G_out, void* rhoT_dev_out);
  * (host, nullable, length of alpha) receives dG/dalpha. */
 int lb_gradient(lb_system* sys, void* stream, double* G_out, double* grad_out);
 
+/* Minimise G(alpha) by L-BFGS (Sec. III and Appendix B: the paper updates the
+ * control vector with L-BFGS steps built from the adjoint gradient; two-loop
+ * recursion of Nocedal & Wright, Numerical Optimization, Algorithm 7.4).
+ * Starts from the controls set last (lb_controls_set) and leaves the final
+ * iterate set; every function value and gradient is one lb_gradient on
+ * `stream`.  Direction -H_k g with H_k^0 = (s^T y / y^T y) I of the newest of
+ * at most `memory` pairs (a pair is kept only when s^T y > 1e-10 |s| |y|);
+ * with no pair, -g scaled to max-norm `step0`.  Backtracking from the unit
+ * step, halving until G(x + t d) <= G(x) + 1e-4 t g^T d (at most 30 trials,
+ * after which the run stops at the current iterate).  Stops when
+ * max|grad| <= gtol or after max_iter accepted steps.
+ * Outputs (host, nullable): G_out the final G; alpha_out the final alpha
+ * (length of alpha); iters_out the accepted steps; evals_out the gradient
+ * evaluations; history [max_iter + 1][2] receives (G, max|grad|) of the start
+ * and of every accepted iterate.  LB_EINVAL for memory < 1, max_iter < 0,
+ * gtol < 0 or step0 <= 0; errors of a gradient evaluation are returned as
+ * they are (the controls then hold the iterate that failed). */
+int lb_optimize(lb_system* sys, void* stream, int32_t max_iter, int32_t memory, double gtol, double step0,
+                double* G_out, double* alpha_out, int32_t* iters_out, int32_t* evals_out, double* history);
+
 /* Device-resident variant of lb_gradient: G and the gradient are written to
  * device memory (G_dev: 1 double, grad_dev: length of alpha) and the call
  * does not synchronise; errors of the device sweep are reported by the next

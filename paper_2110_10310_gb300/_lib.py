@@ -98,6 +98,8 @@ SIGNATURES = {
     "lb_forward": (c_int32, [c_void_p, c_void_p, POINTER(c_double), c_void_p]),
     "lb_gradient": (c_int32, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_double)]),
     "lb_gradient_async": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "lb_optimize": (c_int32, [c_void_p, c_void_p, c_int32, c_int32, c_double, c_double, POINTER(c_double),
+                              POINTER(c_double), POINTER(c_int32), POINTER(c_int32), POINTER(c_double)]),
     "lb_gradient_static": (c_int32, [c_void_p, c_void_p, POINTER(c_double), POINTER(c_double)]),
     "lb_propagate": (c_int32, [c_void_p, c_void_p, c_int32, c_int64, c_int64, c_void_p, c_int32]),
     "lb_apply": (c_int32, [c_void_p, c_void_p, c_int32, c_int64, c_void_p, c_void_p, c_int32]),

@@ -974,6 +974,125 @@ int lb_gradient(lb_system* s, void* stream, double* G_out, double* grad_out) {
   return finish(s, st, G_out, grad_out);
 }
 
+namespace {
+
+double dot(const std::vector<double>& a, const std::vector<double>& b) {
+  double t = 0.0;
+  for (size_t i = 0; i < a.size(); ++i) t += a[i] * b[i];
+  return t;
+}
+double max_abs(const std::vector<double>& a) {
+  double t = 0.0;
+  for (double v : a) t = std::max(t, std::fabs(v));
+  return t;
+}
+
+// d = -H g by the two-loop recursion over the pairs (S[k], Y[k]), oldest
+// first; with no pair, -g scaled to max-norm step0.
+void lbfgs_direction(const std::vector<double>& g, const std::vector<std::vector<double>>& S,
+                     const std::vector<std::vector<double>>& Y, double step0, std::vector<double>& d) {
+  const size_t n = g.size(), m = S.size();
+  d.assign(n, 0.0);
+  if (m == 0) {
+    const double sc = step0 / max_abs(g);
+    for (size_t i = 0; i < n; ++i) d[i] = -g[i] * sc;
+    return;
+  }
+  std::vector<double> q = g, rho(m), a(m);
+  for (size_t k = m; k-- > 0;) {
+    rho[k] = 1.0 / dot(Y[k], S[k]);
+    a[k] = rho[k] * dot(S[k], q);
+    for (size_t i = 0; i < n; ++i) q[i] -= a[k] * Y[k][i];
+  }
+  const double gamma = dot(S[m - 1], Y[m - 1]) / dot(Y[m - 1], Y[m - 1]);
+  for (size_t i = 0; i < n; ++i) q[i] *= gamma;
+  for (size_t k = 0; k < m; ++k) {
+    const double b = rho[k] * dot(Y[k], q);
+    for (size_t i = 0; i < n; ++i) q[i] += (a[k] - b) * S[k][i];
+  }
+  for (size_t i = 0; i < n; ++i) d[i] = -q[i];
+}
+
+}  // namespace
+
+int lb_optimize(lb_system* s, void* stream, int32_t max_iter, int32_t memory, double gtol, double step0,
+                double* G_out, double* alpha_out, int32_t* iters_out, int32_t* evals_out, double* history) {
+  int rc = check_ready(s, true);
+  if (rc) return rc;
+  if (memory < 1 || max_iter < 0 || !(gtol >= 0.0) || !(step0 > 0.0) || !std::isfinite(step0))
+    return fail(LB_EINVAL, "need memory >= 1, max_iter >= 0, gtol >= 0 and step0 > 0");
+  const size_t n = (size_t)s->n_params;
+  constexpr double kC1 = 1e-4, kCurv = 1e-10;
+  constexpr int kMaxTrials = 30;
+  std::vector<double> x = s->alpha, g(n), xn(n), gn(n), d;
+  std::vector<std::vector<double>> S, Y;
+  double f = 0.0;
+  rc = lb_gradient(s, stream, &f, g.data());
+  if (rc) return rc;
+  int evals = 1, iters = 0;
+  if (history) {
+    history[0] = f;
+    history[1] = max_abs(g);
+  }
+  for (; iters < max_iter; ++iters) {
+    if (max_abs(g) <= gtol) break;
+    lbfgs_direction(g, S, Y, step0, d);
+    double gd = dot(g, d);
+    if (!(gd < 0.0)) {
+      S.clear();
+      Y.clear();
+      lbfgs_direction(g, S, Y, step0, d);
+      gd = dot(g, d);
+    }
+    double t = 1.0, fn = 0.0;
+    bool accepted = false;
+    for (int trial = 0; trial < kMaxTrials; ++trial) {
+      for (size_t i = 0; i < n; ++i) xn[i] = x[i] + t * d[i];
+      rc = lb_controls_set(s, xn.data(), (int64_t)n);
+      if (rc) return rc;
+      rc = lb_gradient(s, stream, &fn, gn.data());
+      ++evals;
+      if (rc) return rc;
+      if (fn <= f + kC1 * t * gd) {
+        accepted = true;
+        break;
+      }
+      t *= 0.5;
+    }
+    if (!accepted) {
+      // no sufficient decrease along d: stop at the current iterate
+      rc = lb_controls_set(s, x.data(), (int64_t)n);
+      if (rc) return rc;
+      break;
+    }
+    std::vector<double> sv(n), yv(n);
+    for (size_t i = 0; i < n; ++i) {
+      sv[i] = xn[i] - x[i];
+      yv[i] = gn[i] - g[i];
+    }
+    if (dot(sv, yv) > kCurv * std::sqrt(dot(sv, sv)) * std::sqrt(dot(yv, yv))) {
+      S.push_back(std::move(sv));
+      Y.push_back(std::move(yv));
+      if ((int)S.size() > memory) {
+        S.erase(S.begin());
+        Y.erase(Y.begin());
+      }
+    }
+    x = xn;
+    g = gn;
+    f = fn;
+    if (history) {
+      history[2 * (iters + 1)] = f;
+      history[2 * (iters + 1) + 1] = max_abs(g);
+    }
+  }
+  if (G_out) *G_out = f;
+  if (alpha_out) std::memcpy(alpha_out, x.data(), sizeof(double) * n);
+  if (iters_out) *iters_out = iters;
+  if (evals_out) *evals_out = evals;
+  return LB_OK;
+}
+
 int lb_gradient_async(lb_system* s, void* stream, void* G_dev, void* grad_dev) {
   int rc = check_ready(s, true);
   if (rc) return rc;

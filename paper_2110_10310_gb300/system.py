@@ -152,6 +152,20 @@ class LindbladSystem:
         L.check(self.lib.lb_gradient(self.h, _stream_handle(stream), byref(G), _dptr(g)))
         return G.value, g
 
+    def optimize(self, max_iter: int = 50, memory: int = 10, gtol: float = 1e-8, step0: float = 1e-2, stream=None):
+        """L-BFGS on G(alpha) from the current controls (``lb_optimize``); the
+        final alpha stays set.  Returns a dict with G, alpha, iterations,
+        gradient evaluations and the (G, max|grad|) history."""
+        G = c_double()
+        a = np.zeros(self.n_params, dtype=np.float64)
+        it = c_int32()
+        ev = c_int32()
+        hist = np.zeros((int(max_iter) + 1, 2), dtype=np.float64)
+        L.check(self.lib.lb_optimize(self.h, _stream_handle(stream), int(max_iter), int(memory), float(gtol),
+                                     float(step0), byref(G), _dptr(a), byref(it), byref(ev), _dptr(hist)))
+        return {"G": G.value, "alpha": a, "iterations": it.value, "evaluations": ev.value,
+                "history": hist[: it.value + 1].copy()}
+
     def gradient_async(self, G_dev: torch.Tensor, grad_dev: torch.Tensor, stream=None):
         L.check(self.lib.lb_gradient_async(self.h, _stream_handle(stream), c_void_p(G_dev.data_ptr()),
                                            c_void_p(grad_dev.data_ptr())))

@@ -528,3 +528,35 @@ def test_batch_with_gmres_members():
         off = sum(len(plain[k][1]) for k in range(i))
         assert abs(Gb[i] - Go) <= 1e-10 * abs(Go)
         assert _rel(gb[off:off + len(go)], go) < 1e-9
+
+
+# ----------------------------------------------------------------------------
+# L-BFGS on top of the gradient (lb_optimize)
+
+
+def test_lbfgs_trajectory_matches_oracle():
+    """lb_optimize against the oracle's L-BFGS driven by the oracle gradient,
+    on the Fock-superposition problem at 1000 steps: the same accepted
+    iterates (G to 1e-9, alpha to 1e-7) and the same number of evaluations."""
+    from oracle import lbfgs
+
+    p = W.fock_superposition(n_steps=1000)
+    s = _sys(p)
+    res = s.optimize(max_iter=8, memory=5, gtol=0.0, step0=1e-2)
+
+    def fg(x):
+        q = copy.deepcopy(p)
+        q.controls.alpha = np.array(x)
+        G, g, _ = imr.gradient(q)
+        return G, g
+
+    x, f, hist = lbfgs.minimize(fg, p.controls.alpha, memory=5, max_iter=8, gtol=0.0, step0=1e-2)
+    assert res["iterations"] == len(hist) - 1 == 8
+    assert res["evaluations"] == hist.evals
+    Gh = np.array([h[0] for h in hist])
+    assert np.max(np.abs(res["history"][:, 0] - Gh) / Gh) < 1e-9
+    assert _rel(res["alpha"], x) < 1e-7
+    assert all(res["history"][k + 1, 0] <= res["history"][k, 0] for k in range(8))
+    # the final iterate stays set: a plain gradient call reproduces the final G
+    G, _ = s.gradient()
+    assert G == res["G"]

@@ -17,6 +17,7 @@ from .synthetic import (  # noqa: F401
     config3,
     config4,
     config5,
+    fock_superposition,
     random_problem,
     basis_outer,
     random_pure_state,

@@ -273,6 +273,31 @@ def config(n: int, **kw):
 # random small problems for tests
 
 
+def fock_superposition(seed: int = 6, n_steps: int = 10000, T_ns: float = 200.0, amp: float = 0.01) -> Problem:
+    """One 4-level qudit driven from |0><0| towards the Fock superposition
+    (|0> + |3>)/sqrt(2): the paper's state-to-state example (Sec. III-A, its
+    footnote parameters: rotating frame, anharmonicity 0.23 GHz, T1 = 93.79 us,
+    T2 = 102.52 us, 10 splines, carriers {0, -0.23} GHz).  The horizon is read
+    as 0.2 us = 200 ns; controls start uniform in [-amp, amp] GHz."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sysm = SystemSpec(
+        levels=(4,),
+        detuning_ghz=np.array([0.0]),
+        selfkerr_ghz=np.array([0.23]),
+        crosskerr_ghz=np.zeros((1, 1)),
+        t1_us=np.array([93.79]),
+        t2_us=np.array([102.52]),
+        T_ns=T_ns,
+        n_steps=n_steps,
+    )
+    ctrl = ControlSpec(10, [np.array([0.0, -0.23])], _alpha(rng, 1, 10, [2], amp))
+    psi = np.zeros(4, dtype=np.complex128)
+    psi[0] = psi[3] = 1.0 / np.sqrt(2.0)
+    rho0 = np.zeros((1, 4, 4), dtype=np.complex128)
+    rho0[0, 0, 0] = 1.0
+    return Problem("fock_superposition", sysm, ctrl, rho0, "frob", targets=pure_density(psi)[None].copy())
+
+
 def random_problem(
     seed: int,
     levels=(2, 3),

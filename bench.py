@@ -40,8 +40,10 @@ WORKLOADS = {
                  "each, 5000 steps, T=100 ns, fwd + adjoint, one persistent launch per sweep captured in a CUDA graph"),
     "qudits_4x4": ("qudits_4x4: 4 qudits x 4 levels (vec 65536), 3 random pure states, dt=0.0125 ns, "
                    "first {n} of 40000 steps, fwd + adjoint with checkpoints every 100 steps, grid-wide sweep"),
-    "qutrits_6x3": ("qutrits_6x3: 6 qutrits (vec 531441), 64 random pure states, dt=0.015 ns, "
+    "qutrits_6x3": ("qutrits_6x3: 6 qutrits (vec 531441), {m} random pure states, dt=0.015 ns, "
                     "first {n} of 20000 steps, fwd + adjoint with checkpoints every 10 steps, grid-wide sweep"),
+    "apply_6x3": ("apply_6x3: y = M(t) x, the matrix-free Lindblad apply (lb_apply, one thread per element) on "
+                  "{n} states of 6 qutrits (vec 531441, 8.5 MB each), x and y in HBM"),
     "fock_lbfgs": ("fock_lbfgs: one 4-level qudit |0> -> (|0>+|3>)/sqrt 2, J_Frob, 10 splines x 2 carriers, "
                    "T=200 ns, 10000 steps; one bench step = one L-BFGS run (lb_optimize, memory 10, "
                    "at most 150 iterations, gtol 1e-9) from the seeded controls"),
@@ -54,7 +56,7 @@ CPU_SAMPLE_STEPS = 8000  # oracle sample for the CPU baseline (same dt, 16 state
 REF_SAMPLE_STEPS = 400  # oracle sample per reference-arm step
 
 
-def problem(n_steps=None, workload="cnot_2x3"):
+def problem(n_steps=None, workload="cnot_2x3", states=0):
     import workloads as W
 
     if workload == "qubit_x":
@@ -63,7 +65,7 @@ def problem(n_steps=None, workload="cnot_2x3"):
         p = W.config4()
         n_steps = n_steps or PREFIX[workload]
     elif workload == "qutrits_6x3":
-        p = W.config5()
+        p = W.config5(n_states=states or 64)
         p.ckpt_every = 10
         n_steps = n_steps or PREFIX[workload]
     else:
@@ -238,6 +240,106 @@ def run_reference(args, rank: int, world: int):
     print(json.dumps(line), flush=True)
 
 
+def measured_peaks() -> dict:
+    """The machine's measured copy bandwidth and GEMM rates (MEASURED_PEAKS.json
+    at the repository root), or {} when absent."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(path))
+    except (OSError, ValueError):
+        return {}
+
+
+def run_apply(args, rank, world, dev):
+    """Workload apply_6x3: the Lindblad apply kernel alone at the largest state
+    size, timed per launch with CUDA events; reports its algorithmic HBM
+    bandwidth and FP64 rate against the measured copy bandwidth and the
+    derived FP64 peak."""
+    import ctypes
+
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2110_10310_gb300 import _lib
+    from paper_2110_10310_gb300.system import LindbladSystem, colmajor
+
+    n = args.states or 64
+    p = W.config5(n_steps=40, n_states=n)
+    p.system.T_ns = 300.0 * 40 / 20000
+    p.ckpt_every = 10
+    s = LindbladSystem(p, device=dev)
+    lib = _lib.load()
+    V = s.N * s.N
+    x = torch.from_numpy(colmajor(p.rho0)).to(dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    h = ctypes.c_void_p(stream.cuda_stream)
+
+    def launch():
+        _lib.check(lib.lb_apply(s.h, h, 0, 17, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()), n))
+
+    for _ in range(args.warmup):
+        launch()
+    torch.cuda.synchronize()
+    ms = []
+    gpu_id = None
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    with ClockSampler(gpu_id) as clk:
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            launch()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms) * 1e-3
+    Q = len(p.system.levels)
+    n_decay = int(sum(1 for v in p.system.t1_us if np.isfinite(v) and v > 0))
+    flops = n * V * (24 * Q + 4 * n_decay + 10)
+    nbytes = n * V * 32
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs") or 6800.0
+    fp64_peak = FP64_FLOP_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
+    if rank == 0:
+        line = {
+            "metric": "Lindblad apply state-applies/s (FP64)",
+            "value": world * n / t,
+            "unit": "state-applies/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": 1e3 * t,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS["apply_6x3"].format(n=n),
+                       "l2": "inputs ({:.0f} MB in, {:.0f} MB out) larger than L2".format(nbytes / 2e6, nbytes / 2e6),
+                       "flops_per_element": 24 * Q + 4 * n_decay + 10, "bytes_per_element": 32},
+            "roofline": {
+                "kernel": "k_apply",
+                "bound": "alu",
+                "achieved": flops / t / 1e12,
+                "peak": fp64_peak,
+                "unit": "TFLOP/s",
+                "frac": flops / t / 1e12 / fp64_peak,
+                "hbm_achieved_gbs": nbytes / t / 1e9,
+                "hbm_peak_gbs": hbm_peak,
+                "hbm_frac": nbytes / t / 1e9 / hbm_peak,
+                "traffic": None,
+            },
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+
+
 def run_optimize(args, rank, world, dev):
     """Workload fock_lbfgs: the L-BFGS loop above the gradient.  Every bench
     step runs the whole optimisation from the same seeded controls (the runs
@@ -398,6 +500,8 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="cnot_2x3", choices=sorted(WORKLOADS))
+    ap.add_argument("--states", type=int, default=0,
+                    help="initial states of qutrits_6x3 / apply_6x3 (default 64; smaller for ncu captures)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
 
@@ -436,7 +540,9 @@ def main():
         return run_batch(args, rank, world, dev)
     if args.workload == "fock_lbfgs":
         return run_optimize(args, rank, world, dev)
-    p = problem(workload=args.workload)
+    if args.workload == "apply_6x3":
+        return run_apply(args, rank, world, dev)
+    p = problem(workload=args.workload, states=args.states)
     s = LindbladSystem(p, device=dev)
     s.set_timing(True)
     stream = torch.cuda.current_stream()
@@ -544,7 +650,7 @@ def main():
             "dtype": "f64",
             "data": "synthetic",
             "config": {
-                "workload": WORKLOADS[args.workload].format(n=p.system.n_steps),
+                "workload": WORKLOADS[args.workload].format(n=p.system.n_steps, m=p.M),
                 "states": p.M,
                 "n_steps": p.system.n_steps,
                 "ckpt_every": st["ckpt_every"],

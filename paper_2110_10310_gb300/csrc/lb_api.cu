@@ -168,11 +168,17 @@ int effective_K(const lb_system* s) {
   return s->NT < 100 ? (int)s->NT : 100;
 }
 
+// Cluster sweep configuration of this system with 2Q (cs = false) or 4Q
+// lanes per element; C == 0 when it cannot apply.
+lbk::ClusterConfig cluster_cfg(const lb_system* s, bool cs) {
+  if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT || s->method == LB_SOLVER_GMRES) return lbk::ClusterConfig{};
+  return lbk::cluster_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, cs);
+}
+
 // CTAs per state of the cluster sweep if it can apply to this system (0: never)
 int cluster_ctas(const lb_system* s) {
-  if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT || s->method == LB_SOLVER_GMRES) return 0;
-  const lbk::ClusterConfig cc = lbk::cluster_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N);
-  return cc.C > 0 ? cc.C : 0;
+  const int c0 = cluster_cfg(s, false).C, c1 = cluster_cfg(s, true).C;
+  return std::max(std::max(c0, c1), 0);
 }
 
 // complex values of the GMRES Krylov basis in shared memory (0 for the
@@ -197,18 +203,17 @@ int decide_krylov(lb_system* s) {
   return LB_OK;
 }
 
-// warps per CTA of the cluster sweep (0 when it cannot apply)
-int cluster_warps(const lb_system* s) {
-  if (cluster_ctas(s) <= 0) return 0;
-  return lbk::cluster_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N).threads / 32;
-}
-
 // slots of the gradient pieces: one (summed) for grid sweeps, one per state,
-// CTA and warp where cluster sweeps can run, one per state otherwise
+// CTA and warp where cluster sweeps can run (enough for either lane layout),
+// one per state otherwise
 size_t gproj_slots(const lb_system* s) {
   if (use_grid(s)) return 1;
-  const int C = cluster_ctas(s);
-  return C > 0 ? (size_t)s->M * C * cluster_warps(s) : (size_t)s->M;
+  size_t per = 1;
+  for (int cs = 0; cs < 2; ++cs) {
+    const lbk::ClusterConfig cc = cluster_cfg(s, cs != 0);
+    if (cc.C > 0) per = std::max(per, (size_t)cc.C * (cc.threads / 32));
+  }
+  return (size_t)s->M * per;
 }
 
 // slots the bound sweep writes
@@ -561,13 +566,16 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
       if (threads > 512 || (E > 1 && threads < 64)) continue;
       cands.push_back({LB_SWEEP_RESIDENT, m, E});
     }
-    if (s->cc.C > 0 && m != LB_SOLVER_GMRES) cands.push_back({LB_SWEEP_CLUSTER, m, 0});
+    if (m != LB_SOLVER_GMRES && s->cc.C > 0)
+      for (int cs = 0; cs < 2; ++cs)
+        if (cluster_cfg(s, cs != 0).C > 0) cands.push_back({LB_SWEEP_CLUSTER, m, cs});
   }
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   LB_CUDA(cudaEventCreate(&e0), "cudaEventCreate");
   LB_CUDA(cudaEventCreate(&e1), "cudaEventCreate");
   const lbk::ResidentConfig rc0 = s->rc;
   const bool cl0 = s->cluster;
+  const lbk::ClusterConfig cc0 = s->cc;
   const int m0 = s->method;
   float best = -1.0f;
   Cand win{-1, m0, 0};
@@ -577,6 +585,7 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
     s->method = c.method;
     s->hp.method = c.method;
     s->cluster = c.sweep == LB_SWEEP_CLUSTER;
+    if (s->cluster) s->cc = cluster_cfg(s, c.E != 0);
     s->hp.gM = gproj_used(s);
     if (c.sweep == LB_SWEEP_RESIDENT) {
       s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true, kry_elems(s));
@@ -614,6 +623,7 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
   if (win.sweep < 0) {
     s->rc = rc0;
     s->cluster = cl0;
+    s->cc = cc0;
     s->method = s->hp.method = m0;
     s->hp.gM = gproj_used(s);
     LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
@@ -621,6 +631,7 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
   }
   s->method = s->hp.method = win.method;
   s->cluster = win.sweep == LB_SWEEP_CLUSTER;
+  s->cc = s->cluster ? cluster_cfg(s, win.E != 0) : cc0;
   s->hp.gM = gproj_used(s);
   if (win.sweep == LB_SWEEP_RESIDENT) {
     s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true, kry_elems(s));
@@ -764,7 +775,7 @@ int lb_set_sweep(lb_system* s, int32_t sweep) {
   if (s->ws) return fail(LB_EINVAL, "choose the sweep before binding a workspace");
   if (sweep != LB_SWEEP_AUTO && sweep != LB_SWEEP_RESIDENT && sweep != LB_SWEEP_GRID && sweep != LB_SWEEP_CLUSTER)
     return fail(LB_EINVAL, "unknown sweep kind");
-  if (sweep == LB_SWEEP_CLUSTER && lbk::cluster_config(s->V, s->Q, 1, 1, 1).C <= 0)
+  if (sweep == LB_SWEEP_CLUSTER && lbk::cluster_config(s->V, s->Q, 1, 1, 1, false).C <= 0)
     return fail(LB_EINVAL, "cluster sweeps need Q <= 4 and N^2 * 2Q <= 1024");
   if (sweep == LB_SWEEP_RESIDENT && s->V > lbk::kMaxResidentV)
     return fail(LB_EINVAL, "one CTA per state needs N^2 <= 4096");
@@ -798,15 +809,19 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
   if (rc) return rc;
   s->cluster = false;
   if (!use_grid(s) && s->sweep != LB_SWEEP_RESIDENT && s->method != LB_SOLVER_GMRES) {
-    s->cc = lbk::cluster_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N);
+    // 4Q lanes per element (shorter FP64 chain per iteration) when every
+    // state's cluster still gets its own SMs, else 2Q lanes
+    const lbk::ClusterConfig c1 = cluster_cfg(s, true), c0 = cluster_cfg(s, false);
     int dev = 0, nsm = 0;
     LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     LB_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    const bool fit1 = c1.C > 0 && (long long)s->M * c1.C <= nsm, fit0 = c0.C > 0 && (long long)s->M * c0.C <= nsm;
+    s->cc = fit1 ? c1 : c0;
     if (s->sweep == LB_SWEEP_CLUSTER) {
       if (s->cc.C <= 0) return fail(LB_EINVAL, "cluster sweeps need Q <= 4 and N^2 * 2Q <= 1024");
       s->cluster = true;
     } else {
-      s->cluster = s->cc.C > 0 && (long long)s->M * s->cc.C <= nsm;
+      s->cluster = fit1 || fit0;
     }
   }
   if (use_grid(s)) {

@@ -149,14 +149,16 @@ cudaError_t launch_sweep_grid(const ProbDev* d_prob, int mode, int init_from_q0,
 cudaError_t launch_backward_grid(const ProbDev* d_prob, int nblocks, size_t smem, cudaStream_t s);
 
 // cluster-split sweeps for small states: one cluster of C CTAs per state,
-// 2Q lanes per element (Q <= 4, N^2 * lanes <= 1024)
+// 2Q lanes per element, or 4Q with the component split (Q <= 4,
+// N^2 * lanes <= 1024)
 struct ClusterConfig {
   int C;        // CTAs per cluster (0: not applicable)
   int QT;       // subsystems (compile-time kernel variant)
   int threads;  // threads per CTA
   size_t smem;  // dynamic shared memory per CTA
+  bool cs;      // 4Q lanes per element (one per half and component) instead of 2Q
 };
-ClusterConfig cluster_config(int V, int Q, int ncoef, int njcoef, int N);
+ClusterConfig cluster_config(int V, int Q, int ncoef, int njcoef, int N, bool cs);
 cudaError_t launch_forward_cluster(const ProbDev* d_prob, int M, int tape, const ClusterConfig& cc, cudaStream_t s);
 cudaError_t launch_backward_cluster(const ProbDev* d_prob, int M, const ClusterConfig& cc, cudaStream_t s);
 cudaError_t launch_propagate_cluster(const ProbDev* d_prob, int adjoint, int64_t j0, int64_t j1, double2* x, int n_vec,

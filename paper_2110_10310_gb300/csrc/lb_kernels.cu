@@ -1158,9 +1158,12 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
 // next time step is formed locally from the replicas, so a time step needs
 // no exchange besides the inner iterations.
 
-template <int QT>
+// Lanes per element: 2Q (one half P or R of a subsystem each), or with CS
+// ("component split") 4Q, two lanes per half, one for the real and one for
+// the imaginary part of its contribution; rounded up to a power of two.
+template <int QT, bool CS = false>
 struct ClLanes {
-  static constexpr int L = 2 * QT <= 2 ? 2 : (2 * QT <= 4 ? 4 : 8);
+  static constexpr int L = CS ? (4 * QT <= 4 ? 4 : (4 * QT <= 8 ? 8 : 16)) : (2 * QT <= 2 ? 2 : (2 * QT <= 4 ? 4 : 8));
 };
 
 constexpr long long kMbarSpinLimit = 1LL << 24;
@@ -1302,14 +1305,15 @@ struct ClPlan {
   int r;        // lane within the element, 0..L-1
   int q;        // subsystem of this lane's half (0 for padding lanes)
   bool rhalf;   // R half (else P half)
+  bool act;     // the lane has a half (not a padding lane)
   int oa, ob, ojf, oja;
   double ca, cb, cjf, cja;
   double2 d;    // the element's entry of S.dv
 };
 
-template <int QT>
+template <int QT, bool CS>
 __device__ ClPlan cl_plan(const ClSmem& S, int C, int crank) {
-  constexpr int L = ClLanes<QT>::L;
+  constexpr int L = ClLanes<QT, CS>::L;
   const Hdr& H = *S.hdr;
   const int Vc = (H.V + C - 1) / C;
   const int le = threadIdx.x / L;
@@ -1318,7 +1322,9 @@ __device__ ClPlan cl_plan(const ClSmem& S, int C, int crank) {
   const int v = crank * Vc + le;
   pl.ev = le < Vc && v < H.V;
   pl.v = pl.ev ? v : 0;
-  const int u = pl.r < 2 * QT ? pl.r : -1;
+  const int hv = CS ? (pl.r >> 1) : pl.r;  // half index of this lane
+  const int u = hv < 2 * QT ? hv : -1;
+  pl.act = pl.ev && u >= 0;
   pl.q = u >= 0 ? u / 2 : 0;
   pl.rhalf = u >= 0 && (u & 1);
   pl.oa = pl.ob = pl.ojf = pl.oja = pl.v;
@@ -1398,11 +1404,11 @@ __device__ __forceinline__ void cl_record(const ClSmem& S, int e, double2 z, dou
   S.ch[(size_t)h.slot * V + e] = make_double2(cr, ci);
 }
 
-template <int QT, bool ADJ>
+template <int QT, bool ADJ, bool CS>
 __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __restrict__ rr,
                         const double2* __restrict__ ct, double fac, int C, int crank, ClCount& cnt,
                         double2& zout, ClHist hist = ClHist()) {
-  constexpr int L = ClLanes<QT>::L;
+  constexpr int L = ClLanes<QT, CS>::L;
   const Hdr& H = *S.hdr;
   const int V = H.V;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -1442,10 +1448,16 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
     Ai = -Ai;
   }
   const double di = ADJ ? -pl.d.y : pl.d.y;
-  const bool odd = pl.r & 1;
+  const bool odd = pl.r & 1;  // with CS: this lane's component (imaginary)
   const double sdi = odd ? di : -di;
   const double2 rhs = rr[pl.v];
   const double2 r0 = pl.r == 0 ? rhs : make_double2(0.0, 0.0);
+  // CS: this lane's component of U xa + W xb, U = A ca, W = -A cb (real:
+  // U.r xa.x - U.i xa.y + W.r xb.x - W.i xb.y; imaginary: U.r xa.y + U.i xa.x
+  // + W.r xb.y + W.i xb.x), started from rhs on the two lanes of half 0
+  const double u1 = Ar * pl.ca, u2 = odd ? Ai * pl.ca : -(Ai * pl.ca);
+  const double u3 = -(Ar * pl.cb), u4 = odd ? -(Ai * pl.cb) : Ai * pl.cb;
+  const double init = pl.r < 2 ? (odd ? rhs.y : rhs.x) : 0.0;
   const double cj = ADJ ? pl.cja : pl.cjf;
   const int oj = ADJ ? pl.oja : pl.ojf;
   const unsigned tx = (unsigned)V * 16u + (unsigned)(C * nwarps) * 4u;
@@ -1465,20 +1477,30 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
     if (threadIdx.x == 0) mbar_arrive_expect_tx(mb_local, tx);
     const double2* __restrict__ zc = S.zb + (size_t)(cnt.gk & 1) * V;
     const double2 xa = zc[pl.oa], xb = zc[pl.ob], x5 = zc[oj], zo = zc[pl.v];
-    const double xr = fma(-pl.cb, xb.x, pl.ca * xa.x);
-    const double xi = fma(-pl.cb, xb.y, pl.ca * xa.y);
-    // lane 0 of the element starts from the right-hand side
-    double accr = fma(Ar, xr, fma(-Ai, xi, r0.x));
-    double acci = fma(Ar, xi, fma(Ai, xr, r0.y));
-    accr = fma(cj, x5.x, accr);
-    acci = fma(cj, x5.y, acci);
-    // Sum over the element's L lanes with one component per lane: after the
-    // first exchange even lanes carry the real and odd lanes the imaginary
-    // part, so each level costs one FP64 add.
-    double k = odd ? acci : accr;
-    k += __shfl_xor_sync(kFull, odd ? accr : acci, 1);
+    double k;
+    if constexpr (CS) {
+      k = fma(u1, odd ? xa.y : xa.x,
+              fma(u2, odd ? xa.x : xa.y, fma(u3, odd ? xb.y : xb.x, fma(u4, odd ? xb.x : xb.y,
+                                                                       fma(cj, odd ? x5.y : x5.x, init)))));
+      // sum over the halves: lanes of the same component
 #pragma unroll
-    for (int o = 2; o < L; o <<= 1) k += __shfl_xor_sync(kFull, k, o);
+      for (int o = 2; o < L; o <<= 1) k += __shfl_xor_sync(kFull, k, o);
+    } else {
+      const double xr = fma(-pl.cb, xb.x, pl.ca * xa.x);
+      const double xi = fma(-pl.cb, xb.y, pl.ca * xa.y);
+      // lane 0 of the element starts from the right-hand side
+      double accr = fma(Ar, xr, fma(-Ai, xi, r0.x));
+      double acci = fma(Ar, xi, fma(Ai, xr, r0.y));
+      accr = fma(cj, x5.x, accr);
+      acci = fma(cj, x5.y, acci);
+      // Sum over the element's L lanes with one component per lane: after the
+      // first exchange even lanes carry the real and odd lanes the imaginary
+      // part, so each level costs one FP64 add.
+      k = odd ? acci : accr;
+      k += __shfl_xor_sync(kFull, odd ? accr : acci, 1);
+#pragma unroll
+      for (int o = 2; o < L; o <<= 1) k += __shfl_xor_sync(kFull, k, o);
+    }
     const double am = k;  // this lane's component of rhs + dt/2 O z
     const double zom = odd ? zo.y : zo.x;
     double zm;
@@ -1529,7 +1551,7 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
 
 __device__ __forceinline__ int cl_code(int it) { return it == -1 ? LB_ENOTCONV : (it == -2 ? LB_ENAN : LB_ECUDA); }
 
-template <int QT>
+template <int QT, bool CS>
 __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict__ pp, int tape) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
@@ -1539,7 +1561,7 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
   const ClSmem S = cl_carve(smem, P.ncoef, P.njcoef, P.N, P.V);
   cl_setup(S, P, cl);
   const Hdr& H = *S.hdr;
-  const ClPlan pl = cl_plan<QT>(S, C, crank);
+  const ClPlan pl = cl_plan<QT, CS>(S, C, crank);
   const size_t base = (size_t)i * H.V;
   for (int e = threadIdx.x; e < H.V; e += blockDim.x) S.rr[e] = P.q0[base + e];
   ClCount cnt;
@@ -1553,7 +1575,7 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
     if (tape && H.K > 0 && j % H.K == 0 && crank == 0)
       for (int e = threadIdx.x; e < H.V; e += blockDim.x) P.ckpt[((size_t)i * H.n_ckpt + j / H.K) * H.V + e] = S.rr[e];
     double2 z;
-    const int it = cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z, pred ? hist : ClHist());
+    const int it = cl_solve<QT, false, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z, pred ? hist : ClHist());
     if (it < 0) {
       if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
       failed = true;
@@ -1596,18 +1618,18 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
   cl.sync();  // no CTA leaves while another may still push into it
 }
 
-template <int QT>
+template <int QT, bool CS>
 __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restrict__ pp) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
-  constexpr int L = ClLanes<QT>::L;
+  constexpr int L = ClLanes<QT, CS>::L;
   const ProbDev& P = *pp;
   const int C = (int)cl.num_blocks(), crank = (int)cl.block_rank();
   const int i = blockIdx.x / C;
   const ClSmem S = cl_carve(smem, P.ncoef, P.njcoef, P.N, P.V);
   cl_setup(S, P, cl);
   const Hdr& H = *S.hdr;
-  const ClPlan pl = cl_plan<QT>(S, C, crank);
+  const ClPlan pl = cl_plan<QT, CS>(S, C, crank);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const size_t base = (size_t)i * H.V;
   const double w = P.wgt[i];
@@ -1638,7 +1660,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
       for (int e = threadIdx.x; e < H.V; e += blockDim.x) S.rr[e] = P.ckpt[((size_t)i * H.n_ckpt + sg) * H.V + e];
       for (int j = j0; j < j1; ++j) {
         double2 z;
-        const int it = cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z);
+        const int it = cl_solve<QT, false, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z);
         if (it < 0) {
           if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
           failed = true;
@@ -1657,12 +1679,12 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
     }
     for (int j = j1 - 1; j >= j0; --j) {
       // this lane's stage vector element, loaded before the solve so that its latency is hidden
-      const bool gl = pl.ev && pl.r < 2 * QT;
+      const bool gl = pl.act;
       const double2 Z = gl ? (H.K > 0 ? P.seg[((size_t)i * H.K + (j - j0)) * H.V + pl.v]
                                       : P.ckpt[((size_t)i * H.NT + j) * H.V + pl.v])
                            : make_double2(0.0, 0.0);
       double2 zh;
-      const int it = cl_solve<QT, true>(S, pl, S.ll, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, zh, apred ? ahist : ClHist());
+      const int it = cl_solve<QT, true, CS>(S, pl, S.ll, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, zh, apred ? ahist : ClHist());
       if (it < 0) {
         if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
         failed = true;
@@ -1679,10 +1701,28 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
         const double2 xa = zb[pl.oa], xb = zb[pl.ob];
         const double xr = fma(-pl.cb, xb.x, pl.ca * xa.x);
         const double xi = fma(-pl.cb, xb.y, pl.ca * xa.y);
-        sr = fma(Z.x, xr, Z.y * xi);
-        si = fma(Z.y, xr, -Z.x * xi);
+        if constexpr (CS) {
+          // this lane's component only
+          sr = (pl.r & 1) ? fma(Z.y, xr, -Z.x * xi) : fma(Z.x, xr, Z.y * xi);
+        } else {
+          sr = fma(Z.x, xr, Z.y * xi);
+          si = fma(Z.y, xr, -Z.x * xi);
+        }
       }
-      if constexpr (L < 32) {
+      if constexpr (CS) {
+#pragma unroll
+        for (int o = L; o < 32; o <<= 1) sr += __shfl_xor_sync(kFull, sr, o);
+        // lane r < L holds the warp's sum of component r & 1 of half r >> 1;
+        // store -i (sr + i si) = (si, -sr)
+        const int hv = lane >> 1;
+        if (lane < L && hv < 2 * QT) {
+          double* g = reinterpret_cast<double*>(gbase + ((size_t)j * H.Q + (hv >> 1)) * 2 + ((hv & 1) ? 0 : 1));
+          if (lane & 1)
+            g[0] = sr;
+          else
+            g[1] = -sr;
+        }
+      } else if constexpr (L < 32) {
         const bool hi = lane & L;
         double k = hi ? si : sr;
         k += __shfl_xor_sync(kFull, hi ? sr : si, L);
@@ -1708,7 +1748,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
   cl.sync();
 }
 
-template <int QT>
+template <int QT, bool CS>
 __global__ void __launch_bounds__(128, 1) k_propagate_cl(const ProbDev* __restrict__ pp, int adjoint, int j0, int j1,
                                                       double2* __restrict__ x) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1719,7 +1759,7 @@ __global__ void __launch_bounds__(128, 1) k_propagate_cl(const ProbDev* __restri
   const ClSmem S = cl_carve(smem, P.ncoef, P.njcoef, P.N, P.V);
   cl_setup(S, P, cl);
   const Hdr& H = *S.hdr;
-  const ClPlan pl = cl_plan<QT>(S, C, crank);
+  const ClPlan pl = cl_plan<QT, CS>(S, C, crank);
   double2* xv = x + (size_t)i * H.V;
   for (int e = threadIdx.x; e < H.V; e += blockDim.x) S.rr[e] = xv[e];
   ClCount cnt;
@@ -1728,8 +1768,8 @@ __global__ void __launch_bounds__(128, 1) k_propagate_cl(const ProbDev* __restri
   for (int jj = 0; jj < j1 - j0; ++jj) {
     const int j = adjoint ? j1 - 1 - jj : j0 + jj;
     double2 z;
-    const int it = adjoint ? cl_solve<QT, true>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z)
-                           : cl_solve<QT, false>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z);
+    const int it = adjoint ? cl_solve<QT, true, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z)
+                           : cl_solve<QT, false, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z);
     if (it < 0) {
       if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
       failed = true;
@@ -2743,28 +2783,30 @@ cudaError_t launch_objective_states(const ProbDev* d_prob, int M, cudaStream_t s
 
 // ---- cluster-split sweeps ----------------------------------------------------
 
-ClusterConfig cluster_config(int V, int Q, int ncoef, int njcoef, int N) {
+ClusterConfig cluster_config(int V, int Q, int ncoef, int njcoef, int N, bool cs) {
   ClusterConfig cc{};
   if (Q < 1 || Q > 4) return cc;
-  const int L = 2 * Q <= 2 ? 2 : (2 * Q <= 4 ? 4 : 8);
+  const int L = cs ? (4 * Q <= 4 ? 4 : (4 * Q <= 8 ? 8 : 16)) : (2 * Q <= 2 ? 2 : (2 * Q <= 4 ? 4 : 8));
   const int C = (V * L + 127) / 128;
   if (C < 1 || C > 8) return cc;
   const int Vc = (V + C - 1) / C;
   cc.C = C;
   cc.QT = Q;
+  cc.cs = cs;
   cc.threads = ((Vc * L + 31) / 32) * 32;
   cc.smem = cl_smem_bytes(ncoef, njcoef, N, V);
   return cc;
 }
 
-template <int QT>
+template <int QT, bool CS>
 struct ClKernels {
   static cudaError_t attrs(size_t smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_forward_cl<QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_forward_cl<QT, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_backward_cl<QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_backward_cl<QT, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_propagate_cl<QT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_propagate_cl<QT, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   }
   template <class K, class... Args>
   static cudaError_t launch(K kern, const ClusterConfig& cc, int n_states, cudaStream_t s, Args... args) {
@@ -2786,27 +2828,35 @@ struct ClKernels {
   }
 };
 
-#define LB_CL_DISPATCH(cc, EXPR_T)          \
-  switch ((cc).QT) {                          \
-    case 1: { constexpr int QT_ = 1; EXPR_T } \
-    case 2: { constexpr int QT_ = 2; EXPR_T } \
-    case 3: { constexpr int QT_ = 3; EXPR_T } \
-    case 4: { constexpr int QT_ = 4; EXPR_T } \
-    default: return cudaErrorInvalidValue;    \
+#define LB_CL_DISPATCH_CS(cc, CS_, ...)                                          \
+  switch ((cc).QT) {                                                             \
+    case 1: { constexpr int QT_ = 1; constexpr bool CSV_ = CS_; __VA_ARGS__ }    \
+    case 2: { constexpr int QT_ = 2; constexpr bool CSV_ = CS_; __VA_ARGS__ }    \
+    case 3: { constexpr int QT_ = 3; constexpr bool CSV_ = CS_; __VA_ARGS__ }    \
+    case 4: { constexpr int QT_ = 4; constexpr bool CSV_ = CS_; __VA_ARGS__ }    \
+    default: return cudaErrorInvalidValue;                                       \
   }
+#define LB_CL_DISPATCH(cc, ...)                 \
+  do {                                          \
+    if ((cc).cs) {                              \
+      LB_CL_DISPATCH_CS(cc, true, __VA_ARGS__)  \
+    } else {                                    \
+      LB_CL_DISPATCH_CS(cc, false, __VA_ARGS__) \
+    }                                           \
+  } while (0)
 
 cudaError_t launch_forward_cluster(const ProbDev* d_prob, int M, int tape, const ClusterConfig& cc, cudaStream_t s) {
-  LB_CL_DISPATCH(cc, return ClKernels<QT_>::launch(k_forward_cl<QT_>, cc, M, s, d_prob, tape);)
+  LB_CL_DISPATCH(cc, return ClKernels<QT_, CSV_>::launch(k_forward_cl<QT_, CSV_>, cc, M, s, d_prob, tape););
 }
 
 cudaError_t launch_backward_cluster(const ProbDev* d_prob, int M, const ClusterConfig& cc, cudaStream_t s) {
-  LB_CL_DISPATCH(cc, return ClKernels<QT_>::launch(k_backward_cl<QT_>, cc, M, s, d_prob);)
+  LB_CL_DISPATCH(cc, return ClKernels<QT_, CSV_>::launch(k_backward_cl<QT_, CSV_>, cc, M, s, d_prob););
 }
 
 cudaError_t launch_propagate_cluster(const ProbDev* d_prob, int adjoint, int64_t j0, int64_t j1, double2* x, int n_vec,
                                      const ClusterConfig& cc, cudaStream_t s) {
-  LB_CL_DISPATCH(cc, return ClKernels<QT_>::launch(k_propagate_cl<QT_>, cc, n_vec, s, d_prob, adjoint, (int)j0,
-                                                   (int)j1, x);)
+  LB_CL_DISPATCH(cc, return ClKernels<QT_, CSV_>::launch(k_propagate_cl<QT_, CSV_>, cc, n_vec, s, d_prob, adjoint,
+                                                        (int)j0, (int)j1, x););
 }
 
 }  // namespace lbk

@@ -149,10 +149,15 @@ def test_workspace_size_accounts_for_checkpoints(lib, K):
         else:
             Kc = min(K, NT)
             tape = -(-NT // Kc) * state + Kc * state
-        C = -(-Vl * 4 // 128)  # CTAs per state of the cluster sweep (2Q = 4 lanes per element)
-        nw = -(-(-(-Vl // C)) * 4 // 32)  # warps per CTA
-        # per-warp gradient pieces of every state, and their sum over the slots
-        gproj = M * C * nw * NT * 2 * 2 * 16 + NT * 2 * 2 * 16
+        # per-warp gradient pieces of every state, enough for either lane
+        # layout of the cluster sweep (2Q = 4 or 4Q = 8 lanes per element),
+        # and their sum over the slots
+        per = 0
+        for lanes in (4, 8):
+            C = -(-Vl * lanes // 128)  # CTAs per state
+            nw = -(-(-(-Vl // C)) * lanes // 32)  # warps per CTA
+            per = max(per, C * nw)
+        gproj = M * per * NT * 2 * 2 * 16 + NT * 2 * 2 * 16
         # q0, tar, qT and the six-step ring of the first-iterate predictor
         assert n.value >= tape + gproj + (3 + 6) * state
         assert n.value <= tape + gproj + (3 + 6) * state + 64 * 1024

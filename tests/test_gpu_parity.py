@@ -396,10 +396,11 @@ def test_qudits_4x4_full_size_checkpoints_bitwise():
 
 
 @pytest.mark.parametrize("levels,K,herm", [((2,), 7, False), ((2, 3), 0, True), ((2, 2, 2), 100, False),
-                                            ((3, 2), 5, True), ((3, 3), 7, False)])
+                                            ((3, 2), 5, True), ((3, 3), 7, False), ((4, 4), 0, True)])
 def test_cluster_sweep_matches_oracle(levels, K, herm):
     """The cluster sweep against the oracle (1e-10 / 1e-9) and against the
-    one-CTA-per-state sweep."""
+    one-CTA-per-state sweep.  N^2 4Q <= 1024 runs 4Q lanes per element (one
+    per half and component); (4, 4) only fits 2Q lanes."""
     from paper_2110_10310_gb300 import _lib as L
 
     p = W.random_problem(601, levels=levels, n_states=3, n_steps=40, T_ns=0.8, amp=0.1, ckpt_every=K,
@@ -409,6 +410,29 @@ def test_cluster_sweep_matches_oracle(levels, K, herm):
     Gr, gr = _sys(p, sweep=L.LB_SWEEP_RESIDENT).gradient()
     assert abs(Gc - Gr) <= 1e-12 * abs(Gr)
     assert _rel(gc, gr) < 1e-11
+
+
+def test_cluster_lane_layouts_agree():
+    """Forty states of N^2 = 81: 4Q lanes would need 240 SMs, so the sweep
+    binds with 2Q lanes; the autotuner times both layouts, and all agree."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(603, levels=(3, 3), n_states=40, n_steps=30, T_ns=0.6, amp=0.1)
+    s = _sys(p, sweep=L.LB_SWEEP_CLUSTER)
+    G2, g2 = s.gradient()
+    q = copy.deepcopy(p)
+    q.rho0 = p.rho0[:3]
+    q.targets = p.targets[:3]
+    s4 = _sys(q, sweep=L.LB_SWEEP_CLUSTER)
+    G4, g4 = s4.gradient()
+    s2 = _sys(q, sweep=L.LB_SWEEP_RESIDENT)
+    Gr, gr = s2.gradient()
+    assert abs(G4 - Gr) <= 1e-12 * abs(Gr) and _rel(g4, gr) < 1e-11
+    Go, go, _ = imr.gradient(p)
+    assert abs(G2 - Go) <= 1e-10 * abs(Go) and _rel(g2, go) < 1e-9
+    choice = s.autotune(probe_steps=5)
+    G3, g3 = s.gradient()
+    assert abs(G3 - Go) <= 1e-10 * abs(Go) and _rel(g3, go) < 1e-9
 
 
 def test_cluster_steps_and_bitwise_checkpoints():
@@ -560,3 +584,16 @@ def test_lbfgs_trajectory_matches_oracle():
     # the final iterate stays set: a plain gradient call reproduces the final G
     G, _ = s.gradient()
     assert G == res["G"]
+
+
+def test_autotune_picks_gmres_when_the_fixed_points_diverge():
+    """On the stiff problem only GMRES converges: the autotuner keeps it, and
+    the gradient after tuning matches the oracle."""
+    p = _stiff_problem()
+    s = _sys(p, max_iter=400)
+    choice = s.autotune(probe_steps=10)
+    assert choice["solver"] == "gmres" and choice["sweep"] == "resident"
+    G, g = s.gradient()
+    Go, go, _ = imr.gradient(p)
+    assert abs(G - Go) <= 1e-10 * abs(Go)
+    assert _rel(g, go) < 1e-9

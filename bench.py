@@ -35,6 +35,8 @@ WORKLOAD = ("cnot_2x3: 2 transmons x 3 levels (N=9, vec 81), 16 essential-basis 
 # other workloads (--workload), measured the same way; the default line is cnot_2x3
 WORKLOADS = {
     "cnot_2x3": WORKLOAD,
+    "cnot_3states": ("cnot_3states: the cnot_2x3 system and controls with the three-state gate objective "
+                     "(Sec. III-C: 3 Hermitian states, weights 20, 1, 1), 10000 steps, fwd + adjoint"),
     "qubit_x": "qubit_x: 1 qubit (vec 4), 4 states |i><j|, 1000 steps, T=100 ns, X gate, fwd + adjoint",
     "batch256": ("batch256: 256 independent problems, Q in {1,2,3}, 2-4 levels (vec 4..4096), 3 random pure states "
                  "each, 5000 steps, T=100 ns, fwd + adjoint, one persistent launch per sweep captured in a CUDA graph"),
@@ -61,6 +63,8 @@ def problem(n_steps=None, workload="cnot_2x3", states=0):
 
     if workload == "qubit_x":
         p = W.config1()
+    elif workload == "cnot_3states":
+        p = W.cnot_three_states()
     elif workload == "qudits_4x4":
         p = W.config4()
         n_steps = n_steps or PREFIX[workload]

@@ -597,3 +597,11 @@ def test_autotune_picks_gmres_when_the_fixed_points_diverge():
     Go, go, _ = imr.gradient(p)
     assert abs(G - Go) <= 1e-10 * abs(Go)
     assert _rel(g, go) < 1e-9
+
+
+@pytest.mark.parametrize("objective", ["frob", "trace"])
+def test_three_state_gate_objective_matches_oracle(objective):
+    """The CNOT workload with the three-state gate objective (Sec. III-C:
+    weights 20, 1, 1, purity-scaled for J_Tr) over its full 10000 steps."""
+    p = W.cnot_three_states(objective=objective)
+    _check_problem(p)

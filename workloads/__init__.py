@@ -18,6 +18,8 @@ from .synthetic import (  # noqa: F401
     config4,
     config5,
     fock_superposition,
+    three_gate_states,
+    cnot_three_states,
     random_problem,
     basis_outer,
     random_pure_state,

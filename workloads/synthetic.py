@@ -180,6 +180,41 @@ def config2(seed: int = 2, n_steps: int = 10000, levels=(3, 3)) -> Problem:
     return Problem("cnot_2x3", sysm, ctrl, rho0, "frob", gate=CNOT.copy())
 
 
+def three_gate_states(levels, essential=None) -> np.ndarray:
+    """The three initial states that distinguish any two unitaries on the
+    essential subspace (Sec. III-C), embedded in the full space:
+    rho_1 = sum_j lambda_j |j><j| with distinct lambda_j = 2 (Ne - j) / (Ne (Ne + 1)),
+    rho_2 = |psi><psi| with psi the uniform superposition, rho_3 = I / Ne."""
+    ess = essential if essential is not None else levels
+    Ne = int(np.prod(ess))
+    N = int(np.prod(levels))
+    idx = [essential_to_full(i, levels, essential) for i in range(Ne)]
+    rho = np.zeros((3, N, N), dtype=np.complex128)
+    for j, k in enumerate(idx):
+        rho[0, k, k] = 2.0 * (Ne - j) / (Ne * (Ne + 1))
+        rho[2, k, k] = 1.0 / Ne
+    for a in idx:
+        for c in idx:
+            rho[1, a, c] = 1.0 / Ne
+    return rho
+
+
+def cnot_three_states(n_steps: int = 10000, objective: str = "frob") -> Problem:
+    """The CNOT workload of ``config2`` with the three-state gate objective
+    (Sec. III-C): the states of ``three_gate_states``, weights
+    beta = (20, 1, 1), and for J_Tr each weight scaled by the purity
+    Tr(rho_i(0)^2) of its state."""
+    p = config2(n_steps=n_steps)
+    p.name = "cnot_three_states"
+    p.rho0 = three_gate_states(p.system.levels, p.system.essential)
+    w = np.array([20.0, 1.0, 1.0])
+    if objective == "trace":
+        w = w * np.array([np.real(np.trace(r @ r)) for r in p.rho0])
+    p.weights = w
+    p.objective = objective
+    return p
+
+
 def _random_problem_config3(rng, idx, n_steps):
     Q = int(rng.integers(1, 4))
     levels = tuple(int(x) for x in rng.integers(2, 5, size=Q))

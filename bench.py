@@ -181,7 +181,9 @@ def fp64_flops(V: int, Q: int, n_decay: int, st: dict, phase_set) -> float:
     factor) plus 4 for the decay sandwich when T1 is finite; 6 for the
     multiplication by (I - dt/2 D)^-1 and 2 for the convergence difference.
     Per element and step: 6 for the initial guess, 4 for q <- 2z - q, and for
-    adjoint steps 28 per subsystem for the gradient pieces."""
+    adjoint steps 28 per subsystem for the gradient pieces.  ``V`` is the
+    number of elements a state's sweep computes: N^2, or N (N + 1) / 2 when
+    the Hermitian symmetry leaves the others as mirrored copies."""
     per_it = 24 * Q + 4 * n_decay + 8
     f = 0.0
     for ph in phase_set:
@@ -404,6 +406,7 @@ def run_optimize(args, rank, world, dev):
                 "grad_max_final": float(h[-1, 1]),
                 "ms_per_evaluation": 1e3 * sum(secs) / args.steps / res["evaluations"],
                 "sweep": st["sweep"],
+                "symmetry": st["symmetry"],
             },
             "gpu_launches": st["kernel_launches"] * res["evaluations"] * args.steps,
             "clocks": clk.summary(),
@@ -623,8 +626,9 @@ def main():
     V = s.N * s.N
     n_decay = int(sum(1 for t in p.system.t1_us if np.isfinite(t) and t > 0))
     st = sts[-1]
-    bwd_flops = fp64_flops(V, Q, n_decay, st, (1, 2))
-    fwd_flops = fp64_flops(V, Q, n_decay, st, (0,))
+    Ve = s.N * (s.N + 1) // 2 if st["symmetry"] == "hermitian" else V
+    bwd_flops = fp64_flops(Ve, Q, n_decay, st, (1, 2))
+    fwd_flops = fp64_flops(Ve, Q, n_decay, st, (0,))
     bwd_ms = statistics.median(ms_bwd)
     peak = FP64_FLOP_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
     achieved = bwd_flops / (bwd_ms * 1e-3) / 1e12
@@ -662,6 +666,7 @@ def main():
                                else p.M * (-(-p.system.n_steps // st["ckpt_every"]) + st["ckpt_every"]) * V * 16),
                 "solver": f"{st['solver']} fixed point, rtol 1e-15",
                 "sweep": st["sweep"],
+                "symmetry": st["symmetry"],
                 "l2": "flushed between timed steps (256 MiB write)",
                 "parallelism": f"replicas{world}" if world > 1 else "single",
                 "inner_iters_per_step": st["inner_iterations"] / max(1, st["state_steps"]),

@@ -135,7 +135,7 @@ typedef struct lb_stats {
   int32_t sweep;            /* LB_SWEEP_* kind the call ran with */
   int32_t solver;           /* LB_SOLVER_* it ran with */
   int32_t ckpt_every;       /* checkpoint interval in effect (0 = every stage vector kept) */
-  int32_t pad;
+  int32_t symmetry;         /* LB_SYM_HERMITIAN when the grid sweep iterated k <= l only */
 } lb_stats;
 
 /* ---- system ------------------------------------------------------------- */
@@ -190,6 +190,21 @@ int lb_solver_set(lb_system* sys, int32_t method, double rtol, int32_t max_iter,
 
 /* Choose the sweep kind (LB_SWEEP_*); call before lb_workspace_bytes. */
 int lb_set_sweep(lb_system* sys, int32_t sweep);
+
+/* Hermitian symmetry (Sec. III-B: density matrices, and Lindblad's equation
+ * preserves Hermiticity).  With LB_SYM_HERMITIAN (the default) the grid-wide
+ * sweeps iterate only the elements k <= l of every state and write the
+ * conjugate into (l, k) -- about half the work -- whenever every initial
+ * state set by lb_states_set and every explicit target is Hermitian to
+ * rounding (each entry within 64 eps max|entry| of the conjugate of its
+ * transposed entry; the k <= l entries are then used for both), gate
+ * targets V rho V^+ being Hermitian with their states; the adjoint
+ * states are then Hermitian too and the gradient pieces of the mirrored
+ * elements are formed from those of (k, l).  LB_SYM_NONE always iterates
+ * every element.  May be called at any time; applies from the next call. */
+#define LB_SYM_NONE 0
+#define LB_SYM_HERMITIAN 1
+int lb_set_symmetry(lb_system* sys, int32_t symmetry);
 
 /* ---- device workspace ---------------------------------------------------- */
 

@@ -36,6 +36,8 @@ LB_SOLVER_AUTO = 0
 LB_SOLVER_JACOBI = 1
 LB_SOLVER_NEUMANN = 2
 LB_SOLVER_GMRES = 3
+LB_SYM_NONE = 0
+LB_SYM_HERMITIAN = 1
 
 LB_MAX_SUBSYSTEMS = 8
 LB_MAX_LEVELS = 16
@@ -78,7 +80,7 @@ class lb_stats(ctypes.Structure):
         ("sweep", c_int32),
         ("solver", c_int32),
         ("ckpt_every", c_int32),
-        ("pad", c_int32),
+        ("symmetry", c_int32),
     ]
 
 
@@ -93,6 +95,7 @@ SIGNATURES = {
     "lb_objective_set_gate": (c_int32, [c_void_p, c_int32, c_void_p, c_double]),
     "lb_solver_set": (c_int32, [c_void_p, c_int32, c_double, c_int32, c_int32]),
     "lb_set_sweep": (c_int32, [c_void_p, c_int32]),
+    "lb_set_symmetry": (c_int32, [c_void_p, c_int32]),
     "lb_workspace_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),
     "lb_bind_workspace": (c_int32, [c_void_p, c_void_p, c_size_t, c_void_p]),
     "lb_forward": (c_int32, [c_void_p, c_void_p, POINTER(c_double), c_void_p]),

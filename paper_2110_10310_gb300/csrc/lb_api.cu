@@ -46,7 +46,7 @@ struct Region {
 
 struct Layout {
   Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
-      gproj, gsum, sfac, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist;
+      gproj, gsum, sfac, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, hmap;
   size_t total = 0;
 };
 
@@ -85,6 +85,9 @@ struct lb_system {
   int max_iter = 200;
   int K = 100;       // requested checkpoint interval; < 0 = automatic (effective_K)
   int sweep = LB_SWEEP_AUTO;
+  int symmetry = LB_SYM_HERMITIAN;
+  bool rho_herm = false;  // every initial state exactly Hermitian
+  bool tar_herm = false;  // every explicit target exactly Hermitian (gate targets: always)
   int gblocks = 0;   // cooperative grid size (grid sweeps)
   size_t gsmem = 0;  // its dynamic shared memory
   bool cluster = false;      // cluster-split sweeps (decided at bind)
@@ -273,6 +276,7 @@ Layout make_layout(const lb_system* s) {
   take(L.gslots, grid ? sizeof(unsigned long long) * 5 * M : 0);
   take(L.bar, grid ? sizeof(GridBar) : 0);
   take(L.hist, c2 * lbk::kPredOrder * M * V);
+  take(L.hmap, grid ? sizeof(int32_t) * (size_t)s->N * (s->N + 1) / 2 : 0);
   L.total = off;
   return L;
 }
@@ -340,6 +344,40 @@ int upload_targets(lb_system* s, cudaStream_t st) {
   } else {
     LB_CUDA(cudaMemsetAsync(at<double2>(s, s->L.tar), 0, bytes, st), "clear targets");
   }
+  return LB_OK;
+}
+
+// every M x N x N complex matrix (column-major, interleaved) Hermitian to
+// rounding: each entry within 64 eps max|entry| of the conjugate of its
+// transposed entry (an outer product psi psi^+ formed with fused multiply-adds
+// is Hermitian only to that level)
+bool hermitian_matrices(const double* a, int M, int N) {
+  const size_t NN = (size_t)N * N;
+  for (int i = 0; i < M; ++i) {
+    const double* m = a + 2 * (size_t)i * NN;
+    double amax = 0.0;
+    for (size_t t = 0; t < 2 * NN; ++t) amax = std::max(amax, std::fabs(m[t]));
+    const double tol = 64.0 * 2.220446049250313e-16 * amax;
+    for (int l = 0; l < N; ++l)
+      for (int k = 0; k <= l; ++k) {
+        const size_t p = (size_t)2 * (k + (size_t)N * l), q = (size_t)2 * (l + (size_t)N * k);
+        if (!(std::fabs(m[p] - m[q]) <= tol) || !(std::fabs(m[p + 1] + m[q + 1]) <= tol)) return false;
+      }
+  }
+  return true;
+}
+
+bool use_symmetry(const lb_system* s) {
+  return s->symmetry == LB_SYM_HERMITIAN && use_grid(s) && s->rho_herm && (s->target_mode == 2 || s->tar_herm);
+}
+
+// re-upload the problem block when the symmetry decision changed (bound systems)
+int refresh_symmetry(lb_system* s) {
+  if (!s->ws) return LB_OK;
+  const int h = use_symmetry(s) ? 1 : 0;
+  if (h == s->hp.herm) return LB_OK;
+  s->hp.herm = h;
+  LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, s->bind_stream), "upload problem");
   return LB_OK;
 }
 
@@ -427,7 +465,9 @@ void fill_prob(lb_system* s) {
     P.partials = at<double>(s, s->L.partials);
     P.gslots = at<unsigned long long>(s, s->L.gslots);
     P.bar = at<GridBar>(s, s->L.bar);
+    P.hmap = at<int32_t>(s, s->L.hmap);
   }
+  P.herm = use_symmetry(s) ? 1 : 0;
   P.hist = at<double2>(s, s->L.hist);
 }
 
@@ -706,11 +746,15 @@ int lb_states_set(lb_system* s, int32_t M, const double* rho0, const double* wei
   if (s->M != M && s->target_mode == 1) s->target_mode = 0;  // explicit targets no longer match
   s->M = M;
   s->wgt = w;
+  s->rho_herm = hermitian_matrices(rho0, M, s->N);
   if (s->ws) {
     int rc = upload_states(s, rho0, s->bind_stream);
     if (rc) return rc;
-    if (s->target_mode == 2) return upload_targets(s, s->bind_stream);
-    return LB_OK;
+    if (s->target_mode == 2) {
+      rc = upload_targets(s, s->bind_stream);
+      if (rc) return rc;
+    }
+    return refresh_symmetry(s);
   }
   s->rho0.assign(rho0, rho0 + (size_t)2 * M * s->V);
   return LB_OK;
@@ -725,9 +769,11 @@ int lb_objective_set(lb_system* s, int32_t kind, const double* targets, double g
   s->gamma2 = gamma2;
   s->target_mode = 1;
   s->targets.assign(targets, targets + (size_t)2 * s->M * s->V);
+  s->tar_herm = hermitian_matrices(targets, s->M, s->N);
   if (s->ws) {
     s->hp.kind = kind;
     s->hp.gamma2 = gamma2;
+    s->hp.herm = use_symmetry(s) ? 1 : 0;
     LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, s->bind_stream), "upload problem");
     return upload_targets(s, s->bind_stream);
   }
@@ -744,9 +790,11 @@ int lb_objective_set_gate(lb_system* s, int32_t kind, const double* V, double ga
   s->target_mode = 2;
   s->gateV.assign(V, V + (size_t)2 * s->Ne * s->Ne);
   s->targets.clear();
+  s->tar_herm = true;
   if (s->ws) {
     s->hp.kind = kind;
     s->hp.gamma2 = gamma2;
+    s->hp.herm = use_symmetry(s) ? 1 : 0;
     LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, s->bind_stream), "upload problem");
     return upload_targets(s, s->bind_stream);
   }
@@ -768,6 +816,13 @@ int lb_solver_set(lb_system* s, int32_t method, double rtol, int32_t max_iter, i
   s->K = ckpt_every > s->NT ? (int)s->NT : ckpt_every;
   if (ckpt_every < 0) s->K = LB_CKPT_AUTO;
   return LB_OK;
+}
+
+int lb_set_symmetry(lb_system* s, int32_t symmetry) {
+  if (!s) return fail(LB_EINVAL, "null system handle");
+  if (symmetry != LB_SYM_NONE && symmetry != LB_SYM_HERMITIAN) return fail(LB_EINVAL, "unknown symmetry");
+  s->symmetry = symmetry;
+  return refresh_symmetry(s);
 }
 
 int lb_set_sweep(lb_system* s, int32_t sweep) {
@@ -862,6 +917,17 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
                             cudaMemcpyHostToDevice, st),
             "upload carriers");
   LB_CUDA(lbk::launch_tables(s->dp, s->hp, st), "tables kernel");
+  if (use_grid(s)) {
+    // vec indices k + N l with k <= l, column by column (the grid sweeps' Hermitian loop order)
+    std::vector<int32_t> hmap;
+    hmap.reserve((size_t)s->N * (s->N + 1) / 2);
+    for (int l = 0; l < s->N; ++l)
+      for (int k = 0; k <= l; ++k) hmap.push_back(k + s->N * l);
+    LB_CUDA(cudaMemcpyAsync(at<int32_t>(s, s->L.hmap), hmap.data(), sizeof(int32_t) * hmap.size(),
+                            cudaMemcpyHostToDevice, st),
+            "upload symmetry map");
+    // the pageable source is staged before the call returns
+  }
   rc = upload_states(s, s->rho0.data(), st);
   if (rc) return rc;
   rc = upload_targets(s, st);
@@ -928,6 +994,7 @@ static int finish(lb_system* s, cudaStream_t st, double* G_out, double* grad_out
   s->last.sweep = use_grid(s) ? LB_SWEEP_GRID : (s->cluster ? LB_SWEEP_CLUSTER : LB_SWEEP_RESIDENT);
   s->last.solver = s->method;
   s->last.ckpt_every = effective_K(s);
+  s->last.symmetry = s->hp.herm ? LB_SYM_HERMITIAN : LB_SYM_NONE;
   if (s->timed_fwd) LB_CUDA(cudaEventElapsedTime(&s->last.ms_forward, s->ev[0], s->ev[1]), "cudaEventElapsedTime");
   if (s->timed_bwd) LB_CUDA(cudaEventElapsedTime(&s->last.ms_backward, s->ev[2], s->ev[3]), "cudaEventElapsedTime");
   if (rc) return rc;

@@ -89,6 +89,9 @@ struct ProbDev {
   unsigned long long* gslots;  // [3][M] per-state |z_new - z| maxima, then [2][M] per-state |q| maxima
   GridBar* bar;
   double2* hist;             // [kPredOrder][M*V] first-iterate predictor history (grid and one-CTA sweeps)
+  int32_t* hmap;             // [N (N + 1) / 2] vec indices k + N l with k <= l (grid sweeps)
+  int32_t herm;              // grid sweeps iterate k <= l only: every state and target is Hermitian
+  int32_t pad1;
 };
 
 // one work item of a resident launch: (problem, state)

@@ -2092,9 +2092,38 @@ __device__ bool grid_sync(GridBar* bar, unsigned nblocks) {
 struct GridHdr {
   Hdr h;
   int M;
-  long long total;  // M * V
+  int herm;         // Hermitian symmetry: only elements k <= l are iterated, the rest mirrored
+  int Vh;           // elements per state in the loops: V, or N (N + 1) / 2 with herm
+  long long total;  // M * Vh
   long long chunk;  // elements per block
 };
+
+// Element e of a grid sweep's loops: state b and vec index v; with the
+// Hermitian symmetry the loops visit k <= l only (v from the table hmap) and
+// vm is the mirror index l + N k of an off-diagonal element, whose value is
+// the conjugate (-1 for diagonal elements and without the symmetry).
+struct GEl {
+  int b, v, vm;
+};
+__device__ __forceinline__ GEl gel(const GridHdr& G, const int32_t* __restrict__ hmap, long long e) {
+  GEl r;
+  if (!G.herm) {
+    r.b = (int)(e / G.h.V);
+    r.v = (int)(e - (long long)r.b * G.h.V);
+    r.vm = -1;
+    return r;
+  }
+  r.b = (int)(e / G.Vh);
+  r.v = __ldg(hmap + (e - (long long)r.b * G.Vh));
+  const int N = G.h.N, k = r.v % N, l = r.v / N;
+  r.vm = k != l ? l + N * k : -1;
+  return r;
+}
+// store x at element g of the state array a (and its mirror)
+__device__ __forceinline__ void gput(double2* a, const GEl& g, int V, double2 x) {
+  a[(size_t)g.b * V + g.v] = x;
+  if (g.vm >= 0) a[(size_t)g.b * V + g.vm] = make_double2(x.x, -x.y);
+}
 
 __host__ __device__ inline size_t grid_smem_bytes_impl(int ncoef, int njcoef) {
   return align16(sizeof(GridHdr)) + align16(sizeof(double) * 2 * ncoef) + align16(sizeof(double) * 2 * njcoef) +
@@ -2111,7 +2140,7 @@ struct GridSmem {
   int* flag;
 };
 
-__device__ GridSmem grid_setup(unsigned char* base, const ProbDev& P, int nstates) {
+__device__ GridSmem grid_setup(unsigned char* base, const ProbDev& P, int nstates, int herm) {
   GridSmem S;
   size_t o = 0;
   S.g = reinterpret_cast<GridHdr*>(base + o);
@@ -2128,7 +2157,9 @@ __device__ GridSmem grid_setup(unsigned char* base, const ProbDev& P, int nstate
   if (threadIdx.x == 0) {
     load_hdr(S.g->h, P);
     S.g->M = nstates;
-    S.g->total = (long long)nstates * P.V;
+    S.g->herm = herm;
+    S.g->Vh = herm ? P.N * (P.N + 1) / 2 : P.V;
+    S.g->total = (long long)nstates * S.g->Vh;
     const long long per = (S.g->total + gridDim.x - 1) / gridDim.x;
     S.g->chunk = (per + blockDim.x - 1) / blockDim.x * blockDim.x;
   }
@@ -2229,13 +2260,13 @@ struct GridHist {
 };
 
 template <bool ADJ>
-__device__ __forceinline__ void grid_record(const ProbDev& P, long long total, GridHist h, long long e, int v,
+__device__ __forceinline__ void grid_record(const ProbDev& P, size_t stride, GridHist h, size_t o, int v,
                                             double hh, double2 z, double2 r) {
   const double2 D = __ldg(P.D + v);
   const double dr = hh * D.x, di = hh * (ADJ ? -D.y : D.y);
   const double cr = z.x - fma(dr, z.x, -di * z.y) - r.x;
   const double ci = z.y - fma(dr, z.y, di * z.x) - r.y;
-  P.hist[(size_t)h.slot * total + e] = make_double2(cr, ci);
+  P.hist[(size_t)h.slot * stride + o] = make_double2(cr, ci);
 }
 
 template <bool ADJ>
@@ -2256,10 +2287,12 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
   // z_0 = (I - dt/2 D)^-1 rhs (Jacobi) or rhs (Neumann); per-state max |rhs|
   {
     StateMax sm;
-    sm.init(e0, e1, V);
+    sm.init(e0, e1, G.Vh);
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int b = (int)(e / V), v = (int)(e - (long long)b * V);
-      const double2 r = rhs[e];
+      const GEl g = gel(G, P.hmap, e);
+      const int b = g.b, v = g.v;
+      const size_t o = (size_t)b * V + v;
+      const double2 r = rhs[o];
       double2 z0 = r;
       if (!neumann) {
         double ur = r.x, ui = r.y;
@@ -2267,7 +2300,7 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
         for (int i = 1; i <= hist.n; ++i) {
           sl = sl > 0 ? sl - 1 : kPredOrder - 1;
           const double w = kExtrap[hist.n][i - 1];
-          const double2 c = P.hist[(size_t)sl * G.total + e];
+          const double2 c = P.hist[(size_t)sl * ((size_t)M * V) + o];
           ur = fma(w, c.x, ur);
           ui = fma(w, c.y, ui);
         }
@@ -2275,7 +2308,7 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
         const double di = ADJ ? -d.y : d.y;
         z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
       }
-      P.zA[e] = z0;
+      gput(P.zA, g, V, z0);
       sm.add(b, umax64(abs_bits(r.x), abs_bits(r.y)), qbank);
     }
     sm.push(qbank, red);
@@ -2291,12 +2324,13 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
   for (int it = 0; it < H.max_iter; ++it, ++it_global) {
     unsigned long long* bank = dslots + (it_global % 3) * M;
     StateMax sm;
-    sm.init(e0, e1, V);
+    sm.init(e0, e1, G.Vh);
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int b = (int)(e / V), v = (int)(e - (long long)b * V);
+      const GEl g = gel(G, P.hmap, e);
+      const int b = g.b, v = g.v;
       const double2* xs = zc + (size_t)b * V;
       const int k = v % N, l = v / N;
-      const double2 r = rhs[e];
+      const double2 r = rhs[(size_t)b * V + v];
       double ar = r.x, ai = r.y;
       offdiag_acc<ADJ, true>(ar, ai, xs, v, __ldg(P.digits + k), __ldg(P.digits + l), H, T, ct);
       const double2 zo = __ldcg(xs + v);
@@ -2312,7 +2346,7 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
         z.x = ar + fma(dr, zo.x, -di * zo.y);
         z.y = ai + fma(dr, zo.y, di * zo.x);
       }
-      zn[e] = z;
+      gput(zn, g, V, z);
       sm.add(b, umax64(abs_bits(z.x - zo.x), abs_bits(z.y - zo.y)), bank);
     }
     sm.push(bank, red);
@@ -2363,14 +2397,20 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
                                                              int nstates) {
   extern __shared__ __align__(16) unsigned char smem[];
   const ProbDev& P = *pp;
-  const GridSmem S = grid_setup(smem, P, mode == 0 ? P.M : nstates);
+  // the Hermitian symmetry only for the forward sweep over the system's own
+  // states (vectors given to lb_propagate may be anything)
+  const GridSmem S = grid_setup(smem, P, mode == 0 ? P.M : nstates, mode == 0 ? P.herm : 0);
   const GridHdr& G = *S.g;
   const Hdr& H = G.h;
   const int V = H.V;
   double2* q = mode == 0 ? P.qT : x;
   const long long e0 = (long long)blockIdx.x * G.chunk, e1 = min(G.total, e0 + G.chunk);
+  const size_t hstride = (size_t)G.M * V;
   if (mode == 0 && init)
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) q[e] = P.q0[e];
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const GEl g = gel(G, P.hmap, e);
+      gput(q, g, V, P.q0[(size_t)g.b * V + g.v]);
+    }
   long long itg = 0, nsolve = 0;
   unsigned long long iters = 0, steps = 0;
   int maxit = 0;
@@ -2383,8 +2423,9 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
     const int j = mode == 2 ? j1 - 1 - jj : j0 + jj;
     if (mode == 0 && tape && H.K > 0 && j % H.K == 0) {
       for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const int b = (int)(e / V), v = (int)(e - (long long)b * V);
-        P.ckpt[((size_t)b * H.n_ckpt + j / H.K) * V + v] = q[e];
+        const GEl g = gel(G, P.hmap, e);
+        const double2 qq = q[(size_t)g.b * V + g.v];
+        gput(P.ckpt + ((size_t)g.b * H.n_ckpt + j / H.K) * V, GEl{0, g.v, g.vm}, V, qq);
       }
     }
     double2* z = nullptr;
@@ -2399,11 +2440,12 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
     steps += G.M;
     maxit = max(maxit, it);
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const double2 zz = z[e], qq = q[e];
-      const int b = (int)(e / V), v = (int)(e - (long long)b * V);
-      if (mode == 0 && tape && H.K == 0) P.ckpt[((size_t)b * H.NT + j) * V + v] = zz;
-      if (pred) grid_record<false>(P, G.total, hist, e, v, hh, zz, qq);
-      q[e] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
+      const GEl g = gel(G, P.hmap, e);
+      const size_t o = (size_t)g.b * V + g.v;
+      const double2 zz = z[o], qq = q[o];
+      if (mode == 0 && tape && H.K == 0) gput(P.ckpt + ((size_t)g.b * H.NT + j) * V, GEl{0, g.v, g.vm}, V, zz);
+      if (pred) grid_record<false>(P, hstride, hist, o, g.v, hh, zz, qq);
+      gput(q, g, V, make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y)));
     }
     if (pred) hist.advance();
   }
@@ -2419,22 +2461,24 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
 __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev* __restrict__ pp) {
   extern __shared__ __align__(16) unsigned char smem[];
   const ProbDev& P = *pp;
-  const GridSmem S = grid_setup(smem, P, P.M);
+  const GridSmem S = grid_setup(smem, P, P.M, P.herm);
   const GridHdr& G = *S.g;
   const Hdr& H = G.h;
   const int V = H.V, N = H.N;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const long long e0 = (long long)blockIdx.x * G.chunk, e1 = min(G.total, e0 + G.chunk);
+  const size_t hstride = (size_t)G.M * V;
   // terminal condition qhat^{N_T} = beta_i/M g_i (Appendix B)
   for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const int b = (int)(e / V);
-    const double w = P.wgt[b];
-    const double2 t = P.tar[e];
+    const GEl g = gel(G, P.hmap, e);
+    const size_t o = (size_t)g.b * V + g.v;
+    const double w = P.wgt[g.b];
+    const double2 t = P.tar[o];
     if (H.kind == LB_J_FROB) {
-      const double2 qq = P.qT[e];
-      P.lam[e] = make_double2(w * (qq.x - t.x), w * (qq.y - t.y));
+      const double2 qq = P.qT[o];
+      gput(P.lam, g, V, make_double2(w * (qq.x - t.x), w * (qq.y - t.y)));
     } else {
-      P.lam[e] = make_double2(-w * t.x, -w * t.y);
+      gput(P.lam, g, V, make_double2(-w * t.x, -w * t.y));
     }
   }
   long long itg = 0, nsolve = 0;
@@ -2451,8 +2495,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
     const int j1 = H.K > 0 ? min(H.NT, j0 + H.K) : H.NT;
     if (H.K > 0) {
       for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const int b = (int)(e / V), v = (int)(e - (long long)b * V);
-        P.qf[e] = P.ckpt[((size_t)b * H.n_ckpt + sg) * V + v];
+        const GEl g = gel(G, P.hmap, e);
+        gput(P.qf, g, V, P.ckpt[((size_t)g.b * H.n_ckpt + sg) * V + g.v]);
       }
       for (int j = j0; j < j1; ++j) {
         double2* z = nullptr;
@@ -2466,10 +2510,11 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
         st_rec += G.M;
         maxit = max(maxit, it);
         for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-          const int b = (int)(e / V), v = (int)(e - (long long)b * V);
-          const double2 zz = z[e];
-          P.seg[((size_t)b * H.K + (j - j0)) * V + v] = zz;
-          P.qf[e] = make_double2(fma(2.0, zz.x, -P.qf[e].x), fma(2.0, zz.y, -P.qf[e].y));
+          const GEl g = gel(G, P.hmap, e);
+          const size_t o = (size_t)g.b * V + g.v;
+          const double2 zz = z[o], qq = P.qf[o];
+          P.seg[((size_t)g.b * H.K + (j - j0)) * V + g.v] = zz;  // read back at the same element only
+          gput(P.qf, g, V, make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y)));
         }
       }
       if (failed) break;
@@ -2491,7 +2536,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
         const int n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * N;
         double sar = 0.0, sai = 0.0, sdr = 0.0, sdi = 0.0;
         for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-          const int b = (int)(e / V), v = (int)(e - (long long)b * V);
+          const GEl g = gel(G, P.hmap, e);
+          const int b = g.b, v = g.v;
           const double2* zs = zh + (size_t)b * V;
           const double2 Z = H.K > 0 ? P.seg[((size_t)b * H.K + (j - j0)) * V + v]
                                     : P.ckpt[((size_t)b * H.NT + j) * V + v];
@@ -2507,10 +2553,21 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
           const double pi = fma(-c2, x2.y, c1 * x1.y);
           const double rr = fma(-c4, x4.x, c3 * x3.x);
           const double ri = fma(-c4, x4.y, c3 * x3.y);
-          sar = fma(Z.x, rr, fma(Z.y, ri, sar));
-          sai = fma(Z.y, rr, fma(-Z.x, ri, sai));
-          sdr = fma(Z.x, pr, fma(Z.y, pi, sdr));
-          sdi = fma(Z.y, pr, fma(-Z.x, pi, sdi));
+          if (g.vm < 0) {
+            sar = fma(Z.x, rr, fma(Z.y, ri, sar));
+            sai = fma(Z.y, rr, fma(-Z.x, ri, sai));
+            sdr = fma(Z.x, pr, fma(Z.y, pi, sdr));
+            sdi = fma(Z.y, pr, fma(-Z.x, pi, sdi));
+          } else {
+            // Hermitian Z and zhat: the mirror element (l, k) adds -conj(B) to
+            // the g_a sum and -conj(A) to the g_ad sum, A = Z conj(R), B = Z conj(P)
+            const double ar = fma(Z.x, rr, Z.y * ri), ai = fma(Z.y, rr, -Z.x * ri);
+            const double br = fma(Z.x, pr, Z.y * pi), bi = fma(Z.y, pr, -Z.x * pi);
+            sar += ar - br;
+            sai += ai + bi;
+            sdr += br - ar;
+            sdi += bi + ai;
+          }
         }
         const double r = warp_sum4(sar, sai, sdr, sdi, lane);
         if ((lane & 7) == 0) S.red[(lane >> 3) * 8 + warp] = r;
@@ -2524,9 +2581,11 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
       }
       // qhat^j = 2 zhat - qhat^{j+1}
       for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const double2 z = zh[e], ll = P.lam[e];
-        if (apred) grid_record<true>(P, G.total, ahist, e, (int)(e % V), hh, z, ll);
-        P.lam[e] = make_double2(fma(2.0, z.x, -ll.x), fma(2.0, z.y, -ll.y));
+        const GEl g = gel(G, P.hmap, e);
+        const size_t o = (size_t)g.b * V + g.v;
+        const double2 z = zh[o], ll = P.lam[o];
+        if (apred) grid_record<true>(P, hstride, ahist, o, g.v, hh, z, ll);
+        gput(P.lam, g, V, make_double2(fma(2.0, z.x, -ll.x), fma(2.0, z.y, -ll.y)));
       }
       if (apred) ahist.advance();
       if (!grid_sync(P.bar, gridDim.x)) {

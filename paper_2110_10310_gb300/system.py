@@ -41,6 +41,7 @@ def _stats_dict(s) -> dict:
             "ms_forward": s.ms_forward, "ms_backward": s.ms_backward,
             "sweep": {1: "resident", 2: "grid", 3: "cluster"}.get(s.sweep, s.sweep),
             "solver": {1: "jacobi", 2: "neumann", 3: "gmres"}.get(s.solver, s.solver),
+            "symmetry": "hermitian" if s.symmetry == L.LB_SYM_HERMITIAN else "none",
             "ckpt_every": s.ckpt_every}
 
 
@@ -58,7 +59,8 @@ class LindbladSystem:
     ckpt_every)."""
 
     def __init__(self, problem, *, solver: int = L.LB_SOLVER_AUTO, rtol: float = 1e-15, max_iter: int = 200,
-                 ckpt_every: int | None = None, sweep: int = L.LB_SWEEP_AUTO, device=None, stream=None):
+                 ckpt_every: int | None = None, sweep: int = L.LB_SWEEP_AUTO, symmetry: int = L.LB_SYM_HERMITIAN,
+                 device=None, stream=None):
         self.lib = L.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         sysm = problem.system
@@ -108,6 +110,7 @@ class LindbladSystem:
         K = int(getattr(problem, "ckpt_every", 100)) if ckpt_every is None else int(ckpt_every)
         L.check(self.lib.lb_solver_set(h, int(solver), float(rtol), int(max_iter), K))
         L.check(self.lib.lb_set_sweep(h, int(sweep)))
+        L.check(self.lib.lb_set_symmetry(h, int(symmetry)))
         nbytes = c_size_t()
         L.check(self.lib.lb_workspace_bytes(h, byref(nbytes)))
         self.workspace_bytes = int(nbytes.value)

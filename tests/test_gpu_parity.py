@@ -605,3 +605,40 @@ def test_three_state_gate_objective_matches_oracle(objective):
     weights 20, 1, 1, purity-scaled for J_Tr) over its full 10000 steps."""
     p = W.cnot_three_states(objective=objective)
     _check_problem(p)
+
+
+# ----------------------------------------------------------------------------
+# Hermitian symmetry of the grid sweeps
+
+
+@pytest.mark.parametrize("levels,K,objective", [((3, 2, 2), 0, "frob"), ((3, 3), 7, "trace"), ((2, 2, 2), 100, "frob")])
+def test_grid_hermitian_symmetry_matches_oracle(levels, K, objective):
+    """Hermitian states and targets on the grid sweep: the half-element
+    iteration agrees with the full one (1e-12) and with the oracle."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(901, levels=levels, n_states=3, n_steps=40, T_ns=0.8, amp=0.1, ckpt_every=K,
+                         hermitian=True, objective=objective, gamma2=0.05)
+    s_h, g_h = _check_problem(p, sweep=L.LB_SWEEP_GRID)
+    G_h = s_h.gradient()[0]
+    assert s_h.stats()["symmetry"] == "hermitian"
+    s_f = _sys(p, sweep=L.LB_SWEEP_GRID, symmetry=L.LB_SYM_NONE)
+    G_f, g_f = s_f.gradient()
+    assert s_f.stats()["symmetry"] == "none"
+    assert abs(G_h - G_f) <= 1e-12 * abs(G_f)
+    assert _rel(g_h, g_f) < 1e-11
+
+
+def test_grid_hermitian_symmetry_with_gate_targets():
+    """The three Hermitian gate states (targets V rho V^+ formed on the
+    device) on the grid sweep, against the oracle."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.cnot_three_states(n_steps=200)
+    p.system.T_ns = 200.0 * 200 / 10000
+    s_h, _ = _check_problem(p, sweep=L.LB_SWEEP_GRID)
+    assert s_h.stats()["symmetry"] == "hermitian"
+    G_h, g_h = s_h.gradient()
+    G_f, g_f = _sys(p, sweep=L.LB_SWEEP_GRID, symmetry=L.LB_SYM_NONE).gradient()
+    assert abs(G_h - G_f) <= 1e-12 * abs(G_f)
+    assert _rel(g_h, g_f) < 1e-11

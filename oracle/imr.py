@@ -42,6 +42,9 @@ def embedding(levels, essential) -> np.ndarray:
 def targets_of(prob) -> np.ndarray:
     """rho_i^tar: given explicitly, or V rho_i(0) V^+ with V lifted to the
     full space, V_full = P V P^T (Sec. III-C, gate optimisation)."""
+    if prob.objective == "nm":
+        N = int(np.prod(prob.system.levels))
+        return np.stack([observable_nm(N, int(prob.meta["m"]))] * prob.M)
     if prob.targets is not None:
         return np.asarray(prob.targets, dtype=np.complex128)
     P = embedding(prob.system.levels, prob.system.essential)
@@ -88,12 +91,21 @@ def forward(prob, n_steps: int | None = None, keep: bool = True):
 # objective (Sec. III, eq. optimproblem and the merit functionals)
 
 
+def observable_nm(N: int, m: int) -> np.ndarray:
+    """N_m = diag(|l - m|), l = 0..N-1 over the full basis index (Sec. III-B,
+    eq. Jmeasure): J_Nm(rho) = Tr(N_m rho) vanishes only at |m><m|."""
+    return np.diag(np.abs(np.arange(N) - m).astype(np.float64)).astype(np.complex128)
+
+
 def merit(kind: str, tar: np.ndarray, rho: np.ndarray) -> float:
-    """J_Frob = 1/2 ||rho_tar - rho||_F^2, J_Tr = 1 - Re Tr(rho_tar^+ rho)."""
+    """J_Frob = 1/2 ||rho_tar - rho||_F^2, J_Tr = 1 - Re Tr(rho_tar^+ rho)
+    (Sec. III, eq. Jmeasure), and J_Nm = Re Tr(N_m rho) with ``tar`` = N_m."""
     if kind == "frob":
         return 0.5 * float(np.sum(np.abs(tar - rho) ** 2))
     if kind == "trace":
         return 1.0 - float(np.real(np.trace(tar.conj().T @ rho)))
+    if kind == "nm":
+        return float(np.real(np.trace(tar @ rho)))
     raise ValueError(kind)
 
 
@@ -109,13 +121,15 @@ def objective(prob, rhoT: np.ndarray) -> float:
 def terminal_adjoint(prob, rhoT: np.ndarray) -> np.ndarray:
     """q^_i(N_T) = beta_i/M * g_i (Appendix B), with g the gradient of J with
     respect to conj(q) under <a, b> = Re(a^H b): g = q - q_tar for J_Frob and
-    g = -q_tar for J_Tr."""
+    g = -q_tar for J_Tr and g = vec(N_m) for J_Nm."""
     tars = targets_of(prob)
     w = weights_of(prob)
     cols = []
     for i in range(prob.M):
         if prob.objective == "frob":
             g = vec(rhoT[i]) - vec(tars[i])
+        elif prob.objective == "nm":
+            g = vec(tars[i])
         else:
             g = -vec(tars[i])
         cols.append(w[i] / prob.M * g)

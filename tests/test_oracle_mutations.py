@@ -25,6 +25,7 @@ PIN_TESTS = [
     pins.test_adjoint_dot_product_identity,
     lambda: pins.test_gradient_matches_central_differences("frob", False, 0.0),
     lambda: pins.test_gradient_matches_central_differences("trace", True, 0.3),
+    pins.test_jnm_values_and_gradient,
 ]
 
 
@@ -147,7 +148,23 @@ ORIG = {
     "dd_dalpha": imr.dd_dalpha,
 }
 
+def _merit_nm_transposed_index(kind, tar, rho):
+    if kind == "nm":
+        # N_m read as diag(|l - m|) with l counted from the other end
+        return float(np.real(np.trace(tar[::-1, ::-1] @ rho)))
+    return ORIG_MERIT(kind, tar, rho)
+
+
+def _terminal_nm_negated(prob, rhoT):
+    out = ORIG["terminal_adjoint"](prob, rhoT)
+    return -out if prob.objective == "nm" else out
+
+
+ORIG_MERIT = imr.merit
+
 MUTATIONS = {
+    "J_Nm observable reversed": [(imr, "merit", _merit_nm_transposed_index)],
+    "J_Nm terminal adjoint negated": [(imr, "terminal_adjoint", _terminal_nm_negated)],
     "hamiltonian part uses H instead of H^T": [(model, "hamiltonian_part", _ham_part_transposed),
                                                (imr, "hamiltonian_part", _ham_part_transposed)],
     "hamiltonian part with +i": [(model, "hamiltonian_part", _ham_part_sign),

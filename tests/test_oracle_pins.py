@@ -385,3 +385,41 @@ def test_gradient_matches_fd_for_config_shapes():
     scale = np.max(np.abs(g))
     for k in idx:
         assert abs(g[k] - fd[k]) <= 1e-6 * scale, (k, g[k], fd[k])
+
+
+def test_jnm_values_and_gradient():
+    """J_Nm (Sec. III-B, eq. Jmeasure): Tr(N_m |l><l|) = |l - m|, J_Nm >= 0 on
+    density matrices with equality only at |m><m|; the adjoint gradient of
+    the reset problem from the ensemble state agrees with central
+    differences."""
+    N, m = 6, 2
+    Nm = imr.observable_nm(N, m)
+    for l in range(N):
+        e = np.zeros((N, N), dtype=np.complex128)
+        e[l, l] = 1.0
+        assert imr.merit("nm", Nm, e) == abs(l - m)
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        A = rng.standard_normal((N, N)) + 1j * rng.standard_normal((N, N))
+        rho = A @ A.conj().T
+        rho /= np.trace(rho).real
+        assert imr.merit("nm", Nm, rho) > 0.0
+    p = W.reset_ensemble(levels=(2, 3), n_steps=12, T_ns=1.0, n_splines=5, amp=0.2)
+    assert abs(np.trace(p.rho0[0]) - 1.0) < 1e-15 and np.min(np.linalg.eigvalsh(p.rho0[0])) > 0.0
+    G, g, _ = imr.gradient(p)
+    fd = imr.fd_gradient(p, eps=1e-6)
+    scale = np.max(np.abs(g))
+    for k, v in fd.items():
+        assert abs(g[k] - v) <= 1e-6 * scale, (k, g[k], v)
+
+
+def test_basis_matrices_are_pure_states():
+    """The N^2 basis matrices B^kj (Sec. III-B) are density matrices of pure
+    states (Hermitian, unit trace, rank one), as the paper states -- which
+    pins the reading of the garbled k > j case."""
+    B = W.basis_matrices(4).reshape(-1, 4, 4)
+    for b in B:
+        assert np.allclose(b, b.conj().T, atol=0)
+        assert abs(np.trace(b) - 1.0) < 1e-15
+        ev = np.linalg.eigvalsh(b)
+        assert abs(ev[-1] - 1.0) < 1e-14 and np.max(np.abs(ev[:-1])) < 1e-14

@@ -20,6 +20,9 @@ from .synthetic import (  # noqa: F401
     fock_superposition,
     three_gate_states,
     cnot_three_states,
+    basis_matrices,
+    ensemble_state,
+    reset_ensemble,
     random_problem,
     basis_outer,
     random_pure_state,

@@ -180,6 +180,62 @@ def config2(seed: int = 2, n_steps: int = 10000, levels=(3, 3)) -> Problem:
     return Problem("cnot_2x3", sysm, ctrl, rho0, "frob", gate=CNOT.copy())
 
 
+def basis_matrices(N: int) -> np.ndarray:
+    """The N^2 pure basis states B^{kj} of Sec. III-B: 1/2 (|k><k| + |j><j|)
+    plus 1/2 (|k><j| + |j><k|) for k < j, or i/2 (|j><k| - |k><j|) for k > j
+    (the printed k > j case is garbled; read as the pure state
+    (|k> + i|j>)/sqrt 2)."""
+    B = np.zeros((N, N, N, N), dtype=np.complex128)
+    for k in range(N):
+        for j in range(N):
+            B[k, j, k, k] += 0.5
+            B[k, j, j, j] += 0.5
+            if k < j:
+                B[k, j, k, j] += 0.5
+                B[k, j, j, k] += 0.5
+            elif k > j:
+                B[k, j, j, k] += 0.5j
+                B[k, j, k, j] -= 0.5j
+    return B
+
+
+def ensemble_state(N: int) -> np.ndarray:
+    """rho_s = 1/N^2 sum_kj B^{kj} (Sec. III-B), one state spanning all
+    initial states for a linear merit functional."""
+    return basis_matrices(N).sum(axis=(0, 1)) / (N * N)
+
+
+def reset_ensemble(levels=(2, 2, 20), n_steps: int = 100000, T_ns: float = 5000.0, seed: int = 7,
+                   n_splines: int = 100, amp: float = 0.01) -> Problem:
+    """Ground-state reset of two qubits and a readout cavity from the ensemble
+    state, J_N0 (Sec. III-B and its footnote: rotating frames at the qubit
+    and cavity frequencies, anharmonicities 230.56, 251.0, 0 MHz, cross-Kerr
+    0.001, 1.176, 1.2 MHz for the pairs (1,2), (1,3), (2,3), T1 = 80, 90,
+    0.3892 us, T2 = 26, 30 us and none for the cavity, 100 splines, carriers
+    0, T = 5 us).  The step count is not printed; dt = 0.05 ns is the
+    reading.  Controls start uniform in [-amp, amp] GHz."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Q = len(levels)
+    ck = np.zeros((Q, Q))
+    for (a, c), v in {(0, 1): 1e-6, (0, 2): 1.176e-3, (1, 2): 1.2e-3}.items():
+        if c < Q:
+            ck[a, c] = v
+    sysm = SystemSpec(
+        levels=tuple(levels),
+        detuning_ghz=np.zeros(Q),
+        selfkerr_ghz=np.array([0.23056, 0.251, 0.0])[:Q],
+        crosskerr_ghz=ck,
+        t1_us=np.array([80.0, 90.0, 0.3892])[:Q],
+        t2_us=np.array([26.0, 30.0, 0.0])[:Q],
+        T_ns=T_ns,
+        n_steps=n_steps,
+    )
+    ctrl = ControlSpec(n_splines, [np.array([0.0]) for _ in range(Q)], _alpha(rng, Q, n_splines, [1] * Q, amp))
+    N = int(np.prod(levels))
+    rho0 = ensemble_state(N)[None].copy()
+    return Problem("reset_ensemble", sysm, ctrl, rho0, "nm", meta={"m": 0})
+
+
 def three_gate_states(levels, essential=None) -> np.ndarray:
     """The three initial states that distinguish any two unitaries on the
     essential subspace (Sec. III-C), embedded in the full space:

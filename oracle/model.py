@@ -65,16 +65,18 @@ def system_hamiltonian(sysm) -> np.ndarray:
 
 def collapse_operators(sysm) -> list:
     """L_1q = a_q / sqrt(T1_q) (decay), L_2q = a_q^+ a_q / sqrt(T2_q)
-    (dephasing), Sec. II.  T in microseconds -> ns; an infinite time drops
-    the operator."""
+    (dephasing), Sec. II.  T in microseconds -> ns; an infinite time, or a
+    time printed as 0 (the cavity's T2 in the reset example of Sec. III-B),
+    drops the operator."""
     levels = sysm.levels
     out = []
     for q in range(len(levels)):
         a = a_op(q, levels)
-        if math.isfinite(sysm.t1_us[q]):
-            out.append(a / math.sqrt(1000.0 * sysm.t1_us[q]))
-        if math.isfinite(sysm.t2_us[q]):
-            out.append((a.conj().T @ a) / math.sqrt(1000.0 * sysm.t2_us[q]))
+        t1, t2 = float(sysm.t1_us[q]), float(sysm.t2_us[q])
+        if math.isfinite(t1) and t1 > 0.0:
+            out.append(a / math.sqrt(1000.0 * t1))
+        if math.isfinite(t2) and t2 > 0.0:
+            out.append((a.conj().T @ a) / math.sqrt(1000.0 * t2))
     return out
 
 

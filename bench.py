@@ -37,6 +37,8 @@ WORKLOADS = {
     "cnot_2x3": WORKLOAD,
     "cnot_3states": ("cnot_3states: the cnot_2x3 system and controls with the three-state gate objective "
                      "(Sec. III-C: 3 Hermitian states, weights 20, 1, 1), 10000 steps, fwd + adjoint"),
+    "reset_2x2x20": ("reset_2x2x20: 2 qubits + 20-level cavity (vec 6400) from the ensemble state, J_N0, "
+                     "dt=0.05 ns, first {n} of 100000 steps, 100 splines, fwd + adjoint, grid-wide sweep"),
     "qubit_x": "qubit_x: 1 qubit (vec 4), 4 states |i><j|, 1000 steps, T=100 ns, X gate, fwd + adjoint",
     "batch256": ("batch256: 256 independent problems, Q in {1,2,3}, 2-4 levels (vec 4..4096), 3 random pure states "
                  "each, 5000 steps, T=100 ns, fwd + adjoint, one persistent launch per sweep captured in a CUDA graph"),
@@ -50,7 +52,7 @@ WORKLOADS = {
                    "T=200 ns, 10000 steps; one bench step = one L-BFGS run (lb_optimize, memory 10, "
                    "at most 150 iterations, gtol 1e-9) from the seeded controls"),
 }
-PREFIX = {"qudits_4x4": 2000, "qutrits_6x3": 40}
+PREFIX = {"qudits_4x4": 2000, "qutrits_6x3": 40, "reset_2x2x20": 2000}
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 FP64_FLOP_PER_CLK_PER_SM = 4.0  # 2 FP64 FMA lanes per SM per clock, 2 flops each
@@ -65,6 +67,9 @@ def problem(n_steps=None, workload="cnot_2x3", states=0):
         p = W.config1()
     elif workload == "cnot_3states":
         p = W.cnot_three_states()
+    elif workload == "reset_2x2x20":
+        p = W.reset_ensemble()
+        n_steps = n_steps or PREFIX[workload]
     elif workload == "qudits_4x4":
         p = W.config4()
         n_steps = n_steps or PREFIX[workload]

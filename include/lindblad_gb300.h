@@ -58,6 +58,7 @@ extern "C" {
 /* merit functionals, Sec. III */
 #define LB_J_FROB 0 /* J = 1/2 ||rho_tar - rho||_F^2 */
 #define LB_J_TR 1   /* J = 1 - Re Tr(rho_tar^+ rho) */
+#define LB_J_NM 2   /* J = Tr(N_m rho), N_m = diag(|l - m|) over the full basis index l (lb_objective_set_measure) */
 
 /* inner solvers for (I - dt/2 M) z = q, Appendix A (the paper solves it with
  * GMRES, Sec. IV); all converge to the same unique z:
@@ -101,7 +102,7 @@ extern "C" {
 #define LB_SWEEP_CLUSTER 3
 
 #define LB_MAX_SUBSYSTEMS 8 /* Q <= 8 */
-#define LB_MAX_LEVELS 16    /* n_q <= 16 */
+#define LB_MAX_LEVELS 64    /* n_q <= 64, and Q * max(4, ceil(log2 max n_q)) <= 32 */
 
 typedef struct lb_system lb_system;
 typedef struct lb_batch lb_batch;
@@ -187,6 +188,15 @@ int lb_objective_set_gate(lb_system* sys, int32_t kind, const double* V, double 
  * Defaults: LB_SOLVER_AUTO, 1e-15, 200, 100.  Call before lb_workspace_bytes. */
 #define LB_CKPT_AUTO (-1)
 int lb_solver_set(lb_system* sys, int32_t method, double rtol, int32_t max_iter, int32_t ckpt_every);
+
+/* Merit functional J_Nm (Sec. III-B, eq. Jmeasure) for every state:
+ * J = Tr(N_m rho(T)) with the observable N_m = diag(|l - m|), l = 0..N-1 the
+ * full basis index, which vanishes only at rho = |m><m| (unconditional
+ * preparation of |m><m|, e.g. ground-state reset m = 0, usually from the
+ * single ensemble state 1/N^2 sum_kj B^kj).  Terminal adjoint condition
+ * beta_i/M vec(N_m).  LB_EINVAL for m outside 0..N-1 or a bad gamma2; call
+ * after lb_states_set. */
+int lb_objective_set_measure(lb_system* sys, int32_t m, double gamma2);
 
 /* Choose the sweep kind (LB_SWEEP_*); call before lb_workspace_bytes. */
 int lb_set_sweep(lb_system* sys, int32_t sweep);

@@ -36,6 +36,7 @@ LB_SOLVER_AUTO = 0
 LB_SOLVER_JACOBI = 1
 LB_SOLVER_NEUMANN = 2
 LB_SOLVER_GMRES = 3
+LB_J_NM = 2
 LB_SYM_NONE = 0
 LB_SYM_HERMITIAN = 1
 
@@ -93,6 +94,7 @@ SIGNATURES = {
     "lb_states_set": (c_int32, [c_void_p, c_int32, c_void_p, POINTER(c_double)]),
     "lb_objective_set": (c_int32, [c_void_p, c_int32, c_void_p, c_double]),
     "lb_objective_set_gate": (c_int32, [c_void_p, c_int32, c_void_p, c_double]),
+    "lb_objective_set_measure": (c_int32, [c_void_p, c_int32, c_double]),
     "lb_solver_set": (c_int32, [c_void_p, c_int32, c_double, c_int32, c_int32]),
     "lb_set_sweep": (c_int32, [c_void_p, c_int32]),
     "lb_set_symmetry": (c_int32, [c_void_p, c_int32]),

@@ -81,6 +81,7 @@ struct lb_system {
   // solver
   int method = LB_SOLVER_JACOBI;
   int krylov = 0;  // GMRES cycle length that fits shared memory (decided at bind)
+  int dbits = 4;   // bits per packed digit of a basis index
   double rtol = 1e-15;
   int max_iter = 200;
   int K = 100;       // requested checkpoint interval; < 0 = automatic (effective_K)
@@ -403,6 +404,7 @@ void fill_prob(lb_system* s) {
   P.max_iter = s->max_iter;
   P.method = s->method;
   P.krylov = s->krylov;
+  P.dbits = s->dbits;
   P.kind = s->kind;
   P.Ns = s->Ns;
   P.n_params = s->n_params;
@@ -533,7 +535,7 @@ int lb_system_create(const lb_system_desc* d, lb_system** out) {
     const int n = d->levels[q];
     if (n < 2 || n > LB_MAX_LEVELS) {
       delete s;
-      return fail(LB_EINVAL, "levels must be in 2..16");
+      return fail(LB_EINVAL, "levels must be in 2..64");
     }
     s->levels[q] = n;
     const int e = d->essential ? d->essential[q] : n;
@@ -553,6 +555,18 @@ int lb_system_create(const lb_system_desc* d, lb_system** out) {
       delete s;
       return fail(LB_EINVAL, "non-finite detuning or self-Kerr");
     }
+  }
+  {
+    // every basis index's digits packed into 32 bits
+    int nmax = 2;
+    for (int q = 0; q < d->Q; ++q) nmax = std::max(nmax, s->levels[q]);
+    int db = 4;
+    while ((1 << db) < nmax) ++db;
+    if (db * d->Q > 32) {
+      delete s;
+      return fail(LB_EINVAL, "Q * ceil(log2 max levels) must be <= 32");
+    }
+    s->dbits = db;
   }
   if (N > (1 << 15)) {
     delete s;
@@ -772,6 +786,31 @@ int lb_objective_set(lb_system* s, int32_t kind, const double* targets, double g
   s->tar_herm = hermitian_matrices(targets, s->M, s->N);
   if (s->ws) {
     s->hp.kind = kind;
+    s->hp.gamma2 = gamma2;
+    s->hp.herm = use_symmetry(s) ? 1 : 0;
+    LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, s->bind_stream), "upload problem");
+    return upload_targets(s, s->bind_stream);
+  }
+  return LB_OK;
+}
+
+int lb_objective_set_measure(lb_system* s, int32_t m, double gamma2) {
+  if (!s) return fail(LB_EINVAL, "null argument");
+  if (m < 0 || m >= s->N) return fail(LB_EINVAL, "m must be in 0..N-1");
+  if (!(gamma2 >= 0.0) || !std::isfinite(gamma2)) return fail(LB_EINVAL, "gamma2 must be finite and >= 0");
+  if (s->M < 1) return fail(LB_EINVAL, "call lb_states_set first");
+  if (s->ws && s->target_mode == 2) return fail(LB_EINVAL, "cannot leave a gate objective once a workspace is bound");
+  // N_m as the (real, diagonal) target of every state
+  std::vector<double> t((size_t)2 * s->M * s->V, 0.0);
+  for (int i = 0; i < s->M; ++i)
+    for (int l = 0; l < s->N; ++l) t[(size_t)2 * ((size_t)i * s->V + l + (size_t)s->N * l)] = std::abs(l - m);
+  s->kind = LB_J_NM;
+  s->gamma2 = gamma2;
+  s->target_mode = 1;
+  s->targets.swap(t);
+  s->tar_herm = true;
+  if (s->ws) {
+    s->hp.kind = LB_J_NM;
     s->hp.gamma2 = gamma2;
     s->hp.herm = use_symmetry(s) ? 1 : 0;
     LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, s->bind_stream), "upload problem");

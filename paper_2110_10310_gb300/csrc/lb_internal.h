@@ -38,7 +38,7 @@ struct ProbDev {
   int32_t n_ckpt, max_iter, method, kind;
   int32_t Ns, n_params;
   int32_t krylov;            // GMRES cycle length m (Krylov basis of m + 1 vectors in shared memory)
-  int32_t pad0;
+  int32_t dbits;             // bits per packed digit: ceil(log2 max n_q), at least 4
   double h, rtol, T, gamma2;
   int32_t levels[LB_MAXQ];
   int32_t stride[LB_MAXQ];   // s_q = prod_{p>q} n_p
@@ -57,7 +57,7 @@ struct ProbDev {
   double* cd;                // [ncoef]  sqrt(n)
   double* jf;                // [njcoef] jump_q sqrt((nk+1)(nl+1)), 0 if a digit would leave the range
   double* ja;                // [njcoef] jump_q sqrt(nk nl)
-  uint32_t* digits;          // [N] 4-bit digits of a basis index, subsystem q at bits 4q..4q+3
+  uint32_t* digits;          // [N] digits of a basis index, subsystem q at bits dbits q .. dbits (q + 1) - 1
   double2* D;                // [V] diagonal of M
   double2* Dinv;             // [V] 1/(1 - dt/2 D)
   // controls

@@ -107,6 +107,16 @@ __device__ __forceinline__ double bspline2(double x) {
   return 0.0;
 }
 
+// J from the sum the kernels reduce: 1/2 sum |q - t|^2 for J_Frob, else
+// sum Re(conj(t) q): J_Tr = 1 - Re Tr(t^+ q), J_Nm = Re Tr(N_m q) (t = N_m)
+// (Sec. III, eq. Jmeasure)
+__device__ __forceinline__ double merit_value(int kind, double sum) {
+  return kind == LB_J_FROB ? 0.5 * sum : (kind == LB_J_TR ? 1.0 - sum : sum);
+}
+// factor of the target in the terminal condition beta_i/M g_i for the
+// functionals linear in q: g = -t (J_Tr), g = N_m = t (J_Nm)
+__device__ __forceinline__ double linear_sign(int kind) { return kind == LB_J_NM ? 1.0 : -1.0; }
+
 __device__ void record_error(DevStatus* st, int code, int step) {
   if (atomicCAS(&st->code, 0, code) == 0) st->step = step;
 }
@@ -126,6 +136,7 @@ __device__ __forceinline__ double stop_factor(const ProbDev& P, int j) {
 
 struct Hdr {
   int Q, N, V, NT, K, n_ckpt, max_iter, method, kind, M, krylov;
+  int db, dm;  // bits per packed digit and their mask
   double h, rtol;
   int lev[LB_MAXQ], stride[LB_MAXQ], coff[LB_MAXQ], joff[LB_MAXQ];
   double jump[LB_MAXQ];
@@ -150,6 +161,8 @@ __device__ void load_hdr(Hdr& H, const ProbDev& P) {
   H.kind = P.kind;
   H.M = P.M;
   H.krylov = P.krylov;
+  H.db = P.dbits;
+  H.dm = (1 << P.dbits) - 1;
   H.h = P.h;
   H.rtol = P.rtol;
   for (int q = 0; q < LB_MAXQ; ++q) {
@@ -181,7 +194,7 @@ __device__ __forceinline__ void offdiag_acc(double& ar, double& ai, const double
   const int N = H.N;
   for (int q = 0; q < H.Q; ++q) {
     const int n = H.lev[q], s = H.stride[q], co = H.coff[q];
-    const int nk = (kd >> (4 * q)) & 15, nl = (ld >> (4 * q)) & 15;
+    const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
     const int sN = s * N;
     // control: -i[H_c, X] with H_c = d a + conj(d) a^+ (Sec. II):
     //   P = sqrt(nk+1) x[k+s,l] - sqrt(nl) x[k,l-s]     (a X - X a)
@@ -364,7 +377,7 @@ __device__ void build_plan(Plan<QT>& pl, const ResSmem& S, const Hdr& H, uint32_
 #pragma unroll
     for (int q = 0; q < QT; ++q) {
       const int n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * H.N;
-      const int nk = (kd >> (4 * q)) & 15, nl = (ld >> (4 * q)) & 15;
+      const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
       const int jo = H.joff[q] + nk * n + nl;
       pl.c[q][0] = ok ? S.cu[co + nk] : 0.0;
       pl.c[q][1] = ok ? S.cd[co + nl] : 0.0;
@@ -922,7 +935,7 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
     }
   }
   const double tot = cta_sum(S, acc);
-  if (threadIdx.x == 0) P.J[i] = H.kind == LB_J_FROB ? 0.5 * tot : 1.0 - tot;
+  if (threadIdx.x == 0) P.J[i] = merit_value(H.kind, tot);
   stats.flush(P.status);
 }
 
@@ -947,6 +960,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const size_t base = (size_t)i * H.V;
   const double w = P.wgt[i];
+  const double wt = linear_sign(P.kind) * w;
   // terminal condition qhat^{N_T} = beta_i/M g_i (Appendix B): g = q - q_tar
   // for J_Frob, g = -q_tar for J_Tr
   double2 lam[E], qf[E];
@@ -961,7 +975,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
         const double2 qq = P.qT[base + v];
         lam[e] = make_double2(w * (qq.x - t.x), w * (qq.y - t.y));
       } else {
-        lam[e] = make_double2(-w * t.x, -w * t.y);
+        lam[e] = make_double2(wt * t.x, wt * t.y);
       }
     }
   }
@@ -1037,7 +1051,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
         for (int e = 0; e < E; ++e) {
           const int v = threadIdx.x + e * blockDim.x;
           if (v < H.V) {
-            const int nk = (el.kd[e] >> (4 * q)) & 15, nl = (el.ld[e] >> (4 * q)) & 15;
+            const int nk = (el.kd[e] >> (H.db * q)) & H.dm, nl = (el.ld[e] >> (H.db * q)) & H.dm;
             const double c1 = S.cu[co + nk], c2 = S.cd[co + nl], c3 = S.cd[co + nk], c4 = S.cu[co + nl];
             const double2 x1 = zh[v + (nk + 1 < n ? s : 0)];
             const double2 x2 = zh[v - (nl > 0 ? sN : 0)];
@@ -1333,7 +1347,7 @@ __device__ ClPlan cl_plan(const ClSmem& S, int C, int crank) {
   if (pl.ev && u >= 0) {
     const uint32_t kd = S.dig[v % H.N], ld = S.dig[v / H.N];
     const int q = pl.q, n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * H.N;
-    const int nk = (kd >> (4 * q)) & 15, nl = (ld >> (4 * q)) & 15;
+    const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
     if (!pl.rhalf) {
       pl.oa = v + (nk + 1 < n ? s : 0);
       pl.ob = v - (nl > 0 ? sN : 0);
@@ -1611,7 +1625,7 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
     if (threadIdx.x == 0) {
       double t = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += S.gred[w];
-      P.J[i] = H.kind == LB_J_FROB ? 0.5 * t : 1.0 - t;
+      P.J[i] = merit_value(H.kind, t);
     }
   }
   stats.flush(P.status);
@@ -1633,6 +1647,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const size_t base = (size_t)i * H.V;
   const double w = P.wgt[i];
+  const double wt = linear_sign(P.kind) * w;
   // terminal condition qhat^{N_T} = beta_i/M g_i (Appendix B), replicated
   for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
     const double2 t = P.tar[base + e];
@@ -1640,7 +1655,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
       const double2 qq = P.qT[base + e];
       S.ll[e] = make_double2(w * (qq.x - t.x), w * (qq.y - t.y));
     } else {
-      S.ll[e] = make_double2(-w * t.x, -w * t.y);
+      S.ll[e] = make_double2(wt * t.x, wt * t.y);
     }
   }
   ClCount cnt;
@@ -1806,7 +1821,7 @@ __global__ void k_tables(ProbDev* __restrict__ pp) {
     uint32_t code = 0;
     int rem = tid;
     for (int q = Q - 1; q >= 0; --q) {
-      code |= (uint32_t)(rem % P.levels[q]) << (4 * q);
+      code |= (uint32_t)(rem % P.levels[q]) << (P.dbits * q);
       rem /= P.levels[q];
     }
     P.digits[tid] = code;
@@ -2473,12 +2488,13 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
     const GEl g = gel(G, P.hmap, e);
     const size_t o = (size_t)g.b * V + g.v;
     const double w = P.wgt[g.b];
+    const double wt = linear_sign(P.kind) * w;
     const double2 t = P.tar[o];
     if (H.kind == LB_J_FROB) {
       const double2 qq = P.qT[o];
       gput(P.lam, g, V, make_double2(w * (qq.x - t.x), w * (qq.y - t.y)));
     } else {
-      gput(P.lam, g, V, make_double2(-w * t.x, -w * t.y));
+      gput(P.lam, g, V, make_double2(wt * t.x, wt * t.y));
     }
   }
   long long itg = 0, nsolve = 0;
@@ -2543,7 +2559,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
                                     : P.ckpt[((size_t)b * H.NT + j) * V + v];
           const int k = v % N, l = v / N;
           const uint32_t kd = __ldg(P.digits + k), ld = __ldg(P.digits + l);
-          const int nk = (kd >> (4 * q)) & 15, nl = (ld >> (4 * q)) & 15;
+          const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
           const double c1 = S.cu[co + nk], c2 = S.cd[co + nl], c3 = S.cd[co + nk], c4 = S.cu[co + nl];
           const double2 x1 = __ldcg(zs + v + (nk + 1 < n ? s : 0));
           const double2 x2 = __ldcg(zs + v - (nl > 0 ? sN : 0));
@@ -2638,7 +2654,7 @@ __global__ void k_objective_states(const ProbDev* __restrict__ pp) {
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    P.J[i] = P.kind == LB_J_FROB ? 0.5 * t : 1.0 - t;
+    P.J[i] = merit_value(P.kind, t);
   }
 }
 }  // namespace

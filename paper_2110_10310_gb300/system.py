@@ -101,7 +101,9 @@ class LindbladSystem:
         L.check(self.lib.lb_states_set(h, self.M, rho.ctypes.data_as(c_void_p), None if w is None else _dptr(w)))
         kind = L.LB_J_FROB if problem.objective == "frob" else L.LB_J_TR
         g2 = float(getattr(problem, "gamma2", 0.0))
-        if problem.targets is not None:
+        if problem.objective == "nm":
+            L.check(self.lib.lb_objective_set_measure(h, int(problem.meta["m"]), g2))
+        elif problem.targets is not None:
             tar = colmajor(problem.targets)
             L.check(self.lib.lb_objective_set(h, kind, tar.ctypes.data_as(c_void_p), g2))
         else:

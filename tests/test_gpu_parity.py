@@ -642,3 +642,18 @@ def test_grid_hermitian_symmetry_with_gate_targets():
     G_f, g_f = _sys(p, sweep=L.LB_SWEEP_GRID, symmetry=L.LB_SYM_NONE).gradient()
     assert abs(G_h - G_f) <= 1e-12 * abs(G_f)
     assert _rel(g_h, g_f) < 1e-11
+
+
+# ----------------------------------------------------------------------------
+# J_Nm from the ensemble state (ground-state reset)
+
+
+@pytest.mark.parametrize("levels,sweep", [((2, 2, 3), "auto"), ((2, 3), "cluster"), ((2, 2, 3), "grid")])
+def test_reset_from_ensemble_state_matches_oracle(levels, sweep):
+    """J_N0 of the qubit-qubit-cavity reset (reduced cavity) from the single
+    ensemble state, on each sweep kind, against the oracle."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    sw = {"auto": L.LB_SWEEP_AUTO, "cluster": L.LB_SWEEP_CLUSTER, "grid": L.LB_SWEEP_GRID}[sweep]
+    p = W.reset_ensemble(levels=levels, n_steps=400, T_ns=20.0, n_splines=8, amp=0.05)
+    _check_problem(p, sweep=sw)

@@ -46,7 +46,8 @@ def a_op(q: int, levels) -> np.ndarray:
 def system_hamiltonian(sysm) -> np.ndarray:
     """H_sys = sum_q [(w_q - w_q^rot) a_q^+ a_q - xi_q/2 a_q^+ a_q^+ a_q a_q]
     - sum_{p<q} xi_pq a_p^+ a_p a_q^+ a_q   (Sec. II, cross-Kerr model; the
-    Jaynes-Cummings coupling g_pq is zero in this path)."""
+    Jaynes-Cummings coupling is time dependent in the rotating frame and
+    added by ``jc_hamiltonian``)."""
     levels = sysm.levels
     N = int(np.prod(levels))
     H = np.zeros((N, N), dtype=np.complex128)
@@ -124,6 +125,29 @@ def control_amplitudes(ctrl, t: float, T: float) -> np.ndarray:
                 i = alpha_index(ctrl, q, f, s)
                 d[q] += TWO_PI * S * complex(ctrl.alpha[i], ctrl.alpha[i + 1]) * carrier
     return d
+
+
+def jc_hamiltonian(sysm, t: float) -> np.ndarray:
+    """Jaynes-Cummings coupling of H_sys in its general rotating-frame form
+    (Sec. II): sum_{p<q} g_pq (e^{i eta t} a_p^+ a_q + e^{-i eta t} a_p a_q^+),
+    eta = omega_p^rot - omega_q^rot (rad/ns from GHz)."""
+    levels = tuple(sysm.levels)
+    N = int(np.prod(levels))
+    H = np.zeros((N, N), dtype=np.complex128)
+    g = getattr(sysm, "jc_ghz", None)
+    if g is None:
+        return H
+    rot = getattr(sysm, "rot_ghz", None)
+    Q = len(levels)
+    for p in range(Q):
+        for q in range(p + 1, Q):
+            if g[p][q] == 0.0:
+                continue
+            eta = TWO_PI * ((rot[p] - rot[q]) if rot is not None else 0.0)
+            ap, aq = a_op(p, levels), a_op(q, levels)
+            ph = np.exp(1j * eta * t)
+            H += TWO_PI * g[p][q] * (ph * (ap.conj().T @ aq) + np.conj(ph) * (ap @ aq.conj().T))
+    return H
 
 
 def control_hamiltonian(d: np.ndarray, levels) -> np.ndarray:
@@ -225,7 +249,7 @@ class Model:
         return control_amplitudes(self.ctrl, t, self.sys.T_ns)
 
     def H(self, t: float) -> np.ndarray:
-        return self.H_sys + control_hamiltonian(self.d(t), self.levels)
+        return self.H_sys + jc_hamiltonian(self.sys, t) + control_hamiltonian(self.d(t), self.levels)
 
     def M(self, t: float) -> np.ndarray:
         """Dense N^2 x N^2 vectorised Lindbladian at time t (Appendix A)."""

@@ -26,6 +26,8 @@ PIN_TESTS = [
     lambda: pins.test_gradient_matches_central_differences("frob", False, 0.0),
     lambda: pins.test_gradient_matches_central_differences("trace", True, 0.3),
     pins.test_jnm_values_and_gradient,
+    pins.test_jaynes_cummings_resonant_swap_discrete_closed_form,
+    pins.test_jaynes_cummings_detuned_phases_against_schrodinger,
 ]
 
 
@@ -161,9 +163,20 @@ def _terminal_nm_negated(prob, rhoT):
 
 
 ORIG_MERIT = imr.merit
+ORIG_JC = model.jc_hamiltonian
+
+
+def _jc_phase_conjugated(sysm, t):
+    return ORIG_JC(sysm, -t)
+
+
+def _jc_half_coupling(sysm, t):
+    return 0.5 * ORIG_JC(sysm, t)
 
 MUTATIONS = {
     "J_Nm observable reversed": [(imr, "merit", _merit_nm_transposed_index)],
+    "JC phase conjugated": [(model, "jc_hamiltonian", _jc_phase_conjugated)],
+    "JC coupling halved": [(model, "jc_hamiltonian", _jc_half_coupling)],
     "J_Nm terminal adjoint negated": [(imr, "terminal_adjoint", _terminal_nm_negated)],
     "hamiltonian part uses H instead of H^T": [(model, "hamiltonian_part", _ham_part_transposed),
                                                (imr, "hamiltonian_part", _ham_part_transposed)],

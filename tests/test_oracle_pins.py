@@ -423,3 +423,60 @@ def test_basis_matrices_are_pure_states():
         assert abs(np.trace(b) - 1.0) < 1e-15
         ev = np.linalg.eigvalsh(b)
         assert abs(ev[-1] - 1.0) < 1e-14 and np.max(np.abs(ev[:-1])) < 1e-14
+
+
+def _jc_pair(g, eta, T, n_steps, levels=(2, 2)):
+    sysm, ctrl = _undriven(levels, [0.0, 0.0], [0.0, 0.0], [INF, INF], [INF, INF], T=T, n_steps=n_steps)
+    jc = np.zeros((2, 2))
+    jc[0, 1] = g
+    sysm.jc_ghz = jc
+    sysm.rot_ghz = np.array([eta, 0.0])
+    return sysm, ctrl
+
+
+def test_jaynes_cummings_resonant_swap_discrete_closed_form():
+    """Resonant Jaynes-Cummings coupling of two qubits (Sec. II), |10> at
+    t = 0: the eigenstates (|01> +- |10>)/sqrt 2 of the one-excitation block
+    have energies +-omega, omega = 2 pi g, so their coherence turns by
+    2 atan(omega dt) per implicit-midpoint step and P(|01>) after n steps is
+    (1 - cos(2 n atan(omega dt)))/2 exactly."""
+    g, T, n = 0.0123, 37.0, 300
+    sysm, ctrl = _jc_pair(g, 0.0, T, n)
+    rho = np.zeros((4, 4), dtype=np.complex128)
+    rho[2, 2] = 1.0
+    rT = imr.forward(_problem(sysm, ctrl, rho), keep=False)["rhoT"][0]
+    om, h = TWO_PI * g, T / n
+    p01 = 0.5 * (1 - math.cos(2 * n * math.atan(om * h)))
+    assert abs(rT[1, 1].real - p01) < 1e-13
+    assert abs(rT[2, 2].real - (1 - p01)) < 1e-13
+    assert abs(np.trace(rT) - 1) < 1e-14
+
+
+def test_jaynes_cummings_detuned_phases_against_schrodinger():
+    """Detuned coupling (omega_0^rot - omega_1^rot = eta): the state of the
+    closed system is a pure state whose one-excitation amplitudes obey
+    i c' = H(t) c with H = g [[0, e^{-i eta t}], [e^{i eta t}, 0]] in the
+    basis (|01>, |10>); the IMR density matrix matches the outer product of a
+    tight Runge-Kutta solution to the method's O(dt^2) error, phases
+    included (which fixes the sign of eta)."""
+    from scipy.integrate import solve_ivp
+
+    g, eta, T, n = 0.02, 0.031, 20.0, 4000
+    sysm, ctrl = _jc_pair(g, eta, T, n)
+    rho = np.zeros((4, 4), dtype=np.complex128)
+    rho[2, 2] = 1.0
+    rT = imr.forward(_problem(sysm, ctrl, rho), keep=False)["rhoT"][0]
+    w, e = TWO_PI * g, TWO_PI * eta
+
+    def rhs(t, y):
+        c = y[:2] + 1j * y[2:]
+        Hm = np.array([[0, w * np.exp(-1j * e * t)], [w * np.exp(1j * e * t), 0]])
+        dc = -1j * Hm @ c
+        return np.concatenate([dc.real, dc.imag])
+
+    sol = solve_ivp(rhs, (0, T), [0.0, 1.0, 0.0, 0.0], rtol=1e-12, atol=1e-13)
+    c = sol.y[:2, -1] + 1j * sol.y[2:, -1]
+    ref = np.outer(c, c.conj())  # rows/columns: |01> (index 1), |10> (index 2)
+    sub = rT[np.ix_([1, 2], [1, 2])]
+    assert np.max(np.abs(sub - ref)) < 2e-5
+    assert abs(ref[0, 1]) > 0.01  # a coherence large enough for its phase to matter

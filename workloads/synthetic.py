@@ -43,6 +43,8 @@ class SystemSpec:
     T_ns: float
     n_steps: int
     essential: Optional[tuple] = None
+    jc_ghz: Optional[np.ndarray] = None  # (Q, Q) Jaynes-Cummings couplings g_pq/2pi; entries p < q used
+    rot_ghz: Optional[np.ndarray] = None  # (Q,) rotating-frame frequencies omega_q^rot/2pi (for the JC phases)
 
     @property
     def Q(self) -> int:
@@ -403,6 +405,7 @@ def random_problem(
     dissipation: bool = True,
     gamma2: float = 0.0,
     ckpt_every: int = -1,
+    jc: float = 0.0,
 ) -> Problem:
     """A small driven, dissipative problem with every term of the model active.
 
@@ -432,6 +435,12 @@ def random_problem(
         T_ns=T_ns,
         n_steps=n_steps,
     )
+    if jc > 0.0:
+        # Jaynes-Cummings couplings of every pair and rotating frames (drawn
+        # after the system so that jc = 0 keeps the earlier draws unchanged)
+        jrng = np.random.Generator(np.random.PCG64(seed + 7919))
+        sysm.jc_ghz = np.triu(jrng.uniform(0.2 * jc, jc, size=(Q, Q)), 1)
+        sysm.rot_ghz = jrng.uniform(-0.2, 0.2, size=Q)
     carriers = [np.concatenate([[0.0], rng.uniform(-0.3, 0.3, size=n_carriers - 1)]) for _ in range(Q)]
     ctrl = ControlSpec(n_splines, carriers, _alpha(rng, Q, n_splines, [n_carriers] * Q, amp))
     if hermitian:

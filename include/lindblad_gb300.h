@@ -201,6 +201,16 @@ int lb_objective_set_measure(lb_system* sys, int32_t m, double gamma2);
 /* Choose the sweep kind (LB_SWEEP_*); call before lb_workspace_bytes. */
 int lb_set_sweep(lb_system* sys, int32_t sweep);
 
+/* Jaynes-Cummings coupling of the system Hamiltonian (Sec. II):
+ *   sum_{p<q} g_pq (e^{i eta_pq t} a_p^+ a_q + e^{-i eta_pq t} a_p a_q^+),
+ *   eta_pq = omega_p^rot - omega_q^rot,
+ * the general rotating-frame form with time-dependent factors.  jc_ghz:
+ * Q x Q row-major g_pq/2pi in GHz, entries p < q used (0 = no coupling);
+ * rot_ghz: Q rotating-frame frequencies omega_q^rot/2pi in GHz (nullable: all
+ * equal, eta = 0).  Copied.  Call before lb_workspace_bytes; coupled systems
+ * run the one-CTA-per-state or grid sweeps (not the cluster sweep). */
+int lb_system_set_coupling(lb_system* sys, const double* jc_ghz, const double* rot_ghz);
+
 /* Hermitian symmetry (Sec. III-B: density matrices, and Lindblad's equation
  * preserves Hermiticity).  With LB_SYM_HERMITIAN (the default) the grid-wide
  * sweeps iterate only the elements k <= l of every state and write the

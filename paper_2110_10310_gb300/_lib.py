@@ -98,6 +98,7 @@ SIGNATURES = {
     "lb_solver_set": (c_int32, [c_void_p, c_int32, c_double, c_int32, c_int32]),
     "lb_set_sweep": (c_int32, [c_void_p, c_int32]),
     "lb_set_symmetry": (c_int32, [c_void_p, c_int32]),
+    "lb_system_set_coupling": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_double)]),
     "lb_workspace_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),
     "lb_bind_workspace": (c_int32, [c_void_p, c_void_p, c_size_t, c_void_p]),
     "lb_forward": (c_int32, [c_void_p, c_void_p, POINTER(c_double), c_void_p]),

@@ -82,6 +82,9 @@ struct lb_system {
   int method = LB_SOLVER_JACOBI;
   int krylov = 0;  // GMRES cycle length that fits shared memory (decided at bind)
   int dbits = 4;   // bits per packed digit of a basis index
+  // Jaynes-Cummings pairs p < q with g != 0: g and eta = omega_p^rot - omega_q^rot (rad/ns)
+  std::vector<int> jp, jq;
+  std::vector<double> jg, je;
   double rtol = 1e-15;
   int max_iter = 200;
   int K = 100;       // requested checkpoint interval; < 0 = automatic (effective_K)
@@ -175,7 +178,8 @@ int effective_K(const lb_system* s) {
 // Cluster sweep configuration of this system with 2Q (cs = false) or 4Q
 // lanes per element; C == 0 when it cannot apply.
 lbk::ClusterConfig cluster_cfg(const lb_system* s, bool cs) {
-  if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT || s->method == LB_SOLVER_GMRES) return lbk::ClusterConfig{};
+  if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT || s->method == LB_SOLVER_GMRES || !s->jp.empty())
+    return lbk::ClusterConfig{};
   return lbk::cluster_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, cs);
 }
 
@@ -249,7 +253,7 @@ Layout make_layout(const lb_system* s) {
   take(L.Dinv, c2 * V);
   take(L.alpha, sizeof(double) * s->n_params);
   take(L.carriers, sizeof(double) * n_carriers_total(s));
-  take(L.ctab, c2 * NT * s->Q);
+  take(L.ctab, c2 * NT * (s->Q + s->jp.size()));
   take(L.sfac, sizeof(double) * NT);
   take(L.q0, c2 * M * V);
   take(L.tar, c2 * M * V);
@@ -405,6 +409,14 @@ void fill_prob(lb_system* s) {
   P.method = s->method;
   P.krylov = s->krylov;
   P.dbits = s->dbits;
+  P.npair = (int32_t)s->jp.size();
+  P.cq = s->Q + P.npair;
+  for (int k = 0; k < P.npair; ++k) {
+    P.jp[k] = s->jp[k];
+    P.jq[k] = s->jq[k];
+    P.jg[k] = s->jg[k];
+    P.je[k] = s->je[k];
+  }
   P.kind = s->kind;
   P.Ns = s->Ns;
   P.n_params = s->n_params;
@@ -642,11 +654,11 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
     if (s->cluster) s->cc = cluster_cfg(s, c.E != 0);
     s->hp.gM = gproj_used(s);
     if (c.sweep == LB_SWEEP_RESIDENT) {
-      s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true, kry_elems(s));
+      s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, s->jp.empty(), kry_elems(s));
       const int threads = ((s->V + c.E - 1) / c.E + 31) / 32 * 32;
       s->rc.E = c.E;
       s->rc.threads = threads;
-      s->rc.QT = (c.E == 1 && s->Q <= 4) ? s->Q : 0;
+      s->rc.QT = (c.E == 1 && s->Q <= 4 && s->jp.empty()) ? s->Q : 0;
     }
     LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
     LB_CUDA(cudaMemcpyAsync(probe, at<double2>(s, s->L.q0), bytes, cudaMemcpyDeviceToDevice, st), "probe states");
@@ -688,10 +700,10 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
   s->cc = s->cluster ? cluster_cfg(s, win.E != 0) : cc0;
   s->hp.gM = gproj_used(s);
   if (win.sweep == LB_SWEEP_RESIDENT) {
-    s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true, kry_elems(s));
+    s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, s->jp.empty(), kry_elems(s));
     s->rc.E = win.E;
     s->rc.threads = ((s->V + win.E - 1) / win.E + 31) / 32 * 32;
-    s->rc.QT = (win.E == 1 && s->Q <= 4) ? s->Q : 0;
+    s->rc.QT = (win.E == 1 && s->Q <= 4 && s->jp.empty()) ? s->Q : 0;
   }
   LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
   LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
@@ -857,6 +869,30 @@ int lb_solver_set(lb_system* s, int32_t method, double rtol, int32_t max_iter, i
   return LB_OK;
 }
 
+int lb_system_set_coupling(lb_system* s, const double* jc_ghz, const double* rot_ghz) {
+  if (!s || !jc_ghz) return fail(LB_EINVAL, "null argument");
+  if (s->ws) return fail(LB_EINVAL, "set the coupling before binding a workspace");
+  std::vector<int> jp, jq;
+  std::vector<double> jg, je;
+  for (int p = 0; p < s->Q; ++p)
+    for (int q = p + 1; q < s->Q; ++q) {
+      const double g = jc_ghz[p * s->Q + q];
+      const double dr = rot_ghz ? rot_ghz[p] - rot_ghz[q] : 0.0;
+      if (!std::isfinite(g) || !std::isfinite(dr)) return fail(LB_EINVAL, "non-finite coupling or frequency");
+      if (g == 0.0) continue;
+      jp.push_back(p);
+      jq.push_back(q);
+      jg.push_back(kTwoPi * g);
+      je.push_back(kTwoPi * dr);
+    }
+  s->jp.swap(jp);
+  s->jq.swap(jq);
+  s->jg.swap(jg);
+  s->je.swap(je);
+  s->ctab_dirty = true;
+  return LB_OK;
+}
+
 int lb_set_symmetry(lb_system* s, int32_t symmetry) {
   if (!s) return fail(LB_EINVAL, "null system handle");
   if (symmetry != LB_SYM_NONE && symmetry != LB_SYM_HERMITIAN) return fail(LB_EINVAL, "unknown symmetry");
@@ -869,7 +905,7 @@ int lb_set_sweep(lb_system* s, int32_t sweep) {
   if (s->ws) return fail(LB_EINVAL, "choose the sweep before binding a workspace");
   if (sweep != LB_SWEEP_AUTO && sweep != LB_SWEEP_RESIDENT && sweep != LB_SWEEP_GRID && sweep != LB_SWEEP_CLUSTER)
     return fail(LB_EINVAL, "unknown sweep kind");
-  if (sweep == LB_SWEEP_CLUSTER && lbk::cluster_config(s->V, s->Q, 1, 1, 1, false).C <= 0)
+  if (sweep == LB_SWEEP_CLUSTER && (lbk::cluster_config(s->V, s->Q, 1, 1, 1, false).C <= 0 || !s->jp.empty()))
     return fail(LB_EINVAL, "cluster sweeps need Q <= 4 and N^2 * 2Q <= 1024");
   if (sweep == LB_SWEEP_RESIDENT && s->V > lbk::kMaxResidentV)
     return fail(LB_EINVAL, "one CTA per state needs N^2 <= 4096");
@@ -973,7 +1009,7 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
   if (rc) return rc;
   rc = upload_controls(s, st);
   if (rc) return rc;
-  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true, kry_elems(s));
+  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, s->jp.empty(), kry_elems(s));
   // the workspace now owns the states; pageable copies above are staged
   s->rho0.clear();
   s->rho0.shrink_to_fit();
@@ -1294,6 +1330,7 @@ int lb_batch_create(lb_system* const* systems, int32_t n, lb_batch** out) {
   if (!b) return fail(LB_ENOMEM, "host allocation failed");
   int maxV = 0, maxQ = 0, maxc = 0, maxj = 0, maxN = 0, minQ = LB_MAXQ + 1;
   size_t maxkry = 0;
+  bool pairs = false;
   for (int i = 0; i < n; ++i) {
     lb_system* s = systems[i];
     if (!s || !s->ws) {
@@ -1315,9 +1352,10 @@ int lb_batch_create(lb_system* const* systems, int32_t n, lb_batch** out) {
     maxj = std::max(maxj, n_jcoef(s));
     maxN = std::max(maxN, s->N);
     maxkry = std::max(maxkry, kry_elems(s));
+    pairs = pairs || !s->jp.empty();
     b->max_param_warps = std::max(b->max_param_warps, param_warps(s));
   }
-  b->rc = lbk::resident_config(maxV, maxQ, maxc, maxj, maxN, minQ == maxQ, maxkry);
+  b->rc = lbk::resident_config(maxV, maxQ, maxc, maxj, maxN, minQ == maxQ && !pairs, maxkry);
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
@@ -1612,7 +1650,7 @@ int static_bind(lb_system* s, void* ws, cudaStream_t st) {
   if (rc) return rc;
   rc = upload_controls(s, st);
   if (rc) return rc;
-  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, true, kry_elems(s));
+  s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, s->jp.empty(), kry_elems(s));
   return LB_OK;
 }
 

@@ -39,6 +39,11 @@ struct ProbDev {
   int32_t Ns, n_params;
   int32_t krylov;            // GMRES cycle length m (Krylov basis of m + 1 vectors in shared memory)
   int32_t dbits;             // bits per packed digit: ceil(log2 max n_q), at least 4
+  int32_t npair;             // Jaynes-Cummings pairs p < q with g_pq != 0
+  int32_t cq;                // entries per step of ctab: Q control factors, then npair coupling factors
+  int32_t jp[LB_MAXQ * (LB_MAXQ - 1) / 2], jq[LB_MAXQ * (LB_MAXQ - 1) / 2];
+  double jg[LB_MAXQ * (LB_MAXQ - 1) / 2];  // g_pq (rad/ns)
+  double je[LB_MAXQ * (LB_MAXQ - 1) / 2];  // eta_pq = omega_p^rot - omega_q^rot (rad/ns)
   double h, rtol, T, gamma2;
   int32_t levels[LB_MAXQ];
   int32_t stride[LB_MAXQ];   // s_q = prod_{p>q} n_p
@@ -63,7 +68,7 @@ struct ProbDev {
   // controls
   double* alpha;             // [n_params]
   double* carriers;          // [sum nf] Omega (rad/ns)
-  double2* ctab;             // [NT*Q] (dt/2) d_q(t_j + dt/2)
+  double2* ctab;             // [NT][cq] (dt/2) d_q(t_j + dt/2), then (dt/2) g_pq e^{i eta_pq (t_j + dt/2)}
   double* sfac;              // [NT] factor of the inner stopping test per step (k_stop_factors)
   // states and objective
   double2* q0;               // [M*V]

@@ -137,6 +137,8 @@ __device__ __forceinline__ double stop_factor(const ProbDev& P, int j) {
 struct Hdr {
   int Q, N, V, NT, K, n_ckpt, max_iter, method, kind, M, krylov;
   int db, dm;  // bits per packed digit and their mask
+  int npair, cq;  // Jaynes-Cummings pairs, entries per step of the control table
+  int jp[LB_MAXQ * (LB_MAXQ - 1) / 2], jq[LB_MAXQ * (LB_MAXQ - 1) / 2];
   double h, rtol;
   int lev[LB_MAXQ], stride[LB_MAXQ], coff[LB_MAXQ], joff[LB_MAXQ];
   double jump[LB_MAXQ];
@@ -163,6 +165,12 @@ __device__ void load_hdr(Hdr& H, const ProbDev& P) {
   H.krylov = P.krylov;
   H.db = P.dbits;
   H.dm = (1 << P.dbits) - 1;
+  H.npair = P.npair;
+  H.cq = P.cq;
+  for (int k = 0; k < P.npair; ++k) {
+    H.jp[k] = P.jp[k];
+    H.jq[k] = P.jq[k];
+  }
   H.h = P.h;
   H.rtol = P.rtol;
   for (int q = 0; q < LB_MAXQ; ++q) {
@@ -230,6 +238,31 @@ __device__ __forceinline__ void offdiag_acc(double& ar, double& ai, const double
       ar = fma(cj, x5.x, ar);
       ai = fma(cj, x5.y, ai);
     }
+  }
+  // Jaynes-Cummings pairs (Sec. II): -i[G a_p^+ a_q + conj(G) a_p a_q^+, X] with
+  //   U = sqrt(np_k) sqrt(nq_k+1) x[k-sp+sq, l] - sqrt(np_l+1) sqrt(nq_l) x[k, l+sp-sq]
+  //   W = sqrt(np_k+1) sqrt(nq_k) x[k+sp-sq, l] - sqrt(np_l) sqrt(nq_l+1) x[k, l-sp+sq]
+  //   -i G U - i conj(G) W = b (U - W) - i a (U + W), (a + i b) = (dt/2) G
+  for (int k = 0; k < H.npair; ++k) {
+    const int p = H.jp[k], q = H.jq[k];
+    const int np = H.lev[p], nq = H.lev[q], sp = H.stride[p], sq = H.stride[q];
+    const int pk = (kd >> (H.db * p)) & H.dm, qk = (kd >> (H.db * q)) & H.dm;
+    const int pl = (ld >> (H.db * p)) & H.dm, ql = (ld >> (H.db * q)) & H.dm;
+    const double u1 = T.cd[H.coff[p] + pk] * T.cu[H.coff[q] + qk];
+    const double u2 = T.cu[H.coff[p] + pl] * T.cd[H.coff[q] + ql];
+    const double w1 = T.cu[H.coff[p] + pk] * T.cd[H.coff[q] + qk];
+    const double w2 = T.cd[H.coff[p] + pl] * T.cu[H.coff[q] + ql];
+    const int d = sq - sp;  // row offset of a_p^+ a_q
+    const double2 xu1 = ldz<CG>(x + v + ((pk > 0 && qk + 1 < nq) ? d : 0));
+    const double2 xu2 = ldz<CG>(x + v - ((ql > 0 && pl + 1 < np) ? d * N : 0));
+    const double2 xw1 = ldz<CG>(x + v - ((qk > 0 && pk + 1 < np) ? d : 0));
+    const double2 xw2 = ldz<CG>(x + v + ((pl > 0 && ql + 1 < nq) ? d * N : 0));
+    const double ur = fma(-u2, xu2.x, u1 * xu1.x), ui = fma(-u2, xu2.y, u1 * xu1.y);
+    const double wr = fma(-w2, xw2.x, w1 * xw1.x), wi = fma(-w2, xw2.y, w1 * xw1.y);
+    const double2 c = ct[H.Q + k];
+    const double a = ADJ ? -c.x : c.x, b = ADJ ? -c.y : c.y;
+    ar = fma(b, ur - wr, fma(a, ui + wi, ar));
+    ai = fma(b, ui - wi, fma(-a, ur + wr, ai));
   }
 }
 
@@ -896,7 +929,7 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
     }
     int cur;
     if (pred) pr.predict(pc, H.V);
-    const int it = res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, stop_factor(P, j), cur,
+    const int it = res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur,
                                                  pred ? pc : nullptr);
     if (it < 0) {
       if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
@@ -999,7 +1032,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       }
       for (int j = j0; j < j1; ++j) {
         int cur;
-        const int it = res_solve<E, QT, false, GM>(S, H, el, pl, qf, P.ctab + (size_t)j * H.Q, stop_factor(P, j), cur);
+        const int it = res_solve<E, QT, false, GM>(S, H, el, pl, qf, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur);
         if (it < 0) {
           if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
           stats.flush(P.status);
@@ -1020,7 +1053,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       }
     }
     for (int j = j1 - 1; j >= j0; --j) {
-      const double2* ct = P.ctab + (size_t)j * H.Q;
+      const double2* ct = P.ctab + (size_t)j * H.cq;
       int cur;
       // (I - dt/2 (M^{j+1/2})^+) zhat^j = qhat^{j+1}   (eq. linsystem_adjoint)
       if (apred) pr.predict(pc, H.V);
@@ -1123,8 +1156,8 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
   for (int jj = 0; jj < j1 - j0; ++jj) {
     const int j = adjoint ? j1 - 1 - jj : j0 + jj;
     int cur;
-    const int it = adjoint ? res_solve<E, QT, true, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, stop_factor(P, j), cur)
-                           : res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.Q, stop_factor(P, j), cur);
+    const int it = adjoint ? res_solve<E, QT, true, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur)
+                           : res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur);
     if (it < 0) {
       if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
       stats.flush(P.status);
@@ -1589,7 +1622,7 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
     if (tape && H.K > 0 && j % H.K == 0 && crank == 0)
       for (int e = threadIdx.x; e < H.V; e += blockDim.x) P.ckpt[((size_t)i * H.n_ckpt + j / H.K) * H.V + e] = S.rr[e];
     double2 z;
-    const int it = cl_solve<QT, false, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z, pred ? hist : ClHist());
+    const int it = cl_solve<QT, false, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.cq, stop_factor(P, j), C, crank, cnt, z, pred ? hist : ClHist());
     if (it < 0) {
       if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
       failed = true;
@@ -1675,7 +1708,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
       for (int e = threadIdx.x; e < H.V; e += blockDim.x) S.rr[e] = P.ckpt[((size_t)i * H.n_ckpt + sg) * H.V + e];
       for (int j = j0; j < j1; ++j) {
         double2 z;
-        const int it = cl_solve<QT, false, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z);
+        const int it = cl_solve<QT, false, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.cq, stop_factor(P, j), C, crank, cnt, z);
         if (it < 0) {
           if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
           failed = true;
@@ -1699,7 +1732,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
                                       : P.ckpt[((size_t)i * H.NT + j) * H.V + pl.v])
                            : make_double2(0.0, 0.0);
       double2 zh;
-      const int it = cl_solve<QT, true, CS>(S, pl, S.ll, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, zh, apred ? ahist : ClHist());
+      const int it = cl_solve<QT, true, CS>(S, pl, S.ll, P.ctab + (size_t)j * H.cq, stop_factor(P, j), C, crank, cnt, zh, apred ? ahist : ClHist());
       if (it < 0) {
         if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
         failed = true;
@@ -1783,8 +1816,8 @@ __global__ void __launch_bounds__(128, 1) k_propagate_cl(const ProbDev* __restri
   for (int jj = 0; jj < j1 - j0; ++jj) {
     const int j = adjoint ? j1 - 1 - jj : j0 + jj;
     double2 z;
-    const int it = adjoint ? cl_solve<QT, true, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z)
-                           : cl_solve<QT, false, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.Q, stop_factor(P, j), C, crank, cnt, z);
+    const int it = adjoint ? cl_solve<QT, true, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.cq, stop_factor(P, j), C, crank, cnt, z)
+                           : cl_solve<QT, false, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.cq, stop_factor(P, j), C, crank, cnt, z);
     if (it < 0) {
       if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
       failed = true;
@@ -1904,9 +1937,18 @@ __global__ void k_gate_targets(ProbDev P, const double2* __restrict__ Vg, const 
 __global__ void k_control_table(const ProbDev* __restrict__ pp) {
   const ProbDev& P = *pp;
   const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (size_t)P.NT * P.Q) return;
-  const int j = (int)(tid / P.Q), q = (int)(tid % P.Q);
+  if (tid >= (size_t)P.NT * P.cq) return;
+  const int j = (int)(tid / P.cq), q = (int)(tid % P.cq);
   const double t = (j + 0.5) * P.h;
+  if (q >= P.Q) {
+    // Jaynes-Cummings pair: (dt/2) g e^{i eta t}
+    const int k = q - P.Q;
+    double sn, cs;
+    sincos(P.je[k] * t, &sn, &cs);
+    const double gg = 0.5 * P.h * P.jg[k];
+    P.ctab[tid] = make_double2(gg * cs, gg * sn);
+    return;
+  }
   const double dtau = P.T / (P.Ns - 2);
   const double x = t / dtau;
   const int slo = max(0, (int)floor(x - 1.0)), shi = min(P.Ns - 1, (int)floor(x + 2.0));
@@ -1939,8 +1981,14 @@ __global__ void k_stop_factors(const ProbDev* __restrict__ pp) {
   double rho = 0.0;
   for (int q = 0; q < P.Q; ++q) {
     const double n = P.levels[q];
-    const double2 c = P.ctab[(size_t)j * P.Q + q];
+    const double2 c = P.ctab[(size_t)j * P.cq + q];
     rho += hypot(c.x, c.y) * 2.0 * (sqrt(n - 1.0) + sqrt(n - 2.0)) + P.jump[q] * (n - 1.0);
+  }
+  // each of the four terms of a Jaynes-Cummings pair couples with at most
+  // |dt/2 g| sqrt((n_p - 1)(n_q - 1))
+  for (int k = 0; k < P.npair; ++k) {
+    const double2 c = P.ctab[(size_t)j * P.cq + P.Q + k];
+    rho += 4.0 * hypot(c.x, c.y) * sqrt((P.levels[P.jp[k]] - 1.0) * (P.levels[P.jq[k]] - 1.0));
   }
   // (1 - rho)/rho, capped so that rtol ||q|| times it stays finite
   P.sfac[j] = rho < 0.5 ? fmin((1.0 - rho) / fmax(rho, 1e-200), 1e200) : 1.0;
@@ -2043,7 +2091,7 @@ __global__ void k_apply(const ProbDev* __restrict__ pp, int step, const double2*
   const Tabs T{P.cu, P.cd, P.jf, P.ja};
   const double2* xv = x + (size_t)b * H.V;
   double ar = 0.0, ai = 0.0;
-  offdiag_acc<ADJ>(ar, ai, xv, v, P.digits[k], P.digits[l], H, T, P.ctab + (size_t)step * H.Q);
+  offdiag_acc<ADJ>(ar, ai, xv, v, P.digits[k], P.digits[l], H, T, P.ctab + (size_t)step * H.cq);
   const double inv = 2.0 / H.h;
   const double2 D = P.D[v];
   const double di = ADJ ? -D.y : D.y;
@@ -2444,8 +2492,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
       }
     }
     double2* z = nullptr;
-    const int it = mode == 2 ? grid_solve<true>(P, S, q, P.ctab + (size_t)j * H.Q, stop_factor(P, j), itg, nsolve, &z)
-                             : grid_solve<false>(P, S, q, P.ctab + (size_t)j * H.Q, stop_factor(P, j), itg, nsolve, &z,
+    const int it = mode == 2 ? grid_solve<true>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, &z)
+                             : grid_solve<false>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, &z,
                                                  pred ? hist : GridHist());
     if (it < 0) {
       grid_fail(P, it, j);
@@ -2516,7 +2564,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
       }
       for (int j = j0; j < j1; ++j) {
         double2* z = nullptr;
-        const int it = grid_solve<false>(P, S, P.qf, P.ctab + (size_t)j * H.Q, stop_factor(P, j), itg, nsolve, &z);
+        const int it = grid_solve<false>(P, S, P.qf, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, &z);
         if (it < 0) {
           grid_fail(P, it, j);
           failed = true;
@@ -2536,7 +2584,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
       if (failed) break;
     }
     for (int j = j1 - 1; j >= j0; --j) {
-      const double2* ct = P.ctab + (size_t)j * H.Q;
+      const double2* ct = P.ctab + (size_t)j * H.cq;
       double2* zh = nullptr;
       const int it = grid_solve<true>(P, S, P.lam, ct, stop_factor(P, j), itg, nsolve, &zh, apred ? ahist : GridHist());
       if (it < 0) {
@@ -2781,7 +2829,7 @@ cudaError_t launch_gate_targets(const ProbDev& h, const double2* Vg, const int32
 }
 
 cudaError_t launch_control_table(const ProbDev* d_prob, const ProbDev& h, cudaStream_t s) {
-  const size_t n = (size_t)h.NT * h.Q;
+  const size_t n = (size_t)h.NT * h.cq;
   k_control_table<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(d_prob);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -90,6 +90,12 @@ class LindbladSystem:
         h = c_void_p()
         L.check(self.lib.lb_system_create(byref(desc), byref(h)))
         self.h = h
+        jc = getattr(sysm, "jc_ghz", None)
+        if jc is not None and np.any(np.asarray(jc) != 0.0):
+            rot = getattr(sysm, "rot_ghz", None)
+            L.check(self.lib.lb_system_set_coupling(
+                h, arr(np.asarray(jc, dtype=np.float64).reshape(Q * Q), c_double, np.float64),
+                None if rot is None else arr(rot, c_double, np.float64)))
         ctrl = problem.controls
         nf = np.array([len(c) for c in ctrl.carriers_ghz], dtype=np.int32)
         car = np.concatenate([np.asarray(c, dtype=np.float64) for c in ctrl.carriers_ghz])

@@ -657,3 +657,49 @@ def test_reset_from_ensemble_state_matches_oracle(levels, sweep):
     sw = {"auto": L.LB_SWEEP_AUTO, "cluster": L.LB_SWEEP_CLUSTER, "grid": L.LB_SWEEP_GRID}[sweep]
     p = W.reset_ensemble(levels=levels, n_steps=400, T_ns=20.0, n_splines=8, amp=0.05)
     _check_problem(p, sweep=sw)
+
+
+# ----------------------------------------------------------------------------
+# Jaynes-Cummings coupling
+
+
+@pytest.mark.parametrize("levels", [(2, 3), (2, 2, 2), (3, 2, 4)])
+def test_apply_with_jaynes_cummings_matches_dense(levels):
+    """y = M x and M^+ x with time-dependent Jaynes-Cummings pairs against
+    the dense Kronecker M."""
+    p = W.random_problem(111, levels=levels, n_states=1, n_steps=10, jc=0.05)
+    s = _sys(p)
+    m = model.Model(p.system, p.controls)
+    N = m.N
+    X = _rand_states(np.random.default_rng(9), 2, N)
+    xt = torch.from_numpy(X).cuda()
+    for j in (0, 6):
+        Md = m.M(m.t_half(j))
+        for adj in (False, True):
+            A = Md.conj().T if adj else Md
+            y = s.apply(xt, j, adjoint=adj).cpu().numpy()
+            ref = np.stack([model.unvec(A @ model.vec(X[b]), N) for b in range(2)])
+            scale = np.max(np.abs(A).sum(axis=1)) * np.max(np.abs(X))
+            assert np.max(np.abs(y - ref)) <= 1e-14 * scale, (levels, j, adj)
+
+
+@pytest.mark.parametrize("levels,sweep,solver", [((2, 3), "resident", "jacobi"), ((3, 2, 2), "grid", "jacobi"),
+                                                  ((2, 3), "resident", "gmres")])
+def test_jaynes_cummings_gradient_matches_oracle(levels, sweep, solver):
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(112, levels=levels, n_states=2, n_steps=40, T_ns=0.8, amp=0.1, jc=0.05, ckpt_every=7)
+    sw = {"resident": L.LB_SWEEP_RESIDENT, "grid": L.LB_SWEEP_GRID}[sweep]
+    sv = {"jacobi": L.LB_SOLVER_JACOBI, "gmres": L.LB_SOLVER_GMRES}[solver]
+    _check_problem(p, sweep=sw, solver=sv)
+
+
+def test_jaynes_cummings_rejects_cluster_and_auto_avoids_it():
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(113, levels=(2, 3), n_states=2, n_steps=10, T_ns=0.2, amp=0.1, jc=0.05)
+    with pytest.raises(L.LBError):
+        _sys(p, sweep=L.LB_SWEEP_CLUSTER)
+    s = _sys(p)
+    s.gradient()
+    assert s.stats()["sweep"] == "resident"

@@ -136,7 +136,48 @@ def terminal_adjoint(prob, rhoT: np.ndarray) -> np.ndarray:
     return np.stack(cols, axis=1)
 
 
+def penalty_weights(prob, NT: int | None = None) -> np.ndarray:
+    """dt beta(t_j), j = 0..N_T-1, beta(t) = exp(-((t - T)/a)^2)/a: the
+    running penalty gamma1 int_0^T beta(t) J(rho_tar, rho(t)) dt of eq.
+    optimproblem by the left rectangle rule on the time grid."""
+    NT = prob.system.n_steps if NT is None else NT
+    h = prob.system.T_ns / prob.system.n_steps
+    t = np.arange(NT) * h
+    a = float(prob.penalty_a)
+    return h * np.exp(-(((t - prob.system.T_ns) / a) ** 2)) / a
+
+
+def penalty(prob, qs) -> float:
+    """gamma1/M sum_i beta_i sum_j dt beta(t_j) J(rho_i^tar, q_i^j) (the
+    running penalty per state, weighted like the final-time term)."""
+    g1 = float(getattr(prob, "gamma1", 0.0))
+    if g1 == 0.0:
+        return 0.0
+    tars = targets_of(prob)
+    w = weights_of(prob)
+    pw = penalty_weights(prob, len(qs) - 1)
+    N = tars.shape[1]
+    tot = 0.0
+    for i in range(prob.M):
+        for j in range(len(qs) - 1):
+            tot += w[i] * pw[j] * merit(prob.objective, tars[i], unvec(qs[j][:, i], N))
+    return g1 * tot / prob.M
+
+
+def merit_gradient(prob, tar: np.ndarray, q: np.ndarray) -> np.ndarray:
+    """2 dJ/dconj(q) of the merit functional at q (vectors): q - q_tar,
+    -q_tar or vec(N_m)."""
+    if prob.objective == "frob":
+        return q - tar
+    if prob.objective == "nm":
+        return tar
+    return -tar
+
+
 def value(prob) -> float:
+    if float(getattr(prob, "gamma1", 0.0)) != 0.0:
+        fw = forward(prob, keep=True)
+        return objective(prob, fw["rhoT"]) + penalty(prob, fw["q"])
     return objective(prob, forward(prob, keep=False)["rhoT"])
 
 
@@ -162,7 +203,9 @@ def dd_dalpha(ctrl, T: float, t: float):
 
 
 def gradient(prob, n_steps: int | None = None):
-    """Objective G and its exact discrete gradient (Appendix B).
+    """Objective G and its exact discrete gradient (Appendix B), with the
+    running penalty's source gamma1 beta_i/M dt beta(t_j) g(q^j) added to
+    qhat^j when gamma1 != 0.
 
     Backward sweep for j = N_T-1..0:
       (I - dt/2 (M^{j+1/2})^+) zhat^j = qhat^{j+1}     (eq. linsystem_adjoint)
@@ -176,8 +219,13 @@ def gradient(prob, n_steps: int | None = None):
     model = fw["model"]
     h = model.h
     NT = len(fw["z"])
-    G = objective(prob, fw["rhoT"])
+    G = objective(prob, fw["rhoT"]) + penalty(prob, fw["q"])
     Lam = terminal_adjoint(prob, fw["rhoT"])
+    g1 = float(getattr(prob, "gamma1", 0.0))
+    if g1 != 0.0:
+        tars = np.stack([vec(t) for t in targets_of(prob)], axis=1)
+        wts = weights_of(prob)
+        pw = penalty_weights(prob, NT)
     levels = model.levels
     Ma = [hamiltonian_part(a_op(q, levels)) for q in range(len(levels))]
     Mad = [hamiltonian_part(a_op(q, levels).conj().T) for q in range(len(levels))]
@@ -193,6 +241,10 @@ def gradient(prob, n_steps: int | None = None):
         for k, q, dd in dd_dalpha(prob.controls, prob.system.T_ns, t):
             grad[k] += h * np.real(dd * Ca[q] + np.conj(dd) * Cad[q])
         Lam = Lam + h * (MH @ Zh)
+        if g1 != 0.0:
+            # source of the running penalty at q^j (Appendix B)
+            for i in range(prob.M):
+                Lam[:, i] += g1 * wts[i] / prob.M * pw[j] * merit_gradient(prob, tars[:, i], fw["q"][j][:, i])
     grad += prob.gamma2 * prob.controls.alpha
     return G, grad, fw
 
@@ -209,7 +261,11 @@ def fd_gradient(prob, eps: float = 1e-6, indices=None, n_steps: int | None = Non
             p = copy.deepcopy(prob)
             p.controls.alpha = prob.controls.alpha.copy()
             p.controls.alpha[k] += sgn * eps
-            vals.append(objective(p, forward(p, n_steps=n_steps, keep=False)["rhoT"]))
+            if float(getattr(p, "gamma1", 0.0)) != 0.0:
+                fw = forward(p, n_steps=n_steps, keep=True)
+                vals.append(objective(p, fw["rhoT"]) + penalty(p, fw["q"]))
+            else:
+                vals.append(objective(p, forward(p, n_steps=n_steps, keep=False)["rhoT"]))
         out[k] = (vals[0] - vals[1]) / (2 * eps)
     return out
 

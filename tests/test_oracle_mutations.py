@@ -28,6 +28,7 @@ PIN_TESTS = [
     pins.test_jnm_values_and_gradient,
     pins.test_jaynes_cummings_resonant_swap_discrete_closed_form,
     pins.test_jaynes_cummings_detuned_phases_against_schrodinger,
+    pins.test_running_penalty_closed_form_and_gradient,
 ]
 
 
@@ -164,6 +165,20 @@ def _terminal_nm_negated(prob, rhoT):
 
 ORIG_MERIT = imr.merit
 ORIG_JC = model.jc_hamiltonian
+ORIG_PW = imr.penalty_weights
+ORIG_MG = imr.merit_gradient
+
+
+def _penalty_weights_right_endpoints(prob, NT=None):
+    w = ORIG_PW(prob, NT)
+    h = prob.system.T_ns / prob.system.n_steps
+    a = float(prob.penalty_a)
+    t = (np.arange(len(w)) + 1) * h
+    return h * np.exp(-(((t - prob.system.T_ns) / a) ** 2)) / a
+
+
+def _penalty_source_negated(prob, tar, q):
+    return -ORIG_MG(prob, tar, q)
 
 
 def _jc_phase_conjugated(sysm, t):
@@ -176,6 +191,8 @@ def _jc_half_coupling(sysm, t):
 MUTATIONS = {
     "J_Nm observable reversed": [(imr, "merit", _merit_nm_transposed_index)],
     "JC phase conjugated": [(model, "jc_hamiltonian", _jc_phase_conjugated)],
+    "penalty sampled at t_j+1": [(imr, "penalty_weights", _penalty_weights_right_endpoints)],
+    "penalty source negated": [(imr, "merit_gradient", _penalty_source_negated)],
     "JC coupling halved": [(model, "jc_hamiltonian", _jc_half_coupling)],
     "J_Nm terminal adjoint negated": [(imr, "terminal_adjoint", _terminal_nm_negated)],
     "hamiltonian part uses H instead of H^T": [(model, "hamiltonian_part", _ham_part_transposed),

@@ -480,3 +480,37 @@ def test_jaynes_cummings_detuned_phases_against_schrodinger():
     sub = rT[np.ix_([1, 2], [1, 2])]
     assert np.max(np.abs(sub - ref)) < 2e-5
     assert abs(ref[0, 1]) > 0.01  # a coherence large enough for its phase to matter
+
+
+def test_running_penalty_closed_form_and_gradient():
+    """The running penalty gamma1 int beta(t) J dt (Sec. III, eq.
+    optimproblem), by the left rectangle rule: for an undriven qubit from
+    |1><1| with J_Frob to |0><0|, J(q^j) = (1 - c^j)^2 with c the Cayley
+    factor of the T1 decay, so the penalty is a closed-form sum; and with
+    controls on, the adjoint gradient (sources included) matches central
+    differences for every merit functional."""
+    sysm, ctrl = _undriven((2,), [0.0], [0.0], [0.4], [INF], T=30.0, n_steps=300)
+    one = np.diag([0.0, 1.0]).astype(np.complex128)
+    zero = np.diag([1.0, 0.0]).astype(np.complex128)
+    p = W.Problem("pen", sysm, ctrl, one[None], "frob", targets=zero[None], gamma1=0.7, penalty_a=8.0)
+    h = sysm.T_ns / sysm.n_steps
+    g1 = 1.0 / 400.0
+    c = (1 - h * g1 / 2) / (1 + h * g1 / 2)
+    expect = 0.0
+    for j in range(sysm.n_steps):
+        pop1 = c ** j
+        J = pop1 ** 2  # |rho - |0><0||_F^2 / 2 with rho = diag(1 - pop1, pop1)
+        t = j * h
+        expect += h * math.exp(-(((t - sysm.T_ns) / 8.0) ** 2)) / 8.0 * J
+    G = imr.value(p)
+    GT = c ** (2 * sysm.n_steps)
+    assert abs(G - (GT + 0.7 * expect)) < 1e-13
+    for objective in ("frob", "trace"):
+        q = W.random_problem(43, levels=(2, 3), n_states=2, n_steps=12, objective=objective, n_splines=5)
+        q.gamma1, q.penalty_a = 0.8, 0.3
+        Gq, g, _ = imr.gradient(q)
+        assert abs(Gq - imr.value(q)) < 1e-15
+        fd = imr.fd_gradient(q, eps=1e-6)
+        scale = np.max(np.abs(g))
+        for k, v in fd.items():
+            assert abs(g[k] - v) <= 1e-6 * scale, (objective, k, g[k], v)

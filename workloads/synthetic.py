@@ -78,6 +78,8 @@ class Problem:
     weights: Optional[np.ndarray] = None  # (M,) float64, None = all ones
     gamma2: float = 0.0
     ckpt_every: int = -1  # -1: automatic (full stage tape when it fits, else every 100 steps)
+    gamma1: float = 0.0  # weight of the running penalty (Sec. III, eq. optimproblem)
+    penalty_a: float = 1.0  # width a (ns) of beta(t) = exp(-((t - T)/a)^2)/a
     meta: dict = field(default_factory=dict)
 
     @property

@@ -198,6 +198,17 @@ int lb_solver_set(lb_system* sys, int32_t method, double rtol, int32_t max_iter,
  * after lb_states_set. */
 int lb_objective_set_measure(lb_system* sys, int32_t m, double gamma2);
 
+/* Running penalty of eq. optimproblem (Sec. III):
+ *   G += gamma1/M sum_i beta_i sum_{j=0}^{N_T-1} dt beta(t_j) J(rho_i^tar, rho_i(t_j)),
+ *   beta(t) = exp(-((t - T)/a)^2)/a,
+ * the time integral by the left rectangle rule, weighted per state like the
+ * final-time term; its derivative enters the adjoint sweep as the source
+ * gamma1 beta_i/M dt beta(t_j) g(q^j) at qhat^j (Appendix B).  gamma1 >= 0
+ * (0 = off, the default), a_ns > 0.  Runs in the one-CTA-per-state sweep
+ * (N^2 <= 4096; lb_bind_workspace refuses grid or cluster sweeps with it).
+ * Call before lb_workspace_bytes. */
+int lb_objective_set_penalty(lb_system* sys, double gamma1, double a_ns);
+
 /* Choose the sweep kind (LB_SWEEP_*); call before lb_workspace_bytes. */
 int lb_set_sweep(lb_system* sys, int32_t sweep);
 

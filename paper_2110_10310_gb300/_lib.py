@@ -95,6 +95,7 @@ SIGNATURES = {
     "lb_objective_set": (c_int32, [c_void_p, c_int32, c_void_p, c_double]),
     "lb_objective_set_gate": (c_int32, [c_void_p, c_int32, c_void_p, c_double]),
     "lb_objective_set_measure": (c_int32, [c_void_p, c_int32, c_double]),
+    "lb_objective_set_penalty": (c_int32, [c_void_p, c_double, c_double]),
     "lb_solver_set": (c_int32, [c_void_p, c_int32, c_double, c_int32, c_int32]),
     "lb_set_sweep": (c_int32, [c_void_p, c_int32]),
     "lb_set_symmetry": (c_int32, [c_void_p, c_int32]),

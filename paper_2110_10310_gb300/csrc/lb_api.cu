@@ -46,7 +46,7 @@ struct Region {
 
 struct Layout {
   Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
-      gproj, gsum, sfac, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, hmap;
+      gproj, gsum, sfac, pen, qb, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, hmap;
   size_t total = 0;
 };
 
@@ -90,6 +90,7 @@ struct lb_system {
   int K = 100;       // requested checkpoint interval; < 0 = automatic (effective_K)
   int sweep = LB_SWEEP_AUTO;
   int symmetry = LB_SYM_HERMITIAN;
+  double gamma1 = 0.0, pen_a = 1.0;  // running penalty (one CTA per state)
   bool rho_herm = false;  // every initial state exactly Hermitian
   bool tar_herm = false;  // every explicit target exactly Hermitian (gate targets: always)
   int gblocks = 0;   // cooperative grid size (grid sweeps)
@@ -143,6 +144,7 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 bool use_grid(const lb_system* s) {
   if (s->V > lbk::kMaxResidentV) return true;
   if (s->method == LB_SOLVER_GMRES) return false;  // GMRES runs one CTA per state
+  if (s->gamma1 != 0.0) return false;              // so does the running penalty
   if (s->sweep == LB_SWEEP_GRID) return true;
   if (s->sweep == LB_SWEEP_RESIDENT || s->sweep == LB_SWEEP_CLUSTER) return false;
   return s->V >= 1024 && s->M < 64;
@@ -178,7 +180,8 @@ int effective_K(const lb_system* s) {
 // Cluster sweep configuration of this system with 2Q (cs = false) or 4Q
 // lanes per element; C == 0 when it cannot apply.
 lbk::ClusterConfig cluster_cfg(const lb_system* s, bool cs) {
-  if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT || s->method == LB_SOLVER_GMRES || !s->jp.empty())
+  if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT || s->method == LB_SOLVER_GMRES || !s->jp.empty() ||
+      s->gamma1 != 0.0)
     return lbk::ClusterConfig{};
   return lbk::cluster_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, cs);
 }
@@ -202,6 +205,11 @@ int decide_krylov(lb_system* s) {
   LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   LB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "cudaDeviceGetAttribute");
   s->krylov = s->V <= lbk::kMaxResidentV ? lbk::gmres_krylov_dim(s->V, n_coef(s), n_jcoef(s), s->N, (size_t)optin) : 0;
+  if (s->gamma1 != 0.0) {
+    if (s->V > lbk::kMaxResidentV || s->sweep == LB_SWEEP_GRID || s->sweep == LB_SWEEP_CLUSTER)
+      return fail(LB_EINVAL, "the running penalty runs in the one-CTA-per-state sweep only (N^2 <= 4096)");
+    s->sweep = LB_SWEEP_RESIDENT;
+  }
   if (s->method != LB_SOLVER_GMRES) return LB_OK;
   if (s->sweep == LB_SWEEP_GRID || s->sweep == LB_SWEEP_CLUSTER)
     return fail(LB_EINVAL, "GMRES runs in the one-CTA-per-state sweep only (LB_SWEEP_RESIDENT or AUTO)");
@@ -255,6 +263,8 @@ Layout make_layout(const lb_system* s) {
   take(L.carriers, sizeof(double) * n_carriers_total(s));
   take(L.ctab, c2 * NT * (s->Q + s->jp.size()));
   take(L.sfac, sizeof(double) * NT);
+  take(L.pen, sizeof(double) * NT);
+  take(L.qb, s->gamma1 != 0.0 ? c2 * M * V : 0);
   take(L.q0, c2 * M * V);
   take(L.tar, c2 * M * V);
   take(L.wgt, sizeof(double) * M);
@@ -464,6 +474,10 @@ void fill_prob(lb_system* s) {
   P.gproj = at<double2>(s, s->L.gproj);
   P.gsum = at<double2>(s, s->L.gsum);
   P.sfac = at<double>(s, s->L.sfac);
+  P.pen = at<double>(s, s->L.pen);
+  P.qb = at<double2>(s, s->L.qb);
+  P.gamma1 = s->gamma1;
+  P.pen_a = s->pen_a;
   P.J = at<double>(s, s->L.J);
   P.G = at<double>(s, s->L.G);
   P.grad = at<double>(s, s->L.grad);
@@ -890,6 +904,16 @@ int lb_system_set_coupling(lb_system* s, const double* jc_ghz, const double* rot
   s->jg.swap(jg);
   s->je.swap(je);
   s->ctab_dirty = true;
+  return LB_OK;
+}
+
+int lb_objective_set_penalty(lb_system* s, double gamma1, double a_ns) {
+  if (!s) return fail(LB_EINVAL, "null system handle");
+  if (s->ws) return fail(LB_EINVAL, "set the penalty before binding a workspace");
+  if (!(gamma1 >= 0.0) || !std::isfinite(gamma1)) return fail(LB_EINVAL, "gamma1 must be finite and >= 0");
+  if (!(a_ns > 0.0) || !std::isfinite(a_ns)) return fail(LB_EINVAL, "a must be finite and > 0");
+  s->gamma1 = gamma1;
+  s->pen_a = a_ns;
   return LB_OK;
 }
 

@@ -70,6 +70,9 @@ struct ProbDev {
   double* carriers;          // [sum nf] Omega (rad/ns)
   double2* ctab;             // [NT][cq] (dt/2) d_q(t_j + dt/2), then (dt/2) g_pq e^{i eta_pq (t_j + dt/2)}
   double* sfac;              // [NT] factor of the inner stopping test per step (k_stop_factors)
+  double* pen;               // [NT] running-penalty weights dt beta(t_j) (gamma1 != 0)
+  double2* qb;               // [M*V] q^j rebuilt backwards in the adjoint sweep (gamma1 != 0)
+  double gamma1, pen_a;      // running-penalty weight and width a (ns)
   // states and objective
   double2* q0;               // [M*V]
   double2* tar;              // [M*V]

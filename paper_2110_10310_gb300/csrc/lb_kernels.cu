@@ -113,6 +113,27 @@ __device__ __forceinline__ double bspline2(double x) {
 __device__ __forceinline__ double merit_value(int kind, double sum) {
   return kind == LB_J_FROB ? 0.5 * sum : (kind == LB_J_TR ? 1.0 - sum : sum);
 }
+// this thread's share of the merit sum for state values q[e] against t
+template <int E>
+__device__ __forceinline__ double merit_partial(int kind, const double2 (&q)[E], const double2* __restrict__ tar,
+                                                int V) {
+  double acc = 0.0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int v = threadIdx.x + e * blockDim.x;
+    if (v < V) {
+      const double2 t = tar[v];
+      if (kind == LB_J_FROB) {
+        const double dr = q[e].x - t.x, di = q[e].y - t.y;
+        acc = fma(dr, dr, fma(di, di, acc));
+      } else {
+        acc = fma(t.x, q[e].x, fma(t.y, q[e].y, acc));
+      }
+    }
+  }
+  return acc;
+}
+
 // factor of the target in the terminal condition beta_i/M g_i for the
 // functionals linear in q: g = -t (J_Tr), g = N_m = t (J_Nm)
 __device__ __forceinline__ double linear_sign(int kind) { return kind == LB_J_NM ? 1.0 : -1.0; }
@@ -138,6 +159,7 @@ struct Hdr {
   int Q, N, V, NT, K, n_ckpt, max_iter, method, kind, M, krylov;
   int db, dm;  // bits per packed digit and their mask
   int npair, cq;  // Jaynes-Cummings pairs, entries per step of the control table
+  double gamma1;  // weight of the running penalty (0: none)
   int jp[LB_MAXQ * (LB_MAXQ - 1) / 2], jq[LB_MAXQ * (LB_MAXQ - 1) / 2];
   double h, rtol;
   int lev[LB_MAXQ], stride[LB_MAXQ], coff[LB_MAXQ], joff[LB_MAXQ];
@@ -167,6 +189,7 @@ __device__ void load_hdr(Hdr& H, const ProbDev& P) {
   H.dm = (1 << P.dbits) - 1;
   H.npair = P.npair;
   H.cq = P.cq;
+  H.gamma1 = P.gamma1;
   for (int k = 0; k < P.npair; ++k) {
     H.jp[k] = P.jp[k];
     H.jq[k] = P.jq[k];
@@ -918,7 +941,10 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
   Pred<E> pr;
   if (pred) pr.init(P, base);
   double2 pc[E];
+  // running penalty sum_j dt beta(t_j) J(q^j) (Sec. III, eq. optimproblem)
+  double jpen = 0.0;
   for (int j = 0; j < H.NT; ++j) {
+    if (H.gamma1 != 0.0) jpen = fma(P.pen[j], merit_value(H.kind, cta_sum(S, merit_partial<E>(H.kind, q, P.tar + base, H.V))), jpen);
     if (tape && H.K > 0 && j % H.K == 0) {
       double2* ck = P.ckpt + ((size_t)i * H.n_ckpt + j / H.K) * H.V;
 #pragma unroll
@@ -968,7 +994,7 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
     }
   }
   const double tot = cta_sum(S, acc);
-  if (threadIdx.x == 0) P.J[i] = merit_value(H.kind, tot);
+  if (threadIdx.x == 0) P.J[i] = merit_value(H.kind, tot) + H.gamma1 * jpen;
   stats.flush(P.status);
 }
 
@@ -997,6 +1023,10 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
   // terminal condition qhat^{N_T} = beta_i/M g_i (Appendix B): g = q - q_tar
   // for J_Frob, g = -q_tar for J_Tr
   double2 lam[E], qf[E];
+  // running penalty: q^j is rebuilt backwards, q^j = 2 z^j - q^{j+1}, in the
+  // workspace buffer qb (each thread its own elements), starting from q^{N_T}
+  if (H.gamma1 != 0.0)
+    for (int v = threadIdx.x; v < H.V; v += blockDim.x) P.qb[base + v] = P.qT[base + v];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int v = threadIdx.x + e * blockDim.x;
@@ -1116,13 +1146,28 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
         if (c == 2) g[3] = -t;
         if (c == 3) g[2] = t;
       }
-      // qhat^j = qhat^{j+1} + dt M^+ zhat = 2 zhat - qhat^{j+1}
+      // qhat^j = qhat^{j+1} + dt M^+ zhat = 2 zhat - qhat^{j+1}, plus the running
+      // penalty's source gamma1 beta_i/M dt beta(t_j) g(q^j) (Appendix B)
+      const double pw = H.gamma1 != 0.0 ? H.gamma1 * w * P.pen[j] : 0.0;
+      const double ls = linear_sign(H.kind);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
         const int v = threadIdx.x + e * blockDim.x;
         if (v < H.V) {
           const double2 z = zh[v];
           lam[e] = make_double2(fma(2.0, z.x, -lam[e].x), fma(2.0, z.y, -lam[e].y));
+          if (H.gamma1 != 0.0) {
+            const double2 qn = P.qb[base + v], t = P.tar[base + v];
+            const double2 qj = make_double2(fma(2.0, Z[e].x, -qn.x), fma(2.0, Z[e].y, -qn.y));
+            P.qb[base + v] = qj;
+            if (H.kind == LB_J_FROB) {
+              lam[e].x = fma(pw, qj.x - t.x, lam[e].x);
+              lam[e].y = fma(pw, qj.y - t.y, lam[e].y);
+            } else {
+              lam[e].x = fma(pw * ls, t.x, lam[e].x);
+              lam[e].y = fma(pw * ls, t.y, lam[e].y);
+            }
+          }
         }
       }
     }
@@ -1992,6 +2037,11 @@ __global__ void k_stop_factors(const ProbDev* __restrict__ pp) {
   }
   // (1 - rho)/rho, capped so that rtol ||q|| times it stays finite
   P.sfac[j] = rho < 0.5 ? fmin((1.0 - rho) / fmax(rho, 1e-200), 1e200) : 1.0;
+  // running penalty weight dt beta(t_j), beta(t) = exp(-((t - T)/a)^2)/a, left rectangle rule
+  if (P.gamma1 != 0.0) {
+    const double x = (j * P.h - P.T) / P.pen_a;
+    P.pen[j] = P.h * exp(-x * x) / P.pen_a;
+  }
 }
 
 // G = sum_i beta_i/M J_i + gamma2/2 ||alpha||^2 (eq. optimproblem), one warp

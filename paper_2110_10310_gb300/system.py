@@ -115,6 +115,9 @@ class LindbladSystem:
         else:
             V = np.ascontiguousarray(np.asarray(problem.gate, dtype=np.complex128).T).view(np.float64)
             L.check(self.lib.lb_objective_set_gate(h, kind, V.ctypes.data_as(c_void_p), g2))
+        g1 = float(getattr(problem, "gamma1", 0.0))
+        if g1 != 0.0:
+            L.check(self.lib.lb_objective_set_penalty(h, g1, float(problem.penalty_a)))
         K = int(getattr(problem, "ckpt_every", 100)) if ckpt_every is None else int(ckpt_every)
         L.check(self.lib.lb_solver_set(h, int(solver), float(rtol), int(max_iter), K))
         L.check(self.lib.lb_set_sweep(h, int(sweep)))

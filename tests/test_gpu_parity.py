@@ -703,3 +703,31 @@ def test_jaynes_cummings_rejects_cluster_and_auto_avoids_it():
     s = _sys(p)
     s.gradient()
     assert s.stats()["sweep"] == "resident"
+
+
+# ----------------------------------------------------------------------------
+# running penalty gamma1 int beta(t) J dt
+
+
+@pytest.mark.parametrize("levels,objective,K,solver", [((2, 3), "frob", 0, "jacobi"), ((3, 3), "trace", 7, "jacobi"),
+                                                        ((2, 3), "frob", 5, "gmres")])
+def test_running_penalty_matches_oracle(levels, objective, K, solver):
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(121, levels=levels, n_states=2, n_steps=40, T_ns=0.8, amp=0.1, objective=objective,
+                         ckpt_every=K, gamma2=0.05)
+    p.gamma1, p.penalty_a = 0.6, 0.3
+    sv = {"jacobi": L.LB_SOLVER_JACOBI, "gmres": L.LB_SOLVER_GMRES}[solver]
+    s, _ = _check_problem(p, solver=sv)
+    assert s.stats()["sweep"] == "resident"
+
+
+def test_running_penalty_with_jnm_and_sweep_rules():
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.reset_ensemble(levels=(2, 3), n_steps=300, T_ns=15.0, n_splines=8, amp=0.05)
+    p.gamma1, p.penalty_a = 0.4, 5.0
+    _check_problem(p)
+    for sweep in (L.LB_SWEEP_GRID, L.LB_SWEEP_CLUSTER):
+        with pytest.raises(L.LBError):
+            _sys(p, sweep=sweep)

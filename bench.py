@@ -672,6 +672,8 @@ def main():
                 "solver": f"{st['solver']} fixed point, rtol 1e-15",
                 "sweep": st["sweep"],
                 "symmetry": st["symmetry"],
+                "workspace_bytes": s.workspace_bytes,
+                "peak_device_bytes": int(torch.cuda.max_memory_allocated(dev)),
                 "l2": "flushed between timed steps (256 MiB write)",
                 "parallelism": f"replicas{world}" if world > 1 else "single",
                 "inner_iters_per_step": st["inner_iterations"] / max(1, st["state_steps"]),

@@ -13,6 +13,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "lb_internal.h"
 
 namespace {
@@ -395,6 +397,15 @@ int refresh_symmetry(lb_system* s) {
   LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, s->bind_stream), "upload problem");
   return LB_OK;
 }
+
+// NVTX range over a host scope (the enqueueing of a sweep; visible in
+// Nsight timelines beside the kernels it launches)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 int upload_controls(lb_system* s, cudaStream_t st) {
   if (s->n_params)
@@ -1041,6 +1052,7 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
 }
 
 static int run_forward(lb_system* s, cudaStream_t st, int tape) {
+  NvtxRange nvtx("lb forward sweep");
   int rc = order_after_uploads(s, st);
   if (rc) return rc;
   s->launches = 0;
@@ -1126,6 +1138,7 @@ static int param_warps(const lb_system* s) {
 static int gradient_device(lb_system* s, cudaStream_t st) {
   int rc = run_forward(s, st, 1);
   if (rc) return rc;
+  NvtxRange nvtx("lb recompute + adjoint sweep");
   if (use_grid(s)) {
     LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.gslots), 0, s->L.gslots.bytes, st), "clear grid slots");
     LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.bar), 0, s->L.bar.bytes, st), "clear grid barrier");
@@ -1202,6 +1215,7 @@ int lb_optimize(lb_system* s, void* stream, int32_t max_iter, int32_t memory, do
   if (rc) return rc;
   if (memory < 1 || max_iter < 0 || !(gtol >= 0.0) || !(step0 > 0.0) || !std::isfinite(step0))
     return fail(LB_EINVAL, "need memory >= 1, max_iter >= 0, gtol >= 0 and step0 > 0");
+  NvtxRange nvtx("lb_optimize");
   const size_t n = (size_t)s->n_params;
   constexpr double kC1 = 1e-4, kCurv = 1e-10;
   constexpr int kMaxTrials = 30;
@@ -1476,6 +1490,7 @@ int lb_batch_bind_workspace(lb_batch* b, void* ws, size_t bytes, void* stream) {
 
 // device work of one batch call (graph-capturable: no host synchronisation)
 static int batch_enqueue(lb_batch* b, cudaStream_t st, int with_grad) {
+  NvtxRange nvtx(with_grad ? "lb batch gradient" : "lb batch forward");
   for (lb_system* s : b->sys) {
     LB_CUDA(lbk::launch_control_table(s->dp, s->hp, st), "control table kernel");
     s->ctab_dirty = false;

@@ -293,7 +293,7 @@ Layout make_layout(const lb_system* s) {
   take(L.gslots, grid ? sizeof(unsigned long long) * 5 * M : 0);
   take(L.bar, grid ? sizeof(GridBar) : 0);
   take(L.hist, c2 * lbk::kPredOrder * M * V);
-  take(L.hmap, grid ? sizeof(int32_t) * (size_t)s->N * (s->N + 1) / 2 : 0);
+  take(L.hmap, sizeof(int32_t) * (size_t)s->N * (s->N + 1) / 2);
   L.total = off;
   return L;
 }
@@ -316,6 +316,20 @@ int order_after_uploads(lb_system* s, cudaStream_t stream) {
   if (stream == s->bind_stream) return LB_OK;
   LB_CUDA(cudaEventRecord(s->upload_done, s->bind_stream), "cudaEventRecord");
   LB_CUDA(cudaStreamWaitEvent(stream, s->upload_done, 0), "cudaStreamWaitEvent");
+  return LB_OK;
+}
+
+// vec indices k + N l with k <= l, column by column: the element order of
+// the Hermitian sweeps (entries below the diagonal are written as mirrors).
+// The pageable source is staged before cudaMemcpyAsync returns.
+int upload_symmetry_map(lb_system* s, cudaStream_t st) {
+  std::vector<int32_t> hmap;
+  hmap.reserve((size_t)s->N * (s->N + 1) / 2);
+  for (int l = 0; l < s->N; ++l)
+    for (int k = 0; k <= l; ++k) hmap.push_back(k + s->N * l);
+  LB_CUDA(cudaMemcpyAsync(at<int32_t>(s, s->L.hmap), hmap.data(), sizeof(int32_t) * hmap.size(),
+                          cudaMemcpyHostToDevice, st),
+          "upload symmetry map");
   return LB_OK;
 }
 
@@ -384,8 +398,12 @@ bool hermitian_matrices(const double* a, int M, int N) {
   return true;
 }
 
+// the Hermitian symmetry runs in the grid sweeps and in the one-CTA sweeps
+// with a fixed-point solver (not in the cluster sweeps or GMRES)
 bool use_symmetry(const lb_system* s) {
-  return s->symmetry == LB_SYM_HERMITIAN && use_grid(s) && s->rho_herm && (s->target_mode == 2 || s->tar_herm);
+  if (s->symmetry != LB_SYM_HERMITIAN || !s->rho_herm || !(s->target_mode == 2 || s->tar_herm)) return false;
+  if (use_grid(s)) return true;
+  return !s->cluster && s->method != LB_SOLVER_GMRES;
 }
 
 // re-upload the problem block when the symmetry decision changed (bound systems)
@@ -504,8 +522,8 @@ void fill_prob(lb_system* s) {
     P.partials = at<double>(s, s->L.partials);
     P.gslots = at<unsigned long long>(s, s->L.gslots);
     P.bar = at<GridBar>(s, s->L.bar);
-    P.hmap = at<int32_t>(s, s->L.hmap);
   }
+  P.hmap = at<int32_t>(s, s->L.hmap);
   P.herm = use_symmetry(s) ? 1 : 0;
   P.hist = at<double2>(s, s->L.hist);
 }
@@ -678,6 +696,7 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
     s->cluster = c.sweep == LB_SWEEP_CLUSTER;
     if (s->cluster) s->cc = cluster_cfg(s, c.E != 0);
     s->hp.gM = gproj_used(s);
+    s->hp.herm = use_symmetry(s) ? 1 : 0;
     if (c.sweep == LB_SWEEP_RESIDENT) {
       s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, s->jp.empty(), kry_elems(s));
       const int threads = ((s->V + c.E - 1) / c.E + 31) / 32 * 32;
@@ -717,6 +736,7 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
     s->cc = cc0;
     s->method = s->hp.method = m0;
     s->hp.gM = gproj_used(s);
+    s->hp.herm = use_symmetry(s) ? 1 : 0;
     LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
     return fail(LB_ENOTCONV, "no candidate's inner solve converged on the probe steps");
   }
@@ -724,6 +744,7 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
   s->cluster = win.sweep == LB_SWEEP_CLUSTER;
   s->cc = s->cluster ? cluster_cfg(s, win.E != 0) : cc0;
   s->hp.gM = gproj_used(s);
+  s->hp.herm = use_symmetry(s) ? 1 : 0;
   if (win.sweep == LB_SWEEP_RESIDENT) {
     s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, s->jp.empty(), kry_elems(s));
     s->rc.E = win.E;
@@ -1027,17 +1048,8 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
                             cudaMemcpyHostToDevice, st),
             "upload carriers");
   LB_CUDA(lbk::launch_tables(s->dp, s->hp, st), "tables kernel");
-  if (use_grid(s)) {
-    // vec indices k + N l with k <= l, column by column (the grid sweeps' Hermitian loop order)
-    std::vector<int32_t> hmap;
-    hmap.reserve((size_t)s->N * (s->N + 1) / 2);
-    for (int l = 0; l < s->N; ++l)
-      for (int k = 0; k <= l; ++k) hmap.push_back(k + s->N * l);
-    LB_CUDA(cudaMemcpyAsync(at<int32_t>(s, s->L.hmap), hmap.data(), sizeof(int32_t) * hmap.size(),
-                            cudaMemcpyHostToDevice, st),
-            "upload symmetry map");
-    // the pageable source is staged before the call returns
-  }
+  rc = upload_symmetry_map(s, st);
+  if (rc) return rc;
   rc = upload_states(s, s->rho0.data(), st);
   if (rc) return rc;
   rc = upload_targets(s, st);
@@ -1683,7 +1695,9 @@ int static_bind(lb_system* s, void* ws, cudaStream_t st) {
                             cudaMemcpyHostToDevice, st),
             "upload carriers");
   LB_CUDA(lbk::launch_tables(s->dp, s->hp, st), "tables kernel");
-  int rc = upload_states(s, s->rho0.data(), st);
+  int rc = upload_symmetry_map(s, st);
+  if (rc) return rc;
+  rc = upload_states(s, s->rho0.data(), st);
   if (rc) return rc;
   rc = upload_targets(s, st);
   if (rc) return rc;

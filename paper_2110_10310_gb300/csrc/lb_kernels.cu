@@ -113,27 +113,6 @@ __device__ __forceinline__ double bspline2(double x) {
 __device__ __forceinline__ double merit_value(int kind, double sum) {
   return kind == LB_J_FROB ? 0.5 * sum : (kind == LB_J_TR ? 1.0 - sum : sum);
 }
-// this thread's share of the merit sum for state values q[e] against t
-template <int E>
-__device__ __forceinline__ double merit_partial(int kind, const double2 (&q)[E], const double2* __restrict__ tar,
-                                                int V) {
-  double acc = 0.0;
-#pragma unroll
-  for (int e = 0; e < E; ++e) {
-    const int v = threadIdx.x + e * blockDim.x;
-    if (v < V) {
-      const double2 t = tar[v];
-      if (kind == LB_J_FROB) {
-        const double dr = q[e].x - t.x, di = q[e].y - t.y;
-        acc = fma(dr, dr, fma(di, di, acc));
-      } else {
-        acc = fma(t.x, q[e].x, fma(t.y, q[e].y, acc));
-      }
-    }
-  }
-  return acc;
-}
-
 // factor of the target in the terminal condition beta_i/M g_i for the
 // functionals linear in q: g = -t (J_Tr), g = N_m = t (J_Nm)
 __device__ __forceinline__ double linear_sign(int kind) { return kind == LB_J_NM ? 1.0 : -1.0; }
@@ -160,6 +139,7 @@ struct Hdr {
   int db, dm;  // bits per packed digit and their mask
   int npair, cq;  // Jaynes-Cummings pairs, entries per step of the control table
   double gamma1;  // weight of the running penalty (0: none)
+  int herm, Vh;   // Hermitian symmetry: only the Vh = N (N + 1) / 2 elements k <= l are iterated
   int jp[LB_MAXQ * (LB_MAXQ - 1) / 2], jq[LB_MAXQ * (LB_MAXQ - 1) / 2];
   double h, rtol;
   int lev[LB_MAXQ], stride[LB_MAXQ], coff[LB_MAXQ], joff[LB_MAXQ];
@@ -190,6 +170,8 @@ __device__ void load_hdr(Hdr& H, const ProbDev& P) {
   H.npair = P.npair;
   H.cq = P.cq;
   H.gamma1 = P.gamma1;
+  H.herm = P.herm;
+  H.Vh = P.N * (P.N + 1) / 2;
   for (int k = 0; k < P.npair; ++k) {
     H.jp[k] = P.jp[k];
     H.jq[k] = P.jq[k];
@@ -299,6 +281,7 @@ struct ResSmem {
   double* jf;
   double* ja;
   uint32_t* dig;
+  uint16_t* hmap;             // [N (N + 1) / 2] vec indices of the elements k <= l (Hermitian symmetry)
   unsigned long long* slots;  // [3][16]
   double* red;                // [4 * LB_MAXQ][16]
   double2* dsm;               // [V] Dinv (Jacobi) or dt/2 D (Neumann)
@@ -334,6 +317,7 @@ __host__ __device__ inline size_t res_smem_bytes(int ncoef, int njcoef, int N, i
   b += align16(sizeof(double) * 2 * ncoef);
   b += align16(sizeof(double) * 2 * njcoef);
   b += align16(sizeof(uint32_t) * N);
+  b += align16(sizeof(uint16_t) * (size_t)N * (N + 1) / 2);
   b += align16(sizeof(unsigned long long) * 48);
   b += align16(sizeof(double) * 4 * LB_MAXQ * 16);
   b += sizeof(double2) * 3 * (size_t)V;
@@ -354,6 +338,8 @@ __device__ ResSmem carve(unsigned char* base, int ncoef, int njcoef, int N, int 
   o += align16(sizeof(double) * 2 * njcoef);
   S.dig = reinterpret_cast<uint32_t*>(base + o);
   o += align16(sizeof(uint32_t) * N);
+  S.hmap = reinterpret_cast<uint16_t*>(base + o);
+  o += align16(sizeof(uint16_t) * (size_t)N * (N + 1) / 2);
   S.slots = reinterpret_cast<unsigned long long*>(base + o);
   o += align16(sizeof(unsigned long long) * 48);
   S.red = reinterpret_cast<double*>(base + o);
@@ -368,8 +354,14 @@ __device__ ResSmem carve(unsigned char* base, int ncoef, int njcoef, int N, int 
 }
 
 // Load constants and tables of problem P into shared memory (all threads).
-__device__ void res_setup(const ResSmem& S, const ProbDev& P) {
-  if (threadIdx.x == 0) load_hdr(*S.hdr, P);
+// herm_ok = false keeps every element (vectors of lb_propagate may be anything).
+__device__ void res_setup(const ResSmem& S, const ProbDev& P, bool herm_ok = true) {
+  if (threadIdx.x == 0) {
+    load_hdr(*S.hdr, P);
+    if (!herm_ok) S.hdr->herm = 0;
+  }
+  if (herm_ok && P.herm)
+    for (int i = threadIdx.x; i < P.N * (P.N + 1) / 2; i += blockDim.x) S.hmap[i] = (uint16_t)P.hmap[i];
   for (int i = threadIdx.x; i < P.ncoef; i += blockDim.x) {
     S.cu[i] = P.cu[i];
     S.cd[i] = P.cd[i];
@@ -388,19 +380,66 @@ __device__ void res_setup(const ResSmem& S, const ProbDev& P) {
   __syncthreads();
 }
 
+// vec index of this thread's element e: slot threadIdx.x + e blockDim.x of
+// the CTA's element list, which with the Hermitian symmetry is the table of
+// the k <= l elements (slots past it map to V, i.e. no element)
+__device__ __forceinline__ int rel(const ResSmem& S, const Hdr& H, int e) {
+  const int u = threadIdx.x + e * blockDim.x;
+  if (!H.herm) return u;
+  return u < H.Vh ? (int)S.hmap[u] : H.V;
+}
+// the mirror element l + N k of an off-diagonal element k + N l under the
+// Hermitian symmetry (-1 otherwise)
+__device__ __forceinline__ int rmirror(const Hdr& H, int v) {
+  const int k = v % H.N, l = v / H.N;
+  return (H.herm && k != l) ? l + H.N * k : -1;
+}
+// store x at element v of a state array and, under the symmetry, its
+// conjugate at the mirror element
+__device__ __forceinline__ void rput(const Hdr& H, double2* a, int v, double2 x) {
+  a[v] = x;
+  const int vm = rmirror(H, v);
+  if (vm >= 0) a[vm] = make_double2(x.x, -x.y);
+}
+
+// this thread's share of the merit sum for state values q[e] against t (an
+// off-diagonal element under the Hermitian symmetry counts for its mirror too)
+template <int E>
+__device__ double merit_partial(const ResSmem& S, const Hdr& H, const double2 (&q)[E],
+                                const double2* __restrict__ tar) {
+  double acc = 0.0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int v = rel(S, H, e);
+    if (v < H.V) {
+      const double2 t = tar[v];
+      const double wm = rmirror(H, v) >= 0 ? 2.0 : 1.0;
+      double x;
+      if (H.kind == LB_J_FROB) {
+        const double dr = q[e].x - t.x, di = q[e].y - t.y;
+        x = fma(dr, dr, di * di);
+      } else {
+        x = fma(t.x, q[e].x, t.y * q[e].y);
+      }
+      acc = fma(wm, x, acc);
+    }
+  }
+  return acc;
+}
+
 template <int E>
 struct Elems {
   uint32_t kd[E], ld[E];
 };
 
 template <int E>
-__device__ __forceinline__ void init_elems(Elems<E>& el, const ResSmem& S, int V, int N) {
+__device__ __forceinline__ void init_elems(Elems<E>& el, const ResSmem& S, const Hdr& H) {
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int v = threadIdx.x + e * blockDim.x;
-    if (v < V) {
-      el.kd[e] = S.dig[v % N];
-      el.ld[e] = S.dig[v / N];
+    const int v = rel(S, H, e);
+    if (v < H.V) {
+      el.kd[e] = S.dig[v % H.N];
+      el.ld[e] = S.dig[v / H.N];
     } else {
       el.kd[e] = el.ld[e] = 0;
     }
@@ -521,7 +560,7 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
   unsigned qmax = 0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int v = threadIdx.x + e * blockDim.x;
+    const int v = rel(S, H, e);
     if (v < H.V) {
       double2 z0 = rhs[e];
       if (!neumann) {
@@ -530,7 +569,7 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
         const double ur = pc ? rhs[e].x + pc[e].x : rhs[e].x, ui = pc ? rhs[e].y + pc[e].y : rhs[e].y;
         z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
       }
-      S.zb0[v] = z0;
+      rput(H, S.zb0, v, z0);
       if (gmres) S.zb1[v] = rhs[e];
       qmax = max(qmax, max(hi_abs(rhs[e].x), hi_abs(rhs[e].y)));
     }
@@ -554,7 +593,7 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
     unsigned dmax = 0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int v = threadIdx.x + e * blockDim.x;
+      const int v = rel(S, H, e);
       if (v < H.V) {
         double ar = rhs[e].x, ai = rhs[e].y;
         double2 d;
@@ -575,7 +614,7 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
           z.x = ar + fma(d.x, zo.x, -di * zo.y);
           z.y = ai + fma(d.x, zo.y, di * zo.x);
         }
-        zn[v] = z;
+        rput(H, zn, v, z);
         dmax = max(dmax, max(hi_abs(z.x - zo.x), hi_abs(z.y - zo.y)));
       }
     }
@@ -609,12 +648,12 @@ struct Pred {
     hh = 0.5 * P.h;
     n = slot = 0;
   }
-  __device__ void predict(double2 (&pc)[E], int V) const {
+  __device__ void predict(double2 (&pc)[E], const ResSmem& S, const Hdr& H) const {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int v = threadIdx.x + e * blockDim.x;
+      const int v = rel(S, H, e);
       double pr = 0.0, pi = 0.0;
-      if (v < V) {
+      if (v < H.V) {
         int sl = slot;
         for (int i = 1; i <= n; ++i) {
           sl = sl > 0 ? sl - 1 : kPredOrder - 1;
@@ -628,11 +667,11 @@ struct Pred {
     }
   }
   template <bool ADJ>
-  __device__ void record(const double2* zc, const double2 (&rhs)[E], int V) {
+  __device__ void record(const double2* zc, const double2 (&rhs)[E], const ResSmem& S, const Hdr& H) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int v = threadIdx.x + e * blockDim.x;
-      if (v < V) {
+      const int v = rel(S, H, e);
+      if (v < H.V) {
         const double2 z = zc[v], d = __ldg(D + v);
         const double dr = hh * d.x, di = hh * (ADJ ? -d.y : d.y);
         hist[(size_t)slot * stride + v] = make_double2(z.x - fma(dr, z.x, -di * z.y) - rhs[e].x,
@@ -924,14 +963,14 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
   res_setup(S, P);
   const Hdr& H = *S.hdr;
   Elems<E> el;
-  init_elems<E>(el, S, H.V, H.N);
+  init_elems<E>(el, S, H);
   Plan<QT> pl;
-  build_plan<QT>(pl, S, H, el.kd[0], el.ld[0], threadIdx.x);
+  build_plan<QT>(pl, S, H, el.kd[0], el.ld[0], rel(S, H, 0));
   const size_t base = (size_t)i * H.V;
   double2 q[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int v = threadIdx.x + e * blockDim.x;
+    const int v = rel(S, H, e);
     q[e] = v < H.V ? P.q0[base + v] : make_double2(0.0, 0.0);
   }
   CtaStats stats;
@@ -944,17 +983,17 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
   // running penalty sum_j dt beta(t_j) J(q^j) (Sec. III, eq. optimproblem)
   double jpen = 0.0;
   for (int j = 0; j < H.NT; ++j) {
-    if (H.gamma1 != 0.0) jpen = fma(P.pen[j], merit_value(H.kind, cta_sum(S, merit_partial<E>(H.kind, q, P.tar + base, H.V))), jpen);
+    if (H.gamma1 != 0.0) jpen = fma(P.pen[j], merit_value(H.kind, cta_sum(S, merit_partial<E>(S, H, q, P.tar + base))), jpen);
     if (tape && H.K > 0 && j % H.K == 0) {
       double2* ck = P.ckpt + ((size_t)i * H.n_ckpt + j / H.K) * H.V;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int v = threadIdx.x + e * blockDim.x;
+        const int v = rel(S, H, e);
         if (v < H.V) ck[v] = q[e];
       }
     }
     int cur;
-    if (pred) pr.predict(pc, H.V);
+    if (pred) pr.predict(pc, S, H);
     const int it = res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur,
                                                  pred ? pc : nullptr);
     if (it < 0) {
@@ -964,11 +1003,11 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
     }
     stats.add(0, it);
     const double2* zc = cur ? S.zb1 : S.zb0;
-    if (pred) pr.template record<false>(zc, q, H.V);
+    if (pred) pr.template record<false>(zc, q, S, H);
     double2* tp = (tape && H.K == 0) ? P.ckpt + ((size_t)i * H.NT + j) * H.V : nullptr;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int v = threadIdx.x + e * blockDim.x;
+      const int v = rel(S, H, e);
       if (v < H.V) {
         const double2 z = zc[v];
         if (tp) tp[v] = z;
@@ -981,15 +1020,23 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
   double acc = 0.0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int v = threadIdx.x + e * blockDim.x;
+    const int v = rel(S, H, e);
     if (v < H.V) {
-      P.qT[base + v] = q[e];
+      rput(H, P.qT + base, v, q[e]);
       const double2 t = P.tar[base + v];
+      // an off-diagonal element under the symmetry stands for its mirror too
+      const double wm = rmirror(H, v) >= 0 ? 2.0 : 1.0;
       if (H.kind == LB_J_FROB) {
         const double dr = q[e].x - t.x, di = q[e].y - t.y;
-        acc = fma(dr, dr, fma(di, di, acc));
+        if (wm == 1.0)
+          acc = fma(dr, dr, fma(di, di, acc));
+        else
+          acc = fma(wm, fma(dr, dr, di * di), acc);
       } else {
-        acc = fma(t.x, q[e].x, fma(t.y, q[e].y, acc));
+        if (wm == 1.0)
+          acc = fma(t.x, q[e].x, fma(t.y, q[e].y, acc));
+        else
+          acc = fma(wm, fma(t.x, q[e].x, t.y * q[e].y), acc);
       }
     }
   }
@@ -1013,9 +1060,9 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
   res_setup(S, P);
   const Hdr& H = *S.hdr;
   Elems<E> el;
-  init_elems<E>(el, S, H.V, H.N);
+  init_elems<E>(el, S, H);
   Plan<QT> pl;
-  build_plan<QT>(pl, S, H, el.kd[0], el.ld[0], threadIdx.x);
+  build_plan<QT>(pl, S, H, el.kd[0], el.ld[0], rel(S, H, 0));
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const size_t base = (size_t)i * H.V;
   const double w = P.wgt[i];
@@ -1029,7 +1076,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
     for (int v = threadIdx.x; v < H.V; v += blockDim.x) P.qb[base + v] = P.qT[base + v];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int v = threadIdx.x + e * blockDim.x;
+    const int v = rel(S, H, e);
     lam[e] = make_double2(0.0, 0.0);
     qf[e] = lam[e];
     if (v < H.V) {
@@ -1057,7 +1104,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       const double2* ck = P.ckpt + ((size_t)i * H.n_ckpt + sg) * H.V;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int v = threadIdx.x + e * blockDim.x;
+        const int v = rel(S, H, e);
         if (v < H.V) qf[e] = ck[v];
       }
       for (int j = j0; j < j1; ++j) {
@@ -1073,7 +1120,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
         double2* sgv = P.seg + ((size_t)i * H.K + (j - j0)) * H.V;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          const int v = threadIdx.x + e * blockDim.x;
+          const int v = rel(S, H, e);
           if (v < H.V) {
             const double2 z = zc[v];
             sgv[v] = z;
@@ -1086,7 +1133,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       const double2* ct = P.ctab + (size_t)j * H.cq;
       int cur;
       // (I - dt/2 (M^{j+1/2})^+) zhat^j = qhat^{j+1}   (eq. linsystem_adjoint)
-      if (apred) pr.predict(pc, H.V);
+      if (apred) pr.predict(pc, S, H);
       const int it = res_solve<E, QT, true, GM>(S, H, el, pl, lam, ct, stop_factor(P, j), cur, apred ? pc : nullptr);
       if (it < 0) {
         if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
@@ -1095,7 +1142,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       }
       stats.add(2, it);
       const double2* zh = cur ? S.zb1 : S.zb0;
-      if (apred) pr.template record<true>(zh, lam, H.V);
+      if (apred) pr.template record<true>(zh, lam, S, H);
       const double2* Zt = H.K > 0 ? P.seg + ((size_t)i * H.K + (j - j0)) * H.V : P.ckpt + ((size_t)i * H.NT + j) * H.V;
       // gradient pieces (eq. reducedgradient): for every subsystem q,
       //   g_a  = zhat^H vec(-i[a_q, Z])   = -i sum_kl Z_kl conj(R_zhat)
@@ -1104,7 +1151,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       double2 Z[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int v = threadIdx.x + e * blockDim.x;
+        const int v = rel(S, H, e);
         Z[e] = v < H.V ? Zt[v] : make_double2(0.0, 0.0);
       }
       for (int q = 0; q < H.Q; ++q) {
@@ -1112,7 +1159,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
         double sar = 0.0, sai = 0.0, sdr = 0.0, sdi = 0.0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          const int v = threadIdx.x + e * blockDim.x;
+          const int v = rel(S, H, e);
           if (v < H.V) {
             const int nk = (el.kd[e] >> (H.db * q)) & H.dm, nl = (el.ld[e] >> (H.db * q)) & H.dm;
             const double c1 = S.cu[co + nk], c2 = S.cd[co + nl], c3 = S.cd[co + nk], c4 = S.cu[co + nl];
@@ -1125,10 +1172,21 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
             const double rr = fma(-c4, x4.x, c3 * x3.x);
             const double ri = fma(-c4, x4.y, c3 * x3.y);
             // Z conj(R) and Z conj(P)
-            sar = fma(Z[e].x, rr, fma(Z[e].y, ri, sar));
-            sai = fma(Z[e].y, rr, fma(-Z[e].x, ri, sai));
-            sdr = fma(Z[e].x, pr, fma(Z[e].y, pi, sdr));
-            sdi = fma(Z[e].y, pr, fma(-Z[e].x, pi, sdi));
+            if (rmirror(H, v) < 0) {
+              sar = fma(Z[e].x, rr, fma(Z[e].y, ri, sar));
+              sai = fma(Z[e].y, rr, fma(-Z[e].x, ri, sai));
+              sdr = fma(Z[e].x, pr, fma(Z[e].y, pi, sdr));
+              sdi = fma(Z[e].y, pr, fma(-Z[e].x, pi, sdi));
+            } else {
+              // Hermitian Z and zhat: the mirror element (l, k) adds -conj(B) to
+              // the g_a sum and -conj(A) to the g_ad sum, A = Z conj(R), B = Z conj(P)
+              const double ar = fma(Z[e].x, rr, Z[e].y * ri), ai = fma(Z[e].y, rr, -Z[e].x * ri);
+              const double br = fma(Z[e].x, pr, Z[e].y * pi), bi = fma(Z[e].y, pr, -Z[e].x * pi);
+              sar += ar - br;
+              sai += ai + bi;
+              sdr += br - ar;
+              sdi += bi + ai;
+            }
           }
         }
         const double r = warp_sum4(sar, sai, sdr, sdi, lane);
@@ -1152,7 +1210,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       const double ls = linear_sign(H.kind);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int v = threadIdx.x + e * blockDim.x;
+        const int v = rel(S, H, e);
         if (v < H.V) {
           const double2 z = zh[v];
           lam[e] = make_double2(fma(2.0, z.x, -lam[e].x), fma(2.0, z.y, -lam[e].y));
@@ -1184,12 +1242,12 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
   extern __shared__ __align__(16) unsigned char smem[];
   const ProbDev& P = *pp;
   const ResSmem S = carve(smem, P.ncoef, P.njcoef, P.N, P.V);
-  res_setup(S, P);
+  res_setup(S, P, false);
   const Hdr& H = *S.hdr;
   Elems<E> el;
-  init_elems<E>(el, S, H.V, H.N);
+  init_elems<E>(el, S, H);
   Plan<QT> pl;
-  build_plan<QT>(pl, S, H, el.kd[0], el.ld[0], threadIdx.x);
+  build_plan<QT>(pl, S, H, el.kd[0], el.ld[0], rel(S, H, 0));
   double2* xv = x + (size_t)blockIdx.x * H.V;
   double2 q[E];
 #pragma unroll

@@ -731,3 +731,67 @@ def test_running_penalty_with_jnm_and_sweep_rules():
     for sweep in (L.LB_SWEEP_GRID, L.LB_SWEEP_CLUSTER):
         with pytest.raises(L.LBError):
             _sys(p, sweep=sweep)
+
+
+# ----------------------------------------------------------------------------
+# Hermitian symmetry of the one-CTA sweeps
+
+
+@pytest.mark.parametrize("levels,K,objective,solver", [
+    ((2, 3), 0, "frob", "jacobi"),
+    ((3, 3), 7, "trace", "neumann"),
+    ((2, 2, 2), 100, "frob", "jacobi"),
+    ((4, 3), 5, "trace", "jacobi"),
+    ((3, 2, 4), 9, "frob", "jacobi"),
+])
+def test_resident_hermitian_symmetry_matches_oracle(levels, K, objective, solver):
+    """Hermitian states and targets on the one-CTA sweep: the half-element
+    iteration agrees with the full one (1e-12) and with the oracle."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    sv = {"jacobi": L.LB_SOLVER_JACOBI, "neumann": L.LB_SOLVER_NEUMANN}[solver]
+    p = W.random_problem(905, levels=levels, n_states=3, n_steps=40, T_ns=0.8, amp=0.1, ckpt_every=K,
+                         hermitian=True, objective=objective, gamma2=0.05)
+    s_h, g_h = _check_problem(p, sweep=L.LB_SWEEP_RESIDENT, solver=sv)
+    assert s_h.stats()["symmetry"] == "hermitian"
+    G_h = s_h.gradient()[0]
+    s_f = _sys(p, sweep=L.LB_SWEEP_RESIDENT, solver=sv, symmetry=L.LB_SYM_NONE)
+    G_f, g_f = s_f.gradient()
+    assert s_f.stats()["symmetry"] == "none"
+    assert abs(G_h - G_f) <= 1e-12 * abs(G_f)
+    assert _rel(g_h, g_f) < 1e-11
+
+
+def test_resident_hermitian_symmetry_with_gate_targets_penalty_and_coupling():
+    """The three Hermitian gate states, a running penalty and
+    Jaynes-Cummings pairs on the one-CTA sweep, each against the oracle and
+    the full-element iteration."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p1 = W.cnot_three_states(n_steps=200)
+    p1.system.T_ns = 200.0 * 200 / 10000
+    p2 = W.random_problem(906, levels=(2, 3), n_states=2, n_steps=40, T_ns=0.8, amp=0.1, hermitian=True,
+                          gamma2=0.05, ckpt_every=6)
+    p2.gamma1, p2.penalty_a = 0.6, 0.3
+    p3 = W.random_problem(907, levels=(3, 2, 2), n_states=2, n_steps=40, T_ns=0.8, amp=0.1, hermitian=True,
+                          jc=0.05, ckpt_every=7)
+    for p in (p1, p2, p3):
+        s_h, g_h = _check_problem(p, sweep=L.LB_SWEEP_RESIDENT)
+        assert s_h.stats()["symmetry"] == "hermitian"
+        G_h = s_h.gradient()[0]
+        G_f, g_f = _sys(p, sweep=L.LB_SWEEP_RESIDENT, symmetry=L.LB_SYM_NONE).gradient()
+        assert abs(G_h - G_f) <= 1e-12 * abs(G_f)
+        assert _rel(g_h, g_f) < 1e-11
+
+
+def test_resident_hermitian_symmetry_not_taken_for_gmres_or_general_states():
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(908, levels=(2, 3), n_states=2, n_steps=20, T_ns=0.4, amp=0.1, hermitian=True)
+    s = _sys(p, sweep=L.LB_SWEEP_RESIDENT, solver=L.LB_SOLVER_GMRES)
+    s.gradient()
+    assert s.stats()["symmetry"] == "none"
+    q = W.random_problem(909, levels=(2, 3), n_states=2, n_steps=20, T_ns=0.4, amp=0.1, hermitian=False)
+    s = _sys(q, sweep=L.LB_SWEEP_RESIDENT)
+    s.gradient()
+    assert s.stats()["symmetry"] == "none"

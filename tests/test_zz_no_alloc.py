@@ -64,7 +64,7 @@ def _unbound_handle(lib, L, prob, K):
     return h
 
 
-@pytest.mark.parametrize("name", ["cnot", "random"])
+@pytest.mark.parametrize("name", ["cnot", "random", "hermitian"])
 def test_static_scratch_gradient_matches_workspace_gradient(name):
     """Two calls in a row through the static-scratch entry point agree with
     lb_gradient on a caller-allocated workspace (states and objectives to
@@ -79,7 +79,7 @@ def test_static_scratch_gradient_matches_workspace_gradient(name):
         prob = W.config2(n_steps=400)
     else:
         prob = W.random_problem(301, levels=(3, 2), n_states=3, n_steps=60, T_ns=1.2, amp=0.1,
-                                objective="trace", gamma2=0.1, ckpt_every=7)
+                                objective="trace", gamma2=0.1, ckpt_every=7, hermitian=name == "hermitian")
     ref = LindbladSystem(prob, ckpt_every=prob.ckpt_every)
     G_ref, g_ref = ref.gradient()
     h = _unbound_handle(lib, L, prob, prob.ckpt_every)

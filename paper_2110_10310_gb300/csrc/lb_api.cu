@@ -188,12 +188,6 @@ lbk::ClusterConfig cluster_cfg(const lb_system* s, bool cs) {
   return lbk::cluster_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, cs);
 }
 
-// CTAs per state of the cluster sweep if it can apply to this system (0: never)
-int cluster_ctas(const lb_system* s) {
-  const int c0 = cluster_cfg(s, false).C, c1 = cluster_cfg(s, true).C;
-  return std::max(std::max(c0, c1), 0);
-}
-
 // complex values of the GMRES Krylov basis in shared memory (0 for the
 // fixed-point solvers)
 size_t kry_elems(const lb_system* s) {

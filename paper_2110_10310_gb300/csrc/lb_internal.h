@@ -111,7 +111,7 @@ struct WorkItem {
 namespace lbk {
 
 constexpr int kMaxResidentV = 4096;  // states held in one CTA's shared memory
-constexpr int kPredOrder = 6;        // extrapolation order of the first-iterate predictor
+constexpr int kPredOrder = 7;        // extrapolation order of the first-iterate predictor
 
 struct ResidentConfig {
   int threads;  // CTA size (multiple of 32, <= 512)

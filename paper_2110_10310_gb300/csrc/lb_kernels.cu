@@ -91,10 +91,11 @@ __device__ __forceinline__ double warp_sum2(double a, double b, int lane) {
 // c_j = (I - dt/2 D) z^j - rhs^j of a step is extrapolated by the polynomial
 // through the last n recorded ones, c_j ~ sum_{i=1..n} (-1)^(i+1) binom(n, i)
 // c_{j-i}, n <= kPredOrder; the table holds these weights for each n.
-static_assert(kPredOrder == 6, "the weight table below is written for order 6");
+static_assert(kPredOrder == 7, "the weight table below is written for order 7");
 __constant__ double kExtrap[kPredOrder + 1][kPredOrder] = {
-    {0, 0, 0, 0, 0, 0},       {1, 0, 0, 0, 0, 0},        {2, -1, 0, 0, 0, 0},     {3, -3, 1, 0, 0, 0},
-    {4, -6, 4, -1, 0, 0},     {5, -10, 10, -5, 1, 0},    {6, -15, 20, -15, 6, -1}};
+    {0, 0, 0, 0, 0, 0, 0},         {1, 0, 0, 0, 0, 0, 0},          {2, -1, 0, 0, 0, 0, 0},
+    {3, -3, 1, 0, 0, 0, 0},        {4, -6, 4, -1, 0, 0, 0},        {5, -10, 10, -5, 1, 0, 0},
+    {6, -15, 20, -15, 6, -1, 0},   {7, -21, 35, -35, 21, -7, 1}};
 
 // quadratic B-spline of unit knot spacing centred at 0 (Sec. II, eq. rotctrl)
 __device__ __forceinline__ double bspline2(double x) {
@@ -1363,11 +1364,9 @@ struct ClSmem {
   double* jf;
   double* ja;
   uint32_t* dig;
-  double2* zb;               // [2][V] replicated iterate, indexed by iteration parity
-  double2* rr;               // [V] right-hand side replica (forward state, recomputed state, or vectors)
-  double2* ll;               // [V] adjoint state replica (backward sweep)
+  double2* zb;               // [2][V] replicated iterate, indexed by exchange parity
   double2* dv;               // [V] (I - dt/2 D)^-1, or dt/2 D for Neumann
-  double2* hd;               // [V] dt/2 D
+  double2* dm;               // [V] I - dt/2 D
   double2* ch;               // [kPredOrder][V] ring of the previous steps' off-diagonal corrections
   unsigned* dsl;             // [2][32] warp maxima of |z_new - z| received, index cta * 4 + warp
   unsigned* qsl;             // [32] this CTA's warp maxima of |rhs|
@@ -1380,7 +1379,7 @@ __host__ __device__ inline size_t cl_smem_bytes(int ncoef, int njcoef, int N, in
   b += align16(sizeof(double) * 2 * ncoef);
   b += align16(sizeof(double) * 2 * njcoef);
   b += align16(sizeof(uint32_t) * N);
-  b += sizeof(double2) * (6 + kPredOrder) * (size_t)V;
+  b += sizeof(double2) * (4 + kPredOrder) * (size_t)V;
   b += align16(sizeof(unsigned) * 64);
   b += align16(sizeof(unsigned) * 32);
   b += align16(sizeof(unsigned long long) * 2);
@@ -1402,12 +1401,10 @@ __device__ ClSmem cl_carve(unsigned char* base, int ncoef, int njcoef, int N, in
   S.dig = reinterpret_cast<uint32_t*>(base + o);
   o += align16(sizeof(uint32_t) * N);
   S.zb = reinterpret_cast<double2*>(base + o);
-  S.rr = S.zb + 2 * (size_t)V;
-  S.ll = S.rr + V;
-  S.dv = S.ll + V;
-  S.hd = S.dv + V;
-  S.ch = S.hd + V;
-  o += sizeof(double2) * (6 + kPredOrder) * (size_t)V;
+  S.dv = S.zb + 2 * (size_t)V;
+  S.dm = S.dv + V;
+  S.ch = S.dm + V;
+  o += sizeof(double2) * (4 + kPredOrder) * (size_t)V;
   S.dsl = reinterpret_cast<unsigned*>(base + o);
   o += align16(sizeof(unsigned) * 64);
   S.qsl = reinterpret_cast<unsigned*>(base + o);
@@ -1436,7 +1433,7 @@ __device__ void cl_setup(const ClSmem& S, const ProbDev& P, cg::cluster_group& c
   for (int i = threadIdx.x; i < P.V; i += blockDim.x) {
     const double2 D = P.D[i];
     S.dv[i] = neumann ? make_double2(hh * D.x, hh * D.y) : P.Dinv[i];
-    S.hd[i] = make_double2(hh * D.x, hh * D.y);
+    S.dm[i] = make_double2(1.0 - hh * D.x, -(hh * D.y));
   }
   for (int i = threadIdx.x; i < 64; i += blockDim.x) S.dsl[i] = 0u;
   if (threadIdx.x == 0) {
@@ -1459,6 +1456,7 @@ struct ClPlan {
   int oa, ob, ojf, oja;
   double ca, cb, cjf, cja;
   double2 d;    // the element's entry of S.dv
+  double2 dmv;  // the element's entry of S.dm
 };
 
 template <int QT, bool CS>
@@ -1480,6 +1478,7 @@ __device__ ClPlan cl_plan(const ClSmem& S, int C, int crank) {
   pl.oa = pl.ob = pl.ojf = pl.oja = pl.v;
   pl.ca = pl.cb = pl.cjf = pl.cja = 0.0;
   pl.d = pl.ev ? S.dv[v] : make_double2(0.0, 0.0);
+  pl.dmv = pl.ev ? S.dm[v] : make_double2(0.0, 0.0);
   if (pl.ev && u >= 0) {
     const uint32_t kd = S.dig[v % H.N], ld = S.dig[v / H.N];
     const int q = pl.q, n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * H.N;
@@ -1512,95 +1511,199 @@ struct ClCount {
   unsigned ph = 0u;               // bit b: completed phases of mbar[b] (mod 2)
 };
 
-// Solve (I - dt/2 M) z = rhs (ADJ: M^+) for the cluster's state, rhs given by
-// the replica `rr`.  Returns the iteration count, -1 (max_iter), -2 (NaN/Inf)
-// or -3 (a wait gave up).  On success S.zb + (gk & 1) * V holds z in every
-// CTA, and zout the lane's element of it.
 // Predictor of the off-diagonal correction c = (I - dt/2 D) z - rhs of a step:
 // the polynomial extrapolation through the last n recorded corrections,
 // c_j ~ sum_i (-1)^(i+1) binom(n, i) c_{j-i}, n = min(steps recorded,
 // kPredOrder).  hist.slot is where the next correction will be recorded.
 struct ClHist {
-  int n = 0;     // corrections recorded so far (capped at kPredOrder)
-  int slot = 0;  // ring position of the next record
+  bool on = false;  // the sweep uses the predictor
+  int n = 0;        // corrections recorded so far (capped at kPredOrder)
+  int slot = 0;     // ring position of the next record
   __device__ void advance() {
     n = n < kPredOrder ? n + 1 : kPredOrder;
     slot = slot + 1 < kPredOrder ? slot + 1 : 0;
   }
 };
-__device__ __forceinline__ double2 cl_predict(const ClSmem& S, int e, ClHist h, int V) {
-  double pr = 0.0, pi = 0.0;
-  int sl = h.slot;
-  for (int i = 1; i <= h.n; ++i) {
-    sl = sl > 0 ? sl - 1 : kPredOrder - 1;
-    const double w = kExtrap[h.n][i - 1];
-    const double2 c = S.ch[(size_t)sl * V + e];
-    pr = fma(w, c.x, pr);
-    pi = fma(w, c.y, pi);
+__device__ __forceinline__ ClHist cl_hist_on() {
+  ClHist h;
+  h.on = true;
+  return h;
+}
+
+// Cluster addresses an inner iteration uses, fixed for a launch: per buffer
+// parity, this lane's element in CTA pl.r (its first store target) with that
+// CTA's mbarrier, and this warp's maximum slot in CTA `lane` with that CTA's
+// mbarrier.
+struct ClAddr {
+  unsigned zb[2], mb[2], dsl[2], mbl[2];
+};
+__device__ ClAddr cl_addr(const ClSmem& S, const ClPlan& pl, int C, int crank) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int V = S.hdr->V;
+  const unsigned rr0 = pl.r < C ? pl.r : 0, lr = lane < C ? lane : 0;
+  ClAddr A;
+  for (int b = 0; b < 2; ++b) {
+    A.zb[b] = mapa_u32(smem_u32(S.zb + (size_t)b * V + pl.v), rr0);
+    A.mb[b] = mapa_u32(smem_u32(&S.mbar[b]), rr0);
+    A.dsl[b] = mapa_u32(smem_u32(S.dsl + 32 * b + crank * 4 + warp), lr);
+    A.mbl[b] = mapa_u32(smem_u32(&S.mbar[b]), lr);
   }
-  return make_double2(pr, pi);
+  return A;
 }
 
-// After a converged step, record c = (I - dt/2 D) z - rhs for element e of
-// the replica (identical in every CTA) in ring slot h.slot.  Called from the
-// loop that forms the next right-hand side, with the step's z and rhs.
-template <bool ADJ>
-__device__ __forceinline__ void cl_record(const ClSmem& S, int e, double2 z, double2 r, ClHist h, int V) {
-  const double2 d = S.hd[e];
-  const double di = ADJ ? -d.y : d.y;
-  // (I - dt/2 D) z - rhs
-  const double cr = z.x - fma(d.x, z.x, -di * z.y) - r.x;
-  const double ci = z.y - fma(d.x, z.y, di * z.x) - r.y;
-  S.ch[(size_t)h.slot * V + e] = make_double2(cr, ci);
+// the control factors and stop factor of one step, loaded a step ahead
+struct ClStep {
+  double2 c;   // d_q or its Jaynes-Cummings factor for this lane's half
+  double fac;  // stopping-test factor
+};
+__device__ __forceinline__ ClStep cl_step(const ProbDev& P, const ClPlan& pl, int cq, int j) {
+  ClStep st;
+  st.c = P.ctab[(size_t)j * cq + pl.q];
+  st.fac = stop_factor(P, j);
+  return st;
 }
 
+// One exchange.  Lanes with pl.ev && pl.r < C push this lane's element
+// value z into every CTA's next buffer (the element's lanes share the C
+// stores), and one lane per CTA pushes this warp's maximum of m into that
+// CTA's slot; then wait (bounded) for every CTA's pushes.  Returns 0 with
+// the largest slot value in mmax, or -3 if a wait gave up; the vote keeps a
+// timeout, should one ever happen, a decision of the whole CTA.
+template <int L>
+__device__ __forceinline__ int cl_exchange(const ClSmem& S, const ClPlan& pl, const ClAddr& A, double2 z,
+                                           unsigned m, int C, ClCount& cnt, unsigned& mmax) {
+  const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  const int V = S.hdr->V;
+  const unsigned p = (cnt.gk + 1) & 1;
+  const unsigned mb_local = smem_u32(&S.mbar[p]);
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(mb_local, (unsigned)V * 16u + (unsigned)(C * nwarps) * 4u);
+  if (pl.ev && pl.r < C) {
+    st_async_f64x2(A.zb[p], z.x, z.y, A.mb[p]);
+    const unsigned dst = smem_u32(S.zb + (size_t)p * V + pl.v);
+    for (int cc = pl.r + L; cc < C; cc += L) st_async_f64x2(mapa_u32(dst, cc), z.x, z.y, mapa_u32(mb_local, cc));
+  }
+  m = __reduce_max_sync(kFull, m);
+  if (lane < C) st_async_u32(A.dsl[p], m, A.mbl[p]);
+  long long spins = 0;
+  int timed_out = 0;
+  while (!mbar_try_wait(mb_local, (cnt.ph >> p) & 1u)) {
+    if (++spins > kMbarSpinLimit) {
+      timed_out = 1;
+      break;
+    }
+  }
+  if (__syncthreads_or(timed_out)) return -3;
+  cnt.ph ^= 1u << p;
+  ++cnt.gk;
+  unsigned mx = 0;
+  const uint4* d4 = reinterpret_cast<const uint4*>(S.dsl + p * 32);
+  for (int k = 0; k < C; ++k) {
+    const uint4 t = d4[k];
+    mx = max(mx, max(max(t.x, t.y), max(t.z, t.w)));
+  }
+  mmax = mx;
+  return 0;
+}
+
+// Every lane of an element holds the element's complex values; lane r
+// computes component r & 1 (imaginary when odd) of each new one.
+__device__ __forceinline__ double cl_comp(const ClPlan& pl, double2 x) { return (pl.r & 1) ? x.y : x.x; }
+__device__ __forceinline__ double2 cl_join(const ClPlan& pl, double c) {
+  const double o = __shfl_xor_sync(kFull, c, 1);
+  return (pl.r & 1) ? make_double2(o, c) : make_double2(c, o);
+}
+
+// rc + the predicted correction, this lane's component: the terms of the
+// extrapolation (hist h, the step being predicted) are split among the
+// element's lanes of that component and summed over them; term 0 is `c0`
+// when has_c0 (the correction just recorded), else read from the ring.
+template <int L>
+__device__ __forceinline__ double cl_predicted(const ClSmem& S, const ClPlan& pl, double rc, ClHist h, bool has_c0,
+                                               double c0) {
+  constexpr int LH = L / 2;
+  const int hh = pl.r >> 1, odd = pl.r & 1, n = h.n, V = S.hdr->V;
+  const double* ring = reinterpret_cast<const double*>(S.ch);
+  double acc = hh == 0 ? rc : 0.0;
+#pragma unroll
+  for (int k = 0; k < (kPredOrder + LH - 1) / LH; ++k) {
+    const int t = hh + k * LH;
+    if (t < n) {
+      int sl = h.slot - 1 - t;
+      if (sl < 0) sl += kPredOrder;
+      const double c = (t == 0 && has_c0) ? c0 : ring[2 * ((size_t)sl * V + pl.v) + odd];
+      acc = fma(kExtrap[n][t], c, acc);
+    }
+  }
+#pragma unroll
+  for (int o = 2; o < L; o <<= 1) acc += __shfl_xor_sync(kFull, acc, o);
+  return acc;
+}
+
+// Start of a step: the first iterate of this lane's element from its
+// right-hand side (this lane's component rc): rc itself (Neumann), else
+// (I - dt/2 D)^-1 (rhs + predicted correction), no correction before the
+// first recorded step; pushed to every CTA with max |rhs|, which comes back
+// in qmax.  Returns 0 or -3 (a wait gave up).
 template <int QT, bool ADJ, bool CS>
-__device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __restrict__ rr,
-                        const double2* __restrict__ ct, double fac, int C, int crank, ClCount& cnt,
-                        double2& zout, ClHist hist = ClHist()) {
+__device__ int cl_start(const ClSmem& S, const ClPlan& pl, const ClAddr& A, double rc, ClHist h, bool has_c0,
+                        double c0, int C, ClCount& cnt, unsigned& qmax) {
+  constexpr int L = ClLanes<QT, CS>::L;
+  double zc = rc;
+  if (S.hdr->method != LB_SOLVER_NEUMANN) {
+    const double u = h.n > 0 ? cl_predicted<L>(S, pl, rc, h, has_c0, c0) : rc;
+    const double di = ADJ ? -pl.d.y : pl.d.y;
+    // real: d.x ur - di ui, imaginary: d.x ui + di ur
+    zc = fma(pl.d.x, u, ((pl.r & 1) ? di : -di) * __shfl_xor_sync(kFull, u, 1));
+  }
+  const double2 z0 = cl_join(pl, zc);
+  const unsigned m = (pl.ev && pl.r < 2) ? hi_abs(rc) : 0u;
+  return cl_exchange<L>(S, pl, A, z0, m, C, cnt, qmax);
+}
+
+// End of a converged step for this lane's element: records this lane's
+// component of c_j = (I - dt/2 D) z - rhs in ring slot h.slot (predictor on;
+// returned in cc) and returns its component of the next right-hand side
+// 2 z - rhs.
+template <bool ADJ>
+__device__ __forceinline__ double cl_update(const ClSmem& S, const ClPlan& pl, double2 z, double2 rhs, ClHist h,
+                                            double& cc) {
+  const int odd = pl.r & 1;
+  const double zc = odd ? z.y : z.x, zo = odd ? z.x : z.y, rc = odd ? rhs.y : rhs.x;
+  if (h.on) {
+    const double b = ADJ ? -pl.dmv.y : pl.dmv.y;
+    // real: dm.x z.x - b z.y - r.x, imaginary: dm.x z.y + b z.x - r.y
+    cc = fma(pl.dmv.x, zc, fma(odd ? b : -b, zo, -rc));
+    if (pl.ev && pl.r < 2) reinterpret_cast<double*>(S.ch)[2 * ((size_t)h.slot * S.hdr->V + pl.v) + odd] = cc;
+  }
+  return fma(2.0, zc, -rc);
+}
+
+// Inner iterations of (I - dt/2 M) z = rhs (ADJ: M^+) for the cluster's
+// state from the first iterate in buffer (gk & 1); `rhs` is this lane's
+// element of the right-hand side and qmax the high word of max |rhs|.
+// Returns the iteration count, -1 (max_iter), -2 (NaN/Inf) or -3 (a wait
+// gave up).  On success S.zb + (gk & 1) * V holds z in every CTA, and zout
+// the lane's element of it.
+template <int QT, bool ADJ, bool CS>
+__device__ int cl_iterate(const ClSmem& S, const ClPlan& pl, const ClAddr& A, double2 rhs, ClStep st,
+                          unsigned qmax, int C, ClCount& cnt, double2& zout) {
   constexpr int L = ClLanes<QT, CS>::L;
   const Hdr& H = *S.hdr;
   const int V = H.V;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const bool neumann = H.method == LB_SOLVER_NEUMANN;
-  // the step's control factor, loaded first so that its latency overlaps z_0
-  const double2 c = ct[pl.q];
-  // z_0 for all elements of the local replica, and max |rhs|
-  {
-    double2* z0b = S.zb + (size_t)(cnt.gk & 1) * V;
-    unsigned qm = 0;
-    for (int e = threadIdx.x; e < V; e += blockDim.x) {
-      const double2 r = rr[e];
-      double2 z0 = r;
-      if (!neumann) {
-        const double2 d = S.dv[e];
-        const double di = ADJ ? -d.y : d.y;
-        const double2 pc = cl_predict(S, e, hist, V);
-        const double ur = r.x + pc.x, ui = r.y + pc.y;
-        z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
-      }
-      z0b[e] = z0;
-      qm = max(qm, max(hi_abs(r.x), hi_abs(r.y)));
-    }
-    qm = __reduce_max_sync(kFull, qm);
-    if (lane == 0) S.qsl[warp] = qm;
-  }
-  __syncthreads();
-  unsigned qmax = 0;
-  for (int w = 0; w < nwarps; ++w) qmax = max(qmax, S.qsl[w]);
   if (qmax >= kInfHi) return -2;
   const unsigned thr =
-      hi_abs(H.rtol * __longlong_as_double(static_cast<long long>((unsigned long long)qmax << 32)) * fac);
+      hi_abs(H.rtol * __longlong_as_double(static_cast<long long>((unsigned long long)qmax << 32)) * st.fac);
   // this lane's complex factor: -i d P -> (b - i a) P, -i conj(d) R -> (-b - i a) R
+  const double2 c = st.c;
   double Ar = pl.rhalf ? -c.y : c.y, Ai = -c.x;
   if (ADJ) {
     Ar = -Ar;
     Ai = -Ai;
   }
   const double di = ADJ ? -pl.d.y : pl.d.y;
-  const bool odd = pl.r & 1;  // with CS: this lane's component (imaginary)
+  const bool odd = pl.r & 1;  // this lane's component (imaginary)
   const double sdi = odd ? di : -di;
-  const double2 rhs = rr[pl.v];
   const double2 r0 = pl.r == 0 ? rhs : make_double2(0.0, 0.0);
   // CS: this lane's component of U xa + W xb, U = A ca, W = -A cb (real:
   // U.r xa.x - U.i xa.y + W.r xb.x - W.i xb.y; imaginary: U.r xa.y + U.i xa.x
@@ -1610,21 +1713,7 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
   const double init = pl.r < 2 ? (odd ? rhs.y : rhs.x) : 0.0;
   const double cj = ADJ ? pl.cja : pl.cjf;
   const int oj = ADJ ? pl.oja : pl.ojf;
-  const unsigned tx = (unsigned)V * 16u + (unsigned)(C * nwarps) * 4u;
-  // cluster addresses used every iteration, per buffer parity: this lane's
-  // element in CTA pl.r (its first store target) with that CTA's mbarrier,
-  // and this warp's maximum slot in CTA `lane` with that CTA's mbarrier
-  const unsigned rr0 = pl.r < C ? pl.r : 0, lr = lane < C ? lane : 0;
-  const unsigned zb_rem0 = mapa_u32(smem_u32(S.zb + pl.v), rr0);
-  const unsigned zb_rem1 = mapa_u32(smem_u32(S.zb + (size_t)V + pl.v), rr0);
-  const unsigned mb_rem0 = mapa_u32(smem_u32(&S.mbar[0]), rr0), mb_rem1 = mapa_u32(smem_u32(&S.mbar[1]), rr0);
-  const unsigned dsl_rem0 = mapa_u32(smem_u32(S.dsl + crank * 4 + warp), lr);
-  const unsigned dsl_rem1 = mapa_u32(smem_u32(S.dsl + 32 + crank * 4 + warp), lr);
-  const unsigned mb_lane0 = mapa_u32(smem_u32(&S.mbar[0]), lr), mb_lane1 = mapa_u32(smem_u32(&S.mbar[1]), lr);
   for (int it = 0; it < H.max_iter; ++it) {
-    const unsigned p = (cnt.gk + 1) & 1;
-    const unsigned mb_local = smem_u32(&S.mbar[p]);
-    if (threadIdx.x == 0) mbar_arrive_expect_tx(mb_local, tx);
     const double2* __restrict__ zc = S.zb + (size_t)(cnt.gk & 1) * V;
     const double2 xa = zc[pl.oa], xb = zc[pl.ob], x5 = zc[oj], zo = zc[pl.v];
     double k;
@@ -1660,36 +1749,10 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
     } else {
       zm = am + fma(pl.d.x, zom, sdi * __shfl_xor_sync(kFull, zom, 1));
     }
-    const double zp = __shfl_xor_sync(kFull, zm, 1);
-    const double2 z = odd ? make_double2(zp, zm) : make_double2(zm, zp);
-    // push the element into every CTA's next buffer; the element's lanes share the C stores
-    if (pl.ev && pl.r < C) {
-      st_async_f64x2(p ? zb_rem1 : zb_rem0, z.x, z.y, p ? mb_rem1 : mb_rem0);
-      const unsigned dst = smem_u32(S.zb + (size_t)p * V + pl.v);
-      for (int cc = pl.r + L; cc < C; cc += L) st_async_f64x2(mapa_u32(dst, cc), z.x, z.y, mapa_u32(mb_local, cc));
-    }
-    unsigned dm = (pl.ev && pl.r < 2) ? hi_abs(zm - zom) : 0u;
-    dm = __reduce_max_sync(kFull, dm);
-    if (lane < C) st_async_u32(p ? dsl_rem1 : dsl_rem0, dm, p ? mb_lane1 : mb_lane0);
-    // wait for every CTA's pushes of this iteration (bounded); the vote keeps a
-    // timeout, should one ever happen, a decision of the whole CTA
-    long long spins = 0;
-    int timed_out = 0;
-    while (!mbar_try_wait(mb_local, (cnt.ph >> p) & 1u)) {
-      if (++spins > kMbarSpinLimit) {
-        timed_out = 1;
-        break;
-      }
-    }
-    if (__syncthreads_or(timed_out)) return -3;
-    cnt.ph ^= 1u << p;
-    ++cnt.gk;
-    unsigned dmax = 0;
-    const uint4* d4 = reinterpret_cast<const uint4*>(S.dsl + p * 32);
-    for (int k = 0; k < C; ++k) {
-      const uint4 t = d4[k];
-      dmax = max(dmax, max(max(t.x, t.y), max(t.z, t.w)));
-    }
+    const double2 z = cl_join(pl, zm);
+    const unsigned dm = (pl.ev && pl.r < 2) ? hi_abs(zm - zom) : 0u;
+    unsigned dmax;
+    if (cl_exchange<L>(S, pl, A, z, dm, C, cnt, dmax)) return -3;
     if (dmax >= kInfHi) return -2;
     if (dmax < thr) {
       zout = z;
@@ -1700,6 +1763,40 @@ __device__ int cl_solve(const ClSmem& S, const ClPlan& pl, const double2* __rest
 }
 
 __device__ __forceinline__ int cl_code(int it) { return it == -1 ? LB_ENOTCONV : (it == -2 ? LB_ENAN : LB_ECUDA); }
+
+// A step's work in every sweep below: the first iterate was pushed by
+// cl_start (at a sweep's start, or at the end of the previous step), the
+// step's constants were loaded one step ahead, cl_iterate converges, and
+// cl_update ends the step.  Each element's right-hand side lives in the
+// registers of its own lanes; only iterates travel between the CTAs.
+
+// J_i over the cluster: this CTA's own elements (lanes r == 0), summed per
+// CTA in a fixed order and gathered in CTA 0's shared memory; the cluster
+// barrier that follows makes them visible there.
+__device__ void cl_objective_part(const ClSmem& S, const ClPlan& pl, const ProbDev& P, size_t base, double2 q,
+                                  int crank) {
+  const Hdr& H = *S.hdr;
+  double acc = 0.0;
+  if (pl.ev && pl.r == 0) {
+    P.qT[base + pl.v] = q;
+    const double2 t = P.tar[base + pl.v];
+    if (H.kind == LB_J_FROB) {
+      const double dr = q.x - t.x, dq = q.y - t.y;
+      acc = fma(dr, dr, dq * dq);
+    } else {
+      acc = fma(t.x, q.x, t.y * q.y);
+    }
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) S.gred[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += S.gred[w];
+    const unsigned dst = mapa_u32(smem_u32(&S.gred[32 + crank]), 0);
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(dst), "d"(t) : "memory");
+  }
+}
 
 template <int QT, bool CS>
 __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict__ pp, int tape) {
@@ -1712,60 +1809,54 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
   cl_setup(S, P, cl);
   const Hdr& H = *S.hdr;
   const ClPlan pl = cl_plan<QT, CS>(S, C, crank);
+  const ClAddr A = cl_addr(S, pl, C, crank);
   const size_t base = (size_t)i * H.V;
-  for (int e = threadIdx.x; e < H.V; e += blockDim.x) S.rr[e] = P.q0[base + e];
+  const bool own = pl.ev && pl.r == 0;  // the lane that writes the element's tapes
+  double2 rhs = P.q0[base + pl.v];
   ClCount cnt;
   CtaStats stats;
   bool failed = false;
   // the predictor is used only when no step is ever recomputed (K == 0), so
   // recomputed stage vectors stay bit-identical to the forward ones
   const bool pred = H.K == 0 && H.method != LB_SOLVER_NEUMANN;
-  ClHist hist;
-  for (int j = 0; j < H.NT; ++j) {
-    if (tape && H.K > 0 && j % H.K == 0 && crank == 0)
-      for (int e = threadIdx.x; e < H.V; e += blockDim.x) P.ckpt[((size_t)i * H.n_ckpt + j / H.K) * H.V + e] = S.rr[e];
+  ClHist hist = pred ? cl_hist_on() : ClHist();
+  unsigned qmax = 0;
+  if (cl_start<QT, false, CS>(S, pl, A, cl_comp(pl, rhs), hist, false, 0.0, C, cnt, qmax)) {
+    if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, 0);
+    failed = true;
+  }
+  ClStep nx = cl_step(P, pl, H.cq, 0);
+  for (int j = 0; j < H.NT && !failed; ++j) {
+    if (tape && H.K > 0 && j % H.K == 0 && own) P.ckpt[((size_t)i * H.n_ckpt + j / H.K) * H.V + pl.v] = rhs;
+    const ClStep st = nx;
+    if (j + 1 < H.NT) nx = cl_step(P, pl, H.cq, j + 1);
     double2 z;
-    const int it = cl_solve<QT, false, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.cq, stop_factor(P, j), C, crank, cnt, z, pred ? hist : ClHist());
+    const int it = cl_iterate<QT, false, CS>(S, pl, A, rhs, st, qmax, C, cnt, z);
     if (it < 0) {
       if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
       failed = true;
       break;
     }
     if (crank == 0) stats.add(0, it);
-    // q^{j+1} = 2 z - q^j on the whole replica (identical in every CTA)
-    const double2* zf = S.zb + (size_t)(cnt.gk & 1) * H.V;
-    for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
-      const double2 zz = zf[e], qq = S.rr[e];
-      if (pred) cl_record<false>(S, e, zz, qq, hist, H.V);
-      if (tape && H.K == 0 && crank == 0) P.ckpt[((size_t)i * H.NT + j) * H.V + e] = zz;
-      S.rr[e] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
-    }
-    if (pred) hist.advance();
-  }
-  if (!failed && crank == 0) {
-    double acc = 0.0;
-    for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
-      const double2 q = S.rr[e];
-      P.qT[base + e] = q;
-      const double2 t = P.tar[base + e];
-      if (H.kind == LB_J_FROB) {
-        const double dr = q.x - t.x, dq = q.y - t.y;
-        acc = fma(dr, dr, fma(dq, dq, acc));
-      } else {
-        acc = fma(t.x, q.x, fma(t.y, q.y, acc));
-      }
-    }
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) S.gred[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += S.gred[w];
-      P.J[i] = merit_value(H.kind, t);
+    if (tape && H.K == 0 && own) P.ckpt[((size_t)i * H.NT + j) * H.V + pl.v] = z;
+    // q^{j+1} = 2 z - q^j
+    double cc = 0.0;
+    const double rn = cl_update<false>(S, pl, z, rhs, hist, cc);
+    rhs = cl_join(pl, rn);
+    if (hist.on) hist.advance();
+    if (j + 1 < H.NT && cl_start<QT, false, CS>(S, pl, A, rn, hist, true, cc, C, cnt, qmax)) {
+      if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, j + 1);
+      failed = true;
     }
   }
+  if (!failed) cl_objective_part(S, pl, P, base, rhs, crank);
   stats.flush(P.status);
-  cl.sync();  // no CTA leaves while another may still push into it
+  cl.sync();  // the partial sums are in CTA 0; no CTA leaves while another may still push into it
+  if (!failed && crank == 0 && threadIdx.x == 0) {
+    double t = 0.0;
+    for (int c = 0; c < C; ++c) t += S.gred[32 + c];
+    P.J[i] = merit_value(H.kind, t);
+  }
 }
 
 template <int QT, bool CS>
@@ -1780,62 +1871,88 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
   cl_setup(S, P, cl);
   const Hdr& H = *S.hdr;
   const ClPlan pl = cl_plan<QT, CS>(S, C, crank);
+  const ClAddr A = cl_addr(S, pl, C, crank);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const size_t base = (size_t)i * H.V;
   const double w = P.wgt[i];
   const double wt = linear_sign(P.kind) * w;
-  // terminal condition qhat^{N_T} = beta_i/M g_i (Appendix B), replicated
-  for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
-    const double2 t = P.tar[base + e];
+  // terminal condition qhat^{N_T} = beta_i/M g_i (Appendix B), this lane's element
+  double2 ll;
+  {
+    const double2 t = P.tar[base + pl.v];
     if (H.kind == LB_J_FROB) {
-      const double2 qq = P.qT[base + e];
-      S.ll[e] = make_double2(w * (qq.x - t.x), w * (qq.y - t.y));
+      const double2 qq = P.qT[base + pl.v];
+      ll = make_double2(w * (qq.x - t.x), w * (qq.y - t.y));
     } else {
-      S.ll[e] = make_double2(wt * t.x, wt * t.y);
+      ll = make_double2(wt * t.x, wt * t.y);
     }
   }
   ClCount cnt;
   CtaStats stats;
   bool failed = false;
   const int nseg = H.K > 0 ? (H.NT + H.K - 1) / H.K : 1;
-  // the adjoint sweep visits the steps in the same order for every K, so its
-  // predictor history never depends on the checkpoint interval
-  const bool apred = H.method != LB_SOLVER_NEUMANN;
-  ClHist ahist;
+  // the adjoint sweep visits the steps in the same order for every K, and
+  // its first iterates are the same arithmetic whether formed at a segment
+  // start or at the end of the previous step, so its results never depend
+  // on the checkpoint interval
+  ClHist ahist = H.method != LB_SOLVER_NEUMANN ? cl_hist_on() : ClHist();
+  ClHist none;
+  const bool own = pl.ev && pl.r == 0;
   // gradient pieces of this warp go to state slot (i * C + crank) * nwarps + warp of gproj
   double2* gbase = P.gproj + (size_t)((i * C + crank) * nwarps + warp) * H.NT * H.Q * 2;
   for (int sg = nseg - 1; sg >= 0 && !failed; --sg) {
     const int j0 = H.K > 0 ? sg * H.K : 0;
     const int j1 = H.K > 0 ? min(H.NT, j0 + H.K) : H.NT;
     if (H.K > 0) {
-      for (int e = threadIdx.x; e < H.V; e += blockDim.x) S.rr[e] = P.ckpt[((size_t)i * H.n_ckpt + sg) * H.V + e];
+      double2 rr = P.ckpt[((size_t)i * H.n_ckpt + sg) * H.V + pl.v];
+      unsigned qr = 0;
+      if (cl_start<QT, false, CS>(S, pl, A, cl_comp(pl, rr), none, false, 0.0, C, cnt, qr)) {
+        if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, j0);
+        failed = true;
+        break;
+      }
+      ClStep nx = cl_step(P, pl, H.cq, j0);
       for (int j = j0; j < j1; ++j) {
+        const ClStep st = nx;
+        if (j + 1 < j1) nx = cl_step(P, pl, H.cq, j + 1);
         double2 z;
-        const int it = cl_solve<QT, false, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.cq, stop_factor(P, j), C, crank, cnt, z);
+        const int it = cl_iterate<QT, false, CS>(S, pl, A, rr, st, qr, C, cnt, z);
         if (it < 0) {
           if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
           failed = true;
           break;
         }
         if (crank == 0) stats.add(1, it);
-        const double2* zf = S.zb + (size_t)(cnt.gk & 1) * H.V;
-        for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
-          const double2 zz = zf[e], qq = S.rr[e];
-          if (crank == 0) P.seg[((size_t)i * H.K + (j - j0)) * H.V + e] = zz;
-          S.rr[e] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
+        if (own) P.seg[((size_t)i * H.K + (j - j0)) * H.V + pl.v] = z;
+        double cc = 0.0;
+        const double rn = cl_update<false>(S, pl, z, rr, none, cc);
+        rr = cl_join(pl, rn);
+        if (j + 1 < j1 && cl_start<QT, false, CS>(S, pl, A, rn, none, false, 0.0, C, cnt, qr)) {
+          if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, j + 1);
+          failed = true;
+          break;
         }
       }
       if (failed) break;
-      __syncthreads();  // segment tape written by this CTA before it is read back below
+      __syncthreads();  // segment tape written by each element's lane r = 0 before its other lanes read it
     }
+    unsigned qmax = 0;
+    if (cl_start<QT, true, CS>(S, pl, A, cl_comp(pl, ll), ahist, false, 0.0, C, cnt, qmax)) {
+      if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, j1 - 1);
+      failed = true;
+      break;
+    }
+    ClStep nx = cl_step(P, pl, H.cq, j1 - 1);
     for (int j = j1 - 1; j >= j0; --j) {
       // this lane's stage vector element, loaded before the solve so that its latency is hidden
       const bool gl = pl.act;
       const double2 Z = gl ? (H.K > 0 ? P.seg[((size_t)i * H.K + (j - j0)) * H.V + pl.v]
                                       : P.ckpt[((size_t)i * H.NT + j) * H.V + pl.v])
                            : make_double2(0.0, 0.0);
+      const ClStep st = nx;
+      if (j > j0) nx = cl_step(P, pl, H.cq, j - 1);
       double2 zh;
-      const int it = cl_solve<QT, true, CS>(S, pl, S.ll, P.ctab + (size_t)j * H.cq, stop_factor(P, j), C, crank, cnt, zh, apred ? ahist : ClHist());
+      const int it = cl_iterate<QT, true, CS>(S, pl, A, ll, st, qmax, C, cnt, zh);
       if (it < 0) {
         if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
         failed = true;
@@ -1847,6 +1964,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
       // X the half's neighbour combination of zhat; P half -> g_ad, R half -> g_a.
       // Summed over the warp's elements (one component per lane after the
       // first exchange) and stored per warp; k_gproj_reduce adds the slots.
+      // The next exchange writes the other buffer, so these reads need no barrier.
       double sr = 0.0, si = 0.0;
       if (gl) {
         const double2 xa = zb[pl.oa], xb = zb[pl.ob];
@@ -1886,13 +2004,16 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
           g[hi ? 0 : 1] = hi ? k : -k;
         }
       }
-      // qhat^j = 2 zhat - qhat^{j+1} on the whole replica
-      for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
-        const double2 zz = zb[e], ll = S.ll[e];
-        if (apred) cl_record<true>(S, e, zz, ll, ahist, H.V);
-        S.ll[e] = make_double2(fma(2.0, zz.x, -ll.x), fma(2.0, zz.y, -ll.y));
+      // qhat^j = 2 zhat - qhat^{j+1}
+      double cc = 0.0;
+      const double rn = cl_update<true>(S, pl, zh, ll, ahist, cc);
+      ll = cl_join(pl, rn);
+      if (ahist.on) ahist.advance();
+      if (j > j0 && cl_start<QT, true, CS>(S, pl, A, rn, ahist, true, cc, C, cnt, qmax)) {
+        if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, j - 1);
+        failed = true;
+        break;
       }
-      if (apred) ahist.advance();
     }
   }
   stats.flush(P.status);
@@ -1911,30 +2032,51 @@ __global__ void __launch_bounds__(128, 1) k_propagate_cl(const ProbDev* __restri
   cl_setup(S, P, cl);
   const Hdr& H = *S.hdr;
   const ClPlan pl = cl_plan<QT, CS>(S, C, crank);
+  const ClAddr A = cl_addr(S, pl, C, crank);
   double2* xv = x + (size_t)i * H.V;
-  for (int e = threadIdx.x; e < H.V; e += blockDim.x) S.rr[e] = xv[e];
+  double2 rr = xv[pl.v];
   ClCount cnt;
   CtaStats stats;
   bool failed = false;
-  for (int jj = 0; jj < j1 - j0; ++jj) {
+  ClHist none;
+  const int n = j1 - j0;
+  unsigned qmax = 0;
+  if (n > 0) {
+    const int rc = adjoint ? cl_start<QT, true, CS>(S, pl, A, cl_comp(pl, rr), none, false, 0.0, C, cnt, qmax)
+                           : cl_start<QT, false, CS>(S, pl, A, cl_comp(pl, rr), none, false, 0.0, C, cnt, qmax);
+    if (rc) {
+      if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, adjoint ? j1 - 1 : j0);
+      failed = true;
+    }
+  }
+  ClStep nx;
+  if (n > 0) nx = cl_step(P, pl, H.cq, adjoint ? j1 - 1 : j0);
+  for (int jj = 0; jj < n && !failed; ++jj) {
     const int j = adjoint ? j1 - 1 - jj : j0 + jj;
+    const ClStep st = nx;
+    if (jj + 1 < n) nx = cl_step(P, pl, H.cq, adjoint ? j - 1 : j + 1);
     double2 z;
-    const int it = adjoint ? cl_solve<QT, true, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.cq, stop_factor(P, j), C, crank, cnt, z)
-                           : cl_solve<QT, false, CS>(S, pl, S.rr, P.ctab + (size_t)j * H.cq, stop_factor(P, j), C, crank, cnt, z);
+    const int it = adjoint ? cl_iterate<QT, true, CS>(S, pl, A, rr, st, qmax, C, cnt, z)
+                           : cl_iterate<QT, false, CS>(S, pl, A, rr, st, qmax, C, cnt, z);
     if (it < 0) {
       if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
       failed = true;
       break;
     }
     if (crank == 0) stats.add(adjoint ? 2 : 0, it);
-    const double2* zf = S.zb + (size_t)(cnt.gk & 1) * H.V;
-    for (int e = threadIdx.x; e < H.V; e += blockDim.x) {
-      const double2 zz = zf[e], qq = S.rr[e];
-      S.rr[e] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
+    double cc = 0.0;
+    const double rn = adjoint ? cl_update<true>(S, pl, z, rr, none, cc) : cl_update<false>(S, pl, z, rr, none, cc);
+    rr = cl_join(pl, rn);
+    if (jj + 1 < n) {
+      const int rc = adjoint ? cl_start<QT, true, CS>(S, pl, A, rn, none, false, 0.0, C, cnt, qmax)
+                             : cl_start<QT, false, CS>(S, pl, A, rn, none, false, 0.0, C, cnt, qmax);
+      if (rc) {
+        if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, adjoint ? j - 1 : j + 1);
+        failed = true;
+      }
     }
   }
-  if (!failed && crank == 0)
-    for (int e = threadIdx.x; e < H.V; e += blockDim.x) xv[e] = S.rr[e];
+  if (!failed && pl.ev && pl.r == 0) xv[pl.v] = rr;
   stats.flush(P.status);
   cl.sync();
 }

@@ -158,9 +158,9 @@ def test_workspace_size_accounts_for_checkpoints(lib, K):
             nw = -(-(-(-Vl // C)) * lanes // 32)  # warps per CTA
             per = max(per, C * nw)
         gproj = M * per * NT * 2 * 2 * 16 + NT * 2 * 2 * 16
-        # q0, tar, qT and the six-step ring of the first-iterate predictor
-        assert n.value >= tape + gproj + (3 + 6) * state
-        assert n.value <= tape + gproj + (3 + 6) * state + 64 * 1024
+        # q0, tar, qT and the seven-step ring of the first-iterate predictor
+        assert n.value >= tape + gproj + (3 + 7) * state
+        assert n.value <= tape + gproj + (3 + 7) * state + 64 * 1024
     finally:
         lib.lb_system_destroy(h)
 
@@ -181,9 +181,9 @@ def test_grid_sweep_workspace_and_sweep_choice(lib):
         V, M = 81 * 81, 2
         state = 16 * M * V
         # q0, tar, qT, 4 checkpoints, 10-step segment tape, zA, zB, lam, qf,
-        # and the six-step ring of the first-iterate predictor
-        assert n.value >= (3 + 4 + 10 + 4 + 6) * state
-        assert n.value <= (3 + 4 + 10 + 4 + 6) * state + 2 * 1024 * 1024
+        # and the seven-step ring of the first-iterate predictor
+        assert n.value >= (3 + 4 + 10 + 4 + 7) * state
+        assert n.value <= (3 + 4 + 10 + 4 + 7) * state + 2 * 1024 * 1024
     finally:
         lib.lb_system_destroy(h)
 

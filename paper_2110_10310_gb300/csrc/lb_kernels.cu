@@ -1365,11 +1365,12 @@ struct ClSmem {
   double* ja;
   uint32_t* dig;
   double2* zb;               // [2][V] replicated iterate, indexed by exchange parity
+  double2* zs;               // [2][V] next step's first iterate, pushed with each inner iteration, by step parity
   double2* dv;               // [V] (I - dt/2 D)^-1, or dt/2 D for Neumann
   double2* dm;               // [V] I - dt/2 D
   double2* ch;               // [kPredOrder][V] ring of the previous steps' off-diagonal corrections
-  unsigned* dsl;             // [2][32] warp maxima of |z_new - z| received, index cta * 4 + warp
-  unsigned* qsl;             // [32] this CTA's warp maxima of |rhs|
+  unsigned* dsl;             // [2][64] per exchange parity: warp maxima of |z_new - z| (index cta * 4 + warp),
+                             // then of the next step's |rhs| (32 + cta * 4 + warp)
   unsigned long long* mbar;  // [2]
   double* gred;              // [8 units][4 warps][2]
 };
@@ -1379,9 +1380,8 @@ __host__ __device__ inline size_t cl_smem_bytes(int ncoef, int njcoef, int N, in
   b += align16(sizeof(double) * 2 * ncoef);
   b += align16(sizeof(double) * 2 * njcoef);
   b += align16(sizeof(uint32_t) * N);
-  b += sizeof(double2) * (4 + kPredOrder) * (size_t)V;
-  b += align16(sizeof(unsigned) * 64);
-  b += align16(sizeof(unsigned) * 32);
+  b += sizeof(double2) * (6 + kPredOrder) * (size_t)V;
+  b += align16(sizeof(unsigned) * 128);
   b += align16(sizeof(unsigned long long) * 2);
   b += align16(sizeof(double) * 64);
   return b;
@@ -1401,14 +1401,13 @@ __device__ ClSmem cl_carve(unsigned char* base, int ncoef, int njcoef, int N, in
   S.dig = reinterpret_cast<uint32_t*>(base + o);
   o += align16(sizeof(uint32_t) * N);
   S.zb = reinterpret_cast<double2*>(base + o);
-  S.dv = S.zb + 2 * (size_t)V;
+  S.zs = S.zb + 2 * (size_t)V;
+  S.dv = S.zs + 2 * (size_t)V;
   S.dm = S.dv + V;
   S.ch = S.dm + V;
-  o += sizeof(double2) * (4 + kPredOrder) * (size_t)V;
+  o += sizeof(double2) * (6 + kPredOrder) * (size_t)V;
   S.dsl = reinterpret_cast<unsigned*>(base + o);
-  o += align16(sizeof(unsigned) * 64);
-  S.qsl = reinterpret_cast<unsigned*>(base + o);
-  o += align16(sizeof(unsigned) * 32);
+  o += align16(sizeof(unsigned) * 128);
   S.mbar = reinterpret_cast<unsigned long long*>(base + o);
   o += align16(sizeof(unsigned long long) * 2);
   S.gred = reinterpret_cast<double*>(base + o);
@@ -1435,7 +1434,7 @@ __device__ void cl_setup(const ClSmem& S, const ProbDev& P, cg::cluster_group& c
     S.dv[i] = neumann ? make_double2(hh * D.x, hh * D.y) : P.Dinv[i];
     S.dm[i] = make_double2(1.0 - hh * D.x, -(hh * D.y));
   }
-  for (int i = threadIdx.x; i < 64; i += blockDim.x) S.dsl[i] = 0u;
+  for (int i = threadIdx.x; i < 128; i += blockDim.x) S.dsl[i] = 0u;
   if (threadIdx.x == 0) {
     mbar_init(smem_u32(&S.mbar[0]), 1);
     mbar_init(smem_u32(&S.mbar[1]), 1);
@@ -1535,7 +1534,7 @@ __device__ __forceinline__ ClHist cl_hist_on() {
 // CTA's mbarrier, and this warp's maximum slot in CTA `lane` with that CTA's
 // mbarrier.
 struct ClAddr {
-  unsigned zb[2], mb[2], dsl[2], mbl[2];
+  unsigned zb[2], zs[2], mb[2], dsl[2], qsl[2], mbl[2];
 };
 __device__ ClAddr cl_addr(const ClSmem& S, const ClPlan& pl, int C, int crank) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1545,7 +1544,9 @@ __device__ ClAddr cl_addr(const ClSmem& S, const ClPlan& pl, int C, int crank) {
   for (int b = 0; b < 2; ++b) {
     A.zb[b] = mapa_u32(smem_u32(S.zb + (size_t)b * V + pl.v), rr0);
     A.mb[b] = mapa_u32(smem_u32(&S.mbar[b]), rr0);
-    A.dsl[b] = mapa_u32(smem_u32(S.dsl + 32 * b + crank * 4 + warp), lr);
+    A.zs[b] = mapa_u32(smem_u32(S.zs + (size_t)b * V + pl.v), rr0);
+    A.dsl[b] = mapa_u32(smem_u32(S.dsl + 64 * b + crank * 4 + warp), lr);
+    A.qsl[b] = mapa_u32(smem_u32(S.dsl + 64 * b + 32 + crank * 4 + warp), lr);
     A.mbl[b] = mapa_u32(smem_u32(&S.mbar[b]), lr);
   }
   return A;
@@ -1566,24 +1567,40 @@ __device__ __forceinline__ ClStep cl_step(const ProbDev& P, const ClPlan& pl, in
 // One exchange.  Lanes with pl.ev && pl.r < C push this lane's element
 // value z into every CTA's next buffer (the element's lanes share the C
 // stores), and one lane per CTA pushes this warp's maximum of m into that
-// CTA's slot; then wait (bounded) for every CTA's pushes.  Returns 0 with
-// the largest slot value in mmax, or -3 if a wait gave up; the vote keeps a
-// timeout, should one ever happen, a decision of the whole CTA.
+// CTA's slot.  With `spec` the lanes also push zn, the element's first
+// iterate for the next step, into spec buffer sb, and the warp's maximum of
+// mn into the second slot set.  Then wait (bounded) for every CTA's pushes.
+// Returns 0 with the largest slot values in mmax (and mnmax), or -3 if a wait
+// gave up; the vote keeps a timeout, should one ever happen, a decision of
+// the whole CTA.
 template <int L>
 __device__ __forceinline__ int cl_exchange(const ClSmem& S, const ClPlan& pl, const ClAddr& A, double2 z,
-                                           unsigned m, int C, ClCount& cnt, unsigned& mmax) {
+                                           unsigned m, int C, ClCount& cnt, unsigned& mmax, bool spec = false,
+                                           int sb = 0, double2 zn = double2(), unsigned mn = 0u,
+                                           unsigned* mnmax = nullptr) {
   const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   const int V = S.hdr->V;
   const unsigned p = (cnt.gk + 1) & 1;
   const unsigned mb_local = smem_u32(&S.mbar[p]);
-  if (threadIdx.x == 0) mbar_arrive_expect_tx(mb_local, (unsigned)V * 16u + (unsigned)(C * nwarps) * 4u);
+  const unsigned per = (unsigned)V * 16u + (unsigned)(C * nwarps) * 4u;
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(mb_local, spec ? 2u * per : per);
   if (pl.ev && pl.r < C) {
     st_async_f64x2(A.zb[p], z.x, z.y, A.mb[p]);
+    if (spec) st_async_f64x2(A.zs[sb], zn.x, zn.y, A.mb[p]);
     const unsigned dst = smem_u32(S.zb + (size_t)p * V + pl.v);
-    for (int cc = pl.r + L; cc < C; cc += L) st_async_f64x2(mapa_u32(dst, cc), z.x, z.y, mapa_u32(mb_local, cc));
+    const unsigned dsp = smem_u32(S.zs + (size_t)sb * V + pl.v);
+    for (int cc = pl.r + L; cc < C; cc += L) {
+      const unsigned mbr = mapa_u32(mb_local, cc);
+      st_async_f64x2(mapa_u32(dst, cc), z.x, z.y, mbr);
+      if (spec) st_async_f64x2(mapa_u32(dsp, cc), zn.x, zn.y, mbr);
+    }
   }
   m = __reduce_max_sync(kFull, m);
-  if (lane < C) st_async_u32(A.dsl[p], m, A.mbl[p]);
+  if (spec) mn = __reduce_max_sync(kFull, mn);
+  if (lane < C) {
+    st_async_u32(A.dsl[p], m, A.mbl[p]);
+    if (spec) st_async_u32(A.qsl[p], mn, A.mbl[p]);
+  }
   long long spins = 0;
   int timed_out = 0;
   while (!mbar_try_wait(mb_local, (cnt.ph >> p) & 1u)) {
@@ -1595,13 +1612,18 @@ __device__ __forceinline__ int cl_exchange(const ClSmem& S, const ClPlan& pl, co
   if (__syncthreads_or(timed_out)) return -3;
   cnt.ph ^= 1u << p;
   ++cnt.gk;
-  unsigned mx = 0;
-  const uint4* d4 = reinterpret_cast<const uint4*>(S.dsl + p * 32);
+  unsigned mx = 0, nx = 0;
+  const uint4* d4 = reinterpret_cast<const uint4*>(S.dsl + p * 64);
   for (int k = 0; k < C; ++k) {
     const uint4 t = d4[k];
     mx = max(mx, max(max(t.x, t.y), max(t.z, t.w)));
+    if (spec) {
+      const uint4 u = d4[8 + k];
+      nx = max(nx, max(max(u.x, u.y), max(u.z, u.w)));
+    }
   }
   mmax = mx;
+  if (spec) *mnmax = nx;
   return 0;
 }
 
@@ -1644,39 +1666,52 @@ __device__ __forceinline__ double cl_predicted(const ClSmem& S, const ClPlan& pl
 // (I - dt/2 D)^-1 (rhs + predicted correction), no correction before the
 // first recorded step; pushed to every CTA with max |rhs|, which comes back
 // in qmax.  Returns 0 or -3 (a wait gave up).
+template <int L, bool ADJ>
+__device__ __forceinline__ double cl_first_comp(const ClSmem& S, const ClPlan& pl, double rc, ClHist h, bool has_c0,
+                                                double c0) {
+  if (S.hdr->method == LB_SOLVER_NEUMANN) return rc;
+  const double u = h.n > 0 ? cl_predicted<L>(S, pl, rc, h, has_c0, c0) : rc;
+  const double di = ADJ ? -pl.d.y : pl.d.y;
+  // real: d.x ur - di ui, imaginary: d.x ui + di ur
+  return fma(pl.d.x, u, ((pl.r & 1) ? di : -di) * __shfl_xor_sync(kFull, u, 1));
+}
+
 template <int QT, bool ADJ, bool CS>
 __device__ int cl_start(const ClSmem& S, const ClPlan& pl, const ClAddr& A, double rc, ClHist h, bool has_c0,
                         double c0, int C, ClCount& cnt, unsigned& qmax) {
   constexpr int L = ClLanes<QT, CS>::L;
-  double zc = rc;
-  if (S.hdr->method != LB_SOLVER_NEUMANN) {
-    const double u = h.n > 0 ? cl_predicted<L>(S, pl, rc, h, has_c0, c0) : rc;
-    const double di = ADJ ? -pl.d.y : pl.d.y;
-    // real: d.x ur - di ui, imaginary: d.x ui + di ur
-    zc = fma(pl.d.x, u, ((pl.r & 1) ? di : -di) * __shfl_xor_sync(kFull, u, 1));
-  }
-  const double2 z0 = cl_join(pl, zc);
+  const double2 z0 = cl_join(pl, cl_first_comp<L, ADJ>(S, pl, rc, h, has_c0, c0));
   const unsigned m = (pl.ev && pl.r < 2) ? hi_abs(rc) : 0u;
   return cl_exchange<L>(S, pl, A, z0, m, C, cnt, qmax);
 }
 
-// End of a converged step for this lane's element: records this lane's
-// component of c_j = (I - dt/2 D) z - rhs in ring slot h.slot (predictor on;
-// returned in cc) and returns its component of the next right-hand side
-// 2 z - rhs.
+// End of a step for this lane's element, given its z: this lane's
+// component of c_j = (I - dt/2 D) z - rhs (predictor on; returned in cc) and
+// of the next right-hand side 2 z - rhs (returned).  cl_commit records cc in
+// ring slot h.slot once the step has converged.
 template <bool ADJ>
-__device__ __forceinline__ double cl_update(const ClSmem& S, const ClPlan& pl, double2 z, double2 rhs, ClHist h,
-                                            double& cc) {
+__device__ __forceinline__ double cl_update(const ClPlan& pl, double2 z, double2 rhs, ClHist h, double& cc) {
   const int odd = pl.r & 1;
   const double zc = odd ? z.y : z.x, zo = odd ? z.x : z.y, rc = odd ? rhs.y : rhs.x;
   if (h.on) {
     const double b = ADJ ? -pl.dmv.y : pl.dmv.y;
     // real: dm.x z.x - b z.y - r.x, imaginary: dm.x z.y + b z.x - r.y
     cc = fma(pl.dmv.x, zc, fma(odd ? b : -b, zo, -rc));
-    if (pl.ev && pl.r < 2) reinterpret_cast<double*>(S.ch)[2 * ((size_t)h.slot * S.hdr->V + pl.v) + odd] = cc;
   }
   return fma(2.0, zc, -rc);
 }
+__device__ __forceinline__ void cl_commit(const ClSmem& S, const ClPlan& pl, ClHist h, double cc) {
+  if (h.on && pl.ev && pl.r < 2)
+    reinterpret_cast<double*>(S.ch)[2 * ((size_t)h.slot * S.hdr->V + pl.v) + (pl.r & 1)] = cc;
+}
+
+// What a converged inner solve hands to the next step when it pushed the
+// next step's first iterate speculatively: this lane's components of c_j
+// and of the next right-hand side, and max |next rhs| over the cluster.
+struct ClNext {
+  double cc = 0.0, rn = 0.0;
+  unsigned qmax = 0u;
+};
 
 // Inner iterations of (I - dt/2 M) z = rhs (ADJ: M^+) for the cluster's
 // state from the first iterate in buffer (gk & 1); `rhs` is this lane's
@@ -1684,9 +1719,17 @@ __device__ __forceinline__ double cl_update(const ClSmem& S, const ClPlan& pl, d
 // Returns the iteration count, -1 (max_iter), -2 (NaN/Inf) or -3 (a wait
 // gave up).  On success S.zb + (gk & 1) * V holds z in every CTA, and zout
 // the lane's element of it.
+//
+// The first iteration reads the first iterate from z0 (the buffer cl_start
+// or the previous step's speculative push filled).  With `spec` (a next step
+// follows) every iteration also pushes the first iterate of the next step
+// computed from its own z as if it were the converged one (hist hn: the
+// predictor state of the next step), into spec buffer sb, so a step that
+// converges needs no further exchange; nx returns what the next step needs.
 template <int QT, bool ADJ, bool CS>
-__device__ int cl_iterate(const ClSmem& S, const ClPlan& pl, const ClAddr& A, double2 rhs, ClStep st,
-                          unsigned qmax, int C, ClCount& cnt, double2& zout) {
+__device__ int cl_iterate(const ClSmem& S, const ClPlan& pl, const ClAddr& A, const double2* z0, double2 rhs,
+                          ClStep st, unsigned qmax, int C, ClCount& cnt, double2& zout, bool spec = false,
+                          ClHist hn = ClHist(), int sb = 0, ClNext* nx = nullptr) {
   constexpr int L = ClLanes<QT, CS>::L;
   const Hdr& H = *S.hdr;
   const int V = H.V;
@@ -1714,7 +1757,7 @@ __device__ int cl_iterate(const ClSmem& S, const ClPlan& pl, const ClAddr& A, do
   const double cj = ADJ ? pl.cja : pl.cjf;
   const int oj = ADJ ? pl.oja : pl.ojf;
   for (int it = 0; it < H.max_iter; ++it) {
-    const double2* __restrict__ zc = S.zb + (size_t)(cnt.gk & 1) * V;
+    const double2* __restrict__ zc = it == 0 ? z0 : S.zb + (size_t)(cnt.gk & 1) * V;
     const double2 xa = zc[pl.oa], xb = zc[pl.ob], x5 = zc[oj], zo = zc[pl.v];
     double k;
     if constexpr (CS) {
@@ -1752,7 +1795,19 @@ __device__ int cl_iterate(const ClSmem& S, const ClPlan& pl, const ClAddr& A, do
     const double2 z = cl_join(pl, zm);
     const unsigned dm = (pl.ev && pl.r < 2) ? hi_abs(zm - zom) : 0u;
     unsigned dmax;
-    if (cl_exchange<L>(S, pl, A, z, dm, C, cnt, dmax)) return -3;
+    if (spec) {
+      double cc = 0.0;
+      const double rn = cl_update<ADJ>(pl, z, rhs, hn, cc);
+      const double2 zn = cl_join(pl, cl_first_comp<L, ADJ>(S, pl, rn, hn, true, cc));
+      const unsigned qn = (pl.ev && pl.r < 2) ? hi_abs(rn) : 0u;
+      unsigned qnmax = 0u;
+      if (cl_exchange<L>(S, pl, A, z, dm, C, cnt, dmax, true, sb, zn, qn, &qnmax)) return -3;
+      nx->cc = cc;
+      nx->rn = rn;
+      nx->qmax = qnmax;
+    } else if (cl_exchange<L>(S, pl, A, z, dm, C, cnt, dmax)) {
+      return -3;
+    }
     if (dmax >= kInfHi) return -2;
     if (dmax < thr) {
       zout = z;
@@ -1764,11 +1819,13 @@ __device__ int cl_iterate(const ClSmem& S, const ClPlan& pl, const ClAddr& A, do
 
 __device__ __forceinline__ int cl_code(int it) { return it == -1 ? LB_ENOTCONV : (it == -2 ? LB_ENAN : LB_ECUDA); }
 
-// A step's work in every sweep below: the first iterate was pushed by
-// cl_start (at a sweep's start, or at the end of the previous step), the
-// step's constants were loaded one step ahead, cl_iterate converges, and
-// cl_update ends the step.  Each element's right-hand side lives in the
-// registers of its own lanes; only iterates travel between the CTAs.
+// A step's work in every sweep below: the first iterate is in every CTA
+// (pushed by cl_start at a sweep's or segment's start, else by the previous
+// step's inner iterations along with their iterates), the step's constants
+// were loaded one step ahead, and cl_iterate converges; a step that
+// converges in one inner iteration costs one exchange.  Each element's
+// right-hand side lives in the registers of its own lanes; only iterates
+// travel between the CTAs.
 
 // J_i over the cluster: this CTA's own elements (lanes r == 0), summed per
 // CTA in a fixed order and gathered in CTA 0's shared memory; the cluster
@@ -1825,13 +1882,18 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
     if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, 0);
     failed = true;
   }
+  const double2* z0 = S.zb + (size_t)(cnt.gk & 1) * H.V;
   ClStep nx = cl_step(P, pl, H.cq, 0);
   for (int j = 0; j < H.NT && !failed; ++j) {
     if (tape && H.K > 0 && j % H.K == 0 && own) P.ckpt[((size_t)i * H.n_ckpt + j / H.K) * H.V + pl.v] = rhs;
     const ClStep st = nx;
     if (j + 1 < H.NT) nx = cl_step(P, pl, H.cq, j + 1);
+    ClHist hn = hist;
+    if (hist.on) hn.advance();
+    const bool spec = j + 1 < H.NT;
+    ClNext nxt;
     double2 z;
-    const int it = cl_iterate<QT, false, CS>(S, pl, A, rhs, st, qmax, C, cnt, z);
+    const int it = cl_iterate<QT, false, CS>(S, pl, A, z0, rhs, st, qmax, C, cnt, z, spec, hn, (j + 1) & 1, &nxt);
     if (it < 0) {
       if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
       failed = true;
@@ -1839,15 +1901,17 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
     }
     if (crank == 0) stats.add(0, it);
     if (tape && H.K == 0 && own) P.ckpt[((size_t)i * H.NT + j) * H.V + pl.v] = z;
-    // q^{j+1} = 2 z - q^j
-    double cc = 0.0;
-    const double rn = cl_update<false>(S, pl, z, rhs, hist, cc);
-    rhs = cl_join(pl, rn);
-    if (hist.on) hist.advance();
-    if (j + 1 < H.NT && cl_start<QT, false, CS>(S, pl, A, rn, hist, true, cc, C, cnt, qmax)) {
-      if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, j + 1);
-      failed = true;
+    // q^{j+1} = 2 z - q^j; the next step's first iterate is already in every CTA
+    if (spec) {
+      cl_commit(S, pl, hist, nxt.cc);
+      rhs = cl_join(pl, nxt.rn);
+      qmax = nxt.qmax;
+      z0 = S.zs + (size_t)((j + 1) & 1) * H.V;
+    } else {
+      double cc = 0.0;
+      rhs = cl_join(pl, cl_update<false>(pl, z, rhs, hist, cc));
     }
+    hist = hn;
   }
   if (!failed) cl_objective_part(S, pl, P, base, rhs, crank);
   stats.flush(P.status);
@@ -1911,12 +1975,15 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
         failed = true;
         break;
       }
+      const double2* z0r = S.zb + (size_t)(cnt.gk & 1) * H.V;
       ClStep nx = cl_step(P, pl, H.cq, j0);
       for (int j = j0; j < j1; ++j) {
         const ClStep st = nx;
         if (j + 1 < j1) nx = cl_step(P, pl, H.cq, j + 1);
+        const bool spec = j + 1 < j1;
+        ClNext nxt;
         double2 z;
-        const int it = cl_iterate<QT, false, CS>(S, pl, A, rr, st, qr, C, cnt, z);
+        const int it = cl_iterate<QT, false, CS>(S, pl, A, z0r, rr, st, qr, C, cnt, z, spec, none, (j + 1) & 1, &nxt);
         if (it < 0) {
           if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
           failed = true;
@@ -1924,13 +1991,10 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
         }
         if (crank == 0) stats.add(1, it);
         if (own) P.seg[((size_t)i * H.K + (j - j0)) * H.V + pl.v] = z;
-        double cc = 0.0;
-        const double rn = cl_update<false>(S, pl, z, rr, none, cc);
-        rr = cl_join(pl, rn);
-        if (j + 1 < j1 && cl_start<QT, false, CS>(S, pl, A, rn, none, false, 0.0, C, cnt, qr)) {
-          if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, j + 1);
-          failed = true;
-          break;
+        if (spec) {
+          rr = cl_join(pl, nxt.rn);
+          qr = nxt.qmax;
+          z0r = S.zs + (size_t)((j + 1) & 1) * H.V;
         }
       }
       if (failed) break;
@@ -1942,6 +2006,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
       failed = true;
       break;
     }
+    const double2* z0 = S.zb + (size_t)(cnt.gk & 1) * H.V;
     ClStep nx = cl_step(P, pl, H.cq, j1 - 1);
     for (int j = j1 - 1; j >= j0; --j) {
       // this lane's stage vector element, loaded before the solve so that its latency is hidden
@@ -1951,8 +2016,12 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
                            : make_double2(0.0, 0.0);
       const ClStep st = nx;
       if (j > j0) nx = cl_step(P, pl, H.cq, j - 1);
+      ClHist hn = ahist;
+      if (ahist.on) hn.advance();
+      const bool spec = j > j0;
+      ClNext nxt;
       double2 zh;
-      const int it = cl_iterate<QT, true, CS>(S, pl, A, ll, st, qmax, C, cnt, zh);
+      const int it = cl_iterate<QT, true, CS>(S, pl, A, z0, ll, st, qmax, C, cnt, zh, spec, hn, (j - 1) & 1, &nxt);
       if (it < 0) {
         if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
         failed = true;
@@ -1964,7 +2033,8 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
       // X the half's neighbour combination of zhat; P half -> g_ad, R half -> g_a.
       // Summed over the warp's elements (one component per lane after the
       // first exchange) and stored per warp; k_gproj_reduce adds the slots.
-      // The next exchange writes the other buffer, so these reads need no barrier.
+      // Later exchanges write the other buffer or the spec buffers first, so
+      // these reads need no barrier.
       double sr = 0.0, si = 0.0;
       if (gl) {
         const double2 xa = zb[pl.oa], xb = zb[pl.ob];
@@ -2004,16 +2074,20 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
           g[hi ? 0 : 1] = hi ? k : -k;
         }
       }
-      // qhat^j = 2 zhat - qhat^{j+1}
-      double cc = 0.0;
-      const double rn = cl_update<true>(S, pl, zh, ll, ahist, cc);
-      ll = cl_join(pl, rn);
-      if (ahist.on) ahist.advance();
-      if (j > j0 && cl_start<QT, true, CS>(S, pl, A, rn, ahist, true, cc, C, cnt, qmax)) {
-        if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, j - 1);
-        failed = true;
-        break;
+      // qhat^j = 2 zhat - qhat^{j+1}; within a segment the next step's first
+      // iterate is already in every CTA
+      if (spec) {
+        cl_commit(S, pl, ahist, nxt.cc);
+        ll = cl_join(pl, nxt.rn);
+        qmax = nxt.qmax;
+        z0 = S.zs + (size_t)((j - 1) & 1) * H.V;
+      } else {
+        double cc = 0.0;
+        const double rn = cl_update<true>(pl, zh, ll, ahist, cc);
+        cl_commit(S, pl, ahist, cc);
+        ll = cl_join(pl, rn);
       }
+      ahist = hn;
     }
   }
   stats.flush(P.status);
@@ -2049,31 +2123,32 @@ __global__ void __launch_bounds__(128, 1) k_propagate_cl(const ProbDev* __restri
       failed = true;
     }
   }
+  const double2* z0 = S.zb + (size_t)(cnt.gk & 1) * H.V;
   ClStep nx;
   if (n > 0) nx = cl_step(P, pl, H.cq, adjoint ? j1 - 1 : j0);
   for (int jj = 0; jj < n && !failed; ++jj) {
     const int j = adjoint ? j1 - 1 - jj : j0 + jj;
     const ClStep st = nx;
     if (jj + 1 < n) nx = cl_step(P, pl, H.cq, adjoint ? j - 1 : j + 1);
+    const bool spec = jj + 1 < n;
+    ClNext nxt;
     double2 z;
-    const int it = adjoint ? cl_iterate<QT, true, CS>(S, pl, A, rr, st, qmax, C, cnt, z)
-                           : cl_iterate<QT, false, CS>(S, pl, A, rr, st, qmax, C, cnt, z);
+    const int it =
+        adjoint ? cl_iterate<QT, true, CS>(S, pl, A, z0, rr, st, qmax, C, cnt, z, spec, none, (jj + 1) & 1, &nxt)
+                : cl_iterate<QT, false, CS>(S, pl, A, z0, rr, st, qmax, C, cnt, z, spec, none, (jj + 1) & 1, &nxt);
     if (it < 0) {
       if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
       failed = true;
       break;
     }
     if (crank == 0) stats.add(adjoint ? 2 : 0, it);
-    double cc = 0.0;
-    const double rn = adjoint ? cl_update<true>(S, pl, z, rr, none, cc) : cl_update<false>(S, pl, z, rr, none, cc);
-    rr = cl_join(pl, rn);
-    if (jj + 1 < n) {
-      const int rc = adjoint ? cl_start<QT, true, CS>(S, pl, A, rn, none, false, 0.0, C, cnt, qmax)
-                             : cl_start<QT, false, CS>(S, pl, A, rn, none, false, 0.0, C, cnt, qmax);
-      if (rc) {
-        if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, adjoint ? j - 1 : j + 1);
-        failed = true;
-      }
+    if (spec) {
+      rr = cl_join(pl, nxt.rn);
+      qmax = nxt.qmax;
+      z0 = S.zs + (size_t)((jj + 1) & 1) * H.V;
+    } else {
+      double cc = 0.0;
+      rr = cl_join(pl, adjoint ? cl_update<true>(pl, z, rr, none, cc) : cl_update<false>(pl, z, rr, none, cc));
     }
   }
   if (!failed && pl.ev && pl.r == 0) xv[pl.v] = rr;

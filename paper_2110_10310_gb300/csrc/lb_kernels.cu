@@ -1456,6 +1456,11 @@ struct ClPlan {
   double ca, cb, cjf, cja;
   double2 d;    // the element's entry of S.dv
   double2 dmv;  // the element's entry of S.dm
+  // problem constants the inner loops use, kept in registers (shared memory
+  // values are reloaded after every asm statement that clobbers memory)
+  int V, maxit;
+  bool neu;     // Neumann iteration
+  double rtol;
 };
 
 template <int QT, bool CS>
@@ -1478,6 +1483,10 @@ __device__ ClPlan cl_plan(const ClSmem& S, int C, int crank) {
   pl.ca = pl.cb = pl.cjf = pl.cja = 0.0;
   pl.d = pl.ev ? S.dv[v] : make_double2(0.0, 0.0);
   pl.dmv = pl.ev ? S.dm[v] : make_double2(0.0, 0.0);
+  pl.V = H.V;
+  pl.maxit = H.max_iter;
+  pl.neu = H.method == LB_SOLVER_NEUMANN;
+  pl.rtol = H.rtol;
   if (pl.ev && u >= 0) {
     const uint32_t kd = S.dig[v % H.N], ld = S.dig[v / H.N];
     const int q = pl.q, n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * H.N;
@@ -1579,7 +1588,7 @@ __device__ __forceinline__ int cl_exchange(const ClSmem& S, const ClPlan& pl, co
                                            int sb = 0, double2 zn = double2(), unsigned mn = 0u,
                                            unsigned* mnmax = nullptr) {
   const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  const int V = S.hdr->V;
+  const int V = pl.V;
   const unsigned p = (cnt.gk + 1) & 1;
   const unsigned mb_local = smem_u32(&S.mbar[p]);
   const unsigned per = (unsigned)V * 16u + (unsigned)(C * nwarps) * 4u;
@@ -1612,18 +1621,11 @@ __device__ __forceinline__ int cl_exchange(const ClSmem& S, const ClPlan& pl, co
   if (__syncthreads_or(timed_out)) return -3;
   cnt.ph ^= 1u << p;
   ++cnt.gk;
-  unsigned mx = 0, nx = 0;
-  const uint4* d4 = reinterpret_cast<const uint4*>(S.dsl + p * 64);
-  for (int k = 0; k < C; ++k) {
-    const uint4 t = d4[k];
-    mx = max(mx, max(max(t.x, t.y), max(t.z, t.w)));
-    if (spec) {
-      const uint4 u = d4[8 + k];
-      nx = max(nx, max(max(u.x, u.y), max(u.z, u.w)));
-    }
-  }
-  mmax = mx;
-  if (spec) *mnmax = nx;
+  // slot cta * 4 + warp of each set: one per lane, reduced across the warp
+  const unsigned* d = S.dsl + p * 64;
+  const bool has = lane < 4 * C;
+  mmax = __reduce_max_sync(kFull, has ? d[lane] : 0u);
+  if (spec) *mnmax = __reduce_max_sync(kFull, has ? d[32 + lane] : 0u);
   return 0;
 }
 
@@ -1643,7 +1645,7 @@ template <int L>
 __device__ __forceinline__ double cl_predicted(const ClSmem& S, const ClPlan& pl, double rc, ClHist h, bool has_c0,
                                                double c0) {
   constexpr int LH = L / 2;
-  const int hh = pl.r >> 1, odd = pl.r & 1, n = h.n, V = S.hdr->V;
+  const int hh = pl.r >> 1, odd = pl.r & 1, n = h.n, V = pl.V;
   const double* ring = reinterpret_cast<const double*>(S.ch);
   double acc = hh == 0 ? rc : 0.0;
 #pragma unroll
@@ -1669,7 +1671,7 @@ __device__ __forceinline__ double cl_predicted(const ClSmem& S, const ClPlan& pl
 template <int L, bool ADJ>
 __device__ __forceinline__ double cl_first_comp(const ClSmem& S, const ClPlan& pl, double rc, ClHist h, bool has_c0,
                                                 double c0) {
-  if (S.hdr->method == LB_SOLVER_NEUMANN) return rc;
+  if (pl.neu) return rc;
   const double u = h.n > 0 ? cl_predicted<L>(S, pl, rc, h, has_c0, c0) : rc;
   const double di = ADJ ? -pl.d.y : pl.d.y;
   // real: d.x ur - di ui, imaginary: d.x ui + di ur
@@ -1702,7 +1704,7 @@ __device__ __forceinline__ double cl_update(const ClPlan& pl, double2 z, double2
 }
 __device__ __forceinline__ void cl_commit(const ClSmem& S, const ClPlan& pl, ClHist h, double cc) {
   if (h.on && pl.ev && pl.r < 2)
-    reinterpret_cast<double*>(S.ch)[2 * ((size_t)h.slot * S.hdr->V + pl.v) + (pl.r & 1)] = cc;
+    reinterpret_cast<double*>(S.ch)[2 * ((size_t)h.slot * pl.V + pl.v) + (pl.r & 1)] = cc;
 }
 
 // What a converged inner solve hands to the next step when it pushed the
@@ -1731,12 +1733,11 @@ __device__ int cl_iterate(const ClSmem& S, const ClPlan& pl, const ClAddr& A, co
                           ClStep st, unsigned qmax, int C, ClCount& cnt, double2& zout, bool spec = false,
                           ClHist hn = ClHist(), int sb = 0, ClNext* nx = nullptr) {
   constexpr int L = ClLanes<QT, CS>::L;
-  const Hdr& H = *S.hdr;
-  const int V = H.V;
-  const bool neumann = H.method == LB_SOLVER_NEUMANN;
+  const int V = pl.V;
+  const bool neumann = pl.neu;
   if (qmax >= kInfHi) return -2;
   const unsigned thr =
-      hi_abs(H.rtol * __longlong_as_double(static_cast<long long>((unsigned long long)qmax << 32)) * st.fac);
+      hi_abs(pl.rtol * __longlong_as_double(static_cast<long long>((unsigned long long)qmax << 32)) * st.fac);
   // this lane's complex factor: -i d P -> (b - i a) P, -i conj(d) R -> (-b - i a) R
   const double2 c = st.c;
   double Ar = pl.rhalf ? -c.y : c.y, Ai = -c.x;
@@ -1756,7 +1757,7 @@ __device__ int cl_iterate(const ClSmem& S, const ClPlan& pl, const ClAddr& A, co
   const double init = pl.r < 2 ? (odd ? rhs.y : rhs.x) : 0.0;
   const double cj = ADJ ? pl.cja : pl.cjf;
   const int oj = ADJ ? pl.oja : pl.ojf;
-  for (int it = 0; it < H.max_iter; ++it) {
+  for (int it = 0; it < pl.maxit; ++it) {
     const double2* __restrict__ zc = it == 0 ? z0 : S.zb + (size_t)(cnt.gk & 1) * V;
     const double2 xa = zc[pl.oa], xb = zc[pl.ob], x5 = zc[oj], zo = zc[pl.v];
     double k;

@@ -283,6 +283,7 @@ struct ResSmem {
   double* ja;
   uint32_t* dig;
   uint16_t* hmap;             // [N (N + 1) / 2] vec indices of the elements k <= l (Hermitian symmetry)
+  uint16_t* hmir;             // [N (N + 1) / 2] their mirror elements l + N k (0xffff on the diagonal)
   unsigned long long* slots;  // [3][16]
   double* red;                // [4 * LB_MAXQ][16]
   double2* dsm;               // [V] Dinv (Jacobi) or dt/2 D (Neumann)
@@ -318,7 +319,7 @@ __host__ __device__ inline size_t res_smem_bytes(int ncoef, int njcoef, int N, i
   b += align16(sizeof(double) * 2 * ncoef);
   b += align16(sizeof(double) * 2 * njcoef);
   b += align16(sizeof(uint32_t) * N);
-  b += align16(sizeof(uint16_t) * (size_t)N * (N + 1) / 2);
+  b += 2 * align16(sizeof(uint16_t) * (size_t)N * (N + 1) / 2);
   b += align16(sizeof(unsigned long long) * 48);
   b += align16(sizeof(double) * 4 * LB_MAXQ * 16);
   b += sizeof(double2) * 3 * (size_t)V;
@@ -341,6 +342,8 @@ __device__ ResSmem carve(unsigned char* base, int ncoef, int njcoef, int N, int 
   o += align16(sizeof(uint32_t) * N);
   S.hmap = reinterpret_cast<uint16_t*>(base + o);
   o += align16(sizeof(uint16_t) * (size_t)N * (N + 1) / 2);
+  S.hmir = reinterpret_cast<uint16_t*>(base + o);
+  o += align16(sizeof(uint16_t) * (size_t)N * (N + 1) / 2);
   S.slots = reinterpret_cast<unsigned long long*>(base + o);
   o += align16(sizeof(unsigned long long) * 48);
   S.red = reinterpret_cast<double*>(base + o);
@@ -362,7 +365,11 @@ __device__ void res_setup(const ResSmem& S, const ProbDev& P, bool herm_ok = tru
     if (!herm_ok) S.hdr->herm = 0;
   }
   if (herm_ok && P.herm)
-    for (int i = threadIdx.x; i < P.N * (P.N + 1) / 2; i += blockDim.x) S.hmap[i] = (uint16_t)P.hmap[i];
+    for (int i = threadIdx.x; i < P.N * (P.N + 1) / 2; i += blockDim.x) {
+      const int v = P.hmap[i], k = v % P.N, l = v / P.N;
+      S.hmap[i] = (uint16_t)v;
+      S.hmir[i] = k != l ? (uint16_t)(l + P.N * k) : (uint16_t)0xffffu;
+    }
   for (int i = threadIdx.x; i < P.ncoef; i += blockDim.x) {
     S.cu[i] = P.cu[i];
     S.cd[i] = P.cd[i];
@@ -395,13 +402,6 @@ __device__ __forceinline__ int rmirror(const Hdr& H, int v) {
   const int k = v % H.N, l = v / H.N;
   return (H.herm && k != l) ? l + H.N * k : -1;
 }
-// store x at element v of a state array and, under the symmetry, its
-// conjugate at the mirror element
-__device__ __forceinline__ void rput(const Hdr& H, double2* a, int v, double2 x) {
-  a[v] = x;
-  const int vm = rmirror(H, v);
-  if (vm >= 0) a[vm] = make_double2(x.x, -x.y);
-}
 
 // this thread's share of the merit sum for state values q[e] against t (an
 // off-diagonal element under the Hermitian symmetry counts for its mirror too)
@@ -428,16 +428,44 @@ __device__ double merit_partial(const ResSmem& S, const Hdr& H, const double2 (&
   return acc;
 }
 
+// This thread's elements, fixed for a launch: packed digits of k and l and,
+// for up to two elements per thread, the vec index (V for an empty slot)
+// and mirror element under the Hermitian symmetry (-1 for none) kept in
+// registers; with more elements per thread those two come from the
+// shared-memory tables (registers are the scarcer resource there).
 template <int E>
 struct Elems {
+  static constexpr bool kRegs = E <= 2;
+  int v[kRegs ? E : 1], m[kRegs ? E : 1];
   uint32_t kd[E], ld[E];
 };
+
+template <int E>
+__device__ __forceinline__ int el_v(const Elems<E>& el, const ResSmem& S, const Hdr& H, int e) {
+  if constexpr (Elems<E>::kRegs) return el.v[e];
+  else return rel(S, H, e);
+}
+template <int E>
+__device__ __forceinline__ int el_m(const Elems<E>& el, const ResSmem& S, const Hdr& H, int e) {
+  if constexpr (Elems<E>::kRegs) {
+    return el.m[e];
+  } else {
+    const int u = threadIdx.x + e * blockDim.x;
+    if (!H.herm || u >= H.Vh) return -1;
+    const int mm = S.hmir[u];
+    return mm == 0xffff ? -1 : mm;
+  }
+}
 
 template <int E>
 __device__ __forceinline__ void init_elems(Elems<E>& el, const ResSmem& S, const Hdr& H) {
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int v = rel(S, H, e);
+    if constexpr (Elems<E>::kRegs) {
+      el.v[e] = v;
+      el.m[e] = v < H.V ? rmirror(H, v) : -1;
+    }
     if (v < H.V) {
       el.kd[e] = S.dig[v % H.N];
       el.ld[e] = S.dig[v / H.N];
@@ -445,6 +473,12 @@ __device__ __forceinline__ void init_elems(Elems<E>& el, const ResSmem& S, const
       el.kd[e] = el.ld[e] = 0;
     }
   }
+}
+
+// store x at element v of a state array and its conjugate at the mirror m (m >= 0)
+__device__ __forceinline__ void rputm(double2* a, int v, int m, double2 x) {
+  a[v] = x;
+  if (m >= 0) a[m] = make_double2(x.x, -x.y);
 }
 
 // Per-thread plan for one element per thread and a compile-time subsystem
@@ -546,6 +580,7 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const bool neumann = H.method == LB_SOLVER_NEUMANN;
   const bool gmres = GM && H.method == LB_SOLVER_GMRES;
+  const int V = H.V, maxit = H.max_iter;
   const Tabs T{S.cu, S.cd, S.jf, S.ja};
   unsigned* slots = reinterpret_cast<unsigned*>(S.slots);
   double2 cq[QT > 0 ? QT : 1];
@@ -561,8 +596,8 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
   unsigned qmax = 0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int v = rel(S, H, e);
-    if (v < H.V) {
+    const int v = el_v(el, S, H, e);
+    if (v < V) {
       double2 z0 = rhs[e];
       if (!neumann) {
         const double2 d = QT > 0 ? pl.d : S.dsm[v];
@@ -570,7 +605,7 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
         const double ur = pc ? rhs[e].x + pc[e].x : rhs[e].x, ui = pc ? rhs[e].y + pc[e].y : rhs[e].y;
         z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
       }
-      rput(H, S.zb0, v, z0);
+      rputm(S.zb0, v, el_m(el, S, H, e), z0);
       if (gmres) S.zb1[v] = rhs[e];
       qmax = max(qmax, max(hi_abs(rhs[e].x), hi_abs(rhs[e].y)));
     }
@@ -588,14 +623,14 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
     if (gmres) return res_gmres<E, ADJ>(S, H, el, ct, tol);
   }
   const unsigned thr = hi_abs(tol * fac);
-  for (int it = 0; it < H.max_iter; ++it) {
+  for (int it = 0; it < maxit; ++it) {
     const double2* __restrict__ zc = cur ? S.zb1 : S.zb0;
     double2* __restrict__ zn = cur ? S.zb0 : S.zb1;
     unsigned dmax = 0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int v = rel(S, H, e);
-      if (v < H.V) {
+      const int v = el_v(el, S, H, e);
+      if (v < V) {
         double ar = rhs[e].x, ai = rhs[e].y;
         double2 d;
         if constexpr (QT > 0) {
@@ -615,7 +650,7 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
           z.x = ar + fma(d.x, zo.x, -di * zo.y);
           z.y = ai + fma(d.x, zo.y, di * zo.x);
         }
-        rput(H, zn, v, z);
+        rputm(zn, v, el_m(el, S, H, e), z);
         dmax = max(dmax, max(hi_abs(z.x - zo.x), hi_abs(z.y - zo.y)));
       }
     }
@@ -649,30 +684,42 @@ struct Pred {
     hh = 0.5 * P.h;
     n = slot = 0;
   }
-  __device__ void predict(double2 (&pc)[E], const ResSmem& S, const Hdr& H) const {
+  __device__ void predict(double2 (&pc)[E], const Elems<E>& el, const ResSmem& S, const Hdr& H, int V) const {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int v = rel(S, H, e);
+      const int v = el_v(el, S, H, e);
       double pr = 0.0, pi = 0.0;
-      if (v < H.V) {
+      if (v < V) {
         int sl = slot;
-        for (int i = 1; i <= n; ++i) {
-          sl = sl > 0 ? sl - 1 : kPredOrder - 1;
-          const double w = kExtrap[n][i - 1];
-          const double2 c = hist[(size_t)sl * stride + v];
-          pr = fma(w, c.x, pr);
-          pi = fma(w, c.y, pi);
+        if (n == kPredOrder) {
+          // steady state: all terms, loads issued together
+#pragma unroll
+          for (int i = 1; i <= kPredOrder; ++i) {
+            sl = sl > 0 ? sl - 1 : kPredOrder - 1;
+            const double2 c = hist[(size_t)sl * stride + v];
+            pr = fma(kExtrap[kPredOrder][i - 1], c.x, pr);
+            pi = fma(kExtrap[kPredOrder][i - 1], c.y, pi);
+          }
+        } else {
+          for (int i = 1; i <= n; ++i) {
+            sl = sl > 0 ? sl - 1 : kPredOrder - 1;
+            const double w = kExtrap[n][i - 1];
+            const double2 c = hist[(size_t)sl * stride + v];
+            pr = fma(w, c.x, pr);
+            pi = fma(w, c.y, pi);
+          }
         }
       }
       pc[e] = make_double2(pr, pi);
     }
   }
   template <bool ADJ>
-  __device__ void record(const double2* zc, const double2 (&rhs)[E], const ResSmem& S, const Hdr& H) {
+  __device__ void record(const double2* zc, const double2 (&rhs)[E], const Elems<E>& el, const ResSmem& S,
+                         const Hdr& H, int V) {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int v = rel(S, H, e);
-      if (v < H.V) {
+      const int v = el_v(el, S, H, e);
+      if (v < V) {
         const double2 z = zc[v], d = __ldg(D + v);
         const double dr = hh * d.x, di = hh * (ADJ ? -d.y : d.y);
         hist[(size_t)slot * stride + v] = make_double2(z.x - fma(dr, z.x, -di * z.y) - rhs[e].x,
@@ -963,6 +1010,7 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
   const ResSmem S = carve(smem, P.ncoef, P.njcoef, P.N, P.V);
   res_setup(S, P);
   const Hdr& H = *S.hdr;
+  const int V = H.V;  // kept in a register: H is reloaded after every barrier
   Elems<E> el;
   init_elems<E>(el, S, H);
   Plan<QT> pl;
@@ -971,8 +1019,8 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
   double2 q[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int v = rel(S, H, e);
-    q[e] = v < H.V ? P.q0[base + v] : make_double2(0.0, 0.0);
+    const int v = el_v(el, S, H, e);
+    q[e] = v < V ? P.q0[base + v] : make_double2(0.0, 0.0);
   }
   CtaStats stats;
   // predictor only when no step is ever recomputed (K == 0): recomputed stage
@@ -989,12 +1037,12 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
       double2* ck = P.ckpt + ((size_t)i * H.n_ckpt + j / H.K) * H.V;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int v = rel(S, H, e);
-        if (v < H.V) ck[v] = q[e];
+        const int v = el_v(el, S, H, e);
+        if (v < V) ck[v] = q[e];
       }
     }
     int cur;
-    if (pred) pr.predict(pc, S, H);
+    if (pred) pr.predict(pc, el, S, H, V);
     const int it = res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur,
                                                  pred ? pc : nullptr);
     if (it < 0) {
@@ -1004,12 +1052,12 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
     }
     stats.add(0, it);
     const double2* zc = cur ? S.zb1 : S.zb0;
-    if (pred) pr.template record<false>(zc, q, S, H);
+    if (pred) pr.template record<false>(zc, q, el, S, H, V);
     double2* tp = (tape && H.K == 0) ? P.ckpt + ((size_t)i * H.NT + j) * H.V : nullptr;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int v = rel(S, H, e);
-      if (v < H.V) {
+      const int v = el_v(el, S, H, e);
+      if (v < V) {
         const double2 z = zc[v];
         if (tp) tp[v] = z;
         // q^{j+1} = q^j + dt M z = 2 z - q^j  (eq. IMR with eq. linsystem_primal)
@@ -1021,12 +1069,12 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
   double acc = 0.0;
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int v = rel(S, H, e);
-    if (v < H.V) {
-      rput(H, P.qT + base, v, q[e]);
+    const int v = el_v(el, S, H, e);
+    if (v < V) {
+      rputm(P.qT + base, v, el_m(el, S, H, e), q[e]);
       const double2 t = P.tar[base + v];
       // an off-diagonal element under the symmetry stands for its mirror too
-      const double wm = rmirror(H, v) >= 0 ? 2.0 : 1.0;
+      const double wm = el_m(el, S, H, e) >= 0 ? 2.0 : 1.0;
       if (H.kind == LB_J_FROB) {
         const double dr = q[e].x - t.x, di = q[e].y - t.y;
         if (wm == 1.0)
@@ -1060,6 +1108,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
   const ResSmem S = carve(smem, P.ncoef, P.njcoef, P.N, P.V);
   res_setup(S, P);
   const Hdr& H = *S.hdr;
+  const int V = H.V;  // kept in a register: H is reloaded after every barrier
   Elems<E> el;
   init_elems<E>(el, S, H);
   Plan<QT> pl;
@@ -1074,13 +1123,13 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
   // running penalty: q^j is rebuilt backwards, q^j = 2 z^j - q^{j+1}, in the
   // workspace buffer qb (each thread its own elements), starting from q^{N_T}
   if (H.gamma1 != 0.0)
-    for (int v = threadIdx.x; v < H.V; v += blockDim.x) P.qb[base + v] = P.qT[base + v];
+    for (int v = threadIdx.x; v < V; v += blockDim.x) P.qb[base + v] = P.qT[base + v];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int v = rel(S, H, e);
+    const int v = el_v(el, S, H, e);
     lam[e] = make_double2(0.0, 0.0);
     qf[e] = lam[e];
-    if (v < H.V) {
+    if (v < V) {
       const double2 t = P.tar[base + v];
       if (H.kind == LB_J_FROB) {
         const double2 qq = P.qT[base + v];
@@ -1105,8 +1154,8 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       const double2* ck = P.ckpt + ((size_t)i * H.n_ckpt + sg) * H.V;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int v = rel(S, H, e);
-        if (v < H.V) qf[e] = ck[v];
+        const int v = el_v(el, S, H, e);
+        if (v < V) qf[e] = ck[v];
       }
       for (int j = j0; j < j1; ++j) {
         int cur;
@@ -1121,8 +1170,8 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
         double2* sgv = P.seg + ((size_t)i * H.K + (j - j0)) * H.V;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          const int v = rel(S, H, e);
-          if (v < H.V) {
+          const int v = el_v(el, S, H, e);
+          if (v < V) {
             const double2 z = zc[v];
             sgv[v] = z;
             qf[e] = make_double2(fma(2.0, z.x, -qf[e].x), fma(2.0, z.y, -qf[e].y));
@@ -1134,7 +1183,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       const double2* ct = P.ctab + (size_t)j * H.cq;
       int cur;
       // (I - dt/2 (M^{j+1/2})^+) zhat^j = qhat^{j+1}   (eq. linsystem_adjoint)
-      if (apred) pr.predict(pc, S, H);
+      if (apred) pr.predict(pc, el, S, H, V);
       const int it = res_solve<E, QT, true, GM>(S, H, el, pl, lam, ct, stop_factor(P, j), cur, apred ? pc : nullptr);
       if (it < 0) {
         if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
@@ -1143,7 +1192,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       }
       stats.add(2, it);
       const double2* zh = cur ? S.zb1 : S.zb0;
-      if (apred) pr.template record<true>(zh, lam, S, H);
+      if (apred) pr.template record<true>(zh, lam, el, S, H, V);
       const double2* Zt = H.K > 0 ? P.seg + ((size_t)i * H.K + (j - j0)) * H.V : P.ckpt + ((size_t)i * H.NT + j) * H.V;
       // gradient pieces (eq. reducedgradient): for every subsystem q,
       //   g_a  = zhat^H vec(-i[a_q, Z])   = -i sum_kl Z_kl conj(R_zhat)
@@ -1152,16 +1201,16 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       double2 Z[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int v = rel(S, H, e);
-        Z[e] = v < H.V ? Zt[v] : make_double2(0.0, 0.0);
+        const int v = el_v(el, S, H, e);
+        Z[e] = v < V ? Zt[v] : make_double2(0.0, 0.0);
       }
       for (int q = 0; q < H.Q; ++q) {
         const int n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * H.N;
         double sar = 0.0, sai = 0.0, sdr = 0.0, sdi = 0.0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          const int v = rel(S, H, e);
-          if (v < H.V) {
+          const int v = el_v(el, S, H, e);
+          if (v < V) {
             const int nk = (el.kd[e] >> (H.db * q)) & H.dm, nl = (el.ld[e] >> (H.db * q)) & H.dm;
             const double c1 = S.cu[co + nk], c2 = S.cd[co + nl], c3 = S.cd[co + nk], c4 = S.cu[co + nl];
             const double2 x1 = zh[v + (nk + 1 < n ? s : 0)];
@@ -1173,7 +1222,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
             const double rr = fma(-c4, x4.x, c3 * x3.x);
             const double ri = fma(-c4, x4.y, c3 * x3.y);
             // Z conj(R) and Z conj(P)
-            if (rmirror(H, v) < 0) {
+            if (el_m(el, S, H, e) < 0) {
               sar = fma(Z[e].x, rr, fma(Z[e].y, ri, sar));
               sai = fma(Z[e].y, rr, fma(-Z[e].x, ri, sai));
               sdr = fma(Z[e].x, pr, fma(Z[e].y, pi, sdr));
@@ -1211,8 +1260,8 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       const double ls = linear_sign(H.kind);
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int v = rel(S, H, e);
-        if (v < H.V) {
+        const int v = el_v(el, S, H, e);
+        if (v < V) {
           const double2 z = zh[v];
           lam[e] = make_double2(fma(2.0, z.x, -lam[e].x), fma(2.0, z.y, -lam[e].y));
           if (H.gamma1 != 0.0) {
@@ -1245,6 +1294,7 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
   const ResSmem S = carve(smem, P.ncoef, P.njcoef, P.N, P.V);
   res_setup(S, P, false);
   const Hdr& H = *S.hdr;
+  const int V = H.V;  // kept in a register: H is reloaded after every barrier
   Elems<E> el;
   init_elems<E>(el, S, H);
   Plan<QT> pl;
@@ -1254,7 +1304,7 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int v = threadIdx.x + e * blockDim.x;
-    q[e] = v < H.V ? xv[v] : make_double2(0.0, 0.0);
+    q[e] = v < V ? xv[v] : make_double2(0.0, 0.0);
   }
   CtaStats stats;
   for (int jj = 0; jj < j1 - j0; ++jj) {
@@ -1272,7 +1322,7 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int v = threadIdx.x + e * blockDim.x;
-      if (v < H.V) {
+      if (v < V) {
         const double2 z = zc[v];
         q[e] = make_double2(fma(2.0, z.x, -q[e].x), fma(2.0, z.y, -q[e].y));
       }
@@ -1281,7 +1331,7 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const int v = threadIdx.x + e * blockDim.x;
-    if (v < H.V) xv[v] = q[e];
+    if (v < V) xv[v] = q[e];
   }
   stats.flush(P.status);
 }

@@ -2059,12 +2059,15 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
     }
     const double2* z0 = S.zb + (size_t)(cnt.gk & 1) * H.V;
     ClStep nx = cl_step(P, pl, H.cq, j1 - 1);
+    // this lane's stage vector element of step j, loaded one step ahead so
+    // that its latency is hidden behind a whole step
+    const bool gl = pl.act;
+    const double2* tape = H.K > 0 ? P.seg + (size_t)i * H.K * H.V : P.ckpt + (size_t)i * H.NT * H.V;
+    const int jt = H.K > 0 ? j0 : 0;  // tape row of step j is j - jt
+    double2 Znx = gl ? tape[(size_t)(j1 - 1 - jt) * H.V + pl.v] : make_double2(0.0, 0.0);
     for (int j = j1 - 1; j >= j0; --j) {
-      // this lane's stage vector element, loaded before the solve so that its latency is hidden
-      const bool gl = pl.act;
-      const double2 Z = gl ? (H.K > 0 ? P.seg[((size_t)i * H.K + (j - j0)) * H.V + pl.v]
-                                      : P.ckpt[((size_t)i * H.NT + j) * H.V + pl.v])
-                           : make_double2(0.0, 0.0);
+      const double2 Z = Znx;
+      if (gl && j > j0) Znx = tape[(size_t)(j - 1 - jt) * H.V + pl.v];
       const ClStep st = nx;
       if (j > j0) nx = cl_step(P, pl, H.cq, j - 1);
       ClHist hn = ahist;

@@ -1616,10 +1616,25 @@ struct ClStep {
   double2 c;   // d_q or its Jaynes-Cummings factor for this lane's half
   double fac;  // stopping-test factor
 };
-__device__ __forceinline__ ClStep cl_step(const ProbDev& P, const ClPlan& pl, int cq, int j) {
+// where they come from, resolved once per launch and kept in registers (the
+// problem record is in global memory and is reloaded after every asm
+// statement that clobbers memory)
+struct ClSrc {
+  const double2* ct;  // control table, this lane's column
+  const double* sf;   // stop factors, or null (factor 1)
+  int cq;             // control table entries per step
+};
+__device__ __forceinline__ ClSrc cl_src(const ProbDev& P, const ClPlan& pl, int cq) {
+  ClSrc src;
+  src.ct = P.ctab + pl.q;
+  src.sf = P.method == LB_SOLVER_JACOBI ? P.sfac : nullptr;
+  src.cq = cq;
+  return src;
+}
+__device__ __forceinline__ ClStep cl_step(const ClSrc& src, int j) {
   ClStep st;
-  st.c = P.ctab[(size_t)j * cq + pl.q];
-  st.fac = stop_factor(P, j);
+  st.c = src.ct[(size_t)j * src.cq];
+  st.fac = src.sf ? src.sf[j] : 1.0;
   return st;
 }
 
@@ -1918,8 +1933,12 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
   const Hdr& H = *S.hdr;
   const ClPlan pl = cl_plan<QT, CS>(S, C, crank);
   const ClAddr A = cl_addr(S, pl, C, crank);
+  const ClSrc src = cl_src(P, pl, H.cq);
   const size_t base = (size_t)i * H.V;
   const bool own = pl.ev && pl.r == 0;  // the lane that writes the element's tapes
+  const int NT = H.NT, K = H.K, V = H.V;
+  // this lane's element in the checkpoints (K > 0) or the stage tape (K == 0), step 0
+  double2* const tp0 = P.ckpt + (K > 0 ? (size_t)i * H.n_ckpt * V : (size_t)i * NT * V) + pl.v;
   double2 rhs = P.q0[base + pl.v];
   ClCount cnt;
   CtaStats stats;
@@ -1934,14 +1953,14 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
     failed = true;
   }
   const double2* z0 = S.zb + (size_t)(cnt.gk & 1) * H.V;
-  ClStep nx = cl_step(P, pl, H.cq, 0);
-  for (int j = 0; j < H.NT && !failed; ++j) {
-    if (tape && H.K > 0 && j % H.K == 0 && own) P.ckpt[((size_t)i * H.n_ckpt + j / H.K) * H.V + pl.v] = rhs;
+  ClStep nx = cl_step(src, 0);
+  for (int j = 0; j < NT && !failed; ++j) {
+    if (tape && K > 0 && j % K == 0 && own) tp0[(size_t)(j / K) * V] = rhs;
     const ClStep st = nx;
-    if (j + 1 < H.NT) nx = cl_step(P, pl, H.cq, j + 1);
+    if (j + 1 < NT) nx = cl_step(src, j + 1);
     ClHist hn = hist;
     if (hist.on) hn.advance();
-    const bool spec = j + 1 < H.NT;
+    const bool spec = j + 1 < NT;
     ClNext nxt;
     double2 z;
     const int it = cl_iterate<QT, false, CS>(S, pl, A, z0, rhs, st, qmax, C, cnt, z, spec, hn, (j + 1) & 1, &nxt);
@@ -1951,13 +1970,13 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
       break;
     }
     if (crank == 0) stats.add(0, it);
-    if (tape && H.K == 0 && own) P.ckpt[((size_t)i * H.NT + j) * H.V + pl.v] = z;
+    if (tape && K == 0 && own) tp0[(size_t)j * V] = z;
     // q^{j+1} = 2 z - q^j; the next step's first iterate is already in every CTA
     if (spec) {
       cl_commit(S, pl, hist, nxt.cc);
       rhs = cl_join(pl, nxt.rn);
       qmax = nxt.qmax;
-      z0 = S.zs + (size_t)((j + 1) & 1) * H.V;
+      z0 = S.zs + (size_t)((j + 1) & 1) * V;
     } else {
       double cc = 0.0;
       rhs = cl_join(pl, cl_update<false>(pl, z, rhs, hist, cc));
@@ -1987,8 +2006,10 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
   const Hdr& H = *S.hdr;
   const ClPlan pl = cl_plan<QT, CS>(S, C, crank);
   const ClAddr A = cl_addr(S, pl, C, crank);
+  const ClSrc src = cl_src(P, pl, H.cq);
+  const int V = H.V, K = H.K, NT = H.NT, Qn = H.Q;  // in registers: H is reloaded after every asm clobber
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  const size_t base = (size_t)i * H.V;
+  const size_t base = (size_t)i * V;
   const double w = P.wgt[i];
   const double wt = linear_sign(P.kind) * w;
   // terminal condition qhat^{N_T} = beta_i/M g_i (Appendix B), this lane's element
@@ -2005,7 +2026,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
   ClCount cnt;
   CtaStats stats;
   bool failed = false;
-  const int nseg = H.K > 0 ? (H.NT + H.K - 1) / H.K : 1;
+  const int nseg = K > 0 ? (NT + K - 1) / K : 1;
   // the adjoint sweep visits the steps in the same order for every K, and
   // its first iterates are the same arithmetic whether formed at a segment
   // start or at the end of the previous step, so its results never depend
@@ -2014,23 +2035,23 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
   ClHist none;
   const bool own = pl.ev && pl.r == 0;
   // gradient pieces of this warp go to state slot (i * C + crank) * nwarps + warp of gproj
-  double2* gbase = P.gproj + (size_t)((i * C + crank) * nwarps + warp) * H.NT * H.Q * 2;
+  double2* gbase = P.gproj + (size_t)((i * C + crank) * nwarps + warp) * NT * Qn * 2;
   for (int sg = nseg - 1; sg >= 0 && !failed; --sg) {
-    const int j0 = H.K > 0 ? sg * H.K : 0;
-    const int j1 = H.K > 0 ? min(H.NT, j0 + H.K) : H.NT;
-    if (H.K > 0) {
-      double2 rr = P.ckpt[((size_t)i * H.n_ckpt + sg) * H.V + pl.v];
+    const int j0 = K > 0 ? sg * K : 0;
+    const int j1 = K > 0 ? min(NT, j0 + K) : NT;
+    if (K > 0) {
+      double2 rr = P.ckpt[((size_t)i * H.n_ckpt + sg) * V + pl.v];
       unsigned qr = 0;
       if (cl_start<QT, false, CS>(S, pl, A, cl_comp(pl, rr), none, false, 0.0, C, cnt, qr)) {
         if (threadIdx.x == 0 && crank == 0) record_error(P.status, LB_ECUDA, j0);
         failed = true;
         break;
       }
-      const double2* z0r = S.zb + (size_t)(cnt.gk & 1) * H.V;
-      ClStep nx = cl_step(P, pl, H.cq, j0);
+      const double2* z0r = S.zb + (size_t)(cnt.gk & 1) * V;
+      ClStep nx = cl_step(src, j0);
       for (int j = j0; j < j1; ++j) {
         const ClStep st = nx;
-        if (j + 1 < j1) nx = cl_step(P, pl, H.cq, j + 1);
+        if (j + 1 < j1) nx = cl_step(src, j + 1);
         const bool spec = j + 1 < j1;
         ClNext nxt;
         double2 z;
@@ -2041,11 +2062,11 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
           break;
         }
         if (crank == 0) stats.add(1, it);
-        if (own) P.seg[((size_t)i * H.K + (j - j0)) * H.V + pl.v] = z;
+        if (own) P.seg[((size_t)i * K + (j - j0)) * V + pl.v] = z;
         if (spec) {
           rr = cl_join(pl, nxt.rn);
           qr = nxt.qmax;
-          z0r = S.zs + (size_t)((j + 1) & 1) * H.V;
+          z0r = S.zs + (size_t)((j + 1) & 1) * V;
         }
       }
       if (failed) break;
@@ -2057,19 +2078,19 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
       failed = true;
       break;
     }
-    const double2* z0 = S.zb + (size_t)(cnt.gk & 1) * H.V;
-    ClStep nx = cl_step(P, pl, H.cq, j1 - 1);
+    const double2* z0 = S.zb + (size_t)(cnt.gk & 1) * V;
+    ClStep nx = cl_step(src, j1 - 1);
     // this lane's stage vector element of step j, loaded one step ahead so
     // that its latency is hidden behind a whole step
     const bool gl = pl.act;
-    const double2* tape = H.K > 0 ? P.seg + (size_t)i * H.K * H.V : P.ckpt + (size_t)i * H.NT * H.V;
-    const int jt = H.K > 0 ? j0 : 0;  // tape row of step j is j - jt
-    double2 Znx = gl ? tape[(size_t)(j1 - 1 - jt) * H.V + pl.v] : make_double2(0.0, 0.0);
+    const double2* tape = K > 0 ? P.seg + (size_t)i * K * V : P.ckpt + (size_t)i * NT * V;
+    const int jt = K > 0 ? j0 : 0;  // tape row of step j is j - jt
+    double2 Znx = gl ? tape[(size_t)(j1 - 1 - jt) * V + pl.v] : make_double2(0.0, 0.0);
     for (int j = j1 - 1; j >= j0; --j) {
       const double2 Z = Znx;
-      if (gl && j > j0) Znx = tape[(size_t)(j - 1 - jt) * H.V + pl.v];
+      if (gl && j > j0) Znx = tape[(size_t)(j - 1 - jt) * V + pl.v];
       const ClStep st = nx;
-      if (j > j0) nx = cl_step(P, pl, H.cq, j - 1);
+      if (j > j0) nx = cl_step(src, j - 1);
       ClHist hn = ahist;
       if (ahist.on) hn.advance();
       const bool spec = j > j0;
@@ -2082,7 +2103,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
         break;
       }
       if (crank == 0) stats.add(2, it);
-      const double2* zb = S.zb + (size_t)(cnt.gk & 1) * H.V;
+      const double2* zb = S.zb + (size_t)(cnt.gk & 1) * V;
       // gradient piece of this lane's half (eq. reducedgradient): sum_kl Z conj(X_zhat),
       // X the half's neighbour combination of zhat; P half -> g_ad, R half -> g_a.
       // Summed over the warp's elements (one component per lane after the
@@ -2109,7 +2130,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
         // store -i (sr + i si) = (si, -sr)
         const int hv = lane >> 1;
         if (lane < L && hv < 2 * QT) {
-          double* g = reinterpret_cast<double*>(gbase + ((size_t)j * H.Q + (hv >> 1)) * 2 + ((hv & 1) ? 0 : 1));
+          double* g = reinterpret_cast<double*>(gbase + ((size_t)j * Qn + (hv >> 1)) * 2 + ((hv & 1) ? 0 : 1));
           if (lane & 1)
             g[0] = sr;
           else
@@ -2124,7 +2145,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
         // lane r < 2Q holds sum sr of half r, lane L + r the sum si; store -i (sr + i si) = (si, -sr)
         const int r = lane & (L - 1);
         if (lane < 2 * L && r < 2 * QT) {
-          double* g = reinterpret_cast<double*>(gbase + ((size_t)j * H.Q + (r >> 1)) * 2 + ((r & 1) ? 0 : 1));
+          double* g = reinterpret_cast<double*>(gbase + ((size_t)j * Qn + (r >> 1)) * 2 + ((r & 1) ? 0 : 1));
           g[hi ? 0 : 1] = hi ? k : -k;
         }
       }
@@ -2134,7 +2155,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
         cl_commit(S, pl, ahist, nxt.cc);
         ll = cl_join(pl, nxt.rn);
         qmax = nxt.qmax;
-        z0 = S.zs + (size_t)((j - 1) & 1) * H.V;
+        z0 = S.zs + (size_t)((j - 1) & 1) * V;
       } else {
         double cc = 0.0;
         const double rn = cl_update<true>(pl, zh, ll, ahist, cc);
@@ -2161,6 +2182,7 @@ __global__ void __launch_bounds__(128, 1) k_propagate_cl(const ProbDev* __restri
   const Hdr& H = *S.hdr;
   const ClPlan pl = cl_plan<QT, CS>(S, C, crank);
   const ClAddr A = cl_addr(S, pl, C, crank);
+  const ClSrc src = cl_src(P, pl, H.cq);
   double2* xv = x + (size_t)i * H.V;
   double2 rr = xv[pl.v];
   ClCount cnt;
@@ -2179,11 +2201,11 @@ __global__ void __launch_bounds__(128, 1) k_propagate_cl(const ProbDev* __restri
   }
   const double2* z0 = S.zb + (size_t)(cnt.gk & 1) * H.V;
   ClStep nx;
-  if (n > 0) nx = cl_step(P, pl, H.cq, adjoint ? j1 - 1 : j0);
+  if (n > 0) nx = cl_step(src, adjoint ? j1 - 1 : j0);
   for (int jj = 0; jj < n && !failed; ++jj) {
     const int j = adjoint ? j1 - 1 - jj : j0 + jj;
     const ClStep st = nx;
-    if (jj + 1 < n) nx = cl_step(P, pl, H.cq, adjoint ? j - 1 : j + 1);
+    if (jj + 1 < n) nx = cl_step(src, adjoint ? j - 1 : j + 1);
     const bool spec = jj + 1 < n;
     ClNext nxt;
     double2 z;

@@ -2625,7 +2625,10 @@ __device__ GridSmem grid_setup(unsigned char* base, const ProbDev& P, int nstate
     S.g->Vh = herm ? P.N * (P.N + 1) / 2 : P.V;
     S.g->total = (long long)nstates * S.g->Vh;
     const long long per = (S.g->total + gridDim.x - 1) / gridDim.x;
-    S.g->chunk = (per + blockDim.x - 1) / blockDim.x * blockDim.x;
+    // whole warps, not whole blocks: rounding the chunk up to the block size
+    // left up to half of the blocks without elements (three states of
+    // N (N + 1) / 2 = 32896 elements filled 193 of 304 blocks)
+    S.g->chunk = (per + 31) / 32 * 32;
   }
   for (int i = threadIdx.x; i < P.ncoef; i += blockDim.x) {
     S.cu[i] = P.cu[i];

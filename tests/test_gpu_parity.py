@@ -67,11 +67,17 @@ def test_apply_matches_dense_lindbladian(levels):
             assert np.max(np.abs(y - ref)) <= 1e-14 * scale, (levels, j, adj)
 
 
-@pytest.mark.parametrize("levels", [(2, 3), (3, 2, 2), (4, 4)])
-def test_steps_match_oracle(levels):
-    """lb_propagate over a few forward and adjoint IMR steps from random states."""
+@pytest.mark.parametrize("levels,sweep", [((2, 3), "cluster"), ((2, 3), "resident"), ((3, 2, 2), "auto"),
+                                          ((4, 4), "auto"), ((3, 3, 3), "grid")])
+def test_steps_match_oracle(levels, sweep):
+    """lb_propagate over a few forward and adjoint IMR steps from random states,
+    on each sweep kind."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    sw = {"auto": L.LB_SWEEP_AUTO, "cluster": L.LB_SWEEP_CLUSTER, "resident": L.LB_SWEEP_RESIDENT,
+          "grid": L.LB_SWEEP_GRID}[sweep]
     p = W.random_problem(102, levels=levels, n_states=2, n_steps=12, T_ns=0.24, amp=0.1)
-    s = _sys(p)
+    s = _sys(p, sweep=sw)
     mdl = model.Model(p.system, p.controls)
     N = mdl.N
     rng = np.random.default_rng(2)

@@ -208,10 +208,22 @@ def traffic_record(kernel: str):
     if not rec:
         return None
     src = os.path.join(ROOT, "paper_2110_10310_gb300", "csrc", "lb_kernels.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    if rec.get("source_sha256") != sha:
+    if rec.get("code_sha256") != kernel_source_digest(src):
         return None
     return rec.get("dram_bytes_per_launch")
+
+
+def kernel_source_digest(path: str) -> str:
+    """SHA-256 of the kernel source with its // comments and blank lines
+    removed: the counters stay valid across comment edits, not across code
+    edits.  (The kernel source has no block comments and no // inside string
+    literals.)"""
+    lines = []
+    for line in open(path, encoding="utf-8"):
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            lines.append(code)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
 # ----------------------------------------------------------------------------

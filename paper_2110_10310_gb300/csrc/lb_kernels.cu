@@ -1348,16 +1348,17 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
 // instructions on its own data.  The L partial sums meet through shuffles,
 // and a CTA holds at most 4 warps (one per SM sub-partition).
 //
-// Every CTA keeps a full replica of the iterate, of the right-hand side and
-// of the inverse diagonal in shared memory.  An inner iteration ends without
-// any cluster-wide barrier: each element's new value, and each warp's
-// largest change, are pushed into every CTA with st.async, whose completion
-// is counted in bytes on the receiving CTA's mbarrier (one per iteration
-// parity, so a CTA one iteration ahead never disturbs the current phase);
-// each CTA waits only for its own mbarrier, with a bounded wait.  All CTAs
-// see the same data and take the same decisions.  The right-hand side of the
-// next time step is formed locally from the replicas, so a time step needs
-// no exchange besides the inner iterations.
+// Every CTA keeps a full replica of the iterate and the diagonal tables in
+// shared memory; each element's right-hand side lives in the registers of
+// the lanes that own it.  An inner iteration ends without any cluster-wide
+// barrier: each element's new value, and each warp's largest change, are
+// pushed into every CTA with st.async, whose completion is counted in bytes
+// on the receiving CTA's mbarrier (one per exchange parity, so a CTA one
+// exchange ahead never disturbs the current phase); each CTA waits only for
+// its own mbarrier, with a bounded wait.  All CTAs see the same data and
+// take the same decisions.  The next step's first iterate travels with the
+// inner iterations' pushes (cl_iterate), so a step that converges in one
+// inner iteration needs one exchange.
 
 // Lanes per element: 2Q (one half P or R of a subsystem each), or with CS
 // ("component split") 4Q, two lanes per half, one for the real and one for

@@ -175,12 +175,15 @@ def test_checkpoint_interval_bitwise_identical():
     assert _rel(g0, res[0][1]) < 1e-12
 
 
-def test_neumann_solver_agrees_with_jacobi():
+@pytest.mark.parametrize("sweep", ["auto", "cluster", "resident", "grid"])
+def test_neumann_solver_agrees_with_jacobi(sweep):
     from paper_2110_10310_gb300 import _lib as L
 
+    sw = {"auto": L.LB_SWEEP_AUTO, "cluster": L.LB_SWEEP_CLUSTER, "resident": L.LB_SWEEP_RESIDENT,
+          "grid": L.LB_SWEEP_GRID}[sweep]
     p = W.random_problem(207, levels=(3, 3), n_states=2, n_steps=60, T_ns=1.2, amp=0.05)
-    Gj, gj = _sys(p, solver=L.LB_SOLVER_JACOBI).gradient()
-    Gn, gn = _sys(p, solver=L.LB_SOLVER_NEUMANN).gradient()
+    Gj, gj = _sys(p, solver=L.LB_SOLVER_JACOBI, sweep=sw).gradient()
+    Gn, gn = _sys(p, solver=L.LB_SOLVER_NEUMANN, sweep=sw).gradient()
     assert abs(Gj - Gn) <= 1e-12 * abs(Gj)
     assert _rel(gn, gj) < 1e-10
 
@@ -801,3 +804,21 @@ def test_resident_hermitian_symmetry_not_taken_for_gmres_or_general_states():
     s = _sys(q, sweep=L.LB_SWEEP_RESIDENT)
     s.gradient()
     assert s.stats()["symmetry"] == "none"
+
+
+# ----------------------------------------------------------------------------
+# horizons of one and two steps on every sweep kind
+
+
+@pytest.mark.parametrize("n_steps,K", [(1, 0), (1, 1), (2, 0), (2, 1), (3, 2)])
+@pytest.mark.parametrize("sweep", ["cluster", "resident", "grid"])
+def test_short_horizons_match_oracle(n_steps, K, sweep):
+    """The first and last steps of a sweep are special (no predictor history,
+    no next step to prepare, segment boundaries): horizons of one to three
+    steps against the oracle on each sweep kind."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    sw = {"cluster": L.LB_SWEEP_CLUSTER, "resident": L.LB_SWEEP_RESIDENT, "grid": L.LB_SWEEP_GRID}[sweep]
+    p = W.random_problem(950 + n_steps, levels=(2, 3), n_states=2, n_steps=n_steps, T_ns=0.02 * n_steps, amp=0.1,
+                         ckpt_every=K, gamma2=0.05)
+    _check_problem(p, sweep=sw)

@@ -48,6 +48,11 @@ WORKLOADS = {
                     "first {n} of 20000 steps, fwd + adjoint with checkpoints every 10 steps, grid-wide sweep"),
     "apply_6x3": ("apply_6x3: y = M(t) x, the matrix-free Lindblad apply (lb_apply, one thread per element) on "
                   "{n} states of 6 qutrits (vec 531441, 8.5 MB each), x and y in HBM"),
+    "cnot_penalty": ("cnot_penalty: the cnot_2x3 workload with the running penalty gamma1 int beta(t) J dt "
+                     "(gamma1 = 0.1, a = 20 ns: Sec. III, eq. optimproblem), one CTA per state, fwd + adjoint"),
+    "cnot_jc": ("cnot_jc: the cnot_2x3 workload with a Jaynes-Cummings coupling of the two transmons "
+                "(g = 5 MHz, rotating frequencies 4.80 and 4.86 GHz: the coupling rotates at 60 MHz), "
+                "one CTA per state, fwd + adjoint"),
     "fock_lbfgs": ("fock_lbfgs: one 4-level qudit |0> -> (|0>+|3>)/sqrt 2, J_Frob, 10 splines x 2 carriers, "
                    "T=200 ns, 10000 steps; one bench step = one L-BFGS run (lb_optimize, memory 10, "
                    "at most 150 iterations, gtol 1e-9) from the seeded controls"),
@@ -77,6 +82,15 @@ def problem(n_steps=None, workload="cnot_2x3", states=0):
         p = W.config5(n_states=states or 64)
         p.ckpt_every = 10
         n_steps = n_steps or PREFIX[workload]
+    elif workload == "cnot_penalty":
+        p = W.config2()
+        p.gamma1, p.penalty_a = 0.1, 20.0
+    elif workload == "cnot_jc":
+        import numpy as np
+
+        p = W.config2()
+        p.system.jc_ghz = np.array([[0.0, 0.005], [0.0, 0.0]])
+        p.system.rot_ghz = np.array([4.80, 4.86])
     else:
         p = W.config2()
     if n_steps is not None:

@@ -89,8 +89,9 @@ extern "C" {
  *                      iterates in global memory, a grid barrier per inner
  *                      iteration (any N^2);
  *   LB_SWEEP_CLUSTER:  one thread-block cluster per state, each element's
- *                      work split over 2Q lanes, the iterate replicated in
- *                      every CTA's shared memory (Q <= 4, N^2 * 2Q <= 1024);
+ *                      work split over 2P or 4P lanes (P = Q + Jaynes-Cummings
+ *                      pairs), the iterate replicated in every CTA's shared
+ *                      memory (P <= 4, N^2 * 2P <= 1024, no running penalty);
  *                      for small states whose time loop is latency-bound;
  *   LB_SWEEP_AUTO:     GRID when N^2 > 4096 or when N^2 >= 1024 with fewer than
  *                      64 states (most SMs would idle); else CLUSTER when it
@@ -218,8 +219,8 @@ int lb_set_sweep(lb_system* sys, int32_t sweep);
  * the general rotating-frame form with time-dependent factors.  jc_ghz:
  * Q x Q row-major g_pq/2pi in GHz, entries p < q used (0 = no coupling);
  * rot_ghz: Q rotating-frame frequencies omega_q^rot/2pi in GHz (nullable: all
- * equal, eta = 0).  Copied.  Call before lb_workspace_bytes; coupled systems
- * run the one-CTA-per-state or grid sweeps (not the cluster sweep). */
+ * equal, eta = 0).  Copied.  Call before lb_workspace_bytes; each pair adds
+ * two halves to a cluster sweep's lane plan (see LB_SWEEP_CLUSTER). */
 int lb_system_set_coupling(lb_system* sys, const double* jc_ghz, const double* rot_ghz);
 
 /* Hermitian symmetry (Sec. III-B: density matrices, and Lindblad's equation

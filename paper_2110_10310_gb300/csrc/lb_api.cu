@@ -179,13 +179,13 @@ int effective_K(const lb_system* s) {
   return s->NT < 100 ? (int)s->NT : 100;
 }
 
-// Cluster sweep configuration of this system with 2Q (cs = false) or 4Q
-// lanes per element; C == 0 when it cannot apply.
+// Cluster sweep configuration of this system with 2 or 4 lanes per half
+// pair (cs = false / true; a subsystem's control terms, or a Jaynes-Cummings
+// pair, make one half pair); C == 0 when it cannot apply.
 lbk::ClusterConfig cluster_cfg(const lb_system* s, bool cs) {
-  if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT || s->method == LB_SOLVER_GMRES || !s->jp.empty() ||
-      s->gamma1 != 0.0)
+  if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT || s->method == LB_SOLVER_GMRES || s->gamma1 != 0.0)
     return lbk::ClusterConfig{};
-  return lbk::cluster_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, cs);
+  return lbk::cluster_config(s->V, s->Q + (int)s->jp.size(), n_coef(s), n_jcoef(s), s->N, cs);
 }
 
 // complex values of the GMRES Krylov basis in shared memory (0 for the
@@ -955,8 +955,8 @@ int lb_set_sweep(lb_system* s, int32_t sweep) {
   if (s->ws) return fail(LB_EINVAL, "choose the sweep before binding a workspace");
   if (sweep != LB_SWEEP_AUTO && sweep != LB_SWEEP_RESIDENT && sweep != LB_SWEEP_GRID && sweep != LB_SWEEP_CLUSTER)
     return fail(LB_EINVAL, "unknown sweep kind");
-  if (sweep == LB_SWEEP_CLUSTER && (lbk::cluster_config(s->V, s->Q, 1, 1, 1, false).C <= 0 || !s->jp.empty()))
-    return fail(LB_EINVAL, "cluster sweeps need Q <= 4 and N^2 * 2Q <= 1024");
+  if (sweep == LB_SWEEP_CLUSTER && lbk::cluster_config(s->V, s->Q + (int)s->jp.size(), 1, 1, 1, false).C <= 0)
+    return fail(LB_EINVAL, "cluster sweeps need Q + (Jaynes-Cummings pairs) <= 4 and N^2 * 2(Q + pairs) <= 1024");
   if (sweep == LB_SWEEP_RESIDENT && s->V > lbk::kMaxResidentV)
     return fail(LB_EINVAL, "one CTA per state needs N^2 <= 4096");
   s->sweep = sweep;

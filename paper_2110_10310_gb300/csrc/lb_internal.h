@@ -164,7 +164,7 @@ cudaError_t launch_backward_grid(const ProbDev* d_prob, int nblocks, size_t smem
 // N^2 * lanes <= 1024)
 struct ClusterConfig {
   int C;        // CTAs per cluster (0: not applicable)
-  int QT;       // subsystems (compile-time kernel variant)
+  int QT;       // half pairs: subsystems plus Jaynes-Cummings pairs (compile-time kernel variant)
   int threads;  // threads per CTA
   size_t smem;  // dynamic shared memory per CTA
   bool cs;      // 4Q lanes per element (one per half and component) instead of 2Q

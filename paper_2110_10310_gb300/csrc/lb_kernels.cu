@@ -1360,8 +1360,9 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
 // inner iterations' pushes (cl_iterate), so a step that converges in one
 // inner iteration needs one exchange.
 
-// Lanes per element: 2Q (one half P or R of a subsystem each), or with CS
-// ("component split") 4Q, two lanes per half, one for the real and one for
+// Lanes per element: 2QT (one half P or R of a subsystem each, and the two
+// halves U and W of each Jaynes-Cummings pair: QT = Q + pairs), or with CS
+// ("component split") 4QT, two lanes per half, one for the real and one for
 // the imaginary part of its contribution; rounded up to a power of two.
 template <int QT, bool CS = false>
 struct ClLanes {
@@ -1538,7 +1539,29 @@ __device__ ClPlan cl_plan(const ClSmem& S, int C, int crank) {
   pl.maxit = H.max_iter;
   pl.neu = H.method == LB_SOLVER_NEUMANN;
   pl.rtol = H.rtol;
-  if (pl.ev && u >= 0) {
+  if (pl.ev && u >= 0 && pl.q >= H.Q) {
+    // Jaynes-Cummings pair k (Sec. II) as two more halves: U with the factor
+    // (dt/2) G (like a P half) and W with its conjugate (like an R half),
+    //   U = sqrt(np_k) sqrt(nq_k+1) x[k-sp+sq, l] - sqrt(np_l+1) sqrt(nq_l) x[k, l+sp-sq]
+    //   W = sqrt(np_k+1) sqrt(nq_k) x[k+sp-sq, l] - sqrt(np_l) sqrt(nq_l+1) x[k, l-sp+sq]
+    // (a coefficient is zero where its neighbour leaves the range)
+    const uint32_t kd = S.dig[v % H.N], ld = S.dig[v / H.N];
+    const int k = pl.q - H.Q, p = H.jp[k], q = H.jq[k];
+    const int np = H.lev[p], nq = H.lev[q], d = H.stride[q] - H.stride[p], cp = H.coff[p], cqo = H.coff[q];
+    const int pk = (kd >> (H.db * p)) & H.dm, qk = (kd >> (H.db * q)) & H.dm;
+    const int plv = (ld >> (H.db * p)) & H.dm, ql = (ld >> (H.db * q)) & H.dm;
+    if (!pl.rhalf) {
+      pl.ca = S.cd[cp + pk] * S.cu[cqo + qk];
+      pl.oa = v + ((pk > 0 && qk + 1 < nq) ? d : 0);
+      pl.cb = S.cu[cp + plv] * S.cd[cqo + ql];
+      pl.ob = v - ((ql > 0 && plv + 1 < np) ? d * H.N : 0);
+    } else {
+      pl.ca = S.cu[cp + pk] * S.cd[cqo + qk];
+      pl.oa = v - ((qk > 0 && pk + 1 < np) ? d : 0);
+      pl.cb = S.cd[cp + plv] * S.cu[cqo + ql];
+      pl.ob = v + ((plv > 0 && ql + 1 < nq) ? d * H.N : 0);
+    }
+  } else if (pl.ev && u >= 0) {
     const uint32_t kd = S.dig[v % H.N], ld = S.dig[v / H.N];
     const int q = pl.q, n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * H.N;
     const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
@@ -2130,7 +2153,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
         // lane r < L holds the warp's sum of component r & 1 of half r >> 1;
         // store -i (sr + i si) = (si, -sr)
         const int hv = lane >> 1;
-        if (lane < L && hv < 2 * QT) {
+        if (lane < L && hv < 2 * Qn) {
           double* g = reinterpret_cast<double*>(gbase + ((size_t)j * Qn + (hv >> 1)) * 2 + ((hv & 1) ? 0 : 1));
           if (lane & 1)
             g[0] = sr;
@@ -2145,7 +2168,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
         for (int o = 2 * L; o < 32; o <<= 1) k += __shfl_xor_sync(kFull, k, o);
         // lane r < 2Q holds sum sr of half r, lane L + r the sum si; store -i (sr + i si) = (si, -sr)
         const int r = lane & (L - 1);
-        if (lane < 2 * L && r < 2 * QT) {
+        if (lane < 2 * L && r < 2 * Qn) {
           double* g = reinterpret_cast<double*>(gbase + ((size_t)j * Qn + (r >> 1)) * 2 + ((r & 1) ? 0 : 1));
           g[hi ? 0 : 1] = hi ? k : -k;
         }

@@ -693,25 +693,37 @@ def test_apply_with_jaynes_cummings_matches_dense(levels):
 
 
 @pytest.mark.parametrize("levels,sweep,solver", [((2, 3), "resident", "jacobi"), ((3, 2, 2), "grid", "jacobi"),
-                                                  ((2, 3), "resident", "gmres")])
+                                                  ((2, 3), "resident", "gmres"), ((2, 3), "cluster", "jacobi"),
+                                                  ((3, 3), "cluster", "neumann")])
 def test_jaynes_cummings_gradient_matches_oracle(levels, sweep, solver):
     from paper_2110_10310_gb300 import _lib as L
 
     p = W.random_problem(112, levels=levels, n_states=2, n_steps=40, T_ns=0.8, amp=0.1, jc=0.05, ckpt_every=7)
-    sw = {"resident": L.LB_SWEEP_RESIDENT, "grid": L.LB_SWEEP_GRID}[sweep]
-    sv = {"jacobi": L.LB_SOLVER_JACOBI, "gmres": L.LB_SOLVER_GMRES}[solver]
-    _check_problem(p, sweep=sw, solver=sv)
+    sw = {"resident": L.LB_SWEEP_RESIDENT, "grid": L.LB_SWEEP_GRID, "cluster": L.LB_SWEEP_CLUSTER}[sweep]
+    sv = {"jacobi": L.LB_SOLVER_JACOBI, "gmres": L.LB_SOLVER_GMRES, "neumann": L.LB_SOLVER_NEUMANN}[solver]
+    s, g = _check_problem(p, sweep=sw, solver=sv)
+    assert s.stats()["sweep"] == sweep
 
 
-def test_jaynes_cummings_rejects_cluster_and_auto_avoids_it():
+def test_jaynes_cummings_on_the_cluster_sweep():
+    """A coupled pair adds two halves to the cluster sweep's lane plan: the
+    cluster result agrees with the one-CTA sweep (1e-12 / 1e-11) with and
+    without checkpoints, AUTO picks the cluster for it, and three pairs on
+    three subsystems (six half pairs) are refused."""
     from paper_2110_10310_gb300 import _lib as L
 
-    p = W.random_problem(113, levels=(2, 3), n_states=2, n_steps=10, T_ns=0.2, amp=0.1, jc=0.05)
-    with pytest.raises(L.LBError):
-        _sys(p, sweep=L.LB_SWEEP_CLUSTER)
+    p = W.random_problem(113, levels=(2, 3), n_states=3, n_steps=30, T_ns=0.6, amp=0.1, jc=0.05)
+    for K in (0, 7):
+        Gc, gc = _sys(p, sweep=L.LB_SWEEP_CLUSTER, ckpt_every=K).gradient()
+        Gr, gr = _sys(p, sweep=L.LB_SWEEP_RESIDENT, ckpt_every=K).gradient()
+        assert abs(Gc - Gr) <= 1e-12 * abs(Gr)
+        assert _rel(gc, gr) < 1e-11
     s = _sys(p)
     s.gradient()
-    assert s.stats()["sweep"] == "resident"
+    assert s.stats()["sweep"] == "cluster"
+    q = W.random_problem(114, levels=(2, 2, 2), n_states=2, n_steps=10, T_ns=0.2, amp=0.1, jc=0.05)
+    with pytest.raises(L.LBError):
+        _sys(q, sweep=L.LB_SWEEP_CLUSTER)
 
 
 # ----------------------------------------------------------------------------

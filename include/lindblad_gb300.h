@@ -91,7 +91,7 @@ extern "C" {
  *   LB_SWEEP_CLUSTER:  one thread-block cluster per state, each element's
  *                      work split over 2P or 4P lanes (P = Q + Jaynes-Cummings
  *                      pairs), the iterate replicated in every CTA's shared
- *                      memory (P <= 4, N^2 * 2P <= 1024, no running penalty);
+ *                      memory (P <= 4, N^2 * 2P <= 1024);
  *                      for small states whose time loop is latency-bound;
  *   LB_SWEEP_AUTO:     GRID when N^2 > 4096 or when N^2 >= 1024 with fewer than
  *                      64 states (most SMs would idle); else CLUSTER when it
@@ -205,9 +205,9 @@ int lb_objective_set_measure(lb_system* sys, int32_t m, double gamma2);
  * the time integral by the left rectangle rule, weighted per state like the
  * final-time term; its derivative enters the adjoint sweep as the source
  * gamma1 beta_i/M dt beta(t_j) g(q^j) at qhat^j (Appendix B).  gamma1 >= 0
- * (0 = off, the default), a_ns > 0.  Runs in the one-CTA-per-state sweep
- * (N^2 <= 4096; lb_bind_workspace refuses grid or cluster sweeps with it).
- * Call before lb_workspace_bytes. */
+ * (0 = off, the default), a_ns > 0.  Runs in the one-CTA-per-state and
+ * cluster sweeps (N^2 <= 4096; lb_bind_workspace refuses grid sweeps with
+ * it).  Call before lb_workspace_bytes. */
 int lb_objective_set_penalty(lb_system* sys, double gamma1, double a_ns);
 
 /* Choose the sweep kind (LB_SWEEP_*); call before lb_workspace_bytes. */

@@ -146,7 +146,7 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 bool use_grid(const lb_system* s) {
   if (s->V > lbk::kMaxResidentV) return true;
   if (s->method == LB_SOLVER_GMRES) return false;  // GMRES runs one CTA per state
-  if (s->gamma1 != 0.0) return false;              // so does the running penalty
+  if (s->gamma1 != 0.0) return false;              // the running penalty: one CTA or a cluster per state
   if (s->sweep == LB_SWEEP_GRID) return true;
   if (s->sweep == LB_SWEEP_RESIDENT || s->sweep == LB_SWEEP_CLUSTER) return false;
   return s->V >= 1024 && s->M < 64;
@@ -183,8 +183,7 @@ int effective_K(const lb_system* s) {
 // pair (cs = false / true; a subsystem's control terms, or a Jaynes-Cummings
 // pair, make one half pair); C == 0 when it cannot apply.
 lbk::ClusterConfig cluster_cfg(const lb_system* s, bool cs) {
-  if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT || s->method == LB_SOLVER_GMRES || s->gamma1 != 0.0)
-    return lbk::ClusterConfig{};
+  if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT || s->method == LB_SOLVER_GMRES) return lbk::ClusterConfig{};
   return lbk::cluster_config(s->V, s->Q + (int)s->jp.size(), n_coef(s), n_jcoef(s), s->N, cs);
 }
 
@@ -201,11 +200,8 @@ int decide_krylov(lb_system* s) {
   LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   LB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "cudaDeviceGetAttribute");
   s->krylov = s->V <= lbk::kMaxResidentV ? lbk::gmres_krylov_dim(s->V, n_coef(s), n_jcoef(s), s->N, (size_t)optin) : 0;
-  if (s->gamma1 != 0.0) {
-    if (s->V > lbk::kMaxResidentV || s->sweep == LB_SWEEP_GRID || s->sweep == LB_SWEEP_CLUSTER)
-      return fail(LB_EINVAL, "the running penalty runs in the one-CTA-per-state sweep only (N^2 <= 4096)");
-    s->sweep = LB_SWEEP_RESIDENT;
-  }
+  if (s->gamma1 != 0.0 && (s->V > lbk::kMaxResidentV || s->sweep == LB_SWEEP_GRID))
+    return fail(LB_EINVAL, "the running penalty runs in the one-CTA-per-state and cluster sweeps only (N^2 <= 4096)");
   if (s->method != LB_SOLVER_GMRES) return LB_OK;
   if (s->sweep == LB_SWEEP_GRID || s->sweep == LB_SWEEP_CLUSTER)
     return fail(LB_EINVAL, "GMRES runs in the one-CTA-per-state sweep only (LB_SWEEP_RESIDENT or AUTO)");

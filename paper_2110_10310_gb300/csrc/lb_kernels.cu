@@ -1635,10 +1635,12 @@ __device__ ClAddr cl_addr(const ClSmem& S, const ClPlan& pl, int C, int crank) {
   return A;
 }
 
-// the control factors and stop factor of one step, loaded a step ahead
+// the control factors, stop factor and running-penalty weight of one step,
+// loaded a step ahead
 struct ClStep {
   double2 c;   // d_q or its Jaynes-Cummings factor for this lane's half
   double fac;  // stopping-test factor
+  double pen;  // dt beta(t_j) of the running penalty (0 without one)
 };
 // where they come from, resolved once per launch and kept in registers (the
 // problem record is in global memory and is reloaded after every asm
@@ -1646,12 +1648,14 @@ struct ClStep {
 struct ClSrc {
   const double2* ct;  // control table, this lane's column
   const double* sf;   // stop factors, or null (factor 1)
+  const double* pen;  // running-penalty weights, or null (no penalty)
   int cq;             // control table entries per step
 };
 __device__ __forceinline__ ClSrc cl_src(const ProbDev& P, const ClPlan& pl, int cq) {
   ClSrc src;
   src.ct = P.ctab + pl.q;
   src.sf = P.method == LB_SOLVER_JACOBI ? P.sfac : nullptr;
+  src.pen = P.gamma1 != 0.0 ? P.pen : nullptr;
   src.cq = cq;
   return src;
 }
@@ -1659,6 +1663,7 @@ __device__ __forceinline__ ClStep cl_step(const ClSrc& src, int j) {
   ClStep st;
   st.c = src.ct[(size_t)j * src.cq];
   st.fac = src.sf ? src.sf[j] : 1.0;
+  st.pen = src.pen ? src.pen[j] : 0.0;
   return st;
 }
 
@@ -1778,10 +1783,12 @@ __device__ int cl_start(const ClSmem& S, const ClPlan& pl, const ClAddr& A, doub
 
 // End of a step for this lane's element, given its z: this lane's
 // component of c_j = (I - dt/2 D) z - rhs (predictor on; returned in cc) and
-// of the next right-hand side 2 z - rhs (returned).  cl_commit records cc in
-// ring slot h.slot once the step has converged.
+// of the next right-hand side 2 z - rhs + src (returned; src is the lane's
+// component of the adjoint's running-penalty source, else 0).  cl_commit
+// records cc in ring slot h.slot once the step has converged.
 template <bool ADJ>
-__device__ __forceinline__ double cl_update(const ClPlan& pl, double2 z, double2 rhs, ClHist h, double& cc) {
+__device__ __forceinline__ double cl_update(const ClPlan& pl, double2 z, double2 rhs, ClHist h, double& cc,
+                                            double src = 0.0) {
   const int odd = pl.r & 1;
   const double zc = odd ? z.y : z.x, zo = odd ? z.x : z.y, rc = odd ? rhs.y : rhs.x;
   if (h.on) {
@@ -1789,7 +1796,7 @@ __device__ __forceinline__ double cl_update(const ClPlan& pl, double2 z, double2
     // real: dm.x z.x - b z.y - r.x, imaginary: dm.x z.y + b z.x - r.y
     cc = fma(pl.dmv.x, zc, fma(odd ? b : -b, zo, -rc));
   }
-  return fma(2.0, zc, -rc);
+  return fma(2.0, zc, -rc) + src;
 }
 __device__ __forceinline__ void cl_commit(const ClSmem& S, const ClPlan& pl, ClHist h, double cc) {
   if (h.on && pl.ev && pl.r < 2)
@@ -1820,7 +1827,7 @@ struct ClNext {
 template <int QT, bool ADJ, bool CS>
 __device__ int cl_iterate(const ClSmem& S, const ClPlan& pl, const ClAddr& A, const double2* z0, double2 rhs,
                           ClStep st, unsigned qmax, int C, ClCount& cnt, double2& zout, bool spec = false,
-                          ClHist hn = ClHist(), int sb = 0, ClNext* nx = nullptr) {
+                          ClHist hn = ClHist(), int sb = 0, ClNext* nx = nullptr, double src = 0.0) {
   constexpr int L = ClLanes<QT, CS>::L;
   const int V = pl.V;
   const bool neumann = pl.neu;
@@ -1887,7 +1894,7 @@ __device__ int cl_iterate(const ClSmem& S, const ClPlan& pl, const ClAddr& A, co
     unsigned dmax;
     if (spec) {
       double cc = 0.0;
-      const double rn = cl_update<ADJ>(pl, z, rhs, hn, cc);
+      const double rn = cl_update<ADJ>(pl, z, rhs, hn, cc, src);
       const double2 zn = cl_join(pl, cl_first_comp<L, ADJ>(S, pl, rn, hn, true, cc));
       const unsigned qn = (pl.ev && pl.r < 2) ? hi_abs(rn) : 0u;
       unsigned qnmax = 0u;
@@ -1920,8 +1927,12 @@ __device__ __forceinline__ int cl_code(int it) { return it == -1 ? LB_ENOTCONV :
 // J_i over the cluster: this CTA's own elements (lanes r == 0), summed per
 // CTA in a fixed order and gathered in CTA 0's shared memory; the cluster
 // barrier that follows makes them visible there.
+//
+// With the running penalty each own lane also holds pacc, the sum over the
+// steps of dt beta(t_j) f(q^j) for its element (f the merit summand), which
+// is summed the same way into the second slot set.
 __device__ void cl_objective_part(const ClSmem& S, const ClPlan& pl, const ProbDev& P, size_t base, double2 q,
-                                  int crank) {
+                                  int crank, double pacc = 0.0) {
   const Hdr& H = *S.hdr;
   double acc = 0.0;
   if (pl.ev && pl.r == 0) {
@@ -1935,14 +1946,32 @@ __device__ void cl_objective_part(const ClSmem& S, const ClPlan& pl, const ProbD
     }
   }
   acc = warp_sum(acc);
-  if ((threadIdx.x & 31) == 0) S.gred[threadIdx.x >> 5] = acc;
+  const double pw = H.gamma1 != 0.0 ? warp_sum(pacc) : 0.0;
+  if ((threadIdx.x & 31) == 0) {
+    S.gred[threadIdx.x >> 5] = acc;
+    S.gred[8 + (threadIdx.x >> 5)] = pw;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += S.gred[w];
+    double t = 0.0, u = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      t += S.gred[w];
+      u += S.gred[8 + w];
+    }
     const unsigned dst = mapa_u32(smem_u32(&S.gred[32 + crank]), 0);
     asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(dst), "d"(t) : "memory");
+    const unsigned dsu = mapa_u32(smem_u32(&S.gred[48 + crank]), 0);
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(dsu), "d"(u) : "memory");
   }
+}
+
+// the merit summand f of this lane's element for state value q and target t
+__device__ __forceinline__ double cl_merit_summand(int kind, double2 q, double2 t) {
+  if (kind == LB_J_FROB) {
+    const double dr = q.x - t.x, dq = q.y - t.y;
+    return fma(dr, dr, dq * dq);
+  }
+  return fma(t.x, q.x, t.y * q.y);
 }
 
 template <int QT, bool CS>
@@ -1964,6 +1993,12 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
   // this lane's element in the checkpoints (K > 0) or the stage tape (K == 0), step 0
   double2* const tp0 = P.ckpt + (K > 0 ? (size_t)i * H.n_ckpt * V : (size_t)i * NT * V) + pl.v;
   double2 rhs = P.q0[base + pl.v];
+  // running penalty gamma1 sum_j dt beta(t_j) J(q^j) (Sec. III, eq. optimproblem):
+  // J is affine in the merit sum, so each own lane accumulates
+  // sum_j dt beta(t_j) f(q^j) for its element, and ppen = sum_j dt beta(t_j)
+  const bool penal = H.gamma1 != 0.0;
+  const double2 tv = penal && own ? P.tar[base + pl.v] : make_double2(0.0, 0.0);
+  double pacc = 0.0, ppen = 0.0;
   ClCount cnt;
   CtaStats stats;
   bool failed = false;
@@ -1982,6 +2017,10 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
     if (tape && K > 0 && j % K == 0 && own) tp0[(size_t)(j / K) * V] = rhs;
     const ClStep st = nx;
     if (j + 1 < NT) nx = cl_step(src, j + 1);
+    if (penal) {
+      if (own) pacc = fma(st.pen, cl_merit_summand(H.kind, rhs, tv), pacc);
+      ppen += st.pen;
+    }
     ClHist hn = hist;
     if (hist.on) hn.advance();
     const bool spec = j + 1 < NT;
@@ -2007,13 +2046,19 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
     }
     hist = hn;
   }
-  if (!failed) cl_objective_part(S, pl, P, base, rhs, crank);
+  if (!failed) cl_objective_part(S, pl, P, base, rhs, crank, pacc);
   stats.flush(P.status);
   cl.sync();  // the partial sums are in CTA 0; no CTA leaves while another may still push into it
   if (!failed && crank == 0 && threadIdx.x == 0) {
-    double t = 0.0;
-    for (int c = 0; c < C; ++c) t += S.gred[32 + c];
-    P.J[i] = merit_value(H.kind, t);
+    double t = 0.0, u = 0.0;
+    for (int c = 0; c < C; ++c) {
+      t += S.gred[32 + c];
+      u += S.gred[48 + c];
+    }
+    double J = merit_value(H.kind, t);
+    // sum_j pen_j merit(S_j) = a sum_j pen_j S_j + b sum_j pen_j for merit(S) = a S + b
+    if (penal) J += H.gamma1 * (merit_value(H.kind, u) - merit_value(H.kind, 0.0) + merit_value(H.kind, 0.0) * ppen);
+    P.J[i] = J;
   }
 }
 
@@ -2058,6 +2103,14 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
   ClHist ahist = H.method != LB_SOLVER_NEUMANN ? cl_hist_on() : ClHist();
   ClHist none;
   const bool own = pl.ev && pl.r == 0;
+  // running penalty: its adjoint source gamma1 beta_i/M dt beta(t_j) g(q^j)
+  // (Appendix B) needs q^j, rebuilt backwards q^j = 2 z^j - q^{j+1} from the
+  // stage vectors, starting from q^{N_T}, in the registers of each element's lanes
+  const bool penal = H.gamma1 != 0.0;
+  const double g1w = H.gamma1 * w, ls = linear_sign(H.kind);
+  const int kind = H.kind;
+  const double2 tv = penal ? P.tar[base + pl.v] : make_double2(0.0, 0.0);
+  double2 qb = penal ? P.qT[base + pl.v] : make_double2(0.0, 0.0);
   // gradient pieces of this warp go to state slot (i * C + crank) * nwarps + warp of gproj
   double2* gbase = P.gproj + (size_t)((i * C + crank) * nwarps + warp) * NT * Qn * 2;
   for (int sg = nseg - 1; sg >= 0 && !failed; --sg) {
@@ -2107,20 +2160,30 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
     // this lane's stage vector element of step j, loaded one step ahead so
     // that its latency is hidden behind a whole step
     const bool gl = pl.act;
+    const bool zl = gl || (penal && pl.ev);  // lanes that need the stage vector
     const double2* tape = K > 0 ? P.seg + (size_t)i * K * V : P.ckpt + (size_t)i * NT * V;
     const int jt = K > 0 ? j0 : 0;  // tape row of step j is j - jt
-    double2 Znx = gl ? tape[(size_t)(j1 - 1 - jt) * V + pl.v] : make_double2(0.0, 0.0);
+    double2 Znx = zl ? tape[(size_t)(j1 - 1 - jt) * V + pl.v] : make_double2(0.0, 0.0);
     for (int j = j1 - 1; j >= j0; --j) {
       const double2 Z = Znx;
-      if (gl && j > j0) Znx = tape[(size_t)(j - 1 - jt) * V + pl.v];
+      if (zl && j > j0) Znx = tape[(size_t)(j - 1 - jt) * V + pl.v];
       const ClStep st = nx;
       if (j > j0) nx = cl_step(src, j - 1);
+      // this lane's component of the penalty source, added to qhat^j
+      double psrc = 0.0;
+      if (penal) {
+        const double2 qj = make_double2(fma(2.0, Z.x, -qb.x), fma(2.0, Z.y, -qb.y));
+        qb = qj;
+        const double gc = kind == LB_J_FROB ? cl_comp(pl, qj) - cl_comp(pl, tv) : ls * cl_comp(pl, tv);
+        psrc = (g1w * st.pen) * gc;
+      }
       ClHist hn = ahist;
       if (ahist.on) hn.advance();
       const bool spec = j > j0;
       ClNext nxt;
       double2 zh;
-      const int it = cl_iterate<QT, true, CS>(S, pl, A, z0, ll, st, qmax, C, cnt, zh, spec, hn, (j - 1) & 1, &nxt);
+      const int it =
+          cl_iterate<QT, true, CS>(S, pl, A, z0, ll, st, qmax, C, cnt, zh, spec, hn, (j - 1) & 1, &nxt, psrc);
       if (it < 0) {
         if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
         failed = true;
@@ -2173,8 +2236,8 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
           g[hi ? 0 : 1] = hi ? k : -k;
         }
       }
-      // qhat^j = 2 zhat - qhat^{j+1}; within a segment the next step's first
-      // iterate is already in every CTA
+      // qhat^j = 2 zhat - qhat^{j+1} (+ the penalty source); within a segment
+      // the next step's first iterate is already in every CTA
       if (spec) {
         cl_commit(S, pl, ahist, nxt.cc);
         ll = cl_join(pl, nxt.rn);
@@ -2182,7 +2245,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
         z0 = S.zs + (size_t)((j - 1) & 1) * V;
       } else {
         double cc = 0.0;
-        const double rn = cl_update<true>(pl, zh, ll, ahist, cc);
+        const double rn = cl_update<true>(pl, zh, ll, ahist, cc, psrc);
         cl_commit(S, pl, ahist, cc);
         ll = cl_join(pl, rn);
       }

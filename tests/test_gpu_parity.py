@@ -740,7 +740,11 @@ def test_running_penalty_matches_oracle(levels, objective, K, solver):
     p.gamma1, p.penalty_a = 0.6, 0.3
     sv = {"jacobi": L.LB_SOLVER_JACOBI, "gmres": L.LB_SOLVER_GMRES}[solver]
     s, _ = _check_problem(p, solver=sv)
-    assert s.stats()["sweep"] == "resident"
+    assert s.stats()["sweep"] == ("resident" if solver == "gmres" else "cluster")
+    if solver != "gmres":
+        # the one-CTA sweep computes the same penalty
+        s_r, _ = _check_problem(p, solver=sv, sweep=L.LB_SWEEP_RESIDENT)
+        assert s_r.stats()["sweep"] == "resident"
 
 
 def test_running_penalty_with_jnm_and_sweep_rules():
@@ -748,10 +752,26 @@ def test_running_penalty_with_jnm_and_sweep_rules():
 
     p = W.reset_ensemble(levels=(2, 3), n_steps=300, T_ns=15.0, n_splines=8, amp=0.05)
     p.gamma1, p.penalty_a = 0.4, 5.0
-    _check_problem(p)
-    for sweep in (L.LB_SWEEP_GRID, L.LB_SWEEP_CLUSTER):
-        with pytest.raises(L.LBError):
-            _sys(p, sweep=sweep)
+    for sweep in (L.LB_SWEEP_AUTO, L.LB_SWEEP_CLUSTER, L.LB_SWEEP_RESIDENT):
+        _check_problem(p, sweep=sweep)
+    with pytest.raises(L.LBError):
+        _sys(p, sweep=L.LB_SWEEP_GRID)
+
+
+def test_running_penalty_cluster_checkpoints_bitwise():
+    """With the penalty, the cluster sweep's gradient is still bit-identical
+    across checkpoint intervals K >= 1 and agrees with K = 0."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(122, levels=(3, 3), n_states=2, n_steps=45, T_ns=0.9, amp=0.1, gamma2=0.05)
+    p.gamma1, p.penalty_a = 0.6, 0.3
+    res = [_sys(p, ckpt_every=K, sweep=L.LB_SWEEP_CLUSTER).gradient() for K in (1, 7, 100)]
+    for G, g in res[1:]:
+        assert G == res[0][0]
+        assert np.array_equal(g, res[0][1])
+    G0, g0 = _sys(p, ckpt_every=0, sweep=L.LB_SWEEP_CLUSTER).gradient()
+    assert abs(G0 - res[0][0]) <= 1e-13 * abs(res[0][0])
+    assert _rel(g0, res[0][1]) < 1e-12
 
 
 # ----------------------------------------------------------------------------

@@ -184,7 +184,9 @@ int effective_K(const lb_system* s) {
 // pair, make one half pair); C == 0 when it cannot apply.
 lbk::ClusterConfig cluster_cfg(const lb_system* s, bool cs) {
   if (use_grid(s) || s->sweep == LB_SWEEP_RESIDENT || s->method == LB_SOLVER_GMRES) return lbk::ClusterConfig{};
-  return lbk::cluster_config(s->V, s->Q + (int)s->jp.size(), n_coef(s), n_jcoef(s), s->N, cs);
+  lbk::ClusterConfig cc = lbk::cluster_config(s->V, s->Q + (int)s->jp.size(), n_coef(s), n_jcoef(s), s->N, cs);
+  cc.pen = s->gamma1 != 0.0;
+  return cc;
 }
 
 // complex values of the GMRES Krylov basis in shared memory (0 for the

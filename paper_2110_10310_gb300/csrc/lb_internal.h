@@ -168,6 +168,7 @@ struct ClusterConfig {
   int threads;  // threads per CTA
   size_t smem;  // dynamic shared memory per CTA
   bool cs;      // 4Q lanes per element (one per half and component) instead of 2Q
+  bool pen;     // the running penalty (its own kernel instantiation)
 };
 ClusterConfig cluster_config(int V, int Q, int ncoef, int njcoef, int N, bool cs);
 cudaError_t launch_forward_cluster(const ProbDev* d_prob, int M, int tape, const ClusterConfig& cc, cudaStream_t s);

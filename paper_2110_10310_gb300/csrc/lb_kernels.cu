@@ -1931,8 +1931,9 @@ __device__ __forceinline__ int cl_code(int it) { return it == -1 ? LB_ENOTCONV :
 // With the running penalty each own lane also holds pacc, the sum over the
 // steps of dt beta(t_j) f(q^j) for its element (f the merit summand), which
 // is summed the same way into the second slot set.
+template <bool PEN>
 __device__ void cl_objective_part(const ClSmem& S, const ClPlan& pl, const ProbDev& P, size_t base, double2 q,
-                                  int crank, double pacc = 0.0) {
+                                  int crank, double pacc) {
   const Hdr& H = *S.hdr;
   double acc = 0.0;
   if (pl.ev && pl.r == 0) {
@@ -1946,7 +1947,7 @@ __device__ void cl_objective_part(const ClSmem& S, const ClPlan& pl, const ProbD
     }
   }
   acc = warp_sum(acc);
-  const double pw = H.gamma1 != 0.0 ? warp_sum(pacc) : 0.0;
+  const double pw = PEN ? warp_sum(pacc) : 0.0;
   if ((threadIdx.x & 31) == 0) {
     S.gred[threadIdx.x >> 5] = acc;
     S.gred[8 + (threadIdx.x >> 5)] = pw;
@@ -1974,7 +1975,9 @@ __device__ __forceinline__ double cl_merit_summand(int kind, double2 q, double2 
   return fma(t.x, q.x, t.y * q.y);
 }
 
-template <int QT, bool CS>
+// PEN: the running penalty (a separate instantiation, so that the sweeps
+// without it keep their registers)
+template <int QT, bool CS, bool PEN>
 __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict__ pp, int tape) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
@@ -1996,7 +1999,7 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
   // running penalty gamma1 sum_j dt beta(t_j) J(q^j) (Sec. III, eq. optimproblem):
   // J is affine in the merit sum, so each own lane accumulates
   // sum_j dt beta(t_j) f(q^j) for its element, and ppen = sum_j dt beta(t_j)
-  const bool penal = H.gamma1 != 0.0;
+  constexpr bool penal = PEN;
   const double2 tv = penal && own ? P.tar[base + pl.v] : make_double2(0.0, 0.0);
   double pacc = 0.0, ppen = 0.0;
   ClCount cnt;
@@ -2046,7 +2049,7 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
     }
     hist = hn;
   }
-  if (!failed) cl_objective_part(S, pl, P, base, rhs, crank, pacc);
+  if (!failed) cl_objective_part<PEN>(S, pl, P, base, rhs, crank, pacc);
   stats.flush(P.status);
   cl.sync();  // the partial sums are in CTA 0; no CTA leaves while another may still push into it
   if (!failed && crank == 0 && threadIdx.x == 0) {
@@ -2062,7 +2065,7 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
   }
 }
 
-template <int QT, bool CS>
+template <int QT, bool CS, bool PEN>
 __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restrict__ pp) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
@@ -2106,7 +2109,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
   // running penalty: its adjoint source gamma1 beta_i/M dt beta(t_j) g(q^j)
   // (Appendix B) needs q^j, rebuilt backwards q^j = 2 z^j - q^{j+1} from the
   // stage vectors, starting from q^{N_T}, in the registers of each element's lanes
-  const bool penal = H.gamma1 != 0.0;
+  constexpr bool penal = PEN;
   const double g1w = H.gamma1 * w, ls = linear_sign(H.kind);
   const int kind = H.kind;
   const double2 tv = penal ? P.tar[base + pl.v] : make_double2(0.0, 0.0);
@@ -3414,17 +3417,9 @@ ClusterConfig cluster_config(int V, int Q, int ncoef, int njcoef, int N, bool cs
 
 template <int QT, bool CS>
 struct ClKernels {
-  static cudaError_t attrs(size_t smem) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_forward_cl<QT, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_backward_cl<QT, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_propagate_cl<QT, CS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  }
   template <class K, class... Args>
   static cudaError_t launch(K kern, const ClusterConfig& cc, int n_states, cudaStream_t s, Args... args) {
-    cudaError_t e = attrs(cc.smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cc.smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(n_states * cc.C);
@@ -3460,11 +3455,14 @@ struct ClKernels {
   } while (0)
 
 cudaError_t launch_forward_cluster(const ProbDev* d_prob, int M, int tape, const ClusterConfig& cc, cudaStream_t s) {
-  LB_CL_DISPATCH(cc, return ClKernels<QT_, CSV_>::launch(k_forward_cl<QT_, CSV_>, cc, M, s, d_prob, tape););
+  LB_CL_DISPATCH(cc, return cc.pen ? ClKernels<QT_, CSV_>::launch(k_forward_cl<QT_, CSV_, true>, cc, M, s, d_prob, tape)
+                                   : ClKernels<QT_, CSV_>::launch(k_forward_cl<QT_, CSV_, false>, cc, M, s, d_prob,
+                                                                  tape););
 }
 
 cudaError_t launch_backward_cluster(const ProbDev* d_prob, int M, const ClusterConfig& cc, cudaStream_t s) {
-  LB_CL_DISPATCH(cc, return ClKernels<QT_, CSV_>::launch(k_backward_cl<QT_, CSV_>, cc, M, s, d_prob););
+  LB_CL_DISPATCH(cc, return cc.pen ? ClKernels<QT_, CSV_>::launch(k_backward_cl<QT_, CSV_, true>, cc, M, s, d_prob)
+                                   : ClKernels<QT_, CSV_>::launch(k_backward_cl<QT_, CSV_, false>, cc, M, s, d_prob););
 }
 
 cudaError_t launch_propagate_cluster(const ProbDev* d_prob, int adjoint, int64_t j0, int64_t j1, double2* x, int n_vec,

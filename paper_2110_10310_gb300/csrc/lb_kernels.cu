@@ -1786,7 +1786,7 @@ __device__ int cl_start(const ClSmem& S, const ClPlan& pl, const ClAddr& A, doub
 // of the next right-hand side 2 z - rhs + src (returned; src is the lane's
 // component of the adjoint's running-penalty source, else 0).  cl_commit
 // records cc in ring slot h.slot once the step has converged.
-template <bool ADJ>
+template <bool ADJ, bool SRC = false>
 __device__ __forceinline__ double cl_update(const ClPlan& pl, double2 z, double2 rhs, ClHist h, double& cc,
                                             double src = 0.0) {
   const int odd = pl.r & 1;
@@ -1796,7 +1796,9 @@ __device__ __forceinline__ double cl_update(const ClPlan& pl, double2 z, double2
     // real: dm.x z.x - b z.y - r.x, imaginary: dm.x z.y + b z.x - r.y
     cc = fma(pl.dmv.x, zc, fma(odd ? b : -b, zo, -rc));
   }
-  return fma(2.0, zc, -rc) + src;
+  // SRC: a source term exists (its addition is compiled out otherwise)
+  if constexpr (SRC) return fma(2.0, zc, -rc) + src;
+  return fma(2.0, zc, -rc);
 }
 __device__ __forceinline__ void cl_commit(const ClSmem& S, const ClPlan& pl, ClHist h, double cc) {
   if (h.on && pl.ev && pl.r < 2)
@@ -1824,7 +1826,7 @@ struct ClNext {
 // computed from its own z as if it were the converged one (hist hn: the
 // predictor state of the next step), into spec buffer sb, so a step that
 // converges needs no further exchange; nx returns what the next step needs.
-template <int QT, bool ADJ, bool CS>
+template <int QT, bool ADJ, bool CS, bool SRC = false>
 __device__ int cl_iterate(const ClSmem& S, const ClPlan& pl, const ClAddr& A, const double2* z0, double2 rhs,
                           ClStep st, unsigned qmax, int C, ClCount& cnt, double2& zout, bool spec = false,
                           ClHist hn = ClHist(), int sb = 0, ClNext* nx = nullptr, double src = 0.0) {
@@ -1894,7 +1896,7 @@ __device__ int cl_iterate(const ClSmem& S, const ClPlan& pl, const ClAddr& A, co
     unsigned dmax;
     if (spec) {
       double cc = 0.0;
-      const double rn = cl_update<ADJ>(pl, z, rhs, hn, cc, src);
+      const double rn = cl_update<ADJ, SRC>(pl, z, rhs, hn, cc, src);
       const double2 zn = cl_join(pl, cl_first_comp<L, ADJ>(S, pl, rn, hn, true, cc));
       const unsigned qn = (pl.ev && pl.r < 2) ? hi_abs(rn) : 0u;
       unsigned qnmax = 0u;
@@ -2186,7 +2188,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
       ClNext nxt;
       double2 zh;
       const int it =
-          cl_iterate<QT, true, CS>(S, pl, A, z0, ll, st, qmax, C, cnt, zh, spec, hn, (j - 1) & 1, &nxt, psrc);
+          cl_iterate<QT, true, CS, PEN>(S, pl, A, z0, ll, st, qmax, C, cnt, zh, spec, hn, (j - 1) & 1, &nxt, psrc);
       if (it < 0) {
         if (threadIdx.x == 0 && crank == 0) record_error(P.status, cl_code(it), j);
         failed = true;
@@ -2248,7 +2250,7 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
         z0 = S.zs + (size_t)((j - 1) & 1) * V;
       } else {
         double cc = 0.0;
-        const double rn = cl_update<true>(pl, zh, ll, ahist, cc, psrc);
+        const double rn = cl_update<true, PEN>(pl, zh, ll, ahist, cc, psrc);
         cl_commit(S, pl, ahist, cc);
         ll = cl_join(pl, rn);
       }

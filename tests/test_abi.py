@@ -207,3 +207,29 @@ def test_gmres_is_accepted_and_never_grid(lib):
     V, M = 1024, 2
     # grid sweeps add the four iteration buffers of M states each
     assert sizes[L.LB_SOLVER_JACOBI] - sizes[L.LB_SOLVER_GMRES] >= 4 * 16 * M * V
+
+
+def test_cluster_sweep_rules_for_coupled_pairs(lib):
+    """A Jaynes-Cummings pair adds a half pair to the cluster sweep's lane
+    plan: two subsystems with one pair (three half pairs) may choose it,
+    three subsystems with all three pairs (six) may not; the choice is made
+    on the host, before any device work."""
+    ok = W.random_problem(41, levels=(2, 3), n_states=2, n_steps=10, jc=0.05)
+    bad = W.random_problem(42, levels=(2, 2, 2), n_states=2, n_steps=10, jc=0.05)
+    for prob, want in ((ok, L.LB_OK), (bad, L.LB_EINVAL)):
+        h = _make(lib, prob, K=10)
+        try:
+            Q = len(prob.system.levels)
+            g = np.ascontiguousarray(np.asarray(prob.system.jc_ghz, dtype=np.float64).reshape(Q * Q))
+            r = np.ascontiguousarray(np.asarray(prob.system.rot_ghz, dtype=np.float64))
+            L.check(lib.lb_system_set_coupling(h, g.ctypes.data_as(POINTER(c_double)),
+                                               r.ctypes.data_as(POINTER(c_double))))
+            assert lib.lb_set_sweep(h, L.LB_SWEEP_CLUSTER) == want
+            if want != L.LB_OK:
+                assert b"pairs" in lib.lb_last_error()
+            # without the coupling the same three qubits fit the cluster sweep
+            zero = np.zeros(Q * Q)
+            L.check(lib.lb_system_set_coupling(h, zero.ctypes.data_as(POINTER(c_double)), None))
+            assert lib.lb_set_sweep(h, L.LB_SWEEP_CLUSTER) == L.LB_OK
+        finally:
+            lib.lb_system_destroy(h)

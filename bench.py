@@ -1,15 +1,20 @@
 #!/usr/bin/env python3
 """Benchmark of the implicit-midpoint Lindblad path on GB300.
 
-One bench step = one forward sweep plus the checkpointed discrete-adjoint
-gradient (Appendix A-B) of the 2-transmon CNOT workload: two 3-level
-transmons (N = 9, vec length 81), 16 essential-basis initial states,
-10000 implicit-midpoint steps over T = 200 ns, 20 splines x 2 carriers per
-transmon.  Metric: state-steps/s of forward + adjoint (16 x 10000 per step).
+Default workload (the largest single-GPU configuration of the method's
+targets): 6 qutrits (N = 729, vec(rho) of length 531441, complex FP64),
+64 random pure initial states, ring cross-Kerr, dt = 0.015 ns, 40 splines x 2
+carriers per qutrit, J_Frob to a random pure target, checkpoints every 100
+steps.  One bench step = one forward sweep plus the checkpointed discrete
+adjoint gradient (Appendices A-B) over the first 200 of the 20000 steps, so
+that two checkpoint segments, their recompute and the adjoint all run in the
+timed region.  Metric: state-steps/s of forward + adjoint (64 x 200 per step);
+the line also gives the forward-only rate.
 
 Prints one JSON line.  ``--impl reference`` times the CPU oracle instead (the
-reference arm); under torchrun each rank runs its own replica (weak scaling)
-and rank 0 prints the line.
+reference arm).  Under torchrun the initial states are split over the ranks
+(the paper's first level of parallelism) and (G, dG/dalpha) are summed with one
+all-reduce, the path's only exchange.
 """
 
 from __future__ import annotations
@@ -29,12 +34,15 @@ if ROOT not in sys.path:
 
 METRIC = "Lindblad state-steps/s (fwd+adjoint, FP64)"
 UNIT = "state-steps/s"
-WORKLOAD = ("cnot_2x3: 2 transmons x 3 levels (N=9, vec 81), 16 essential-basis states |i><j|, "
-            "10000 IMR steps, T=200 ns, 2x20 splines x 2 carriers, J_Frob to CNOT, "
-            "forward + adjoint gradient (stage vectors kept when the tape fits 8 GiB, else checkpoints)")
-# other workloads (--workload), measured the same way; the default line is cnot_2x3
+DEFAULT_WORKLOAD = "qutrits_6x3"
 WORKLOADS = {
-    "cnot_2x3": WORKLOAD,
+    "qutrits_6x3": ("qutrits_6x3: 6 qutrits (N=729, vec 531441), {m} random pure states, ring cross-Kerr 0.003 GHz, "
+                    "T1 in [40,80] us, T2=T1/2, dt=0.015 ns, first {n} of 20000 steps, 6 controls x 2 carriers x "
+                    "40 splines, J_Frob to a random pure target, fwd + adjoint gradient with checkpoints every "
+                    "{k} steps, grid-wide sweep"),
+    "cnot_2x3": ("cnot_2x3: 2 transmons x 3 levels (N=9, vec 81), 16 essential-basis states |i><j|, "
+                 "10000 IMR steps, T=200 ns, 2x20 splines x 2 carriers, J_Frob to CNOT, "
+                 "forward + adjoint gradient (stage vectors kept when the tape fits 8 GiB, else checkpoints)"),
     "cnot_3states": ("cnot_3states: the cnot_2x3 system and controls with the three-state gate objective "
                      "(Sec. III-C: 3 Hermitian states, weights 20, 1, 1), 10000 steps, fwd + adjoint"),
     "reset_2x2x20": ("reset_2x2x20: 2 qubits + 20-level cavity (vec 6400) from the ensemble state, J_N0, "
@@ -43,29 +51,28 @@ WORKLOADS = {
     "batch256": ("batch256: 256 independent problems, Q in {1,2,3}, 2-4 levels (vec 4..4096), 3 random pure states "
                  "each, 5000 steps, T=100 ns, fwd + adjoint, one persistent launch per sweep captured in a CUDA graph"),
     "qudits_4x4": ("qudits_4x4: 4 qudits x 4 levels (vec 65536), 3 random pure states, dt=0.0125 ns, "
-                   "first {n} of 40000 steps, fwd + adjoint with checkpoints every 100 steps, grid-wide sweep"),
-    "qutrits_6x3": ("qutrits_6x3: 6 qutrits (vec 531441), {m} random pure states, dt=0.015 ns, "
-                    "first {n} of 20000 steps, fwd + adjoint with checkpoints every 10 steps, grid-wide sweep"),
+                   "first {n} of 40000 steps, fwd + adjoint with checkpoints every {k} steps, grid-wide sweep"),
     "apply_6x3": ("apply_6x3: y = M(t) x, the matrix-free Lindblad apply (lb_apply, one thread per element) on "
                   "{n} states of 6 qutrits (vec 531441, 8.5 MB each), x and y in HBM"),
     "cnot_penalty": ("cnot_penalty: the cnot_2x3 workload with the running penalty gamma1 int beta(t) J dt "
-                     "(gamma1 = 0.1, a = 20 ns: Sec. III, eq. optimproblem), one CTA per state, fwd + adjoint"),
+                     "(gamma1 = 0.1, a = 20 ns: Sec. III, eq. optimproblem), fwd + adjoint"),
     "cnot_jc": ("cnot_jc: the cnot_2x3 workload with a Jaynes-Cummings coupling of the two transmons "
                 "(g = 5 MHz, rotating frequencies 4.80 and 4.86 GHz: the coupling rotates at 60 MHz), "
-                "one CTA per state, fwd + adjoint"),
+                "fwd + adjoint"),
     "fock_lbfgs": ("fock_lbfgs: one 4-level qudit |0> -> (|0>+|3>)/sqrt 2, J_Frob, 10 splines x 2 carriers, "
                    "T=200 ns, 10000 steps; one bench step = one L-BFGS run (lb_optimize, memory 10, "
                    "at most 150 iterations, gtol 1e-9) from the seeded controls"),
 }
-PREFIX = {"qudits_4x4": 2000, "qutrits_6x3": 40, "reset_2x2x20": 2000}
-SM_COUNT = 152
-SM_MAX_MHZ = 2070.0
+PREFIX = {"qudits_4x4": 2000, "qutrits_6x3": 200, "reset_2x2x20": 2000}
 FP64_FLOP_PER_CLK_PER_SM = 4.0  # 2 FP64 FMA lanes per SM per clock, 2 flops each
-CPU_SAMPLE_STEPS = 8000  # oracle sample for the CPU baseline (same dt, 16 states)
-REF_SAMPLE_STEPS = 400  # oracle sample per reference-arm step
+E2E_STEPS = 3  # end-to-end steps through host buffers (each re-uploads every state)
+CPU_SAMPLE_STEPS = 8000  # cnot_2x3 oracle sample (same dt, 16 states)
+REF_SAMPLE_STEPS = 400  # cnot_2x3 oracle sample per reference-arm step
+REDUCED_LEVELS = (2, 2, 2, 2, 2, 2)  # qutrits_6x3 reduced to qubits for the dense oracle (vec 4096)
+REDUCED_STEPS = 1  # oracle steps per reduced-shape sample
 
 
-def problem(n_steps=None, workload="cnot_2x3", states=0):
+def problem(n_steps=None, workload=DEFAULT_WORKLOAD, states=0, levels=None):
     import workloads as W
 
     if workload == "qubit_x":
@@ -79,8 +86,7 @@ def problem(n_steps=None, workload="cnot_2x3", states=0):
         p = W.config4()
         n_steps = n_steps or PREFIX[workload]
     elif workload == "qutrits_6x3":
-        p = W.config5(n_states=states or 64)
-        p.ckpt_every = 10
+        p = W.config5(n_states=states or 64, levels=levels or (3,) * 6)
         n_steps = n_steps or PREFIX[workload]
     elif workload == "cnot_penalty":
         p = W.config2()
@@ -94,41 +100,92 @@ def problem(n_steps=None, workload="cnot_2x3", states=0):
     else:
         p = W.config2()
     if n_steps is not None:
-        # a prefix of the horizon at the same step size dt = 0.02 ns
+        # a prefix of the horizon at the workload's step size dt
         p.system.T_ns = p.system.T_ns * n_steps / p.system.n_steps
         p.system.n_steps = n_steps
     return p
+
+
+def static_config(workload: str, p) -> dict:
+    """The workload as both arms name it (the reference arm prints the same)."""
+    K = p.ckpt_every
+    c = {"workload": WORKLOADS[workload].format(n=p.system.n_steps, m=p.M, k=K), "states": p.M,
+         "n_steps": p.system.n_steps, "ckpt_every": K,
+         "l2": "flushed between timed steps (256 MiB write)"}
+    return c
 
 
 # ----------------------------------------------------------------------------
 # CPU oracle timing (reference arm and cpu_baseline)
 
 
-def oracle_sample(n_steps: int) -> dict:
+def oracle_sample(workload: str, n_steps: int, states: int = 0) -> dict:
+    """One oracle gradient (forward + adjoint, dense LU steps) on the sample
+    shape of ``workload``: the workload's first n_steps steps, or for
+    qutrits_6x3 its structure reduced to 2 levels per subsystem (vec 4096)."""
     from oracle import imr
 
-    p = problem(n_steps)
+    if workload == "qutrits_6x3":
+        p = problem(n_steps, workload, states=states, levels=REDUCED_LEVELS)
+    else:
+        p = problem(n_steps, workload)
     t0 = time.perf_counter()
     imr.gradient(p)
     dt = time.perf_counter() - t0
-    return {"seconds": dt, "state_steps": p.M * n_steps}
+    N = 1
+    for n in p.system.levels:
+        N *= n
+    return {"seconds": dt, "state_steps": p.M * n_steps, "vec": N * N}
 
 
-def oracle_subprocess(n_steps: int, reps: int = 1) -> dict:
-    """Run the oracle sample in a fresh single-threaded process (BLAS pinned to
-    one thread) and return the best of ``reps`` runs."""
+def _thread_env(threads: int) -> dict:
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
-        env[k] = "1"
+        env[k] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
-    best = None
-    for _ in range(reps):
-        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(n_steps)],
-                             capture_output=True, text=True, env=env, check=True)
-        r = json.loads(out.stdout.strip().splitlines()[-1])
-        if best is None or r["seconds"] < best["seconds"]:
-            best = r
-    return best
+    return env
+
+
+def oracle_subprocess(workload: str, n_steps: int, threads: int, states: int = 0) -> dict:
+    """Run one oracle sample in a fresh process with BLAS pinned to ``threads``
+    threads (spawned, never forked from a process that touched the GPU)."""
+    out = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample", str(n_steps),
+                          "--workload", workload, "--states", str(states)],
+                         capture_output=True, text=True, env=_thread_env(threads), check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def extrapolate_dense(rate: float, vec_sample: int, vec_full: int) -> float:
+    """State-steps/s of the dense-LU oracle extrapolated from a sample of vec
+    length vec_sample to vec_full: a step's cost is dominated by the LU
+    factorisation of the vec x vec matrix, which grows as vec^3."""
+    return rate * (vec_sample / vec_full) ** 3
+
+
+def cpu_baseline(workload: str, p) -> dict | None:
+    cores = os.cpu_count() or 1
+    if workload == "qutrits_6x3":
+        r1 = oracle_subprocess(workload, REDUCED_STEPS, 1, states=p.M)
+        rn = oracle_subprocess(workload, REDUCED_STEPS, cores, states=p.M)
+        vfull = 729 * 729
+        v1 = r1["state_steps"] / r1["seconds"]
+        vn = rn["state_steps"] / rn["seconds"]
+        return {"value": extrapolate_dense(vn, rn["vec"], vfull), "unit": UNIT, "cores": cores, "kind": "oracle",
+                "extrapolated": True,
+                "sample": (f"dense-LU oracle gradient (forward + adjoint) on the workload's structure reduced to "
+                           f"2 levels per subsystem (6 qubits, vec {rn['vec']}), {p.M} states x {REDUCED_STEPS} step "
+                           f"at dt = 0.015 ns: {vn:.3g} state-steps/s on {cores} threads ({rn['seconds']:.1f} s), "
+                           f"{v1:.3g} on 1 thread ({r1['seconds']:.1f} s); value extrapolated to vec 531441 by the "
+                           f"vec^3 cost of the dense LU (a dense 531441^2 matrix is 4.5 TB)"),
+                "measured_reduced_all_cores": vn, "measured_reduced_one_thread": v1,
+                "one_thread_extrapolated": extrapolate_dense(v1, r1["vec"], vfull), "nproc": cores}
+    if workload == "cnot_2x3":
+        r1 = oracle_subprocess(workload, CPU_SAMPLE_STEPS, 1)
+        return {"value": r1["state_steps"] / r1["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                "nproc": cores,
+                "sample": f"dense-LU oracle gradient (forward + adjoint), 16 states x {CPU_SAMPLE_STEPS} of the "
+                          f"10000 steps at the same dt, one thread, {r1['seconds']:.1f} s"}
+    return None
 
 
 # ----------------------------------------------------------------------------
@@ -143,6 +200,7 @@ class ClockSampler:
     def __init__(self, gpu_id: str | None):
         self.proc = None
         self.gpu_id = gpu_id
+        self.lines = []
 
     def __enter__(self):
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
@@ -164,8 +222,6 @@ class ClockSampler:
                 self.proc.kill()
                 out, _ = self.proc.communicate()
             self.lines = [l for l in out.splitlines() if l.strip()]
-        else:
-            self.lines = []
 
     def summary(self):
         sms, mx, reasons = [], None, set()
@@ -188,12 +244,22 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
+def gpu_uuid(dev):
+    import torch
+
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        return None
+
+
 # ----------------------------------------------------------------------------
-# algorithmic FP64 work of the sweep kernels
+# algorithmic work of the sweep kernels
 
 
 def fp64_flops(V: int, Q: int, n_decay: int, st: dict, phase_set) -> float:
-    """FP64 flops (FMA = 2) of the Jacobi sweeps, from the iteration counts.
+    """FP64 flops (FMA = 2) of the Jacobi sweeps as the kernels compute them,
+    from the iteration counts.
 
     Per element and inner iteration: per subsystem 24 flops for the control
     term (two real-weighted neighbour pairs P, R and the complex control
@@ -212,26 +278,30 @@ def fp64_flops(V: int, Q: int, n_decay: int, st: dict, phase_set) -> float:
     return f
 
 
-def traffic_record(kernel: str):
-    """DRAM bytes per launch of ``kernel`` from the committed ncu summary, or
-    None when the kernel source changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
-    if not os.path.exists(path):
-        return None
-    rec = json.load(open(path)).get(kernel)
-    if not rec:
-        return None
-    src = os.path.join(ROOT, "paper_2110_10310_gb300", "csrc", "lb_kernels.cu")
-    if rec.get("code_sha256") != kernel_source_digest(src):
-        return None
-    return rec.get("dram_bytes_per_launch")
+def method_flops(V: int, Q: int, st: dict, phase_set) -> float:
+    """Algorithmic FP64 flops by the method's own count: one Lindblad apply
+    costs 8 + 36 Q flops per element (a complex diagonal term and, per
+    subsystem, the decay sandwich and the four control neighbours with their
+    complex factors), one per inner iteration; every adjoint step adds the
+    gradient pieces of eq. reducedgradient, 28 Q per element (the two
+    commutator combinations of each subsystem and their two complex dot
+    products).  ``V``: elements the sweep computes (see fp64_flops)."""
+    f = 0.0
+    for ph in phase_set:
+        f += V * (8 + 36 * Q) * st["phase_iterations"][ph]
+        if ph == 2:
+            f += V * 28 * Q * st["phase_steps"][ph]
+    return f
+
+
+BYTES_PER_ELEMENT_ITERATION = 48  # read the iterate and the right-hand side, write the new iterate
 
 
 def kernel_source_digest(path: str) -> str:
-    """SHA-256 of the kernel source with its // comments and blank lines
+    """SHA-256 of a kernel source with its // comments and blank lines
     removed: the counters stay valid across comment edits, not across code
-    edits.  (The kernel source has no block comments and no // inside string
-    literals.)"""
+    edits.  (The kernel sources have no block comments and no // inside
+    string literals.)"""
     lines = []
     for line in open(path, encoding="utf-8"):
         code = line.split("//", 1)[0].rstrip()
@@ -240,21 +310,67 @@ def kernel_source_digest(path: str) -> str:
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
+KERNEL_SOURCES = {
+    "k_backward_grid": ("lb_grid.cu", "lb_device.cuh"),
+    "k_sweep_grid": ("lb_grid.cu", "lb_device.cuh"),
+    "k_backward_cl": ("lb_cluster.cu", "lb_device.cuh"),
+    "k_forward_cl": ("lb_cluster.cu", "lb_device.cuh"),
+    "k_backward_res": ("lb_resident.cu", "lb_device.cuh"),
+    "k_forward_res": ("lb_resident.cu", "lb_device.cuh"),
+}
+
+
+def kernel_digest(kernel: str) -> str:
+    csrc = os.path.join(ROOT, "paper_2110_10310_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[kernel] + ("lb_internal.h",):
+        h.update(kernel_source_digest(os.path.join(csrc, f)).encode())
+    return h.hexdigest()
+
+
+def traffic_record(kernel: str, workload: str):
+    """The committed ncu DRAM record of ``kernel`` on ``workload``, or None
+    when there is none or the kernel code changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(f"{kernel}@{workload}")
+    if not rec or rec.get("code_sha256") != kernel_digest(kernel):
+        return None
+    return rec
+
+
 # ----------------------------------------------------------------------------
 
 
 def run_reference(args, rank: int, world: int):
+    """The reference arm: the dense-LU CPU oracle, timed as it stands on the
+    host cores, on a bounded sample of the same workload per step."""
     if rank != 0:
         return
+    wl = args.workload
+    p = problem(workload=wl, states=args.states)
+    cores = os.cpu_count() or 1
+    if wl == "qutrits_6x3":
+        def sample():
+            return oracle_sample(wl, REDUCED_STEPS, states=p.M)
+        sdesc = (f"per step: dense-LU oracle gradient on the workload reduced to 2 levels per subsystem "
+                 f"(6 qubits, vec 4096), {p.M} states x {REDUCED_STEPS} step, all {cores} threads; the value is "
+                 f"extrapolated to vec 531441 by the vec^3 cost of the dense LU")
+    else:
+        def sample():
+            return oracle_sample(wl, REF_SAMPLE_STEPS)
+        sdesc = f"per step: dense-LU oracle gradient, first {REF_SAMPLE_STEPS} steps of the workload, 1 thread"
     for _ in range(args.warmup):
-        oracle_sample(REF_SAMPLE_STEPS)
-    tot_s, tot_ss = 0.0, 0
+        sample()
+    tot_s, tot_ss, vec = 0.0, 0, 0
     for _ in range(args.steps):
-        r = oracle_sample(REF_SAMPLE_STEPS)
+        r = sample()
         tot_s += r["seconds"]
         tot_ss += r["state_steps"]
-    value = tot_ss / tot_s
-    cores = 1
+        vec = r["vec"]
+    rate = tot_ss / tot_s
+    value = extrapolate_dense(rate, vec, 729 * 729) if wl == "qutrits_6x3" else rate
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -265,13 +381,14 @@ def run_reference(args, rank: int, world: int):
         "warmup": args.warmup,
         "ms_per_step": 1e3 * tot_s / args.steps,
         "higher_is_better": True,
-        "scaling": "weak",
+        "scaling": "strong" if wl == "qutrits_6x3" else "weak",
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"first {REF_SAMPLE_STEPS} of 10000 steps per bench step, all 16 states"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"dense-LU oracle gradient, 16 states x {REF_SAMPLE_STEPS} steps per bench step"},
+        "config": static_config(wl, p),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores if wl == "qutrits_6x3" else 1,
+                         "kind": "oracle", "sample": sdesc, "measured_sample_rate": rate,
+                         "extrapolated": wl == "qutrits_6x3"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -285,6 +402,19 @@ def measured_peaks() -> dict:
         return json.load(open(path))
     except (OSError, ValueError):
         return {}
+
+
+def fp64_peak_tflops(dev, sm_mhz: float | None) -> tuple[float, str]:
+    """FP64 pipe peak of this GPU: 4 flops per SM per clock x the SM count
+    the device reports x the median SM clock sampled during the timed region
+    (the maximum clock when no sample was taken)."""
+    import torch
+
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = sm_mhz or measured_peaks().get("sm_max_mhz") or 2070.0
+    src = (f"FP64 pipe: 2 FMA lanes/SM/clk x 2 flops x {nsm} SMs (queried) x {mhz:.0f} MHz "
+           f"({'median sampled in the timed region' if sm_mhz else 'maximum clock'}); derived")
+    return FP64_FLOP_PER_CLK_PER_SM * nsm * mhz * 1e6 / 1e12, src
 
 
 def run_apply(args, rank, world, dev):
@@ -320,12 +450,7 @@ def run_apply(args, rank, world, dev):
         launch()
     torch.cuda.synchronize()
     ms = []
-    gpu_id = None
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        pass
-    with ClockSampler(gpu_id) as clk:
+    with ClockSampler(gpu_uuid(dev)) as clk:
         for _ in range(args.steps):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -341,7 +466,8 @@ def run_apply(args, rank, world, dev):
     nbytes = n * V * 32
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs") or 6800.0
-    fp64_peak = FP64_FLOP_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
+    clocks = clk.summary()
+    fp64_peak, src = fp64_peak_tflops(dev, clocks["sm_mhz"] if clocks else None)
     if rank == 0:
         line = {
             "metric": "Lindblad apply state-applies/s (FP64)",
@@ -366,13 +492,14 @@ def run_apply(args, rank, world, dev):
                 "peak": fp64_peak,
                 "unit": "TFLOP/s",
                 "frac": flops / t / 1e12 / fp64_peak,
+                "peak_source": src,
                 "hbm_achieved_gbs": nbytes / t / 1e9,
                 "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": nbytes / t / 1e9 / hbm_peak,
                 "traffic": None,
             },
             "gpu_launches": args.steps,
-            "clocks": clk.summary(),
+            "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
 
@@ -394,13 +521,8 @@ def run_optimize(args, rank, world, dev):
     for _ in range(args.warmup):
         s.gradient()
     torch.cuda.synchronize()
-    gpu_id = None
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        pass
     secs, res = [], None
-    with ClockSampler(gpu_id) as clk:
+    with ClockSampler(gpu_uuid(dev)) as clk:
         for _ in range(args.steps):
             s.set_alpha(a0)
             torch.cuda.synchronize()
@@ -449,7 +571,6 @@ def run_batch(args, rank, world, dev):
     """Workload batch256: one persistent launch per sweep over 256 uneven
     problems (captured in a CUDA graph), beside the plain form with one
     lb_gradient (its own launches) per problem on one stream."""
-    import numpy as np
     import torch
 
     import workloads as W
@@ -468,13 +589,8 @@ def run_batch(args, rank, world, dev):
     torch.cuda.synchronize()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     state_steps = sum(p.M * p.system.n_steps for p in probs)
-    gpu_id = None
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        pass
     ms = []
-    with ClockSampler(gpu_id) as clk:
+    with ClockSampler(gpu_uuid(dev)) as clk:
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
@@ -530,6 +646,180 @@ def run_batch(args, rank, world, dev):
         print(json.dumps(line), flush=True)
 
 
+def run_gradient(args, rank, world, dev, dist):
+    """Workloads timed as one lb_gradient per bench step (the default and the
+    single-problem ones).  With several ranks each rank holds its share of
+    the initial states and the per-rank (G, dG/dalpha) are summed."""
+    import numpy as np
+    import torch
+
+    from paper_2110_10310_gb300 import dist as D
+    from paper_2110_10310_gb300.system import LindbladSystem, colmajor
+
+    wl = args.workload
+    full = problem(workload=wl, states=args.states)
+    if args.ckpt is not None:
+        full.ckpt_every = args.ckpt
+    p = D.shard_problem(full, rank, world) if world > 1 else full
+    s = LindbladSystem(p, device=dev, predictor=args.predictor)
+    s.set_timing(True)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def step():
+        G, g = s.gradient()
+        if dist is not None:
+            G, g = D.allreduce_objective(G, g)
+        return G, g
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    state_steps = full.M * full.system.n_steps
+    ms_steps, ms_bwd, ms_fwd, launches, sts = [], [], [], 0, []
+    with ClockSampler(gpu_uuid(dev)) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms_steps.append(e0.elapsed_time(e1))
+            st = s.stats()
+            sts.append(st)
+            ms_bwd.append(st["ms_backward"])
+            ms_fwd.append(st["ms_forward"])
+            launches += st["kernel_launches"]
+    clocks = clk.summary()
+
+    def maxrank(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    total_ms = maxrank(sum(ms_steps))
+    value = state_steps * args.steps / (total_ms * 1e-3)
+    fwd_ms = maxrank(statistics.median(ms_fwd))
+    bwd_ms = statistics.median(ms_bwd)
+
+    # end to end through the public API with host buffers: pinned states and
+    # controls uploaded every step, G and the gradient read back every step
+    pinned = torch.from_numpy(colmajor(p.rho0)).pin_memory()
+    alpha = np.ascontiguousarray(p.controls.alpha)
+    e2e_n = min(args.steps, E2E_STEPS)
+    e2e_s = []
+    for i in range(e2e_n + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        s.set_states_host(pinned, p.weights)
+        s.set_alpha(alpha)
+        step()
+        t1 = time.perf_counter()
+        if i:
+            e2e_s.append(t1 - t0)
+    e2e_tot = maxrank(sum(e2e_s))
+    e2e_value = state_steps * e2e_n / e2e_tot
+    h2d = pinned.numel() * 8 + alpha.size * 8 + (0 if p.weights is None else 8 * p.M)
+    d2h = 8 + 8 * s.n_params + 64  # G, gradient, status block
+
+    # roofline of the dominant kernel, the backward sweep (recompute + adjoint)
+    Q = len(p.system.levels)
+    V = s.N * s.N
+    n_decay = int(sum(1 for t in p.system.t1_us if np.isfinite(t) and t > 0))
+    st = sts[-1]
+    Ve = s.N * (s.N + 1) // 2 if st["symmetry"] == "hermitian" else V
+    kernel_name = {"grid": "k_backward_grid", "cluster": "k_backward_cl"}.get(st["sweep"], "k_backward_res")
+    bwd_method = method_flops(Ve, Q, st, (1, 2))
+    bwd_impl = fp64_flops(Ve, Q, n_decay, st, (1, 2))
+    fwd_method = method_flops(Ve, Q, st, (0,))
+    fp64_peak, peak_src = fp64_peak_tflops(dev, clocks["sm_mhz"] if clocks else None)
+    achieved = bwd_method / (bwd_ms * 1e-3) / 1e12
+    elem_iters = Ve * (st["phase_iterations"][1] + st["phase_iterations"][2])
+    hbm_alg = BYTES_PER_ELEMENT_ITERATION * elem_iters
+    hbm_peak = measured_peaks().get("hbm_gbs") or 6800.0
+    trec = traffic_record(kernel_name, wl)
+    traffic = None
+    if trec:
+        # DRAM bytes of the capture scaled to this launch by the element-iterations
+        traffic = trec["dram_bytes"] / trec["element_iterations"] * elem_iters
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(wl, p)
+
+    if rank == 0:
+        inner = {ph: st["phase_iterations"][i] / max(1, st["phase_steps"][i])
+                 for i, ph in enumerate(("forward", "recompute", "adjoint"))}
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": UNIT,
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak",
+            "vs_baseline": None,
+            "dtype": "f64",
+            "data": "synthetic",
+            "config": static_config(wl, full),
+            "fwd_value": full.M * full.system.n_steps / (fwd_ms * 1e-3),
+            "fwd_unit": "state-steps/s (forward sweep kernel alone, device-timed inside lb_gradient)",
+            "detail": {
+                "parallelism": f"states sharded over {world} ranks, (G, grad) all-reduced" if world > 1 else "single",
+                "sweep": st["sweep"],
+                "symmetry": st["symmetry"],
+                "solver": f"{st['solver']} fixed point, rtol 1e-15",
+                "ckpt_every": st["ckpt_every"],
+                "predictor": args.predictor,
+                "inner_iters_per_step": inner,
+                "ms_forward_kernel": statistics.median(ms_fwd),
+                "ms_backward_kernel": bwd_ms,
+                "workspace_bytes": s.workspace_bytes,
+                "peak_device_bytes": int(torch.cuda.max_memory_allocated(dev)),
+                "fwd_fp64_tflops_method_count": fwd_method / (statistics.median(ms_fwd) * 1e-3) / 1e12,
+            },
+            "roofline": {
+                "kernel": kernel_name,
+                "bound": "alu",
+                "achieved": achieved,
+                "peak": fp64_peak,
+                "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak,
+                "peak_source": peak_src,
+                "flop_count": ("method count: (8 + 36 Q) per element per inner iteration + 28 Q per element per "
+                               "adjoint step (gradient pieces), over the elements the sweep computes "
+                               f"({Ve} per state: {'k <= l under the Hermitian symmetry' if Ve != V else 'all'})"),
+                "frac_instruction_count": bwd_impl / (bwd_ms * 1e-3) / 1e12 / fp64_peak,
+                "hbm_achieved_gbs": hbm_alg / (bwd_ms * 1e-3) / 1e9,
+                "hbm_peak_gbs": hbm_peak,
+                "hbm_frac": hbm_alg / (bwd_ms * 1e-3) / 1e9 / hbm_peak,
+                "hbm_bytes_count": f"{BYTES_PER_ELEMENT_ITERATION} B per element per inner iteration",
+                "traffic": traffic,
+                "traffic_source": (trec or {}).get("command"),
+            },
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_n},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -537,18 +827,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="cnot_2x3", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--states", type=int, default=0,
-                    help="initial states of qutrits_6x3 / apply_6x3 (default 64; smaller for ncu captures)")
+                    help="initial states of qutrits_6x3 / apply_6x3 (default 64; fewer for ncu captures)")
+    ap.add_argument("--ckpt", type=int, default=None, help="checkpoint interval (default: the workload's)")
+    ap.add_argument("--predictor", type=int, default=-1,
+                    help="forward predictor restart period (lb_set_predictor; -1 auto, -2 none)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
 
-    if args.oracle_sample or args.impl == "reference":
-        # the oracle runs single-threaded: BLAS pinned to one thread before numpy loads
-        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
-            os.environ[k] = "1"
     if args.oracle_sample:
-        print(json.dumps(oracle_sample(args.oracle_sample)))
+        print(json.dumps(oracle_sample(args.workload, args.oracle_sample, states=args.states)))
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -556,14 +845,15 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
 
     if args.impl == "reference":
+        if args.workload != "qutrits_6x3":
+            # the short-horizon samples run on one thread: BLAS pinned before numpy loads
+            os.environ.update({k: v for k, v in _thread_env(1).items() if k.endswith("_NUM_THREADS")})
         run_reference(args, rank, world)
         return
 
-    import numpy as np
     import torch
 
     from paper_2110_10310_gb300 import _lib
-    from paper_2110_10310_gb300.system import LindbladSystem, colmajor
 
     assert args.warmup >= 3 or os.environ.get("LB_BENCH_ALLOW_SHORT_WARMUP"), "need >= 3 warm-up steps"
     torch.cuda.set_device(local_rank)
@@ -574,158 +864,19 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     _lib.load(build_if_missing=True)
     dev = torch.device("cuda", local_rank)
-    if args.workload == "batch256":
-        return run_batch(args, rank, world, dev)
-    if args.workload == "fock_lbfgs":
-        return run_optimize(args, rank, world, dev)
-    if args.workload == "apply_6x3":
-        return run_apply(args, rank, world, dev)
-    p = problem(workload=args.workload, states=args.states)
-    s = LindbladSystem(p, device=dev)
-    s.set_timing(True)
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
-
-    def barrier():
+    try:
+        if args.workload == "batch256":
+            run_batch(args, rank, world, dev)
+        elif args.workload == "fock_lbfgs":
+            run_optimize(args, rank, world, dev)
+        elif args.workload == "apply_6x3":
+            run_apply(args, rank, world, dev)
+        else:
+            run_gradient(args, rank, world, dev, dist)
+    finally:
         if dist is not None:
             dist.barrier()
-
-    for _ in range(args.warmup):
-        s.gradient()
-    torch.cuda.synchronize()
-
-    gpu_id = None
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        gpu_id = None
-
-    state_steps = p.M * p.system.n_steps
-    ms_steps, ms_bwd, ms_fwd, launches = [], [], [], 0
-    sts = []
-    with ClockSampler(gpu_id) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
-            torch.cuda.synchronize()
-            barrier()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            s.gradient()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms_steps.append(e0.elapsed_time(e1))
-            st = s.stats()
-            sts.append(st)
-            ms_bwd.append(st["ms_backward"])
-            ms_fwd.append(st["ms_forward"])
-            launches += st["kernel_launches"]
-    total_ms = sum(ms_steps)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * state_steps * args.steps / (total_ms * 1e-3)
-
-    # end to end through the public API with host buffers: pinned states and
-    # controls uploaded every step, G and the gradient read back every step
-    pinned = torch.from_numpy(colmajor(p.rho0)).pin_memory()
-    alpha = np.ascontiguousarray(p.controls.alpha)
-    e2e_s = []
-    for i in range(args.steps + 1):
-        flush.zero_()
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        s.set_states_host(pinned, p.weights)
-        s.set_alpha(alpha)
-        G, g = s.gradient()
-        t1 = time.perf_counter()
-        if i:
-            e2e_s.append(t1 - t0)
-    e2e_tot = sum(e2e_s)
-    if dist is not None:
-        t = torch.tensor([e2e_tot], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = float(t.item())
-    e2e_value = world * state_steps * args.steps / e2e_tot
-    h2d = pinned.numel() * 8 + alpha.size * 8
-    d2h = 8 + 8 * s.n_params + 64  # G, gradient, status block
-
-    # roofline of the dominant kernel (the backward sweep: recompute + adjoint)
-    Q = len(p.system.levels)
-    V = s.N * s.N
-    n_decay = int(sum(1 for t in p.system.t1_us if np.isfinite(t) and t > 0))
-    st = sts[-1]
-    Ve = s.N * (s.N + 1) // 2 if st["symmetry"] == "hermitian" else V
-    bwd_flops = fp64_flops(Ve, Q, n_decay, st, (1, 2))
-    fwd_flops = fp64_flops(Ve, Q, n_decay, st, (0,))
-    bwd_ms = statistics.median(ms_bwd)
-    peak = FP64_FLOP_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = bwd_flops / (bwd_ms * 1e-3) / 1e12
-    kernel_name = {"grid": "k_backward_grid", "cluster": "k_backward_cl"}.get(st["sweep"], "k_backward_res")
-    traffic = traffic_record(kernel_name)
-    clocks = clk.summary()
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "cnot_2x3":
-        r = oracle_subprocess(CPU_SAMPLE_STEPS)
-        cpu = {"value": r["state_steps"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"dense-LU oracle gradient (forward + adjoint), 16 states x {CPU_SAMPLE_STEPS} of the "
-                         f"10000 steps at the same dt, one thread, {r['seconds']:.1f} s"}
-
-    if rank == 0:
-        line = {
-            "metric": METRIC,
-            "value": value,
-            "unit": UNIT,
-            "n_gpus": world,
-            "steps": args.steps,
-            "warmup": args.warmup,
-            "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True,
-            "scaling": "weak",
-            "vs_baseline": None,
-            "dtype": "f64",
-            "data": "synthetic",
-            "config": {
-                "workload": WORKLOADS[args.workload].format(n=p.system.n_steps, m=p.M),
-                "states": p.M,
-                "n_steps": p.system.n_steps,
-                "ckpt_every": st["ckpt_every"],
-                "tape_bytes": (p.M * p.system.n_steps * V * 16 if st["ckpt_every"] == 0
-                               else p.M * (-(-p.system.n_steps // st["ckpt_every"]) + st["ckpt_every"]) * V * 16),
-                "solver": f"{st['solver']} fixed point, rtol 1e-15",
-                "sweep": st["sweep"],
-                "symmetry": st["symmetry"],
-                "workspace_bytes": s.workspace_bytes,
-                "peak_device_bytes": int(torch.cuda.max_memory_allocated(dev)),
-                "l2": "flushed between timed steps (256 MiB write)",
-                "parallelism": f"replicas{world}" if world > 1 else "single",
-                "inner_iters_per_step": st["inner_iterations"] / max(1, st["state_steps"]),
-                "ms_forward_kernel": statistics.median(ms_fwd),
-                "ms_backward_kernel": bwd_ms,
-                "fwd_fp64_tflops": fwd_flops / (statistics.median(ms_fwd) * 1e-3) / 1e12,
-            },
-            "roofline": {
-                "kernel": kernel_name,
-                "bound": "alu",
-                "achieved": achieved,
-                "peak": peak,
-                "unit": "TFLOP/s",
-                "frac": achieved / peak,
-                "traffic": traffic,
-                "peak_source": "FP64 pipe: 2 FMA lanes/SM/clk x 2 flops x 152 SMs x 2070 MHz (derived)",
-            },
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches,
-            "clocks": clocks,
-            "cpu_baseline": cpu,
-        }
-        print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+            dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -213,6 +213,29 @@ int lb_objective_set_penalty(lb_system* sys, double gamma1, double a_ns);
 /* Choose the sweep kind (LB_SWEEP_*); call before lb_workspace_bytes. */
 int lb_set_sweep(lb_system* sys, int32_t sweep);
 
+/* First iterate of the inner solves of the forward sweep (Appendix A,
+ * eq. linsystem_primal; the paper does not say how its Krylov solve is
+ * started).  Every solve starts from (I - dt/2 D)^-1 (q^j + c~), c~ the
+ * extrapolation of the off-diagonal corrections c = (I - dt/2 D) z - q of the
+ * previous steps by the polynomial through them (order up to 7); the
+ * adjoint sweep always predicts this way.  `restart` says when the forward
+ * predictor forgets its history (it then rebuilds it over the next steps):
+ *   LB_PRED_AUTO (default): every K steps with checkpoints (K > 0), never
+ *     with the full stage tape (K = 0);
+ *   R > 0: at every step j with j % R == 0; with K > 0, R must divide K;
+ *   0: never; only with K = 0 (lb_bind_workspace fails with LB_EINVAL else);
+ *   LB_PRED_NONE: no forward predictor, the first iterate is
+ *     (I - dt/2 D)^-1 q^j.
+ * A checkpoint is always a restart point, so a recompute of a checkpoint
+ * segment repeats the forward sweep's iterates bit for bit: for a given
+ * restart period R the gradient with checkpoints every K (R | K) is bitwise
+ * that of the full tape (K = 0), and results for different R agree to
+ * rounding.  The cluster sweep (LB_SWEEP_CLUSTER) predicts its forward
+ * solves only with K = 0.  Call before lb_workspace_bytes. */
+#define LB_PRED_AUTO (-1)
+#define LB_PRED_NONE (-2)
+int lb_set_predictor(lb_system* sys, int32_t restart);
+
 /* Jaynes-Cummings coupling of the system Hamiltonian (Sec. II):
  *   sum_{p<q} g_pq (e^{i eta_pq t} a_p^+ a_q + e^{-i eta_pq t} a_p a_q^+),
  *   eta_pq = omega_p^rot - omega_q^rot,
@@ -339,12 +362,19 @@ int lb_set_timing(lb_system* sys, int32_t on);
  * or by anything it calls.  A problem whose lb_workspace_bytes exceeds
  * LB_STATIC_SCRATCH_BYTES is rejected with LB_ENOMEM.
  *
- * The first call on a device looks the array's device address up (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array and the call clears it before use:
- * calls that overlap on the GPU (other streams, other host threads, another
- * handle) race with each other and must be serialised by the caller.  The
- * call synchronises `stream` before it returns and leaves the handle unbound. */
+ * The call always runs one CTA per state: a handle given
+ * lb_set_sweep(LB_SWEEP_CLUSTER) (or a grid-sized problem) is refused with
+ * LB_EINVAL.  Each call looks the array's device address up with the current
+ * device current (the first call on a device also loads the module there:
+ * make it before any stream capture; during a capture the address found by
+ * the last call outside one is used).  All calls share the one array: every
+ * call clears the part of it the problem uses and uploads all of the
+ * handle's inputs again (states, targets, tables, controls), so each call
+ * pays that host-to-device copy, and calls that overlap on the GPU (other
+ * streams, other host threads, another handle) race with each other and
+ * must be serialised by the caller.  The call synchronises `stream` before it
+ * returns, on error returns too once device work was queued, and leaves the
+ * handle unbound. */
 int lb_gradient_static(lb_system* sys, void* stream, double* G_out, double* grad_out);
 
 /* ---- batches of independent problems ------------------------------------- */

@@ -26,6 +26,8 @@ LB_J_FROB = 0
 LB_J_TR = 1
 
 LB_CKPT_AUTO = -1
+LB_PRED_AUTO = -1
+LB_PRED_NONE = -2
 
 LB_SWEEP_AUTO = 0
 LB_SWEEP_RESIDENT = 1
@@ -41,7 +43,7 @@ LB_SYM_NONE = 0
 LB_SYM_HERMITIAN = 1
 
 LB_MAX_SUBSYSTEMS = 8
-LB_MAX_LEVELS = 16
+LB_MAX_LEVELS = 64
 LB_STATIC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 ERROR_NAMES = {1: "LB_EINVAL", 2: "LB_ENOMEM", 3: "LB_ECUDA", 4: "LB_ENOTCONV", 5: "LB_ENAN"}
@@ -99,6 +101,7 @@ SIGNATURES = {
     "lb_solver_set": (c_int32, [c_void_p, c_int32, c_double, c_int32, c_int32]),
     "lb_set_sweep": (c_int32, [c_void_p, c_int32]),
     "lb_set_symmetry": (c_int32, [c_void_p, c_int32]),
+    "lb_set_predictor": (c_int32, [c_void_p, c_int32]),
     "lb_system_set_coupling": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_double)]),
     "lb_workspace_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),
     "lb_bind_workspace": (c_int32, [c_void_p, c_void_p, c_size_t, c_void_p]),

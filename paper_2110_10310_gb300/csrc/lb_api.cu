@@ -48,7 +48,8 @@ struct Region {
 
 struct Layout {
   Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
-      gproj, gsum, sfac, pen, qb, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, hmap;
+      gproj, gsum, sfac, pen, qb, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, histf,
+      hmap;
   size_t total = 0;
 };
 
@@ -92,6 +93,7 @@ struct lb_system {
   int K = 100;       // requested checkpoint interval; < 0 = automatic (effective_K)
   int sweep = LB_SWEEP_AUTO;
   int symmetry = LB_SYM_HERMITIAN;
+  int pred = LB_PRED_AUTO;  // restart period of the forward predictor as requested (lb_set_predictor)
   double gamma1 = 0.0, pen_a = 1.0;  // running penalty (one CTA per state)
   bool rho_herm = false;  // every initial state exactly Hermitian
   bool tar_herm = false;  // every explicit target exactly Hermitian (gate targets: always)
@@ -178,6 +180,29 @@ int effective_K(const lb_system* s) {
   if (tape <= kTapeBudget) return 0;
   return s->NT < 100 ? (int)s->NT : 100;
 }
+
+// Restart period of the forward first-iterate predictor in effect:
+// LB_PRED_NONE (no forward predictor), 0 (never restarts, full stage tape
+// only) or R > 0 (restarts at every step j with j % R == 0; R divides K
+// with checkpoints, so that every checkpoint is a restart point).
+int effective_pred(const lb_system* s) {
+  if (s->method == LB_SOLVER_NEUMANN || s->pred == LB_PRED_NONE) return LB_PRED_NONE;
+  const int K = effective_K(s);
+  if (s->pred == LB_PRED_AUTO) return K;
+  return s->pred;
+}
+
+// every checkpoint must be a restart point of the forward predictor
+int check_predictor(const lb_system* s) {
+  const int K = effective_K(s), R = effective_pred(s);
+  if (K > 0 && R == 0) return fail(LB_EINVAL, "a predictor that never restarts needs the full stage tape (K = 0)");
+  if (K > 0 && R > 0 && K % R != 0)
+    return fail(LB_EINVAL, "the predictor's restart period must divide the checkpoint interval");
+  return LB_OK;
+}
+
+// the recompute needs its own predictor history when it predicts
+bool recompute_predicts(const lb_system* s) { return effective_K(s) > 0 && effective_pred(s) > 0; }
 
 // Cluster sweep configuration of this system with 2 or 4 lanes per half
 // pair (cs = false / true; a subsystem's control terms, or a Jaynes-Cummings
@@ -284,7 +309,8 @@ Layout make_layout(const lb_system* s) {
   take(L.partials, grid ? sizeof(double) * lbk::kMaxGridBlocks * LB_MAXQ * 4 : 0);
   take(L.gslots, grid ? sizeof(unsigned long long) * 5 * M : 0);
   take(L.bar, grid ? sizeof(GridBar) : 0);
-  take(L.hist, c2 * lbk::kPredOrder * M * V);
+  take(L.hist, c2 * lbk::kRingOrder * M * V);
+  take(L.histf, recompute_predicts(s) ? c2 * lbk::kRingOrder * M * V : 0);
   take(L.hmap, sizeof(int32_t) * (size_t)s->N * (s->N + 1) / 2);
   L.total = off;
   return L;
@@ -518,6 +544,8 @@ void fill_prob(lb_system* s) {
   P.hmap = at<int32_t>(s, s->L.hmap);
   P.herm = use_symmetry(s) ? 1 : 0;
   P.hist = at<double2>(s, s->L.hist);
+  P.histf = at<double2>(s, s->L.histf);
+  P.pred_restart = effective_pred(s);
 }
 
 int ensure_ctab(lb_system* s, cudaStream_t st) {
@@ -948,6 +976,14 @@ int lb_set_symmetry(lb_system* s, int32_t symmetry) {
   return refresh_symmetry(s);
 }
 
+int lb_set_predictor(lb_system* s, int32_t restart) {
+  if (!s) return fail(LB_EINVAL, "null system handle");
+  if (s->ws) return fail(LB_EINVAL, "set the predictor before binding a workspace");
+  if (restart < LB_PRED_NONE) return fail(LB_EINVAL, "restart must be >= 0, LB_PRED_AUTO or LB_PRED_NONE");
+  s->pred = restart;
+  return LB_OK;
+}
+
 int lb_set_sweep(lb_system* s, int32_t sweep) {
   if (!s) return fail(LB_EINVAL, "null system handle");
   if (s->ws) return fail(LB_EINVAL, "choose the sweep before binding a workspace");
@@ -979,6 +1015,8 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
     for (int q = 0; q < s->Q; ++q)
       if (s->essential[q] < 1) return fail(LB_EINVAL, "bad essential levels");
   }
+  rc = check_predictor(s);
+  if (rc) return rc;
   s->L = make_layout(s);
   if (bytes < s->L.total) return fail(LB_ENOMEM, "workspace smaller than lb_workspace_bytes");
   if (s->rho0.empty()) return fail(LB_EINVAL, "initial states are required before binding");
@@ -1636,13 +1674,18 @@ void* g_static_ptr[kMaxStaticDevices] = {};  // device address of the array, per
 
 // Device address of g_lb_static_scratch on the current device.  In host code
 // the array's name only denotes a host-side stand-in, so the address is looked
-// up once per device (with that device current) and cached.
-int static_scratch_address(void** out) {
+// up with that device current.  Outside a stream capture it is looked up on
+// every call (cheap once the module is loaded, and right again after a
+// cudaDeviceReset has reloaded the module); during a capture the address the
+// last call outside one found is used.
+int static_scratch_address(cudaStream_t st, void** out) {
   int dev = 0;
   LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   if (dev < 0 || dev >= kMaxStaticDevices) return fail(LB_EINVAL, "device ordinal too large for the static scratch");
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  LB_CUDA(cudaStreamIsCapturing(st, &cap), "cudaStreamIsCapturing");
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_ptr[dev]) {
+  if (cap == cudaStreamCaptureStatusNone || !g_static_ptr[dev]) {
     void* p = nullptr;
     LB_CUDA(cudaGetSymbolAddress(&p, g_lb_static_scratch), "cudaGetSymbolAddress(static scratch)");
     g_static_ptr[dev] = p;
@@ -1657,6 +1700,7 @@ int static_scratch_address(void** out) {
 int static_bind(lb_system* s, void* ws, cudaStream_t st) {
   int rc0 = decide_krylov(s);
   if (rc0) return rc0;
+  s->cluster = false;  // this entry point always runs one CTA per state
   s->L = make_layout(s);
   s->ws = static_cast<char*>(ws);
   s->ws_bytes = LB_STATIC_SCRATCH_BYTES;
@@ -1699,10 +1743,16 @@ int static_bind(lb_system* s, void* ws, cudaStream_t st) {
   return LB_OK;
 }
 
-// Leave the handle unbound again, whatever happened.
+// Leave the handle unbound again, whatever happened; once device work has
+// been queued, wait for it on every exit path (an early error return
+// included), so that nothing of this call still writes the shared array when
+// the caller gets control back.
 struct StaticUnbind {
   lb_system* s;
+  cudaStream_t st;
+  bool queued = false;
   ~StaticUnbind() {
+    if (queued) (void)cudaStreamSynchronize(st);
     s->ws = nullptr;
     s->ws_bytes = 0;
     s->dp = nullptr;
@@ -1719,6 +1769,10 @@ extern "C" int lb_gradient_static(lb_system* s, void* stream, double* G_out, dou
   if (rc) return rc;
   if (s->ws) return fail(LB_EINVAL, "lb_gradient_static needs a handle without a bound workspace");
   if (use_grid(s)) return fail(LB_EINVAL, "lb_gradient_static supports one CTA per state only (N^2 <= 4096)");
+  if (s->sweep == LB_SWEEP_CLUSTER)
+    return fail(LB_EINVAL, "lb_gradient_static runs one CTA per state; LB_SWEEP_CLUSTER is not available there");
+  rc = check_predictor(s);
+  if (rc) return rc;
   if (s->target_mode == 0) return fail(LB_EINVAL, "no objective (lb_objective_set or lb_objective_set_gate)");
   if (s->rho0.empty()) return fail(LB_EINVAL, "no initial states");
   const size_t need = make_layout(s).total;
@@ -1728,11 +1782,12 @@ extern "C" int lb_gradient_static(lb_system* s, void* stream, double* G_out, dou
                   need, (size_t)LB_STATIC_SCRATCH_BYTES);
     return fail(LB_ENOMEM, buf);
   }
-  void* ws = nullptr;
-  rc = static_scratch_address(&ws);
-  if (rc) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  StaticUnbind guard{s};
+  void* ws = nullptr;
+  rc = static_scratch_address(st, &ws);
+  if (rc) return rc;
+  StaticUnbind guard{s, st};
+  guard.queued = true;
   rc = static_bind(s, ws, st);
   if (rc) return rc;
   rc = gradient_device(s, st);

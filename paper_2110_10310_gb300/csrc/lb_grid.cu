@@ -1,0 +1,676 @@
+// Grid-wide cooperative sweeps for states too large for one CTA, and their
+// launchers.
+
+#include "lb_device.cuh"
+
+namespace lbk {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// grid-wide persistent sweeps (states too large for one CTA's shared memory)
+//
+// One cooperative launch keeps every SM busy on all M states at once.  Block
+// b owns a contiguous chunk of the flattened [M][V] element range; each inner
+// iteration reads the previous iterate of every element (neighbours through
+// L2, bypassing L1) and ends with a grid barrier.  Per-state maxima of
+// |z_new - z| and |q| are combined with atomicMax on the integer bit patterns
+// (order independent), so every block takes the same stopping decision and a
+// recompute is bit-identical.
+
+constexpr long long kSpinLimit = 1LL << 26;  // ~seconds of polling before a barrier gives up
+
+// Grid barrier with a bounded wait.  Returns false on every block once a
+// wait has given up (the kernel then returns).
+__device__ bool grid_sync(GridBar* bar, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* vgen = &bar->gen;
+    volatile int* verr = &bar->err;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&bar->count, 1u);
+    int ok = 1;
+    if (arrived == nblocks - 1) {
+      atomicExch(&bar->count, 0u);
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        if (*verr) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+        if (++spins > kSpinLimit) {
+          atomicExch(&bar->err, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (*verr) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+struct GridHdr {
+  Hdr h;
+  int M;
+  int herm;         // Hermitian symmetry: only elements k <= l are iterated, the rest mirrored
+  int Vh;           // elements per state in the loops: V, or N (N + 1) / 2 with herm
+  long long total;  // M * Vh
+  long long chunk;  // elements per block
+};
+
+// Element e of a grid sweep's loops: state b and vec index v; with the
+// Hermitian symmetry the loops visit k <= l only (v from the table hmap) and
+// vm is the mirror index l + N k of an off-diagonal element, whose value is
+// the conjugate (-1 for diagonal elements and without the symmetry).
+struct GEl {
+  int b, v, vm;
+};
+__device__ __forceinline__ GEl gel(const GridHdr& G, const int32_t* __restrict__ hmap, long long e) {
+  GEl r;
+  if (!G.herm) {
+    r.b = (int)(e / G.h.V);
+    r.v = (int)(e - (long long)r.b * G.h.V);
+    r.vm = -1;
+    return r;
+  }
+  r.b = (int)(e / G.Vh);
+  r.v = __ldg(hmap + (e - (long long)r.b * G.Vh));
+  const int N = G.h.N, k = r.v % N, l = r.v / N;
+  r.vm = k != l ? l + N * k : -1;
+  return r;
+}
+// store x at element g of the state array a (and its mirror)
+__device__ __forceinline__ void gput(double2* a, const GEl& g, int V, double2 x) {
+  a[(size_t)g.b * V + g.v] = x;
+  if (g.vm >= 0) a[(size_t)g.b * V + g.vm] = make_double2(x.x, -x.y);
+}
+
+__host__ __device__ inline size_t grid_smem_bytes_impl(int ncoef, int njcoef) {
+  return align16(sizeof(GridHdr)) + align16(sizeof(double) * 2 * ncoef) + align16(sizeof(double) * 2 * njcoef) +
+         align16(sizeof(double) * 4 * 8) + 64;
+}
+
+struct GridSmem {
+  GridHdr* g;
+  double* cu;
+  double* cd;
+  double* jf;
+  double* ja;
+  double* red;  // [4][8 warps]
+  int* flag;
+};
+
+__device__ GridSmem grid_setup(unsigned char* base, const ProbDev& P, int nstates, int herm) {
+  GridSmem S;
+  size_t o = 0;
+  S.g = reinterpret_cast<GridHdr*>(base + o);
+  o += align16(sizeof(GridHdr));
+  S.cu = reinterpret_cast<double*>(base + o);
+  S.cd = S.cu + P.ncoef;
+  o += align16(sizeof(double) * 2 * P.ncoef);
+  S.jf = reinterpret_cast<double*>(base + o);
+  S.ja = S.jf + P.njcoef;
+  o += align16(sizeof(double) * 2 * P.njcoef);
+  S.red = reinterpret_cast<double*>(base + o);
+  o += align16(sizeof(double) * 4 * 8);
+  S.flag = reinterpret_cast<int*>(base + o);
+  if (threadIdx.x == 0) {
+    load_hdr(S.g->h, P);
+    S.g->M = nstates;
+    S.g->herm = herm;
+    S.g->Vh = herm ? P.N * (P.N + 1) / 2 : P.V;
+    S.g->total = (long long)nstates * S.g->Vh;
+    const long long per = (S.g->total + gridDim.x - 1) / gridDim.x;
+    // whole warps, not whole blocks: rounding the chunk up to the block size
+    // left up to half of the blocks without elements (three states of
+    // N (N + 1) / 2 = 32896 elements filled 193 of 304 blocks)
+    S.g->chunk = (per + 31) / 32 * 32;
+  }
+  for (int i = threadIdx.x; i < P.ncoef; i += blockDim.x) {
+    S.cu[i] = P.cu[i];
+    S.cd[i] = P.cd[i];
+  }
+  for (int i = threadIdx.x; i < P.njcoef; i += blockDim.x) {
+    S.jf[i] = P.jf[i];
+    S.ja[i] = P.ja[i];
+  }
+  __syncthreads();
+  return S;
+}
+
+// Flush a per-thread running maximum for state b into the global slot.
+__device__ __forceinline__ void flush_max(unsigned long long* slots, int b, unsigned long long m) {
+  if (b >= 0 && m) atomicMax(slots + b, m);
+}
+
+// Per-state maxima over a block's chunk [e0, e1).  When the chunk covers at
+// most kLocalStates states (large states), each thread keeps one maximum per
+// state in registers and the block pushes one atomicMax per state; otherwise
+// (many small states per block) each thread pushes its own running maximum.
+// `local` depends only on the chunk, so it is uniform over the block.
+constexpr int kLocalStates = 4;
+
+struct StateMax {
+  int sb0, ns;
+  bool local;
+  unsigned long long m[kLocalStates];
+  int bcur;
+  unsigned long long mcur;
+
+  __device__ void init(long long e0, long long e1, int V) {
+    sb0 = (int)(e0 / V);
+    const int sb1 = e1 > e0 ? (int)((e1 - 1) / V) : sb0;
+    ns = sb1 - sb0 + 1;
+    local = ns <= kLocalStates;
+#pragma unroll
+    for (int k = 0; k < kLocalStates; ++k) m[k] = 0;
+    bcur = -1;
+    mcur = 0;
+  }
+  __device__ __forceinline__ void add(int b, unsigned long long x, unsigned long long* slots) {
+    if (local) {
+      const int i = b - sb0;
+#pragma unroll
+      for (int k = 0; k < kLocalStates; ++k)
+        if (k == i) m[k] = umax64(m[k], x);
+    } else {
+      if (b != bcur) {
+        flush_max(slots, bcur, mcur);
+        bcur = b;
+        mcur = 0;
+      }
+      mcur = umax64(mcur, x);
+    }
+  }
+  // all threads of the block call this
+  __device__ void push(unsigned long long* slots, unsigned long long* red) {
+    if (local) {
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+      for (int k = 0; k < kLocalStates; ++k) {
+        const unsigned long long v = warp_max_u64(m[k]);
+        if (lane == 0) red[k * 8 + warp] = v;
+      }
+      __syncthreads();
+      if ((int)threadIdx.x < ns) {
+        unsigned long long r = 0;
+        for (int w = 0; w < nwarps; ++w) r = umax64(r, red[threadIdx.x * 8 + w]);
+        if (r) atomicMax(slots + sb0 + threadIdx.x, r);
+      }
+      __syncthreads();
+    } else {
+      flush_max(slots, bcur, mcur);
+    }
+  }
+};
+
+// One implicit-midpoint solve over all M states: z satisfies
+// (I - dt/2 M) z = rhs (ADJ: M^+) to the per-state tolerance.  `it_global`
+// counts iterations and `solve` counts solves across the launch; they select
+// the banks of the per-state maxima.  Returns the iteration count, -1
+// (max_iter), -2 (NaN/Inf) or -3 (a barrier wait gave up); on success *zout
+// points at the buffer holding z.
+// First-iterate predictor of the grid sweeps: the off-diagonal corrections
+// c = (I - dt/2 D) z - rhs of the last n steps, kept per element in a ring
+// (P.hist, or P.histf for the forward predictor of a recompute; each element
+// always handled by the same thread, so no synchronisation is needed),
+// extrapolated in each element's rotating frame (rot_extrap).
+struct GridHist {
+  double2* ring = nullptr;
+  int n = 0, slot = 0;
+  __device__ void advance() {
+    n = n < kRingOrder ? n + 1 : kRingOrder;
+    slot = slot + 1 < kRingOrder ? slot + 1 : 0;
+  }
+};
+
+template <bool ADJ>
+__device__ __forceinline__ void grid_record(const ProbDev& P, size_t stride, GridHist h, size_t o, int v,
+                                            double hh, double2 z, double2 r) {
+  const double2 D = __ldg(P.D + v);
+  const double dr = hh * D.x, di = hh * (ADJ ? -D.y : D.y);
+  const double cr = z.x - fma(dr, z.x, -di * z.y) - r.x;
+  const double ci = z.y - fma(dr, z.y, di * z.x) - r.y;
+  h.ring[(size_t)h.slot * stride + o] = make_double2(cr, ci);
+}
+
+template <bool ADJ>
+__device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __restrict__ rhs,
+                          const double2* __restrict__ ct, double fac, long long& it_global, long long& solve,
+                          double2** zout, GridHist hist = GridHist()) {
+  const GridHdr& G = *S.g;
+  const Hdr& H = G.h;
+  const Tabs T{S.cu, S.cd, S.jf, S.ja};
+  const bool neumann = H.method == LB_SOLVER_NEUMANN;
+  const int M = G.M, V = H.V, N = H.N;
+  const long long e0 = (long long)blockIdx.x * G.chunk;
+  const long long e1 = min(G.total, e0 + G.chunk);
+  unsigned long long* dslots = P.gslots;          // [3][M]
+  unsigned long long* qslots = P.gslots + 3 * M;  // [2][M]
+  unsigned long long* qbank = qslots + (solve & 1) * M;
+  unsigned long long* red = reinterpret_cast<unsigned long long*>(S.red);
+  // z_0 = (I - dt/2 D)^-1 rhs (Jacobi) or rhs (Neumann); per-state max |rhs|
+  {
+    StateMax sm;
+    sm.init(e0, e1, G.Vh);
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const GEl g = gel(G, P.hmap, e);
+      const int b = g.b, v = g.v;
+      const size_t o = (size_t)b * V + v;
+      const double2 r = rhs[o];
+      double2 z0 = r;
+      if (!neumann) {
+        double ur = r.x, ui = r.y;
+        const double2 d = __ldg(P.Dinv + v);
+        const double di = ADJ ? -d.y : d.y;
+        if (hist.n > 0) {
+          // g = 2 (I - dt/2 D)^-1 - 1, the element's free step factor
+          const double2 c = rot_extrap(hist.ring + o, (size_t)M * V, hist.slot, hist.n,
+                                       make_double2(fma(2.0, d.x, -1.0), 2.0 * di));
+          ur += c.x;
+          ui += c.y;
+        }
+        z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
+      }
+      gput(P.zA, g, V, z0);
+      sm.add(b, umax64(abs_bits(r.x), abs_bits(r.y)), qbank);
+    }
+    sm.push(qbank, red);
+  }
+  if (!grid_sync(P.bar, gridDim.x)) return -3;
+  // the previous solve's |q| bank is free again: clear it for the next solve
+  if (blockIdx.x == 0)
+    for (int b = threadIdx.x; b < M; b += blockDim.x) qslots[((solve + 1) & 1) * M + b] = 0;
+  ++solve;
+  const double hh = 0.5 * H.h;
+  double2* zc = P.zA;
+  double2* zn = P.zB;
+  for (int it = 0; it < H.max_iter; ++it, ++it_global) {
+    unsigned long long* bank = dslots + (it_global % 3) * M;
+    StateMax sm;
+    sm.init(e0, e1, G.Vh);
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const GEl g = gel(G, P.hmap, e);
+      const int b = g.b, v = g.v;
+      const double2* xs = zc + (size_t)b * V;
+      const int k = v % N, l = v / N;
+      const double2 r = rhs[(size_t)b * V + v];
+      double ar = r.x, ai = r.y;
+      offdiag_acc<ADJ, true>(ar, ai, xs, v, __ldg(P.digits + k), __ldg(P.digits + l), H, T, ct);
+      const double2 zo = __ldcg(xs + v);
+      double2 z;
+      if (!neumann) {
+        const double2 d = __ldg(P.Dinv + v);
+        const double di = ADJ ? -d.y : d.y;
+        z.x = fma(d.x, ar, -di * ai);
+        z.y = fma(d.x, ai, di * ar);
+      } else {
+        const double2 D = __ldg(P.D + v);
+        const double dr = hh * D.x, di = hh * (ADJ ? -D.y : D.y);
+        z.x = ar + fma(dr, zo.x, -di * zo.y);
+        z.y = ai + fma(dr, zo.y, di * zo.x);
+      }
+      gput(zn, g, V, z);
+      sm.add(b, umax64(abs_bits(z.x - zo.x), abs_bits(z.y - zo.y)), bank);
+    }
+    sm.push(bank, red);
+    if (!grid_sync(P.bar, gridDim.x)) return -3;
+    // bank of iteration it_global + 2 is no longer read by anyone: clear it
+    if (blockIdx.x == 0)
+      for (int b = threadIdx.x; b < M; b += blockDim.x) dslots[((it_global + 2) % 3) * M + b] = 0;
+    // every block takes the same decision from the same slots
+    if (threadIdx.x == 0) {
+      int state = 1;  // 1 converged, 0 not yet, -2 NaN/Inf
+      for (int b = 0; b < M; ++b) {
+        const unsigned long long d = __ldcg(bank + b);
+        const unsigned long long q = __ldcg(qbank + b);
+        if (d >= kInfBits || q >= kInfBits) {
+          state = -2;
+          break;
+        }
+        const unsigned long long thr = abs_bits(H.rtol * __longlong_as_double((long long)q) * fac);
+        if (d > thr) state = 0;
+      }
+      *S.flag = state;
+    }
+    __syncthreads();
+    const int state = *S.flag;
+    __syncthreads();
+    double2* t = zc;
+    zc = zn;
+    zn = t;
+    if (state == -2) return -2;
+    if (state == 1) {
+      ++it_global;
+      *zout = zc;
+      return it + 1;
+    }
+  }
+  return -1;
+}
+
+__device__ void grid_fail(const ProbDev& P, int code, int step) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    record_error(P.status, code == -1 ? LB_ENOTCONV : (code == -2 ? LB_ENAN : LB_ECUDA), step);
+}
+
+// mode 0: forward sweep on P.qT (from P.q0 if init), checkpoints if tape
+// mode 1: forward steps j0..j1-1 in place on x; mode 2: adjoint steps j1-1..j0 in place on x
+__global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* __restrict__ pp, int mode, int init,
+                                                             int tape, int j0, int j1, double2* __restrict__ x,
+                                                             int nstates) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const ProbDev& P = *pp;
+  // the Hermitian symmetry only for the forward sweep over the system's own
+  // states (vectors given to lb_propagate may be anything)
+  const GridSmem S = grid_setup(smem, P, mode == 0 ? P.M : nstates, mode == 0 ? P.herm : 0);
+  const GridHdr& G = *S.g;
+  const Hdr& H = G.h;
+  const int V = H.V;
+  double2* q = mode == 0 ? P.qT : x;
+  const long long e0 = (long long)blockIdx.x * G.chunk, e1 = min(G.total, e0 + G.chunk);
+  const size_t hstride = (size_t)G.M * V;
+  if (mode == 0 && init)
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const GEl g = gel(G, P.hmap, e);
+      gput(q, g, V, P.q0[(size_t)g.b * V + g.v]);
+    }
+  long long itg = 0, nsolve = 0;
+  unsigned long long iters = 0, steps = 0;
+  int maxit = 0;
+  const int phase = mode == 2 ? 2 : 0;
+  // first-iterate predictor of the forward sweep, forgetting its history at
+  // every step j with j % R == 0 (R > 0 divides K, so every checkpoint is a
+  // restart point and the recompute repeats these iterates bit for bit)
+  const int R = P.pred_restart;
+  const bool pred = mode == 0 && R >= 0;
+  const double hh = 0.5 * H.h;
+  GridHist hist;
+  hist.ring = P.hist;
+  for (int jj = 0; jj < j1 - j0; ++jj) {
+    const int j = mode == 2 ? j1 - 1 - jj : j0 + jj;
+    if (pred && R > 0 && j % R == 0) hist.n = 0;
+    if (mode == 0 && tape && H.K > 0 && j % H.K == 0) {
+      for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const GEl g = gel(G, P.hmap, e);
+        const double2 qq = q[(size_t)g.b * V + g.v];
+        gput(P.ckpt + ((size_t)g.b * H.n_ckpt + j / H.K) * V, GEl{0, g.v, g.vm}, V, qq);
+      }
+    }
+    double2* z = nullptr;
+    const int it = mode == 2 ? grid_solve<true>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, &z)
+                             : grid_solve<false>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, &z,
+                                                 pred ? hist : GridHist());
+    if (it < 0) {
+      grid_fail(P, it, j);
+      break;
+    }
+    iters += (unsigned long long)it * G.M;
+    steps += G.M;
+    maxit = max(maxit, it);
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const GEl g = gel(G, P.hmap, e);
+      const size_t o = (size_t)g.b * V + g.v;
+      const double2 zz = z[o], qq = q[o];
+      if (mode == 0 && tape && H.K == 0) gput(P.ckpt + ((size_t)g.b * H.NT + j) * V, GEl{0, g.v, g.vm}, V, zz);
+      if (pred) grid_record<false>(P, hstride, hist, o, g.v, hh, zz, qq);
+      gput(q, g, V, make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y)));
+    }
+    if (pred) hist.advance();
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicAdd(&P.status->iters[phase], iters);
+    atomicAdd(&P.status->steps[phase], steps);
+    atomicMax(&P.status->max_iter_seen, maxit);
+  }
+}
+
+// backward sweep over all states: recompute each checkpoint segment, then the
+// adjoint steps with the gradient pieces summed over states and blocks
+__global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev* __restrict__ pp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const ProbDev& P = *pp;
+  const GridSmem S = grid_setup(smem, P, P.M, P.herm);
+  const GridHdr& G = *S.g;
+  const Hdr& H = G.h;
+  const int V = H.V, N = H.N;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const long long e0 = (long long)blockIdx.x * G.chunk, e1 = min(G.total, e0 + G.chunk);
+  const size_t hstride = (size_t)G.M * V;
+  // terminal condition qhat^{N_T} = beta_i/M g_i (Appendix B)
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const GEl g = gel(G, P.hmap, e);
+    const size_t o = (size_t)g.b * V + g.v;
+    const double w = P.wgt[g.b];
+    const double wt = linear_sign(P.kind) * w;
+    const double2 t = P.tar[o];
+    if (H.kind == LB_J_FROB) {
+      const double2 qq = P.qT[o];
+      gput(P.lam, g, V, make_double2(w * (qq.x - t.x), w * (qq.y - t.y)));
+    } else {
+      gput(P.lam, g, V, make_double2(wt * t.x, wt * t.y));
+    }
+  }
+  long long itg = 0, nsolve = 0;
+  unsigned long long it_rec = 0, st_rec = 0, it_adj = 0, st_adj = 0;
+  int maxit = 0;
+  const int nseg = H.K > 0 ? (H.NT + H.K - 1) / H.K : 1;
+  bool failed = false;
+  // adjoint predictor: the adjoint steps come in the same order for every K
+  const bool apred = H.method != LB_SOLVER_NEUMANN;
+  const double hh = 0.5 * H.h;
+  GridHist ahist;
+  ahist.ring = P.hist;
+  // forward predictor of the recompute, restarted as in the forward sweep
+  const int R = P.pred_restart;
+  const bool fpred = H.K > 0 && R > 0;
+  GridHist fhist;
+  fhist.ring = P.histf;
+  for (int sg = nseg - 1; sg >= 0 && !failed; --sg) {
+    const int j0 = H.K > 0 ? sg * H.K : 0;
+    const int j1 = H.K > 0 ? min(H.NT, j0 + H.K) : H.NT;
+    if (H.K > 0) {
+      for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const GEl g = gel(G, P.hmap, e);
+        gput(P.qf, g, V, P.ckpt[((size_t)g.b * H.n_ckpt + sg) * V + g.v]);
+      }
+      for (int j = j0; j < j1; ++j) {
+        double2* z = nullptr;
+        if (fpred && j % R == 0) fhist.n = 0;  // every checkpoint is a restart point
+        const int it = grid_solve<false>(P, S, P.qf, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, &z,
+                                         fpred ? fhist : GridHist());
+        if (it < 0) {
+          grid_fail(P, it, j);
+          failed = true;
+          break;
+        }
+        it_rec += (unsigned long long)it * G.M;
+        st_rec += G.M;
+        maxit = max(maxit, it);
+        for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+          const GEl g = gel(G, P.hmap, e);
+          const size_t o = (size_t)g.b * V + g.v;
+          const double2 zz = z[o], qq = P.qf[o];
+          P.seg[((size_t)g.b * H.K + (j - j0)) * V + g.v] = zz;  // read back at the same element only
+          if (fpred) grid_record<false>(P, hstride, fhist, o, g.v, hh, zz, qq);
+          gput(P.qf, g, V, make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y)));
+        }
+        if (fpred) fhist.advance();
+      }
+      if (failed) break;
+    }
+    for (int j = j1 - 1; j >= j0; --j) {
+      const double2* ct = P.ctab + (size_t)j * H.cq;
+      double2* zh = nullptr;
+      const int it = grid_solve<true>(P, S, P.lam, ct, stop_factor(P, j), itg, nsolve, &zh, apred ? ahist : GridHist());
+      if (it < 0) {
+        grid_fail(P, it, j);
+        failed = true;
+        break;
+      }
+      it_adj += (unsigned long long)it * G.M;
+      st_adj += G.M;
+      maxit = max(maxit, it);
+      // gradient pieces (eq. reducedgradient), summed over this block's elements
+      for (int q = 0; q < H.Q; ++q) {
+        const int n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * N;
+        double sar = 0.0, sai = 0.0, sdr = 0.0, sdi = 0.0;
+        for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+          const GEl g = gel(G, P.hmap, e);
+          const int b = g.b, v = g.v;
+          const double2* zs = zh + (size_t)b * V;
+          const double2 Z = H.K > 0 ? P.seg[((size_t)b * H.K + (j - j0)) * V + v]
+                                    : P.ckpt[((size_t)b * H.NT + j) * V + v];
+          const int k = v % N, l = v / N;
+          const uint32_t kd = __ldg(P.digits + k), ld = __ldg(P.digits + l);
+          const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
+          const double c1 = S.cu[co + nk], c2 = S.cd[co + nl], c3 = S.cd[co + nk], c4 = S.cu[co + nl];
+          const double2 x1 = __ldcg(zs + v + (nk + 1 < n ? s : 0));
+          const double2 x2 = __ldcg(zs + v - (nl > 0 ? sN : 0));
+          const double2 x3 = __ldcg(zs + v - (nk > 0 ? s : 0));
+          const double2 x4 = __ldcg(zs + v + (nl + 1 < n ? sN : 0));
+          const double pr = fma(-c2, x2.x, c1 * x1.x);
+          const double pi = fma(-c2, x2.y, c1 * x1.y);
+          const double rr = fma(-c4, x4.x, c3 * x3.x);
+          const double ri = fma(-c4, x4.y, c3 * x3.y);
+          if (g.vm < 0) {
+            sar = fma(Z.x, rr, fma(Z.y, ri, sar));
+            sai = fma(Z.y, rr, fma(-Z.x, ri, sai));
+            sdr = fma(Z.x, pr, fma(Z.y, pi, sdr));
+            sdi = fma(Z.y, pr, fma(-Z.x, pi, sdi));
+          } else {
+            // Hermitian Z and zhat: the mirror element (l, k) adds -conj(B) to
+            // the g_a sum and -conj(A) to the g_ad sum, A = Z conj(R), B = Z conj(P)
+            const double ar = fma(Z.x, rr, Z.y * ri), ai = fma(Z.y, rr, -Z.x * ri);
+            const double br = fma(Z.x, pr, Z.y * pi), bi = fma(Z.y, pr, -Z.x * pi);
+            sar += ar - br;
+            sai += ai + bi;
+            sdr += br - ar;
+            sdi += bi + ai;
+          }
+        }
+        const double r = warp_sum4(sar, sai, sdr, sdi, lane);
+        if ((lane & 7) == 0) S.red[(lane >> 3) * 8 + warp] = r;
+        __syncthreads();
+        if (threadIdx.x < 4) {
+          double t = 0.0;
+          for (int w = 0; w < nwarps; ++w) t += S.red[threadIdx.x * 8 + w];
+          P.partials[((size_t)blockIdx.x * LB_MAXQ + q) * 4 + threadIdx.x] = t;
+        }
+        __syncthreads();
+      }
+      // qhat^j = 2 zhat - qhat^{j+1}
+      for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const GEl g = gel(G, P.hmap, e);
+        const size_t o = (size_t)g.b * V + g.v;
+        const double2 z = zh[o], ll = P.lam[o];
+        if (apred) grid_record<true>(P, hstride, ahist, o, g.v, hh, z, ll);
+        gput(P.lam, g, V, make_double2(fma(2.0, z.x, -ll.x), fma(2.0, z.y, -ll.y)));
+      }
+      if (apred) ahist.advance();
+      if (!grid_sync(P.bar, gridDim.x)) {
+        grid_fail(P, -3, j);
+        failed = true;
+        break;
+      }
+      // block 0: fixed-order sum over blocks; multiply by -i: g = (S.im, -S.re)
+      if (blockIdx.x == 0 && threadIdx.x < 4 * H.Q) {
+        const int q = threadIdx.x >> 2, c = threadIdx.x & 3;
+        double t = 0.0;
+        for (int bb = 0; bb < (int)gridDim.x; ++bb) t += P.partials[((size_t)bb * LB_MAXQ + q) * 4 + c];
+        double* g = reinterpret_cast<double*>(P.gproj + ((size_t)j * H.Q + q) * 2);
+        if (c == 0) g[1] = -t;
+        if (c == 1) g[0] = t;
+        if (c == 2) g[3] = -t;
+        if (c == 3) g[2] = t;
+      }
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicAdd(&P.status->iters[1], it_rec);
+    atomicAdd(&P.status->steps[1], st_rec);
+    atomicAdd(&P.status->iters[2], it_adj);
+    atomicAdd(&P.status->steps[2], st_adj);
+    atomicMax(&P.status->max_iter_seen, maxit);
+  }
+}
+
+// J_i per state from P.qT (one block per state, fixed-order reduction)
+__global__ void k_objective_states(const ProbDev* __restrict__ pp) {
+  const ProbDev& P = *pp;
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  const size_t base = (size_t)i * P.V;
+  double acc = 0.0;
+  for (int v = threadIdx.x; v < P.V; v += blockDim.x) {
+    const double2 q = P.qT[base + v];
+    const double2 t = P.tar[base + v];
+    if (P.kind == LB_J_FROB) {
+      const double dr = q.x - t.x, di = q.y - t.y;
+      acc = fma(dr, dr, fma(di, di, acc));
+    } else {
+      acc = fma(t.x, q.x, fma(t.y, q.y, acc));
+    }
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    P.J[i] = merit_value(P.kind, t);
+  }
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+
+size_t grid_smem_bytes(int ncoef, int njcoef) { return grid_smem_bytes_impl(ncoef, njcoef); }
+
+int grid_blocks_max(size_t smem) {
+  int dev = 0, nsm = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(k_sweep_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  if (cudaFuncSetAttribute(k_backward_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int a = 0, b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_sweep_grid, kGridThreads, smem) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward_grid, kGridThreads, smem) != cudaSuccess) return 0;
+  per = a < b ? a : b;
+  int n = nsm * per;
+  return n < kMaxGridBlocks ? n : kMaxGridBlocks;
+}
+
+cudaError_t launch_sweep_grid(const ProbDev* d_prob, int mode, int init_from_q0, int tape, int64_t j0, int64_t j1,
+                              double2* x, int nstates, int nblocks, size_t smem, cudaStream_t s) {
+  int m = mode, in = init_from_q0, tp = tape, a = (int)j0, b = (int)j1, ns = nstates;
+  const ProbDev* p = d_prob;
+  double2* xx = x;
+  void* args[] = {(void*)&p, (void*)&m, (void*)&in, (void*)&tp, (void*)&a, (void*)&b, (void*)&xx, (void*)&ns};
+  return cudaLaunchCooperativeKernel((const void*)k_sweep_grid, dim3(nblocks), dim3(kGridThreads), args, smem, s);
+}
+
+cudaError_t launch_backward_grid(const ProbDev* d_prob, int nblocks, size_t smem, cudaStream_t s) {
+  const ProbDev* p = d_prob;
+  void* args[] = {(void*)&p};
+  return cudaLaunchCooperativeKernel((const void*)k_backward_grid, dim3(nblocks), dim3(kGridThreads), args, smem, s);
+}
+
+cudaError_t launch_objective_states(const ProbDev* d_prob, int M, cudaStream_t s) {
+  k_objective_states<<<M, 256, 0, s>>>(d_prob);
+  return cudaGetLastError();
+}
+
+}  // namespace lbk

@@ -96,7 +96,10 @@ struct ProbDev {
   double* partials;          // [grid_blocks][LB_MAXQ][4] gradient pieces per block
   unsigned long long* gslots;  // [3][M] per-state |z_new - z| maxima, then [2][M] per-state |q| maxima
   GridBar* bar;
-  double2* hist;             // [kPredOrder][M*V] first-iterate predictor history (grid and one-CTA sweeps)
+  double2* hist;             // [kRingOrder][M*V] first-iterate predictor history (grid and one-CTA sweeps)
+  double2* histf;            // [kRingOrder][M*V] the forward predictor's history in a recompute (K > 0)
+  int32_t pred_restart;      // forward predictor: -2 none, 0 never restarts, R > 0 restarts when j % R == 0
+  int32_t pad2;
   int32_t* hmap;             // [N (N + 1) / 2] vec indices k + N l with k <= l (grid sweeps)
   int32_t herm;              // grid sweeps iterate k <= l only: every state and target is Hermitian
   int32_t pad1;
@@ -111,7 +114,8 @@ struct WorkItem {
 namespace lbk {
 
 constexpr int kMaxResidentV = 4096;  // states held in one CTA's shared memory
-constexpr int kPredOrder = 7;        // extrapolation order of the first-iterate predictor
+constexpr int kPredOrder = 7;        // extrapolation order of the cluster sweeps' first-iterate predictor
+constexpr int kRingOrder = 8;        // order of the rotated first-iterate predictor (grid and one-CTA sweeps)
 
 struct ResidentConfig {
   int threads;  // CTA size (multiple of 32, <= 512)

@@ -158,9 +158,11 @@ def test_workspace_size_accounts_for_checkpoints(lib, K):
             nw = -(-(-(-Vl // C)) * lanes // 32)  # warps per CTA
             per = max(per, C * nw)
         gproj = M * per * NT * 2 * 2 * 16 + NT * 2 * 2 * 16
-        # q0, tar, qT and the seven-step ring of the first-iterate predictor
-        assert n.value >= tape + gproj + (3 + 7) * state
-        assert n.value <= tape + gproj + (3 + 7) * state + 64 * 1024
+        # q0, tar, qT and the eight-step ring of the first-iterate predictor;
+        # with checkpoints the recompute's forward predictor has a ring of its own
+        rings = 8 if K == 0 else 16
+        assert n.value >= tape + gproj + (3 + rings) * state
+        assert n.value <= tape + gproj + (3 + rings) * state + 64 * 1024
     finally:
         lib.lb_system_destroy(h)
 
@@ -181,9 +183,10 @@ def test_grid_sweep_workspace_and_sweep_choice(lib):
         V, M = 81 * 81, 2
         state = 16 * M * V
         # q0, tar, qT, 4 checkpoints, 10-step segment tape, zA, zB, lam, qf,
-        # and the seven-step ring of the first-iterate predictor
-        assert n.value >= (3 + 4 + 10 + 4 + 7) * state
-        assert n.value <= (3 + 4 + 10 + 4 + 7) * state + 2 * 1024 * 1024
+        # and the eight-step rings of the adjoint's and the recompute's
+        # first-iterate predictors
+        assert n.value >= (3 + 4 + 10 + 4 + 16) * state
+        assert n.value <= (3 + 4 + 10 + 4 + 16) * state + 2 * 1024 * 1024
     finally:
         lib.lb_system_destroy(h)
 

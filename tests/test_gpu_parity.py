@@ -159,13 +159,15 @@ def test_gradient_matches_central_differences_on_gpu():
 
 
 def test_checkpoint_interval_bitwise_identical():
-    """Checkpoint intervals K = 1, 7 and 100 give bit-identical gradients; the
-    full tape (K = 0, whose forward sweep also uses the predicted first
-    iterate) agrees to rounding."""
+    """Without a forward predictor, checkpoint intervals K = 1, 7 and 100 give
+    bit-identical gradients; the full tape (K = 0, whose forward sweep
+    predicts its first iterates) agrees to rounding."""
+    from paper_2110_10310_gb300 import _lib as L
+
     p = W.random_problem(206, levels=(2, 2), n_states=2, n_steps=45, T_ns=0.9, amp=0.1)
     res = []
     for K in (1, 7, 100):
-        s = _sys(p, ckpt_every=K)
+        s = _sys(p, ckpt_every=K, predictor=L.LB_PRED_NONE)
         res.append(s.gradient())
     for G, g in res[1:]:
         assert G == res[0][0]
@@ -283,18 +285,72 @@ def test_grid_sweep_matches_oracle(levels, K, herm):
 
 
 def test_grid_checkpoint_interval_bitwise_identical():
-    """Grid sweeps: K = 1, 7, 100 bit-identical; the full tape (K = 0, whose
-    forward sweep also uses the predicted first iterate) agrees to rounding."""
+    """Grid sweeps without a forward predictor: K = 1, 7, 100 bit-identical;
+    the full tape (K = 0, whose forward sweep predicts its first iterates)
+    agrees to rounding."""
     from paper_2110_10310_gb300 import _lib as L
 
     p = W.random_problem(402, levels=(3, 3), n_states=2, n_steps=45, T_ns=0.9, amp=0.1)
-    res = [_sys(p, ckpt_every=K, sweep=L.LB_SWEEP_GRID).gradient() for K in (1, 7, 100)]
+    res = [_sys(p, ckpt_every=K, sweep=L.LB_SWEEP_GRID, predictor=L.LB_PRED_NONE).gradient() for K in (1, 7, 100)]
     for G, g in res[1:]:
         assert G == res[0][0]
         assert np.array_equal(g, res[0][1])
     G0, g0 = _sys(p, ckpt_every=0, sweep=L.LB_SWEEP_GRID).gradient()
     assert abs(G0 - res[0][0]) <= 1e-13 * abs(res[0][0])
     assert _rel(g0, res[0][1]) < 1e-12
+
+
+@pytest.mark.parametrize("sweep,solver", [("resident", "jacobi"), ("grid", "jacobi"), ("resident", "gmres"),
+                                          ("cluster", "jacobi")])
+def test_recompute_repeats_the_forward_predictor_bitwise(sweep, solver):
+    """The forward predictor restarts at every checkpoint, so with
+    checkpoints every K steps the gradient is bitwise that of the full stage
+    tape whose forward predictor restarts every K steps (the recompute
+    repeats every forward iterate), different K agree to rounding, and both
+    match the oracle.  The cluster sweep predicts forward solves only with the
+    full tape, so there every K >= 1 is bitwise the run without the
+    predictor."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    sw = {"resident": L.LB_SWEEP_RESIDENT, "grid": L.LB_SWEEP_GRID, "cluster": L.LB_SWEEP_CLUSTER}[sweep]
+    sv = {"jacobi": L.LB_SOLVER_JACOBI, "gmres": L.LB_SOLVER_GMRES}[solver]
+    p = W.random_problem(411, levels=(3, 2), n_states=2, n_steps=45, T_ns=0.9, amp=0.1, ckpt_every=0)
+    Go, go, _ = imr.gradient(p)
+    out = {}
+    for K in (5, 9):
+        s = _sys(p, ckpt_every=K, sweep=sw, solver=sv)
+        G, g = s.gradient()
+        out[K] = (G, g, s.stats())
+        R = L.LB_PRED_NONE if sweep == "cluster" else K
+        G0, g0 = _sys(p, ckpt_every=0 if sweep != "cluster" else K, sweep=sw, solver=sv, predictor=R).gradient()
+        assert G == G0
+        assert np.array_equal(g, g0)
+        assert abs(G - Go) <= 1e-10 * abs(Go)
+        assert _rel(g, go) < 1e-9
+    assert abs(out[5][0] - out[9][0]) <= 1e-13 * abs(out[5][0])
+    assert _rel(out[5][1], out[9][1]) < 1e-11
+    if sweep != "cluster":
+        s0 = _sys(p, ckpt_every=9, sweep=sw, solver=sv, predictor=L.LB_PRED_NONE)
+        s0.gradient()
+        st0 = s0.stats()
+        for ph in (0, 1):
+            assert out[9][2]["phase_iterations"][ph] < st0["phase_iterations"][ph]
+
+
+def test_predictor_restart_rules():
+    """A predictor that never restarts needs the full tape; a restart period
+    must divide the checkpoint interval."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(412, levels=(2, 2), n_states=1, n_steps=20, T_ns=0.4, amp=0.1)
+    with pytest.raises(L.LBError) as e:
+        _sys(p, ckpt_every=10, predictor=0)
+    assert e.value.code == L.LB_EINVAL
+    with pytest.raises(L.LBError) as e:
+        _sys(p, ckpt_every=10, predictor=3)
+    assert e.value.code == L.LB_EINVAL
+    _sys(p, ckpt_every=10, predictor=5).gradient()
+    _sys(p, ckpt_every=0, predictor=0).gradient()
 
 
 def _imr_residual(mdl, j, q0, q1, adjoint=False):
@@ -391,13 +447,33 @@ def test_qutrits_6x3_reduced_to_qubits_matches_oracle():
 
 def test_qudits_4x4_full_size_checkpoints_bitwise():
     """Full-size workload 4 states (N^2 = 65536) over 200 steps at its dt:
-    checkpoint intervals 1 and 100 give bit-identical objective and gradient."""
+    without a forward predictor, checkpoint intervals 1 and 100 give
+    bit-identical objective and gradient; with it (restarted every 100
+    steps), checkpoints every 100 steps give bitwise the gradient of the full
+    stage tape with the same restarts -- the recompute repeats the forward
+    sweep exactly -- and the two agree to rounding."""
+    from paper_2110_10310_gb300 import _lib as L
+
     p = W.config4(n_steps=200)
     p.system.T_ns = 500.0 * 200 / 40000
-    G1, g1 = _sys(p, ckpt_every=1).gradient()
-    G2, g2 = _sys(p, ckpt_every=100).gradient()
+    G1, g1 = _sys(p, ckpt_every=1, predictor=L.LB_PRED_NONE).gradient()
+    G2, g2 = _sys(p, ckpt_every=100, predictor=L.LB_PRED_NONE).gradient()
     assert G1 == G2
     assert np.array_equal(g1, g2)
+    s = _sys(p, ckpt_every=100)
+    G3, g3 = s.gradient()
+    st = s.stats()
+    G4, g4 = _sys(p, ckpt_every=0, predictor=100).gradient()
+    assert G3 == G4
+    assert np.array_equal(g3, g4)
+    assert abs(G3 - G1) <= 1e-12 * abs(G1)
+    assert _rel(g3, g1) < 1e-10
+    # predicted first iterates: forward and recompute converge in fewer inner iterations
+    s0 = _sys(p, ckpt_every=100, predictor=L.LB_PRED_NONE)
+    s0.gradient()
+    st0 = s0.stats()
+    for ph in (0, 1):
+        assert st["phase_iterations"][ph] < st0["phase_iterations"][ph], (ph, st, st0)
 
 
 # ----------------------------------------------------------------------------
@@ -523,7 +599,7 @@ def test_gmres_checkpoints_bitwise_and_steps():
     from paper_2110_10310_gb300 import _lib as L
 
     p = W.random_problem(803, levels=(3, 2), n_states=2, n_steps=24, T_ns=0.5, amp=0.1)
-    res = [_sys(p, ckpt_every=K, solver=L.LB_SOLVER_GMRES).gradient() for K in (1, 5, 100)]
+    res = [_sys(p, ckpt_every=K, solver=L.LB_SOLVER_GMRES, predictor=L.LB_PRED_NONE).gradient() for K in (1, 5, 100)]
     for G, g in res[1:]:
         assert G == res[0][0]
         assert np.array_equal(g, res[0][1])

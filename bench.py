@@ -100,9 +100,9 @@ def problem(n_steps=None, workload=DEFAULT_WORKLOAD, states=0, levels=None):
     else:
         p = W.config2()
     if n_steps is not None:
-        # a prefix of the horizon at the workload's step size dt
-        p.system.T_ns = p.system.T_ns * n_steps / p.system.n_steps
-        p.system.n_steps = n_steps
+        # the first n_steps steps of the workload at its step size dt; the
+        # controls stay those of the whole horizon
+        W.prefix(p, n_steps)
     return p
 
 
@@ -432,8 +432,7 @@ def run_apply(args, rank, world, dev):
     from paper_2110_10310_gb300.system import LindbladSystem, colmajor
 
     n = args.states or 64
-    p = W.config5(n_steps=40, n_states=n)
-    p.system.T_ns = 300.0 * 40 / 20000
+    p = W.prefix(W.config5(n_states=n), 40)
     p.ckpt_every = 10
     s = LindbladSystem(p, device=dev)
     lib = _lib.load()

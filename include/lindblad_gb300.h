@@ -153,6 +153,14 @@ void lb_system_destroy(lb_system* sys);
  * Resets alpha to zero. */
 int lb_controls_define(lb_system* sys, int32_t n_splines, const int32_t* n_carriers, const double* carrier_ghz);
 
+/* Interval [0, T_c] the B-splines of eq. rotctrl span (knot spacing
+ * T_c/(N_s - 2)): T_c = T_ns, or the system's final time T for T_ns = 0 (the
+ * default).  A system that integrates the first N_T steps of a longer
+ * horizon (its T = N_T dt) keeps that horizon's controls by setting T_c to
+ * the longer horizon.  LB_EINVAL for a negative or non-finite T_ns; call
+ * before lb_bind_workspace. */
+int lb_controls_set_horizon(lb_system* sys, double T_ns);
+
 /* Set the control vector alpha (host, length n = 2 sum_q N_s N_f(q); layout
  * [q][f][s][re, im], GHz).  If a workspace is bound, the copy to the device
  * is issued on the bound stream before returning. */
@@ -235,6 +243,16 @@ int lb_set_sweep(lb_system* sys, int32_t sweep);
 #define LB_PRED_AUTO (-1)
 #define LB_PRED_NONE (-2)
 int lb_set_predictor(lb_system* sys, int32_t restart);
+
+/* Bound of the grid sweeps' barrier waits (failure detection; the paper has
+ * no counterpart).  Each block polls the grid barrier at most `polls` times
+ * (about 64 ns apart) before it gives up; a wait that gives up makes every
+ * block of the launch return, and the call reports LB_ECUDA with the time
+ * step ("a grid barrier wait gave up at time step j").  The handle stays
+ * usable: the next call clears the barrier.  0 restores the default
+ * (2^26 polls, seconds).  May be called at any time; with a workspace bound
+ * the new bound is uploaded on the bind stream, which is synchronised. */
+int lb_set_wait_limit(lb_system* sys, int64_t polls);
 
 /* Jaynes-Cummings coupling of the system Hamiltonian (Sec. II):
  *   sum_{p<q} g_pq (e^{i eta_pq t} a_p^+ a_q + e^{-i eta_pq t} a_p a_q^+),

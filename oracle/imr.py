@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .model import Model, TWO_PI, a_op, alpha_index, bspline_basis, hamiltonian_part, unvec, vec
+from .model import Model, TWO_PI, a_op, alpha_index, bspline_basis, control_horizon, hamiltonian_part, unvec, vec
 
 
 # ----------------------------------------------------------------------------
@@ -238,7 +238,7 @@ def gradient(prob, n_steps: int | None = None):
         Z = fw["z"][j]
         Ca = [np.sum(Zh.conj() * (Ma[q] @ Z)) for q in range(len(levels))]
         Cad = [np.sum(Zh.conj() * (Mad[q] @ Z)) for q in range(len(levels))]
-        for k, q, dd in dd_dalpha(prob.controls, prob.system.T_ns, t):
+        for k, q, dd in dd_dalpha(prob.controls, control_horizon(prob.controls, prob.system), t):
             grad[k] += h * np.real(dd * Ca[q] + np.conj(dd) * Cad[q])
         Lam = Lam + h * (MH @ Zh)
         if g1 != 0.0:

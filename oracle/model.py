@@ -110,6 +110,14 @@ def alpha_index(ctrl, q: int, f: int, s: int) -> int:
     return off + 2 * (f * ctrl.n_splines + s)
 
 
+def control_horizon(ctrl, sysm) -> float:
+    """The interval [0, T_c] the B-splines of eq. rotctrl span: the final
+    time T of the problem, or the longer horizon of which the problem
+    integrates the first steps (its controls are then that problem's)."""
+    hz = getattr(ctrl, "horizon_ns", None)
+    return float(hz) if hz else float(sysm.T_ns)
+
+
 def control_amplitudes(ctrl, t: float, T: float) -> np.ndarray:
     """d_q(t) = sum_s S_s(t) sum_f alpha_q^{s,f} exp(i t Omega_q^f), eq.
     rotctrl, in rad/ns (alpha and Omega given /2pi in GHz)."""
@@ -246,7 +254,7 @@ class Model:
         return (j + 0.5) * self.h
 
     def d(self, t: float) -> np.ndarray:
-        return control_amplitudes(self.ctrl, t, self.sys.T_ns)
+        return control_amplitudes(self.ctrl, t, control_horizon(self.ctrl, self.sys))
 
     def H(self, t: float) -> np.ndarray:
         return self.H_sys + jc_hamiltonian(self.sys, t) + control_hamiltonian(self.d(t), self.levels)

@@ -93,6 +93,7 @@ SIGNATURES = {
     "lb_system_destroy": (None, [c_void_p]),
     "lb_controls_define": (c_int32, [c_void_p, c_int32, POINTER(c_int32), POINTER(c_double)]),
     "lb_controls_set": (c_int32, [c_void_p, POINTER(c_double), c_int64]),
+    "lb_controls_set_horizon": (c_int32, [c_void_p, c_double]),
     "lb_states_set": (c_int32, [c_void_p, c_int32, c_void_p, POINTER(c_double)]),
     "lb_objective_set": (c_int32, [c_void_p, c_int32, c_void_p, c_double]),
     "lb_objective_set_gate": (c_int32, [c_void_p, c_int32, c_void_p, c_double]),
@@ -102,6 +103,7 @@ SIGNATURES = {
     "lb_set_sweep": (c_int32, [c_void_p, c_int32]),
     "lb_set_symmetry": (c_int32, [c_void_p, c_int32]),
     "lb_set_predictor": (c_int32, [c_void_p, c_int32]),
+    "lb_set_wait_limit": (c_int32, [c_void_p, c_int64]),
     "lb_system_set_coupling": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_double)]),
     "lb_workspace_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),
     "lb_bind_workspace": (c_int32, [c_void_p, c_void_p, c_size_t, c_void_p]),

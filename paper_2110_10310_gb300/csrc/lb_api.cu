@@ -68,6 +68,7 @@ struct lb_system {
   // controls (eq. rotctrl)
   bool ctrl_defined = false;
   int Ns = 0;
+  double Tc = 0.0;  // horizon the B-splines span; 0 = the final time T
   int nf[LB_MAXQ] = {};
   std::vector<double> carriers;  // rad/ns
   std::vector<double> alpha;     // GHz, [q][f][s][re, im]
@@ -94,6 +95,7 @@ struct lb_system {
   int sweep = LB_SWEEP_AUTO;
   int symmetry = LB_SYM_HERMITIAN;
   int pred = LB_PRED_AUTO;  // restart period of the forward predictor as requested (lb_set_predictor)
+  long long spin_limit = 0;  // polls of a grid-barrier wait (0: the kernels' default; lb_set_wait_limit)
   double gamma1 = 0.0, pen_a = 1.0;  // running penalty (one CTA per state)
   bool rho_herm = false;  // every initial state exactly Hermitian
   bool tar_herm = false;  // every explicit target exactly Hermitian (gate targets: always)
@@ -480,6 +482,7 @@ void fill_prob(lb_system* s) {
   P.h = s->h;
   P.rtol = s->rtol;
   P.T = s->T;
+  P.Tc = s->Tc > 0.0 ? s->Tc : s->T;
   P.gamma2 = s->gamma2;
   int stride = 1, co = 0, jo = 0, fo = 0, ao = 0;
   for (int q = s->Q - 1; q >= 0; --q) {
@@ -546,6 +549,7 @@ void fill_prob(lb_system* s) {
   P.hist = at<double2>(s, s->L.hist);
   P.histf = at<double2>(s, s->L.histf);
   P.pred_restart = effective_pred(s);
+  P.spin_limit = s->spin_limit;
 }
 
 int ensure_ctab(lb_system* s, cudaStream_t st) {
@@ -812,6 +816,15 @@ int lb_controls_define(lb_system* s, int32_t n_splines, const int32_t* n_carrier
   return LB_OK;
 }
 
+int lb_controls_set_horizon(lb_system* s, double T_ns) {
+  if (!s) return fail(LB_EINVAL, "null system handle");
+  if (s->ws) return fail(LB_EINVAL, "set the control horizon before binding a workspace");
+  if (!(T_ns >= 0.0) || !std::isfinite(T_ns)) return fail(LB_EINVAL, "the control horizon must be finite and >= 0");
+  s->Tc = T_ns;
+  s->ctab_dirty = true;
+  return LB_OK;
+}
+
 int lb_controls_set(lb_system* s, const double* alpha, int64_t n) {
   if (!s || !alpha) return fail(LB_EINVAL, "null argument");
   if (!s->ctrl_defined) return fail(LB_EINVAL, "controls not defined");
@@ -974,6 +987,20 @@ int lb_set_symmetry(lb_system* s, int32_t symmetry) {
   if (symmetry != LB_SYM_NONE && symmetry != LB_SYM_HERMITIAN) return fail(LB_EINVAL, "unknown symmetry");
   s->symmetry = symmetry;
   return refresh_symmetry(s);
+}
+
+int lb_set_wait_limit(lb_system* s, int64_t polls) {
+  if (!s) return fail(LB_EINVAL, "null system handle");
+  if (polls < 0) return fail(LB_EINVAL, "polls must be >= 0");
+  s->spin_limit = polls;
+  if (s->ws) {
+    s->hp.spin_limit = polls;
+    cudaStream_t st = s->bind_stream;
+    LB_CUDA(cudaMemcpyAsync(&s->dp->spin_limit, &s->hp.spin_limit, sizeof(long long), cudaMemcpyHostToDevice, st),
+            "upload wait limit");
+    LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  }
+  return LB_OK;
 }
 
 int lb_set_predictor(lb_system* s, int32_t restart) {

@@ -216,6 +216,7 @@ struct Hdr {
   double h, rtol;
   int lev[LB_MAXQ], stride[LB_MAXQ], coff[LB_MAXQ], joff[LB_MAXQ];
   double jump[LB_MAXQ];
+  unsigned jon;  // bit q set when subsystem q decays (jump[q] != 0), tested on the integer pipe
 };
 
 struct Tabs {
@@ -257,6 +258,9 @@ __device__ void load_hdr(Hdr& H, const ProbDev& P) {
     H.joff[q] = P.joff[q];
     H.jump[q] = P.jump[q];
   }
+  H.jon = 0u;
+  for (int q = 0; q < P.Q; ++q)
+    if (P.jump[q] != 0.0) H.jon |= 1u << q;
 }
 
 // (dt/2) (O x)_v accumulated into (ar, ai); O = M - D (or its adjoint part
@@ -300,7 +304,7 @@ __device__ __forceinline__ void offdiag_acc(double& ar, double& ai, const double
     const double a = ADJ ? -c.x : c.x, b = ADJ ? -c.y : c.y;
     ar = fma(b, wr, fma(a, ui, ar));
     ai = fma(b, wi, fma(-a, ur, ai));
-    if (H.jump[q] != 0.0) {
+    if ((H.jon >> q) & 1u) {
       // decay sandwich: M couples x[k+s, l+s], M^+ couples x[k-s, l-s]
       const int jo = H.joff[q] + nk * n + nl;
       double cj;

@@ -20,9 +20,10 @@ namespace {
 
 constexpr long long kSpinLimit = 1LL << 26;  // ~seconds of polling before a barrier gives up
 
-// Grid barrier with a bounded wait.  Returns false on every block once a
-// wait has given up (the kernel then returns).
-__device__ bool grid_sync(GridBar* bar, unsigned nblocks) {
+// Grid barrier with a bounded wait: at most `limit` polls (kSpinLimit unless
+// the handle set another bound, lb_set_wait_limit).  Returns false on every
+// block once a wait has given up (the kernel then returns).
+__device__ bool grid_sync(GridBar* bar, unsigned nblocks, long long limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -44,7 +45,7 @@ __device__ bool grid_sync(GridBar* bar, unsigned nblocks) {
           break;
         }
         __nanosleep(64);
-        if (++spins > kSpinLimit) {
+        if (++spins > limit) {
           atomicExch(&bar->err, 1);
           ok = 0;
           break;
@@ -287,7 +288,7 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
     }
     sm.push(qbank, red);
   }
-  if (!grid_sync(P.bar, gridDim.x)) return -3;
+  if (!grid_sync(P.bar, gridDim.x, P.spin_limit > 0 ? P.spin_limit : kSpinLimit)) return -3;
   // the previous solve's |q| bank is free again: clear it for the next solve
   if (blockIdx.x == 0)
     for (int b = threadIdx.x; b < M; b += blockDim.x) qslots[((solve + 1) & 1) * M + b] = 0;
@@ -324,24 +325,27 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
       sm.add(b, umax64(abs_bits(z.x - zo.x), abs_bits(z.y - zo.y)), bank);
     }
     sm.push(bank, red);
-    if (!grid_sync(P.bar, gridDim.x)) return -3;
+    if (!grid_sync(P.bar, gridDim.x, P.spin_limit > 0 ? P.spin_limit : kSpinLimit)) return -3;
     // bank of iteration it_global + 2 is no longer read by anyone: clear it
     if (blockIdx.x == 0)
       for (int b = threadIdx.x; b < M; b += blockDim.x) dslots[((it_global + 2) % 3) * M + b] = 0;
-    // every block takes the same decision from the same slots
-    if (threadIdx.x == 0) {
-      int state = 1;  // 1 converged, 0 not yet, -2 NaN/Inf
-      for (int b = 0; b < M; ++b) {
+    // every block takes the same decision from the same slots (the states
+    // spread over the lanes of warp 0)
+    if (threadIdx.x < 32) {
+      bool bad = false, open = false;
+      for (int b = threadIdx.x; b < M; b += 32) {
         const unsigned long long d = __ldcg(bank + b);
         const unsigned long long q = __ldcg(qbank + b);
         if (d >= kInfBits || q >= kInfBits) {
-          state = -2;
-          break;
+          bad = true;
+        } else {
+          const unsigned long long thr = abs_bits(H.rtol * __longlong_as_double((long long)q) * fac);
+          if (d > thr) open = true;
         }
-        const unsigned long long thr = abs_bits(H.rtol * __longlong_as_double((long long)q) * fac);
-        if (d > thr) state = 0;
       }
-      *S.flag = state;
+      bad = __any_sync(kFull, bad);
+      open = __any_sync(kFull, open);
+      if (threadIdx.x == 0) *S.flag = bad ? -2 : (open ? 0 : 1);  // NaN/Inf, not yet, converged
     }
     __syncthreads();
     const int state = *S.flag;
@@ -521,64 +525,85 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
       it_adj += (unsigned long long)it * G.M;
       st_adj += G.M;
       maxit = max(maxit, it);
-      // gradient pieces (eq. reducedgradient), summed over this block's elements
-      for (int q = 0; q < H.Q; ++q) {
-        const int n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * N;
-        double sar = 0.0, sai = 0.0, sdr = 0.0, sdi = 0.0;
+      // Passes over this block's elements, four subsystems each (so that the
+      // sums stay in registers): the gradient pieces (eq. reducedgradient),
+      // summed per block, and in the last pass the update
+      // qhat^j = 2 zhat - qhat^{j+1} with the predictor's record.
+      //   g_a  = -i sum_kl Z_kl conj(R_zhat),  g_ad = -i sum_kl Z_kl conj(P_zhat)
+      // with P, R the neighbour combinations of offdiag_acc taken on zhat.
+      constexpr int kQP = 4;  // subsystems per pass
+      const int Qn = H.Q;
+      for (int q0 = 0; q0 < Qn; q0 += kQP) {
+        const bool last = q0 + kQP >= Qn;
+        double sar[kQP], sai[kQP], sdr[kQP], sdi[kQP];
+#pragma unroll
+        for (int u = 0; u < kQP; ++u) sar[u] = sai[u] = sdr[u] = sdi[u] = 0.0;
         for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
           const GEl g = gel(G, P.hmap, e);
           const int b = g.b, v = g.v;
+          const size_t o = (size_t)b * V + v;
           const double2* zs = zh + (size_t)b * V;
           const double2 Z = H.K > 0 ? P.seg[((size_t)b * H.K + (j - j0)) * V + v]
                                     : P.ckpt[((size_t)b * H.NT + j) * V + v];
           const int k = v % N, l = v / N;
           const uint32_t kd = __ldg(P.digits + k), ld = __ldg(P.digits + l);
-          const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
-          const double c1 = S.cu[co + nk], c2 = S.cd[co + nl], c3 = S.cd[co + nk], c4 = S.cu[co + nl];
-          const double2 x1 = __ldcg(zs + v + (nk + 1 < n ? s : 0));
-          const double2 x2 = __ldcg(zs + v - (nl > 0 ? sN : 0));
-          const double2 x3 = __ldcg(zs + v - (nk > 0 ? s : 0));
-          const double2 x4 = __ldcg(zs + v + (nl + 1 < n ? sN : 0));
-          const double pr = fma(-c2, x2.x, c1 * x1.x);
-          const double pi = fma(-c2, x2.y, c1 * x1.y);
-          const double rr = fma(-c4, x4.x, c3 * x3.x);
-          const double ri = fma(-c4, x4.y, c3 * x3.y);
-          if (g.vm < 0) {
-            sar = fma(Z.x, rr, fma(Z.y, ri, sar));
-            sai = fma(Z.y, rr, fma(-Z.x, ri, sai));
-            sdr = fma(Z.x, pr, fma(Z.y, pi, sdr));
-            sdi = fma(Z.y, pr, fma(-Z.x, pi, sdi));
-          } else {
-            // Hermitian Z and zhat: the mirror element (l, k) adds -conj(B) to
-            // the g_a sum and -conj(A) to the g_ad sum, A = Z conj(R), B = Z conj(P)
-            const double ar = fma(Z.x, rr, Z.y * ri), ai = fma(Z.y, rr, -Z.x * ri);
-            const double br = fma(Z.x, pr, Z.y * pi), bi = fma(Z.y, pr, -Z.x * pi);
-            sar += ar - br;
-            sai += ai + bi;
-            sdr += br - ar;
-            sdi += bi + ai;
+#pragma unroll
+          for (int u = 0; u < kQP; ++u) {
+            const int q = q0 + u;
+            if (q < Qn) {
+              const int n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * N;
+              const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
+              const double c1 = S.cu[co + nk], c2 = S.cd[co + nl], c3 = S.cd[co + nk], c4 = S.cu[co + nl];
+              const double2 x1 = __ldcg(zs + v + (nk + 1 < n ? s : 0));
+              const double2 x2 = __ldcg(zs + v - (nl > 0 ? sN : 0));
+              const double2 x3 = __ldcg(zs + v - (nk > 0 ? s : 0));
+              const double2 x4 = __ldcg(zs + v + (nl + 1 < n ? sN : 0));
+              const double pr = fma(-c2, x2.x, c1 * x1.x);
+              const double pi = fma(-c2, x2.y, c1 * x1.y);
+              const double rr = fma(-c4, x4.x, c3 * x3.x);
+              const double ri = fma(-c4, x4.y, c3 * x3.y);
+              if (g.vm < 0) {
+                sar[u] = fma(Z.x, rr, fma(Z.y, ri, sar[u]));
+                sai[u] = fma(Z.y, rr, fma(-Z.x, ri, sai[u]));
+                sdr[u] = fma(Z.x, pr, fma(Z.y, pi, sdr[u]));
+                sdi[u] = fma(Z.y, pr, fma(-Z.x, pi, sdi[u]));
+              } else {
+                // Hermitian Z and zhat: the mirror element (l, k) adds -conj(B) to
+                // the g_a sum and -conj(A) to the g_ad sum, A = Z conj(R), B = Z conj(P)
+                const double ar = fma(Z.x, rr, Z.y * ri), ai = fma(Z.y, rr, -Z.x * ri);
+                const double br = fma(Z.x, pr, Z.y * pi), bi = fma(Z.y, pr, -Z.x * pi);
+                sar[u] += ar - br;
+                sai[u] += ai + bi;
+                sdr[u] += br - ar;
+                sdi[u] += bi + ai;
+              }
+            }
+          }
+          if (last) {
+            // qhat^j = 2 zhat - qhat^{j+1}: no other thread reads this element in the pass
+            const double2 zz = zh[o], ll = P.lam[o];
+            if (apred) grid_record<true>(P, hstride, ahist, o, v, hh, zz, ll);
+            gput(P.lam, g, V, make_double2(fma(2.0, zz.x, -ll.x), fma(2.0, zz.y, -ll.y)));
           }
         }
-        const double r = warp_sum4(sar, sai, sdr, sdi, lane);
-        if ((lane & 7) == 0) S.red[(lane >> 3) * 8 + warp] = r;
-        __syncthreads();
-        if (threadIdx.x < 4) {
-          double t = 0.0;
-          for (int w = 0; w < nwarps; ++w) t += S.red[threadIdx.x * 8 + w];
-          P.partials[((size_t)blockIdx.x * LB_MAXQ + q) * 4 + threadIdx.x] = t;
+#pragma unroll
+        for (int u = 0; u < kQP; ++u) {
+          const int q = q0 + u;
+          if (q < Qn) {
+            const double r = warp_sum4(sar[u], sai[u], sdr[u], sdi[u], lane);
+            if ((lane & 7) == 0) S.red[(lane >> 3) * 8 + warp] = r;
+            __syncthreads();
+            if (threadIdx.x < 4) {
+              double t = 0.0;
+              for (int w = 0; w < nwarps; ++w) t += S.red[threadIdx.x * 8 + w];
+              P.partials[((size_t)blockIdx.x * LB_MAXQ + q) * 4 + threadIdx.x] = t;
+            }
+            __syncthreads();
+          }
         }
-        __syncthreads();
-      }
-      // qhat^j = 2 zhat - qhat^{j+1}
-      for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const GEl g = gel(G, P.hmap, e);
-        const size_t o = (size_t)g.b * V + g.v;
-        const double2 z = zh[o], ll = P.lam[o];
-        if (apred) grid_record<true>(P, hstride, ahist, o, g.v, hh, z, ll);
-        gput(P.lam, g, V, make_double2(fma(2.0, z.x, -ll.x), fma(2.0, z.y, -ll.y)));
       }
       if (apred) ahist.advance();
-      if (!grid_sync(P.bar, gridDim.x)) {
+      if (!grid_sync(P.bar, gridDim.x, P.spin_limit > 0 ? P.spin_limit : kSpinLimit)) {
         grid_fail(P, -3, j);
         failed = true;
         break;

@@ -45,6 +45,7 @@ struct ProbDev {
   double jg[LB_MAXQ * (LB_MAXQ - 1) / 2];  // g_pq (rad/ns)
   double je[LB_MAXQ * (LB_MAXQ - 1) / 2];  // eta_pq = omega_p^rot - omega_q^rot (rad/ns)
   double h, rtol, T, gamma2;
+  double Tc;                 // horizon the B-splines span (knot spacing Tc / (Ns - 2))
   int32_t levels[LB_MAXQ];
   int32_t stride[LB_MAXQ];   // s_q = prod_{p>q} n_p
   int32_t coff[LB_MAXQ];     // offset of subsystem q in cu/cd
@@ -100,6 +101,7 @@ struct ProbDev {
   double2* histf;            // [kRingOrder][M*V] the forward predictor's history in a recompute (K > 0)
   int32_t pred_restart;      // forward predictor: -2 none, 0 never restarts, R > 0 restarts when j % R == 0
   int32_t pad2;
+  long long spin_limit;      // polls of a grid-barrier wait before it gives up (0: the kernels' default)
   int32_t* hmap;             // [N (N + 1) / 2] vec indices k + N l with k <= l (grid sweeps)
   int32_t herm;              // grid sweeps iterate k <= l only: every state and target is Hermitian
   int32_t pad1;

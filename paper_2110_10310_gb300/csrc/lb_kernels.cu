@@ -121,7 +121,7 @@ __global__ void k_control_table(const ProbDev* __restrict__ pp) {
     P.ctab[tid] = make_double2(gg * cs, gg * sn);
     return;
   }
-  const double dtau = P.T / (P.Ns - 2);
+  const double dtau = P.Tc / (P.Ns - 2);
   const double x = t / dtau;
   const int slo = max(0, (int)floor(x - 1.0)), shi = min(P.Ns - 1, (int)floor(x + 2.0));
   double dr = 0.0, di = 0.0;
@@ -214,7 +214,7 @@ __global__ void k_gradient_project(const ProbDev* __restrict__ probs) {
   if (q >= P.Q) return;
   const int f = rem / P.Ns, s = rem % P.Ns;
   const double om = P.carriers[P.foff[q] + f];
-  const double dtau = P.T / (P.Ns - 2);
+  const double dtau = P.Tc / (P.Ns - 2);
   // S_s(t) > 0 for t in ((s - 2) dtau, (s + 1) dtau)
   const int jlo = max(0, (int)floor((s - 2) * dtau / P.h - 1.0));
   const int jhi = min(P.NT - 1, (int)ceil((s + 1) * dtau / P.h));

@@ -100,6 +100,8 @@ class LindbladSystem:
         nf = np.array([len(c) for c in ctrl.carriers_ghz], dtype=np.int32)
         car = np.concatenate([np.asarray(c, dtype=np.float64) for c in ctrl.carriers_ghz])
         L.check(self.lib.lb_controls_define(h, int(ctrl.n_splines), nf.ctypes.data_as(POINTER(c_int32)), _dptr(car)))
+        if getattr(ctrl, "horizon_ns", None):
+            L.check(self.lib.lb_controls_set_horizon(h, float(ctrl.horizon_ns)))
         self.n_params = 2 * int(ctrl.n_splines) * int(nf.sum())
         self.set_alpha(ctrl.alpha)
         rho = colmajor(problem.rho0)

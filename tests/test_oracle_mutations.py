@@ -29,6 +29,7 @@ PIN_TESTS = [
     pins.test_jaynes_cummings_resonant_swap_discrete_closed_form,
     pins.test_jaynes_cummings_detuned_phases_against_schrodinger,
     pins.test_running_penalty_closed_form_and_gradient,
+    pins.test_control_horizon_prefix_is_the_longer_problem_truncated,
 ]
 
 
@@ -138,6 +139,10 @@ def _terminal_sign(prob, rhoT):
     return -ORIG["terminal_adjoint"](prob, rhoT)
 
 
+def _horizon_ignored(ctrl, sysm):
+    return float(sysm.T_ns)
+
+
 def _dd_no_imag_i(ctrl, T, t):
     out = ORIG["dd_dalpha"](ctrl, T, t)
     return [(k, q, (v / 1j if k % 2 == 1 else v)) for k, q, v in out]
@@ -212,6 +217,9 @@ MUTATIONS = {
     "controls sampled at t_j, not t_j+1/2": [(imr, "imr_step", _imr_step_wrong_time)],
     "terminal adjoint sign": [(imr, "terminal_adjoint", _terminal_sign)],
     "imaginary-part derivative missing i": [(imr, "dd_dalpha", _dd_no_imag_i)],
+    "control horizon ignored": [(model, "control_horizon", _horizon_ignored),
+                                (imr, "control_horizon", _horizon_ignored)],
+    "gradient's spline factors on the final time, not the horizon": [(imr, "control_horizon", _horizon_ignored)],
 }
 
 

@@ -373,6 +373,38 @@ def test_gradient_matches_central_differences(objective, hermitian, gamma2):
         assert abs(g[k] - v) <= 1e-6 * scale, (k, g[k], v)
 
 
+def test_control_horizon_prefix_is_the_longer_problem_truncated():
+    """A problem that integrates the first steps of a longer horizon with the
+    longer horizon's controls (eq. rotctrl, splines on [0, T_c]) steps
+    exactly like the longer problem's first steps, and its adjoint gradient
+    -- whose spline factors come from the same horizon -- matches central
+    differences; spline coefficients whose support starts after the prefix
+    get no gradient."""
+    p = W.random_problem(71, levels=(2, 2), n_states=2, n_steps=40, T_ns=0.8, amp=0.1, n_splines=8)
+    full = imr.forward(p, keep=True)
+    pre = copy.deepcopy(p)
+    pre.controls.horizon_ns = p.system.T_ns
+    pre.system.n_steps = 10
+    pre.system.T_ns = 0.2
+    fp = imr.forward(pre, keep=True)
+    for j in range(11):
+        assert np.max(np.abs(fp["q"][j] - full["q"][j])) <= 1e-14
+    G, g, _ = imr.gradient(pre)
+    idx = [0, 1, 2, 3, 9, 10]
+    fd = imr.fd_gradient(pre, eps=1e-6, indices=idx)
+    scale = max(np.max(np.abs(g)), 1e-3)
+    for k in idx:
+        assert abs(g[k] - fd[k]) <= 1e-6 * scale, (k, g[k], fd[k])
+    # spline s is supported on ((s - 2) dtau, (s + 1) dtau), dtau = 0.8/6: the
+    # 0.2 ns prefix meets splines 0..3 only
+    ctrl = pre.controls
+    for q, car in enumerate(ctrl.carriers_ghz):
+        for f in range(len(car)):
+            for sp in range(4, ctrl.n_splines):
+                k = model.alpha_index(ctrl, q, f, sp)
+                assert g[k] == 0.0 and g[k + 1] == 0.0
+
+
 def test_gradient_matches_fd_for_config_shapes():
     """The workload conventions (essential levels, CNOT, two carriers) under
     central differences, on a 100-step prefix of the 2 x 3-level workload."""

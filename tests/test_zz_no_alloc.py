@@ -85,10 +85,19 @@ def test_static_scratch_gradient_matches_workspace_gradient(name):
     h = _unbound_handle(lib, L, prob, prob.ckpt_every)
     try:
         stream = c_void_p(torch.cuda.current_stream().cuda_stream)
-        for _ in range(2):
+        for call in range(2):
             G = c_double()
             g = np.zeros(len(g_ref))
+            if call == 1:
+                # the first call has loaded the module; the second allocates nothing
+                torch.cuda.synchronize()
+                used0 = torch.cuda.memory_allocated()
+                free0 = torch.cuda.mem_get_info()[0]
             L.check(lib.lb_gradient_static(h, stream, byref(G), g.ctypes.data_as(POINTER(c_double))))
+            if call == 1:
+                torch.cuda.synchronize()
+                assert torch.cuda.memory_allocated() == used0
+                assert torch.cuda.mem_get_info()[0] == free0
             assert abs(G.value - G_ref) <= 1e-10 * abs(G_ref)
             assert np.max(np.abs(g - g_ref)) <= 1e-9 * np.max(np.abs(g_ref))
         # the handle is left unbound and still usable
@@ -113,5 +122,25 @@ def test_static_scratch_rejects_oversized_problem():
         rc = lib.lb_gradient_static(h, None, byref(G), None)
         assert rc == L.LB_ENOMEM
         assert b"static scratch" in lib.lb_last_error()
+    finally:
+        lib.lb_system_destroy(h)
+
+
+def test_static_scratch_refuses_the_cluster_sweep():
+    """The entry point runs one CTA per state; an explicit cluster-sweep
+    request is refused on the host rather than silently dropped."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2110_10310_gb300 import _lib as L
+
+    lib = L.load(build_if_missing=True)
+    prob = W.config2(n_steps=50)
+    h = _unbound_handle(lib, L, prob, 10)
+    try:
+        L.check(lib.lb_set_sweep(h, L.LB_SWEEP_CLUSTER))
+        G = c_double()
+        rc = lib.lb_gradient_static(h, None, byref(G), None)
+        assert rc == L.LB_EINVAL
+        assert b"cluster" in lib.lb_last_error().lower()
     finally:
         lib.lb_system_destroy(h)

@@ -17,6 +17,7 @@ from .synthetic import (  # noqa: F401
     config3,
     config4,
     config5,
+    prefix,
     fock_superposition,
     three_gate_states,
     cnot_three_states,

@@ -60,6 +60,10 @@ class ControlSpec:
     n_splines: int
     carriers_ghz: list  # list of 1-D float arrays, one per subsystem
     alpha: np.ndarray  # float64, layout [q][f][s][re, im]
+    # the B-splines span [0, horizon_ns] (None: the system's final time T); a
+    # run over the first steps of a longer horizon keeps that horizon here, so
+    # that its controls are the longer problem's
+    horizon_ns: float | None = None
 
     @property
     def n_params(self) -> int:
@@ -358,6 +362,17 @@ def config5(seed: int = 5, n_steps: int = 20000, levels=(3, 3, 3, 3, 3, 3), n_st
     rho0 = np.stack([pure_density(random_pure_state(rng, N)) for _ in range(n_states)])
     tar = pure_density(random_pure_state(rng, N))
     return Problem("qutrits_6x3", sysm, ctrl, rho0, "frob", targets=np.stack([tar] * n_states), ckpt_every=100)
+
+
+def prefix(prob: Problem, n_steps: int) -> Problem:
+    """The first n_steps steps of ``prob`` at its step size: the final time
+    becomes n_steps dt and the controls keep their horizon (in place; returns
+    ``prob``)."""
+    if not prob.controls.horizon_ns:
+        prob.controls.horizon_ns = prob.system.T_ns
+    prob.system.T_ns = prob.system.T_ns * n_steps / prob.system.n_steps
+    prob.system.n_steps = n_steps
+    return prob
 
 
 def config(n: int, **kw):

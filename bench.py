@@ -656,7 +656,7 @@ def run_gradient(args, rank, world, dev, dist):
     from paper_2110_10310_gb300.system import LindbladSystem, colmajor
 
     wl = args.workload
-    full = problem(workload=wl, states=args.states)
+    full = problem(n_steps=args.n_steps, workload=wl, states=args.states)
     if args.ckpt is not None:
         full.ckpt_every = args.ckpt
     p = D.shard_problem(full, rank, world) if world > 1 else full
@@ -716,9 +716,9 @@ def run_gradient(args, rank, world, dev, dist):
     # controls uploaded every step, G and the gradient read back every step
     pinned = torch.from_numpy(colmajor(p.rho0)).pin_memory()
     alpha = np.ascontiguousarray(p.controls.alpha)
-    e2e_n = min(args.steps, E2E_STEPS)
+    e2e_n = 0 if args.no_e2e else min(args.steps, E2E_STEPS)
     e2e_s = []
-    for i in range(e2e_n + 1):
+    for i in range(e2e_n + 1 if e2e_n else 0):
         flush.zero_()
         torch.cuda.synchronize()
         barrier()
@@ -730,7 +730,7 @@ def run_gradient(args, rank, world, dev, dist):
         if i:
             e2e_s.append(t1 - t0)
     e2e_tot = maxrank(sum(e2e_s))
-    e2e_value = state_steps * e2e_n / e2e_tot
+    e2e_value = state_steps * e2e_n / e2e_tot if e2e_n else None
     h2d = pinned.numel() * 8 + alpha.size * 8 + (0 if p.weights is None else 8 * p.M)
     d2h = 8 + 8 * s.n_params + 64  # G, gradient, status block
 
@@ -826,10 +826,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (long single runs)")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--states", type=int, default=0,
                     help="initial states of qutrits_6x3 / apply_6x3 (default 64; fewer for ncu captures)")
     ap.add_argument("--ckpt", type=int, default=None, help="checkpoint interval (default: the workload's)")
+    ap.add_argument("--n-steps", type=int, default=None,
+                    help="steps of the prefix (default: the workload's; smaller for ncu captures)")
     ap.add_argument("--predictor", type=int, default=-1,
                     help="forward predictor restart period (lb_set_predictor; -1 auto, -2 none)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)

@@ -213,9 +213,12 @@ int lb_objective_set_measure(lb_system* sys, int32_t m, double gamma2);
  * the time integral by the left rectangle rule, weighted per state like the
  * final-time term; its derivative enters the adjoint sweep as the source
  * gamma1 beta_i/M dt beta(t_j) g(q^j) at qhat^j (Appendix B).  gamma1 >= 0
- * (0 = off, the default), a_ns > 0.  Runs in the one-CTA-per-state and
- * cluster sweeps (N^2 <= 4096; lb_bind_workspace refuses grid sweeps with
- * it).  Call before lb_workspace_bytes. */
+ * (0 = off, the default), a_ns > 0.  Runs in every sweep; LB_SWEEP_AUTO
+ * keeps states with N^2 <= 4096 on the one-CTA-per-state or cluster sweeps.
+ * The grid sweep sums each step's merit per block over the states its
+ * contiguous share of the elements covers, so lb_bind_workspace refuses it
+ * (LB_EINVAL) when a block's share spans more than 4 states (very many small
+ * states).  Call before lb_workspace_bytes. */
 int lb_objective_set_penalty(lb_system* sys, double gamma1, double a_ns);
 
 /* Choose the sweep kind (LB_SWEEP_*); call before lb_workspace_bytes. */

@@ -48,7 +48,7 @@ struct Region {
 
 struct Layout {
   Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
-      gproj, gsum, sfac, pen, qb, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, histf,
+      gproj, gsum, sfac, pen, qb, jpen, mpart, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, histf,
       hmap;
   size_t total = 0;
 };
@@ -150,7 +150,7 @@ bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
 bool use_grid(const lb_system* s) {
   if (s->V > lbk::kMaxResidentV) return true;
   if (s->method == LB_SOLVER_GMRES) return false;  // GMRES runs one CTA per state
-  if (s->gamma1 != 0.0) return false;              // the running penalty: one CTA or a cluster per state
+  if (s->gamma1 != 0.0) return s->sweep == LB_SWEEP_GRID;  // the running penalty: AUTO keeps small states per CTA
   if (s->sweep == LB_SWEEP_GRID) return true;
   if (s->sweep == LB_SWEEP_RESIDENT || s->sweep == LB_SWEEP_CLUSTER) return false;
   return s->V >= 1024 && s->M < 64;
@@ -194,6 +194,24 @@ int effective_pred(const lb_system* s) {
   return s->pred;
 }
 
+// The grid sweep's running penalty sums each step's merit per block over the
+// at most 4 states a block's contiguous chunk of elements covers: check that
+// for both element counts per state (all N^2, or N (N + 1) / 2 under the
+// Hermitian symmetry, which is decided per call).
+bool grid_chunks_cover_few_states(const lb_system* s) {
+  const long long vh[2] = {(long long)s->V, (long long)s->N * (s->N + 1) / 2};
+  for (long long Vh : vh) {
+    const long long total = (long long)s->M * Vh;
+    const long long per = (total + s->gblocks - 1) / s->gblocks;
+    const long long chunk = (per + 31) / 32 * 32;
+    for (long long e0 = 0; e0 < total; e0 += chunk) {
+      const long long e1 = std::min(total, e0 + chunk);
+      if ((e1 - 1) / Vh - e0 / Vh + 1 > 4) return false;
+    }
+  }
+  return true;
+}
+
 // every checkpoint must be a restart point of the forward predictor
 int check_predictor(const lb_system* s) {
   const int K = effective_K(s), R = effective_pred(s);
@@ -229,8 +247,6 @@ int decide_krylov(lb_system* s) {
   LB_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
   LB_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "cudaDeviceGetAttribute");
   s->krylov = s->V <= lbk::kMaxResidentV ? lbk::gmres_krylov_dim(s->V, n_coef(s), n_jcoef(s), s->N, (size_t)optin) : 0;
-  if (s->gamma1 != 0.0 && (s->V > lbk::kMaxResidentV || s->sweep == LB_SWEEP_GRID))
-    return fail(LB_EINVAL, "the running penalty runs in the one-CTA-per-state and cluster sweeps only (N^2 <= 4096)");
   if (s->method != LB_SOLVER_GMRES) return LB_OK;
   if (s->sweep == LB_SWEEP_GRID || s->sweep == LB_SWEEP_CLUSTER)
     return fail(LB_EINVAL, "GMRES runs in the one-CTA-per-state sweep only (LB_SWEEP_RESIDENT or AUTO)");
@@ -286,6 +302,8 @@ Layout make_layout(const lb_system* s) {
   take(L.sfac, sizeof(double) * NT);
   take(L.pen, sizeof(double) * NT);
   take(L.qb, s->gamma1 != 0.0 ? c2 * M * V : 0);
+  take(L.jpen, s->gamma1 != 0.0 ? sizeof(double) * M : 0);
+  take(L.mpart, s->gamma1 != 0.0 && use_grid(s) ? sizeof(double) * lbk::kMaxGridBlocks * 4 : 0);
   take(L.q0, c2 * M * V);
   take(L.tar, c2 * M * V);
   take(L.wgt, sizeof(double) * M);
@@ -526,6 +544,8 @@ void fill_prob(lb_system* s) {
   P.sfac = at<double>(s, s->L.sfac);
   P.pen = at<double>(s, s->L.pen);
   P.qb = at<double2>(s, s->L.qb);
+  P.jpen = at<double>(s, s->L.jpen);
+  P.mpart = at<double>(s, s->L.mpart);
   P.gamma1 = s->gamma1;
   P.pen_a = s->pen_a;
   P.J = at<double>(s, s->L.J);
@@ -1075,6 +1095,9 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
     s->gsmem = lbk::grid_smem_bytes(n_coef(s), n_jcoef(s));
     s->gblocks = lbk::grid_blocks_max(s->gsmem);
     if (s->gblocks <= 0) return fail(LB_ECUDA, "cannot size the cooperative grid of the sweep kernels");
+    if (s->gamma1 != 0.0 && !grid_chunks_cover_few_states(s))
+      return fail(LB_EINVAL, "the running penalty on grid sweeps needs every block's elements to span at most "
+                             "4 states (too many small states for the grid sweep)");
   }
   if (!s->upload_done) LB_CUDA(cudaEventCreateWithFlags(&s->upload_done, cudaEventDisableTiming), "cudaEventCreate");
   s->ws = static_cast<char*>(ws);
@@ -1132,6 +1155,7 @@ static int run_forward(lb_system* s, cudaStream_t st, int tape) {
   if (use_grid(s)) {
     LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.gslots), 0, s->L.gslots.bytes, st), "clear grid slots");
     LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.bar), 0, s->L.bar.bytes, st), "clear grid barrier");
+    if (s->gamma1 != 0.0) LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.jpen), 0, s->L.jpen.bytes, st), "clear penalty");
     if (s->timing) LB_CUDA(cudaEventRecord(s->ev[0], st), "cudaEventRecord");
     LB_CUDA(lbk::launch_sweep_grid(s->dp, 0, 1, tape, 0, s->NT, nullptr, s->M, s->gblocks, s->gsmem, st),
             "forward grid sweep");

@@ -245,10 +245,24 @@ __device__ __forceinline__ void grid_record(const ProbDev& P, size_t stride, Gri
   h.ring[(size_t)h.slot * stride + o] = make_double2(cr, ci);
 }
 
+// Running penalty (Sec. III, eq. optimproblem): with penw != 0 the first
+// pass of a forward solve also sums each state's merit summand of its
+// right-hand side q^j against the target, per block for the (at most
+// kLocalStates) states of the block's chunk; after the first grid barrier
+// block 0 adds penw * J(q^j) to P.jpen per state, summing the blocks in a
+// fixed order.
+__device__ __forceinline__ double merit_summand(int kind, double2 q, double2 t) {
+  if (kind == LB_J_FROB) {
+    const double dr = q.x - t.x, di = q.y - t.y;
+    return fma(dr, dr, di * di);
+  }
+  return fma(t.x, q.x, t.y * q.y);
+}
+
 template <bool ADJ>
 __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __restrict__ rhs,
                           const double2* __restrict__ ct, double fac, long long& it_global, long long& solve,
-                          double2** zout, GridHist hist = GridHist()) {
+                          double2** zout, GridHist hist = GridHist(), double penw = 0.0) {
   const GridHdr& G = *S.g;
   const Hdr& H = G.h;
   const Tabs T{S.cu, S.cd, S.jf, S.ja};
@@ -264,11 +278,20 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
   {
     StateMax sm;
     sm.init(e0, e1, G.Vh);
+    double msum[kLocalStates] = {0.0, 0.0, 0.0, 0.0};
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       const GEl g = gel(G, P.hmap, e);
       const int b = g.b, v = g.v;
       const size_t o = (size_t)b * V + v;
       const double2 r = rhs[o];
+      if (penw != 0.0) {
+        // an off-diagonal element under the symmetry stands for its mirror too
+        const double f = merit_summand(H.kind, r, P.tar[o]) * (g.vm >= 0 ? 2.0 : 1.0);
+        const int k = b - sm.sb0;
+#pragma unroll
+        for (int u = 0; u < kLocalStates; ++u)
+          if (u == k) msum[u] += f;
+      }
       double2 z0 = r;
       if (!neumann) {
         double ur = r.x, ui = r.y;
@@ -287,8 +310,38 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
       sm.add(b, umax64(abs_bits(r.x), abs_bits(r.y)), qbank);
     }
     sm.push(qbank, red);
+    if (penw != 0.0) {
+      // per-block merit sums of the chunk's states, in a fixed order
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+      double* dred = S.red;
+#pragma unroll
+      for (int u = 0; u < kLocalStates; ++u) {
+        const double w = warp_sum(msum[u]);
+        if (lane == 0) dred[u * 8 + warp] = w;
+      }
+      __syncthreads();
+      if ((int)threadIdx.x < kLocalStates) {
+        double t = 0.0;
+        for (int w = 0; w < nwarps; ++w) t += dred[threadIdx.x * 8 + w];
+        P.mpart[(size_t)blockIdx.x * kLocalStates + threadIdx.x] = t;
+      }
+      __syncthreads();
+    }
   }
   if (!grid_sync(P.bar, gridDim.x, P.spin_limit > 0 ? P.spin_limit : kSpinLimit)) return -3;
+  if (penw != 0.0 && blockIdx.x == 0) {
+    // state b's merit sum over the blocks whose chunk covers it, in block order
+    for (int b = threadIdx.x; b < M; b += blockDim.x) {
+      double t = 0.0;
+      for (int bb = 0; bb < (int)gridDim.x; ++bb) {
+        const long long f0 = (long long)bb * G.chunk, f1 = min(G.total, f0 + G.chunk);
+        if (f0 >= f1) break;
+        const int s0 = (int)(f0 / G.Vh), s1 = (int)((f1 - 1) / G.Vh);
+        if (b >= s0 && b <= s1) t += __ldcg(P.mpart + (size_t)bb * kLocalStates + (b - s0));
+      }
+      P.jpen[b] = fma(penw, merit_value(H.kind, t), P.jpen[b]);
+    }
+  }
   // the previous solve's |q| bank is free again: clear it for the next solve
   if (blockIdx.x == 0)
     for (int b = threadIdx.x; b < M; b += blockDim.x) qslots[((solve + 1) & 1) * M + b] = 0;
@@ -398,6 +451,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
   // restart point and the recompute repeats these iterates bit for bit)
   const int R = P.pred_restart;
   const bool pred = mode == 0 && R >= 0;
+  // the running penalty is summed over the forward sweep of the system's own states
+  const bool penal = mode == 0 && H.gamma1 != 0.0;
   const double hh = 0.5 * H.h;
   GridHist hist;
   hist.ring = P.hist;
@@ -414,7 +469,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
     double2* z = nullptr;
     const int it = mode == 2 ? grid_solve<true>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, &z)
                              : grid_solve<false>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, &z,
-                                                 pred ? hist : GridHist());
+                                                 pred ? hist : GridHist(), penal ? P.pen[j] : 0.0);
     if (it < 0) {
       grid_fail(P, it, j);
       break;
@@ -465,6 +520,15 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
       gput(P.lam, g, V, make_double2(wt * t.x, wt * t.y));
     }
   }
+  // running penalty: q^j is rebuilt backwards, q^j = 2 z^j - q^{j+1}, in
+  // P.qb (each element by its own thread), from q^{N_T}
+  const bool penal = H.gamma1 != 0.0;
+  if (penal)
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const GEl g = gel(G, P.hmap, e);
+      const size_t o = (size_t)g.b * V + g.v;
+      P.qb[o] = P.qT[o];
+    }
   long long itg = 0, nsolve = 0;
   unsigned long long it_rec = 0, st_rec = 0, it_adj = 0, st_adj = 0;
   int maxit = 0;
@@ -583,7 +647,23 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
             // qhat^j = 2 zhat - qhat^{j+1}: no other thread reads this element in the pass
             const double2 zz = zh[o], ll = P.lam[o];
             if (apred) grid_record<true>(P, hstride, ahist, o, v, hh, zz, ll);
-            gput(P.lam, g, V, make_double2(fma(2.0, zz.x, -ll.x), fma(2.0, zz.y, -ll.y)));
+            double2 ln = make_double2(fma(2.0, zz.x, -ll.x), fma(2.0, zz.y, -ll.y));
+            if (penal) {
+              // the running penalty's source gamma1 beta_i/M dt beta(t_j) g(q^j) (Appendix B)
+              const double2 qn = P.qb[o], t = P.tar[o];
+              const double2 qj = make_double2(fma(2.0, Z.x, -qn.x), fma(2.0, Z.y, -qn.y));
+              P.qb[o] = qj;
+              const double pw = H.gamma1 * P.wgt[b] * P.pen[j];
+              if (H.kind == LB_J_FROB) {
+                ln.x = fma(pw, qj.x - t.x, ln.x);
+                ln.y = fma(pw, qj.y - t.y, ln.y);
+              } else {
+                const double ls = pw * linear_sign(H.kind);
+                ln.x = fma(ls, t.x, ln.x);
+                ln.y = fma(ls, t.y, ln.y);
+              }
+            }
+            gput(P.lam, g, V, ln);
           }
         }
 #pragma unroll
@@ -653,7 +733,7 @@ __global__ void k_objective_states(const ProbDev* __restrict__ pp) {
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-    P.J[i] = merit_value(P.kind, t);
+    P.J[i] = merit_value(P.kind, t) + (P.gamma1 != 0.0 ? P.gamma1 * P.jpen[i] : 0.0);
   }
 }
 }  // namespace

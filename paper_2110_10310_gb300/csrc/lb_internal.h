@@ -73,6 +73,8 @@ struct ProbDev {
   double* sfac;              // [NT] factor of the inner stopping test per step (k_stop_factors)
   double* pen;               // [NT] running-penalty weights dt beta(t_j) (gamma1 != 0)
   double2* qb;               // [M*V] q^j rebuilt backwards in the adjoint sweep (gamma1 != 0)
+  double* jpen;              // [M] grid sweeps: sum_j dt beta(t_j) J(q^j) per state (gamma1 != 0)
+  double* mpart;             // [grid_blocks][4] grid sweeps: per-block merit sums of one step (gamma1 != 0)
   double gamma1, pen_a;      // running-penalty weight and width a (ns)
   // states and objective
   double2* q0;               // [M*V]

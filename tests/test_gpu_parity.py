@@ -273,12 +273,12 @@ def test_overflowing_input_reports_nan_with_its_step(sweep):
     s.set_alpha(a0)
     bad = p.rho0.copy()
     bad[1, 2, 2] = np.nan
-    s.set_states_host(bad)
+    s.set_states_host(bad, p.weights)
     with pytest.raises(L.LBError) as e:
         s.forward()
     assert e.value.code == L.LB_ENAN
     assert "time step 0" in str(e.value)
-    s.set_states_host(p.rho0)
+    s.set_states_host(p.rho0, p.weights)
     G, g = s.gradient()
     Go, go, _ = imr.gradient(p)
     assert abs(G - Go) <= 1e-10 * abs(Go)
@@ -845,10 +845,30 @@ def test_running_penalty_with_jnm_and_sweep_rules():
 
     p = W.reset_ensemble(levels=(2, 3), n_steps=300, T_ns=15.0, n_splines=8, amp=0.05)
     p.gamma1, p.penalty_a = 0.4, 5.0
-    for sweep in (L.LB_SWEEP_AUTO, L.LB_SWEEP_CLUSTER, L.LB_SWEEP_RESIDENT):
+    for sweep in (L.LB_SWEEP_AUTO, L.LB_SWEEP_CLUSTER, L.LB_SWEEP_RESIDENT, L.LB_SWEEP_GRID):
         _check_problem(p, sweep=sweep)
-    with pytest.raises(L.LBError):
-        _sys(p, sweep=L.LB_SWEEP_GRID)
+
+
+@pytest.mark.parametrize("levels,objective,K,herm", [((3, 3), "frob", 7, True), ((2, 3), "trace", 0, False),
+                                                     ((3, 2, 2), "frob", 100, False)])
+def test_running_penalty_on_the_grid_sweep_matches_oracle(levels, objective, K, herm):
+    """The grid sweep sums the running penalty's merit per step over blocks
+    in a fixed order and adds its adjoint source from q^j rebuilt backwards:
+    objective and gradient against the oracle, the same with and without
+    checkpoints, and bitwise across checkpoint intervals with the same
+    predictor restarts."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(123, levels=levels, n_states=3, n_steps=40, T_ns=0.8, amp=0.1, objective=objective,
+                         ckpt_every=K, gamma2=0.05, hermitian=herm)
+    p.gamma1, p.penalty_a = 0.6, 0.3
+    s, g = _check_problem(p, sweep=L.LB_SWEEP_GRID)
+    assert s.stats()["sweep"] == "grid"
+    assert s.stats()["symmetry"] == ("hermitian" if herm else "none")
+    if K:
+        G0, g0 = _sys(p, sweep=L.LB_SWEEP_GRID, ckpt_every=0, predictor=K).gradient()
+        G1, g1 = s.gradient()
+        assert G0 == G1 and np.array_equal(g0, g1)
 
 
 def test_running_penalty_cluster_checkpoints_bitwise():

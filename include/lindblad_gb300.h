@@ -137,7 +137,8 @@ typedef struct lb_stats {
   int32_t sweep;            /* LB_SWEEP_* kind the call ran with */
   int32_t solver;           /* LB_SOLVER_* it ran with */
   int32_t ckpt_every;       /* checkpoint interval in effect (0 = every stage vector kept) */
-  int32_t symmetry;         /* LB_SYM_HERMITIAN when the grid sweep iterated k <= l only */
+  int32_t symmetry;         /* LB_SYM_HERMITIAN when the sweep iterated k <= l only */
+  int32_t states_integrated; /* states the sweeps integrated (conjugate pairs count once, lb_set_pairing) */
 } lb_stats;
 
 /* ---- system ------------------------------------------------------------- */
@@ -220,6 +221,22 @@ int lb_objective_set_measure(lb_system* sys, int32_t m, double gamma2);
  * (LB_EINVAL) when a block's share spans more than 4 states (very many small
  * states).  Call before lb_workspace_bytes. */
 int lb_objective_set_penalty(lb_system* sys, double gamma1, double a_ns);
+
+/* Conjugate pairs of initial states (Sec. III-B: the basis |k><j| of a gate
+ * objective holds |k><j| and |j><k| = (|k><j|)^+).  Lindblad's equation and
+ * the implicit midpoint step commute with the conjugate transpose, so with
+ * on = 1 (the default) a state that is exactly (entry by entry) the
+ * conjugate transpose of an earlier one, and whose explicit target is that
+ * earlier target's conjugate transpose (gate and J_Nm targets follow), is not
+ * integrated: its final state is the conjugate transpose of its partner's,
+ * its merit equals the partner's (J_Frob, J_Tr and J_Nm are invariant), and
+ * so does its share of the gradient (eq. reducedgradient), so the partner is
+ * integrated once with the sum of both weights.  lb_forward still returns all
+ * M final states; lb_stats.states_integrated and the state-steps count the
+ * integrated ones.  With a workspace bound, new states or targets must pair
+ * the same way (LB_EINVAL otherwise).  on = 0 integrates every state.  Call
+ * before lb_workspace_bytes. */
+int lb_set_pairing(lb_system* sys, int32_t on);
 
 /* Choose the sweep kind (LB_SWEEP_*); call before lb_workspace_bytes. */
 int lb_set_sweep(lb_system* sys, int32_t sweep);

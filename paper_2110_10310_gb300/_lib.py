@@ -84,6 +84,7 @@ class lb_stats(ctypes.Structure):
         ("solver", c_int32),
         ("ckpt_every", c_int32),
         ("symmetry", c_int32),
+        ("states_integrated", c_int32),
     ]
 
 
@@ -103,6 +104,7 @@ SIGNATURES = {
     "lb_set_sweep": (c_int32, [c_void_p, c_int32]),
     "lb_set_symmetry": (c_int32, [c_void_p, c_int32]),
     "lb_set_predictor": (c_int32, [c_void_p, c_int32]),
+    "lb_set_pairing": (c_int32, [c_void_p, c_int32]),
     "lb_set_wait_limit": (c_int32, [c_void_p, c_int64]),
     "lb_system_set_coupling": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_double)]),
     "lb_workspace_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),

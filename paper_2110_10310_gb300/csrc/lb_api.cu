@@ -48,7 +48,7 @@ struct Region {
 
 struct Layout {
   Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
-      gproj, gsum, sfac, pen, qb, jpen, mpart, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, histf,
+      gproj, gsum, sfac, pen, qb, jpen, mpart, pmap, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, histf,
       hmap;
   size_t total = 0;
 };
@@ -73,10 +73,19 @@ struct lb_system {
   std::vector<double> carriers;  // rad/ns
   std::vector<double> alpha;     // GHz, [q][f][s][re, im]
   int n_params = 0;
-  // states and objective (Sec. III)
+  // states and objective (Sec. III).  Of two states that are each other's
+  // conjugate transpose, with targets that are too, only the first is
+  // integrated (Lindblad's equation and the implicit midpoint step commute
+  // with the conjugate transpose, so the second's final state, merit and
+  // gradient share follow from the first's); M counts the integrated states.
   int M = 0;
-  std::vector<double> rho0;  // kept only while no workspace is bound
-  std::vector<double> wgt;   // beta_i / M
+  int Mu = 0;                  // states given by lb_states_set
+  int pairing = 1;             // integrate one state of each conjugate pair (lb_set_pairing)
+  std::vector<int32_t> pmap;   // [Mu] integrated index * 2 (+1 when the state is its conjugate transpose)
+  std::vector<int32_t> evo;    // [M] lb_states_set index of each integrated state
+  std::vector<double> rho0;    // [Mu] kept only while no workspace is bound
+  std::vector<double> wgt_u;   // [Mu] beta_u / Mu
+  std::vector<double> wgt;     // [M] sum of beta_u / Mu over the states each one stands for
   int kind = LB_J_FROB;
   int target_mode = 0;  // 0 none, 1 explicit, 2 gate
   std::vector<double> targets;
@@ -332,6 +341,7 @@ Layout make_layout(const lb_system* s) {
   take(L.hist, c2 * lbk::kRingOrder * M * V);
   take(L.histf, recompute_predicts(s) ? c2 * lbk::kRingOrder * M * V : 0);
   take(L.hmap, sizeof(int32_t) * (size_t)s->N * (s->N + 1) / 2);
+  take(L.pmap, sizeof(int32_t) * (size_t)s->Mu);
   L.total = off;
   return L;
 }
@@ -371,9 +381,88 @@ int upload_symmetry_map(lb_system* s, cudaStream_t st) {
   return LB_OK;
 }
 
+// b == a^+ entry by entry (column-major N x N complex, interleaved)
+bool is_conj_transpose(const double* a, const double* b, int N) {
+  for (int l = 0; l < N; ++l)
+    for (int k = 0; k < N; ++k) {
+      const size_t p = (size_t)2 * (k + (size_t)N * l), q = (size_t)2 * (l + (size_t)N * k);
+      if (b[p] != a[q] || b[p + 1] != -a[q + 1]) return false;
+    }
+  return true;
+}
+
+// Conjugate pairs among the Mu states `rho` (with explicit targets `tar`, or
+// null when the targets follow from the states or are all the same real
+// diagonal): state w after u with rho_w = rho_u^+ (and tar_w = tar_u^+) is
+// carried by u.  pmap[u] = 2 e (+1 for a carried state), evo[e] = u.
+void find_pairs(const lb_system* s, const double* rho, const double* tar, std::vector<int32_t>& pmap,
+                std::vector<int32_t>& evo) {
+  const int Mu = s->Mu, N = s->N;
+  const size_t st = (size_t)2 * s->V;
+  pmap.assign(Mu, -1);
+  evo.clear();
+  for (int u = 0; u < Mu; ++u) {
+    if (pmap[u] >= 0) continue;
+    const int e = (int)evo.size();
+    evo.push_back(u);
+    pmap[u] = 2 * e;
+    if (!s->pairing) continue;
+    for (int w = u + 1; w < Mu; ++w) {
+      if (pmap[w] >= 0) continue;
+      if (!is_conj_transpose(rho + u * st, rho + w * st, N)) continue;
+      if (tar && !is_conj_transpose(tar + u * st, tar + w * st, N)) continue;
+      pmap[w] = 2 * e + 1;
+      break;
+    }
+  }
+}
+
+// explicit targets that must pair with the states (null: none, or every
+// state's target the same real diagonal N_m)
+const double* pairing_targets(const lb_system* s) {
+  return (s->target_mode == 1 && s->kind != LB_J_NM && !s->targets.empty()) ? s->targets.data() : nullptr;
+}
+
+// the integrated states' weights from the per-state ones
+void apply_pairs(lb_system* s) {
+  s->M = (int)s->evo.size();
+  s->wgt.assign(s->M, 0.0);
+  for (int u = 0; u < s->Mu; ++u) s->wgt[s->pmap[u] >> 1] += s->wgt_u[u];
+}
+
+// re-decide the pairs from the host copies (no workspace bound)
+void update_pairs(lb_system* s) {
+  if (s->Mu < 1 || s->rho0.empty()) return;
+  find_pairs(s, s->rho0.data(), pairing_targets(s), s->pmap, s->evo);
+  apply_pairs(s);
+}
+
+// with a workspace bound the pairs are fixed: new states or targets must pair
+// the same way
+int check_pairs(lb_system* s, const double* rho, const double* tar) {
+  std::vector<int32_t> pm, ev;
+  find_pairs(s, rho, tar, pm, ev);
+  if (pm != s->pmap)
+    return fail(LB_EINVAL, "the states' conjugate pairs differ from those the workspace was bound with (rebind)");
+  return LB_OK;
+}
+
+// the integrated states of the Mu given ones (pageable; staged before cudaMemcpyAsync returns)
+std::vector<double> gather_states(const lb_system* s, const double* a) {
+  const size_t st = (size_t)2 * s->V;
+  std::vector<double> out(st * s->M);
+  for (int e = 0; e < s->M; ++e) std::memcpy(out.data() + e * st, a + s->evo[e] * st, sizeof(double) * st);
+  return out;
+}
+
 int upload_states(lb_system* s, const double* rho0, cudaStream_t st) {
   const size_t bytes = sizeof(double2) * (size_t)s->M * s->V;
-  LB_CUDA(cudaMemcpyAsync(at<double2>(s, s->L.q0), rho0, bytes, cudaMemcpyHostToDevice, st), "upload states");
+  if (s->M == s->Mu) {
+    LB_CUDA(cudaMemcpyAsync(at<double2>(s, s->L.q0), rho0, bytes, cudaMemcpyHostToDevice, st), "upload states");
+  } else {
+    const std::vector<double> g = gather_states(s, rho0);
+    LB_CUDA(cudaMemcpyAsync(at<double2>(s, s->L.q0), g.data(), bytes, cudaMemcpyHostToDevice, st), "upload states");
+  }
   LB_CUDA(cudaMemcpyAsync(at<double>(s, s->L.wgt), s->wgt.data(), sizeof(double) * s->M, cudaMemcpyHostToDevice, st),
           "upload weights");
   return LB_OK;
@@ -382,8 +471,14 @@ int upload_states(lb_system* s, const double* rho0, cudaStream_t st) {
 int upload_targets(lb_system* s, cudaStream_t st) {
   const size_t bytes = sizeof(double2) * (size_t)s->M * s->V;
   if (s->target_mode == 1) {
-    LB_CUDA(cudaMemcpyAsync(at<double2>(s, s->L.tar), s->targets.data(), bytes, cudaMemcpyHostToDevice, st),
-            "upload targets");
+    if (s->M == s->Mu) {
+      LB_CUDA(cudaMemcpyAsync(at<double2>(s, s->L.tar), s->targets.data(), bytes, cudaMemcpyHostToDevice, st),
+              "upload targets");
+    } else {
+      const std::vector<double> g = gather_states(s, s->targets.data());
+      LB_CUDA(cudaMemcpyAsync(at<double2>(s, s->L.tar), g.data(), bytes, cudaMemcpyHostToDevice, st),
+              "upload targets");
+    }
   } else if (s->target_mode == 2) {
     // essential <-> full index maps (subsystem 0 most significant)
     std::vector<int32_t> emap(s->N, -1), efull(s->Ne, 0);
@@ -860,7 +955,7 @@ int lb_controls_set(lb_system* s, const double* alpha, int64_t n) {
 int lb_states_set(lb_system* s, int32_t M, const double* rho0, const double* weights) {
   if (!s || !rho0) return fail(LB_EINVAL, "null argument");
   if (M < 1) return fail(LB_EINVAL, "M must be >= 1");
-  if (s->ws && M != s->M) return fail(LB_EINVAL, "M cannot change while a workspace is bound");
+  if (s->ws && M != s->Mu) return fail(LB_EINVAL, "M cannot change while a workspace is bound");
   std::vector<double> w(M, 1.0);
   if (weights)
     for (int i = 0; i < M; ++i) {
@@ -868,11 +963,16 @@ int lb_states_set(lb_system* s, int32_t M, const double* rho0, const double* wei
       w[i] = weights[i];
     }
   for (int i = 0; i < M; ++i) w[i] /= (double)M;
-  if (s->M != M && s->target_mode == 1) s->target_mode = 0;  // explicit targets no longer match
-  s->M = M;
-  s->wgt = w;
+  if (s->ws) {
+    int rc = check_pairs(s, rho0, pairing_targets(s));
+    if (rc) return rc;
+  }
+  if (s->Mu != M && s->target_mode == 1) s->target_mode = 0;  // explicit targets no longer match
+  s->Mu = M;
+  s->wgt_u = w;
   s->rho_herm = hermitian_matrices(rho0, M, s->N);
   if (s->ws) {
+    apply_pairs(s);
     int rc = upload_states(s, rho0, s->bind_stream);
     if (rc) return rc;
     if (s->target_mode == 2) {
@@ -882,6 +982,7 @@ int lb_states_set(lb_system* s, int32_t M, const double* rho0, const double* wei
     return refresh_symmetry(s);
   }
   s->rho0.assign(rho0, rho0 + (size_t)2 * M * s->V);
+  update_pairs(s);
   return LB_OK;
 }
 
@@ -889,12 +990,22 @@ int lb_objective_set(lb_system* s, int32_t kind, const double* targets, double g
   if (!s || !targets) return fail(LB_EINVAL, "null argument");
   if (kind != LB_J_FROB && kind != LB_J_TR) return fail(LB_EINVAL, "unknown merit functional");
   if (!(gamma2 >= 0.0) || !std::isfinite(gamma2)) return fail(LB_EINVAL, "gamma2 must be finite and >= 0");
-  if (s->M < 1) return fail(LB_EINVAL, "call lb_states_set first");
+  if (s->Mu < 1) return fail(LB_EINVAL, "call lb_states_set first");
+  if (s->ws) {
+    // the pairs are fixed while bound: these targets must not split them
+    for (int u = 0; u < s->Mu; ++u) {
+      const int e = s->pmap[u] >> 1, c = s->pmap[u] & 1;
+      const size_t st = (size_t)2 * s->V;
+      if (c && !is_conj_transpose(targets + s->evo[e] * st, targets + u * st, s->N))
+        return fail(LB_EINVAL, "the targets split conjugate pairs of states the workspace was bound with (rebind)");
+    }
+  }
   s->kind = kind;
   s->gamma2 = gamma2;
   s->target_mode = 1;
-  s->targets.assign(targets, targets + (size_t)2 * s->M * s->V);
-  s->tar_herm = hermitian_matrices(targets, s->M, s->N);
+  s->targets.assign(targets, targets + (size_t)2 * s->Mu * s->V);
+  s->tar_herm = hermitian_matrices(targets, s->Mu, s->N);
+  if (!s->ws) update_pairs(s);
   if (s->ws) {
     s->hp.kind = kind;
     s->hp.gamma2 = gamma2;
@@ -909,17 +1020,18 @@ int lb_objective_set_measure(lb_system* s, int32_t m, double gamma2) {
   if (!s) return fail(LB_EINVAL, "null argument");
   if (m < 0 || m >= s->N) return fail(LB_EINVAL, "m must be in 0..N-1");
   if (!(gamma2 >= 0.0) || !std::isfinite(gamma2)) return fail(LB_EINVAL, "gamma2 must be finite and >= 0");
-  if (s->M < 1) return fail(LB_EINVAL, "call lb_states_set first");
+  if (s->Mu < 1) return fail(LB_EINVAL, "call lb_states_set first");
   if (s->ws && s->target_mode == 2) return fail(LB_EINVAL, "cannot leave a gate objective once a workspace is bound");
   // N_m as the (real, diagonal) target of every state
-  std::vector<double> t((size_t)2 * s->M * s->V, 0.0);
-  for (int i = 0; i < s->M; ++i)
+  std::vector<double> t((size_t)2 * s->Mu * s->V, 0.0);
+  for (int i = 0; i < s->Mu; ++i)
     for (int l = 0; l < s->N; ++l) t[(size_t)2 * ((size_t)i * s->V + l + (size_t)s->N * l)] = std::abs(l - m);
   s->kind = LB_J_NM;
   s->gamma2 = gamma2;
   s->target_mode = 1;
   s->targets.swap(t);
   s->tar_herm = true;
+  if (!s->ws) update_pairs(s);
   if (s->ws) {
     s->hp.kind = LB_J_NM;
     s->hp.gamma2 = gamma2;
@@ -941,6 +1053,7 @@ int lb_objective_set_gate(lb_system* s, int32_t kind, const double* V, double ga
   s->gateV.assign(V, V + (size_t)2 * s->Ne * s->Ne);
   s->targets.clear();
   s->tar_herm = true;
+  if (!s->ws) update_pairs(s);
   if (s->ws) {
     s->hp.kind = kind;
     s->hp.gamma2 = gamma2;
@@ -1020,6 +1133,15 @@ int lb_set_wait_limit(lb_system* s, int64_t polls) {
             "upload wait limit");
     LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
   }
+  return LB_OK;
+}
+
+int lb_set_pairing(lb_system* s, int32_t on) {
+  if (!s) return fail(LB_EINVAL, "null system handle");
+  if (s->ws) return fail(LB_EINVAL, "choose the pairing before binding a workspace");
+  if (on != 0 && on != 1) return fail(LB_EINVAL, "pairing must be 0 or 1");
+  s->pairing = on;
+  update_pairs(s);
   return LB_OK;
 }
 
@@ -1136,6 +1258,9 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
   if (rc) return rc;
   rc = upload_controls(s, st);
   if (rc) return rc;
+  LB_CUDA(cudaMemcpyAsync(at<int32_t>(s, s->L.pmap), s->pmap.data(), sizeof(int32_t) * s->Mu, cudaMemcpyHostToDevice,
+                          st),
+          "upload state pairs");
   s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, s->jp.empty(), kry_elems(s));
   // the workspace now owns the states; pageable copies above are staged
   s->rho0.clear();
@@ -1199,6 +1324,7 @@ static int finish(lb_system* s, cudaStream_t st, double* G_out, double* grad_out
   s->last.solver = s->method;
   s->last.ckpt_every = effective_K(s);
   s->last.symmetry = s->hp.herm ? LB_SYM_HERMITIAN : LB_SYM_NONE;
+  s->last.states_integrated = s->M;
   if (s->timed_fwd) LB_CUDA(cudaEventElapsedTime(&s->last.ms_forward, s->ev[0], s->ev[1]), "cudaEventElapsedTime");
   if (s->timed_bwd) LB_CUDA(cudaEventElapsedTime(&s->last.ms_backward, s->ev[2], s->ev[3]), "cudaEventElapsedTime");
   if (rc) return rc;
@@ -1215,10 +1341,19 @@ int lb_forward(lb_system* s, void* stream, double* G_out, void* rhoT_dev_out) {
   if (rc) return rc;
   LB_CUDA(lbk::launch_finalize(s->dp, 1, 0, 0, st), "objective kernel");
   s->launches += 1;
-  if (rhoT_dev_out)
-    LB_CUDA(cudaMemcpyAsync(rhoT_dev_out, at<double2>(s, s->L.qT), sizeof(double2) * (size_t)s->M * s->V,
-                            cudaMemcpyDeviceToDevice, st),
-            "copy final states");
+  if (rhoT_dev_out) {
+    if (s->M == s->Mu) {
+      LB_CUDA(cudaMemcpyAsync(rhoT_dev_out, at<double2>(s, s->L.qT), sizeof(double2) * (size_t)s->M * s->V,
+                              cudaMemcpyDeviceToDevice, st),
+              "copy final states");
+    } else {
+      // every given state: its integrated state or that state's conjugate transpose
+      LB_CUDA(lbk::launch_expand_states(at<double2>(s, s->L.qT), at<int32_t>(s, s->L.pmap), s->Mu, s->N,
+                                        static_cast<double2*>(rhoT_dev_out), st),
+              "final states kernel");
+      s->launches += 1;
+    }
+  }
   return finish(s, st, G_out, nullptr);
 }
 
@@ -1790,6 +1925,9 @@ int static_bind(lb_system* s, void* ws, cudaStream_t st) {
   if (rc) return rc;
   rc = upload_controls(s, st);
   if (rc) return rc;
+  LB_CUDA(cudaMemcpyAsync(at<int32_t>(s, s->L.pmap), s->pmap.data(), sizeof(int32_t) * s->Mu, cudaMemcpyHostToDevice,
+                          st),
+          "upload state pairs");
   s->rc = lbk::resident_config(s->V, s->Q, n_coef(s), n_jcoef(s), s->N, s->jp.empty(), kry_elems(s));
   return LB_OK;
 }

@@ -184,5 +184,7 @@ cudaError_t launch_backward_cluster(const ProbDev* d_prob, int M, const ClusterC
 cudaError_t launch_propagate_cluster(const ProbDev* d_prob, int adjoint, int64_t j0, int64_t j1, double2* x, int n_vec,
                                      const ClusterConfig& cc, cudaStream_t s);
 cudaError_t launch_objective_states(const ProbDev* d_prob, int M, cudaStream_t s);
+// out[u] = qT[pmap[u] / 2], conjugate-transposed when pmap[u] is odd (u < Mu)
+cudaError_t launch_expand_states(const double2* qT, const int32_t* pmap, int Mu, int N, double2* out, cudaStream_t s);
 
 }  // namespace lbk

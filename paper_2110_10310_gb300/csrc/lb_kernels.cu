@@ -277,6 +277,26 @@ __global__ void k_apply(const ProbDev* __restrict__ pp, int step, const double2*
 }
 
 
+// The final state of every given state (lb_forward): its integrated state,
+// or for the second state of a conjugate pair the conjugate transpose of its
+// partner's (Lindblad's equation and the implicit midpoint step commute with
+// the conjugate transpose).
+__global__ void k_expand_states(const double2* __restrict__ qT, const int32_t* __restrict__ pmap, int Mu, int N,
+                                double2* __restrict__ out) {
+  const size_t V = (size_t)N * N;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)Mu * V) return;
+  const int u = (int)(t / V);
+  const int v = (int)(t - (size_t)u * V);
+  const int e = pmap[u] >> 1;
+  if (pmap[u] & 1) {
+    const int k = v % N, l = v / N;
+    const double2 x = qT[(size_t)e * V + l + (size_t)N * k];
+    out[t] = make_double2(x.x, -x.y);
+  } else {
+    out[t] = qT[(size_t)e * V + v];
+  }
+}
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -322,6 +342,12 @@ cudaError_t launch_finalize(const ProbDev* d_probs, int n_probs, int max_param_w
 cudaError_t launch_gather(const ProbDev* d_probs, int n_probs, const int64_t* grad_off, double* G_all,
                           double* grad_all, DevStatus* st_all, cudaStream_t s) {
   k_gather<<<n_probs, 128, 0, s>>>(d_probs, grad_off, G_all, grad_all, st_all);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_expand_states(const double2* qT, const int32_t* pmap, int Mu, int N, double2* out, cudaStream_t s) {
+  const size_t n = (size_t)Mu * N * N;
+  k_expand_states<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(qT, pmap, Mu, N, out);
   return cudaGetLastError();
 }
 

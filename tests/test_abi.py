@@ -142,7 +142,9 @@ def test_workspace_size_accounts_for_checkpoints(lib, K):
         L.check(lib.lb_objective_set_gate(h, 0, Vb.ctypes.data_as(c_void_p), 0.0))
         n = c_size_t()
         L.check(lib.lb_workspace_bytes(h, byref(n)))
-        M, Vl, NT = 16, 81, 250
+        # the 16 states |i><j| of the essential basis form 6 conjugate pairs:
+        # 10 states are integrated (lb_set_pairing)
+        M, Vl, NT = 10, 81, 250
         state = 16 * M * Vl
         if K == 0:
             tape = NT * state
@@ -163,6 +165,44 @@ def test_workspace_size_accounts_for_checkpoints(lib, K):
         rings = 8 if K == 0 else 16
         assert n.value >= tape + gproj + (3 + rings) * state
         assert n.value <= tape + gproj + (3 + rings) * state + 64 * 1024
+    finally:
+        lib.lb_system_destroy(h)
+
+
+def test_conjugate_pairs_shrink_the_workspace(lib):
+    """|i><j| and |j><i| = (|i><j|)^+ are integrated once: the gate workload's
+    16 states need the workspace of 10; with pairing off, of 16; a target set
+    that is not conjugate-paired like the states splits the pairs."""
+    p = W.config2(n_steps=250)
+    sizes = {}
+    for on in (1, 0):
+        h = _make(lib, p, K=0)
+        try:
+            V = np.ascontiguousarray(np.asarray(p.gate.T, dtype=np.complex128)).view(np.float64)
+            L.check(lib.lb_objective_set_gate(h, 0, V.ctypes.data_as(c_void_p), 0.0))
+            L.check(lib.lb_set_pairing(h, on))
+            n = c_size_t()
+            L.check(lib.lb_workspace_bytes(h, byref(n)))
+            sizes[on] = n.value
+        finally:
+            lib.lb_system_destroy(h)
+    tape_state = 16 * 81 * 250  # stage tape bytes per state (K = 0)
+    # every per-state array (tape, states, targets, predictor ring, gradient
+    # slots) holds 10 states instead of 16
+    assert 0.6 < sizes[1] / sizes[0] < 0.66
+    assert lib.lb_set_pairing(None, 1) == L.LB_EINVAL
+    # explicit targets that are all the same Hermitian matrix do not pair like
+    # the states |i><j| and |j><i| (tar_j != tar_i^+ unless tar is Hermitian:
+    # a non-Hermitian common target splits every pair)
+    h = _make(lib, p, K=0)
+    try:
+        rng = np.random.default_rng(5)
+        t = rng.standard_normal((16, 9, 9)) + 1j * rng.standard_normal((16, 9, 9))
+        tb = colmajor(t)
+        L.check(lib.lb_objective_set(h, 0, tb.ctypes.data_as(c_void_p), 0.0))
+        n = c_size_t()
+        L.check(lib.lb_workspace_bytes(h, byref(n)))
+        assert abs(n.value - sizes[0]) < 0.1 * tape_state
     finally:
         lib.lb_system_destroy(h)
 

@@ -122,8 +122,10 @@ def test_config2_full_horizon():
     """2 transmons x 3 levels, 10000 steps, CNOT on the essential subspace."""
     s, _ = _check_problem(W.config2())
     st = s.stats()
-    # forward and adjoint sweeps, plus the recompute sweep when checkpointing
-    assert st["state_steps"] == 16 * 10000 * (3 if st["ckpt_every"] > 0 else 2)
+    # 16 states |i><j|, 6 conjugate pairs: 10 integrated; forward and adjoint
+    # sweeps, plus the recompute sweep when checkpointing
+    assert st["states_integrated"] == 10
+    assert st["state_steps"] == 10 * 10000 * (3 if st["ckpt_every"] > 0 else 2)
 
 
 @pytest.mark.parametrize("seed,objective,hermitian,gamma2,diss", [
@@ -136,6 +138,39 @@ def test_random_problems_match_oracle(seed, objective, hermitian, gamma2, diss):
     p = W.random_problem(seed, levels=(2, 3), n_states=3, n_steps=40, T_ns=0.8, amp=0.1, objective=objective,
                          hermitian=hermitian, gamma2=gamma2, dissipation=diss, ckpt_every=7)
     _check_problem(p)
+
+
+@pytest.mark.parametrize("sweep", ["auto", "resident", "grid"])
+def test_conjugate_pairs_match_oracle_and_unpaired_run(sweep):
+    """|i><j| and |j><i| integrated once (lb_set_pairing): all 16 final states,
+    the objective and the gradient of the gate workload against the oracle,
+    and against the run that integrates every state; explicit targets that
+    pair like the states (J_Tr) too."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    sw = {"auto": L.LB_SWEEP_AUTO, "resident": L.LB_SWEEP_RESIDENT, "grid": L.LB_SWEEP_GRID}[sweep]
+    p = W.prefix(W.config2(), 300)
+    s, g = _check_problem(p, sweep=sw)
+    assert s.stats()["states_integrated"] == 10
+    s0 = _sys(p, sweep=sw, pairing=0)
+    G0, g0 = s0.gradient()
+    G1, g1 = s.gradient()
+    assert s0.stats()["states_integrated"] == 16
+    assert abs(G1 - G0) <= 1e-13 * abs(G0)
+    assert _rel(g1, g0) < 1e-12
+    # explicit targets in the same conjugate pairs as the states
+    rng = np.random.default_rng(8)
+    q = W.random_problem(417, levels=(3, 2), n_states=4, n_steps=30, T_ns=0.6, amp=0.1, objective="trace")
+    X = rng.standard_normal((2, 6, 6)) + 1j * rng.standard_normal((2, 6, 6))
+    T = rng.standard_normal((2, 6, 6)) + 1j * rng.standard_normal((2, 6, 6))
+    q.rho0 = np.stack([X[0], X[0].conj().T, X[1], X[1].conj().T])
+    q.targets = np.stack([T[0], T[0].conj().T, T[1], T[1].conj().T])
+    sq, _ = _check_problem(q, sweep=sw)
+    assert sq.stats()["states_integrated"] == 2
+    # a workspace bound with these pairs refuses states that pair otherwise
+    with pytest.raises(L.LBError) as e:
+        sq.set_states_host(np.stack([X[0], X[1], X[0].conj().T, X[1].conj().T]), q.weights)
+    assert e.value.code == L.LB_EINVAL
 
 
 def test_gradient_matches_central_differences_on_gpu():

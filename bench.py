@@ -660,7 +660,7 @@ def run_gradient(args, rank, world, dev, dist):
     if args.ckpt is not None:
         full.ckpt_every = args.ckpt
     p = D.shard_problem(full, rank, world) if world > 1 else full
-    s = LindbladSystem(p, device=dev, predictor=args.predictor)
+    s = LindbladSystem(p, device=dev, predictor=args.predictor, pred_order=args.pred_order)
     s.set_timing(True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -784,6 +784,7 @@ def run_gradient(args, rank, world, dev, dist):
                 "solver": f"{st['solver']} fixed point, rtol 1e-15",
                 "ckpt_every": st["ckpt_every"],
                 "predictor": args.predictor,
+                "pred_order": args.pred_order,
                 "inner_iters_per_step": inner,
                 "ms_forward_kernel": statistics.median(ms_fwd),
                 "ms_backward_kernel": bwd_ms,
@@ -835,6 +836,7 @@ def main():
                     help="steps of the prefix (default: the workload's; smaller for ncu captures)")
     ap.add_argument("--predictor", type=int, default=-1,
                     help="forward predictor restart period (lb_set_predictor; -1 auto, -2 none)")
+    ap.add_argument("--pred-order", type=int, default=0, help="predictor order (lb_set_predictor; 0: default)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
 

@@ -241,13 +241,16 @@ int lb_set_pairing(lb_system* sys, int32_t on);
 /* Choose the sweep kind (LB_SWEEP_*); call before lb_workspace_bytes. */
 int lb_set_sweep(lb_system* sys, int32_t sweep);
 
-/* First iterate of the inner solves of the forward sweep (Appendix A,
- * eq. linsystem_primal; the paper does not say how its Krylov solve is
- * started).  Every solve starts from (I - dt/2 D)^-1 (q^j + c~), c~ the
- * extrapolation of the off-diagonal corrections c = (I - dt/2 D) z - q of the
- * previous steps by the polynomial through them (order up to 7); the
- * adjoint sweep always predicts this way.  `restart` says when the forward
- * predictor forgets its history (it then rebuilds it over the next steps):
+/* First iterate of the inner solves (Appendix A, eq. linsystem_primal; the
+ * paper does not say how its Krylov solve is started).  Every solve starts
+ * from (I - dt/2 D)^-1 (q^j + c~), c~ the extrapolation of the off-diagonal
+ * corrections c = (I - dt/2 D) z - q of the previous steps by the polynomial
+ * through them; the grid and one-CTA sweeps extrapolate each element in the
+ * frame of its own free evolution, g = 2 (I - dt/2 D)^-1 - 1 per step, up to
+ * `order` (1..10; 0 = the default, 8), the cluster sweep without the frame up
+ * to order 7.  The adjoint sweep always predicts.  `restart` says when the
+ * forward predictor forgets its history (it then rebuilds it over the next
+ * steps):
  *   LB_PRED_AUTO (default): every K steps with checkpoints (K > 0), never
  *     with the full stage tape (K = 0);
  *   R > 0: at every step j with j % R == 0; with K > 0, R must divide K;
@@ -262,7 +265,7 @@ int lb_set_sweep(lb_system* sys, int32_t sweep);
  * solves only with K = 0.  Call before lb_workspace_bytes. */
 #define LB_PRED_AUTO (-1)
 #define LB_PRED_NONE (-2)
-int lb_set_predictor(lb_system* sys, int32_t restart);
+int lb_set_predictor(lb_system* sys, int32_t restart, int32_t order);
 
 /* Bound of the grid sweeps' barrier waits (failure detection; the paper has
  * no counterpart).  Each block polls the grid barrier at most `polls` times

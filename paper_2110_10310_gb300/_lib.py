@@ -103,7 +103,7 @@ SIGNATURES = {
     "lb_solver_set": (c_int32, [c_void_p, c_int32, c_double, c_int32, c_int32]),
     "lb_set_sweep": (c_int32, [c_void_p, c_int32]),
     "lb_set_symmetry": (c_int32, [c_void_p, c_int32]),
-    "lb_set_predictor": (c_int32, [c_void_p, c_int32]),
+    "lb_set_predictor": (c_int32, [c_void_p, c_int32, c_int32]),
     "lb_set_pairing": (c_int32, [c_void_p, c_int32]),
     "lb_set_wait_limit": (c_int32, [c_void_p, c_int64]),
     "lb_system_set_coupling": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_double)]),

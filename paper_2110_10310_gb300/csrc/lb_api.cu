@@ -104,6 +104,7 @@ struct lb_system {
   int sweep = LB_SWEEP_AUTO;
   int symmetry = LB_SYM_HERMITIAN;
   int pred = LB_PRED_AUTO;  // restart period of the forward predictor as requested (lb_set_predictor)
+  int pred_order = lbk::kDefaultRingOrder;  // its order (grid and one-CTA sweeps)
   long long spin_limit = 0;  // polls of a grid-barrier wait (0: the kernels' default; lb_set_wait_limit)
   double gamma1 = 0.0, pen_a = 1.0;  // running penalty (one CTA per state)
   bool rho_herm = false;  // every initial state exactly Hermitian
@@ -664,6 +665,7 @@ void fill_prob(lb_system* s) {
   P.hist = at<double2>(s, s->L.hist);
   P.histf = at<double2>(s, s->L.histf);
   P.pred_restart = effective_pred(s);
+  P.pred_order = s->pred_order;
   P.spin_limit = s->spin_limit;
 }
 
@@ -1145,11 +1147,13 @@ int lb_set_pairing(lb_system* s, int32_t on) {
   return LB_OK;
 }
 
-int lb_set_predictor(lb_system* s, int32_t restart) {
+int lb_set_predictor(lb_system* s, int32_t restart, int32_t order) {
   if (!s) return fail(LB_EINVAL, "null system handle");
   if (s->ws) return fail(LB_EINVAL, "set the predictor before binding a workspace");
   if (restart < LB_PRED_NONE) return fail(LB_EINVAL, "restart must be >= 0, LB_PRED_AUTO or LB_PRED_NONE");
+  if (order < 0 || order > lbk::kRingOrder) return fail(LB_EINVAL, "order must be in 1..10 (0: the default, 8)");
   s->pred = restart;
+  s->pred_order = order ? order : lbk::kDefaultRingOrder;
   return LB_OK;
 }
 

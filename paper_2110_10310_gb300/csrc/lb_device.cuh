@@ -114,40 +114,53 @@ __constant__ double kExtrap[kPredOrder + 1][kPredOrder] = {
 // Without the rotation the fast diagonal phases (h |E_k - E_l| up to a few
 // tenths of a radian per step on the six-qutrit system) limit the order-7
 // extrapolation to a first iterate several digits short of the tolerance.
-static_assert(kRingOrder == 8, "the weight table below is written for order 8");
+// The corrections are recorded as computed by the last inner iteration (the
+// off-diagonal sum alone, accurate relative to |c|), not as
+// (I - dt/2 D) z - rhs, whose cancellation leaves rounding errors of order
+// eps |q| that the weights (their magnitudes sum to 2^n - 1) would amplify
+// to the size of the stopping tolerance.
+static_assert(kRingOrder == 10, "the weight table below is written for order 10");
 __constant__ double kExtrapR[kRingOrder + 1][kRingOrder] = {
-    {0, 0, 0, 0, 0, 0, 0, 0},          {1, 0, 0, 0, 0, 0, 0, 0},
-    {2, -1, 0, 0, 0, 0, 0, 0},         {3, -3, 1, 0, 0, 0, 0, 0},
-    {4, -6, 4, -1, 0, 0, 0, 0},        {5, -10, 10, -5, 1, 0, 0, 0},
-    {6, -15, 20, -15, 6, -1, 0, 0},    {7, -21, 35, -35, 21, -7, 1, 0},
-    {8, -28, 56, -70, 56, -28, 8, -1}};
+    {0, 0, 0, 0, 0, 0, 0, 0, 0, 0},
+    {1, 0, 0, 0, 0, 0, 0, 0, 0, 0},
+    {2, -1, 0, 0, 0, 0, 0, 0, 0, 0},
+    {3, -3, 1, 0, 0, 0, 0, 0, 0, 0},
+    {4, -6, 4, -1, 0, 0, 0, 0, 0, 0},
+    {5, -10, 10, -5, 1, 0, 0, 0, 0, 0},
+    {6, -15, 20, -15, 6, -1, 0, 0, 0, 0},
+    {7, -21, 35, -35, 21, -7, 1, 0, 0, 0},
+    {8, -28, 56, -70, 56, -28, 8, -1, 0, 0},
+    {9, -36, 84, -126, 126, -84, 36, -9, 1, 0},
+    {10, -45, 120, -210, 252, -210, 120, -45, 10, -1}};
 
 // The rotated prediction of one element by Horner's rule,
 //   g (w_1 c_{j-1} + g (w_2 c_{j-2} + ... + g w_n c_{j-n})),
 // from the ring of corrections `ring` (entry of slot s at ring[s * stride];
 // `slot` is where the next correction will be recorded, so c_{j-i} is in
-// slot - i modulo kRingOrder) and the element's step factor g.
-__device__ __forceinline__ double2 rot_extrap(const double2* __restrict__ ring, size_t stride, int slot, int n,
-                                              double2 g) {
-  if (n <= 0) return make_double2(0.0, 0.0);
+// slot - i modulo kRingOrder) and the element's step factor g.  NO: the
+// order n as a compile-time constant (loads issued together), 0 = runtime n.
+template <int NO>
+__device__ __forceinline__ double2 rot_extrap_n(const double2* __restrict__ ring, size_t stride, int slot, int n,
+                                                double2 g) {
+  constexpr int NC = NO > 0 ? NO : 1;
+  if (NO > 0) n = NO;
   int sl = slot - n;
   if (sl < 0) sl += kRingOrder;
   double pr, pi;
-  if (n == kRingOrder) {
-    // steady state: compile-time weights, loads issued together
-    double2 c[kRingOrder];
+  if constexpr (NO > 0) {
+    double2 c[NC];
 #pragma unroll
-    for (int i = 0; i < kRingOrder; ++i) {
+    for (int i = 0; i < NC; ++i) {
       const int s = sl + i < kRingOrder ? sl + i : sl + i - kRingOrder;
       c[i] = ring[(size_t)s * stride];
     }
-    constexpr double w[kRingOrder] = {-1, 8, -28, 56, -70, 56, -28, 8};  // w_8 .. w_1
-    pr = w[0] * c[0].x;
-    pi = w[0] * c[0].y;
+    pr = kExtrapR[NC][NC - 1] * c[0].x;
+    pi = kExtrapR[NC][NC - 1] * c[0].y;
 #pragma unroll
-    for (int i = 1; i < kRingOrder; ++i) {
-      const double tr = fma(g.x, pr, fma(-g.y, pi, w[i] * c[i].x));
-      const double ti = fma(g.x, pi, fma(g.y, pr, w[i] * c[i].y));
+    for (int i = 1; i < NC; ++i) {
+      const double w = kExtrapR[NC][NC - 1 - i];
+      const double tr = fma(g.x, pr, fma(-g.y, pi, w * c[i].x));
+      const double ti = fma(g.x, pi, fma(g.y, pr, w * c[i].y));
       pr = tr;
       pi = ti;
     }
@@ -166,6 +179,19 @@ __device__ __forceinline__ double2 rot_extrap(const double2* __restrict__ ring, 
     }
   }
   return make_double2(fma(g.x, pr, -g.y * pi), fma(g.x, pi, g.y * pr));
+}
+
+// n recorded corrections (0 < n <= kRingOrder); the orders a sweep runs at
+// in its steady state take the unrolled paths
+__device__ __forceinline__ double2 rot_extrap(const double2* __restrict__ ring, size_t stride, int slot, int n,
+                                              double2 g) {
+  switch (n) {
+    case 0: return make_double2(0.0, 0.0);
+    case 8: return rot_extrap_n<8>(ring, stride, slot, n, g);
+    case 9: return rot_extrap_n<9>(ring, stride, slot, n, g);
+    case 10: return rot_extrap_n<10>(ring, stride, slot, n, g);
+    default: return rot_extrap_n<0>(ring, stride, slot, n, g);
+  }
 }
 
 // quadratic B-spline of unit knot spacing centred at 0 (Sec. II, eq. rotctrl)

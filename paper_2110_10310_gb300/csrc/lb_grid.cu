@@ -228,22 +228,12 @@ struct StateMax {
 // extrapolated in each element's rotating frame (rot_extrap).
 struct GridHist {
   double2* ring = nullptr;
-  int n = 0, slot = 0;
+  int n = 0, slot = 0, cap = kRingOrder;  // cap: the predictor's order
   __device__ void advance() {
-    n = n < kRingOrder ? n + 1 : kRingOrder;
+    n = n < cap ? n + 1 : cap;
     slot = slot + 1 < kRingOrder ? slot + 1 : 0;
   }
 };
-
-template <bool ADJ>
-__device__ __forceinline__ void grid_record(const ProbDev& P, size_t stride, GridHist h, size_t o, int v,
-                                            double hh, double2 z, double2 r) {
-  const double2 D = __ldg(P.D + v);
-  const double dr = hh * D.x, di = hh * (ADJ ? -D.y : D.y);
-  const double cr = z.x - fma(dr, z.x, -di * z.y) - r.x;
-  const double ci = z.y - fma(dr, z.y, di * z.x) - r.y;
-  h.ring[(size_t)h.slot * stride + o] = make_double2(cr, ci);
-}
 
 // Running penalty (Sec. III, eq. optimproblem): with penw != 0 the first
 // pass of a forward solve also sums each state's merit summand of its
@@ -358,9 +348,16 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
       const int b = g.b, v = g.v;
       const double2* xs = zc + (size_t)b * V;
       const int k = v % N, l = v / N;
-      const double2 r = rhs[(size_t)b * V + v];
-      double ar = r.x, ai = r.y;
-      offdiag_acc<ADJ, true>(ar, ai, xs, v, __ldg(P.digits + k), __ldg(P.digits + l), H, T, ct);
+      const size_t o = (size_t)b * V + v;
+      const double2 r = rhs[o];
+      // the correction (dt/2) O z of this iterate, kept apart from the
+      // right-hand side; with the predictor on it goes to the ring slot of
+      // this step (the last iteration's write stays: the correction whose
+      // Jacobi image is the returned z)
+      double cr = 0.0, ci = 0.0;
+      offdiag_acc<ADJ, true>(cr, ci, xs, v, __ldg(P.digits + k), __ldg(P.digits + l), H, T, ct);
+      if (hist.ring) hist.ring[(size_t)hist.slot * ((size_t)M * V) + o] = make_double2(cr, ci);
+      const double ar = r.x + cr, ai = r.y + ci;
       const double2 zo = __ldcg(xs + v);
       double2 z;
       if (!neumann) {
@@ -436,7 +433,6 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
   const int V = H.V;
   double2* q = mode == 0 ? P.qT : x;
   const long long e0 = (long long)blockIdx.x * G.chunk, e1 = min(G.total, e0 + G.chunk);
-  const size_t hstride = (size_t)G.M * V;
   if (mode == 0 && init)
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       const GEl g = gel(G, P.hmap, e);
@@ -453,9 +449,9 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
   const bool pred = mode == 0 && R >= 0;
   // the running penalty is summed over the forward sweep of the system's own states
   const bool penal = mode == 0 && H.gamma1 != 0.0;
-  const double hh = 0.5 * H.h;
   GridHist hist;
   hist.ring = P.hist;
+  hist.cap = P.pred_order;
   for (int jj = 0; jj < j1 - j0; ++jj) {
     const int j = mode == 2 ? j1 - 1 - jj : j0 + jj;
     if (pred && R > 0 && j % R == 0) hist.n = 0;
@@ -482,7 +478,6 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
       const size_t o = (size_t)g.b * V + g.v;
       const double2 zz = z[o], qq = q[o];
       if (mode == 0 && tape && H.K == 0) gput(P.ckpt + ((size_t)g.b * H.NT + j) * V, GEl{0, g.v, g.vm}, V, zz);
-      if (pred) grid_record<false>(P, hstride, hist, o, g.v, hh, zz, qq);
       gput(q, g, V, make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y)));
     }
     if (pred) hist.advance();
@@ -505,7 +500,6 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
   const int V = H.V, N = H.N;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const long long e0 = (long long)blockIdx.x * G.chunk, e1 = min(G.total, e0 + G.chunk);
-  const size_t hstride = (size_t)G.M * V;
   // terminal condition qhat^{N_T} = beta_i/M g_i (Appendix B)
   for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
     const GEl g = gel(G, P.hmap, e);
@@ -536,14 +530,15 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
   bool failed = false;
   // adjoint predictor: the adjoint steps come in the same order for every K
   const bool apred = H.method != LB_SOLVER_NEUMANN;
-  const double hh = 0.5 * H.h;
   GridHist ahist;
   ahist.ring = P.hist;
+  ahist.cap = P.pred_order;
   // forward predictor of the recompute, restarted as in the forward sweep
   const int R = P.pred_restart;
   const bool fpred = H.K > 0 && R > 0;
   GridHist fhist;
   fhist.ring = P.histf;
+  fhist.cap = P.pred_order;
   for (int sg = nseg - 1; sg >= 0 && !failed; --sg) {
     const int j0 = H.K > 0 ? sg * H.K : 0;
     const int j1 = H.K > 0 ? min(H.NT, j0 + H.K) : H.NT;
@@ -570,7 +565,6 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
           const size_t o = (size_t)g.b * V + g.v;
           const double2 zz = z[o], qq = P.qf[o];
           P.seg[((size_t)g.b * H.K + (j - j0)) * V + g.v] = zz;  // read back at the same element only
-          if (fpred) grid_record<false>(P, hstride, fhist, o, g.v, hh, zz, qq);
           gput(P.qf, g, V, make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y)));
         }
         if (fpred) fhist.advance();
@@ -646,7 +640,6 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
           if (last) {
             // qhat^j = 2 zhat - qhat^{j+1}: no other thread reads this element in the pass
             const double2 zz = zh[o], ll = P.lam[o];
-            if (apred) grid_record<true>(P, hstride, ahist, o, v, hh, zz, ll);
             double2 ln = make_double2(fma(2.0, zz.x, -ll.x), fma(2.0, zz.y, -ll.y));
             if (penal) {
               // the running penalty's source gamma1 beta_i/M dt beta(t_j) g(q^j) (Appendix B)

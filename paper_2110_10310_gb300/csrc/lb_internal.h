@@ -102,7 +102,7 @@ struct ProbDev {
   double2* hist;             // [kRingOrder][M*V] first-iterate predictor history (grid and one-CTA sweeps)
   double2* histf;            // [kRingOrder][M*V] the forward predictor's history in a recompute (K > 0)
   int32_t pred_restart;      // forward predictor: -2 none, 0 never restarts, R > 0 restarts when j % R == 0
-  int32_t pad2;
+  int32_t pred_order;        // highest extrapolation order of the rotated predictor (1..kRingOrder)
   long long spin_limit;      // polls of a grid-barrier wait before it gives up (0: the kernels' default)
   int32_t* hmap;             // [N (N + 1) / 2] vec indices k + N l with k <= l (grid sweeps)
   int32_t herm;              // grid sweeps iterate k <= l only: every state and target is Hermitian
@@ -119,7 +119,8 @@ namespace lbk {
 
 constexpr int kMaxResidentV = 4096;  // states held in one CTA's shared memory
 constexpr int kPredOrder = 7;        // extrapolation order of the cluster sweeps' first-iterate predictor
-constexpr int kRingOrder = 8;        // order of the rotated first-iterate predictor (grid and one-CTA sweeps)
+constexpr int kRingOrder = 10;       // ring slots (highest order) of the rotated first-iterate predictor
+constexpr int kDefaultRingOrder = 8; // its default order (grid and one-CTA sweeps)
 
 struct ResidentConfig {
   int threads;  // CTA size (multiple of 32, <= 512)

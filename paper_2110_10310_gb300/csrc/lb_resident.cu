@@ -302,10 +302,13 @@ __device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
 // QT > 0 (with E == 1) uses the per-thread plan.  GM: the kernel variant
 // that can also run GMRES (res_gmres) when the problem's method asks for it;
 // the fixed-point kernels are compiled without it.
+// cl receives, per element, the correction (dt/2) O z of the last iteration's
+// input (the correction whose Jacobi image is the returned z; not written by
+// GMRES), which the predictor records.
 template <int E, int QT, bool ADJ, bool GM = false>
 __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, const Plan<QT>& pl,
                          const double2 (&rhs)[E], const double2* __restrict__ ct, double fac, int& cur,
-                         const double2* pc = nullptr) {
+                         double2 (&cl)[E], const double2* pc = nullptr) {
   static_assert(QT == 0 || E == 1, "the per-thread plan holds one element");
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const bool neumann = H.method == LB_SOLVER_NEUMANN;
@@ -361,15 +364,17 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
     for (int e = 0; e < E; ++e) {
       const int v = el_v(el, S, H, e);
       if (v < V) {
-        double ar = rhs[e].x, ai = rhs[e].y;
+        double cr = 0.0, ci = 0.0;
         double2 d;
         if constexpr (QT > 0) {
-          offdiag_plan<QT, ADJ>(ar, ai, zc, pl, cq, jon);
+          offdiag_plan<QT, ADJ>(cr, ci, zc, pl, cq, jon);
           d = pl.d;
         } else {
-          offdiag_acc<ADJ>(ar, ai, zc, v, el.kd[e], el.ld[e], H, T, ct);
+          offdiag_acc<ADJ>(cr, ci, zc, v, el.kd[e], el.ld[e], H, T, ct);
           d = S.dsm[v];
         }
+        cl[e] = make_double2(cr, ci);
+        const double ar = rhs[e].x + cr, ai = rhs[e].y + ci;
         const double di = ADJ ? -d.y : d.y;
         const double2 zo = zc[v];
         double2 z;
@@ -407,13 +412,14 @@ struct Pred {
   const double2* D = nullptr;
   size_t stride = 0;
   double hh = 0.0;
-  int n = 0, slot = 0;
+  int n = 0, slot = 0, cap = kRingOrder;  // cap: the predictor's order
   __device__ void init(const ProbDev& P, size_t base) {
     hist = P.hist + base;
     D = P.D;
     stride = (size_t)P.M * P.V;
     hh = 0.5 * P.h;
     n = slot = 0;
+    cap = P.pred_order;
   }
   // pc[e]: the predicted correction of element e (S.dsm holds (I - dt/2 D)^-1)
   template <bool ADJ>
@@ -429,6 +435,17 @@ struct Pred {
       }
     }
   }
+  // record the corrections the last inner iteration computed (fixed points)
+  __device__ void record_c(const double2 (&cl)[E], const Elems<E>& el, const ResSmem& S, const Hdr& H, int V) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int v = el_v(el, S, H, e);
+      if (v < V) hist[(size_t)slot * stride + v] = cl[e];
+    }
+    n = n < cap ? n + 1 : cap;
+    slot = slot + 1 < kRingOrder ? slot + 1 : 0;
+  }
+  // record c = (I - dt/2 D) z - rhs from the solution (GMRES)
   template <bool ADJ>
   __device__ void record(const double2* zc, const double2 (&rhs)[E], const Elems<E>& el, const ResSmem& S,
                          const Hdr& H, int V) {
@@ -442,7 +459,7 @@ struct Pred {
                                                        z.y - fma(dr, z.y, di * z.x) - rhs[e].y);
       }
     }
-    n = n < kRingOrder ? n + 1 : kRingOrder;
+    n = n < cap ? n + 1 : cap;
     slot = slot + 1 < kRingOrder ? slot + 1 : 0;
   }
 };
@@ -744,7 +761,8 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
       if (R > 0 && j % R == 0) pr.n = 0;
       pr.template predict<false>(pc, el, S, H, V);
     }
-    const int it = res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur,
+    // pc: the prediction in, the last iteration's corrections out
+    const int it = res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur, pc,
                                                  pred ? pc : nullptr);
     if (it < 0) {
       if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
@@ -753,7 +771,12 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
     }
     stats.add(0, it);
     const double2* zc = cur ? S.zb1 : S.zb0;
-    if (pred) pr.template record<false>(zc, q, el, S, H, V);
+    if (pred) {
+      if (H.method == LB_SOLVER_GMRES)
+        pr.template record<false>(zc, q, el, S, H, V);
+      else
+        pr.record_c(pc, el, S, H, V);
+    }
     double2* tp = (tape && H.K == 0) ? P.ckpt + ((size_t)i * H.NT + j) * H.V : nullptr;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -875,7 +898,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
           pr.template predict<false>(pc, el, S, H, V);
         }
         const int it = res_solve<E, QT, false, GM>(S, H, el, pl, qf, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur,
-                                                   fpred ? pc : nullptr);
+                                                   pc, fpred ? pc : nullptr);
         if (it < 0) {
           if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
           stats.flush(P.status);
@@ -883,7 +906,12 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
         }
         stats.add(1, it);
         const double2* zc = cur ? S.zb1 : S.zb0;
-        if (fpred) pr.template record<false>(zc, qf, el, S, H, V);
+        if (fpred) {
+          if (H.method == LB_SOLVER_GMRES)
+            pr.template record<false>(zc, qf, el, S, H, V);
+          else
+            pr.record_c(pc, el, S, H, V);
+        }
         double2* sgv = P.seg + ((size_t)i * H.K + (j - j0)) * H.V;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
@@ -906,7 +934,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       int cur;
       // (I - dt/2 (M^{j+1/2})^+) zhat^j = qhat^{j+1}   (eq. linsystem_adjoint)
       if (apred) pr.template predict<true>(pc, el, S, H, V);
-      const int it = res_solve<E, QT, true, GM>(S, H, el, pl, lam, ct, stop_factor(P, j), cur, apred ? pc : nullptr);
+      const int it = res_solve<E, QT, true, GM>(S, H, el, pl, lam, ct, stop_factor(P, j), cur, pc, apred ? pc : nullptr);
       if (it < 0) {
         if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
         stats.flush(P.status);
@@ -914,7 +942,12 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
       }
       stats.add(2, it);
       const double2* zh = cur ? S.zb1 : S.zb0;
-      if (apred) pr.template record<true>(zh, lam, el, S, H, V);
+      if (apred) {
+        if (H.method == LB_SOLVER_GMRES)
+          pr.template record<true>(zh, lam, el, S, H, V);
+        else
+          pr.record_c(pc, el, S, H, V);
+      }
       const double2* Zt = H.K > 0 ? P.seg + ((size_t)i * H.K + (j - j0)) * H.V : P.ckpt + ((size_t)i * H.NT + j) * H.V;
       // gradient pieces (eq. reducedgradient): for every subsystem q,
       //   g_a  = zhat^H vec(-i[a_q, Z])   = -i sum_kl Z_kl conj(R_zhat)
@@ -1032,8 +1065,9 @@ __global__ void __launch_bounds__(512) k_propagate_res(const ProbDev* __restrict
   for (int jj = 0; jj < j1 - j0; ++jj) {
     const int j = adjoint ? j1 - 1 - jj : j0 + jj;
     int cur;
-    const int it = adjoint ? res_solve<E, QT, true, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur)
-                           : res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur);
+    double2 cl[E];
+    const int it = adjoint ? res_solve<E, QT, true, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur, cl)
+                           : res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur, cl);
     if (it < 0) {
       if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
       stats.flush(P.status);

@@ -60,7 +60,7 @@ class LindbladSystem:
 
     def __init__(self, problem, *, solver: int = L.LB_SOLVER_AUTO, rtol: float = 1e-15, max_iter: int = 200,
                  ckpt_every: int | None = None, sweep: int = L.LB_SWEEP_AUTO, symmetry: int = L.LB_SYM_HERMITIAN,
-                 predictor: int = L.LB_PRED_AUTO, pairing: int = 1, device=None, stream=None):
+                 predictor: int = L.LB_PRED_AUTO, pred_order: int = 0, pairing: int = 1, device=None, stream=None):
         self.lib = L.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         sysm = problem.system
@@ -124,7 +124,7 @@ class LindbladSystem:
         L.check(self.lib.lb_solver_set(h, int(solver), float(rtol), int(max_iter), K))
         L.check(self.lib.lb_set_sweep(h, int(sweep)))
         L.check(self.lib.lb_set_symmetry(h, int(symmetry)))
-        L.check(self.lib.lb_set_predictor(h, int(predictor)))
+        L.check(self.lib.lb_set_predictor(h, int(predictor), int(pred_order)))
         L.check(self.lib.lb_set_pairing(h, int(pairing)))
         nbytes = c_size_t()
         L.check(self.lib.lb_workspace_bytes(h, byref(nbytes)))

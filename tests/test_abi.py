@@ -160,9 +160,9 @@ def test_workspace_size_accounts_for_checkpoints(lib, K):
             nw = -(-(-(-Vl // C)) * lanes // 32)  # warps per CTA
             per = max(per, C * nw)
         gproj = M * per * NT * 2 * 2 * 16 + NT * 2 * 2 * 16
-        # q0, tar, qT and the eight-step ring of the first-iterate predictor;
+        # q0, tar, qT and the ten-slot ring of the first-iterate predictor;
         # with checkpoints the recompute's forward predictor has a ring of its own
-        rings = 8 if K == 0 else 16
+        rings = 10 if K == 0 else 20
         assert n.value >= tape + gproj + (3 + rings) * state
         assert n.value <= tape + gproj + (3 + rings) * state + 64 * 1024
     finally:
@@ -223,10 +223,10 @@ def test_grid_sweep_workspace_and_sweep_choice(lib):
         V, M = 81 * 81, 2
         state = 16 * M * V
         # q0, tar, qT, 4 checkpoints, 10-step segment tape, zA, zB, lam, qf,
-        # and the eight-step rings of the adjoint's and the recompute's
+        # and the ten-slot rings of the adjoint's and the recompute's
         # first-iterate predictors
-        assert n.value >= (3 + 4 + 10 + 4 + 16) * state
-        assert n.value <= (3 + 4 + 10 + 4 + 16) * state + 2 * 1024 * 1024
+        assert n.value >= (3 + 4 + 10 + 4 + 20) * state
+        assert n.value <= (3 + 4 + 10 + 4 + 20) * state + 2 * 1024 * 1024
     finally:
         lib.lb_system_destroy(h)
 

@@ -661,6 +661,11 @@ def run_gradient(args, rank, world, dev, dist):
         full.ckpt_every = args.ckpt
     p = D.shard_problem(full, rank, world) if world > 1 else full
     s = LindbladSystem(p, device=dev, predictor=args.predictor, pred_order=args.pred_order)
+    tuned = None
+    if args.autotune == "on" or (args.autotune == "auto" and wl in ("qutrits_6x3", "qudits_4x4") and not args.pred_order):
+        # the library's autotuner (outside the timed region): sweep, inner
+        # solver and, on grid sweeps, the predictor's order
+        tuned = s.autotune()
     s.set_timing(True)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -784,7 +789,8 @@ def run_gradient(args, rank, world, dev, dist):
                 "solver": f"{st['solver']} fixed point, rtol 1e-15",
                 "ckpt_every": st["ckpt_every"],
                 "predictor": args.predictor,
-                "pred_order": args.pred_order,
+                "pred_order": (tuned or {}).get("pred_order", args.pred_order or 8),
+                "autotune": tuned,
                 "inner_iters_per_step": inner,
                 "ms_forward_kernel": statistics.median(ms_fwd),
                 "ms_backward_kernel": bwd_ms,
@@ -837,6 +843,8 @@ def main():
     ap.add_argument("--predictor", type=int, default=-1,
                     help="forward predictor restart period (lb_set_predictor; -1 auto, -2 none)")
     ap.add_argument("--pred-order", type=int, default=0, help="predictor order (lb_set_predictor; 0: default)")
+    ap.add_argument("--autotune", default="auto", choices=["auto", "on", "off"],
+                    help="run lb_autotune before timing (auto: on for the grid-sweep workloads)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
 

@@ -267,6 +267,11 @@ int lb_set_sweep(lb_system* sys, int32_t sweep);
 #define LB_PRED_NONE (-2)
 int lb_set_predictor(lb_system* sys, int32_t restart, int32_t order);
 
+/* The forward predictor's restart period in effect (LB_PRED_NONE, 0 or R;
+ * see lb_set_predictor) and its order (which lb_autotune may have chosen).
+ * Either output pointer may be NULL. */
+int lb_get_predictor(const lb_system* sys, int32_t* restart, int32_t* order);
+
 /* Bound of the grid sweeps' barrier waits (failure detection; the paper has
  * no counterpart).  Each block polls the grid barrier at most `polls` times
  * (about 64 ns apart) before it gives up; a wait that gives up makes every
@@ -373,7 +378,10 @@ int lb_get_stats(lb_system* sys, lb_stats* out);
  * thread, cluster-split when it applies; grid when the workspace was bound
  * for grid sweeps) x inner solver (Jacobi, Neumann, and GMRES for one CTA
  * per state where its Krylov basis fits) -- and keep the fastest
- * candidate whose inner solve converges for later calls.  Synchronises
+ * candidate whose inner solve converges for later calls.  Grid sweeps with a
+ * forward predictor then time the forward sweep with the predictor over the
+ * first max(probe_steps, 30) steps for the orders 6..10 and keep the fastest
+ * (lb_get_predictor reports it).  Synchronises
  * `stream`.  choice_out (nullable, [3]) receives the chosen LB_SWEEP_*,
  * LB_SOLVER_* and the threads per CTA (resident), CTAs per cluster (cluster)
  * or blocks (grid).  LB_ENOTCONV when no candidate converges. */

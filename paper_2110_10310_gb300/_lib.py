@@ -105,6 +105,7 @@ SIGNATURES = {
     "lb_set_symmetry": (c_int32, [c_void_p, c_int32]),
     "lb_set_predictor": (c_int32, [c_void_p, c_int32, c_int32]),
     "lb_set_pairing": (c_int32, [c_void_p, c_int32]),
+    "lb_get_predictor": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
     "lb_set_wait_limit": (c_int32, [c_void_p, c_int64]),
     "lb_system_set_coupling": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_double)]),
     "lb_workspace_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),

@@ -894,6 +894,46 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
   }
   LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
   LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  if (use_grid(s) && s->hp.pred_restart >= 0) {
+    // the predictor's order: time the forward sweep over the first steps (at
+    // least three rings' worth, so that the full order is reached) per order
+    const int64_t pst = std::min<int64_t>(s->NT, std::max<int64_t>(probe_steps, 3 * lbk::kRingOrder));
+    cudaEvent_t a = nullptr, b = nullptr;
+    LB_CUDA(cudaEventCreate(&a), "cudaEventCreate");
+    LB_CUDA(cudaEventCreate(&b), "cudaEventCreate");
+    rc = ensure_ctab(s, st);
+    if (rc) return rc;
+    float tbest = -1.0f;
+    int obest = s->pred_order;
+    for (int o = 6; o <= lbk::kRingOrder; ++o) {
+      s->hp.pred_order = o;
+      LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
+      LB_CUDA(cudaMemsetAsync(at<DevStatus>(s, s->L.status), 0, sizeof(DevStatus), st), "clear status");
+      LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.gslots), 0, s->L.gslots.bytes, st), "clear grid slots");
+      LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.bar), 0, s->L.bar.bytes, st), "clear grid barrier");
+      LB_CUDA(cudaEventRecord(a, st), "cudaEventRecord");
+      LB_CUDA(lbk::launch_sweep_grid(s->dp, 0, 1, 0, 0, pst, nullptr, s->M, s->gblocks, s->gsmem, st),
+              "forward grid sweep");
+      LB_CUDA(cudaEventRecord(b, st), "cudaEventRecord");
+      DevStatus d{};
+      LB_CUDA(cudaMemcpyAsync(&d, at<DevStatus>(s, s->L.status), sizeof(DevStatus), cudaMemcpyDeviceToHost, st),
+              "read status");
+      LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+      if (d.code) continue;
+      float ms = 0.0f;
+      LB_CUDA(cudaEventElapsedTime(&ms, a, b), "cudaEventElapsedTime");
+      if (tbest < 0.0f || ms < tbest) {
+        tbest = ms;
+        obest = o;
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    s->pred_order = obest;
+    s->hp.pred_order = obest;
+    LB_CUDA(cudaMemcpyAsync(s->dp, &s->hp, sizeof(ProbDev), cudaMemcpyHostToDevice, st), "upload problem");
+    LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  }
   if (choice_out) {
     choice_out[0] = win.sweep;
     choice_out[1] = win.method;
@@ -1135,6 +1175,13 @@ int lb_set_wait_limit(lb_system* s, int64_t polls) {
             "upload wait limit");
     LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
   }
+  return LB_OK;
+}
+
+int lb_get_predictor(const lb_system* s, int32_t* restart, int32_t* order) {
+  if (!s) return fail(LB_EINVAL, "null system handle");
+  if (restart) *restart = s->ws ? s->hp.pred_restart : effective_pred(s);
+  if (order) *order = s->pred_order;
   return LB_OK;
 }
 

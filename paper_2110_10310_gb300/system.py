@@ -218,7 +218,10 @@ class LindbladSystem:
         L.check(self.lib.lb_autotune(self.h, _stream_handle(stream), int(probe_steps), out))
         names = {L.LB_SWEEP_RESIDENT: "resident", L.LB_SWEEP_GRID: "grid", L.LB_SWEEP_CLUSTER: "cluster"}
         solvers = {L.LB_SOLVER_JACOBI: "jacobi", L.LB_SOLVER_NEUMANN: "neumann", L.LB_SOLVER_GMRES: "gmres"}
-        return {"sweep": names.get(out[0], out[0]), "solver": solvers.get(out[1], out[1]), "shape": out[2]}
+        r, o = c_int32(), c_int32()
+        L.check(self.lib.lb_get_predictor(self.h, byref(r), byref(o)))
+        return {"sweep": names.get(out[0], out[0]), "solver": solvers.get(out[1], out[1]), "shape": out[2],
+                "pred_order": o.value}
 
     def set_timing(self, on: bool = True):
         L.check(self.lib.lb_set_timing(self.h, int(on)))

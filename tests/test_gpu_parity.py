@@ -441,6 +441,21 @@ def test_control_horizon_longer_than_the_run_matches_oracle(sweep):
     _check_problem(p, sweep=sw, ckpt_every=7)
 
 
+def test_autotune_chooses_the_predictor_order_on_grid_sweeps():
+    """On a grid sweep the autotuner also times the predictor orders 6..10 and
+    keeps one; the gradient afterwards still matches the oracle."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(416, levels=(3, 3), n_states=2, n_steps=60, T_ns=1.2, amp=0.1, ckpt_every=20)
+    s = _sys(p, sweep=L.LB_SWEEP_GRID)
+    choice = s.autotune(probe_steps=30)
+    assert choice["sweep"] == "grid" and 6 <= choice["pred_order"] <= 10
+    G, g = s.gradient()
+    Go, go, _ = imr.gradient(p)
+    assert abs(G - Go) <= 1e-10 * abs(Go)
+    assert _rel(g, go) < 1e-9
+
+
 def test_predictor_restart_rules():
     """A predictor that never restarts needs the full tape; a restart period
     must divide the checkpoint interval."""

@@ -294,8 +294,9 @@ int lb_system_set_coupling(lb_system* sys, const double* jc_ghz, const double* r
 
 /* Hermitian symmetry (Sec. III-B: density matrices, and Lindblad's equation
  * preserves Hermiticity).  With LB_SYM_HERMITIAN (the default) the grid-wide
- * sweeps iterate only the elements k <= l of every state and write the
- * conjugate into (l, k) -- about half the work -- whenever every initial
+ * and one-CTA-per-state sweeps (fixed points and GMRES, whose inner products
+ * are then real) iterate only the elements k <= l of every state and write
+ * the conjugate into (l, k) -- about half the work -- whenever every initial
  * state set by lb_states_set and every explicit target is Hermitian to
  * rounding (each entry within 64 eps max|entry| of the conjugate of its
  * transposed entry; the k <= l entries are then used for both), gate

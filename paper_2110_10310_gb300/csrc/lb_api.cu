@@ -533,11 +533,11 @@ bool hermitian_matrices(const double* a, int M, int N) {
 }
 
 // the Hermitian symmetry runs in the grid sweeps and in the one-CTA sweeps
-// with a fixed-point solver (not in the cluster sweeps or GMRES)
+// (fixed points and GMRES), not in the cluster sweeps
 bool use_symmetry(const lb_system* s) {
   if (s->symmetry != LB_SYM_HERMITIAN || !s->rho_herm || !(s->target_mode == 2 || s->tar_herm)) return false;
   if (use_grid(s)) return true;
-  return !s->cluster && s->method != LB_SOLVER_GMRES;
+  return !s->cluster;
 }
 
 // re-upload the problem block when the symmetry decision changed (bound systems)

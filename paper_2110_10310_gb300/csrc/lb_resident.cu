@@ -499,15 +499,23 @@ __device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
                          double tol) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int V = H.V, m = H.krylov;
+  // With the Hermitian symmetry every Krylov vector is Hermitian (the
+  // preconditioned operator maps Hermitian matrices to Hermitian ones), so the
+  // inner products over all N^2 entries are real: the k <= l entries are
+  // summed with weight 2 off the diagonal and the imaginary parts vanish;
+  // vectors are written at (k, l) and, conjugated, at the mirror (l, k).
+  const bool hm = H.herm != 0;
   const Tabs T{S.cu, S.cd, S.jf, S.ja};
   double* gm = S.gm;
   double2* kry = S.kry;
   const double2* rhs = S.zb1;
   double2* xs = S.zb0;
   double2 x[E];
+  // weight of element e in the inner products
+  auto wt = [&](int e) { return el_m(el, S, H, e) >= 0 ? 2.0 : 1.0; };
 #pragma unroll
   for (int e = 0; e < E; ++e) {
-    const int v = threadIdx.x + e * blockDim.x;
+    const int v = el_v(el, S, H, e);
     x[e] = v < V ? xs[v] : make_double2(0.0, 0.0);
   }
   int its = 0;
@@ -516,15 +524,15 @@ __device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
     double nrm = 0.0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int v = threadIdx.x + e * blockDim.x;
+      const int v = el_v(el, S, H, e);
       if (v < V) {
         double ar = rhs[v].x, ai = rhs[v].y;
         offdiag_acc<ADJ>(ar, ai, xs, v, el.kd[e], el.ld[e], H, T, ct);
         const double2 d = S.dsm[v];
         const double di = ADJ ? -d.y : d.y;
         const double2 r = make_double2(fma(d.x, ar, -di * ai) - x[e].x, fma(d.x, ai, di * ar) - x[e].y);
-        kry[v] = r;
-        nrm = fma(r.x, r.x, fma(r.y, r.y, nrm));
+        rputm(kry, v, el_m(el, S, H, e), r);
+        nrm = fma(wt(e), fma(r.x, r.x, r.y * r.y), nrm);
       }
     }
     ++its;
@@ -535,8 +543,8 @@ __device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
     const double ib = 1.0 / beta;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int v = threadIdx.x + e * blockDim.x;
-      if (v < V) kry[v] = make_double2(kry[v].x * ib, kry[v].y * ib);
+      const int v = el_v(el, S, H, e);
+      if (v < V) rputm(kry, v, el_m(el, S, H, e), make_double2(kry[v].x * ib, kry[v].y * ib));
     }
     if (threadIdx.x == 0) {
       gm[kGmG] = beta;
@@ -552,7 +560,7 @@ __device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
       double2 w[E];
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int v = threadIdx.x + e * blockDim.x;
+        const int v = el_v(el, S, H, e);
         w[e] = make_double2(0.0, 0.0);
         if (v < V) {
           double ar = 0.0, ai = 0.0;
@@ -571,11 +579,15 @@ __device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
           double sr = 0.0, si = 0.0;
 #pragma unroll
           for (int e = 0; e < E; ++e) {
-            const int v = threadIdx.x + e * blockDim.x;
+            const int v = el_v(el, S, H, e);
             if (v < V) {
               const double2 u = kry[(size_t)i * V + v];
-              sr = fma(u.x, w[e].x, fma(u.y, w[e].y, sr));
-              si = fma(u.x, w[e].y, fma(-u.y, w[e].x, si));
+              if (hm) {
+                sr = fma(wt(e), fma(u.x, w[e].x, u.y * w[e].y), sr);
+              } else {
+                sr = fma(u.x, w[e].x, fma(u.y, w[e].y, sr));
+                si = fma(u.x, w[e].y, fma(-u.y, w[e].x, si));
+              }
             }
           }
           const double t = warp_sum2(sr, si, lane);
@@ -590,7 +602,7 @@ __device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
           }
 #pragma unroll
           for (int e = 0; e < E; ++e) {
-            const int v = threadIdx.x + e * blockDim.x;
+            const int v = el_v(el, S, H, e);
             if (v < V) {
               const double2 u = kry[(size_t)i * V + v];
               w[e].x -= fma(hr, u.x, -hi * u.y);
@@ -605,7 +617,7 @@ __device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
       }
       double n2 = 0.0;
 #pragma unroll
-      for (int e = 0; e < E; ++e) n2 = fma(w[e].x, w[e].x, fma(w[e].y, w[e].y, n2));
+      for (int e = 0; e < E; ++e) n2 = fma(wt(e), fma(w[e].x, w[e].x, w[e].y * w[e].y), n2);
       n2 = warp_sum(n2);
       if (lane == 0) gm[kGmR3 + warp] = n2;
       __syncthreads();
@@ -616,8 +628,8 @@ __device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
       const double ih = hn > 0.0 ? 1.0 / hn : 0.0;
 #pragma unroll
       for (int e = 0; e < E; ++e) {
-        const int v = threadIdx.x + e * blockDim.x;
-        if (v < V) vn[v] = make_double2(w[e].x * ih, w[e].y * ih);
+        const int v = el_v(el, S, H, e);
+        if (v < V) rputm(vn, v, el_m(el, S, H, e), make_double2(w[e].x * ih, w[e].y * ih));
       }
       ++its;
       k = j + 1;
@@ -691,7 +703,7 @@ __device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
     if (gm[kGmFlag + 1] != 0.0) return -2;  // singular triangle or overflow
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      const int v = threadIdx.x + e * blockDim.x;
+      const int v = el_v(el, S, H, e);
       if (v < V) {
         double2 z = x[e];
         for (int i = 0; i < k; ++i) {
@@ -701,7 +713,7 @@ __device__ int res_gmres(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
           z.y += fma(yr, u.y, yi * u.x);
         }
         x[e] = z;
-        xs[v] = z;
+        rputm(xs, v, el_m(el, S, H, e), z);
       }
     }
     __syncthreads();

@@ -947,13 +947,18 @@ def test_running_penalty_cluster_checkpoints_bitwise():
     ((2, 2, 2), 100, "frob", "jacobi"),
     ((4, 3), 5, "trace", "jacobi"),
     ((3, 2, 4), 9, "frob", "jacobi"),
+    ((2, 3), 0, "frob", "gmres"),
+    ((3, 3), 7, "trace", "gmres"),
+    ((3, 2, 2), 9, "frob", "gmres"),
 ])
 def test_resident_hermitian_symmetry_matches_oracle(levels, K, objective, solver):
-    """Hermitian states and targets on the one-CTA sweep: the half-element
-    iteration agrees with the full one (1e-12) and with the oracle."""
+    """Hermitian states and targets on the one-CTA sweep (fixed points and
+    GMRES, whose inner products become real sums over k <= l with weight 2 off
+    the diagonal): the half-element iteration agrees with the full one (1e-12)
+    and with the oracle."""
     from paper_2110_10310_gb300 import _lib as L
 
-    sv = {"jacobi": L.LB_SOLVER_JACOBI, "neumann": L.LB_SOLVER_NEUMANN}[solver]
+    sv = {"jacobi": L.LB_SOLVER_JACOBI, "neumann": L.LB_SOLVER_NEUMANN, "gmres": L.LB_SOLVER_GMRES}[solver]
     p = W.random_problem(905, levels=levels, n_states=3, n_steps=40, T_ns=0.8, amp=0.1, ckpt_every=K,
                          hermitian=True, objective=objective, gamma2=0.05)
     s_h, g_h = _check_problem(p, sweep=L.LB_SWEEP_RESIDENT, solver=sv)
@@ -988,13 +993,13 @@ def test_resident_hermitian_symmetry_with_gate_targets_penalty_and_coupling():
         assert _rel(g_h, g_f) < 1e-11
 
 
-def test_resident_hermitian_symmetry_not_taken_for_gmres_or_general_states():
+def test_resident_hermitian_symmetry_not_taken_for_general_states():
     from paper_2110_10310_gb300 import _lib as L
 
     p = W.random_problem(908, levels=(2, 3), n_states=2, n_steps=20, T_ns=0.4, amp=0.1, hermitian=True)
     s = _sys(p, sweep=L.LB_SWEEP_RESIDENT, solver=L.LB_SOLVER_GMRES)
     s.gradient()
-    assert s.stats()["symmetry"] == "none"
+    assert s.stats()["symmetry"] == "hermitian"
     q = W.random_problem(909, levels=(2, 3), n_states=2, n_steps=20, T_ns=0.4, amp=0.1, hermitian=False)
     s = _sys(q, sweep=L.LB_SWEEP_RESIDENT)
     s.gradient()

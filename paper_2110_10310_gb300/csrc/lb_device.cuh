@@ -303,23 +303,42 @@ __device__ __forceinline__ double2 ldz(const double2* p) {
   }
 }
 
-template <bool ADJ, bool CG = false>
+// Entry (k, l) of a Hermitian matrix stored packed, column by column over
+// k <= l (entry (k, l) at l (l + 1)/2 + k): entries below the diagonal are the
+// conjugates of their mirrors (the sign flip on the integer pipe).
+template <bool CG>
+__device__ __forceinline__ double2 ldpk(const double2* p, int k, int l) {
+  const bool lo = k > l;
+  const int a = lo ? l : k, c = lo ? k : l;
+  double2 x = ldz<CG>(p + ((c * (c + 1)) >> 1) + a);
+  x.y = __longlong_as_double(__double_as_longlong(x.y) ^ (lo ? (long long)0x8000000000000000ULL : 0LL));
+  return x;
+}
+
+// PK: x is one state stored packed (ldpk), and the neighbours are addressed
+// by (k, l) of element v = k + N l; else x is indexed by the vec index.
+template <bool ADJ, bool CG = false, bool PK = false>
 __device__ __forceinline__ void offdiag_acc(double& ar, double& ai, const double2* __restrict__ x, int v, uint32_t kd,
-                                            uint32_t ld, const Hdr& H, const Tabs& T, const double2* __restrict__ ct) {
+                                            uint32_t ld, const Hdr& H, const Tabs& T, const double2* __restrict__ ct,
+                                            int k = 0, int l = 0) {
   const int N = H.N;
+  // entry at row offset dk and column offset dl from the element
+  auto nb = [&](int dk, int dl) -> double2 {
+    if constexpr (PK) return ldpk<CG>(x, k + dk, l + dl);
+    else return ldz<CG>(x + v + dk + dl * N);
+  };
   for (int q = 0; q < H.Q; ++q) {
     const int n = H.lev[q], s = H.stride[q], co = H.coff[q];
     const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
-    const int sN = s * N;
     // control: -i[H_c, X] with H_c = d a + conj(d) a^+ (Sec. II):
     //   P = sqrt(nk+1) x[k+s,l] - sqrt(nl) x[k,l-s]     (a X - X a)
     //   R = sqrt(nk) x[k-s,l] - sqrt(nl+1) x[k,l+s]     (a^+ X - X a^+)
     //   -i d P - i conj(d) R = b (P - R) - i a (P + R), d = (a + i b) * 2/dt
     const double c1 = T.cu[co + nk], c2 = T.cd[co + nl], c3 = T.cd[co + nk], c4 = T.cu[co + nl];
-    const double2 x1 = ldz<CG>(x + v + (nk + 1 < n ? s : 0));
-    const double2 x2 = ldz<CG>(x + v - (nl > 0 ? sN : 0));
-    const double2 x3 = ldz<CG>(x + v - (nk > 0 ? s : 0));
-    const double2 x4 = ldz<CG>(x + v + (nl + 1 < n ? sN : 0));
+    const double2 x1 = nb(nk + 1 < n ? s : 0, 0);
+    const double2 x2 = nb(0, nl > 0 ? -s : 0);
+    const double2 x3 = nb(nk > 0 ? -s : 0, 0);
+    const double2 x4 = nb(0, nl + 1 < n ? s : 0);
     const double pr = fma(-c2, x2.x, c1 * x1.x);
     const double pi = fma(-c2, x2.y, c1 * x1.y);
     const double rr = fma(-c4, x4.x, c3 * x3.x);
@@ -337,10 +356,12 @@ __device__ __forceinline__ void offdiag_acc(double& ar, double& ai, const double
       double2 x5;
       if (!ADJ) {
         cj = T.jf[jo];
-        x5 = ldz<CG>(x + v + ((nk + 1 < n && nl + 1 < n) ? s + sN : 0));
+        const int d = (nk + 1 < n && nl + 1 < n) ? s : 0;
+        x5 = nb(d, d);
       } else {
         cj = T.ja[jo];
-        x5 = ldz<CG>(x + v - ((nk > 0 && nl > 0) ? s + sN : 0));
+        const int d = (nk > 0 && nl > 0) ? s : 0;
+        x5 = nb(-d, -d);
       }
       ar = fma(cj, x5.x, ar);
       ai = fma(cj, x5.y, ai);
@@ -360,10 +381,10 @@ __device__ __forceinline__ void offdiag_acc(double& ar, double& ai, const double
     const double w1 = T.cu[H.coff[p] + pk] * T.cd[H.coff[q] + qk];
     const double w2 = T.cd[H.coff[p] + pl] * T.cu[H.coff[q] + ql];
     const int d = sq - sp;  // row offset of a_p^+ a_q
-    const double2 xu1 = ldz<CG>(x + v + ((pk > 0 && qk + 1 < nq) ? d : 0));
-    const double2 xu2 = ldz<CG>(x + v - ((ql > 0 && pl + 1 < np) ? d * N : 0));
-    const double2 xw1 = ldz<CG>(x + v - ((qk > 0 && pk + 1 < np) ? d : 0));
-    const double2 xw2 = ldz<CG>(x + v + ((pl > 0 && ql + 1 < nq) ? d * N : 0));
+    const double2 xu1 = nb((pk > 0 && qk + 1 < nq) ? d : 0, 0);
+    const double2 xu2 = nb(0, (ql > 0 && pl + 1 < np) ? -d : 0);
+    const double2 xw1 = nb((qk > 0 && pk + 1 < np) ? -d : 0, 0);
+    const double2 xw2 = nb(0, (pl > 0 && ql + 1 < nq) ? d : 0);
     const double ur = fma(-u2, xu2.x, u1 * xu1.x), ui = fma(-u2, xu2.y, u1 * xu1.y);
     const double wr = fma(-w2, xw2.x, w1 * xw1.x), wi = fma(-w2, xw2.y, w1 * xw1.y);
     const double2 c = ct[H.Q + k];

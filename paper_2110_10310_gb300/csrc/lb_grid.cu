@@ -63,34 +63,49 @@ __device__ bool grid_sync(GridBar* bar, unsigned nblocks, long long limit) {
 struct GridHdr {
   Hdr h;
   int M;
-  int herm;         // Hermitian symmetry: only elements k <= l are iterated, the rest mirrored
-  int Vh;           // elements per state in the loops: V, or N (N + 1) / 2 with herm
+  int herm;         // Hermitian symmetry: only elements k <= l are iterated and stored
+  int Vh;           // elements per state in the loops and in the sweep's own buffers: V, or N (N + 1) / 2
   long long total;  // M * Vh
   long long chunk;  // elements per block
 };
 
-// Element e of a grid sweep's loops: state b and vec index v; with the
-// Hermitian symmetry the loops visit k <= l only (v from the table hmap) and
-// vm is the mirror index l + N k of an off-diagonal element, whose value is
-// the conjugate (-1 for diagonal elements and without the symmetry).
+// Element e of a grid sweep's loops: state b, vec index v = k + N l, and i,
+// its place in the state's slab of the sweep's own buffers (iterates,
+// adjoint, recomputed state, checkpoints, segment tape, predictor rings).
+// Without the symmetry the slab is the vec layout (i = v).  With it the loops
+// visit k <= l only (v from the table hmap) and the slabs hold those entries
+// packed, column by column (i = l (l + 1)/2 + k); vm is then the mirror index
+// l + N k of an off-diagonal element in the vec layout of the inputs and
+// outputs (q0, targets, final states), whose value is the conjugate (-1 for
+// diagonal elements and without the symmetry).
 struct GEl {
-  int b, v, vm;
+  int b, v, vm, i, k, l;
 };
 __device__ __forceinline__ GEl gel(const GridHdr& G, const int32_t* __restrict__ hmap, long long e) {
   GEl r;
+  const int N = G.h.N;
   if (!G.herm) {
     r.b = (int)(e / G.h.V);
     r.v = (int)(e - (long long)r.b * G.h.V);
+    r.i = r.v;
     r.vm = -1;
+    r.k = r.v % N;
+    r.l = r.v / N;
     return r;
   }
   r.b = (int)(e / G.Vh);
-  r.v = __ldg(hmap + (e - (long long)r.b * G.Vh));
-  const int N = G.h.N, k = r.v % N, l = r.v / N;
-  r.vm = k != l ? l + N * k : -1;
+  r.i = (int)(e - (long long)r.b * G.Vh);
+  r.v = __ldg(hmap + r.i);
+  r.k = r.v % N;
+  r.l = r.v / N;
+  r.vm = r.k != r.l ? r.l + N * r.k : -1;
   return r;
 }
-// store x at element g of the state array a (and its mirror)
+// offset of element g in slab `slab` (state b's, or a checkpoint's) of a sweep buffer
+__device__ __forceinline__ size_t gslab(const GridHdr& G, const GEl& g, size_t slab) {
+  return slab * (size_t)G.Vh + g.i;
+}
+// store x at element g of an input/output array in the vec layout (and its mirror)
 __device__ __forceinline__ void gput(double2* a, const GEl& g, int V, double2 x) {
   a[(size_t)g.b * V + g.v] = x;
   if (g.vm >= 0) a[(size_t)g.b * V + g.vm] = make_double2(x.x, -x.y);
@@ -257,7 +272,7 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
   const Hdr& H = G.h;
   const Tabs T{S.cu, S.cd, S.jf, S.ja};
   const bool neumann = H.method == LB_SOLVER_NEUMANN;
-  const int M = G.M, V = H.V, N = H.N;
+  const int M = G.M, V = H.V;
   const long long e0 = (long long)blockIdx.x * G.chunk;
   const long long e1 = min(G.total, e0 + G.chunk);
   unsigned long long* dslots = P.gslots;          // [3][M]
@@ -272,11 +287,11 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       const GEl g = gel(G, P.hmap, e);
       const int b = g.b, v = g.v;
-      const size_t o = (size_t)b * V + v;
+      const size_t o = gslab(G, g, b);
       const double2 r = rhs[o];
       if (penw != 0.0) {
         // an off-diagonal element under the symmetry stands for its mirror too
-        const double f = merit_summand(H.kind, r, P.tar[o]) * (g.vm >= 0 ? 2.0 : 1.0);
+        const double f = merit_summand(H.kind, r, P.tar[(size_t)b * V + v]) * (g.vm >= 0 ? 2.0 : 1.0);
         const int k = b - sm.sb0;
 #pragma unroll
         for (int u = 0; u < kLocalStates; ++u)
@@ -289,14 +304,14 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
         const double di = ADJ ? -d.y : d.y;
         if (hist.n > 0) {
           // g = 2 (I - dt/2 D)^-1 - 1, the element's free step factor
-          const double2 c = rot_extrap(hist.ring + o, (size_t)M * V, hist.slot, hist.n,
+          const double2 c = rot_extrap(hist.ring + o, (size_t)M * G.Vh, hist.slot, hist.n,
                                        make_double2(fma(2.0, d.x, -1.0), 2.0 * di));
           ur += c.x;
           ui += c.y;
         }
         z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
       }
-      gput(P.zA, g, V, z0);
+      P.zA[o] = z0;
       sm.add(b, umax64(abs_bits(r.x), abs_bits(r.y)), qbank);
     }
     sm.push(qbank, red);
@@ -346,19 +361,22 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       const GEl g = gel(G, P.hmap, e);
       const int b = g.b, v = g.v;
-      const double2* xs = zc + (size_t)b * V;
-      const int k = v % N, l = v / N;
-      const size_t o = (size_t)b * V + v;
+      const double2* xs = zc + (size_t)b * G.Vh;
+      const size_t o = gslab(G, g, b);
       const double2 r = rhs[o];
       // the correction (dt/2) O z of this iterate, kept apart from the
       // right-hand side; with the predictor on it goes to the ring slot of
       // this step (the last iteration's write stays: the correction whose
       // Jacobi image is the returned z)
       double cr = 0.0, ci = 0.0;
-      offdiag_acc<ADJ, true>(cr, ci, xs, v, __ldg(P.digits + k), __ldg(P.digits + l), H, T, ct);
-      if (hist.ring) hist.ring[(size_t)hist.slot * ((size_t)M * V) + o] = make_double2(cr, ci);
+      const uint32_t kd = __ldg(P.digits + g.k), ld = __ldg(P.digits + g.l);
+      if (G.herm)
+        offdiag_acc<ADJ, true, true>(cr, ci, xs, v, kd, ld, H, T, ct, g.k, g.l);
+      else
+        offdiag_acc<ADJ, true, false>(cr, ci, xs, v, kd, ld, H, T, ct);
+      if (hist.ring) hist.ring[(size_t)hist.slot * ((size_t)M * G.Vh) + o] = make_double2(cr, ci);
       const double ar = r.x + cr, ai = r.y + ci;
-      const double2 zo = __ldcg(xs + v);
+      const double2 zo = __ldcg(xs + g.i);
       double2 z;
       if (!neumann) {
         const double2 d = __ldg(P.Dinv + v);
@@ -371,7 +389,7 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
         z.x = ar + fma(dr, zo.x, -di * zo.y);
         z.y = ai + fma(dr, zo.y, di * zo.x);
       }
-      gput(zn, g, V, z);
+      zn[o] = z;
       sm.add(b, umax64(abs_bits(z.x - zo.x), abs_bits(z.y - zo.y)), bank);
     }
     sm.push(bank, red);
@@ -431,13 +449,16 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
   const GridHdr& G = *S.g;
   const Hdr& H = G.h;
   const int V = H.V;
-  double2* q = mode == 0 ? P.qT : x;
+  // the running state: the system's own states in the sweep buffer qf (its
+  // slab layout), or the caller's vectors (vec layout, no symmetry)
+  double2* q = mode == 0 ? P.qf : x;
   const long long e0 = (long long)blockIdx.x * G.chunk, e1 = min(G.total, e0 + G.chunk);
-  if (mode == 0 && init)
+  if (mode == 0)
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       const GEl g = gel(G, P.hmap, e);
-      gput(q, g, V, P.q0[(size_t)g.b * V + g.v]);
+      q[gslab(G, g, g.b)] = (init ? P.q0 : P.qT)[(size_t)g.b * V + g.v];
     }
+  bool failed = false;
   long long itg = 0, nsolve = 0;
   unsigned long long iters = 0, steps = 0;
   int maxit = 0;
@@ -458,8 +479,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
     if (mode == 0 && tape && H.K > 0 && j % H.K == 0) {
       for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const GEl g = gel(G, P.hmap, e);
-        const double2 qq = q[(size_t)g.b * V + g.v];
-        gput(P.ckpt + ((size_t)g.b * H.n_ckpt + j / H.K) * V, GEl{0, g.v, g.vm}, V, qq);
+        P.ckpt[gslab(G, g, (size_t)g.b * H.n_ckpt + j / H.K)] = q[gslab(G, g, g.b)];
       }
     }
     double2* z = nullptr;
@@ -468,6 +488,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
                                                  pred ? hist : GridHist(), penal ? P.pen[j] : 0.0);
     if (it < 0) {
       grid_fail(P, it, j);
+      failed = true;
       break;
     }
     iters += (unsigned long long)it * G.M;
@@ -475,13 +496,19 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
     maxit = max(maxit, it);
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       const GEl g = gel(G, P.hmap, e);
-      const size_t o = (size_t)g.b * V + g.v;
+      const size_t o = gslab(G, g, g.b);
       const double2 zz = z[o], qq = q[o];
-      if (mode == 0 && tape && H.K == 0) gput(P.ckpt + ((size_t)g.b * H.NT + j) * V, GEl{0, g.v, g.vm}, V, zz);
-      gput(q, g, V, make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y)));
+      if (mode == 0 && tape && H.K == 0) P.ckpt[gslab(G, g, (size_t)g.b * H.NT + j)] = zz;
+      q[o] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
     }
     if (pred) hist.advance();
   }
+  // the final states rho_i(T), in the vec layout with their mirrors
+  if (mode == 0 && !failed)
+    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+      const GEl g = gel(G, P.hmap, e);
+      gput(P.qT, g, V, q[gslab(G, g, g.b)]);
+    }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     atomicAdd(&P.status->iters[phase], iters);
     atomicAdd(&P.status->steps[phase], steps);
@@ -509,9 +536,9 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
     const double2 t = P.tar[o];
     if (H.kind == LB_J_FROB) {
       const double2 qq = P.qT[o];
-      gput(P.lam, g, V, make_double2(w * (qq.x - t.x), w * (qq.y - t.y)));
+      P.lam[gslab(G, g, g.b)] = make_double2(w * (qq.x - t.x), w * (qq.y - t.y));
     } else {
-      gput(P.lam, g, V, make_double2(wt * t.x, wt * t.y));
+      P.lam[gslab(G, g, g.b)] = make_double2(wt * t.x, wt * t.y);
     }
   }
   // running penalty: q^j is rebuilt backwards, q^j = 2 z^j - q^{j+1}, in
@@ -520,8 +547,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
   if (penal)
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
       const GEl g = gel(G, P.hmap, e);
-      const size_t o = (size_t)g.b * V + g.v;
-      P.qb[o] = P.qT[o];
+      P.qb[gslab(G, g, g.b)] = P.qT[(size_t)g.b * V + g.v];
     }
   long long itg = 0, nsolve = 0;
   unsigned long long it_rec = 0, st_rec = 0, it_adj = 0, st_adj = 0;
@@ -545,7 +571,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
     if (H.K > 0) {
       for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const GEl g = gel(G, P.hmap, e);
-        gput(P.qf, g, V, P.ckpt[((size_t)g.b * H.n_ckpt + sg) * V + g.v]);
+        P.qf[gslab(G, g, g.b)] = P.ckpt[gslab(G, g, (size_t)g.b * H.n_ckpt + sg)];
       }
       for (int j = j0; j < j1; ++j) {
         double2* z = nullptr;
@@ -562,10 +588,10 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
         maxit = max(maxit, it);
         for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
           const GEl g = gel(G, P.hmap, e);
-          const size_t o = (size_t)g.b * V + g.v;
+          const size_t o = gslab(G, g, g.b);
           const double2 zz = z[o], qq = P.qf[o];
-          P.seg[((size_t)g.b * H.K + (j - j0)) * V + g.v] = zz;  // read back at the same element only
-          gput(P.qf, g, V, make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y)));
+          P.seg[gslab(G, g, (size_t)g.b * H.K + (j - j0))] = zz;  // read back at the same element only
+          P.qf[o] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
         }
         if (fpred) fhist.advance();
       }
@@ -599,23 +625,26 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
         for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
           const GEl g = gel(G, P.hmap, e);
           const int b = g.b, v = g.v;
-          const size_t o = (size_t)b * V + v;
-          const double2* zs = zh + (size_t)b * V;
-          const double2 Z = H.K > 0 ? P.seg[((size_t)b * H.K + (j - j0)) * V + v]
-                                    : P.ckpt[((size_t)b * H.NT + j) * V + v];
-          const int k = v % N, l = v / N;
-          const uint32_t kd = __ldg(P.digits + k), ld = __ldg(P.digits + l);
+          const size_t o = gslab(G, g, b);
+          const double2* zs = zh + (size_t)b * G.Vh;
+          const double2 Z = H.K > 0 ? P.seg[gslab(G, g, (size_t)b * H.K + (j - j0))]
+                                    : P.ckpt[gslab(G, g, (size_t)b * H.NT + j)];
+          const uint32_t kd = __ldg(P.digits + g.k), ld = __ldg(P.digits + g.l);
+          // entry at row offset dk, column offset dl of zhat (packed under the symmetry)
+          auto nb = [&](int dk, int dl) -> double2 {
+            return G.herm ? ldpk<true>(zs, g.k + dk, g.l + dl) : __ldcg(zs + v + dk + dl * N);
+          };
 #pragma unroll
           for (int u = 0; u < kQP; ++u) {
             const int q = q0 + u;
             if (q < Qn) {
-              const int n = H.lev[q], s = H.stride[q], co = H.coff[q], sN = s * N;
+              const int n = H.lev[q], s = H.stride[q], co = H.coff[q];
               const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
               const double c1 = S.cu[co + nk], c2 = S.cd[co + nl], c3 = S.cd[co + nk], c4 = S.cu[co + nl];
-              const double2 x1 = __ldcg(zs + v + (nk + 1 < n ? s : 0));
-              const double2 x2 = __ldcg(zs + v - (nl > 0 ? sN : 0));
-              const double2 x3 = __ldcg(zs + v - (nk > 0 ? s : 0));
-              const double2 x4 = __ldcg(zs + v + (nl + 1 < n ? sN : 0));
+              const double2 x1 = nb(nk + 1 < n ? s : 0, 0);
+              const double2 x2 = nb(0, nl > 0 ? -s : 0);
+              const double2 x3 = nb(nk > 0 ? -s : 0, 0);
+              const double2 x4 = nb(0, nl + 1 < n ? s : 0);
               const double pr = fma(-c2, x2.x, c1 * x1.x);
               const double pi = fma(-c2, x2.y, c1 * x1.y);
               const double rr = fma(-c4, x4.x, c3 * x3.x);
@@ -643,7 +672,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
             double2 ln = make_double2(fma(2.0, zz.x, -ll.x), fma(2.0, zz.y, -ll.y));
             if (penal) {
               // the running penalty's source gamma1 beta_i/M dt beta(t_j) g(q^j) (Appendix B)
-              const double2 qn = P.qb[o], t = P.tar[o];
+              const double2 qn = P.qb[o], t = P.tar[(size_t)b * V + v];
               const double2 qj = make_double2(fma(2.0, Z.x, -qn.x), fma(2.0, Z.y, -qn.y));
               P.qb[o] = qj;
               const double pw = H.gamma1 * P.wgt[b] * P.pen[j];
@@ -656,7 +685,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
                 ln.y = fma(ls, t.y, ln.y);
               }
             }
-            gput(P.lam, g, V, ln);
+            P.lam[o] = ln;
           }
         }
 #pragma unroll

@@ -48,7 +48,7 @@ struct Region {
 
 struct Layout {
   Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
-      gproj, gsum, sfac, pen, qb, jpen, mpart, pmap, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, histf,
+      gproj, gsum, sfac, pen, qb, jpen, mpart, pmap, Ginv, hgp, hgm, fgp, fgm, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, histf,
       hmap;
   size_t total = 0;
 };
@@ -341,6 +341,11 @@ Layout make_layout(const lb_system* s) {
   take(L.bar, grid ? sizeof(GridBar) : 0);
   take(L.hist, c2 * lbk::kRingOrder * M * V);
   take(L.histf, recompute_predicts(s) ? c2 * lbk::kRingOrder * M * V : 0);
+  take(L.Ginv, grid ? c2 * V : 0);
+  take(L.hgp, grid ? c2 * M * V : 0);
+  take(L.hgm, grid ? c2 * M * V : 0);
+  take(L.fgp, grid && recompute_predicts(s) ? c2 * M * V : 0);
+  take(L.fgm, grid && recompute_predicts(s) ? c2 * M * V : 0);
   take(L.hmap, sizeof(int32_t) * (size_t)s->N * (s->N + 1) / 2);
   take(L.pmap, sizeof(int32_t) * (size_t)s->Mu);
   L.total = off;
@@ -664,6 +669,11 @@ void fill_prob(lb_system* s) {
   P.herm = use_symmetry(s) ? 1 : 0;
   P.hist = at<double2>(s, s->L.hist);
   P.histf = at<double2>(s, s->L.histf);
+  P.Ginv = grid ? at<double2>(s, s->L.Ginv) : nullptr;
+  P.hgp = at<double2>(s, s->L.hgp);
+  P.hgm = at<double2>(s, s->L.hgm);
+  P.fgp = at<double2>(s, s->L.fgp);
+  P.fgm = at<double2>(s, s->L.fgm);
   P.pred_restart = effective_pred(s);
   P.pred_order = s->pred_order;
   P.spin_limit = s->spin_limit;

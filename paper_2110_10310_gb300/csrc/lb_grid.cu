@@ -237,18 +237,111 @@ struct StateMax {
 // (max_iter), -2 (NaN/Inf) or -3 (a barrier wait gave up); on success *zout
 // points at the buffer holding z.
 // First-iterate predictor of the grid sweeps: the off-diagonal corrections
-// c = (I - dt/2 D) z - rhs of the last n steps, kept per element in a ring
-// (P.hist, or P.histf for the forward predictor of a recompute; each element
-// always handled by the same thread, so no synchronisation is needed),
-// extrapolated in each element's rotating frame (rot_extrap).
+// c = (dt/2) O z of the last n steps, kept per element in a ring (P.hist, or
+// P.histf for the forward predictor of a recompute; each element always
+// handled by the same thread, so no synchronisation is needed) and
+// extrapolated in each element's rotating frame.  The ring holds them in the
+// frame of an anchor step, c~_j = g^-m_j c_j with m_j the steps since the
+// anchor and g the element's free step factor, so that the prediction
+//   c_j ~ sum_{i=1..n} w_i g^i c_{j-i} = g^m_j sum_i w_i c~_{j-i}
+// costs n real-weight multiply-adds and one complex product; the powers g^m
+// and g^-m are kept per element (gp, gm) and advanced once per step.  The
+// anchor is the last restart, or moves every kAnchorSteps steps (the ring's
+// entries are then brought to the new frame), so that the powers stay within
+// a few hundred factors of rounding.
+constexpr int kAnchorSteps = 256;
+
 struct GridHist {
   double2* ring = nullptr;
+  double2* gp = nullptr;  // g^m per element (slab layout)
+  double2* gm = nullptr;  // g^-m
   int n = 0, slot = 0, cap = kRingOrder;  // cap: the predictor's order
+  int m = 0;                              // steps since the anchor
   __device__ void advance() {
     n = n < cap ? n + 1 : cap;
     slot = slot + 1 < kRingOrder ? slot + 1 : 0;
+    ++m;
+  }
+  __device__ void restart() {
+    n = 0;
+    m = 0;
   }
 };
+
+// sum_{i=1..n} w_i c~_{j-i} of one element (real weights, the ring in the
+// anchor frame); NO: n as a compile-time constant, 0 = runtime n
+template <int NO>
+__device__ __forceinline__ double2 anchored_sum_n(const double2* __restrict__ ring, size_t stride, int slot, int n) {
+  constexpr int NC = NO > 0 ? NO : 1;
+  if (NO > 0) n = NO;
+  int sl = slot - n;
+  if (sl < 0) sl += kRingOrder;
+  double pr = 0.0, pi = 0.0;
+  if constexpr (NO > 0) {
+    double2 c[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const int s = sl + i < kRingOrder ? sl + i : sl + i - kRingOrder;
+      c[i] = ring[(size_t)s * stride];
+    }
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      const double w = kExtrapR[NC][NC - 1 - i];
+      pr = fma(w, c[i].x, pr);
+      pi = fma(w, c[i].y, pi);
+    }
+  } else {
+    for (int i = n; i >= 1; --i) {
+      const double2 c = ring[(size_t)sl * stride];
+      const double w = kExtrapR[n][i - 1];
+      pr = fma(w, c.x, pr);
+      pi = fma(w, c.y, pi);
+      sl = sl + 1 < kRingOrder ? sl + 1 : 0;
+    }
+  }
+  return make_double2(pr, pi);
+}
+__device__ __forceinline__ double2 anchored_sum(const double2* __restrict__ ring, size_t stride, int slot, int n) {
+  switch (n) {
+    case 8: return anchored_sum_n<8>(ring, stride, slot, n);
+    case 9: return anchored_sum_n<9>(ring, stride, slot, n);
+    case 10: return anchored_sum_n<10>(ring, stride, slot, n);
+    default: return anchored_sum_n<0>(ring, stride, slot, n);
+  }
+}
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
+// After a step has converged, for element o (slab offset) at vec index v:
+// bring the correction the last iteration recorded into the anchor frame
+// and advance the powers of g to the next step (ADJ: the conjugate factor);
+// every kAnchorSteps steps move the anchor to the next step.  `h` is the
+// ring's state before advance().
+template <bool ADJ>
+__device__ __forceinline__ void grid_commit(const ProbDev& P, const GridHist& h, size_t o, size_t stride, int v) {
+  double2* cs = h.ring + (size_t)h.slot * stride + o;
+  const double2 gmv = h.gm[o], gpv = h.gp[o];
+  *cs = cmul(*cs, gmv);
+  const double2 d = __ldg(P.Dinv + v), gi = __ldg(P.Ginv + v);
+  const double2 g = make_double2(fma(2.0, d.x, -1.0), ADJ ? -2.0 * d.y : 2.0 * d.y);
+  const double2 ginv = make_double2(gi.x, ADJ ? -gi.y : gi.y);
+  double2 gp = cmul(gpv, g), gm = cmul(gmv, ginv);
+  if (h.m + 1 >= kAnchorSteps) {
+    // the next step becomes the anchor: the ring's entries times g^(m+1)
+    const int nn = h.n < h.cap ? h.n + 1 : h.cap;
+    int sl = h.slot;
+    for (int i = 0; i < nn; ++i) {
+      double2* c = h.ring + (size_t)sl * stride + o;
+      *c = cmul(*c, gp);
+      sl = sl > 0 ? sl - 1 : kRingOrder - 1;
+    }
+    gp = make_double2(1.0, 0.0);
+    gm = gp;
+  }
+  h.gp[o] = gp;
+  h.gm[o] = gm;
+}
 
 // Running penalty (Sec. III, eq. optimproblem): with penw != 0 the first
 // pass of a forward solve also sums each state's merit summand of its
@@ -303,11 +396,13 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
         const double2 d = __ldg(P.Dinv + v);
         const double di = ADJ ? -d.y : d.y;
         if (hist.n > 0) {
-          // g = 2 (I - dt/2 D)^-1 - 1, the element's free step factor
-          const double2 c = rot_extrap(hist.ring + o, (size_t)M * G.Vh, hist.slot, hist.n,
-                                       make_double2(fma(2.0, d.x, -1.0), 2.0 * di));
+          const double2 c = cmul(hist.gp[o], anchored_sum(hist.ring + o, (size_t)M * G.Vh, hist.slot, hist.n));
           ur += c.x;
           ui += c.y;
+        } else if (hist.ring) {
+          // a fresh anchor: m = 0
+          hist.gp[o] = make_double2(1.0, 0.0);
+          hist.gm[o] = make_double2(1.0, 0.0);
         }
         z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
       }
@@ -472,10 +567,12 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
   const bool penal = mode == 0 && H.gamma1 != 0.0;
   GridHist hist;
   hist.ring = P.hist;
+  hist.gp = P.hgp;
+  hist.gm = P.hgm;
   hist.cap = P.pred_order;
   for (int jj = 0; jj < j1 - j0; ++jj) {
     const int j = mode == 2 ? j1 - 1 - jj : j0 + jj;
-    if (pred && R > 0 && j % R == 0) hist.n = 0;
+    if (pred && R > 0 && j % R == 0) hist.restart();
     if (mode == 0 && tape && H.K > 0 && j % H.K == 0) {
       for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
         const GEl g = gel(G, P.hmap, e);
@@ -500,8 +597,12 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
       const double2 zz = z[o], qq = q[o];
       if (mode == 0 && tape && H.K == 0) P.ckpt[gslab(G, g, (size_t)g.b * H.NT + j)] = zz;
       q[o] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
+      if (pred) grid_commit<false>(P, hist, o, (size_t)G.M * G.Vh, g.v);
     }
-    if (pred) hist.advance();
+    if (pred) {
+      hist.advance();
+      if (hist.m >= kAnchorSteps) hist.m = 0;
+    }
   }
   // the final states rho_i(T), in the vec layout with their mirrors
   if (mode == 0 && !failed)
@@ -558,12 +659,16 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
   const bool apred = H.method != LB_SOLVER_NEUMANN;
   GridHist ahist;
   ahist.ring = P.hist;
+  ahist.gp = P.hgp;
+  ahist.gm = P.hgm;
   ahist.cap = P.pred_order;
   // forward predictor of the recompute, restarted as in the forward sweep
   const int R = P.pred_restart;
   const bool fpred = H.K > 0 && R > 0;
   GridHist fhist;
   fhist.ring = P.histf;
+  fhist.gp = P.fgp;
+  fhist.gm = P.fgm;
   fhist.cap = P.pred_order;
   for (int sg = nseg - 1; sg >= 0 && !failed; --sg) {
     const int j0 = H.K > 0 ? sg * H.K : 0;
@@ -575,7 +680,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
       }
       for (int j = j0; j < j1; ++j) {
         double2* z = nullptr;
-        if (fpred && j % R == 0) fhist.n = 0;  // every checkpoint is a restart point
+        if (fpred && j % R == 0) fhist.restart();  // every checkpoint is a restart point
         const int it = grid_solve<false>(P, S, P.qf, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, &z,
                                          fpred ? fhist : GridHist());
         if (it < 0) {
@@ -592,8 +697,12 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
           const double2 zz = z[o], qq = P.qf[o];
           P.seg[gslab(G, g, (size_t)g.b * H.K + (j - j0))] = zz;  // read back at the same element only
           P.qf[o] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
+          if (fpred) grid_commit<false>(P, fhist, o, (size_t)G.M * G.Vh, g.v);
         }
-        if (fpred) fhist.advance();
+        if (fpred) {
+          fhist.advance();
+          if (fhist.m >= kAnchorSteps) fhist.m = 0;
+        }
       }
       if (failed) break;
     }
@@ -686,6 +795,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
               }
             }
             P.lam[o] = ln;
+            if (apred) grid_commit<true>(P, ahist, o, (size_t)G.M * G.Vh, v);
           }
         }
 #pragma unroll
@@ -704,7 +814,10 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
           }
         }
       }
-      if (apred) ahist.advance();
+      if (apred) {
+        ahist.advance();
+        if (ahist.m >= kAnchorSteps) ahist.m = 0;
+      }
       if (!grid_sync(P.bar, gridDim.x, P.spin_limit > 0 ? P.spin_limit : kSpinLimit)) {
         grid_fail(P, -3, j);
         failed = true;

@@ -100,6 +100,11 @@ struct ProbDev {
   unsigned long long* gslots;  // [3][M] per-state |z_new - z| maxima, then [2][M] per-state |q| maxima
   GridBar* bar;
   double2* hist;             // [kRingOrder][M*V] first-iterate predictor history (grid and one-CTA sweeps)
+  double2* Ginv;             // [V] grid sweeps: 1/g, g = (1 + dt/2 D)/(1 - dt/2 D) the free step factor
+  double2* hgp;              // [M*V] grid sweeps: g^m per element of the ring hist's frame (m steps from its anchor)
+  double2* hgm;              // [M*V] grid sweeps: g^-m of the same
+  double2* fgp;              // [M*V] the same for the ring histf
+  double2* fgm;
   double2* histf;            // [kRingOrder][M*V] the forward predictor's history in a recompute (K > 0)
   int32_t pred_restart;      // forward predictor: -2 none, 0 never restarts, R > 0 restarts when j % R == 0
   int32_t pred_order;        // highest extrapolation order of the rotated predictor (1..kRingOrder)

@@ -223,10 +223,10 @@ def test_grid_sweep_workspace_and_sweep_choice(lib):
         V, M = 81 * 81, 2
         state = 16 * M * V
         # q0, tar, qT, 4 checkpoints, 10-step segment tape, zA, zB, lam, qf,
-        # and the ten-slot rings of the adjoint's and the recompute's
-        # first-iterate predictors
-        assert n.value >= (3 + 4 + 10 + 4 + 20) * state
-        assert n.value <= (3 + 4 + 10 + 4 + 20) * state + 2 * 1024 * 1024
+        # the ten-slot rings of the adjoint's and the recompute's first-iterate
+        # predictors and the powers g^m, g^-m of each ring's frame
+        assert n.value >= (3 + 4 + 10 + 4 + 20 + 4) * state
+        assert n.value <= (3 + 4 + 10 + 4 + 20 + 4) * state + 2 * 1024 * 1024
     finally:
         lib.lb_system_destroy(h)
 

@@ -257,24 +257,36 @@ def gpu_uuid(dev):
 # algorithmic work of the sweep kernels
 
 
+def fp64_iterations(st: dict, ph: int) -> int:
+    """Inner iterations of phase ``ph`` computed in FP64: all but the
+    single-precision difference iterations of the grid sweeps."""
+    return st["phase_iterations"][ph] - st.get("phase_diff_iterations", [0, 0, 0])[ph]
+
+
 def fp64_flops(V: int, Q: int, n_decay: int, st: dict, phase_set) -> float:
     """FP64 flops (FMA = 2) of the Jacobi sweeps as the kernels compute them,
     from the iteration counts.
 
-    Per element and inner iteration: per subsystem 24 flops for the control
-    term (two real-weighted neighbour pairs P, R and the complex control
-    factor) plus 4 for the decay sandwich when T1 is finite; 6 for the
-    multiplication by (I - dt/2 D)^-1 and 2 for the convergence difference.
-    Per element and step: 6 for the initial guess, 4 for q <- 2z - q, and for
-    adjoint steps 28 per subsystem for the gradient pieces.  ``V`` is the
-    number of elements a state's sweep computes: N^2, or N (N + 1) / 2 when
-    the Hermitian symmetry leaves the others as mirrored copies."""
+    Per element and FP64 inner iteration: per subsystem 24 flops for the
+    control term (two real-weighted neighbour pairs P, R and the complex
+    control factor) plus 4 for the decay sandwich when T1 is finite; 6 for
+    the multiplication by (I - dt/2 D)^-1 and 2 for the convergence
+    difference.  Per element and difference iteration: 4 (the single-precision
+    changes added to the FP64 iterate and correction).  Per element and step:
+    6 for the initial guess, 4 for q <- 2z - q, and for adjoint steps per
+    subsystem 28 flops for the gradient pieces (24 under the Hermitian
+    symmetry, which sums the g_ad piece as the conjugate of the g_a piece).
+    ``V`` is the number of elements a state's sweep computes: N^2, or
+    N (N + 1) / 2 when the Hermitian symmetry leaves the others as mirrored
+    copies."""
     per_it = 24 * Q + 4 * n_decay + 8
+    herm = st.get("symmetry") == "hermitian"
     f = 0.0
     for ph in phase_set:
-        f += V * (10 * st["phase_steps"][ph] + per_it * st["phase_iterations"][ph])
+        dits = st["phase_iterations"][ph] - fp64_iterations(st, ph)
+        f += V * (10 * st["phase_steps"][ph] + per_it * fp64_iterations(st, ph) + 4 * dits)
         if ph == 2:
-            f += V * 28 * Q * st["phase_steps"][ph]
+            f += V * (24 if herm else 28) * Q * st["phase_steps"][ph]
     return f
 
 
@@ -282,13 +294,14 @@ def method_flops(V: int, Q: int, st: dict, phase_set) -> float:
     """Algorithmic FP64 flops by the method's own count: one Lindblad apply
     costs 8 + 36 Q flops per element (a complex diagonal term and, per
     subsystem, the decay sandwich and the four control neighbours with their
-    complex factors), one per inner iteration; every adjoint step adds the
-    gradient pieces of eq. reducedgradient, 28 Q per element (the two
-    commutator combinations of each subsystem and their two complex dot
-    products).  ``V``: elements the sweep computes (see fp64_flops)."""
+    complex factors), one per FP64 inner iteration (the single-precision
+    difference iterations of the grid sweeps are not counted); every adjoint
+    step adds the gradient pieces of eq. reducedgradient, 28 Q per element
+    (the two commutator combinations of each subsystem and their two complex
+    dot products).  ``V``: elements the sweep computes (see fp64_flops)."""
     f = 0.0
     for ph in phase_set:
-        f += V * (8 + 36 * Q) * st["phase_iterations"][ph]
+        f += V * (8 + 36 * Q) * fp64_iterations(st, ph)
         if ph == 2:
             f += V * 28 * Q * st["phase_steps"][ph]
     return f
@@ -660,7 +673,8 @@ def run_gradient(args, rank, world, dev, dist):
     if args.ckpt is not None:
         full.ckpt_every = args.ckpt
     p = D.shard_problem(full, rank, world) if world > 1 else full
-    s = LindbladSystem(p, device=dev, predictor=args.predictor, pred_order=args.pred_order)
+    s = LindbladSystem(p, device=dev, predictor=args.predictor, pred_order=args.pred_order,
+                       difference_iterations=1 if args.diff_iterations == "on" else 0)
     tuned = None
     if args.autotune == "on" or (args.autotune == "auto" and wl in ("qutrits_6x3", "qudits_4x4") and not args.pred_order):
         # the library's autotuner (outside the timed region): sweep, inner
@@ -766,6 +780,8 @@ def run_gradient(args, rank, world, dev, dist):
     if rank == 0:
         inner = {ph: st["phase_iterations"][i] / max(1, st["phase_steps"][i])
                  for i, ph in enumerate(("forward", "recompute", "adjoint"))}
+        diff = {ph: st["phase_diff_iterations"][i] / max(1, st["phase_steps"][i])
+                for i, ph in enumerate(("forward", "recompute", "adjoint"))}
         line = {
             "metric": METRIC,
             "value": value,
@@ -792,6 +808,11 @@ def run_gradient(args, rank, world, dev, dist):
                 "pred_order": (tuned or {}).get("pred_order", args.pred_order or 8),
                 "autotune": tuned,
                 "inner_iters_per_step": inner,
+                "diff_iters_per_step": diff,
+                "precision": ("FP64 states, corrections, objective, gradient and stopping rule; inner iterations "
+                              "after the first of a step apply O to the single-precision change of the iterate "
+                              "once it is below 2^-32 max|q| (lb_set_difference_iterations)"
+                              if args.diff_iterations == "on" else "FP64 throughout"),
                 "ms_forward_kernel": statistics.median(ms_fwd),
                 "ms_backward_kernel": bwd_ms,
                 "workspace_bytes": s.workspace_bytes,
@@ -806,8 +827,9 @@ def run_gradient(args, rank, world, dev, dist):
                 "unit": "TFLOP/s",
                 "frac": achieved / fp64_peak,
                 "peak_source": peak_src,
-                "flop_count": ("method count: (8 + 36 Q) per element per inner iteration + 28 Q per element per "
-                               "adjoint step (gradient pieces), over the elements the sweep computes "
+                "flop_count": ("method count: (8 + 36 Q) per element per FP64 inner iteration (difference "
+                               "iterations not counted) + 28 Q per element per adjoint step (gradient pieces), "
+                               "over the elements the sweep computes "
                                f"({Ve} per state: {'k <= l under the Hermitian symmetry' if Ve != V else 'all'})"),
                 "frac_instruction_count": bwd_impl / (bwd_ms * 1e-3) / 1e12 / fp64_peak,
                 "hbm_achieved_gbs": hbm_alg / (bwd_ms * 1e-3) / 1e9,
@@ -843,6 +865,8 @@ def main():
     ap.add_argument("--predictor", type=int, default=-1,
                     help="forward predictor restart period (lb_set_predictor; -1 auto, -2 none)")
     ap.add_argument("--pred-order", type=int, default=0, help="predictor order (lb_set_predictor; 0: default)")
+    ap.add_argument("--diff-iterations", default="on", choices=["on", "off"],
+                    help="single-precision difference iterations of the grid sweeps (lb_set_difference_iterations)")
     ap.add_argument("--autotune", default="auto", choices=["auto", "on", "off"],
                     help="run lb_autotune before timing (auto: on for the grid-sweep workloads)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)

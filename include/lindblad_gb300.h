@@ -139,6 +139,9 @@ typedef struct lb_stats {
   int32_t ckpt_every;       /* checkpoint interval in effect (0 = every stage vector kept) */
   int32_t symmetry;         /* LB_SYM_HERMITIAN when the sweep iterated k <= l only */
   int32_t states_integrated; /* states the sweeps integrated (conjugate pairs count once, lb_set_pairing) */
+  int32_t pad;
+  int64_t phase_diff_iterations[3]; /* of phase_iterations: difference iterations in single precision
+                                       (grid sweeps, lb_set_difference_iterations) */
 } lb_stats;
 
 /* ---- system ------------------------------------------------------------- */
@@ -281,6 +284,24 @@ int lb_get_predictor(const lb_system* sys, int32_t* restart, int32_t* order);
  * (2^26 polls, seconds).  May be called at any time; with a workspace bound
  * the new bound is uploaded on the bind stream, which is synchronised. */
 int lb_set_wait_limit(lb_system* sys, int64_t polls);
+
+/* Single-precision difference iterations of the grid sweeps' Jacobi solves
+ * (on = 1, the default; 0 = every inner iteration in FP64).  The implicit
+ * midpoint step (I - dt/2 M) z = q (Sec. II-B, eq. IMR) is solved by
+ * z_{k+1} = (I - dt/2 D)^-1 (q + c(z_k)), c(z) = (dt/2) O z, O the
+ * off-diagonal part of M.  Once every state's last change
+ * d_k = z_k - z_{k-1} is below 2^-32 max|q| (and max|q| >= 2^-50), the next
+ * iteration computes c(z_k) - c(z_{k-1}) = (dt/2) O d_k and
+ * z_{k+1} - z_k = (I - dt/2 D)^-1 (dt/2) O d_k in single precision from d_k
+ * rounded to single precision, and adds them to the FP64 correction and
+ * iterate.  Their rounding errors are below 2^-24 of terms that are already
+ * below 2^-32 of the state, under the FP64 rounding of z, and the stopping
+ * rule (rtol) is unchanged; the first iteration of every step is FP64.  The
+ * one-CTA and cluster sweeps, GMRES and the Neumann series ignore the
+ * switch.  lb_stats.phase_diff_iterations counts these iterations.  May be
+ * called at any time; with a workspace bound the switch is uploaded on the
+ * bind stream, which is synchronised. */
+int lb_set_difference_iterations(lb_system* sys, int32_t on);
 
 /* Jaynes-Cummings coupling of the system Hamiltonian (Sec. II):
  *   sum_{p<q} g_pq (e^{i eta_pq t} a_p^+ a_q + e^{-i eta_pq t} a_p a_q^+),

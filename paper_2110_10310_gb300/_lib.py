@@ -85,6 +85,8 @@ class lb_stats(ctypes.Structure):
         ("ckpt_every", c_int32),
         ("symmetry", c_int32),
         ("states_integrated", c_int32),
+        ("pad", c_int32),
+        ("phase_diff_iterations", c_int64 * 3),
     ]
 
 
@@ -107,6 +109,7 @@ SIGNATURES = {
     "lb_set_pairing": (c_int32, [c_void_p, c_int32]),
     "lb_get_predictor": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
     "lb_set_wait_limit": (c_int32, [c_void_p, c_int64]),
+    "lb_set_difference_iterations": (c_int32, [c_void_p, c_int32]),
     "lb_system_set_coupling": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_double)]),
     "lb_workspace_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),
     "lb_bind_workspace": (c_int32, [c_void_p, c_void_p, c_size_t, c_void_p]),

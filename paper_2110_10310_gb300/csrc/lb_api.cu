@@ -48,7 +48,7 @@ struct Region {
 
 struct Layout {
   Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
-      gproj, gsum, sfac, pen, qb, jpen, mpart, pmap, Ginv, hgp, hgm, fgp, fgm, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, histf,
+      gproj, gsum, sfac, pen, qb, jpen, mpart, pmap, Ginv, hgp, hgm, fgp, fgm, dfA, dfB, Dinvf, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, histf,
       hmap;
   size_t total = 0;
 };
@@ -106,6 +106,7 @@ struct lb_system {
   int pred = LB_PRED_AUTO;  // restart period of the forward predictor as requested (lb_set_predictor)
   int pred_order = lbk::kDefaultRingOrder;  // its order (grid and one-CTA sweeps)
   long long spin_limit = 0;  // polls of a grid-barrier wait (0: the kernels' default; lb_set_wait_limit)
+  int diffit = 1;            // single-precision difference iterations in the grid sweeps (lb_set_difference_iterations)
   double gamma1 = 0.0, pen_a = 1.0;  // running penalty (one CTA per state)
   bool rho_herm = false;  // every initial state exactly Hermitian
   bool tar_herm = false;  // every explicit target exactly Hermitian (gate targets: always)
@@ -346,6 +347,9 @@ Layout make_layout(const lb_system* s) {
   take(L.hgm, grid ? c2 * M * V : 0);
   take(L.fgp, grid && recompute_predicts(s) ? c2 * M * V : 0);
   take(L.fgm, grid && recompute_predicts(s) ? c2 * M * V : 0);
+  take(L.dfA, grid ? sizeof(float2) * M * V : 0);
+  take(L.dfB, grid ? sizeof(float2) * M * V : 0);
+  take(L.Dinvf, grid ? sizeof(float2) * V : 0);
   take(L.hmap, sizeof(int32_t) * (size_t)s->N * (s->N + 1) / 2);
   take(L.pmap, sizeof(int32_t) * (size_t)s->Mu);
   L.total = off;
@@ -677,6 +681,10 @@ void fill_prob(lb_system* s) {
   P.pred_restart = effective_pred(s);
   P.pred_order = s->pred_order;
   P.spin_limit = s->spin_limit;
+  P.diffit = s->diffit;
+  P.dfA = grid ? at<float2>(s, s->L.dfA) : nullptr;
+  P.dfB = grid ? at<float2>(s, s->L.dfB) : nullptr;
+  P.Dinvf = grid ? at<float2>(s, s->L.Dinvf) : nullptr;
 }
 
 int ensure_ctab(lb_system* s, cudaStream_t st) {
@@ -693,6 +701,7 @@ int read_status(const DevStatus& d, lb_stats* st, int launches) {
     for (int p = 0; p < 3; ++p) {
       st->phase_steps[p] = (int64_t)d.steps[p];
       st->phase_iterations[p] = (int64_t)d.iters[p];
+      st->phase_diff_iterations[p] = (int64_t)d.diters[p];
       st->state_steps += (int64_t)d.steps[p];
       st->inner_iterations += (int64_t)d.iters[p];
     }
@@ -1183,6 +1192,20 @@ int lb_set_wait_limit(lb_system* s, int64_t polls) {
     cudaStream_t st = s->bind_stream;
     LB_CUDA(cudaMemcpyAsync(&s->dp->spin_limit, &s->hp.spin_limit, sizeof(long long), cudaMemcpyHostToDevice, st),
             "upload wait limit");
+    LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
+  }
+  return LB_OK;
+}
+
+int lb_set_difference_iterations(lb_system* s, int32_t on) {
+  if (!s) return fail(LB_EINVAL, "null system handle");
+  if (on != 0 && on != 1) return fail(LB_EINVAL, "on must be 0 or 1");
+  s->diffit = on;
+  if (s->ws) {
+    s->hp.diffit = on;
+    cudaStream_t st = s->bind_stream;
+    LB_CUDA(cudaMemcpyAsync(&s->dp->diffit, &s->hp.diffit, sizeof(int32_t), cudaMemcpyHostToDevice, st),
+            "upload difference-iteration switch");
     LB_CUDA(cudaStreamSynchronize(st), "cudaStreamSynchronize");
   }
   return LB_OK;
@@ -1835,6 +1858,7 @@ static int batch_call(lb_batch* b, cudaStream_t st, int with_grad, double* G_out
     for (int ph = 0; ph < 3; ++ph) {
       tot.phase_steps[ph] += one.phase_steps[ph];
       tot.phase_iterations[ph] += one.phase_iterations[ph];
+      tot.phase_diff_iterations[ph] += one.phase_diff_iterations[ph];
     }
     tot.max_iterations = std::max(tot.max_iterations, one.max_iterations);
   }

@@ -111,8 +111,12 @@ __device__ __forceinline__ void gput(double2* a, const GEl& g, int V, double2 x)
   if (g.vm >= 0) a[(size_t)g.b * V + g.vm] = make_double2(x.x, -x.y);
 }
 
+// entries of one step of the control table at most: Q factors and the pairs p < q
+constexpr int kMaxCq = LB_MAXQ + LB_MAXQ * (LB_MAXQ - 1) / 2;
+
 __host__ __device__ inline size_t grid_smem_bytes_impl(int ncoef, int njcoef) {
   return align16(sizeof(GridHdr)) + align16(sizeof(double) * 2 * ncoef) + align16(sizeof(double) * 2 * njcoef) +
+         align16(sizeof(float) * 2 * ncoef) + align16(sizeof(float) * 2 * njcoef) + align16(sizeof(float2) * kMaxCq) +
          align16(sizeof(double) * 4 * 8) + 64;
 }
 
@@ -122,8 +126,13 @@ struct GridSmem {
   double* cd;
   double* jf;
   double* ja;
+  float* cuf;  // the same four tables in single precision (difference iterations)
+  float* cdf;
+  float* jff;
+  float* jaf;
+  float2* ctf;  // this solve's control-table entries in single precision
   double* red;  // [4][8 warps]
-  int* flag;
+  int* flag;    // [0]: the iteration's decision, [1]: next iteration in single precision
 };
 
 __device__ GridSmem grid_setup(unsigned char* base, const ProbDev& P, int nstates, int herm) {
@@ -137,6 +146,14 @@ __device__ GridSmem grid_setup(unsigned char* base, const ProbDev& P, int nstate
   S.jf = reinterpret_cast<double*>(base + o);
   S.ja = S.jf + P.njcoef;
   o += align16(sizeof(double) * 2 * P.njcoef);
+  S.cuf = reinterpret_cast<float*>(base + o);
+  S.cdf = S.cuf + P.ncoef;
+  o += align16(sizeof(float) * 2 * P.ncoef);
+  S.jff = reinterpret_cast<float*>(base + o);
+  S.jaf = S.jff + P.njcoef;
+  o += align16(sizeof(float) * 2 * P.njcoef);
+  S.ctf = reinterpret_cast<float2*>(base + o);
+  o += align16(sizeof(float2) * kMaxCq);
   S.red = reinterpret_cast<double*>(base + o);
   o += align16(sizeof(double) * 4 * 8);
   S.flag = reinterpret_cast<int*>(base + o);
@@ -155,10 +172,14 @@ __device__ GridSmem grid_setup(unsigned char* base, const ProbDev& P, int nstate
   for (int i = threadIdx.x; i < P.ncoef; i += blockDim.x) {
     S.cu[i] = P.cu[i];
     S.cd[i] = P.cd[i];
+    S.cuf[i] = (float)P.cu[i];
+    S.cdf[i] = (float)P.cd[i];
   }
   for (int i = threadIdx.x; i < P.njcoef; i += blockDim.x) {
     S.jf[i] = P.jf[i];
     S.ja[i] = P.ja[i];
+    S.jff[i] = (float)P.jf[i];
+    S.jaf[i] = (float)P.ja[i];
   }
   __syncthreads();
   return S;
@@ -357,10 +378,158 @@ __device__ __forceinline__ double merit_summand(int kind, double2 q, double2 t) 
   return fma(t.x, q.x, t.y * q.y);
 }
 
+// ---------------------------------------------------------------------------
+// Difference iterations (lb_set_difference_iterations).  Once every state's
+// last change d = z_k - z_{k-1} is below kDiffRel of its max|q|, the next
+// Jacobi iteration computes the change of the correction, (dt/2) O d, and of
+// the iterate, (I - dt/2 D)^-1 (dt/2) O d, in single precision from d
+// rounded to single precision, and adds them to the FP64 correction and
+// iterate: z_{k+1} = z_k + (I - dt/2 D)^-1 (c(z_k) - c(z_{k-1})) is the
+// Jacobi step.  Their rounding errors (2^-24 of terms below kDiffRel max|q|)
+// stay under the FP64 rounding of z.  The format conversions run on the
+// integer pipe (the FP64 pipe bounds the sweeps): truncation to single
+// precision, values below its normal range flushed to zero.
+constexpr double kDiffRel = 0x1p-32;    // largest change, relative to max|q|, for a difference iteration
+constexpr double kDiffFloor = 0x1p-50;  // smallest max|q| for which they are taken
+
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sgn = (unsigned)(b >> 32) & 0x80000000u;
+  int e = (int)((b >> 52) & 0x7ff) - 896;  // the single-precision exponent field
+  e = e > 254 ? 255 : e;                   // out of range: infinity (not reached where used)
+  const unsigned man = e == 255 ? 0u : (unsigned)(b >> 29) & 0x7fffffu;
+  return __uint_as_float(e <= 0 ? sgn : (sgn | ((unsigned)e << 23) | man));
+}
+__device__ __forceinline__ double f32_to_f64(float x) {
+  const unsigned u = __float_as_uint(x);
+  const unsigned e = (u >> 23) & 0xffu;
+  const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+  const unsigned long long ed = e == 255u ? 2047ull : (unsigned long long)(e + 896u);
+  const unsigned long long man = (unsigned long long)(u & 0x7fffffu) << 29;
+  return __longlong_as_double((long long)(e == 0u ? sgn : (sgn | (ed << 52) | man)));
+}
+// entry (k, l) of a packed Hermitian difference (as ldpk)
+__device__ __forceinline__ float2 ldpkf(const float2* p, int k, int l) {
+  const bool lo = k > l;
+  const int a = lo ? l : k, c = lo ? k : l;
+  float2 x = __ldcg(p + ((c * (c + 1)) >> 1) + a);
+  x.y = __uint_as_float(__float_as_uint(x.y) ^ (lo ? 0x80000000u : 0u));
+  return x;
+}
+
+// offdiag_acc in single precision on a difference d (the same terms: the
+// control commutators, the decay sandwich and the Jaynes-Cummings pairs)
+template <bool ADJ, bool PK>
+__device__ __forceinline__ void offdiag_acc_f(float& ar, float& ai, const float2* __restrict__ x, int v, uint32_t kd,
+                                              uint32_t ld, const Hdr& H, const GridSmem& S, int k, int l) {
+  const int N = H.N;
+  auto nb = [&](int dk, int dl) -> float2 {
+    if constexpr (PK) return ldpkf(x, k + dk, l + dl);
+    else return __ldcg(x + v + dk + dl * N);
+  };
+  for (int q = 0; q < H.Q; ++q) {
+    const int n = H.lev[q], s = H.stride[q], co = H.coff[q];
+    const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
+    const float c1 = S.cuf[co + nk], c2 = S.cdf[co + nl], c3 = S.cdf[co + nk], c4 = S.cuf[co + nl];
+    const float2 x1 = nb(nk + 1 < n ? s : 0, 0);
+    const float2 x2 = nb(0, nl > 0 ? -s : 0);
+    const float2 x3 = nb(nk > 0 ? -s : 0, 0);
+    const float2 x4 = nb(0, nl + 1 < n ? s : 0);
+    const float pr = fmaf(-c2, x2.x, c1 * x1.x);
+    const float pi = fmaf(-c2, x2.y, c1 * x1.y);
+    const float rr = fmaf(-c4, x4.x, c3 * x3.x);
+    const float ri = fmaf(-c4, x4.y, c3 * x3.y);
+    const float ur = pr + rr, ui = pi + ri, wr = pr - rr, wi = pi - ri;
+    const float2 c = S.ctf[q];
+    const float a = ADJ ? -c.x : c.x, b = ADJ ? -c.y : c.y;
+    ar = fmaf(b, wr, fmaf(a, ui, ar));
+    ai = fmaf(b, wi, fmaf(-a, ur, ai));
+    if ((H.jon >> q) & 1u) {
+      const int jo = H.joff[q] + nk * n + nl;
+      float cj;
+      float2 x5;
+      if (!ADJ) {
+        cj = S.jff[jo];
+        const int d = (nk + 1 < n && nl + 1 < n) ? s : 0;
+        x5 = nb(d, d);
+      } else {
+        cj = S.jaf[jo];
+        const int d = (nk > 0 && nl > 0) ? s : 0;
+        x5 = nb(-d, -d);
+      }
+      ar = fmaf(cj, x5.x, ar);
+      ai = fmaf(cj, x5.y, ai);
+    }
+  }
+  for (int kp = 0; kp < H.npair; ++kp) {
+    const int p = H.jp[kp], q = H.jq[kp];
+    const int np = H.lev[p], nq = H.lev[q], sp = H.stride[p], sq = H.stride[q];
+    const int pk = (kd >> (H.db * p)) & H.dm, qk = (kd >> (H.db * q)) & H.dm;
+    const int pl = (ld >> (H.db * p)) & H.dm, ql = (ld >> (H.db * q)) & H.dm;
+    const float u1 = S.cdf[H.coff[p] + pk] * S.cuf[H.coff[q] + qk];
+    const float u2 = S.cuf[H.coff[p] + pl] * S.cdf[H.coff[q] + ql];
+    const float w1 = S.cuf[H.coff[p] + pk] * S.cdf[H.coff[q] + qk];
+    const float w2 = S.cdf[H.coff[p] + pl] * S.cuf[H.coff[q] + ql];
+    const int d = sq - sp;
+    const float2 xu1 = nb((pk > 0 && qk + 1 < nq) ? d : 0, 0);
+    const float2 xu2 = nb(0, (ql > 0 && pl + 1 < np) ? -d : 0);
+    const float2 xw1 = nb((qk > 0 && pk + 1 < np) ? -d : 0, 0);
+    const float2 xw2 = nb(0, (pl > 0 && ql + 1 < nq) ? d : 0);
+    const float ur = fmaf(-u2, xu2.x, u1 * xu1.x), ui = fmaf(-u2, xu2.y, u1 * xu1.y);
+    const float wr = fmaf(-w2, xw2.x, w1 * xw1.x), wi = fmaf(-w2, xw2.y, w1 * xw1.y);
+    const float2 c = S.ctf[H.Q + kp];
+    const float a = ADJ ? -c.x : c.x, b = ADJ ? -c.y : c.y;
+    ar = fmaf(b, ur - wr, fmaf(a, ui + wi, ar));
+    ai = fmaf(b, ui - wi, fmaf(-a, ur + wr, ai));
+  }
+}
+
+// One difference iteration over a block's chunk [e0, e1): from the change dc
+// of the last iteration (single precision), the new iterate zn = zc + its
+// change dn, the FP64 correction in cring (the predictor's ring slot, when
+// the solve records one) updated, and the per-state maxima of the change
+// pushed to `bank`.
+template <bool ADJ>
+__device__ __forceinline__ void grid_diff_pass(const ProbDev& P, const GridSmem& S, long long e0, long long e1,
+                                            const float2* __restrict__ dc, float2* __restrict__ dn,
+                                            const double2* __restrict__ zc, double2* __restrict__ zn,
+                                            double2* __restrict__ cring, unsigned long long* bank) {
+  const GridHdr& G = *S.g;
+  const Hdr& H = G.h;
+  StateMax sm;
+  sm.init(e0, e1, G.Vh);
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const GEl g = gel(G, P.hmap, e);
+    const int b = g.b, v = g.v;
+    const size_t o = gslab(G, g, b);
+    const uint32_t kd = __ldg(P.digits + g.k), ld = __ldg(P.digits + g.l);
+    // (dt/2) O d in single precision: the change of the correction
+    float fr = 0.0f, fi = 0.0f;
+    if (G.herm)
+      offdiag_acc_f<ADJ, true>(fr, fi, dc + (size_t)b * G.Vh, v, kd, ld, H, S, g.k, g.l);
+    else
+      offdiag_acc_f<ADJ, false>(fr, fi, dc + (size_t)b * G.Vh, v, kd, ld, H, S, g.k, g.l);
+    if (cring) {
+      const double2 c = cring[o];
+      cring[o] = make_double2(c.x + f32_to_f64(fr), c.y + f32_to_f64(fi));
+    }
+    // the change of the iterate, (I - dt/2 D)^-1 times that
+    const float2 df = __ldg(P.Dinvf + v);
+    const float dfi = ADJ ? -df.y : df.y;
+    const float ex = fmaf(df.x, fr, -dfi * fi), ey = fmaf(df.x, fi, dfi * fr);
+    const double ddx = f32_to_f64(ex), ddy = f32_to_f64(ey);
+    const double2 zo = __ldcg(zc + o);
+    zn[o] = make_double2(zo.x + ddx, zo.y + ddy);
+    dn[o] = make_float2(ex, ey);
+    sm.add(b, umax64(abs_bits(ddx), abs_bits(ddy)), bank);
+  }
+  sm.push(bank, reinterpret_cast<unsigned long long*>(S.red));
+}
+
 template <bool ADJ>
 __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __restrict__ rhs,
                           const double2* __restrict__ ct, double fac, long long& it_global, long long& solve,
-                          double2** zout, GridHist hist = GridHist(), double penw = 0.0) {
+                          int& ndiff, double2** zout, GridHist hist = GridHist(), double penw = 0.0) {
   const GridHdr& G = *S.g;
   const Hdr& H = G.h;
   const Tabs T{S.cu, S.cd, S.jf, S.ja};
@@ -372,6 +541,10 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
   unsigned long long* qslots = P.gslots + 3 * M;  // [2][M]
   unsigned long long* qbank = qslots + (solve & 1) * M;
   unsigned long long* red = reinterpret_cast<unsigned long long*>(S.red);
+  // difference iterations: Jacobi only; this solve's control factors in single precision
+  const bool dok = P.diffit && !neumann && P.dfA != nullptr;
+  if (dok && (int)threadIdx.x < H.cq) S.ctf[threadIdx.x] = make_float2((float)ct[threadIdx.x].x, (float)ct[threadIdx.x].y);
+  ndiff = 0;
   // z_0 = (I - dt/2 D)^-1 rhs (Jacobi) or rhs (Neumann); per-state max |rhs|
   {
     StateMax sm;
@@ -449,8 +622,17 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
   const double hh = 0.5 * H.h;
   double2* zc = P.zA;
   double2* zn = P.zB;
+  // single-precision changes of the iterates: iteration `it` writes the
+  // change of zn to dfB (even it) or dfA (odd it) and a difference iteration
+  // reads the other buffer
+  bool dit = false;  // this iteration is a difference iteration
   for (int it = 0; it < H.max_iter; ++it, ++it_global) {
     unsigned long long* bank = dslots + (it_global % 3) * M;
+    if (dit) {
+      ++ndiff;
+      grid_diff_pass<ADJ>(P, S, e0, e1, (it & 1) ? P.dfB : P.dfA, (it & 1) ? P.dfA : P.dfB, zc, zn,
+                          hist.ring ? hist.ring + (size_t)hist.slot * ((size_t)M * G.Vh) : nullptr, bank);
+    } else {
     StateMax sm;
     sm.init(e0, e1, G.Vh);
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
@@ -485,9 +667,12 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
         z.y = ai + fma(dr, zo.y, di * zo.x);
       }
       zn[o] = z;
-      sm.add(b, umax64(abs_bits(z.x - zo.x), abs_bits(z.y - zo.y)), bank);
+      const double ddx = z.x - zo.x, ddy = z.y - zo.y;
+      if (dok) ((it & 1) ? P.dfA : P.dfB)[o] = make_float2(f64_to_f32_trunc(ddx), f64_to_f32_trunc(ddy));
+      sm.add(b, umax64(abs_bits(ddx), abs_bits(ddy)), bank);
     }
     sm.push(bank, red);
+    }
     if (!grid_sync(P.bar, gridDim.x, P.spin_limit > 0 ? P.spin_limit : kSpinLimit)) return -3;
     // bank of iteration it_global + 2 is no longer read by anyone: clear it
     if (blockIdx.x == 0)
@@ -495,23 +680,31 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
     // every block takes the same decision from the same slots (the states
     // spread over the lanes of warp 0)
     if (threadIdx.x < 32) {
-      bool bad = false, open = false;
+      bool bad = false, open = false, small = true;
       for (int b = threadIdx.x; b < M; b += 32) {
         const unsigned long long d = __ldcg(bank + b);
         const unsigned long long q = __ldcg(qbank + b);
         if (d >= kInfBits || q >= kInfBits) {
           bad = true;
         } else {
-          const unsigned long long thr = abs_bits(H.rtol * __longlong_as_double((long long)q) * fac);
+          const double qd = __longlong_as_double((long long)q);
+          const unsigned long long thr = abs_bits(H.rtol * qd * fac);
           if (d > thr) open = true;
+          // a difference iteration next: every state's change below kDiffRel max|q|
+          if (!(qd >= kDiffFloor) || d > abs_bits(kDiffRel * qd)) small = false;
         }
       }
       bad = __any_sync(kFull, bad);
       open = __any_sync(kFull, open);
-      if (threadIdx.x == 0) *S.flag = bad ? -2 : (open ? 0 : 1);  // NaN/Inf, not yet, converged
+      small = __all_sync(kFull, small);
+      if (threadIdx.x == 0) {
+        S.flag[0] = bad ? -2 : (open ? 0 : 1);  // NaN/Inf, not yet, converged
+        S.flag[1] = dok && small ? 1 : 0;
+      }
     }
     __syncthreads();
-    const int state = *S.flag;
+    const int state = S.flag[0];
+    dit = S.flag[1] != 0;
     __syncthreads();
     double2* t = zc;
     zc = zn;
@@ -555,7 +748,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
     }
   bool failed = false;
   long long itg = 0, nsolve = 0;
-  unsigned long long iters = 0, steps = 0;
+  unsigned long long iters = 0, steps = 0, diters = 0;
   int maxit = 0;
   const int phase = mode == 2 ? 2 : 0;
   // first-iterate predictor of the forward sweep, forgetting its history at
@@ -580,15 +773,18 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
       }
     }
     double2* z = nullptr;
-    const int it = mode == 2 ? grid_solve<true>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, &z)
-                             : grid_solve<false>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, &z,
-                                                 pred ? hist : GridHist(), penal ? P.pen[j] : 0.0);
+    int nd = 0;
+    const int it = mode == 2 ? grid_solve<true>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve,
+                                                nd, &z)
+                             : grid_solve<false>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve,
+                                                 nd, &z, pred ? hist : GridHist(), penal ? P.pen[j] : 0.0);
     if (it < 0) {
       grid_fail(P, it, j);
       failed = true;
       break;
     }
     iters += (unsigned long long)it * G.M;
+    diters += (unsigned long long)nd * G.M;
     steps += G.M;
     maxit = max(maxit, it);
     for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
@@ -613,6 +809,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     atomicAdd(&P.status->iters[phase], iters);
     atomicAdd(&P.status->steps[phase], steps);
+    atomicAdd(&P.status->diters[phase], diters);
     atomicMax(&P.status->max_iter_seen, maxit);
   }
 }
@@ -651,7 +848,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
       P.qb[gslab(G, g, g.b)] = P.qT[(size_t)g.b * V + g.v];
     }
   long long itg = 0, nsolve = 0;
-  unsigned long long it_rec = 0, st_rec = 0, it_adj = 0, st_adj = 0;
+  unsigned long long it_rec = 0, st_rec = 0, it_adj = 0, st_adj = 0, dit_rec = 0, dit_adj = 0;
   int maxit = 0;
   const int nseg = H.K > 0 ? (H.NT + H.K - 1) / H.K : 1;
   bool failed = false;
@@ -681,14 +878,16 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
       for (int j = j0; j < j1; ++j) {
         double2* z = nullptr;
         if (fpred && j % R == 0) fhist.restart();  // every checkpoint is a restart point
-        const int it = grid_solve<false>(P, S, P.qf, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, &z,
-                                         fpred ? fhist : GridHist());
+        int nd = 0;
+        const int it = grid_solve<false>(P, S, P.qf, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, nd,
+                                         &z, fpred ? fhist : GridHist());
         if (it < 0) {
           grid_fail(P, it, j);
           failed = true;
           break;
         }
         it_rec += (unsigned long long)it * G.M;
+        dit_rec += (unsigned long long)nd * G.M;
         st_rec += G.M;
         maxit = max(maxit, it);
         for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
@@ -709,13 +908,16 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
     for (int j = j1 - 1; j >= j0; --j) {
       const double2* ct = P.ctab + (size_t)j * H.cq;
       double2* zh = nullptr;
-      const int it = grid_solve<true>(P, S, P.lam, ct, stop_factor(P, j), itg, nsolve, &zh, apred ? ahist : GridHist());
+      int nd = 0;
+      const int it =
+          grid_solve<true>(P, S, P.lam, ct, stop_factor(P, j), itg, nsolve, nd, &zh, apred ? ahist : GridHist());
       if (it < 0) {
         grid_fail(P, it, j);
         failed = true;
         break;
       }
       it_adj += (unsigned long long)it * G.M;
+      dit_adj += (unsigned long long)nd * G.M;
       st_adj += G.M;
       maxit = max(maxit, it);
       // Passes over this block's elements, four subsystems each (so that the
@@ -758,20 +960,23 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
               const double pi = fma(-c2, x2.y, c1 * x1.y);
               const double rr = fma(-c4, x4.x, c3 * x3.x);
               const double ri = fma(-c4, x4.y, c3 * x3.y);
-              if (g.vm < 0) {
+              if (!G.herm) {
                 sar[u] = fma(Z.x, rr, fma(Z.y, ri, sar[u]));
                 sai[u] = fma(Z.y, rr, fma(-Z.x, ri, sai[u]));
                 sdr[u] = fma(Z.x, pr, fma(Z.y, pi, sdr[u]));
                 sdi[u] = fma(Z.y, pr, fma(-Z.x, pi, sdi[u]));
+              } else if (g.vm >= 0) {
+                // Hermitian Z and zhat, A = Z conj(R), B = Z conj(P): the element
+                // and its mirror (l, k) add A - conj(B) to the g_a sum and
+                // B - conj(A), its negated conjugate, to the g_ad sum
+                const double dr = rr - pr, di = ri - pi, ur = rr + pr, ui = ri + pi;
+                sar[u] = fma(Z.x, dr, fma(Z.y, di, sar[u]));
+                sai[u] = fma(Z.y, ur, fma(-Z.x, ui, sai[u]));
               } else {
-                // Hermitian Z and zhat: the mirror element (l, k) adds -conj(B) to
-                // the g_a sum and -conj(A) to the g_ad sum, A = Z conj(R), B = Z conj(P)
-                const double ar = fma(Z.x, rr, Z.y * ri), ai = fma(Z.y, rr, -Z.x * ri);
-                const double br = fma(Z.x, pr, Z.y * pi), bi = fma(Z.y, pr, -Z.x * pi);
-                sar[u] += ar - br;
-                sai[u] += ai + bi;
-                sdr[u] += br - ar;
-                sdi[u] += bi + ai;
+                // a diagonal element of Hermitian Z and zhat has conj(R) = -P, so
+                // B = -conj(A): it adds A to g_a and its negated conjugate to g_ad
+                sar[u] = fma(Z.x, rr, fma(Z.y, ri, sar[u]));
+                sai[u] = fma(Z.y, rr, fma(-Z.x, ri, sai[u]));
               }
             }
           }
@@ -796,6 +1001,14 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
             }
             P.lam[o] = ln;
             if (apred) grid_commit<true>(P, ahist, o, (size_t)G.M * G.Vh, v);
+          }
+        }
+        if (G.herm) {
+          // the g_ad sum of Hermitian Z and zhat is minus the conjugate of the g_a sum
+#pragma unroll
+          for (int u = 0; u < kQP; ++u) {
+            sdr[u] = -sar[u];
+            sdi[u] = sai[u];
           }
         }
 #pragma unroll
@@ -841,6 +1054,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
     atomicAdd(&P.status->steps[1], st_rec);
     atomicAdd(&P.status->iters[2], it_adj);
     atomicAdd(&P.status->steps[2], st_adj);
+    atomicAdd(&P.status->diters[1], dit_rec);
+    atomicAdd(&P.status->diters[2], dit_adj);
     atomicMax(&P.status->max_iter_seen, maxit);
   }
 }

@@ -19,6 +19,7 @@ struct DevStatus {
   int32_t pad;
   unsigned long long iters[3];  // iterations per phase: forward, recompute, adjoint
   unsigned long long steps[3];  // state-steps per phase
+  unsigned long long diters[3]; // of iters: difference iterations in single precision (grid sweeps)
 };
 
 // Grid-wide barrier state of a cooperative launch (zeroed before each launch).
@@ -111,7 +112,10 @@ struct ProbDev {
   long long spin_limit;      // polls of a grid-barrier wait before it gives up (0: the kernels' default)
   int32_t* hmap;             // [N (N + 1) / 2] vec indices k + N l with k <= l (grid sweeps)
   int32_t herm;              // grid sweeps iterate k <= l only: every state and target is Hermitian
-  int32_t pad1;
+  int32_t diffit;            // grid sweeps: difference iterations in single precision allowed (Jacobi)
+  float2* dfA;               // [M*V] grid sweeps: single-precision differences of successive iterates
+  float2* dfB;
+  float2* Dinvf;             // [V] grid sweeps: (I - dt/2 D)^-1 in single precision
 };
 
 // one work item of a resident launch: (problem, state)

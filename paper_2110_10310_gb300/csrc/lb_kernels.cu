@@ -76,6 +76,7 @@ __global__ void k_tables(ProbDev* __restrict__ pp) {
     const double ar = 1.0 - hh * D.x, ai = -hh * D.y;  // 1 - dt/2 D
     const double den = ar * ar + ai * ai;
     P.Dinv[tid] = make_double2(ar / den, -ai / den);
+    if (P.Dinvf) P.Dinvf[tid] = make_float2((float)(ar / den), (float)(-ai / den));
     if (P.Ginv) {
       // 1/g = (1 - dt/2 D)/(1 + dt/2 D), g the element's free step factor
       const double br = 1.0 + hh * D.x, bi = hh * D.y;

@@ -988,23 +988,31 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
             const double pi = fma(-c2, x2.y, c1 * x1.y);
             const double rr = fma(-c4, x4.x, c3 * x3.x);
             const double ri = fma(-c4, x4.y, c3 * x3.y);
-            // Z conj(R) and Z conj(P)
-            if (el_m(el, S, H, e) < 0) {
+            // A = Z conj(R) to g_a and B = Z conj(P) to g_ad
+            if (!H.herm) {
               sar = fma(Z[e].x, rr, fma(Z[e].y, ri, sar));
               sai = fma(Z[e].y, rr, fma(-Z[e].x, ri, sai));
               sdr = fma(Z[e].x, pr, fma(Z[e].y, pi, sdr));
               sdi = fma(Z[e].y, pr, fma(-Z[e].x, pi, sdi));
+            } else if (el_m(el, S, H, e) >= 0) {
+              // Hermitian Z and zhat: the element and its mirror (l, k) add
+              // A - conj(B) to the g_a sum and B - conj(A), its negated
+              // conjugate, to the g_ad sum
+              const double dr = rr - pr, di = ri - pi, ur = rr + pr, ui = ri + pi;
+              sar = fma(Z[e].x, dr, fma(Z[e].y, di, sar));
+              sai = fma(Z[e].y, ur, fma(-Z[e].x, ui, sai));
             } else {
-              // Hermitian Z and zhat: the mirror element (l, k) adds -conj(B) to
-              // the g_a sum and -conj(A) to the g_ad sum, A = Z conj(R), B = Z conj(P)
-              const double ar = fma(Z[e].x, rr, Z[e].y * ri), ai = fma(Z[e].y, rr, -Z[e].x * ri);
-              const double br = fma(Z[e].x, pr, Z[e].y * pi), bi = fma(Z[e].y, pr, -Z[e].x * pi);
-              sar += ar - br;
-              sai += ai + bi;
-              sdr += br - ar;
-              sdi += bi + ai;
+              // a diagonal element of Hermitian Z and zhat has conj(R) = -P, so
+              // B = -conj(A): it adds A to g_a and its negated conjugate to g_ad
+              sar = fma(Z[e].x, rr, fma(Z[e].y, ri, sar));
+              sai = fma(Z[e].y, rr, fma(-Z[e].x, ri, sai));
             }
           }
+        }
+        if (H.herm) {
+          // the g_ad sum of Hermitian Z and zhat is minus the conjugate of the g_a sum
+          sdr = -sar;
+          sdi = sai;
         }
         const double r = warp_sum4(sar, sai, sdr, sdi, lane);
         if ((lane & 7) == 0) S.red[(q * 4 + (lane >> 3)) * 16 + warp] = r;

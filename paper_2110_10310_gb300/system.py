@@ -42,7 +42,8 @@ def _stats_dict(s) -> dict:
             "sweep": {1: "resident", 2: "grid", 3: "cluster"}.get(s.sweep, s.sweep),
             "solver": {1: "jacobi", 2: "neumann", 3: "gmres"}.get(s.solver, s.solver),
             "symmetry": "hermitian" if s.symmetry == L.LB_SYM_HERMITIAN else "none",
-            "ckpt_every": s.ckpt_every, "states_integrated": s.states_integrated}
+            "ckpt_every": s.ckpt_every, "states_integrated": s.states_integrated,
+            "phase_diff_iterations": list(s.phase_diff_iterations)}
 
 
 def _stream_handle(stream) -> c_void_p:
@@ -60,7 +61,8 @@ class LindbladSystem:
 
     def __init__(self, problem, *, solver: int = L.LB_SOLVER_AUTO, rtol: float = 1e-15, max_iter: int = 200,
                  ckpt_every: int | None = None, sweep: int = L.LB_SWEEP_AUTO, symmetry: int = L.LB_SYM_HERMITIAN,
-                 predictor: int = L.LB_PRED_AUTO, pred_order: int = 0, pairing: int = 1, device=None, stream=None):
+                 predictor: int = L.LB_PRED_AUTO, pred_order: int = 0, pairing: int = 1,
+                 difference_iterations: int = 1, device=None, stream=None):
         self.lib = L.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         sysm = problem.system
@@ -126,6 +128,7 @@ class LindbladSystem:
         L.check(self.lib.lb_set_symmetry(h, int(symmetry)))
         L.check(self.lib.lb_set_predictor(h, int(predictor), int(pred_order)))
         L.check(self.lib.lb_set_pairing(h, int(pairing)))
+        L.check(self.lib.lb_set_difference_iterations(h, int(difference_iterations)))
         nbytes = c_size_t()
         L.check(self.lib.lb_workspace_bytes(h, byref(nbytes)))
         self.workspace_bytes = int(nbytes.value)

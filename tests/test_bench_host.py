@@ -48,6 +48,20 @@ def test_fp64_counts_match_their_definitions():
     assert bench.method_flops(V, Q, st, (1, 2)) == V * 80 * 9 + V * 56 * 5
 
 
+def test_difference_iterations_are_not_counted_as_fp64_applies():
+    """A single-precision difference iteration adds 4 FP64 flops per element
+    to the instruction count and nothing to the method count; the Hermitian
+    symmetry's gradient pieces take 24 flops per subsystem."""
+    st = {"phase_steps": [5, 0, 5], "phase_iterations": [7, 0, 9], "phase_diff_iterations": [2, 0, 3],
+          "symmetry": "hermitian"}
+    V, Q, nd = 81, 2, 2
+    per_it = 24 * Q + 4 * nd + 8
+    assert bench.fp64_flops(V, Q, nd, st, (0,)) == V * (10 * 5 + per_it * 5 + 4 * 2)
+    assert bench.fp64_flops(V, Q, nd, st, (2,)) == V * (10 * 5 + per_it * 6 + 4 * 3) + V * 24 * Q * 5
+    assert bench.method_flops(V, Q, st, (0,)) == V * 80 * 5
+    assert bench.method_flops(V, Q, st, (1, 2)) == V * 80 * 6 + V * 56 * 5
+
+
 def test_dense_oracle_extrapolation_is_cubic():
     assert bench.extrapolate_dense(8.0, 4096, 8192) == 1.0
     assert abs(bench.extrapolate_dense(2.0, 4096, 531441) - 2.0 / (531441 / 4096) ** 3) < 1e-20

@@ -375,6 +375,63 @@ def test_grid_sweep_matches_oracle(levels, K, herm):
     assert _rel(gg, gr) < 1e-11
 
 
+@pytest.mark.parametrize("levels,K,herm,coupled", [((3, 3), 7, True, False), ((2, 3), 0, False, False),
+                                                  ((3, 2, 2), 10, True, True)])
+def test_difference_iterations_match_oracle_and_fp64_iterations(levels, K, herm, coupled):
+    """Grid sweeps with single-precision difference iterations (the default)
+    against every iteration in FP64 and against the oracle.  A coarse step
+    without a predictor needs ~10 inner iterations per step, the last third
+    of them difference iterations: states and objective to 1e-10 of the oracle,
+    gradient to 1e-9, and the two iteration schemes to 1e-12 (both stop at
+    rtol 1e-15 of |q|; they differ by rounding)."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(411, levels=levels, n_states=3, n_steps=30, T_ns=1.2, amp=0.1, ckpt_every=K,
+                         hermitian=herm, jc=0.05 if coupled else 0.0)
+    kw = dict(sweep=L.LB_SWEEP_GRID, predictor=L.LB_PRED_NONE)
+    s, g = _check_problem(p, **kw)
+    st = s.stats()
+    assert st["sweep"] == "grid"
+    assert st["symmetry"] == ("hermitian" if herm else "none")
+    its = np.array(st["phase_iterations"])
+    dits = np.array(st["phase_diff_iterations"])
+    steps = np.array(st["phase_steps"])
+    assert its[0] >= 6 * steps[0]                   # a coarse step: many inner iterations
+    assert dits[0] >= 0.2 * its[0] and dits[2] >= 0.2 * its[2]
+    assert np.all(dits <= its - steps)              # the first iteration of every step is FP64
+    G1, rho1 = s.forward(want_states=True)
+    s0 = _sys(p, difference_iterations=0, **kw)
+    G0, rho0 = s0.forward(want_states=True)
+    Gg0, g0 = s0.gradient()
+    assert s0.stats()["phase_diff_iterations"] == [0, 0, 0]
+    assert abs(G1 - G0) <= 1e-12 * abs(G0)
+    assert _rel(rho1.cpu().numpy(), rho0.cpu().numpy()) < 1e-12
+    assert _rel(g, g0) < 1e-12
+
+
+def test_difference_iterations_keep_recompute_bitwise():
+    """The decision to take a difference iteration depends only on the
+    iterates, so a recompute repeats it: without a forward predictor the
+    gradient is bitwise the same for K = 1, 5, 30 with difference iterations
+    on, and the switch may be flipped on a bound handle."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(412, levels=(3, 3), n_states=2, n_steps=30, T_ns=1.2, amp=0.1, hermitian=True)
+    res = []
+    for K in (1, 5, 30):
+        s = _sys(p, ckpt_every=K, sweep=L.LB_SWEEP_GRID, predictor=L.LB_PRED_NONE)
+        res.append(s.gradient())
+        assert s.stats()["phase_diff_iterations"][1] > 0
+    for G, g in res[1:]:
+        assert G == res[0][0]
+        assert np.array_equal(g, res[0][1])
+    L.check(s.lib.lb_set_difference_iterations(s.h, 0))
+    G0, g0 = s.gradient()
+    assert s.stats()["phase_diff_iterations"] == [0, 0, 0]
+    assert abs(G0 - res[0][0]) <= 1e-12 * abs(res[0][0]) and _rel(g0, res[0][1]) < 1e-12
+    assert s.lib.lb_set_difference_iterations(s.h, 2) == L.LB_EINVAL
+
+
 def test_grid_checkpoint_interval_bitwise_identical():
     """Grid sweeps without a forward predictor: K = 1, 7, 100 bit-identical;
     the full tape (K = 0, whose forward sweep predicts its first iterates)

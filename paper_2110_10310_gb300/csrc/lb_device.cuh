@@ -317,7 +317,9 @@ __device__ __forceinline__ double2 ldpk(const double2* p, int k, int l) {
 
 // PK: x is one state stored packed (ldpk), and the neighbours are addressed
 // by (k, l) of element v = k + N l; else x is indexed by the vec index.
-template <bool ADJ, bool CG = false, bool PK = false>
+// QN > 0: H.Q as a compile-time count (the subsystem loop unrolls, so the
+// loads and the arithmetic of different subsystems can interleave).
+template <bool ADJ, bool CG = false, bool PK = false, int QN = 0>
 __device__ __forceinline__ void offdiag_acc(double& ar, double& ai, const double2* __restrict__ x, int v, uint32_t kd,
                                             uint32_t ld, const Hdr& H, const Tabs& T, const double2* __restrict__ ct,
                                             int k = 0, int l = 0) {
@@ -327,7 +329,7 @@ __device__ __forceinline__ void offdiag_acc(double& ar, double& ai, const double
     if constexpr (PK) return ldpk<CG>(x, k + dk, l + dl);
     else return ldz<CG>(x + v + dk + dl * N);
   };
-  for (int q = 0; q < H.Q; ++q) {
+  auto sub = [&](int q) {
     const int n = H.lev[q], s = H.stride[q], co = H.coff[q];
     const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
     // control: -i[H_c, X] with H_c = d a + conj(d) a^+ (Sec. II):
@@ -366,6 +368,12 @@ __device__ __forceinline__ void offdiag_acc(double& ar, double& ai, const double
       ar = fma(cj, x5.x, ar);
       ai = fma(cj, x5.y, ai);
     }
+  };
+  if constexpr (QN > 0) {
+#pragma unroll
+    for (int q = 0; q < QN; ++q) sub(q);
+  } else {
+    for (int q = 0; q < H.Q; ++q) sub(q);
   }
   // Jaynes-Cummings pairs (Sec. II): -i[G a_p^+ a_q + conj(G) a_p a_q^+, X] with
   //   U = sqrt(np_k) sqrt(nq_k+1) x[k-sp+sq, l] - sqrt(np_l+1) sqrt(nq_l) x[k, l+sp-sq]

@@ -20,6 +20,14 @@ namespace {
 
 constexpr long long kSpinLimit = 1LL << 26;  // ~seconds of polling before a barrier gives up
 
+// Neighbour reads of the iterates go through L1 (kNbL2 = false): each value
+// is read by up to 1 + 5Q elements, most of them in the same block's chunk.
+// The iterates are rewritten by other blocks between iterations; every such
+// read follows a grid_sync, whose fence after the wait (acquire, GPU scope)
+// makes the writes of the previous iteration visible to ordinary loads (the
+// ordering cooperative groups' grid sync provides with the same pattern).
+constexpr bool kNbL2 = false;
+
 // Grid barrier with a bounded wait: at most `limit` polls (kSpinLimit unless
 // the handle set another bound, lb_set_wait_limit).  Returns false on every
 // block once a wait has given up (the kernel then returns).
@@ -412,22 +420,27 @@ __device__ __forceinline__ double f32_to_f64(float x) {
 __device__ __forceinline__ float2 ldpkf(const float2* p, int k, int l) {
   const bool lo = k > l;
   const int a = lo ? l : k, c = lo ? k : l;
-  float2 x = __ldcg(p + ((c * (c + 1)) >> 1) + a);
+  const float2* q = p + ((c * (c + 1)) >> 1) + a;
+  float2 x = kNbL2 ? __ldcg(q) : *q;
   x.y = __uint_as_float(__float_as_uint(x.y) ^ (lo ? 0x80000000u : 0u));
   return x;
 }
 
 // offdiag_acc in single precision on a difference d (the same terms: the
-// control commutators, the decay sandwich and the Jaynes-Cummings pairs)
-template <bool ADJ, bool PK>
+// control commutators, the decay sandwich and the Jaynes-Cummings pairs).
+// QN = H.Q as a compile-time count, so that the subsystem loop unrolls and
+// every neighbour load can be issued before the arithmetic: with little
+// arithmetic per load this pass is bound by the latency of L2 reads.
+template <bool ADJ, bool PK, int QN>
 __device__ __forceinline__ void offdiag_acc_f(float& ar, float& ai, const float2* __restrict__ x, int v, uint32_t kd,
                                               uint32_t ld, const Hdr& H, const GridSmem& S, int k, int l) {
   const int N = H.N;
   auto nb = [&](int dk, int dl) -> float2 {
     if constexpr (PK) return ldpkf(x, k + dk, l + dl);
-    else return __ldcg(x + v + dk + dl * N);
+    else return kNbL2 ? __ldcg(x + v + dk + dl * N) : x[v + dk + dl * N];
   };
-  for (int q = 0; q < H.Q; ++q) {
+#pragma unroll
+  for (int q = 0; q < QN; ++q) {
     const int n = H.lev[q], s = H.stride[q], co = H.coff[q];
     const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
     const float c1 = S.cuf[co + nk], c2 = S.cdf[co + nl], c3 = S.cdf[co + nk], c4 = S.cuf[co + nl];
@@ -489,7 +502,7 @@ __device__ __forceinline__ void offdiag_acc_f(float& ar, float& ai, const float2
 // change dn, the FP64 correction in cring (the predictor's ring slot, when
 // the solve records one) updated, and the per-state maxima of the change
 // pushed to `bank`.
-template <bool ADJ>
+template <bool ADJ, int QN>
 __device__ __forceinline__ void grid_diff_pass(const ProbDev& P, const GridSmem& S, long long e0, long long e1,
                                             const float2* __restrict__ dc, float2* __restrict__ dn,
                                             const double2* __restrict__ zc, double2* __restrict__ zn,
@@ -506,9 +519,9 @@ __device__ __forceinline__ void grid_diff_pass(const ProbDev& P, const GridSmem&
     // (dt/2) O d in single precision: the change of the correction
     float fr = 0.0f, fi = 0.0f;
     if (G.herm)
-      offdiag_acc_f<ADJ, true>(fr, fi, dc + (size_t)b * G.Vh, v, kd, ld, H, S, g.k, g.l);
+      offdiag_acc_f<ADJ, true, QN>(fr, fi, dc + (size_t)b * G.Vh, v, kd, ld, H, S, g.k, g.l);
     else
-      offdiag_acc_f<ADJ, false>(fr, fi, dc + (size_t)b * G.Vh, v, kd, ld, H, S, g.k, g.l);
+      offdiag_acc_f<ADJ, false, QN>(fr, fi, dc + (size_t)b * G.Vh, v, kd, ld, H, S, g.k, g.l);
     if (cring) {
       const double2 c = cring[o];
       cring[o] = make_double2(c.x + f32_to_f64(fr), c.y + f32_to_f64(fi));
@@ -521,6 +534,59 @@ __device__ __forceinline__ void grid_diff_pass(const ProbDev& P, const GridSmem&
     const double2 zo = __ldcg(zc + o);
     zn[o] = make_double2(zo.x + ddx, zo.y + ddy);
     dn[o] = make_float2(ex, ey);
+    sm.add(b, umax64(abs_bits(ddx), abs_bits(ddy)), bank);
+  }
+  sm.push(bank, reinterpret_cast<unsigned long long*>(S.red));
+}
+
+// One FP64 Jacobi (or Neumann) iteration over a block's chunk [e0, e1): the
+// correction (dt/2) O z of the iterate zc, kept apart from the right-hand
+// side (with the predictor on it goes to the ring slot cring of this step;
+// the last iteration's write stays: the correction whose Jacobi image is the
+// returned z), the new iterate zn, its single-precision change dnew (for a
+// difference iteration next) and the per-state maxima of the change pushed
+// to `bank`.  QN: the subsystem count at compile time (0: H.Q at run time).
+template <bool ADJ, int QN>
+__device__ __forceinline__ void grid_full_pass(const ProbDev& P, const GridSmem& S, long long e0, long long e1,
+                                            const double2* __restrict__ rhs, const double2* __restrict__ ct,
+                                            const double2* __restrict__ zc, double2* __restrict__ zn,
+                                            double2* __restrict__ cring, float2* __restrict__ dnew, bool neumann,
+                                            double hh, unsigned long long* bank) {
+  const GridHdr& G = *S.g;
+  const Hdr& H = G.h;
+  const Tabs T{S.cu, S.cd, S.jf, S.ja};
+  StateMax sm;
+  sm.init(e0, e1, G.Vh);
+  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+    const GEl g = gel(G, P.hmap, e);
+    const int b = g.b, v = g.v;
+    const double2* xs = zc + (size_t)b * G.Vh;
+    const size_t o = gslab(G, g, b);
+    const double2 r = rhs[o];
+    double cr = 0.0, ci = 0.0;
+    const uint32_t kd = __ldg(P.digits + g.k), ld = __ldg(P.digits + g.l);
+    if (G.herm)
+      offdiag_acc<ADJ, kNbL2, true, QN>(cr, ci, xs, v, kd, ld, H, T, ct, g.k, g.l);
+    else
+      offdiag_acc<ADJ, kNbL2, false, QN>(cr, ci, xs, v, kd, ld, H, T, ct);
+    if (cring) cring[o] = make_double2(cr, ci);
+    const double ar = r.x + cr, ai = r.y + ci;
+    const double2 zo = __ldcg(xs + g.i);
+    double2 z;
+    if (!neumann) {
+      const double2 d = __ldg(P.Dinv + v);
+      const double di = ADJ ? -d.y : d.y;
+      z.x = fma(d.x, ar, -di * ai);
+      z.y = fma(d.x, ai, di * ar);
+    } else {
+      const double2 D = __ldg(P.D + v);
+      const double dr = hh * D.x, di = hh * (ADJ ? -D.y : D.y);
+      z.x = ar + fma(dr, zo.x, -di * zo.y);
+      z.y = ai + fma(dr, zo.y, di * zo.x);
+    }
+    zn[o] = z;
+    const double ddx = z.x - zo.x, ddy = z.y - zo.y;
+    if (dnew) dnew[o] = make_float2(f64_to_f32_trunc(ddx), f64_to_f32_trunc(ddy));
     sm.add(b, umax64(abs_bits(ddx), abs_bits(ddy)), bank);
   }
   sm.push(bank, reinterpret_cast<unsigned long long*>(S.red));
@@ -630,48 +696,29 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
     unsigned long long* bank = dslots + (it_global % 3) * M;
     if (dit) {
       ++ndiff;
-      grid_diff_pass<ADJ>(P, S, e0, e1, (it & 1) ? P.dfB : P.dfA, (it & 1) ? P.dfA : P.dfB, zc, zn,
-                          hist.ring ? hist.ring + (size_t)hist.slot * ((size_t)M * G.Vh) : nullptr, bank);
-    } else {
-    StateMax sm;
-    sm.init(e0, e1, G.Vh);
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const GEl g = gel(G, P.hmap, e);
-      const int b = g.b, v = g.v;
-      const double2* xs = zc + (size_t)b * G.Vh;
-      const size_t o = gslab(G, g, b);
-      const double2 r = rhs[o];
-      // the correction (dt/2) O z of this iterate, kept apart from the
-      // right-hand side; with the predictor on it goes to the ring slot of
-      // this step (the last iteration's write stays: the correction whose
-      // Jacobi image is the returned z)
-      double cr = 0.0, ci = 0.0;
-      const uint32_t kd = __ldg(P.digits + g.k), ld = __ldg(P.digits + g.l);
-      if (G.herm)
-        offdiag_acc<ADJ, true, true>(cr, ci, xs, v, kd, ld, H, T, ct, g.k, g.l);
-      else
-        offdiag_acc<ADJ, true, false>(cr, ci, xs, v, kd, ld, H, T, ct);
-      if (hist.ring) hist.ring[(size_t)hist.slot * ((size_t)M * G.Vh) + o] = make_double2(cr, ci);
-      const double ar = r.x + cr, ai = r.y + ci;
-      const double2 zo = __ldcg(xs + g.i);
-      double2 z;
-      if (!neumann) {
-        const double2 d = __ldg(P.Dinv + v);
-        const double di = ADJ ? -d.y : d.y;
-        z.x = fma(d.x, ar, -di * ai);
-        z.y = fma(d.x, ai, di * ar);
-      } else {
-        const double2 D = __ldg(P.D + v);
-        const double dr = hh * D.x, di = hh * (ADJ ? -D.y : D.y);
-        z.x = ar + fma(dr, zo.x, -di * zo.y);
-        z.y = ai + fma(dr, zo.y, di * zo.x);
+      const float2* dcur = (it & 1) ? P.dfB : P.dfA;
+      float2* dnew = (it & 1) ? P.dfA : P.dfB;
+      double2* cring = hist.ring ? hist.ring + (size_t)hist.slot * ((size_t)M * G.Vh) : nullptr;
+      switch (H.Q) {
+        case 1: grid_diff_pass<ADJ, 1>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
+        case 2: grid_diff_pass<ADJ, 2>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
+        case 3: grid_diff_pass<ADJ, 3>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
+        case 4: grid_diff_pass<ADJ, 4>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
+        case 5: grid_diff_pass<ADJ, 5>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
+        case 6: grid_diff_pass<ADJ, 6>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
+        case 7: grid_diff_pass<ADJ, 7>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
+        default: grid_diff_pass<ADJ, 8>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
       }
-      zn[o] = z;
-      const double ddx = z.x - zo.x, ddy = z.y - zo.y;
-      if (dok) ((it & 1) ? P.dfA : P.dfB)[o] = make_float2(f64_to_f32_trunc(ddx), f64_to_f32_trunc(ddy));
-      sm.add(b, umax64(abs_bits(ddx), abs_bits(ddy)), bank);
-    }
-    sm.push(bank, red);
+    } else {
+      double2* cring = hist.ring ? hist.ring + (size_t)hist.slot * ((size_t)M * G.Vh) : nullptr;
+      float2* dnew = dok ? ((it & 1) ? P.dfA : P.dfB) : nullptr;
+      // the subsystem counts of the large workloads (4 and 6) get an
+      // unrolled subsystem loop; other counts run the general loop
+      switch (H.Q) {
+        case 4: grid_full_pass<ADJ, 4>(P, S, e0, e1, rhs, ct, zc, zn, cring, dnew, neumann, hh, bank); break;
+        case 6: grid_full_pass<ADJ, 6>(P, S, e0, e1, rhs, ct, zc, zn, cring, dnew, neumann, hh, bank); break;
+        default: grid_full_pass<ADJ, 0>(P, S, e0, e1, rhs, ct, zc, zn, cring, dnew, neumann, hh, bank); break;
+      }
     }
     if (!grid_sync(P.bar, gridDim.x, P.spin_limit > 0 ? P.spin_limit : kSpinLimit)) return -3;
     // bank of iteration it_global + 2 is no longer read by anyone: clear it
@@ -943,7 +990,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
           const uint32_t kd = __ldg(P.digits + g.k), ld = __ldg(P.digits + g.l);
           // entry at row offset dk, column offset dl of zhat (packed under the symmetry)
           auto nb = [&](int dk, int dl) -> double2 {
-            return G.herm ? ldpk<true>(zs, g.k + dk, g.l + dl) : __ldcg(zs + v + dk + dl * N);
+            return G.herm ? ldpk<kNbL2>(zs, g.k + dk, g.l + dl) : ldz<kNbL2>(zs + v + dk + dl * N);
           };
 #pragma unroll
           for (int u = 0; u < kQP; ++u) {

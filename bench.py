@@ -665,6 +665,7 @@ def run_gradient(args, rank, world, dev, dist):
     import numpy as np
     import torch
 
+    from paper_2110_10310_gb300 import _lib
     from paper_2110_10310_gb300 import dist as D
     from paper_2110_10310_gb300.system import LindbladSystem, colmajor
 
@@ -674,7 +675,8 @@ def run_gradient(args, rank, world, dev, dist):
         full.ckpt_every = args.ckpt
     p = D.shard_problem(full, rank, world) if world > 1 else full
     s = LindbladSystem(p, device=dev, predictor=args.predictor, pred_order=args.pred_order,
-                       difference_iterations=1 if args.diff_iterations == "on" else 0)
+                       difference_iterations=1 if args.diff_iterations == "on" else 0,
+                       precision=_lib.LB_PREC_F32X2 if args.precision == "f32x2" else _lib.LB_PREC_F64)
     tuned = None
     if args.autotune == "on" or (args.autotune == "auto" and wl in ("qutrits_6x3", "qudits_4x4") and not args.pred_order):
         # the library's autotuner (outside the timed region): sweep, inner
@@ -793,7 +795,7 @@ def run_gradient(args, rank, world, dev, dist):
             "higher_is_better": True,
             "scaling": "strong" if world > 1 else "weak",
             "vs_baseline": None,
-            "dtype": "f64",
+            "dtype": "f64" if args.precision == "f64" else "f64+f32x2",
             "data": "synthetic",
             "config": static_config(wl, full),
             "fwd_value": full.M * full.system.n_steps / (fwd_ms * 1e-3),
@@ -812,7 +814,10 @@ def run_gradient(args, rank, world, dev, dist):
                 "precision": ("FP64 states, corrections, objective, gradient and stopping rule; inner iterations "
                               "after the first of a step apply O to the single-precision change of the iterate "
                               "once it is below 2^-32 max|q| (lb_set_difference_iterations)"
-                              if args.diff_iterations == "on" else "FP64 throughout"),
+                              if args.diff_iterations == "on" else "FP64 throughout")
+                             + ("; the other inner iterations apply O in pairs of single-precision numbers "
+                                "(about 48 significant bits, lb_set_precision LB_PREC_F32X2)"
+                                if args.precision == "f32x2" else ""),
                 "ms_forward_kernel": statistics.median(ms_fwd),
                 "ms_backward_kernel": bwd_ms,
                 "workspace_bytes": s.workspace_bytes,
@@ -867,6 +872,8 @@ def main():
     ap.add_argument("--pred-order", type=int, default=0, help="predictor order (lb_set_predictor; 0: default)")
     ap.add_argument("--diff-iterations", default="on", choices=["on", "off"],
                     help="single-precision difference iterations of the grid sweeps (lb_set_difference_iterations)")
+    ap.add_argument("--precision", default="f64", choices=["f64", "f32x2"],
+                    help="arithmetic of the grid sweeps' FP64 inner iterations (lb_set_precision)")
     ap.add_argument("--autotune", default="auto", choices=["auto", "on", "off"],
                     help="run lb_autotune before timing (auto: on for the grid-sweep workloads)")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)

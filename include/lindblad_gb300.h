@@ -303,6 +303,29 @@ int lb_set_wait_limit(lb_system* sys, int64_t polls);
  * bind stream, which is synchronised. */
 int lb_set_difference_iterations(lb_system* sys, int32_t on);
 
+/* Arithmetic of the grid sweeps' FP64 inner iterations (the first of every
+ * step and any before the difference iterations take over).
+ *   LB_PREC_F64 (default): the off-diagonal apply c = (dt/2) O z in FP64.
+ *   LB_PREC_F32X2: the apply in pairs of single-precision numbers (hi + lo,
+ *     about 48 significant bits): every iterate is also stored split into
+ *     such pairs, each product of a coefficient and a neighbour is formed
+ *     with its exact rounding error and the sums carry theirs (two-sum), so
+ *     c is within about 2^-48 of the sum of the magnitudes of its terms,
+ *     i.e. within about 2^-48 rho |z| where rho < 1 is the Jacobi
+ *     contraction bound: a few FP64 roundings of z.  (dt/2) O is the
+ *     part of the implicit midpoint step (Sec. II-B) that moves z by about
+ *     rho |z| per step, so this keeps z within the solver's tolerance of the
+ *     FP64 iteration's while the FP64 pipe, which runs single precision at
+ *     64 times its FP64 rate on this GPU, only forms z = (I - dt/2 D)^-1
+ *     (q + c).  States, the right-hand side, the diagonal, the objective,
+ *     the gradient pieces and the stopping rule stay FP64.  Systems with
+ *     Jaynes-Cummings couplings keep LB_PREC_F64.  Call before
+ *     lb_workspace_bytes (the split iterates take 32 bytes per element and
+ *     state). */
+#define LB_PREC_F64 0
+#define LB_PREC_F32X2 1
+int lb_set_precision(lb_system* sys, int32_t precision);
+
 /* Jaynes-Cummings coupling of the system Hamiltonian (Sec. II):
  *   sum_{p<q} g_pq (e^{i eta_pq t} a_p^+ a_q + e^{-i eta_pq t} a_p a_q^+),
  *   eta_pq = omega_p^rot - omega_q^rot,

@@ -28,6 +28,8 @@ LB_J_TR = 1
 LB_CKPT_AUTO = -1
 LB_PRED_AUTO = -1
 LB_PRED_NONE = -2
+LB_PREC_F64 = 0
+LB_PREC_F32X2 = 1
 
 LB_SWEEP_AUTO = 0
 LB_SWEEP_RESIDENT = 1
@@ -110,6 +112,7 @@ SIGNATURES = {
     "lb_get_predictor": (c_int32, [c_void_p, POINTER(c_int32), POINTER(c_int32)]),
     "lb_set_wait_limit": (c_int32, [c_void_p, c_int64]),
     "lb_set_difference_iterations": (c_int32, [c_void_p, c_int32]),
+    "lb_set_precision": (c_int32, [c_void_p, c_int32]),
     "lb_system_set_coupling": (c_int32, [c_void_p, POINTER(c_double), POINTER(c_double)]),
     "lb_workspace_bytes": (c_int32, [c_void_p, POINTER(c_size_t)]),
     "lb_bind_workspace": (c_int32, [c_void_p, c_void_p, c_size_t, c_void_p]),

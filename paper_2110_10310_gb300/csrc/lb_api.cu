@@ -48,7 +48,7 @@ struct Region {
 
 struct Layout {
   Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
-      gproj, gsum, sfac, pen, qb, jpen, mpart, pmap, Ginv, hgp, hgm, fgp, fgm, dfA, dfB, Dinvf, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, histf,
+      gproj, gsum, sfac, pen, qb, jpen, mpart, pmap, Ginv, hgp, hgm, fgp, fgm, dfA, dfB, Dinvf, zsA, zsB, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, histf,
       hmap;
   size_t total = 0;
 };
@@ -107,6 +107,7 @@ struct lb_system {
   int pred_order = lbk::kDefaultRingOrder;  // its order (grid and one-CTA sweeps)
   long long spin_limit = 0;  // polls of a grid-barrier wait (0: the kernels' default; lb_set_wait_limit)
   int diffit = 1;            // single-precision difference iterations in the grid sweeps (lb_set_difference_iterations)
+  int precision = LB_PREC_F64;  // arithmetic of the grid sweeps' FP64 iterations (lb_set_precision)
   double gamma1 = 0.0, pen_a = 1.0;  // running penalty (one CTA per state)
   bool rho_herm = false;  // every initial state exactly Hermitian
   bool tar_herm = false;  // every explicit target exactly Hermitian (gate targets: always)
@@ -350,6 +351,8 @@ Layout make_layout(const lb_system* s) {
   take(L.dfA, grid ? sizeof(float2) * M * V : 0);
   take(L.dfB, grid ? sizeof(float2) * M * V : 0);
   take(L.Dinvf, grid ? sizeof(float2) * V : 0);
+  take(L.zsA, grid && s->precision == LB_PREC_F32X2 ? sizeof(float4) * M * V : 0);
+  take(L.zsB, grid && s->precision == LB_PREC_F32X2 ? sizeof(float4) * M * V : 0);
   take(L.hmap, sizeof(int32_t) * (size_t)s->N * (s->N + 1) / 2);
   take(L.pmap, sizeof(int32_t) * (size_t)s->Mu);
   L.total = off;
@@ -685,6 +688,11 @@ void fill_prob(lb_system* s) {
   P.dfA = grid ? at<float2>(s, s->L.dfA) : nullptr;
   P.dfB = grid ? at<float2>(s, s->L.dfB) : nullptr;
   P.Dinvf = grid ? at<float2>(s, s->L.Dinvf) : nullptr;
+  // the paired-single apply covers the control and decay terms; with
+  // Jaynes-Cummings pairs the iterations stay FP64
+  P.ff = grid && s->precision == LB_PREC_F32X2 && s->jp.empty() ? 1 : 0;
+  P.zsA = P.ff ? at<float4>(s, s->L.zsA) : nullptr;
+  P.zsB = P.ff ? at<float4>(s, s->L.zsB) : nullptr;
 }
 
 int ensure_ctab(lb_system* s, cudaStream_t st) {
@@ -931,7 +939,7 @@ int lb_autotune(lb_system* s, void* stream, int32_t probe_steps, int32_t* choice
       LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.gslots), 0, s->L.gslots.bytes, st), "clear grid slots");
       LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.bar), 0, s->L.bar.bytes, st), "clear grid barrier");
       LB_CUDA(cudaEventRecord(a, st), "cudaEventRecord");
-      LB_CUDA(lbk::launch_sweep_grid(s->dp, 0, 1, 0, 0, pst, nullptr, s->M, s->gblocks, s->gsmem, st),
+      LB_CUDA(lbk::launch_sweep_grid(s->dp, 0, 1, 0, 0, pst, nullptr, s->M, s->gblocks, s->gsmem, s->hp.ff, st),
               "forward grid sweep");
       LB_CUDA(cudaEventRecord(b, st), "cudaEventRecord");
       DevStatus d{};
@@ -1211,6 +1219,14 @@ int lb_set_difference_iterations(lb_system* s, int32_t on) {
   return LB_OK;
 }
 
+int lb_set_precision(lb_system* s, int32_t precision) {
+  if (!s) return fail(LB_EINVAL, "null system handle");
+  if (s->ws) return fail(LB_EINVAL, "choose the precision before binding a workspace");
+  if (precision != LB_PREC_F64 && precision != LB_PREC_F32X2) return fail(LB_EINVAL, "unknown precision");
+  s->precision = precision;
+  return LB_OK;
+}
+
 int lb_get_predictor(const lb_system* s, int32_t* restart, int32_t* order) {
   if (!s) return fail(LB_EINVAL, "null system handle");
   if (restart) *restart = s->ws ? s->hp.pred_restart : effective_pred(s);
@@ -1366,7 +1382,7 @@ static int run_forward(lb_system* s, cudaStream_t st, int tape) {
     LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.bar), 0, s->L.bar.bytes, st), "clear grid barrier");
     if (s->gamma1 != 0.0) LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.jpen), 0, s->L.jpen.bytes, st), "clear penalty");
     if (s->timing) LB_CUDA(cudaEventRecord(s->ev[0], st), "cudaEventRecord");
-    LB_CUDA(lbk::launch_sweep_grid(s->dp, 0, 1, tape, 0, s->NT, nullptr, s->M, s->gblocks, s->gsmem, st),
+    LB_CUDA(lbk::launch_sweep_grid(s->dp, 0, 1, tape, 0, s->NT, nullptr, s->M, s->gblocks, s->gsmem, s->hp.ff, st),
             "forward grid sweep");
     if (s->timing) {
       LB_CUDA(cudaEventRecord(s->ev[1], st), "cudaEventRecord");
@@ -1457,7 +1473,7 @@ static int gradient_device(lb_system* s, cudaStream_t st) {
   }
   if (s->timing) LB_CUDA(cudaEventRecord(s->ev[2], st), "cudaEventRecord");
   if (use_grid(s))
-    LB_CUDA(lbk::launch_backward_grid(s->dp, s->gblocks, s->gsmem, st), "backward grid sweep");
+    LB_CUDA(lbk::launch_backward_grid(s->dp, s->gblocks, s->gsmem, s->hp.ff, st), "backward grid sweep");
   else if (s->cluster)
     LB_CUDA(lbk::launch_backward_cluster(s->dp, s->M, s->cc, st), "backward cluster kernel");
   else
@@ -1628,7 +1644,7 @@ static int propagate_impl(lb_system* s, cudaStream_t st, int adjoint, int64_t j0
       if (n_vec > s->M) return fail(LB_EINVAL, "grid sweeps propagate at most M vectors at a time");
       LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.gslots), 0, s->L.gslots.bytes, st), "clear grid slots");
       LB_CUDA(cudaMemsetAsync(at<char>(s, s->L.bar), 0, s->L.bar.bytes, st), "clear grid barrier");
-      LB_CUDA(lbk::launch_sweep_grid(s->dp, adjoint ? 2 : 1, 0, 0, j0, j1, x, n_vec, s->gblocks, s->gsmem, st),
+      LB_CUDA(lbk::launch_sweep_grid(s->dp, adjoint ? 2 : 1, 0, 0, j0, j1, x, n_vec, s->gblocks, s->gsmem, s->hp.ff, st),
               "propagate grid sweep");
     } else if (s->cluster) {
       LB_CUDA(lbk::launch_propagate_cluster(s->dp, adjoint, j0, j1, x, n_vec, s->cc, st), "propagate cluster kernel");

@@ -122,10 +122,31 @@ __device__ __forceinline__ void gput(double2* a, const GEl& g, int V, double2 x)
 // entries of one step of the control table at most: Q factors and the pairs p < q
 constexpr int kMaxCq = LB_MAXQ + LB_MAXQ * (LB_MAXQ - 1) / 2;
 
+// z as a pair of single-precision numbers (hi, lo) with hi + lo = z to about
+// 2^-48 |z| (lb_set_precision): hi is z truncated to 24 significant bits, lo
+// the remaining 29 bits rounded to 24.  |z| below 2^-126 is flushed to zero,
+// and lo is dropped for |z| below 2^-74 (an absolute error under 2^-98).
+// Integer pipe except one conversion and one multiplication by a power of
+// two.
+__device__ __forceinline__ float2 split_f64(double z) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(z);
+  const unsigned sgn = (unsigned)(bits >> 32) & 0x80000000u;
+  const int E = (int)((bits >> 52) & 0x7ff);
+  const int eh = E - 896;  // single-precision exponent field of hi
+  const float hi = __uint_as_float(eh <= 0 ? sgn : (sgn | ((unsigned)min(eh, 254) << 23) |
+                                                    ((unsigned)(bits >> 29) & 0x7fffffu)));
+  const int el = E - 948;  // exponent field of 2^(E - 1075), the weight of the mantissa's last bit
+  const float lo = (eh <= 0 || el <= 0) ? 0.0f
+                                        : __uint2float_rn((unsigned)bits & 0x1fffffffu) *
+                                              __uint_as_float((unsigned)min(el, 254) << 23);
+  return make_float2(hi, sgn ? -lo : lo);
+}
+
 __host__ __device__ inline size_t grid_smem_bytes_impl(int ncoef, int njcoef) {
   return align16(sizeof(GridHdr)) + align16(sizeof(double) * 2 * ncoef) + align16(sizeof(double) * 2 * njcoef) +
          align16(sizeof(float) * 2 * ncoef) + align16(sizeof(float) * 2 * njcoef) + align16(sizeof(float2) * kMaxCq) +
-         align16(sizeof(double) * 4 * 8) + 64;
+         align16(sizeof(float4) * 2 * ncoef) + align16(sizeof(float2) * 2 * njcoef) + align16(sizeof(double) * 4 * 8) +
+         64;
 }
 
 struct GridSmem {
@@ -139,6 +160,15 @@ struct GridSmem {
   float* jff;
   float* jaf;
   float2* ctf;  // this solve's control-table entries in single precision
+  // paired-single tables (lb_set_precision): per level entry m of subsystem
+  // q, this solve's control factors times the ladder factors,
+  // ffu[m] = (b cu[m], a cu[m]) and ffd[m] = (b cd[m], a cd[m]) as (hi, lo)
+  // pairs ((a + i b) = (dt/2) d_q, negated for the adjoint), and the decay
+  // tables jf, ja as pairs
+  float4* ffu;
+  float4* ffd;
+  float2* ffjf;
+  float2* ffja;
   double* red;  // [4][8 warps]
   int* flag;    // [0]: the iteration's decision, [1]: next iteration in single precision
 };
@@ -162,6 +192,12 @@ __device__ GridSmem grid_setup(unsigned char* base, const ProbDev& P, int nstate
   o += align16(sizeof(float) * 2 * P.njcoef);
   S.ctf = reinterpret_cast<float2*>(base + o);
   o += align16(sizeof(float2) * kMaxCq);
+  S.ffu = reinterpret_cast<float4*>(base + o);
+  S.ffd = S.ffu + P.ncoef;
+  o += align16(sizeof(float4) * 2 * P.ncoef);
+  S.ffjf = reinterpret_cast<float2*>(base + o);
+  S.ffja = S.ffjf + P.njcoef;
+  o += align16(sizeof(float2) * 2 * P.njcoef);
   S.red = reinterpret_cast<double*>(base + o);
   o += align16(sizeof(double) * 4 * 8);
   S.flag = reinterpret_cast<int*>(base + o);
@@ -188,6 +224,8 @@ __device__ GridSmem grid_setup(unsigned char* base, const ProbDev& P, int nstate
     S.ja[i] = P.ja[i];
     S.jff[i] = (float)P.jf[i];
     S.jaf[i] = (float)P.ja[i];
+    S.ffjf[i] = split_f64(P.jf[i]);
+    S.ffja[i] = split_f64(P.ja[i]);
   }
   __syncthreads();
   return S;
@@ -497,6 +535,109 @@ __device__ __forceinline__ void offdiag_acc_f(float& ar, float& ai, const float2
   }
 }
 
+// ---------------------------------------------------------------------------
+// Paired-single apply (lb_set_precision LB_PREC_F32X2).  A value is a pair
+// (hi, lo) of single-precision numbers; acc += (ch + cl)(xh + xl) forms the
+// product ch xh with its exact rounding error (one FMA), adds the cross terms
+// ch xl + cl xh to that error (cl xl, below 2^-48 of the product, is
+// dropped), and adds ch xh to the running hi part with its exact rounding
+// error (two-sum), which goes to the lo part with the product's error.  The
+// _rn intrinsics keep the compiler from contracting these steps.
+__device__ __forceinline__ void ffmac(float& sh, float& sl, float ch, float cl, float xh, float xl) {
+  const float p = __fmul_rn(ch, xh);
+  float e = __fmaf_rn(ch, xh, -p);
+  e = __fmaf_rn(ch, xl, e);
+  e = __fmaf_rn(cl, xh, e);
+  const float sum = __fadd_rn(sh, p);
+  const float bv = __fsub_rn(sum, sh);
+  const float t = __fadd_rn(__fsub_rn(sh, __fsub_rn(sum, bv)), __fsub_rn(p, bv));
+  sh = sum;
+  sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+__device__ __forceinline__ float4 split4(double2 z) {
+  const float2 a = split_f64(z.x), b = split_f64(z.y);
+  return make_float4(a.x, a.y, b.x, b.y);
+}
+// entry (k, l) of a packed Hermitian split iterate (x_hi, x_lo, y_hi, y_lo)
+__device__ __forceinline__ float4 ldpk4(const float4* p, int k, int l) {
+  const bool lo = k > l;
+  const int a = lo ? l : k, c = lo ? k : l;
+  const float4* q = p + ((c * (c + 1)) >> 1) + a;
+  float4 x = kNbL2 ? __ldcg(q) : *q;
+  const unsigned f = lo ? 0x80000000u : 0u;
+  x.z = __uint_as_float(__float_as_uint(x.z) ^ f);
+  x.w = __uint_as_float(__float_as_uint(x.w) ^ f);
+  return x;
+}
+
+// offdiag_acc on a split iterate in paired single precision: acc = (re hi,
+// re lo, im hi, im lo) of the control and decay terms (the same sums as
+// offdiag_acc, written out term by term with the factors of this solve's
+// tables S.ffu, S.ffd, S.ffjf / S.ffja).  No Jaynes-Cummings pairs.
+template <bool ADJ, bool PK, int QN>
+__device__ __forceinline__ void offdiag_acc_ff(float (&acc)[4], const float4* __restrict__ x, int v, uint32_t kd,
+                                               uint32_t ld, const Hdr& H, const GridSmem& S, int k, int l) {
+  const int N = H.N;
+  auto nb = [&](int dk, int dl) -> float4 {
+    if constexpr (PK) {
+      return ldpk4(x, k + dk, l + dl);
+    } else {
+      const float4* q = x + v + dk + dl * N;
+      return kNbL2 ? __ldcg(q) : *q;
+    }
+  };
+  auto sub = [&](int q) {
+    const int n = H.lev[q], s = H.stride[q], co = H.coff[q];
+    const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
+    // c1 = cu[nk], c2 = cd[nl], c3 = cd[nk], c4 = cu[nl] times (b, a)
+    const float4 f1 = S.ffu[co + nk], f2 = S.ffd[co + nl], f3 = S.ffd[co + nk], f4 = S.ffu[co + nl];
+    const float4 x1 = nb(nk + 1 < n ? s : 0, 0);
+    const float4 x2 = nb(0, nl > 0 ? -s : 0);
+    const float4 x3 = nb(nk > 0 ? -s : 0, 0);
+    const float4 x4 = nb(0, nl + 1 < n ? s : 0);
+    // re += b (c1 x1 - c2 x2 - c3 x3 + c4 x4)_re + a (c1 x1 - c2 x2 + c3 x3 - c4 x4)_im
+    ffmac(acc[0], acc[1], f1.x, f1.y, x1.x, x1.y);
+    ffmac(acc[0], acc[1], -f2.x, -f2.y, x2.x, x2.y);
+    ffmac(acc[0], acc[1], -f3.x, -f3.y, x3.x, x3.y);
+    ffmac(acc[0], acc[1], f4.x, f4.y, x4.x, x4.y);
+    ffmac(acc[0], acc[1], f1.z, f1.w, x1.z, x1.w);
+    ffmac(acc[0], acc[1], -f2.z, -f2.w, x2.z, x2.w);
+    ffmac(acc[0], acc[1], f3.z, f3.w, x3.z, x3.w);
+    ffmac(acc[0], acc[1], -f4.z, -f4.w, x4.z, x4.w);
+    // im += b (c1 x1 - c2 x2 - c3 x3 + c4 x4)_im - a (c1 x1 - c2 x2 + c3 x3 - c4 x4)_re
+    ffmac(acc[2], acc[3], f1.x, f1.y, x1.z, x1.w);
+    ffmac(acc[2], acc[3], -f2.x, -f2.y, x2.z, x2.w);
+    ffmac(acc[2], acc[3], -f3.x, -f3.y, x3.z, x3.w);
+    ffmac(acc[2], acc[3], f4.x, f4.y, x4.z, x4.w);
+    ffmac(acc[2], acc[3], -f1.z, -f1.w, x1.x, x1.y);
+    ffmac(acc[2], acc[3], f2.z, f2.w, x2.x, x2.y);
+    ffmac(acc[2], acc[3], -f3.z, -f3.w, x3.x, x3.y);
+    ffmac(acc[2], acc[3], f4.z, f4.w, x4.x, x4.y);
+    if ((H.jon >> q) & 1u) {
+      const int jo = H.joff[q] + nk * n + nl;
+      float2 cj;
+      float4 x5;
+      if (!ADJ) {
+        cj = S.ffjf[jo];
+        const int d = (nk + 1 < n && nl + 1 < n) ? s : 0;
+        x5 = nb(d, d);
+      } else {
+        cj = S.ffja[jo];
+        const int d = (nk > 0 && nl > 0) ? s : 0;
+        x5 = nb(-d, -d);
+      }
+      ffmac(acc[0], acc[1], cj.x, cj.y, x5.x, x5.y);
+      ffmac(acc[2], acc[3], cj.x, cj.y, x5.z, x5.w);
+    }
+  };
+  if constexpr (QN > 0) {
+#pragma unroll
+    for (int q = 0; q < QN; ++q) sub(q);
+  } else {
+    for (int q = 0; q < H.Q; ++q) sub(q);
+  }
+}
+
 // One difference iteration over a block's chunk [e0, e1): from the change dc
 // of the last iteration (single precision), the new iterate zn = zc + its
 // change dn, the FP64 correction in cring (the predictor's ring slot, when
@@ -506,7 +647,8 @@ template <bool ADJ, int QN>
 __device__ __forceinline__ void grid_diff_pass(const ProbDev& P, const GridSmem& S, long long e0, long long e1,
                                             const float2* __restrict__ dc, float2* __restrict__ dn,
                                             const double2* __restrict__ zc, double2* __restrict__ zn,
-                                            double2* __restrict__ cring, unsigned long long* bank) {
+                                            float4* __restrict__ zsn, double2* __restrict__ cring,
+                                            unsigned long long* bank) {
   const GridHdr& G = *S.g;
   const Hdr& H = G.h;
   StateMax sm;
@@ -532,7 +674,9 @@ __device__ __forceinline__ void grid_diff_pass(const ProbDev& P, const GridSmem&
     const float ex = fmaf(df.x, fr, -dfi * fi), ey = fmaf(df.x, fi, dfi * fr);
     const double ddx = f32_to_f64(ex), ddy = f32_to_f64(ey);
     const double2 zo = __ldcg(zc + o);
-    zn[o] = make_double2(zo.x + ddx, zo.y + ddy);
+    const double2 z = make_double2(zo.x + ddx, zo.y + ddy);
+    zn[o] = z;
+    if (zsn) zsn[o] = split4(z);
     dn[o] = make_float2(ex, ey);
     sm.add(b, umax64(abs_bits(ddx), abs_bits(ddy)), bank);
   }
@@ -546,10 +690,11 @@ __device__ __forceinline__ void grid_diff_pass(const ProbDev& P, const GridSmem&
 // returned z), the new iterate zn, its single-precision change dnew (for a
 // difference iteration next) and the per-state maxima of the change pushed
 // to `bank`.  QN: the subsystem count at compile time (0: H.Q at run time).
-template <bool ADJ, int QN>
+template <bool ADJ, int QN, bool FF>
 __device__ __forceinline__ void grid_full_pass(const ProbDev& P, const GridSmem& S, long long e0, long long e1,
                                             const double2* __restrict__ rhs, const double2* __restrict__ ct,
                                             const double2* __restrict__ zc, double2* __restrict__ zn,
+                                            const float4* __restrict__ zsc, float4* __restrict__ zsn,
                                             double2* __restrict__ cring, float2* __restrict__ dnew, bool neumann,
                                             double hh, unsigned long long* bank) {
   const GridHdr& G = *S.g;
@@ -565,10 +710,20 @@ __device__ __forceinline__ void grid_full_pass(const ProbDev& P, const GridSmem&
     const double2 r = rhs[o];
     double cr = 0.0, ci = 0.0;
     const uint32_t kd = __ldg(P.digits + g.k), ld = __ldg(P.digits + g.l);
-    if (G.herm)
-      offdiag_acc<ADJ, kNbL2, true, QN>(cr, ci, xs, v, kd, ld, H, T, ct, g.k, g.l);
-    else
-      offdiag_acc<ADJ, kNbL2, false, QN>(cr, ci, xs, v, kd, ld, H, T, ct);
+    if constexpr (FF) {
+      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      if (G.herm)
+        offdiag_acc_ff<ADJ, true, QN>(acc, zsc + (size_t)b * G.Vh, v, kd, ld, H, S, g.k, g.l);
+      else
+        offdiag_acc_ff<ADJ, false, QN>(acc, zsc + (size_t)b * G.Vh, v, kd, ld, H, S, g.k, g.l);
+      cr = f32_to_f64(acc[0]) + f32_to_f64(acc[1]);
+      ci = f32_to_f64(acc[2]) + f32_to_f64(acc[3]);
+    } else {
+      if (G.herm)
+        offdiag_acc<ADJ, kNbL2, true, QN>(cr, ci, xs, v, kd, ld, H, T, ct, g.k, g.l);
+      else
+        offdiag_acc<ADJ, kNbL2, false, QN>(cr, ci, xs, v, kd, ld, H, T, ct);
+    }
     if (cring) cring[o] = make_double2(cr, ci);
     const double ar = r.x + cr, ai = r.y + ci;
     const double2 zo = __ldcg(xs + g.i);
@@ -585,6 +740,7 @@ __device__ __forceinline__ void grid_full_pass(const ProbDev& P, const GridSmem&
       z.y = ai + fma(dr, zo.y, di * zo.x);
     }
     zn[o] = z;
+    if constexpr (FF) zsn[o] = split4(z);
     const double ddx = z.x - zo.x, ddy = z.y - zo.y;
     if (dnew) dnew[o] = make_float2(f64_to_f32_trunc(ddx), f64_to_f32_trunc(ddy));
     sm.add(b, umax64(abs_bits(ddx), abs_bits(ddy)), bank);
@@ -592,7 +748,7 @@ __device__ __forceinline__ void grid_full_pass(const ProbDev& P, const GridSmem&
   sm.push(bank, reinterpret_cast<unsigned long long*>(S.red));
 }
 
-template <bool ADJ>
+template <bool ADJ, bool FF>
 __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __restrict__ rhs,
                           const double2* __restrict__ ct, double fac, long long& it_global, long long& solve,
                           int& ndiff, double2** zout, GridHist hist = GridHist(), double penw = 0.0) {
@@ -610,6 +766,18 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
   // difference iterations: Jacobi only; this solve's control factors in single precision
   const bool dok = P.diffit && !neumann && P.dfA != nullptr;
   if (dok && (int)threadIdx.x < H.cq) S.ctf[threadIdx.x] = make_float2((float)ct[threadIdx.x].x, (float)ct[threadIdx.x].y);
+  // paired-single apply: this solve's factor tables (the adjoint's with -a, -b)
+  constexpr bool ff = FF;
+  if (ff)
+    for (int m = threadIdx.x; m < P.ncoef; m += blockDim.x) {
+      int q = 0;
+      while (q + 1 < H.Q && H.coff[q + 1] <= m) ++q;
+      const double a = ADJ ? -ct[q].x : ct[q].x, b = ADJ ? -ct[q].y : ct[q].y;
+      const float2 bu = split_f64(b * S.cu[m]), au = split_f64(a * S.cu[m]);
+      const float2 bd = split_f64(b * S.cd[m]), ad = split_f64(a * S.cd[m]);
+      S.ffu[m] = make_float4(bu.x, bu.y, au.x, au.y);
+      S.ffd[m] = make_float4(bd.x, bd.y, ad.x, ad.y);
+    }
   ndiff = 0;
   // z_0 = (I - dt/2 D)^-1 rhs (Jacobi) or rhs (Neumann); per-state max |rhs|
   {
@@ -646,6 +814,7 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
         z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
       }
       P.zA[o] = z0;
+      if (ff) P.zsA[o] = split4(z0);
       sm.add(b, umax64(abs_bits(r.x), abs_bits(r.y)), qbank);
     }
     sm.push(qbank, red);
@@ -698,26 +867,37 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
       ++ndiff;
       const float2* dcur = (it & 1) ? P.dfB : P.dfA;
       float2* dnew = (it & 1) ? P.dfA : P.dfB;
+      float4* zsdn = ff ? ((it & 1) ? P.zsA : P.zsB) : nullptr;
       double2* cring = hist.ring ? hist.ring + (size_t)hist.slot * ((size_t)M * G.Vh) : nullptr;
       switch (H.Q) {
-        case 1: grid_diff_pass<ADJ, 1>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
-        case 2: grid_diff_pass<ADJ, 2>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
-        case 3: grid_diff_pass<ADJ, 3>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
-        case 4: grid_diff_pass<ADJ, 4>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
-        case 5: grid_diff_pass<ADJ, 5>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
-        case 6: grid_diff_pass<ADJ, 6>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
-        case 7: grid_diff_pass<ADJ, 7>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
-        default: grid_diff_pass<ADJ, 8>(P, S, e0, e1, dcur, dnew, zc, zn, cring, bank); break;
+        case 1: grid_diff_pass<ADJ, 1>(P, S, e0, e1, dcur, dnew, zc, zn, zsdn, cring, bank); break;
+        case 2: grid_diff_pass<ADJ, 2>(P, S, e0, e1, dcur, dnew, zc, zn, zsdn, cring, bank); break;
+        case 3: grid_diff_pass<ADJ, 3>(P, S, e0, e1, dcur, dnew, zc, zn, zsdn, cring, bank); break;
+        case 4: grid_diff_pass<ADJ, 4>(P, S, e0, e1, dcur, dnew, zc, zn, zsdn, cring, bank); break;
+        case 5: grid_diff_pass<ADJ, 5>(P, S, e0, e1, dcur, dnew, zc, zn, zsdn, cring, bank); break;
+        case 6: grid_diff_pass<ADJ, 6>(P, S, e0, e1, dcur, dnew, zc, zn, zsdn, cring, bank); break;
+        case 7: grid_diff_pass<ADJ, 7>(P, S, e0, e1, dcur, dnew, zc, zn, zsdn, cring, bank); break;
+        default: grid_diff_pass<ADJ, 8>(P, S, e0, e1, dcur, dnew, zc, zn, zsdn, cring, bank); break;
       }
     } else {
       double2* cring = hist.ring ? hist.ring + (size_t)hist.slot * ((size_t)M * G.Vh) : nullptr;
       float2* dnew = dok ? ((it & 1) ? P.dfA : P.dfB) : nullptr;
       // the subsystem counts of the large workloads (4 and 6) get an
       // unrolled subsystem loop; other counts run the general loop
-      switch (H.Q) {
-        case 4: grid_full_pass<ADJ, 4>(P, S, e0, e1, rhs, ct, zc, zn, cring, dnew, neumann, hh, bank); break;
-        case 6: grid_full_pass<ADJ, 6>(P, S, e0, e1, rhs, ct, zc, zn, cring, dnew, neumann, hh, bank); break;
-        default: grid_full_pass<ADJ, 0>(P, S, e0, e1, rhs, ct, zc, zn, cring, dnew, neumann, hh, bank); break;
+      if constexpr (ff) {
+        const float4* zsc = (it & 1) ? P.zsB : P.zsA;
+        float4* zsn = (it & 1) ? P.zsA : P.zsB;
+        switch (H.Q) {
+          case 4: grid_full_pass<ADJ, 4, true>(P, S, e0, e1, rhs, ct, zc, zn, zsc, zsn, cring, dnew, neumann, hh, bank); break;
+          case 6: grid_full_pass<ADJ, 6, true>(P, S, e0, e1, rhs, ct, zc, zn, zsc, zsn, cring, dnew, neumann, hh, bank); break;
+          default: grid_full_pass<ADJ, 0, true>(P, S, e0, e1, rhs, ct, zc, zn, zsc, zsn, cring, dnew, neumann, hh, bank); break;
+        }
+      } else {
+        switch (H.Q) {
+          case 4: grid_full_pass<ADJ, 4, false>(P, S, e0, e1, rhs, ct, zc, zn, nullptr, nullptr, cring, dnew, neumann, hh, bank); break;
+          case 6: grid_full_pass<ADJ, 6, false>(P, S, e0, e1, rhs, ct, zc, zn, nullptr, nullptr, cring, dnew, neumann, hh, bank); break;
+          default: grid_full_pass<ADJ, 0, false>(P, S, e0, e1, rhs, ct, zc, zn, nullptr, nullptr, cring, dnew, neumann, hh, bank); break;
+        }
       }
     }
     if (!grid_sync(P.bar, gridDim.x, P.spin_limit > 0 ? P.spin_limit : kSpinLimit)) return -3;
@@ -773,6 +953,9 @@ __device__ void grid_fail(const ProbDev& P, int code, int step) {
 
 // mode 0: forward sweep on P.qT (from P.q0 if init), checkpoints if tape
 // mode 1: forward steps j0..j1-1 in place on x; mode 2: adjoint steps j1-1..j0 in place on x
+// FF: the FP64 iterations apply O in paired single precision (P.ff); the
+// two variants are separate kernels so that each has its own registers
+template <bool FF>
 __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* __restrict__ pp, int mode, int init,
                                                              int tape, int j0, int j1, double2* __restrict__ x,
                                                              int nstates) {
@@ -821,9 +1004,9 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
     }
     double2* z = nullptr;
     int nd = 0;
-    const int it = mode == 2 ? grid_solve<true>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve,
+    const int it = mode == 2 ? grid_solve<true, FF>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve,
                                                 nd, &z)
-                             : grid_solve<false>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve,
+                             : grid_solve<false, FF>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve,
                                                  nd, &z, pred ? hist : GridHist(), penal ? P.pen[j] : 0.0);
     if (it < 0) {
       grid_fail(P, it, j);
@@ -863,6 +1046,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
 
 // backward sweep over all states: recompute each checkpoint segment, then the
 // adjoint steps with the gradient pieces summed over states and blocks
+template <bool FF>
 __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev* __restrict__ pp) {
   extern __shared__ __align__(16) unsigned char smem[];
   const ProbDev& P = *pp;
@@ -926,7 +1110,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
         double2* z = nullptr;
         if (fpred && j % R == 0) fhist.restart();  // every checkpoint is a restart point
         int nd = 0;
-        const int it = grid_solve<false>(P, S, P.qf, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, nd,
+        const int it = grid_solve<false, FF>(P, S, P.qf, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve, nd,
                                          &z, fpred ? fhist : GridHist());
         if (it < 0) {
           grid_fail(P, it, j);
@@ -957,7 +1141,7 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
       double2* zh = nullptr;
       int nd = 0;
       const int it =
-          grid_solve<true>(P, S, P.lam, ct, stop_factor(P, j), itg, nsolve, nd, &zh, apred ? ahist : GridHist());
+          grid_solve<true, FF>(P, S, P.lam, ct, stop_factor(P, j), itg, nsolve, nd, &zh, apred ? ahist : GridHist());
       if (it < 0) {
         grid_fail(P, it, j);
         failed = true;
@@ -1144,30 +1328,34 @@ int grid_blocks_max(size_t smem) {
   int dev = 0, nsm = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  if (cudaFuncSetAttribute(k_sweep_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-  if (cudaFuncSetAttribute(k_backward_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-    return 0;
-  int a = 0, b = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_sweep_grid, kGridThreads, smem) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_backward_grid, kGridThreads, smem) != cudaSuccess) return 0;
-  per = a < b ? a : b;
+  const void* kernels[] = {(const void*)k_sweep_grid<false>, (const void*)k_backward_grid<false>,
+                           (const void*)k_sweep_grid<true>, (const void*)k_backward_grid<true>};
+  per = 1 << 30;
+  for (const void* k : kernels) {
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int a = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k, kGridThreads, smem) != cudaSuccess) return 0;
+    per = a < per ? a : per;
+  }
   int n = nsm * per;
   return n < kMaxGridBlocks ? n : kMaxGridBlocks;
 }
 
 cudaError_t launch_sweep_grid(const ProbDev* d_prob, int mode, int init_from_q0, int tape, int64_t j0, int64_t j1,
-                              double2* x, int nstates, int nblocks, size_t smem, cudaStream_t s) {
+                              double2* x, int nstates, int nblocks, size_t smem, int ff, cudaStream_t s) {
   int m = mode, in = init_from_q0, tp = tape, a = (int)j0, b = (int)j1, ns = nstates;
   const ProbDev* p = d_prob;
   double2* xx = x;
   void* args[] = {(void*)&p, (void*)&m, (void*)&in, (void*)&tp, (void*)&a, (void*)&b, (void*)&xx, (void*)&ns};
-  return cudaLaunchCooperativeKernel((const void*)k_sweep_grid, dim3(nblocks), dim3(kGridThreads), args, smem, s);
+  const void* k = ff ? (const void*)k_sweep_grid<true> : (const void*)k_sweep_grid<false>;
+  return cudaLaunchCooperativeKernel(k, dim3(nblocks), dim3(kGridThreads), args, smem, s);
 }
 
-cudaError_t launch_backward_grid(const ProbDev* d_prob, int nblocks, size_t smem, cudaStream_t s) {
+cudaError_t launch_backward_grid(const ProbDev* d_prob, int nblocks, size_t smem, int ff, cudaStream_t s) {
   const ProbDev* p = d_prob;
   void* args[] = {(void*)&p};
-  return cudaLaunchCooperativeKernel((const void*)k_backward_grid, dim3(nblocks), dim3(kGridThreads), args, smem, s);
+  const void* k = ff ? (const void*)k_backward_grid<true> : (const void*)k_backward_grid<false>;
+  return cudaLaunchCooperativeKernel(k, dim3(nblocks), dim3(kGridThreads), args, smem, s);
 }
 
 cudaError_t launch_objective_states(const ProbDev* d_prob, int M, cudaStream_t s) {

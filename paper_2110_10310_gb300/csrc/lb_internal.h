@@ -116,6 +116,10 @@ struct ProbDev {
   float2* dfA;               // [M*V] grid sweeps: single-precision differences of successive iterates
   float2* dfB;
   float2* Dinvf;             // [V] grid sweeps: (I - dt/2 D)^-1 in single precision
+  int32_t ff;                // grid sweeps: FP64 iterations apply O in single-precision pairs (lb_set_precision)
+  int32_t pad2;
+  float4* zsA;               // [M*V] the iterates zA / zB split into single-precision pairs (x_hi, x_lo, y_hi, y_lo)
+  float4* zsB;
 };
 
 // one work item of a resident launch: (problem, state)
@@ -174,8 +178,8 @@ size_t grid_smem_bytes(int ncoef, int njcoef);
 // mode 0: forward over [j0, j1) on P.qT (initialised from P.q0 when init_from_q0), checkpoints when tape;
 // mode 1: forward over [j0, j1) in place on x; mode 2: adjoint steps j1-1..j0 in place on x
 cudaError_t launch_sweep_grid(const ProbDev* d_prob, int mode, int init_from_q0, int tape, int64_t j0, int64_t j1,
-                              double2* x, int nstates, int nblocks, size_t smem, cudaStream_t s);
-cudaError_t launch_backward_grid(const ProbDev* d_prob, int nblocks, size_t smem, cudaStream_t s);
+                              double2* x, int nstates, int nblocks, size_t smem, int ff, cudaStream_t s);
+cudaError_t launch_backward_grid(const ProbDev* d_prob, int nblocks, size_t smem, int ff, cudaStream_t s);
 
 // cluster-split sweeps for small states: one cluster of C CTAs per state,
 // 2Q lanes per element, or 4Q with the component split (Q <= 4,

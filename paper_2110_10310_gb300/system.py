@@ -62,7 +62,7 @@ class LindbladSystem:
     def __init__(self, problem, *, solver: int = L.LB_SOLVER_AUTO, rtol: float = 1e-15, max_iter: int = 200,
                  ckpt_every: int | None = None, sweep: int = L.LB_SWEEP_AUTO, symmetry: int = L.LB_SYM_HERMITIAN,
                  predictor: int = L.LB_PRED_AUTO, pred_order: int = 0, pairing: int = 1,
-                 difference_iterations: int = 1, device=None, stream=None):
+                 difference_iterations: int = 1, precision: int = L.LB_PREC_F64, device=None, stream=None):
         self.lib = L.load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         sysm = problem.system
@@ -129,6 +129,7 @@ class LindbladSystem:
         L.check(self.lib.lb_set_predictor(h, int(predictor), int(pred_order)))
         L.check(self.lib.lb_set_pairing(h, int(pairing)))
         L.check(self.lib.lb_set_difference_iterations(h, int(difference_iterations)))
+        L.check(self.lib.lb_set_precision(h, int(precision)))
         nbytes = c_size_t()
         L.check(self.lib.lb_workspace_bytes(h, byref(nbytes)))
         self.workspace_bytes = int(nbytes.value)

@@ -409,6 +409,55 @@ def test_difference_iterations_match_oracle_and_fp64_iterations(levels, K, herm,
     assert _rel(g, g0) < 1e-12
 
 
+@pytest.mark.parametrize("levels,K,herm,objective", [((3, 3), 7, True, "frob"), ((2, 3), 0, False, "trace"),
+                                                    ((3, 2, 2), 10, True, "trace"), ((2, 2, 2, 2), 5, False, "frob")])
+def test_paired_single_apply_matches_oracle_and_fp64(levels, K, herm, objective):
+    """lb_set_precision(LB_PREC_F32X2): the grid sweeps' FP64 iterations apply
+    O in pairs of single-precision numbers.  States and objective within
+    1e-10 of the oracle, gradient within 1e-9, and within 1e-11 of the FP64
+    apply (the two differ by a few FP64 roundings of z per step); with
+    checkpoints the recompute repeats the forward sweep bit for bit (the
+    same paired-single iterates), so K and the full tape agree to rounding
+    and two K give the same gradient."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(421, levels=levels, n_states=3, n_steps=40, T_ns=1.2, amp=0.1, ckpt_every=K,
+                         hermitian=herm, objective=objective)
+    kw = dict(sweep=L.LB_SWEEP_GRID, precision=L.LB_PREC_F32X2)
+    s, g = _check_problem(p, **kw)
+    assert s.stats()["sweep"] == "grid"
+    G1, rho1 = s.forward(want_states=True)
+    s0 = _sys(p, sweep=L.LB_SWEEP_GRID)
+    G0, rho0 = s0.forward(want_states=True)
+    _, g0 = s0.gradient()
+    assert abs(G1 - G0) <= 1e-11 * abs(G0)
+    assert _rel(rho1.cpu().numpy(), rho0.cpu().numpy()) < 1e-11
+    assert _rel(g, g0) < 1e-10
+    if K > 0:
+        Ga, ga = _sys(p, ckpt_every=K, predictor=L.LB_PRED_NONE, **kw).gradient()
+        Gb, gb = _sys(p, ckpt_every=1, predictor=L.LB_PRED_NONE, **kw).gradient()
+        assert Ga == Gb and np.array_equal(ga, gb)
+
+
+def test_paired_single_apply_keeps_fp64_with_couplings_and_full_size():
+    """Systems with Jaynes-Cummings couplings run the FP64 apply under
+    LB_PREC_F32X2 (bitwise the default); the paired-single apply on the full
+    six-qutrit state (vec 531441, 2 states, 12 steps) agrees with the FP64
+    apply to 1e-11."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(422, levels=(3, 2, 2), n_states=2, n_steps=30, T_ns=0.6, amp=0.1, jc=0.05)
+    a = _sys(p, sweep=L.LB_SWEEP_GRID, precision=L.LB_PREC_F32X2).gradient()
+    b = _sys(p, sweep=L.LB_SWEEP_GRID).gradient()
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    q = W.prefix(W.config5(n_states=2), 12)
+    q.ckpt_every = 6
+    Gf, gf = _sys(q, precision=L.LB_PREC_F32X2).gradient()
+    Gd, gd = _sys(q).gradient()
+    assert abs(Gf - Gd) <= 1e-11 * abs(Gd)
+    assert _rel(gf, gd) < 1e-10
+
+
 def test_difference_iterations_keep_recompute_bitwise():
     """The decision to take a difference iteration depends only on the
     iterates, so a recompute repeats it: without a forward predictor the

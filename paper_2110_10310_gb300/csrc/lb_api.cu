@@ -49,7 +49,7 @@ struct Region {
 struct Layout {
   Region prob, status, items, sysp, cu, cd, jf, ja, digits, D, Dinv, alpha, carriers, ctab, q0, tar, wgt, qT, ckpt, seg,
       gproj, gsum, sfac, pen, qb, jpen, mpart, pmap, Ginv, hgp, hgm, fgp, fgm, dfA, dfB, Dinvf, zsA, zsB, J, G, grad, gateV, emap, efull, zA, zB, lam, qf, partials, gslots, bar, hist, histf,
-      hmap;
+      hkl;
   size_t total = 0;
 };
 
@@ -353,7 +353,7 @@ Layout make_layout(const lb_system* s) {
   take(L.Dinvf, grid ? sizeof(float2) * V : 0);
   take(L.zsA, grid && s->precision == LB_PREC_F32X2 ? sizeof(float4) * M * V : 0);
   take(L.zsB, grid && s->precision == LB_PREC_F32X2 ? sizeof(float4) * M * V : 0);
-  take(L.hmap, sizeof(int32_t) * (size_t)s->N * (s->N + 1) / 2);
+  take(L.hkl, sizeof(uint32_t) * (size_t)s->N * (s->N + 1) / 2);
   take(L.pmap, sizeof(int32_t) * (size_t)s->Mu);
   L.total = off;
   return L;
@@ -380,15 +380,15 @@ int order_after_uploads(lb_system* s, cudaStream_t stream) {
   return LB_OK;
 }
 
-// vec indices k + N l with k <= l, column by column: the element order of
-// the Hermitian sweeps (entries below the diagonal are written as mirrors).
+// the elements k <= l, column by column, as k | l << 16 (N <= 2^15): the
+// element order of the grid sweeps under the Hermitian symmetry.
 // The pageable source is staged before cudaMemcpyAsync returns.
 int upload_symmetry_map(lb_system* s, cudaStream_t st) {
-  std::vector<int32_t> hmap;
-  hmap.reserve((size_t)s->N * (s->N + 1) / 2);
+  std::vector<uint32_t> hkl;
+  hkl.reserve((size_t)s->N * (s->N + 1) / 2);
   for (int l = 0; l < s->N; ++l)
-    for (int k = 0; k <= l; ++k) hmap.push_back(k + s->N * l);
-  LB_CUDA(cudaMemcpyAsync(at<int32_t>(s, s->L.hmap), hmap.data(), sizeof(int32_t) * hmap.size(),
+    for (int k = 0; k <= l; ++k) hkl.push_back((uint32_t)k | ((uint32_t)l << 16));
+  LB_CUDA(cudaMemcpyAsync(at<uint32_t>(s, s->L.hkl), hkl.data(), sizeof(uint32_t) * hkl.size(),
                           cudaMemcpyHostToDevice, st),
           "upload symmetry map");
   return LB_OK;
@@ -672,7 +672,7 @@ void fill_prob(lb_system* s) {
     P.gslots = at<unsigned long long>(s, s->L.gslots);
     P.bar = at<GridBar>(s, s->L.bar);
   }
-  P.hmap = at<int32_t>(s, s->L.hmap);
+  P.hkl = at<uint32_t>(s, s->L.hkl);
   P.herm = use_symmetry(s) ? 1 : 0;
   P.hist = at<double2>(s, s->L.hist);
   P.histf = at<double2>(s, s->L.histf);

@@ -81,7 +81,7 @@ struct GridHdr {
 // its place in the state's slab of the sweep's own buffers (iterates,
 // adjoint, recomputed state, checkpoints, segment tape, predictor rings).
 // Without the symmetry the slab is the vec layout (i = v).  With it the loops
-// visit k <= l only (v from the table hmap) and the slabs hold those entries
+// visit k <= l only ((k, l) from the table hkl) and the slabs hold those entries
 // packed, column by column (i = l (l + 1)/2 + k); vm is then the mirror index
 // l + N k of an off-diagonal element in the vec layout of the inputs and
 // outputs (q0, targets, final states), whose value is the conjugate (-1 for
@@ -89,26 +89,47 @@ struct GridHdr {
 struct GEl {
   int b, v, vm, i, k, l;
 };
-__device__ __forceinline__ GEl gel(const GridHdr& G, const int32_t* __restrict__ hmap, long long e) {
+// element i of state b's slab
+__device__ __forceinline__ GEl gel_at(const GridHdr& G, const uint32_t* __restrict__ hkl, int b, int i) {
   GEl r;
   const int N = G.h.N;
+  r.b = b;
+  r.i = i;
   if (!G.herm) {
-    r.b = (int)(e / G.h.V);
-    r.v = (int)(e - (long long)r.b * G.h.V);
-    r.i = r.v;
+    r.v = i;
     r.vm = -1;
-    r.k = r.v % N;
-    r.l = r.v / N;
+    r.k = i % N;
+    r.l = i / N;
     return r;
   }
-  r.b = (int)(e / G.Vh);
-  r.i = (int)(e - (long long)r.b * G.Vh);
-  r.v = __ldg(hmap + r.i);
-  r.k = r.v % N;
-  r.l = r.v / N;
+  const uint32_t t = __ldg(hkl + i);
+  r.k = (int)(t & 0xffffu);
+  r.l = (int)(t >> 16);
+  r.v = r.k + N * r.l;
   r.vm = r.k != r.l ? r.l + N * r.k : -1;
   return r;
 }
+
+// A thread's walk over its elements e = e0 + threadIdx.x, + blockDim.x, ...
+// of a block's chunk [e0, e1) of the flattened [M][Vh] range, keeping the
+// state b and slab index i of e (one division at the start).
+struct GIter {
+  long long e;
+  int b, i;
+  __device__ GIter(const GridHdr& G, long long e_start) : e(e_start) {
+    b = (int)(e / G.Vh);
+    i = (int)(e - (long long)b * G.Vh);
+  }
+  __device__ __forceinline__ void next(const GridHdr& G, int step) {
+    e += step;
+    i += step;
+    while (i >= G.Vh) {
+      i -= G.Vh;
+      ++b;
+    }
+  }
+};
+
 // offset of element g in slab `slab` (state b's, or a checkpoint's) of a sweep buffer
 __device__ __forceinline__ size_t gslab(const GridHdr& G, const GEl& g, size_t slab) {
   return slab * (size_t)G.Vh + g.i;
@@ -145,8 +166,8 @@ __device__ __forceinline__ float2 split_f64(double z) {
 __host__ __device__ inline size_t grid_smem_bytes_impl(int ncoef, int njcoef) {
   return align16(sizeof(GridHdr)) + align16(sizeof(double) * 2 * ncoef) + align16(sizeof(double) * 2 * njcoef) +
          align16(sizeof(float) * 2 * ncoef) + align16(sizeof(float) * 2 * njcoef) + align16(sizeof(float2) * kMaxCq) +
-         align16(sizeof(float4) * 2 * ncoef) + align16(sizeof(float2) * 2 * njcoef) + align16(sizeof(double) * 4 * 8) +
-         64;
+         align16(sizeof(float2) * 2 * ncoef) + align16(sizeof(float2) * 2 * njcoef) + align16(sizeof(float4) * LB_MAXQ) +
+         align16(sizeof(double) * 4 * 8) + 64;
 }
 
 struct GridSmem {
@@ -160,15 +181,15 @@ struct GridSmem {
   float* jff;
   float* jaf;
   float2* ctf;  // this solve's control-table entries in single precision
-  // paired-single tables (lb_set_precision): per level entry m of subsystem
-  // q, this solve's control factors times the ladder factors,
-  // ffu[m] = (b cu[m], a cu[m]) and ffd[m] = (b cd[m], a cd[m]) as (hi, lo)
-  // pairs ((a + i b) = (dt/2) d_q, negated for the adjoint), and the decay
-  // tables jf, ja as pairs
-  float4* ffu;
-  float4* ffd;
+  // paired-single tables (lb_set_precision): the ladder factors cu, cd and
+  // the decay factors jf, ja as (hi, lo) pairs, and per subsystem this
+  // solve's control factor (dt/2) d_q = a + i b as (b hi, b lo, a hi, a lo)
+  // (negated for the adjoint)
+  float2* ffcu;
+  float2* ffcd;
   float2* ffjf;
   float2* ffja;
+  float4* ffab;
   double* red;  // [4][8 warps]
   int* flag;    // [0]: the iteration's decision, [1]: next iteration in single precision
 };
@@ -192,12 +213,14 @@ __device__ GridSmem grid_setup(unsigned char* base, const ProbDev& P, int nstate
   o += align16(sizeof(float) * 2 * P.njcoef);
   S.ctf = reinterpret_cast<float2*>(base + o);
   o += align16(sizeof(float2) * kMaxCq);
-  S.ffu = reinterpret_cast<float4*>(base + o);
-  S.ffd = S.ffu + P.ncoef;
-  o += align16(sizeof(float4) * 2 * P.ncoef);
+  S.ffcu = reinterpret_cast<float2*>(base + o);
+  S.ffcd = S.ffcu + P.ncoef;
+  o += align16(sizeof(float2) * 2 * P.ncoef);
   S.ffjf = reinterpret_cast<float2*>(base + o);
   S.ffja = S.ffjf + P.njcoef;
   o += align16(sizeof(float2) * 2 * P.njcoef);
+  S.ffab = reinterpret_cast<float4*>(base + o);
+  o += align16(sizeof(float4) * LB_MAXQ);
   S.red = reinterpret_cast<double*>(base + o);
   o += align16(sizeof(double) * 4 * 8);
   S.flag = reinterpret_cast<int*>(base + o);
@@ -218,6 +241,8 @@ __device__ GridSmem grid_setup(unsigned char* base, const ProbDev& P, int nstate
     S.cd[i] = P.cd[i];
     S.cuf[i] = (float)P.cu[i];
     S.cdf[i] = (float)P.cd[i];
+    S.ffcu[i] = split_f64(P.cu[i]);
+    S.ffcd[i] = split_f64(P.cd[i]);
   }
   for (int i = threadIdx.x; i < P.njcoef; i += blockDim.x) {
     S.jf[i] = P.jf[i];
@@ -554,6 +579,24 @@ __device__ __forceinline__ void ffmac(float& sh, float& sl, float ch, float cl, 
   sh = sum;
   sl = __fadd_rn(sl, __fadd_rn(t, e));
 }
+// (ph, pe) = (ah + al)(bh + bl): the product of the hi parts with its exact
+// rounding error and the cross terms (an unnormalised pair)
+__device__ __forceinline__ float2 ffprod(float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, e);
+  e = __fmaf_rn(al, bh, e);
+  return make_float2(p, e);
+}
+// (ah + al) + (bh + bl): two-sum of the hi parts, the lo parts and the
+// two-sum's error added in single precision (an unnormalised pair)
+__device__ __forceinline__ float2 ffadd(float2 a, float2 b) {
+  const float sum = __fadd_rn(a.x, b.x);
+  const float bv = __fsub_rn(sum, a.x);
+  const float t = __fadd_rn(__fsub_rn(a.x, __fsub_rn(sum, bv)), __fsub_rn(b.x, bv));
+  return make_float2(sum, __fadd_rn(__fadd_rn(a.y, b.y), t));
+}
+__device__ __forceinline__ float2 ffneg(float2 a) { return make_float2(-a.x, -a.y); }
 __device__ __forceinline__ float4 split4(double2 z) {
   const float2 a = split_f64(z.x), b = split_f64(z.y);
   return make_float4(a.x, a.y, b.x, b.y);
@@ -571,9 +614,9 @@ __device__ __forceinline__ float4 ldpk4(const float4* p, int k, int l) {
 }
 
 // offdiag_acc on a split iterate in paired single precision: acc = (re hi,
-// re lo, im hi, im lo) of the control and decay terms (the same sums as
-// offdiag_acc, written out term by term with the factors of this solve's
-// tables S.ffu, S.ffd, S.ffjf / S.ffja).  No Jaynes-Cummings pairs.
+// re lo, im hi, im lo) of the control and decay terms, the same sums as
+// offdiag_acc with the pairs of S.ffcu, S.ffcd, S.ffab and S.ffjf / S.ffja.
+// No Jaynes-Cummings pairs.
 template <bool ADJ, bool PK, int QN>
 __device__ __forceinline__ void offdiag_acc_ff(float (&acc)[4], const float4* __restrict__ x, int v, uint32_t kd,
                                                uint32_t ld, const Hdr& H, const GridSmem& S, int k, int l) {
@@ -589,30 +632,25 @@ __device__ __forceinline__ void offdiag_acc_ff(float (&acc)[4], const float4* __
   auto sub = [&](int q) {
     const int n = H.lev[q], s = H.stride[q], co = H.coff[q];
     const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
-    // c1 = cu[nk], c2 = cd[nl], c3 = cd[nk], c4 = cu[nl] times (b, a)
-    const float4 f1 = S.ffu[co + nk], f2 = S.ffd[co + nl], f3 = S.ffd[co + nk], f4 = S.ffu[co + nl];
+    // the ladder factors c1 = cu[nk], c2 = cd[nl], c3 = cd[nk], c4 = cu[nl]
+    // as pairs; P = c1 x1 - c2 x2, R = c3 x3 - c4 x4 and, with this solve's
+    // (a, b) (negated for the adjoint), re += b (P - R)_re + a (P + R)_im,
+    // im += b (P - R)_im - a (P + R)_re, as in offdiag_acc
+    const float2 c1 = S.ffcu[co + nk], c2 = S.ffcd[co + nl], c3 = S.ffcd[co + nk], c4 = S.ffcu[co + nl];
     const float4 x1 = nb(nk + 1 < n ? s : 0, 0);
     const float4 x2 = nb(0, nl > 0 ? -s : 0);
     const float4 x3 = nb(nk > 0 ? -s : 0, 0);
     const float4 x4 = nb(0, nl + 1 < n ? s : 0);
-    // re += b (c1 x1 - c2 x2 - c3 x3 + c4 x4)_re + a (c1 x1 - c2 x2 + c3 x3 - c4 x4)_im
-    ffmac(acc[0], acc[1], f1.x, f1.y, x1.x, x1.y);
-    ffmac(acc[0], acc[1], -f2.x, -f2.y, x2.x, x2.y);
-    ffmac(acc[0], acc[1], -f3.x, -f3.y, x3.x, x3.y);
-    ffmac(acc[0], acc[1], f4.x, f4.y, x4.x, x4.y);
-    ffmac(acc[0], acc[1], f1.z, f1.w, x1.z, x1.w);
-    ffmac(acc[0], acc[1], -f2.z, -f2.w, x2.z, x2.w);
-    ffmac(acc[0], acc[1], f3.z, f3.w, x3.z, x3.w);
-    ffmac(acc[0], acc[1], -f4.z, -f4.w, x4.z, x4.w);
-    // im += b (c1 x1 - c2 x2 - c3 x3 + c4 x4)_im - a (c1 x1 - c2 x2 + c3 x3 - c4 x4)_re
-    ffmac(acc[2], acc[3], f1.x, f1.y, x1.z, x1.w);
-    ffmac(acc[2], acc[3], -f2.x, -f2.y, x2.z, x2.w);
-    ffmac(acc[2], acc[3], -f3.x, -f3.y, x3.z, x3.w);
-    ffmac(acc[2], acc[3], f4.x, f4.y, x4.z, x4.w);
-    ffmac(acc[2], acc[3], -f1.z, -f1.w, x1.x, x1.y);
-    ffmac(acc[2], acc[3], f2.z, f2.w, x2.x, x2.y);
-    ffmac(acc[2], acc[3], -f3.z, -f3.w, x3.x, x3.y);
-    ffmac(acc[2], acc[3], f4.z, f4.w, x4.x, x4.y);
+    const float2 pr = ffadd(ffprod(c1.x, c1.y, x1.x, x1.y), ffprod(-c2.x, -c2.y, x2.x, x2.y));
+    const float2 pi = ffadd(ffprod(c1.x, c1.y, x1.z, x1.w), ffprod(-c2.x, -c2.y, x2.z, x2.w));
+    const float2 rr = ffadd(ffprod(c3.x, c3.y, x3.x, x3.y), ffprod(-c4.x, -c4.y, x4.x, x4.y));
+    const float2 ri = ffadd(ffprod(c3.x, c3.y, x3.z, x3.w), ffprod(-c4.x, -c4.y, x4.z, x4.w));
+    const float2 ur = ffadd(pr, rr), ui = ffadd(pi, ri), wr = ffadd(pr, ffneg(rr)), wi = ffadd(pi, ffneg(ri));
+    const float4 ab = S.ffab[q];  // (b hi, b lo, a hi, a lo)
+    ffmac(acc[0], acc[1], ab.x, ab.y, wr.x, wr.y);
+    ffmac(acc[0], acc[1], ab.z, ab.w, ui.x, ui.y);
+    ffmac(acc[2], acc[3], ab.x, ab.y, wi.x, wi.y);
+    ffmac(acc[2], acc[3], -ab.z, -ab.w, ur.x, ur.y);
     if ((H.jon >> q) & 1u) {
       const int jo = H.joff[q] + nk * n + nl;
       float2 cj;
@@ -653,8 +691,8 @@ __device__ __forceinline__ void grid_diff_pass(const ProbDev& P, const GridSmem&
   const Hdr& H = G.h;
   StateMax sm;
   sm.init(e0, e1, G.Vh);
-  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const GEl g = gel(G, P.hmap, e);
+  for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
+    const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
     const int b = g.b, v = g.v;
     const size_t o = gslab(G, g, b);
     const uint32_t kd = __ldg(P.digits + g.k), ld = __ldg(P.digits + g.l);
@@ -702,8 +740,8 @@ __device__ __forceinline__ void grid_full_pass(const ProbDev& P, const GridSmem&
   const Tabs T{S.cu, S.cd, S.jf, S.ja};
   StateMax sm;
   sm.init(e0, e1, G.Vh);
-  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const GEl g = gel(G, P.hmap, e);
+  for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
+    const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
     const int b = g.b, v = g.v;
     const double2* xs = zc + (size_t)b * G.Vh;
     const size_t o = gslab(G, g, b);
@@ -768,24 +806,19 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
   if (dok && (int)threadIdx.x < H.cq) S.ctf[threadIdx.x] = make_float2((float)ct[threadIdx.x].x, (float)ct[threadIdx.x].y);
   // paired-single apply: this solve's factor tables (the adjoint's with -a, -b)
   constexpr bool ff = FF;
-  if (ff)
-    for (int m = threadIdx.x; m < P.ncoef; m += blockDim.x) {
-      int q = 0;
-      while (q + 1 < H.Q && H.coff[q + 1] <= m) ++q;
-      const double a = ADJ ? -ct[q].x : ct[q].x, b = ADJ ? -ct[q].y : ct[q].y;
-      const float2 bu = split_f64(b * S.cu[m]), au = split_f64(a * S.cu[m]);
-      const float2 bd = split_f64(b * S.cd[m]), ad = split_f64(a * S.cd[m]);
-      S.ffu[m] = make_float4(bu.x, bu.y, au.x, au.y);
-      S.ffd[m] = make_float4(bd.x, bd.y, ad.x, ad.y);
-    }
+  if (ff && (int)threadIdx.x < H.Q) {
+    const int q = threadIdx.x;
+    const float2 a = split_f64(ADJ ? -ct[q].x : ct[q].x), b = split_f64(ADJ ? -ct[q].y : ct[q].y);
+    S.ffab[q] = make_float4(b.x, b.y, a.x, a.y);
+  }
   ndiff = 0;
   // z_0 = (I - dt/2 D)^-1 rhs (Jacobi) or rhs (Neumann); per-state max |rhs|
   {
     StateMax sm;
     sm.init(e0, e1, G.Vh);
     double msum[kLocalStates] = {0.0, 0.0, 0.0, 0.0};
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const GEl g = gel(G, P.hmap, e);
+    for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
+      const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
       const int b = g.b, v = g.v;
       const size_t o = gslab(G, g, b);
       const double2 r = rhs[o];
@@ -972,8 +1005,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
   double2* q = mode == 0 ? P.qf : x;
   const long long e0 = (long long)blockIdx.x * G.chunk, e1 = min(G.total, e0 + G.chunk);
   if (mode == 0)
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const GEl g = gel(G, P.hmap, e);
+    for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
+      const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
       q[gslab(G, g, g.b)] = (init ? P.q0 : P.qT)[(size_t)g.b * V + g.v];
     }
   bool failed = false;
@@ -997,8 +1030,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
     const int j = mode == 2 ? j1 - 1 - jj : j0 + jj;
     if (pred && R > 0 && j % R == 0) hist.restart();
     if (mode == 0 && tape && H.K > 0 && j % H.K == 0) {
-      for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const GEl g = gel(G, P.hmap, e);
+      for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
+        const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
         P.ckpt[gslab(G, g, (size_t)g.b * H.n_ckpt + j / H.K)] = q[gslab(G, g, g.b)];
       }
     }
@@ -1017,8 +1050,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
     diters += (unsigned long long)nd * G.M;
     steps += G.M;
     maxit = max(maxit, it);
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const GEl g = gel(G, P.hmap, e);
+    for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
+      const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
       const size_t o = gslab(G, g, g.b);
       const double2 zz = z[o], qq = q[o];
       if (mode == 0 && tape && H.K == 0) P.ckpt[gslab(G, g, (size_t)g.b * H.NT + j)] = zz;
@@ -1032,8 +1065,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
   }
   // the final states rho_i(T), in the vec layout with their mirrors
   if (mode == 0 && !failed)
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const GEl g = gel(G, P.hmap, e);
+    for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
+      const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
       gput(P.qT, g, V, q[gslab(G, g, g.b)]);
     }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1057,8 +1090,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const long long e0 = (long long)blockIdx.x * G.chunk, e1 = min(G.total, e0 + G.chunk);
   // terminal condition qhat^{N_T} = beta_i/M g_i (Appendix B)
-  for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-    const GEl g = gel(G, P.hmap, e);
+  for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
+    const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
     const size_t o = (size_t)g.b * V + g.v;
     const double w = P.wgt[g.b];
     const double wt = linear_sign(P.kind) * w;
@@ -1074,8 +1107,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
   // P.qb (each element by its own thread), from q^{N_T}
   const bool penal = H.gamma1 != 0.0;
   if (penal)
-    for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const GEl g = gel(G, P.hmap, e);
+    for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
+      const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
       P.qb[gslab(G, g, g.b)] = P.qT[(size_t)g.b * V + g.v];
     }
   long long itg = 0, nsolve = 0;
@@ -1102,8 +1135,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
     const int j0 = H.K > 0 ? sg * H.K : 0;
     const int j1 = H.K > 0 ? min(H.NT, j0 + H.K) : H.NT;
     if (H.K > 0) {
-      for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const GEl g = gel(G, P.hmap, e);
+      for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
+        const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
         P.qf[gslab(G, g, g.b)] = P.ckpt[gslab(G, g, (size_t)g.b * H.n_ckpt + sg)];
       }
       for (int j = j0; j < j1; ++j) {
@@ -1121,8 +1154,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
         dit_rec += (unsigned long long)nd * G.M;
         st_rec += G.M;
         maxit = max(maxit, it);
-        for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-          const GEl g = gel(G, P.hmap, e);
+        for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
+          const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
           const size_t o = gslab(G, g, g.b);
           const double2 zz = z[o], qq = P.qf[o];
           P.seg[gslab(G, g, (size_t)g.b * H.K + (j - j0))] = zz;  // read back at the same element only
@@ -1164,8 +1197,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
         double sar[kQP], sai[kQP], sdr[kQP], sdi[kQP];
 #pragma unroll
         for (int u = 0; u < kQP; ++u) sar[u] = sai[u] = sdr[u] = sdi[u] = 0.0;
-        for (long long e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-          const GEl g = gel(G, P.hmap, e);
+        for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
+          const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
           const int b = g.b, v = g.v;
           const size_t o = gslab(G, g, b);
           const double2* zs = zh + (size_t)b * G.Vh;

@@ -110,7 +110,7 @@ struct ProbDev {
   int32_t pred_restart;      // forward predictor: -2 none, 0 never restarts, R > 0 restarts when j % R == 0
   int32_t pred_order;        // highest extrapolation order of the rotated predictor (1..kRingOrder)
   long long spin_limit;      // polls of a grid-barrier wait before it gives up (0: the kernels' default)
-  int32_t* hmap;             // [N (N + 1) / 2] vec indices k + N l with k <= l (grid sweeps)
+  uint32_t* hkl;             // [N (N + 1) / 2] the elements k <= l of the grid sweeps, k | l << 16, column by column
   int32_t herm;              // grid sweeps iterate k <= l only: every state and target is Hermitian
   int32_t diffit;            // grid sweeps: difference iterations in single precision allowed (Jacobi)
   float2* dfA;               // [M*V] grid sweeps: single-precision differences of successive iterates

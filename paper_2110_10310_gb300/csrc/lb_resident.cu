@@ -100,7 +100,8 @@ __device__ void res_setup(const ResSmem& S, const ProbDev& P, bool herm_ok = tru
   }
   if (herm_ok && P.herm)
     for (int i = threadIdx.x; i < P.N * (P.N + 1) / 2; i += blockDim.x) {
-      const int v = P.hmap[i], k = v % P.N, l = v / P.N;
+      const uint32_t t = P.hkl[i];
+      const int k = (int)(t & 0xffffu), l = (int)(t >> 16), v = k + P.N * l;
       S.hmap[i] = (uint16_t)v;
       S.hmir[i] = k != l ? (uint16_t)(l + P.N * k) : (uint16_t)0xffffu;
     }

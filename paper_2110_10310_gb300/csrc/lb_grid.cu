@@ -1197,6 +1197,14 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
         double sar[kQP], sai[kQP], sdr[kQP], sdi[kQP];
 #pragma unroll
         for (int u = 0; u < kQP; ++u) sar[u] = sai[u] = sdr[u] = sdi[u] = 0.0;
+        // paired-single sums (FF): (g_a re hi, lo, im hi, lo), (g_ad ...)
+        float fa[kQP][4], fb[kQP][4];
+#pragma unroll
+        for (int u = 0; u < kQP; ++u)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) fa[u][c] = fb[u][c] = 0.0f;
+        // zhat split into pairs: the buffer the solve's last iteration wrote
+        const float4* zsh = FF ? (zh == P.zA ? P.zsA : P.zsB) : nullptr;
         for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
           const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
           const int b = g.b, v = g.v;
@@ -1209,6 +1217,52 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
           auto nb = [&](int dk, int dl) -> double2 {
             return G.herm ? ldpk<kNbL2>(zs, g.k + dk, g.l + dl) : ldz<kNbL2>(zs + v + dk + dl * N);
           };
+          if constexpr (FF) {
+            // the same pieces in paired single precision from the split zhat
+            const float4* zss = zsh + (size_t)b * G.Vh;
+            auto nbf = [&](int dk, int dl) -> float4 {
+              if (G.herm) return ldpk4(zss, g.k + dk, g.l + dl);
+              const float4* qq = zss + v + dk + dl * N;
+              return kNbL2 ? __ldcg(qq) : *qq;
+            };
+            const float4 Zs = split4(Z);
+#pragma unroll
+            for (int u = 0; u < kQP; ++u) {
+              const int q = q0 + u;
+              if (q < Qn) {
+                const int n = H.lev[q], s = H.stride[q], co = H.coff[q];
+                const int nk = (kd >> (H.db * q)) & H.dm, nl = (ld >> (H.db * q)) & H.dm;
+                const float2 c1 = S.ffcu[co + nk], c2 = S.ffcd[co + nl], c3 = S.ffcd[co + nk], c4 = S.ffcu[co + nl];
+                const float4 x1 = nbf(nk + 1 < n ? s : 0, 0);
+                const float4 x2 = nbf(0, nl > 0 ? -s : 0);
+                const float4 x3 = nbf(nk > 0 ? -s : 0, 0);
+                const float4 x4 = nbf(0, nl + 1 < n ? s : 0);
+                const float2 pr = ffadd(ffprod(c1.x, c1.y, x1.x, x1.y), ffprod(-c2.x, -c2.y, x2.x, x2.y));
+                const float2 pi = ffadd(ffprod(c1.x, c1.y, x1.z, x1.w), ffprod(-c2.x, -c2.y, x2.z, x2.w));
+                const float2 rr = ffadd(ffprod(c3.x, c3.y, x3.x, x3.y), ffprod(-c4.x, -c4.y, x4.x, x4.y));
+                const float2 ri = ffadd(ffprod(c3.x, c3.y, x3.z, x3.w), ffprod(-c4.x, -c4.y, x4.z, x4.w));
+                if (G.herm && g.vm >= 0) {
+                  const float2 dr = ffadd(rr, ffneg(pr)), di = ffadd(ri, ffneg(pi));
+                  const float2 ur = ffadd(rr, pr), ui = ffadd(ri, pi);
+                  ffmac(fa[u][0], fa[u][1], Zs.x, Zs.y, dr.x, dr.y);
+                  ffmac(fa[u][0], fa[u][1], Zs.z, Zs.w, di.x, di.y);
+                  ffmac(fa[u][2], fa[u][3], Zs.z, Zs.w, ur.x, ur.y);
+                  ffmac(fa[u][2], fa[u][3], -Zs.x, -Zs.y, ui.x, ui.y);
+                } else {
+                  ffmac(fa[u][0], fa[u][1], Zs.x, Zs.y, rr.x, rr.y);
+                  ffmac(fa[u][0], fa[u][1], Zs.z, Zs.w, ri.x, ri.y);
+                  ffmac(fa[u][2], fa[u][3], Zs.z, Zs.w, rr.x, rr.y);
+                  ffmac(fa[u][2], fa[u][3], -Zs.x, -Zs.y, ri.x, ri.y);
+                  if (!G.herm) {
+                    ffmac(fb[u][0], fb[u][1], Zs.x, Zs.y, pr.x, pr.y);
+                    ffmac(fb[u][0], fb[u][1], Zs.z, Zs.w, pi.x, pi.y);
+                    ffmac(fb[u][2], fb[u][3], Zs.z, Zs.w, pr.x, pr.y);
+                    ffmac(fb[u][2], fb[u][3], -Zs.x, -Zs.y, pi.x, pi.y);
+                  }
+                }
+              }
+            }
+          } else
 #pragma unroll
           for (int u = 0; u < kQP; ++u) {
             const int q = q0 + u;
@@ -1265,6 +1319,15 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev
             }
             P.lam[o] = ln;
             if (apred) grid_commit<true>(P, ahist, o, (size_t)G.M * G.Vh, v);
+          }
+        }
+        if constexpr (FF) {
+#pragma unroll
+          for (int u = 0; u < kQP; ++u) {
+            sar[u] = f32_to_f64(fa[u][0]) + f32_to_f64(fa[u][1]);
+            sai[u] = f32_to_f64(fa[u][2]) + f32_to_f64(fa[u][3]);
+            sdr[u] = f32_to_f64(fb[u][0]) + f32_to_f64(fb[u][1]);
+            sdi[u] = f32_to_f64(fb[u][2]) + f32_to_f64(fb[u][3]);
           }
         }
         if (G.herm) {

@@ -786,10 +786,77 @@ __device__ __forceinline__ void grid_full_pass(const ProbDev& P, const GridSmem&
   sm.push(bank, reinterpret_cast<unsigned long long*>(S.red));
 }
 
+// The first pass of a solve, per element g (slab offset o, right-hand side
+// r): z_0 = (I - dt/2 D)^-1 (r + the predicted correction) for the Jacobi
+// iteration (r itself for the Neumann series) into zA (and its split, FF),
+// |r| into the solve's per-state maxima and, with the running penalty
+// (pen), the merit summand of r into msum.
+template <bool ADJ, bool FF>
+__device__ __forceinline__ void first_elem(const ProbDev& P, const GridHdr& G, const GEl& g, size_t o, double2 r,
+                                           const GridHist& hist, bool pen, bool neumann,
+                                           double (&msum)[kLocalStates], StateMax& sm, unsigned long long* qbank) {
+  const Hdr& H = G.h;
+  const int b = g.b, v = g.v;
+  if (pen) {
+    // an off-diagonal element under the symmetry stands for its mirror too
+    const double f = merit_summand(H.kind, r, P.tar[(size_t)b * H.V + v]) * (g.vm >= 0 ? 2.0 : 1.0);
+    const int k = b - sm.sb0;
+#pragma unroll
+    for (int u = 0; u < kLocalStates; ++u)
+      if (u == k) msum[u] += f;
+  }
+  double2 z0 = r;
+  if (!neumann) {
+    double ur = r.x, ui = r.y;
+    const double2 d = __ldg(P.Dinv + v);
+    const double di = ADJ ? -d.y : d.y;
+    if (hist.n > 0) {
+      const double2 c = cmul(hist.gp[o], anchored_sum(hist.ring + o, (size_t)G.M * G.Vh, hist.slot, hist.n));
+      ur += c.x;
+      ui += c.y;
+    } else if (hist.ring) {
+      // a fresh anchor: m = 0
+      hist.gp[o] = make_double2(1.0, 0.0);
+      hist.gm[o] = make_double2(1.0, 0.0);
+    }
+    z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
+  }
+  P.zA[o] = z0;
+  if constexpr (FF) P.zsA[o] = split4(z0);
+  sm.add(b, umax64(abs_bits(r.x), abs_bits(r.y)), qbank);
+}
+// ... and per block, after the elements (all threads): push the maxima and,
+// with the running penalty, the block's merit sums of its chunk's states in
+// a fixed order
+__device__ __forceinline__ void first_end(const ProbDev& P, const GridSmem& S, StateMax& sm,
+                                          unsigned long long* qbank, bool pen, const double (&msum)[kLocalStates]) {
+  sm.push(qbank, reinterpret_cast<unsigned long long*>(S.red));
+  if (pen) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    double* dred = S.red;
+#pragma unroll
+    for (int u = 0; u < kLocalStates; ++u) {
+      const double w = warp_sum(msum[u]);
+      if (lane == 0) dred[u * 8 + warp] = w;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < kLocalStates) {
+      double t = 0.0;
+      for (int w = 0; w < nwarps; ++w) t += dred[threadIdx.x * 8 + w];
+      P.mpart[(size_t)blockIdx.x * kLocalStates + threadIdx.x] = t;
+    }
+    __syncthreads();
+  }
+}
+
+// One implicit-midpoint solve over all M states (see above).  prepped: the
+// first pass was already done by the caller (first_elem / first_end, fused
+// with the previous step's commit), for this solve's |q| bank.
 template <bool ADJ, bool FF>
 __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __restrict__ rhs,
                           const double2* __restrict__ ct, double fac, long long& it_global, long long& solve,
-                          int& ndiff, double2** zout, GridHist hist = GridHist(), double penw = 0.0) {
+                          int& ndiff, double2** zout, GridHist hist = GridHist(), double penw = 0.0,
+                          bool prepped = false) {
   const GridHdr& G = *S.g;
   const Hdr& H = G.h;
   const Tabs T{S.cu, S.cd, S.jf, S.ja};
@@ -813,61 +880,16 @@ __device__ int grid_solve(const ProbDev& P, const GridSmem& S, const double2* __
   }
   ndiff = 0;
   // z_0 = (I - dt/2 D)^-1 rhs (Jacobi) or rhs (Neumann); per-state max |rhs|
-  {
+  if (!prepped) {
     StateMax sm;
     sm.init(e0, e1, G.Vh);
     double msum[kLocalStates] = {0.0, 0.0, 0.0, 0.0};
     for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
       const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
-      const int b = g.b, v = g.v;
-      const size_t o = gslab(G, g, b);
-      const double2 r = rhs[o];
-      if (penw != 0.0) {
-        // an off-diagonal element under the symmetry stands for its mirror too
-        const double f = merit_summand(H.kind, r, P.tar[(size_t)b * V + v]) * (g.vm >= 0 ? 2.0 : 1.0);
-        const int k = b - sm.sb0;
-#pragma unroll
-        for (int u = 0; u < kLocalStates; ++u)
-          if (u == k) msum[u] += f;
-      }
-      double2 z0 = r;
-      if (!neumann) {
-        double ur = r.x, ui = r.y;
-        const double2 d = __ldg(P.Dinv + v);
-        const double di = ADJ ? -d.y : d.y;
-        if (hist.n > 0) {
-          const double2 c = cmul(hist.gp[o], anchored_sum(hist.ring + o, (size_t)M * G.Vh, hist.slot, hist.n));
-          ur += c.x;
-          ui += c.y;
-        } else if (hist.ring) {
-          // a fresh anchor: m = 0
-          hist.gp[o] = make_double2(1.0, 0.0);
-          hist.gm[o] = make_double2(1.0, 0.0);
-        }
-        z0 = make_double2(fma(d.x, ur, -di * ui), fma(d.x, ui, di * ur));
-      }
-      P.zA[o] = z0;
-      if (ff) P.zsA[o] = split4(z0);
-      sm.add(b, umax64(abs_bits(r.x), abs_bits(r.y)), qbank);
+      const size_t o = gslab(G, g, g.b);
+      first_elem<ADJ, FF>(P, G, g, o, rhs[o], hist, penw != 0.0, neumann, msum, sm, qbank);
     }
-    sm.push(qbank, red);
-    if (penw != 0.0) {
-      // per-block merit sums of the chunk's states, in a fixed order
-      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-      double* dred = S.red;
-#pragma unroll
-      for (int u = 0; u < kLocalStates; ++u) {
-        const double w = warp_sum(msum[u]);
-        if (lane == 0) dred[u * 8 + warp] = w;
-      }
-      __syncthreads();
-      if ((int)threadIdx.x < kLocalStates) {
-        double t = 0.0;
-        for (int w = 0; w < nwarps; ++w) t += dred[threadIdx.x * 8 + w];
-        P.mpart[(size_t)blockIdx.x * kLocalStates + threadIdx.x] = t;
-      }
-      __syncthreads();
-    }
+    first_end(P, S, sm, qbank, penw != 0.0, msum);
   }
   if (!grid_sync(P.bar, gridDim.x, P.spin_limit > 0 ? P.spin_limit : kSpinLimit)) return -3;
   if (penw != 0.0 && blockIdx.x == 0) {
@@ -1026,21 +1048,25 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
   hist.gp = P.hgp;
   hist.gm = P.hgm;
   hist.cap = P.pred_order;
+  const bool neumann = H.method == LB_SOLVER_NEUMANN;
+  bool prepped = false;  // this step's first pass was fused with the previous step's commit
   for (int jj = 0; jj < j1 - j0; ++jj) {
     const int j = mode == 2 ? j1 - 1 - jj : j0 + jj;
-    if (pred && R > 0 && j % R == 0) hist.restart();
-    if (mode == 0 && tape && H.K > 0 && j % H.K == 0) {
-      for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
-        const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
-        P.ckpt[gslab(G, g, (size_t)g.b * H.n_ckpt + j / H.K)] = q[gslab(G, g, g.b)];
+    if (!prepped) {
+      if (pred && R > 0 && j % R == 0) hist.restart();
+      if (mode == 0 && tape && H.K > 0 && j % H.K == 0) {
+        for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
+          const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
+          P.ckpt[gslab(G, g, (size_t)g.b * H.n_ckpt + j / H.K)] = q[gslab(G, g, g.b)];
+        }
       }
     }
     double2* z = nullptr;
     int nd = 0;
     const int it = mode == 2 ? grid_solve<true, FF>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve,
-                                                nd, &z)
+                                                nd, &z, GridHist(), 0.0, prepped)
                              : grid_solve<false, FF>(P, S, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), itg, nsolve,
-                                                 nd, &z, pred ? hist : GridHist(), penal ? P.pen[j] : 0.0);
+                                                 nd, &z, pred ? hist : GridHist(), penal ? P.pen[j] : 0.0, prepped);
     if (it < 0) {
       grid_fail(P, it, j);
       failed = true;
@@ -1050,18 +1076,40 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
     diters += (unsigned long long)nd * G.M;
     steps += G.M;
     maxit = max(maxit, it);
+    // this step's commit (q^{j+1} = 2 z - q^j, the predictor's record), in
+    // the same pass as the first pass of the next step (its predictor state
+    // hn: advanced, restarted where the next step is a restart point)
+    // (the adjoint propagation of mode 2 keeps separate passes)
+    const bool next = mode != 2 && jj + 1 < j1 - j0;
+    const int jn = j + 1;
+    GridHist hn = hist;
+    if (pred) {
+      hn.advance();
+      if (hn.m >= kAnchorSteps) hn.m = 0;
+      if (next && R > 0 && jn % R == 0) hn.restart();
+    }
+    const bool ckn = next && mode == 0 && tape && H.K > 0 && jn % H.K == 0;
+    const bool penn = next && penal && P.pen[jn] != 0.0;
+    unsigned long long* qbn = P.gslots + 3 * G.M + (nsolve & 1) * G.M;  // the next solve's |q| bank
+    StateMax smn;
+    smn.init(e0, e1, G.Vh);
+    double msum[kLocalStates] = {0.0, 0.0, 0.0, 0.0};
     for (GIter it_(G, e0 + threadIdx.x); it_.e < e1; it_.next(G, blockDim.x)) {
       const GEl g = gel_at(G, P.hkl, it_.b, it_.i);
       const size_t o = gslab(G, g, g.b);
       const double2 zz = z[o], qq = q[o];
       if (mode == 0 && tape && H.K == 0) P.ckpt[gslab(G, g, (size_t)g.b * H.NT + j)] = zz;
-      q[o] = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
+      const double2 qn = make_double2(fma(2.0, zz.x, -qq.x), fma(2.0, zz.y, -qq.y));
+      q[o] = qn;
       if (pred) grid_commit<false>(P, hist, o, (size_t)G.M * G.Vh, g.v);
+      if (next) {
+        if (ckn) P.ckpt[gslab(G, g, (size_t)g.b * H.n_ckpt + jn / H.K)] = qn;
+        first_elem<false, FF>(P, G, g, o, qn, pred ? hn : GridHist(), penn, neumann, msum, smn, qbn);
+      }
     }
-    if (pred) {
-      hist.advance();
-      if (hist.m >= kAnchorSteps) hist.m = 0;
-    }
+    if (next) first_end(P, S, smn, qbn, penn, msum);
+    if (pred) hist = hn;
+    prepped = next;
   }
   // the final states rho_i(T), in the vec layout with their mirrors
   if (mode == 0 && !failed)

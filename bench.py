@@ -326,6 +326,9 @@ def kernel_source_digest(path: str) -> str:
 KERNEL_SOURCES = {
     "k_backward_grid": ("lb_grid.cu", "lb_device.cuh"),
     "k_sweep_grid": ("lb_grid.cu", "lb_device.cuh"),
+    # the paired-single instantiations (lb_set_precision LB_PREC_F32X2)
+    "k_backward_grid_f32x2": ("lb_grid.cu", "lb_device.cuh"),
+    "k_sweep_grid_f32x2": ("lb_grid.cu", "lb_device.cuh"),
     "k_backward_cl": ("lb_cluster.cu", "lb_device.cuh"),
     "k_forward_cl": ("lb_cluster.cu", "lb_device.cuh"),
     "k_backward_res": ("lb_resident.cu", "lb_device.cuh"),
@@ -770,7 +773,9 @@ def run_gradient(args, rank, world, dev, dist):
     elem_iters = Ve * (st["phase_iterations"][1] + st["phase_iterations"][2])
     hbm_alg = BYTES_PER_ELEMENT_ITERATION * elem_iters
     hbm_peak = measured_peaks().get("hbm_gbs") or 6800.0
-    trec = traffic_record(kernel_name, wl)
+    # the DRAM record of the instantiation that ran (FP64 or paired-single apply)
+    trec = traffic_record(kernel_name + ("_f32x2" if args.precision == "f32x2" and kernel_name.endswith("grid") else ""),
+                          wl)
     traffic = None
     if trec:
         # DRAM bytes of the capture scaled to this launch by the element-iterations

@@ -355,7 +355,13 @@ int lb_set_symmetry(lb_system* sys, int32_t symmetry);
 /* ---- device workspace ---------------------------------------------------- */
 
 /* Bytes of device memory the system needs (depends on N, M, N_T, Q, the
- * control layout and ckpt_every). */
+ * control layout and ckpt_every).  When the grid-wide sweep runs under the
+ * Hermitian symmetry (Hermitian states and targets, LB_SYM_HERMITIAN), its
+ * checkpoint and segment tapes are sized for the k <= l entries of each
+ * state, N (N + 1) / 2 instead of N^2; a workspace bound so refuses later
+ * calls (LB_EINVAL, "packed tapes") while the states or targets set since
+ * are not Hermitian or the symmetry is switched off, until they are
+ * Hermitian again or a new workspace is bound. */
 int lb_workspace_bytes(const lb_system* sys, size_t* bytes);
 
 /* Bind caller-owned device memory (256-byte aligned, >= lb_workspace_bytes)

@@ -111,9 +111,11 @@ struct lb_system {
   double gamma1 = 0.0, pen_a = 1.0;  // running penalty (one CTA per state)
   bool rho_herm = false;  // every initial state exactly Hermitian
   bool tar_herm = false;  // every explicit target exactly Hermitian (gate targets: always)
+  bool rho_finite = true;  // no NaN or Inf in the initial states
   int gblocks = 0;   // cooperative grid size (grid sweeps)
   size_t gsmem = 0;  // its dynamic shared memory
   bool cluster = false;      // cluster-split sweeps (decided at bind)
+  bool tapes_packed = false;  // the bound workspace holds the grid sweeps' tapes packed (k <= l)
   lbk::ClusterConfig cc{};
   // device binding
   char* ws = nullptr;
@@ -287,6 +289,9 @@ int gproj_used(const lb_system* s) {
   return s->cluster ? s->M * s->cc.C * (s->cc.threads / 32) : s->M;
 }
 
+bool use_symmetry(const lb_system* s);
+bool packed_tapes(const lb_system* s);
+
 Layout make_layout(const lb_system* s) {
   Layout L;
   size_t off = 0;
@@ -322,8 +327,9 @@ Layout make_layout(const lb_system* s) {
   take(L.qT, c2 * M * V);
   const int K = effective_K(s);
   const size_t nck = K > 0 ? (NT + K - 1) / K : NT;
-  take(L.ckpt, c2 * M * nck * V);
-  take(L.seg, K > 0 ? c2 * M * (size_t)K * V : 0);
+  const size_t Vt = packed_tapes(s) ? (size_t)s->N * (s->N + 1) / 2 : V;  // entries per state in the tapes
+  take(L.ckpt, c2 * M * nck * Vt);
+  take(L.seg, K > 0 ? c2 * M * (size_t)K * Vt : 0);
   const bool grid = use_grid(s);
   take(L.gproj, c2 * gproj_slots(s) * NT * s->Q * 2);
   take(L.gsum, c2 * NT * s->Q * 2);
@@ -369,6 +375,13 @@ int check_ready(const lb_system* s, bool need_bound) {
   if (!s->ctrl_defined) return fail(LB_EINVAL, "controls not defined (lb_controls_define)");
   if (s->M <= 0) return fail(LB_EINVAL, "no initial states (lb_states_set)");
   if (need_bound && !s->ws) return fail(LB_EINVAL, "no workspace bound (lb_bind_workspace)");
+  if (need_bound && s->tapes_packed && !use_symmetry(s)) {
+    // a NaN or Inf in a state also breaks the symmetry test: report it as the
+    // sweeps would (at the first step)
+    if (!s->rho_finite) return fail(LB_ENAN, "an initial state holds NaN or Inf (time step 0)");
+    return fail(LB_EINVAL,
+                "the workspace was bound for Hermitian states and targets (packed tapes); bind a new one for these");
+  }
   return LB_OK;
 }
 
@@ -551,6 +564,12 @@ bool use_symmetry(const lb_system* s) {
   if (use_grid(s)) return true;
   return !s->cluster;
 }
+
+// The grid sweeps keep the checkpoint and segment tapes packed (the k <= l
+// entries of each state) under the Hermitian symmetry, so a workspace bound
+// while the states and targets are Hermitian sizes them N (N + 1) / 2 per
+// state instead of N^2.
+bool packed_tapes(const lb_system* s) { return use_grid(s) && use_symmetry(s); }
 
 // re-upload the problem block when the symmetry decision changed (bound systems)
 int refresh_symmetry(lb_system* s) {
@@ -1040,6 +1059,12 @@ int lb_states_set(lb_system* s, int32_t M, const double* rho0, const double* wei
   s->Mu = M;
   s->wgt_u = w;
   s->rho_herm = hermitian_matrices(rho0, M, s->N);
+  s->rho_finite = true;
+  for (size_t t = 0; t < (size_t)2 * M * s->N * s->N; ++t)
+    if (!std::isfinite(rho0[t])) {
+      s->rho_finite = false;
+      break;
+    }
   if (s->ws) {
     apply_pairs(s);
     int rc = upload_states(s, rho0, s->bind_stream);
@@ -1288,6 +1313,7 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
   if (rc) return rc;
   s->L = make_layout(s);
   if (bytes < s->L.total) return fail(LB_ENOMEM, "workspace smaller than lb_workspace_bytes");
+  s->tapes_packed = packed_tapes(s);
   if (s->rho0.empty()) return fail(LB_EINVAL, "initial states are required before binding");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   rc = decide_krylov(s);
@@ -1989,6 +2015,7 @@ int static_bind(lb_system* s, void* ws, cudaStream_t st) {
   if (rc0) return rc0;
   s->cluster = false;  // this entry point always runs one CTA per state
   s->L = make_layout(s);
+  s->tapes_packed = packed_tapes(s);
   s->ws = static_cast<char*>(ws);
   s->ws_bytes = LB_STATIC_SCRATCH_BYTES;
   s->bind_stream = st;

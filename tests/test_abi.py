@@ -219,14 +219,22 @@ def test_grid_sweep_workspace_and_sweep_choice(lib):
         assert lib.lb_set_sweep(h, 7) == L.LB_EINVAL
         L.check(lib.lb_set_sweep(h, L.LB_SWEEP_GRID))
         n = c_size_t()
+        L.check(lib.lb_set_symmetry(h, L.LB_SYM_NONE))
         L.check(lib.lb_workspace_bytes(h, byref(n)))
         V, M = 81 * 81, 2
         state = 16 * M * V
         # q0, tar, qT, 4 checkpoints, 10-step segment tape, zA, zB, lam, qf,
         # the ten-slot rings of the adjoint's and the recompute's first-iterate
-        # predictors and the powers g^m, g^-m of each ring's frame
-        assert n.value >= (3 + 4 + 10 + 4 + 20 + 4) * state
-        assert n.value <= (3 + 4 + 10 + 4 + 20 + 4) * state + 2 * 1024 * 1024
+        # predictors, the powers g^m, g^-m of each ring's frame and the two
+        # single-precision difference buffers (8 bytes per element each)
+        assert n.value >= (3 + 4 + 10 + 4 + 20 + 4 + 1) * state
+        assert n.value <= (3 + 4 + 10 + 4 + 20 + 4 + 1) * state + 2 * 1024 * 1024
+        # Hermitian states and targets: the 14 tape slabs hold k <= l only
+        L.check(lib.lb_set_symmetry(h, L.LB_SYM_HERMITIAN))
+        npk = c_size_t()
+        L.check(lib.lb_workspace_bytes(h, byref(npk)))
+        Vh = 81 * 82 // 2
+        assert n.value - npk.value == 14 * 16 * M * (V - Vh)
     finally:
         lib.lb_system_destroy(h)
 

@@ -481,6 +481,29 @@ def test_difference_iterations_keep_recompute_bitwise():
     assert s.lib.lb_set_difference_iterations(s.h, 2) == L.LB_EINVAL
 
 
+def test_packed_tapes_need_hermitian_states():
+    """A workspace bound while the states and targets are Hermitian holds the
+    grid sweeps' checkpoint and segment tapes packed (N (N + 1) / 2 entries
+    per state): the gradient matches the oracle; after non-Hermitian states
+    are set the call is refused on the host (LB_EINVAL) instead of
+    overrunning the tapes, and Hermitian states run again on the same
+    workspace."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(431, levels=(3, 3), n_states=2, n_steps=30, T_ns=0.6, amp=0.1, ckpt_every=7,
+                         hermitian=True)
+    s, g = _check_problem(p, sweep=L.LB_SWEEP_GRID)
+    q = W.random_problem(432, levels=(3, 3), n_states=2, n_steps=30, T_ns=0.6, amp=0.1, ckpt_every=7,
+                         hermitian=False)
+    s.set_states_host(q.rho0, q.weights)
+    with pytest.raises(L.LBError) as err:
+        s.gradient()
+    assert err.value.code == L.LB_EINVAL and "packed" in str(err.value)
+    s.set_states_host(p.rho0, p.weights)
+    G2, g2 = s.gradient()
+    assert _rel(g2, g) < 1e-13
+
+
 def test_grid_checkpoint_interval_bitwise_identical():
     """Grid sweeps without a forward predictor: K = 1, 7, 100 bit-identical;
     the full tape (K = 0, whose forward sweep predicts its first iterates)

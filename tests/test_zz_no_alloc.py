@@ -4,6 +4,7 @@ memory, with all device scratch in the library's static array.
 Runs last (file name) so that a failure here stops a -x run only after every
 other test has run; it also passes alone in a fresh process."""
 
+import gc
 from ctypes import POINTER, byref, c_double, c_int32, c_size_t, c_void_p
 
 import numpy as np
@@ -89,15 +90,22 @@ def test_static_scratch_gradient_matches_workspace_gradient(name):
             G = c_double()
             g = np.zeros(len(g_ref))
             if call == 1:
-                # the first call has loaded the module; the second allocates nothing
+                # the first call has loaded the module; the second allocates
+                # nothing (the collector is held off so that tensors of earlier
+                # tests are not freed in between)
+                gc.collect()
+                gc.disable()
                 torch.cuda.synchronize()
                 used0 = torch.cuda.memory_allocated()
                 free0 = torch.cuda.mem_get_info()[0]
-            L.check(lib.lb_gradient_static(h, stream, byref(G), g.ctypes.data_as(POINTER(c_double))))
-            if call == 1:
-                torch.cuda.synchronize()
-                assert torch.cuda.memory_allocated() == used0
-                assert torch.cuda.mem_get_info()[0] == free0
+            try:
+                L.check(lib.lb_gradient_static(h, stream, byref(G), g.ctypes.data_as(POINTER(c_double))))
+                if call == 1:
+                    torch.cuda.synchronize()
+                    assert torch.cuda.memory_allocated() == used0
+                    assert torch.cuda.mem_get_info()[0] == free0
+            finally:
+                gc.enable()
             assert abs(G.value - G_ref) <= 1e-10 * abs(G_ref)
             assert np.max(np.abs(g - g_ref)) <= 1e-9 * np.max(np.abs(g_ref))
         # the handle is left unbound and still usable

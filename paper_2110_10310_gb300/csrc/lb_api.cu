@@ -112,7 +112,8 @@ struct lb_system {
   bool rho_herm = false;  // every initial state exactly Hermitian
   bool tar_herm = false;  // every explicit target exactly Hermitian (gate targets: always)
   bool rho_finite = true;  // no NaN or Inf in the initial states
-  int gblocks = 0;   // cooperative grid size (grid sweeps)
+  int gblocks = 0;   // cooperative grid size of the forward grid sweep
+  int gblocks_b = 0;  // ... and of the backward one
   size_t gsmem = 0;  // its dynamic shared memory
   bool cluster = false;      // cluster-split sweeps (decided at bind)
   bool tapes_packed = false;  // the bound workspace holds the grid sweeps' tapes packed (k <= l)
@@ -681,7 +682,7 @@ void fill_prob(lb_system* s) {
   P.status = at<DevStatus>(s, s->L.status);
   const bool grid = use_grid(s);
   P.gM = gproj_used(s);
-  P.grid_blocks = grid ? s->gblocks : 0;
+  P.grid_blocks = grid ? std::max(s->gblocks, s->gblocks_b) : 0;
   if (grid) {
     P.zA = at<double2>(s, s->L.zA);
     P.zB = at<double2>(s, s->L.zB);
@@ -1341,8 +1342,11 @@ int lb_bind_workspace(lb_system* s, void* ws, size_t bytes, void* stream) {
     LB_CUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev), "cudaDeviceGetAttribute");
     if (!coop) return fail(LB_ECUDA, "the device does not support cooperative launches (grid sweeps)");
     s->gsmem = lbk::grid_smem_bytes(n_coef(s), n_jcoef(s));
-    s->gblocks = lbk::grid_blocks_max(s->gsmem);
-    if (s->gblocks <= 0) return fail(LB_ECUDA, "cannot size the cooperative grid of the sweep kernels");
+    const int ffk = s->precision == LB_PREC_F32X2 && s->jp.empty() ? 1 : 0;
+    s->gblocks = lbk::grid_blocks(0, ffk, s->gsmem);
+    s->gblocks_b = lbk::grid_blocks(1, ffk, s->gsmem);
+    if (s->gblocks <= 0 || s->gblocks_b <= 0)
+      return fail(LB_ECUDA, "cannot size the cooperative grid of the sweep kernels");
     if (s->gamma1 != 0.0 && !grid_chunks_cover_few_states(s))
       return fail(LB_EINVAL, "the running penalty on grid sweeps needs every block's elements to span at most "
                              "4 states (too many small states for the grid sweep)");
@@ -1499,7 +1503,7 @@ static int gradient_device(lb_system* s, cudaStream_t st) {
   }
   if (s->timing) LB_CUDA(cudaEventRecord(s->ev[2], st), "cudaEventRecord");
   if (use_grid(s))
-    LB_CUDA(lbk::launch_backward_grid(s->dp, s->gblocks, s->gsmem, s->hp.ff, st), "backward grid sweep");
+    LB_CUDA(lbk::launch_backward_grid(s->dp, s->gblocks_b, s->gsmem, s->hp.ff, st), "backward grid sweep");
   else if (s->cluster)
     LB_CUDA(lbk::launch_backward_cluster(s->dp, s->M, s->cc, st), "backward cluster kernel");
   else

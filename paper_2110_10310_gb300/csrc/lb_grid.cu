@@ -1008,10 +1008,21 @@ __device__ void grid_fail(const ProbDev& P, int code, int step) {
 
 // mode 0: forward sweep on P.qT (from P.q0 if init), checkpoints if tape
 // mode 1: forward steps j0..j1-1 in place on x; mode 2: adjoint steps j1-1..j0 in place on x
+// Blocks per SM the grid kernels are compiled for (registers per thread:
+// 128 at 2 blocks of 256 threads, 85 at 3).  Measured: three blocks (24
+// warps per SM) make the paired-single kernels 8 % faster on workload 5
+// (vec 531441, 64 states) despite their spills to local memory, whose load
+// latency the extra warps hide; the FP64 kernels gain under 1 % there and
+// lose 2-4 % on the smaller grid workloads (vec 65536 and 6400, a few
+// states), where more blocks only lengthen each grid barrier, so they keep
+// two.
+constexpr int kBlocksPerSM64 = 2;
+constexpr int kBlocksPerSMFF = 3;
+
 // FF: the FP64 iterations apply O in paired single precision (P.ff); the
 // two variants are separate kernels so that each has its own registers
 template <bool FF>
-__global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* __restrict__ pp, int mode, int init,
+__global__ void __launch_bounds__(kGridThreads, FF ? kBlocksPerSMFF : kBlocksPerSM64) k_sweep_grid(const ProbDev* __restrict__ pp, int mode, int init,
                                                              int tape, int j0, int j1, double2* __restrict__ x,
                                                              int nstates) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -1128,7 +1139,8 @@ __global__ void __launch_bounds__(kGridThreads, 2) k_sweep_grid(const ProbDev* _
 // backward sweep over all states: recompute each checkpoint segment, then the
 // adjoint steps with the gradient pieces summed over states and blocks
 template <bool FF>
-__global__ void __launch_bounds__(kGridThreads, 2) k_backward_grid(const ProbDev* __restrict__ pp) {
+__global__ void __launch_bounds__(kGridThreads, FF ? kBlocksPerSMFF : kBlocksPerSM64)
+    k_backward_grid(const ProbDev* __restrict__ pp) {
   extern __shared__ __align__(16) unsigned char smem[];
   const ProbDev& P = *pp;
   const GridSmem S = grid_setup(smem, P, P.M, P.herm);
@@ -1468,20 +1480,16 @@ __global__ void k_objective_states(const ProbDev* __restrict__ pp) {
 
 size_t grid_smem_bytes(int ncoef, int njcoef) { return grid_smem_bytes_impl(ncoef, njcoef); }
 
-int grid_blocks_max(size_t smem) {
-  int dev = 0, nsm = 0, per = 0;
+int grid_blocks(int backward, int ff, size_t smem) {
+  int dev = 0, nsm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-  const void* kernels[] = {(const void*)k_sweep_grid<false>, (const void*)k_backward_grid<false>,
-                           (const void*)k_sweep_grid<true>, (const void*)k_backward_grid<true>};
-  per = 1 << 30;
-  for (const void* k : kernels) {
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-    int a = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k, kGridThreads, smem) != cudaSuccess) return 0;
-    per = a < per ? a : per;
-  }
-  int n = nsm * per;
+  const void* k = backward ? (ff ? (const void*)k_backward_grid<true> : (const void*)k_backward_grid<false>)
+                           : (ff ? (const void*)k_sweep_grid<true> : (const void*)k_sweep_grid<false>);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kGridThreads, smem) != cudaSuccess) return 0;
+  const int n = nsm * per;
   return n < kMaxGridBlocks ? n : kMaxGridBlocks;
 }
 

@@ -173,7 +173,9 @@ cudaError_t launch_propagate_resident(const ProbDev* d_prob, int adjoint, int64_
 constexpr int kGridThreads = 256;
 constexpr int kMaxGridBlocks = 4096;
 // largest cooperative grid of the sweep kernels on the current device
-int grid_blocks_max(size_t smem);
+// blocks of the cooperative launch of the forward (backward = 0) or backward
+// grid kernel in its FP64 (ff = 0) or paired-single form: all resident at once
+int grid_blocks(int backward, int ff, size_t smem);
 size_t grid_smem_bytes(int ncoef, int njcoef);
 // mode 0: forward over [j0, j1) on P.qT (initialised from P.q0 when init_from_q0), checkpoints when tape;
 // mode 1: forward over [j0, j1) in place on x; mode 2: adjoint steps j1-1..j0 in place on x

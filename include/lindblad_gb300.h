@@ -287,7 +287,7 @@ int lb_set_wait_limit(lb_system* sys, int64_t polls);
 
 /* Single-precision difference iterations of the grid sweeps' Jacobi solves
  * (on = 1, the default; 0 = every inner iteration in FP64).  The implicit
- * midpoint step (I - dt/2 M) z = q (Sec. II-B, eq. IMR) is solved by
+ * midpoint step (I - dt/2 M) z = q (Appendix A, eqs. IMR, linsystem_primal) is solved by
  * z_{k+1} = (I - dt/2 D)^-1 (q + c(z_k)), c(z) = (dt/2) O z, O the
  * off-diagonal part of M.  Once every state's last change
  * d_k = z_k - z_{k-1} is below 2^-32 max|q| (and max|q| >= 2^-50), the next
@@ -312,12 +312,11 @@ int lb_set_difference_iterations(lb_system* sys, int32_t on);
  *     with its exact rounding error and the sums carry theirs (two-sum), so
  *     c is within about 2^-48 of the sum of the magnitudes of its terms,
  *     i.e. within about 2^-48 rho |z| where rho < 1 is the Jacobi
- *     contraction bound: a few FP64 roundings of z.  (dt/2) O is the
- *     part of the implicit midpoint step (Sec. II-B) that moves z by about
- *     rho |z| per step, so this keeps z within the solver's tolerance of the
- *     FP64 iteration's while the FP64 pipe, which runs single precision at
- *     64 times its FP64 rate on this GPU, only forms z = (I - dt/2 D)^-1
- *     (q + c).  States, the right-hand side, the diagonal, the objective,
+ *     contraction bound: a few FP64 roundings of z, under the solver's
+ *     tolerance (the off-diagonal part c of the implicit midpoint step,
+ *     Appendix A, is at most about rho |z|).  The FP64 pipe, which runs at
+ *     1/64 of the single-precision rate on this GPU, then only forms
+ *     z = (I - dt/2 D)^-1 (q + c).  States, the right-hand side, the diagonal, the objective,
  *     the gradient pieces and the stopping rule stay FP64.  Systems with
  *     Jaynes-Cummings couplings keep LB_PREC_F64.  Call before
  *     lb_workspace_bytes (the split iterates take 32 bytes per element and

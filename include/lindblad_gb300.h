@@ -336,10 +336,14 @@ int lb_set_precision(lb_system* sys, int32_t precision);
 int lb_system_set_coupling(lb_system* sys, const double* jc_ghz, const double* rot_ghz);
 
 /* Hermitian symmetry (Sec. III-B: density matrices, and Lindblad's equation
- * preserves Hermiticity).  With LB_SYM_HERMITIAN (the default) the grid-wide
- * and one-CTA-per-state sweeps (fixed points and GMRES, whose inner products
- * are then real) iterate only the elements k <= l of every state and write
- * the conjugate into (l, k) -- about half the work -- whenever every initial
+ * preserves Hermiticity).  With LB_SYM_HERMITIAN every sweep kind --
+ * grid-wide, one CTA per state (fixed points and GMRES, whose inner products
+ * are then real) and cluster -- iterates only the elements k <= l of every
+ * state and writes the conjugate into (l, k) (the grid sweeps keep them
+ * packed) -- about half the work; LB_SYM_AUTO (the default) does so in the
+ * grid and one-CTA sweeps but not in the cluster sweep, whose steps are
+ * bound by latency rather than by the number of elements -- whenever every
+ * initial
  * state set by lb_states_set and every explicit target is Hermitian to
  * rounding (each entry within 64 eps max|entry| of the conjugate of its
  * transposed entry; the k <= l entries are then used for both), gate
@@ -349,6 +353,7 @@ int lb_system_set_coupling(lb_system* sys, const double* jc_ghz, const double* r
  * every element.  May be called at any time; applies from the next call. */
 #define LB_SYM_NONE 0
 #define LB_SYM_HERMITIAN 1
+#define LB_SYM_AUTO 2
 int lb_set_symmetry(lb_system* sys, int32_t symmetry);
 
 /* ---- device workspace ---------------------------------------------------- */

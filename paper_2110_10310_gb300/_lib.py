@@ -43,6 +43,7 @@ LB_SOLVER_GMRES = 3
 LB_J_NM = 2
 LB_SYM_NONE = 0
 LB_SYM_HERMITIAN = 1
+LB_SYM_AUTO = 2
 
 LB_MAX_SUBSYSTEMS = 8
 LB_MAX_LEVELS = 64

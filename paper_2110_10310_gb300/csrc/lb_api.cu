@@ -102,7 +102,7 @@ struct lb_system {
   int max_iter = 200;
   int K = 100;       // requested checkpoint interval; < 0 = automatic (effective_K)
   int sweep = LB_SWEEP_AUTO;
-  int symmetry = LB_SYM_HERMITIAN;
+  int symmetry = LB_SYM_AUTO;
   int pred = LB_PRED_AUTO;  // restart period of the forward predictor as requested (lb_set_predictor)
   int pred_order = lbk::kDefaultRingOrder;  // its order (grid and one-CTA sweeps)
   long long spin_limit = 0;  // polls of a grid-barrier wait (0: the kernels' default; lb_set_wait_limit)
@@ -558,11 +558,14 @@ bool hermitian_matrices(const double* a, int M, int N) {
   return true;
 }
 
-// the Hermitian symmetry runs in the grid sweeps and in the one-CTA sweeps
-// (fixed points and GMRES), not in the cluster sweeps
+// the Hermitian symmetry runs in every sweep kind: grid, one CTA per state
+// (fixed points and GMRES) and, when asked for explicitly, cluster (LB_SYM_AUTO
+// leaves it out there: the cluster sweep's steps are bound by latency, not by
+// the number of elements, and the pushes to the mirrors made the three-state
+// gate workload 5 % slower)
 bool use_symmetry(const lb_system* s) {
-  if (s->symmetry != LB_SYM_HERMITIAN || !s->rho_herm || !(s->target_mode == 2 || s->tar_herm)) return false;
-  if (use_grid(s)) return true;
+  if (s->symmetry == LB_SYM_NONE || !s->rho_herm || !(s->target_mode == 2 || s->tar_herm)) return false;
+  if (s->symmetry == LB_SYM_HERMITIAN || use_grid(s)) return true;
   return !s->cluster;
 }
 
@@ -1212,7 +1215,8 @@ int lb_objective_set_penalty(lb_system* s, double gamma1, double a_ns) {
 
 int lb_set_symmetry(lb_system* s, int32_t symmetry) {
   if (!s) return fail(LB_EINVAL, "null system handle");
-  if (symmetry != LB_SYM_NONE && symmetry != LB_SYM_HERMITIAN) return fail(LB_EINVAL, "unknown symmetry");
+  if (symmetry != LB_SYM_NONE && symmetry != LB_SYM_HERMITIAN && symmetry != LB_SYM_AUTO)
+    return fail(LB_EINVAL, "unknown symmetry");
   s->symmetry = symmetry;
   return refresh_symmetry(s);
 }

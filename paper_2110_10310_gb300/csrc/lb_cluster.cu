@@ -169,6 +169,7 @@ __device__ void cl_setup(const ClSmem& S, const ProbDev& P, cg::cluster_group& c
 // one lane's share of one element
 struct ClPlan {
   int v;        // element (vec index) of this lane; 0 when none
+  int vm;       // under the Hermitian symmetry the element's mirror l + N k (k < l), else -1
   bool ev;      // the lane belongs to a real element
   int r;        // lane within the element, 0..L-1
   int q;        // subsystem of this lane's half (0 for padding lanes)
@@ -185,17 +186,31 @@ struct ClPlan {
   double rtol;
 };
 
+// herm: the Hermitian symmetry -- the cluster's lanes take the elements
+// k <= l only (column by column), each pushing its value to its mirror too
 template <int QT, bool CS>
-__device__ ClPlan cl_plan(const ClSmem& S, int C, int crank) {
+__device__ ClPlan cl_plan(const ClSmem& S, int C, int crank, bool herm) {
   constexpr int L = ClLanes<QT, CS>::L;
   const Hdr& H = *S.hdr;
-  const int Vc = (H.V + C - 1) / C;
+  const int Ve = herm ? H.N * (H.N + 1) / 2 : H.V;  // elements the sweep computes
+  const int Vc = (Ve + C - 1) / C;
   const int le = threadIdx.x / L;
   ClPlan pl;
   pl.r = threadIdx.x % L;
-  const int v = crank * Vc + le;
-  pl.ev = le < Vc && v < H.V;
+  const int idx = crank * Vc + le;
+  pl.ev = le < Vc && idx < Ve;
+  int v = idx, vm = -1;
+  if (herm && pl.ev) {
+    // packed index idx = l (l + 1) / 2 + k, k <= l
+    int l = (int)((sqrt(8.0 * idx + 1.0) - 1.0) * 0.5);
+    while ((l + 1) * (l + 2) / 2 <= idx) ++l;
+    while (l * (l + 1) / 2 > idx) --l;
+    const int k = idx - l * (l + 1) / 2;
+    v = k + H.N * l;
+    vm = k != l ? l + H.N * k : -1;
+  }
   pl.v = pl.ev ? v : 0;
+  pl.vm = pl.ev ? vm : -1;
   const int hv = CS ? (pl.r >> 1) : pl.r;  // half index of this lane
   const int u = hv < 2 * QT ? hv : -1;
   pl.act = pl.ev && u >= 0;
@@ -288,6 +303,7 @@ __device__ __forceinline__ ClHist cl_hist_on() {
 // mbarrier.
 struct ClAddr {
   unsigned zb[2], zs[2], mb[2], dsl[2], qsl[2], mbl[2];
+  unsigned zbm[2], zsm[2];  // the element's mirror (Hermitian symmetry)
 };
 __device__ ClAddr cl_addr(const ClSmem& S, const ClPlan& pl, int C, int crank) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -298,6 +314,9 @@ __device__ ClAddr cl_addr(const ClSmem& S, const ClPlan& pl, int C, int crank) {
     A.zb[b] = mapa_u32(smem_u32(S.zb + (size_t)b * V + pl.v), rr0);
     A.mb[b] = mapa_u32(smem_u32(&S.mbar[b]), rr0);
     A.zs[b] = mapa_u32(smem_u32(S.zs + (size_t)b * V + pl.v), rr0);
+    const int vm = pl.vm >= 0 ? pl.vm : pl.v;
+    A.zbm[b] = mapa_u32(smem_u32(S.zb + (size_t)b * V + vm), rr0);
+    A.zsm[b] = mapa_u32(smem_u32(S.zs + (size_t)b * V + vm), rr0);
     A.dsl[b] = mapa_u32(smem_u32(S.dsl + 64 * b + crank * 4 + warp), lr);
     A.qsl[b] = mapa_u32(smem_u32(S.dsl + 64 * b + 32 + crank * 4 + warp), lr);
     A.mbl[b] = mapa_u32(smem_u32(&S.mbar[b]), lr);
@@ -358,14 +377,27 @@ __device__ __forceinline__ int cl_exchange(const ClSmem& S, const ClPlan& pl, co
   const unsigned per = (unsigned)V * 16u + (unsigned)(C * nwarps) * 4u;
   if (threadIdx.x == 0) mbar_arrive_expect_tx(mb_local, spec ? 2u * per : per);
   if (pl.ev && pl.r < C) {
+    // under the Hermitian symmetry the element's mirror gets the conjugate,
+    // so every entry of the replicas is still written once per exchange
+    const bool mir = pl.vm >= 0;
     st_async_f64x2(A.zb[p], z.x, z.y, A.mb[p]);
-    if (spec) st_async_f64x2(A.zs[sb], zn.x, zn.y, A.mb[p]);
+    if (mir) st_async_f64x2(A.zbm[p], z.x, -z.y, A.mb[p]);
+    if (spec) {
+      st_async_f64x2(A.zs[sb], zn.x, zn.y, A.mb[p]);
+      if (mir) st_async_f64x2(A.zsm[sb], zn.x, -zn.y, A.mb[p]);
+    }
     const unsigned dst = smem_u32(S.zb + (size_t)p * V + pl.v);
     const unsigned dsp = smem_u32(S.zs + (size_t)sb * V + pl.v);
+    const unsigned dstm = smem_u32(S.zb + (size_t)p * V + (mir ? pl.vm : pl.v));
+    const unsigned dspm = smem_u32(S.zs + (size_t)sb * V + (mir ? pl.vm : pl.v));
     for (int cc = pl.r + L; cc < C; cc += L) {
       const unsigned mbr = mapa_u32(mb_local, cc);
       st_async_f64x2(mapa_u32(dst, cc), z.x, z.y, mbr);
-      if (spec) st_async_f64x2(mapa_u32(dsp, cc), zn.x, zn.y, mbr);
+      if (mir) st_async_f64x2(mapa_u32(dstm, cc), z.x, -z.y, mbr);
+      if (spec) {
+        st_async_f64x2(mapa_u32(dsp, cc), zn.x, zn.y, mbr);
+        if (mir) st_async_f64x2(mapa_u32(dspm, cc), zn.x, -zn.y, mbr);
+      }
     }
   }
   m = __reduce_max_sync(kFull, m);
@@ -610,6 +642,8 @@ __device__ void cl_objective_part(const ClSmem& S, const ClPlan& pl, const ProbD
   double acc = 0.0;
   if (pl.ev && pl.r == 0) {
     P.qT[base + pl.v] = q;
+    // an off-diagonal element under the symmetry stands for its mirror too
+    if (pl.vm >= 0) P.qT[base + pl.vm] = make_double2(q.x, -q.y);
     const double2 t = P.tar[base + pl.v];
     if (H.kind == LB_J_FROB) {
       const double dr = q.x - t.x, dq = q.y - t.y;
@@ -617,6 +651,7 @@ __device__ void cl_objective_part(const ClSmem& S, const ClPlan& pl, const ProbD
     } else {
       acc = fma(t.x, q.x, t.y * q.y);
     }
+    if (pl.vm >= 0) acc *= 2.0;
   }
   acc = warp_sum(acc);
   const double pw = PEN ? warp_sum(pacc) : 0.0;
@@ -659,7 +694,7 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
   const ClSmem S = cl_carve(smem, P.ncoef, P.njcoef, P.N, P.V);
   cl_setup(S, P, cl);
   const Hdr& H = *S.hdr;
-  const ClPlan pl = cl_plan<QT, CS>(S, C, crank);
+  const ClPlan pl = cl_plan<QT, CS>(S, C, crank, H.herm != 0);
   const ClAddr A = cl_addr(S, pl, C, crank);
   const ClSrc src = cl_src(P, pl, H.cq);
   const size_t base = (size_t)i * H.V;
@@ -696,7 +731,7 @@ __global__ void __launch_bounds__(128, 1) k_forward_cl(const ProbDev* __restrict
     const ClStep st = nx;
     if (j + 1 < NT) nx = cl_step(src, j + 1);
     if (penal) {
-      if (own) pacc = fma(st.pen, cl_merit_summand(H.kind, rhs, tv), pacc);
+      if (own) pacc = fma(st.pen * (pl.vm >= 0 ? 2.0 : 1.0), cl_merit_summand(H.kind, rhs, tv), pacc);
       ppen += st.pen;
     }
     ClHist hn = hist;
@@ -754,7 +789,8 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
   const ClSmem S = cl_carve(smem, P.ncoef, P.njcoef, P.N, P.V);
   cl_setup(S, P, cl);
   const Hdr& H = *S.hdr;
-  const ClPlan pl = cl_plan<QT, CS>(S, C, crank);
+  const bool herm = H.herm != 0;
+  const ClPlan pl = cl_plan<QT, CS>(S, C, crank, herm);
   const ClAddr A = cl_addr(S, pl, C, crank);
   const ClSrc src = cl_src(P, pl, H.cq);
   const int V = H.V, K = H.K, NT = H.NT, Qn = H.Q;  // in registers: H is reloaded after every asm clobber
@@ -891,6 +927,24 @@ __global__ void __launch_bounds__(128, 1) k_backward_cl(const ProbDev* __restric
           si = fma(Z.y, xr, -Z.x * xi);
         }
       }
+      if (herm) {
+        // Hermitian Z and zhat: an off-diagonal element and its mirror add
+        // A - conj(B) to g_a and B - conj(A) to g_ad (A = Z conj(R) on the
+        // R half's lanes, B = Z conj(P) on the P half's), i.e. each half's
+        // value minus the conjugate of the other half's; a diagonal element
+        // has B = -conj(A) already.  The other half of the same subsystem
+        // (and component) is lane r ^ 1, or r ^ 2 with the component split.
+        constexpr int pm = CS ? 2 : 1;
+        const double osr = __shfl_xor_sync(kFull, sr, pm), osi = __shfl_xor_sync(kFull, si, pm);
+        if (gl && pl.vm >= 0 && pl.q < Qn) {
+          if constexpr (CS) {
+            sr = (pl.r & 1) ? sr + osr : sr - osr;
+          } else {
+            sr -= osr;
+            si += osi;
+          }
+        }
+      }
       if constexpr (CS) {
 #pragma unroll
         for (int o = L; o < 32; o <<= 1) sr += __shfl_xor_sync(kFull, sr, o);
@@ -948,7 +1002,7 @@ __global__ void __launch_bounds__(128, 1) k_propagate_cl(const ProbDev* __restri
   const ClSmem S = cl_carve(smem, P.ncoef, P.njcoef, P.N, P.V);
   cl_setup(S, P, cl);
   const Hdr& H = *S.hdr;
-  const ClPlan pl = cl_plan<QT, CS>(S, C, crank);
+  const ClPlan pl = cl_plan<QT, CS>(S, C, crank, false);  // vectors given to lb_propagate may be anything
   const ClAddr A = cl_addr(S, pl, C, crank);
   const ClSrc src = cl_src(P, pl, H.cq);
   double2* xv = x + (size_t)i * H.V;

@@ -60,7 +60,7 @@ class LindbladSystem:
     ckpt_every)."""
 
     def __init__(self, problem, *, solver: int = L.LB_SOLVER_AUTO, rtol: float = 1e-15, max_iter: int = 200,
-                 ckpt_every: int | None = None, sweep: int = L.LB_SWEEP_AUTO, symmetry: int = L.LB_SYM_HERMITIAN,
+                 ckpt_every: int | None = None, sweep: int = L.LB_SWEEP_AUTO, symmetry: int = L.LB_SYM_AUTO,
                  predictor: int = L.LB_PRED_AUTO, pred_order: int = 0, pairing: int = 1,
                  difference_iterations: int = 1, precision: int = L.LB_PREC_F64, device=None, stream=None):
         self.lib = L.load()

@@ -1122,6 +1122,50 @@ def test_resident_hermitian_symmetry_with_gate_targets_penalty_and_coupling():
         assert _rel(g_h, g_f) < 1e-11
 
 
+@pytest.mark.parametrize("levels,K,objective,penalty,coupled", [
+    ((2, 3), 0, "frob", False, False), ((3, 3), 7, "trace", False, False), ((2, 2, 2), 10, "frob", True, False),
+    ((2, 3), 5, "frob", False, True)])
+def test_cluster_hermitian_symmetry_matches_oracle(levels, K, objective, penalty, coupled):
+    """Hermitian states and targets on the cluster sweep: the lanes take the
+    elements k <= l and push each value to its mirror as well; oracle parity,
+    and agreement with the full-element cluster sweep (1e-12 / 1e-11), with
+    checkpoints, the running penalty and a Jaynes-Cummings pair."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.random_problem(921, levels=levels, n_states=3, n_steps=40, T_ns=0.8, amp=0.1, ckpt_every=K,
+                         hermitian=True, objective=objective, gamma2=0.05, jc=0.05 if coupled else 0.0)
+    if penalty:
+        p.gamma1, p.penalty_a = 0.2, 5.0
+    s_h, g_h = _check_problem(p, sweep=L.LB_SWEEP_CLUSTER, symmetry=L.LB_SYM_HERMITIAN)
+    st = s_h.stats()
+    assert st["sweep"] == "cluster" and st["symmetry"] == "hermitian"
+    G_h = s_h.gradient()[0]
+    s_f = _sys(p, sweep=L.LB_SWEEP_CLUSTER, symmetry=L.LB_SYM_NONE)
+    G_f, g_f = s_f.gradient()
+    assert s_f.stats()["symmetry"] == "none"
+    assert abs(G_h - G_f) <= 1e-12 * abs(G_f)
+    assert _rel(g_h, g_f) < 1e-11
+
+
+def test_cluster_hermitian_symmetry_three_gate_states():
+    """The three Hermitian gate states (workload cnot_3states) on the cluster
+    sweep with the symmetry, against the oracle and the full-element sweep."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    p = W.cnot_three_states(n_steps=200)
+    p.system.T_ns = 200.0 * 200 / 10000
+    s_h, g_h = _check_problem(p, sweep=L.LB_SWEEP_CLUSTER, symmetry=L.LB_SYM_HERMITIAN)
+    assert s_h.stats()["symmetry"] == "hermitian"
+    G_h = s_h.gradient()[0]
+    # LB_SYM_AUTO (the default) leaves the cluster sweep on every element
+    s_a = _sys(p, sweep=L.LB_SWEEP_CLUSTER)
+    s_a.gradient()
+    assert s_a.stats()["symmetry"] == "none"
+    G_f, g_f = _sys(p, sweep=L.LB_SWEEP_CLUSTER, symmetry=L.LB_SYM_NONE).gradient()
+    assert abs(G_h - G_f) <= 1e-12 * abs(G_f)
+    assert _rel(g_h, g_f) < 1e-11
+
+
 def test_resident_hermitian_symmetry_not_taken_for_general_states():
     from paper_2110_10310_gb300 import _lib as L
 

@@ -336,21 +336,23 @@ int lb_set_precision(lb_system* sys, int32_t precision);
 int lb_system_set_coupling(lb_system* sys, const double* jc_ghz, const double* rot_ghz);
 
 /* Hermitian symmetry (Sec. III-B: density matrices, and Lindblad's equation
- * preserves Hermiticity).  With LB_SYM_HERMITIAN every sweep kind --
- * grid-wide, one CTA per state (fixed points and GMRES, whose inner products
- * are then real) and cluster -- iterates only the elements k <= l of every
- * state and writes the conjugate into (l, k) (the grid sweeps keep them
- * packed) -- about half the work; LB_SYM_AUTO (the default) does so in the
- * grid and one-CTA sweeps but not in the cluster sweep, whose steps are
- * bound by latency rather than by the number of elements -- whenever every
- * initial
- * state set by lb_states_set and every explicit target is Hermitian to
- * rounding (each entry within 64 eps max|entry| of the conjugate of its
- * transposed entry; the k <= l entries are then used for both), gate
- * targets V rho V^+ being Hermitian with their states; the adjoint
- * states are then Hermitian too and the gradient pieces of the mirrored
- * elements are formed from those of (k, l).  LB_SYM_NONE always iterates
- * every element.  May be called at any time; applies from the next call. */
+ * preserves Hermiticity).  It applies when every initial state set by
+ * lb_states_set and every explicit target is Hermitian to rounding (each
+ * entry within 64 eps max|entry| of the conjugate of its transposed entry;
+ * the k <= l entries are then used for both), gate targets V rho V^+ being
+ * Hermitian with their states.  A sweep under it iterates only the elements
+ * k <= l of every state and writes the conjugate into (l, k) (the grid
+ * sweeps keep them packed): about half the work.  The adjoint states are
+ * then Hermitian too and the gradient pieces of the mirrored elements are
+ * formed from those of (k, l).
+ *   LB_SYM_HERMITIAN: every sweep kind -- grid-wide, one CTA per state
+ *     (fixed points and GMRES, whose inner products are then real) and
+ *     cluster.
+ *   LB_SYM_AUTO (the default): the grid and one-CTA sweeps, not the cluster
+ *     sweep, whose steps are bound by latency rather than by the number of
+ *     elements.
+ *   LB_SYM_NONE: every element is always iterated.
+ * May be called at any time; applies from the next call. */
 #define LB_SYM_NONE 0
 #define LB_SYM_HERMITIAN 1
 #define LB_SYM_AUTO 2
@@ -360,12 +362,12 @@ int lb_set_symmetry(lb_system* sys, int32_t symmetry);
 
 /* Bytes of device memory the system needs (depends on N, M, N_T, Q, the
  * control layout and ckpt_every).  When the grid-wide sweep runs under the
- * Hermitian symmetry (Hermitian states and targets, LB_SYM_HERMITIAN), its
- * checkpoint and segment tapes are sized for the k <= l entries of each
- * state, N (N + 1) / 2 instead of N^2; a workspace bound so refuses later
- * calls (LB_EINVAL, "packed tapes") while the states or targets set since
- * are not Hermitian or the symmetry is switched off, until they are
- * Hermitian again or a new workspace is bound. */
+ * Hermitian symmetry (Hermitian states and targets, LB_SYM_AUTO or
+ * LB_SYM_HERMITIAN), its checkpoint and segment tapes are sized for the
+ * k <= l entries of each state, N (N + 1) / 2 instead of N^2; a workspace
+ * bound so refuses later calls (LB_EINVAL, "packed tapes") while the states
+ * or targets set since are not Hermitian or the symmetry is switched off,
+ * until they are Hermitian again or a new workspace is bound. */
 int lb_workspace_bytes(const lb_system* sys, size_t* bytes);
 
 /* Bind caller-owned device memory (256-byte aligned, >= lb_workspace_bytes)

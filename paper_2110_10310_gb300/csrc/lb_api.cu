@@ -350,11 +350,12 @@ Layout make_layout(const lb_system* s) {
   take(L.bar, grid ? sizeof(GridBar) : 0);
   take(L.hist, c2 * lbk::kRingOrder * M * V);
   take(L.histf, recompute_predicts(s) ? c2 * lbk::kRingOrder * M * V : 0);
-  take(L.Ginv, grid ? c2 * V : 0);
-  take(L.hgp, grid ? c2 * M * V : 0);
-  take(L.hgm, grid ? c2 * M * V : 0);
-  take(L.fgp, grid && recompute_predicts(s) ? c2 * M * V : 0);
-  take(L.fgm, grid && recompute_predicts(s) ? c2 * M * V : 0);
+  // the powers g^m, g^-m of each predictor ring's anchor frame, and 1/g
+  take(L.Ginv, c2 * V);
+  take(L.hgp, c2 * M * V);
+  take(L.hgm, c2 * M * V);
+  take(L.fgp, recompute_predicts(s) ? c2 * M * V : 0);
+  take(L.fgm, recompute_predicts(s) ? c2 * M * V : 0);
   take(L.dfA, grid ? sizeof(float2) * M * V : 0);
   take(L.dfB, grid ? sizeof(float2) * M * V : 0);
   take(L.Dinvf, grid ? sizeof(float2) * V : 0);
@@ -699,7 +700,7 @@ void fill_prob(lb_system* s) {
   P.herm = use_symmetry(s) ? 1 : 0;
   P.hist = at<double2>(s, s->L.hist);
   P.histf = at<double2>(s, s->L.histf);
-  P.Ginv = grid ? at<double2>(s, s->L.Ginv) : nullptr;
+  P.Ginv = at<double2>(s, s->L.Ginv);
   P.hgp = at<double2>(s, s->L.hgp);
   P.hgm = at<double2>(s, s->L.hgm);
   P.fgp = at<double2>(s, s->L.fgp);

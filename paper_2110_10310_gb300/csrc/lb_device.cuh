@@ -31,6 +31,7 @@
 //   synchronisation of an inner iteration.
 
 #include <cmath>
+#include <cstring>
 
 #include <cooperative_groups.h>
 
@@ -133,66 +134,134 @@ __constant__ double kExtrapR[kRingOrder + 1][kRingOrder] = {
     {9, -36, 84, -126, 126, -84, 36, -9, 1, 0},
     {10, -45, 120, -210, 252, -210, 120, -45, 10, -1}};
 
-// The rotated prediction of one element by Horner's rule,
-//   g (w_1 c_{j-1} + g (w_2 c_{j-2} + ... + g w_n c_{j-n})),
-// from the ring of corrections `ring` (entry of slot s at ring[s * stride];
-// `slot` is where the next correction will be recorded, so c_{j-i} is in
-// slot - i modulo kRingOrder) and the element's step factor g.  NO: the
-// order n as a compile-time constant (loads issued together), 0 = runtime n.
+// The ring holds the corrections in the frame of an anchor step,
+// c~_j = g^-m_j c_j with m_j the steps since the anchor and g the element's
+// free step factor, so that the prediction
+//   c_j ~ sum_{i=1..n} w_i g^i c_{j-i} = g^m_j sum_i w_i c~_{j-i}
+// costs one weighted sum of the ring (integer weights, on the integer pipe:
+// wsum_int) and one complex product; the powers g^m and g^-m are kept per
+// element and advanced once per step.  The anchor is the last restart, or
+// moves every kAnchorSteps steps (the ring's entries are then brought to the
+// new frame), so that the powers stay within a few hundred factors of
+// rounding.
+constexpr int kAnchorSteps = 256;
+
+// The extrapolation weights as integers, kExtrapR[n][k-1] = (-1)^(k+1) C(n, k)
+__host__ __device__ constexpr int extrap_weight(int n, int k) {
+  int c = 1;
+  for (int j = 1; j <= k; ++j) c = c * (n - j + 1) / j;
+  return (k & 1) ? c : -c;
+}
+__host__ __device__ __forceinline__ unsigned long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+  return (unsigned long long)__double_as_longlong(x);
+#else
+  unsigned long long u;
+  memcpy(&u, &x, sizeof u);
+  return u;
+#endif
+}
+__host__ __device__ __forceinline__ double dfrom(unsigned long long u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double x;
+  memcpy(&x, &u, sizeof x);
+  return x;
+#endif
+}
+__host__ __device__ __forceinline__ int clz64(unsigned long long a) {
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)a);
+#else
+  return __builtin_clzll(a);
+#endif
+}
+
+// sum_i w_i x_i of NC doubles with the integer weights of the order-NC
+// extrapolation (x_0 the oldest), on the integer pipe (the FP64 pipe bounds
+// the sweeps): every x_i as its 53-bit significand aligned to the largest
+// exponent (the bits below the alignment truncated), the weighted sum exact
+// in 64 bits (|w_i| <= 252 and sum |w_i| < 2^10, so |sum| < 2^63), then
+// truncated to double.  The error is below sum |w_i| 2^-52 max |x_i|, the
+// size of an FP64 multiply-add chain's; sums below the normal range are
+// flushed to zero, and a non-finite x_i gives NaN.
+template <int NC>
+__host__ __device__ __forceinline__ double wsum_int(const double (&x)[NC]) {
+  unsigned long long b[NC];
+  int emax = 1;
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    b[i] = dbits(x[i]);
+    const int e = (int)(b[i] >> 52) & 0x7ff;
+    emax = e > emax ? e : emax;
+  }
+  if (emax == 0x7ff) return dfrom(0x7ff8000000000000ull);
+  long long acc = 0;
+#pragma unroll
+  for (int i = 0; i < NC; ++i) {
+    const int e = (int)(b[i] >> 52) & 0x7ff;
+    const unsigned long long m = (b[i] & 0xfffffffffffffull) | (e ? 0x10000000000000ull : 0ull);
+    const int sh = emax - (e ? e : 1);  // a subnormal has the scale of exponent field 1
+    const long long t = sh < 53 ? (long long)(m >> sh) : 0ll;
+    const int w = extrap_weight(NC, NC - i);
+    acc += (long long)((b[i] >> 63) ? -w : w) * t;
+  }
+  if (acc == 0) return 0.0;
+  const unsigned long long sg = acc < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long a = acc < 0 ? 0ull - (unsigned long long)acc : (unsigned long long)acc;
+  const int lz = clz64(a);
+  a <<= lz;                     // leading bit at 63: the sum is a 2^(emax - 1075 - lz)
+  const int E = emax + 11 - lz;  // its biased exponent
+  if (E <= 0) return dfrom(sg);
+  if (E >= 0x7ff) return dfrom(sg | 0x7ff0000000000000ull);
+  return dfrom(sg | ((unsigned long long)E << 52) | ((a >> 11) & 0xfffffffffffffull));
+}
+
+// sum_{i=1..n} w_i c~_{j-i} of one element (real weights, the ring in the
+// anchor frame); NO: n as a compile-time constant (the sum on the integer
+// pipe), 0 = runtime n (the warm-up steps after a restart, in FP64)
 template <int NO>
-__device__ __forceinline__ double2 rot_extrap_n(const double2* __restrict__ ring, size_t stride, int slot, int n,
-                                                double2 g) {
+__device__ __forceinline__ double2 anchored_sum_n(const double2* __restrict__ ring, size_t stride, int slot, int n) {
   constexpr int NC = NO > 0 ? NO : 1;
   if (NO > 0) n = NO;
   int sl = slot - n;
   if (sl < 0) sl += kRingOrder;
-  double pr, pi;
+  double pr = 0.0, pi = 0.0;
   if constexpr (NO > 0) {
-    double2 c[NC];
+    double cr[NC], ci[NC];
 #pragma unroll
     for (int i = 0; i < NC; ++i) {
       const int s = sl + i < kRingOrder ? sl + i : sl + i - kRingOrder;
-      c[i] = ring[(size_t)s * stride];
+      const double2 c = ring[(size_t)s * stride];
+      cr[i] = c.x;
+      ci[i] = c.y;
     }
-    pr = kExtrapR[NC][NC - 1] * c[0].x;
-    pi = kExtrapR[NC][NC - 1] * c[0].y;
-#pragma unroll
-    for (int i = 1; i < NC; ++i) {
-      const double w = kExtrapR[NC][NC - 1 - i];
-      const double tr = fma(g.x, pr, fma(-g.y, pi, w * c[i].x));
-      const double ti = fma(g.x, pi, fma(g.y, pr, w * c[i].y));
-      pr = tr;
-      pi = ti;
-    }
+    pr = wsum_int<NC>(cr);
+    pi = wsum_int<NC>(ci);
   } else {
-    const double2 c0 = ring[(size_t)sl * stride];
-    pr = kExtrapR[n][n - 1] * c0.x;
-    pi = kExtrapR[n][n - 1] * c0.y;
-    for (int i = n - 1; i >= 1; --i) {
-      sl = sl + 1 < kRingOrder ? sl + 1 : 0;
+    for (int i = n; i >= 1; --i) {
       const double2 c = ring[(size_t)sl * stride];
       const double w = kExtrapR[n][i - 1];
-      const double tr = fma(g.x, pr, fma(-g.y, pi, w * c.x));
-      const double ti = fma(g.x, pi, fma(g.y, pr, w * c.y));
-      pr = tr;
-      pi = ti;
+      pr = fma(w, c.x, pr);
+      pi = fma(w, c.y, pi);
+      sl = sl + 1 < kRingOrder ? sl + 1 : 0;
     }
   }
-  return make_double2(fma(g.x, pr, -g.y * pi), fma(g.x, pi, g.y * pr));
+  return make_double2(pr, pi);
 }
-
-// n recorded corrections (0 < n <= kRingOrder); the orders a sweep runs at
-// in its steady state take the unrolled paths
-__device__ __forceinline__ double2 rot_extrap(const double2* __restrict__ ring, size_t stride, int slot, int n,
-                                              double2 g) {
+__device__ __forceinline__ double2 anchored_sum(const double2* __restrict__ ring, size_t stride, int slot, int n) {
   switch (n) {
-    case 0: return make_double2(0.0, 0.0);
-    case 8: return rot_extrap_n<8>(ring, stride, slot, n, g);
-    case 9: return rot_extrap_n<9>(ring, stride, slot, n, g);
-    case 10: return rot_extrap_n<10>(ring, stride, slot, n, g);
-    default: return rot_extrap_n<0>(ring, stride, slot, n, g);
+    case 8: return anchored_sum_n<8>(ring, stride, slot, n);
+    case 9: return anchored_sum_n<9>(ring, stride, slot, n);
+    case 10: return anchored_sum_n<10>(ring, stride, slot, n);
+    default: return anchored_sum_n<0>(ring, stride, slot, n);
   }
 }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+
 
 // quadratic B-spline of unit knot spacing centred at 0 (Sec. II, eq. rotctrl)
 __device__ __forceinline__ double bspline2(double x) {

@@ -1,8 +1,6 @@
 // Grid-wide cooperative sweeps for states too large for one CTA, and their
 // launchers.
 
-#include <cstring>
-
 #include "lb_device.cuh"
 
 namespace lbk {
@@ -330,21 +328,12 @@ struct StateMax {
 // the banks of the per-state maxima.  Returns the iteration count, -1
 // (max_iter), -2 (NaN/Inf) or -3 (a barrier wait gave up); on success *zout
 // points at the buffer holding z.
-// First-iterate predictor of the grid sweeps: the off-diagonal corrections
-// c = (dt/2) O z of the last n steps, kept per element in a ring (P.hist, or
-// P.histf for the forward predictor of a recompute; each element always
-// handled by the same thread, so no synchronisation is needed) and
-// extrapolated in each element's rotating frame.  The ring holds them in the
-// frame of an anchor step, c~_j = g^-m_j c_j with m_j the steps since the
-// anchor and g the element's free step factor, so that the prediction
-//   c_j ~ sum_{i=1..n} w_i g^i c_{j-i} = g^m_j sum_i w_i c~_{j-i}
-// costs n real-weight multiply-adds and one complex product; the powers g^m
-// and g^-m are kept per element (gp, gm) and advanced once per step.  The
-// anchor is the last restart, or moves every kAnchorSteps steps (the ring's
-// entries are then brought to the new frame), so that the powers stay within
-// a few hundred factors of rounding.
-constexpr int kAnchorSteps = 256;
-
+// First-iterate predictor of the grid sweeps (the anchored ring of
+// lb_device.cuh): the off-diagonal corrections c = (dt/2) O z of the last n
+// steps, kept per element in a ring (P.hist, or P.histf for the forward
+// predictor of a recompute; each element always handled by the same thread,
+// so no synchronisation is needed), with the powers g^m and g^-m of its
+// anchor frame per element (gp, gm).
 struct GridHist {
   double2* ring = nullptr;
   double2* gp = nullptr;  // g^m per element (slab layout)
@@ -361,122 +350,6 @@ struct GridHist {
     m = 0;
   }
 };
-
-// The extrapolation weights as integers, kExtrapR[n][k-1] = (-1)^(k+1) C(n, k)
-__host__ __device__ constexpr int extrap_weight(int n, int k) {
-  int c = 1;
-  for (int j = 1; j <= k; ++j) c = c * (n - j + 1) / j;
-  return (k & 1) ? c : -c;
-}
-__host__ __device__ __forceinline__ unsigned long long dbits(double x) {
-#ifdef __CUDA_ARCH__
-  return (unsigned long long)__double_as_longlong(x);
-#else
-  unsigned long long u;
-  memcpy(&u, &x, sizeof u);
-  return u;
-#endif
-}
-__host__ __device__ __forceinline__ double dfrom(unsigned long long u) {
-#ifdef __CUDA_ARCH__
-  return __longlong_as_double((long long)u);
-#else
-  double x;
-  memcpy(&x, &u, sizeof x);
-  return x;
-#endif
-}
-__host__ __device__ __forceinline__ int clz64(unsigned long long a) {
-#ifdef __CUDA_ARCH__
-  return __clzll((long long)a);
-#else
-  return __builtin_clzll(a);
-#endif
-}
-
-// sum_i w_i x_i of NC doubles with the integer weights of the order-NC
-// extrapolation (x_0 the oldest), on the integer pipe (the FP64 pipe bounds
-// the sweeps): every x_i as its 53-bit significand aligned to the largest
-// exponent (the bits below the alignment truncated), the weighted sum exact
-// in 64 bits (|w_i| <= 252 and sum |w_i| < 2^10, so |sum| < 2^63), then
-// truncated to double.  The error is below sum |w_i| 2^-52 max |x_i|, the
-// size of an FP64 multiply-add chain's; sums below the normal range are
-// flushed to zero, and a non-finite x_i gives NaN.
-template <int NC>
-__host__ __device__ __forceinline__ double wsum_int(const double (&x)[NC]) {
-  unsigned long long b[NC];
-  int emax = 1;
-#pragma unroll
-  for (int i = 0; i < NC; ++i) {
-    b[i] = dbits(x[i]);
-    const int e = (int)(b[i] >> 52) & 0x7ff;
-    emax = e > emax ? e : emax;
-  }
-  if (emax == 0x7ff) return dfrom(0x7ff8000000000000ull);
-  long long acc = 0;
-#pragma unroll
-  for (int i = 0; i < NC; ++i) {
-    const int e = (int)(b[i] >> 52) & 0x7ff;
-    const unsigned long long m = (b[i] & 0xfffffffffffffull) | (e ? 0x10000000000000ull : 0ull);
-    const int sh = emax - (e ? e : 1);  // a subnormal has the scale of exponent field 1
-    const long long t = sh < 53 ? (long long)(m >> sh) : 0ll;
-    const int w = extrap_weight(NC, NC - i);
-    acc += (long long)((b[i] >> 63) ? -w : w) * t;
-  }
-  if (acc == 0) return 0.0;
-  const unsigned long long sg = acc < 0 ? 0x8000000000000000ull : 0ull;
-  unsigned long long a = acc < 0 ? 0ull - (unsigned long long)acc : (unsigned long long)acc;
-  const int lz = clz64(a);
-  a <<= lz;                     // leading bit at 63: the sum is a 2^(emax - 1075 - lz)
-  const int E = emax + 11 - lz;  // its biased exponent
-  if (E <= 0) return dfrom(sg);
-  if (E >= 0x7ff) return dfrom(sg | 0x7ff0000000000000ull);
-  return dfrom(sg | ((unsigned long long)E << 52) | ((a >> 11) & 0xfffffffffffffull));
-}
-
-// sum_{i=1..n} w_i c~_{j-i} of one element (real weights, the ring in the
-// anchor frame); NO: n as a compile-time constant (the sum on the integer
-// pipe), 0 = runtime n (the warm-up steps after a restart, in FP64)
-template <int NO>
-__device__ __forceinline__ double2 anchored_sum_n(const double2* __restrict__ ring, size_t stride, int slot, int n) {
-  constexpr int NC = NO > 0 ? NO : 1;
-  if (NO > 0) n = NO;
-  int sl = slot - n;
-  if (sl < 0) sl += kRingOrder;
-  double pr = 0.0, pi = 0.0;
-  if constexpr (NO > 0) {
-    double cr[NC], ci[NC];
-#pragma unroll
-    for (int i = 0; i < NC; ++i) {
-      const int s = sl + i < kRingOrder ? sl + i : sl + i - kRingOrder;
-      const double2 c = ring[(size_t)s * stride];
-      cr[i] = c.x;
-      ci[i] = c.y;
-    }
-    pr = wsum_int<NC>(cr);
-    pi = wsum_int<NC>(ci);
-  } else {
-    for (int i = n; i >= 1; --i) {
-      const double2 c = ring[(size_t)sl * stride];
-      const double w = kExtrapR[n][i - 1];
-      pr = fma(w, c.x, pr);
-      pi = fma(w, c.y, pi);
-      sl = sl + 1 < kRingOrder ? sl + 1 : 0;
-    }
-  }
-  return make_double2(pr, pi);
-}
-__device__ __forceinline__ double2 anchored_sum(const double2* __restrict__ ring, size_t stride, int slot, int n) {
-  switch (n) {
-    case 8: return anchored_sum_n<8>(ring, stride, slot, n);
-    case 9: return anchored_sum_n<9>(ring, stride, slot, n);
-    case 10: return anchored_sum_n<10>(ring, stride, slot, n);
-    default: return anchored_sum_n<0>(ring, stride, slot, n);
-  }
-}
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
 
 // After a step has converged, for element o (slab offset) at vec index v:
 // bring the correction the last iteration recorded into the anchor frame

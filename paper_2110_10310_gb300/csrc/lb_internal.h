@@ -101,9 +101,9 @@ struct ProbDev {
   unsigned long long* gslots;  // [3][M] per-state |z_new - z| maxima, then [2][M] per-state |q| maxima
   GridBar* bar;
   double2* hist;             // [kRingOrder][M*V] first-iterate predictor history (grid and one-CTA sweeps)
-  double2* Ginv;             // [V] grid sweeps: 1/g, g = (1 + dt/2 D)/(1 - dt/2 D) the free step factor
-  double2* hgp;              // [M*V] grid sweeps: g^m per element of the ring hist's frame (m steps from its anchor)
-  double2* hgm;              // [M*V] grid sweeps: g^-m of the same
+  double2* Ginv;             // [V] 1/g, g = (1 + dt/2 D)/(1 - dt/2 D) the free step factor
+  double2* hgp;              // [M*V] g^m per element of the ring hist's frame (m steps from its anchor)
+  double2* hgm;              // [M*V] g^-m of the same
   double2* fgp;              // [M*V] the same for the ring histf
   double2* fgm;
   double2* histf;            // [kRingOrder][M*V] the forward predictor's history in a recompute (K > 0)

@@ -403,65 +403,114 @@ __device__ int res_solve(const ResSmem& S, const Hdr& H, const Elems<E>& el, con
 }
 
 // Predictor of the first iterate for one CTA's state: the corrections of the
-// previous steps live in the ring P.hist ([kRingOrder][M * V], this state's
-// elements at base + v) and are extrapolated in each element's rotating
-// frame (rot_extrap); every element is read and written by the thread that
-// owns it, so no synchronisation is needed.
+// previous steps live in the anchored ring P.hist ([kRingOrder][M * V], this
+// state's elements at base + v) with the powers g^m, g^-m of its frame
+// (P.hgp, P.hgm) and are extrapolated in each element's rotating frame
+// (anchored_sum); every element is read and written by the thread that owns
+// it, so no synchronisation is needed.
 template <int E>
 struct Pred {
   double2* hist = nullptr;
+  double2* gp = nullptr;  // g^m per element of this state
+  double2* gm = nullptr;  // g^-m
   const double2* D = nullptr;
+  const double2* Ginv = nullptr;
   size_t stride = 0;
   double hh = 0.0;
   int n = 0, slot = 0, cap = kRingOrder;  // cap: the predictor's order
+  int m = 0;                              // steps since the anchor
   __device__ void init(const ProbDev& P, size_t base) {
-    hist = P.hist + base;
+    use(P.hist + base, P.hgp + base, P.hgm + base);
     D = P.D;
+    Ginv = P.Ginv;
     stride = (size_t)P.M * P.V;
     hh = 0.5 * P.h;
-    n = slot = 0;
+    n = slot = m = 0;
     cap = P.pred_order;
   }
-  // pc[e]: the predicted correction of element e (S.dsm holds (I - dt/2 D)^-1)
-  template <bool ADJ>
+  __device__ void use(double2* ring, double2* p, double2* q) {
+    hist = ring;
+    gp = p;
+    gm = q;
+  }
+  __device__ void restart() {
+    n = 0;
+    m = 0;
+  }
+  // pc[e]: the predicted correction of element e; a fresh anchor (n = 0)
+  // resets the element's powers
   __device__ void predict(double2 (&pc)[E], const Elems<E>& el, const ResSmem& S, const Hdr& H, int V) const {
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int v = el_v(el, S, H, e);
       pc[e] = make_double2(0.0, 0.0);
-      if (v < V && n > 0) {
-        const double2 d = S.dsm[v];
-        const double di = ADJ ? -d.y : d.y;
-        pc[e] = rot_extrap(hist + v, stride, slot, n, make_double2(fma(2.0, d.x, -1.0), 2.0 * di));
+      if (v < V) {
+        if (n > 0) {
+          pc[e] = cmul(gp[v], anchored_sum(hist + v, stride, slot, n));
+        } else {
+          gp[v] = make_double2(1.0, 0.0);
+          gm[v] = make_double2(1.0, 0.0);
+        }
       }
     }
   }
-  // record the corrections the last inner iteration computed (fixed points)
-  __device__ void record_c(const double2 (&cl)[E], const Elems<E>& el, const ResSmem& S, const Hdr& H, int V) {
+  // the end of a step: its corrections c into the anchor frame, the powers
+  // advanced by g (S.dsm holds (I - dt/2 D)^-1, so g = 2 S.dsm - 1; ADJ: the
+  // conjugate factor), and every kAnchorSteps steps the anchor moved to the
+  // next step
+  template <bool ADJ>
+  __device__ void commit(const double2 (&c)[E], const Elems<E>& el, const ResSmem& S, const Hdr& H, int V) {
+    const bool re = m + 1 >= kAnchorSteps;
+    const int nn = n < cap ? n + 1 : cap;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int v = el_v(el, S, H, e);
-      if (v < V) hist[(size_t)slot * stride + v] = cl[e];
+      if (v < V) {
+        const double2 gpv = gp[v], gmv = gm[v];
+        hist[(size_t)slot * stride + v] = cmul(c[e], gmv);
+        const double2 d = S.dsm[v], gi = __ldg(Ginv + v);
+        const double2 g = make_double2(fma(2.0, d.x, -1.0), ADJ ? -2.0 * d.y : 2.0 * d.y);
+        double2 np = cmul(gpv, g), nm = cmul(gmv, make_double2(gi.x, ADJ ? -gi.y : gi.y));
+        if (re) {
+          // the next step becomes the anchor: the ring's entries times g^(m+1)
+          int sl = slot;
+          for (int i = 0; i < nn; ++i) {
+            double2* r = hist + (size_t)sl * stride + v;
+            *r = cmul(*r, np);
+            sl = sl > 0 ? sl - 1 : kRingOrder - 1;
+          }
+          np = make_double2(1.0, 0.0);
+          nm = np;
+        }
+        gp[v] = np;
+        gm[v] = nm;
+      }
     }
-    n = n < cap ? n + 1 : cap;
+    n = nn;
     slot = slot + 1 < kRingOrder ? slot + 1 : 0;
+    m = re ? 0 : m + 1;
+  }
+  // record the corrections the last inner iteration computed (fixed points)
+  template <bool ADJ>
+  __device__ void record_c(const double2 (&cl)[E], const Elems<E>& el, const ResSmem& S, const Hdr& H, int V) {
+    commit<ADJ>(cl, el, S, H, V);
   }
   // record c = (I - dt/2 D) z - rhs from the solution (GMRES)
   template <bool ADJ>
   __device__ void record(const double2* zc, const double2 (&rhs)[E], const Elems<E>& el, const ResSmem& S,
                          const Hdr& H, int V) {
+    double2 c[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
       const int v = el_v(el, S, H, e);
+      c[e] = make_double2(0.0, 0.0);
       if (v < V) {
         const double2 z = zc[v], d = __ldg(D + v);
         const double dr = hh * d.x, di = hh * (ADJ ? -d.y : d.y);
-        hist[(size_t)slot * stride + v] = make_double2(z.x - fma(dr, z.x, -di * z.y) - rhs[e].x,
-                                                       z.y - fma(dr, z.y, di * z.x) - rhs[e].y);
+        c[e] = make_double2(z.x - fma(dr, z.x, -di * z.y) - rhs[e].x, z.y - fma(dr, z.y, di * z.x) - rhs[e].y);
       }
     }
-    n = n < cap ? n + 1 : cap;
-    slot = slot + 1 < kRingOrder ? slot + 1 : 0;
+    commit<ADJ>(c, el, S, H, V);
   }
 };
 
@@ -771,8 +820,8 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
     }
     int cur;
     if (pred) {
-      if (R > 0 && j % R == 0) pr.n = 0;
-      pr.template predict<false>(pc, el, S, H, V);
+      if (R > 0 && j % R == 0) pr.restart();
+      pr.predict(pc, el, S, H, V);
     }
     // pc: the prediction in, the last iteration's corrections out
     const int it = res_solve<E, QT, false, GM>(S, H, el, pl, q, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur, pc,
@@ -788,7 +837,7 @@ __global__ void __launch_bounds__(512) k_forward_res(const ProbDev* __restrict__
       if (H.method == LB_SOLVER_GMRES)
         pr.template record<false>(zc, q, el, S, H, V);
       else
-        pr.record_c(pc, el, S, H, V);
+        pr.template record_c<false>(pc, el, S, H, V);
     }
     double2* tp = (tape && H.K == 0) ? P.ckpt + ((size_t)i * H.NT + j) * H.V : nullptr;
 #pragma unroll
@@ -899,16 +948,16 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
         const int v = el_v(el, S, H, e);
         if (v < V) qf[e] = ck[v];
       }
-      const int an = pr.n, aslot = pr.slot;
+      const int an = pr.n, aslot = pr.slot, am = pr.m;
       if (fpred) {
-        pr.hist = P.histf + base;
+        pr.use(P.histf + base, P.fgp + base, P.fgm + base);
         pr.slot = 0;
       }
       for (int j = j0; j < j1; ++j) {
         int cur;
         if (fpred) {
-          if (j % R == 0) pr.n = 0;
-          pr.template predict<false>(pc, el, S, H, V);
+          if (j % R == 0) pr.restart();
+          pr.predict(pc, el, S, H, V);
         }
         const int it = res_solve<E, QT, false, GM>(S, H, el, pl, qf, P.ctab + (size_t)j * H.cq, stop_factor(P, j), cur,
                                                    pc, fpred ? pc : nullptr);
@@ -923,7 +972,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
           if (H.method == LB_SOLVER_GMRES)
             pr.template record<false>(zc, qf, el, S, H, V);
           else
-            pr.record_c(pc, el, S, H, V);
+            pr.template record_c<false>(pc, el, S, H, V);
         }
         double2* sgv = P.seg + ((size_t)i * H.K + (j - j0)) * H.V;
 #pragma unroll
@@ -937,16 +986,17 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
         }
       }
       if (fpred) {
-        pr.hist = P.hist + base;
+        pr.use(P.hist + base, P.hgp + base, P.hgm + base);
         pr.n = an;
         pr.slot = aslot;
+        pr.m = am;
       }
     }
     for (int j = j1 - 1; j >= j0; --j) {
       const double2* ct = P.ctab + (size_t)j * H.cq;
       int cur;
       // (I - dt/2 (M^{j+1/2})^+) zhat^j = qhat^{j+1}   (eq. linsystem_adjoint)
-      if (apred) pr.template predict<true>(pc, el, S, H, V);
+      if (apred) pr.predict(pc, el, S, H, V);
       const int it = res_solve<E, QT, true, GM>(S, H, el, pl, lam, ct, stop_factor(P, j), cur, pc, apred ? pc : nullptr);
       if (it < 0) {
         if (threadIdx.x == 0) record_error(P.status, it == -1 ? LB_ENOTCONV : LB_ENAN, j);
@@ -959,7 +1009,7 @@ __global__ void __launch_bounds__(512) k_backward_res(const ProbDev* __restrict_
         if (H.method == LB_SOLVER_GMRES)
           pr.template record<true>(zh, lam, el, S, H, V);
         else
-          pr.record_c(pc, el, S, H, V);
+          pr.template record_c<true>(pc, el, S, H, V);
       }
       const double2* Zt = H.K > 0 ? P.seg + ((size_t)i * H.K + (j - j0)) * H.V : P.ckpt + ((size_t)i * H.NT + j) * H.V;
       // gradient pieces (eq. reducedgradient): for every subsystem q,

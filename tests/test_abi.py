@@ -160,9 +160,10 @@ def test_workspace_size_accounts_for_checkpoints(lib, K):
             nw = -(-(-(-Vl // C)) * lanes // 32)  # warps per CTA
             per = max(per, C * nw)
         gproj = M * per * NT * 2 * 2 * 16 + NT * 2 * 2 * 16
-        # q0, tar, qT and the ten-slot ring of the first-iterate predictor;
-        # with checkpoints the recompute's forward predictor has a ring of its own
-        rings = 10 if K == 0 else 20
+        # q0, tar, qT and the ten-slot ring of the first-iterate predictor
+        # with the powers g^m, g^-m of its anchor frame; with checkpoints the
+        # recompute's forward predictor has a ring (and powers) of its own
+        rings = 12 if K == 0 else 24
         assert n.value >= tape + gproj + (3 + rings) * state
         assert n.value <= tape + gproj + (3 + rings) * state + 64 * 1024
     finally:

@@ -1,5 +1,6 @@
-"""The grid sweeps' predictor sum on the integer pipe (wsum_int, lb_grid.cu),
-compiled for the host from the kernel source and checked on the CPU.
+"""The predictor sum on the integer pipe (wsum_int, lb_device.cuh, used by the
+grid and one-CTA sweeps), compiled for the host from the kernel source and
+checked on the CPU.
 
 The first iterate of a step extrapolates the last n corrections with the
 weights (-1)^(k+1) C(n, k) (polynomial extrapolation through equally spaced

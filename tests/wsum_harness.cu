@@ -1,8 +1,8 @@
-// Host harness for the grid predictor's integer weighted sum (wsum_int in
-// lb_grid.cu, compiled here from the same source).  Reads lines
-// "n x_0 ... x_{n-1}" with every x_i as the hexadecimal bit pattern of a
-// double (x_0 the oldest ring entry) and prints the bit pattern of the
-// weighted sum, one per line.  n is 8, 9 or 10.
+// Host harness for the predictor's integer weighted sum (wsum_int in
+// lb_device.cuh, compiled here from the same source through lb_grid.cu).
+// Reads lines "n x_0 ... x_{n-1}" with every x_i as the hexadecimal bit
+// pattern of a double (x_0 the oldest ring entry) and prints the bit pattern
+// of the weighted sum, one per line.  n is 8, 9 or 10.
 #include "../paper_2110_10310_gb300/csrc/lb_grid.cu"
 
 #include <cinttypes>

@@ -557,6 +557,33 @@ def test_recompute_repeats_the_forward_predictor_bitwise(sweep, solver):
             assert out[9][2]["phase_iterations"][ph] < st0["phase_iterations"][ph]
 
 
+@pytest.mark.parametrize("sweep", ["resident", "grid"])
+def test_anchored_predictor_keeps_iterations_low_across_anchor_moves(sweep):
+    """The first-iterate predictor keeps its ring in the frame of an anchor
+    step and moves the anchor every 256 steps.  Over the first 1200 steps of
+    the CNOT workload at its dt (four anchor moves, no restarts) forward and
+    adjoint solves converge in about one inner iteration per step, the
+    forward ones far fewer than from the unpredicted first iterate
+    (LB_PRED_NONE switches the forward predictor off; the adjoint's stays),
+    and the gradient is that of the run without the forward predictor."""
+    from paper_2110_10310_gb300 import _lib as L
+
+    sw = {"resident": L.LB_SWEEP_RESIDENT, "grid": L.LB_SWEEP_GRID}[sweep]
+    p = W.prefix(W.config2(), 1200)
+    s = _sys(p, ckpt_every=0, sweep=sw)
+    G, g = s.gradient()
+    st = s.stats()
+    s0 = _sys(p, ckpt_every=0, sweep=sw, predictor=L.LB_PRED_NONE)
+    G0, g0 = s0.gradient()
+    st0 = s0.stats()
+    per = [st["phase_iterations"][ph] / st["phase_steps"][ph] for ph in (0, 2)]
+    per0 = [st0["phase_iterations"][ph] / st0["phase_steps"][ph] for ph in (0, 2)]
+    assert max(per) < 1.3, (per, per0)
+    assert per[0] < 0.6 * per0[0], (per, per0)
+    assert abs(G - G0) <= 1e-12 * abs(G0)
+    assert _rel(g, g0) < 1e-10
+
+
 @pytest.mark.parametrize("sweep", ["resident", "grid", "cluster"])
 def test_control_horizon_longer_than_the_run_matches_oracle(sweep):
     """A run over the first steps of a longer horizon keeps that horizon's
